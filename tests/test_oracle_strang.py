@@ -1,0 +1,79 @@
+"""Pins of the oracle's Strang step (§3.4, Algorithm 3, eq. strang-composition, Table 3).
+
+* The rotated circularly polarised Alfven wave (closed form, reading R15)
+  converges in space at about third order for (p, m) = (3, 3).
+* Temporal self-convergence of the Strang composition is second order (Table 3
+  pattern, on a coarser mesh).
+* Mass is conserved and the divergence metric stays at roundoff on every step.
+* Rejection and retry (reading R3): a too-large step is halved until the raw
+  averages are admissible.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2609_10849_b300 import workloads
+from tests.util import oracle_state
+
+
+def alfven_error(N, tf=0.05, dt=1e-3):
+    wl = workloads.alfven_rotated()
+    o = oracle_state(wl, N, N, 3, 3)
+    for _ in range(int(round(tf / dt))):
+        st, taken, _ = o.strang_step(dt)
+        assert st == 0 and taken == dt
+    tot = 0.0
+    for ci, c in enumerate(("Bx", "By", "Bz")):
+        v, X, Y, W = o.sample(c, 6)
+        tot += np.sum(W * (v - wl["exact_B"](X, Y, t=tf)[ci]) ** 2)
+    for ci, c in enumerate(("ux", "uy", "uz")):
+        v, X, Y, W = o.sample(c, 6)
+        tot += np.sum(W * (v - wl["fields"](X, Y, t=tf)[1 + ci]) ** 2)
+    return math.sqrt(tot)
+
+
+def test_alfven_closed_form_convergence():
+    e = [alfven_error(N) for N in (4, 8)]
+    rate = math.log2(e[0] / e[1])
+    assert 2.6 < rate < 4.0, (e, rate)
+    assert e[1] < 2e-4
+
+
+def test_strang_temporal_order_two():
+    wl = workloads.balsara_vortex(L=5.0)
+    tf = 0.2
+    sols = []
+    for dt in (0.04, 0.02, 0.01):
+        o = oracle_state(wl, 8, 8, 2, 2)
+        for _ in range(int(round(tf / dt))):
+            assert o.strang_step(dt)[0] == 0
+        sols.append(o.get_state()[0][0].copy())
+    d = [np.linalg.norm(sols[i] - sols[i + 1]) for i in range(2)]
+    rate = math.log2(d[0] / d[1])
+    assert 1.8 < rate < 2.2, (d, rate)
+
+
+def test_mass_and_divergence_per_step():
+    wl = workloads.orszag_tang()
+    o = oracle_state(wl, 6, 6, 3, 3)
+    o.set_params(oe_hydro=1, oe_vel=1, pp=1, ar=1, C_eta=0.2, cfl=0.4)
+    d0 = o.diagnostics()
+    for _ in range(4):
+        st, dt, _ = o.strang_step(o.cfl_dt())
+        assert st in (0, 1)
+        d = o.diagnostics()
+        assert abs(d["mass"] - d0["mass"]) <= 1e-14 * d0["mass"]
+        assert d["div_B"] <= 1e-12 * d["B_max"]
+        assert d["rho_min"] > 0 and d["p_min"] > 0
+
+
+def test_rejection_and_retry():
+    wl = workloads.blast()
+    o = oracle_state(wl, 8, 8, 2, 2)
+    o.set_params(pp=1, cfl=0.4)
+    dt = 40 * o.cfl_dt()
+    st, taken, nrej = o.strang_step(dt)
+    assert st == 1 and nrej >= 1 and taken == dt / 2 ** nrej
+    d = o.diagnostics()
+    assert d["rho_min"] > 0 and d["p_min"] > 0
