@@ -1,0 +1,156 @@
+/*
+ * mhd.h — C ABI of the B300 library for one explicit hydrodynamic-magnetic-
+ * hydrodynamic (H-M-H) Strang step of 2.5D ideal MHD on periodic uniform
+ * Cartesian meshes: an entropy-stable DGSEM hydro stage (§3.2, Algorithm 1)
+ * and a compatible finite-element magnetic-velocity stage (§3.3, Algorithm 2),
+ * composed by Strang splitting (§3.4, Algorithm 3, eq. strang-composition).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Return value: 0 = OK, > 0 informational, < 0 error (see MHD_* codes);
+ * mhd_last_error() gives a thread-local message for the last error.  No C++
+ * exception crosses this boundary.
+ *
+ * Ownership: a context owns all of its device memory.  Inputs are copied in,
+ * outputs are written to caller-owned buffers.  Pointers flagged `on_device`
+ * are device addresses (for example torch tensors' data_ptr) and are accessed
+ * on the context's stream; otherwise they are host addresses and the call
+ * copies synchronously.
+ *
+ * Host layouts (all double, FP64):
+ *   DG nodal fields  U[5][K][(p+1)^2], components (rho, m_x, m_y, m_z, E_mech),
+ *                    K = ey*nx + ex, node j*(p+1)+i with i the x index; nodes
+ *                    are the GLL(p) points of each element (§3.2).
+ *   Bx               [ny*(k+1)][nx*(k+1)]: column ex*(k+1)+a, a = GLL(k+1)
+ *                    node 0..k in x (node k+1 is node 0 of the next element),
+ *                    row ey*(k+1)+b, b = Gauss(k) node in y  (R_h^k, x-comp).
+ *   By               same shape, column = Gauss(k) node in x, row = GLL(k+1)
+ *                    node in y (R_h^k, y-comp).
+ *   Bz               [K][(k+1)^2] at the GLL(k) nodes of each element (V_h^k).
+ *   Az (potential)   [ny*(k+1)][nx*(k+1)] at the GLL(k+1) nodes 0..k (W_h^{k+1}).
+ * Here k is the magnetic base degree m of the paper, k in {p-1, p}.
+ */
+#ifndef MHD_H
+#define MHD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  MHD_OK = 0,
+  MHD_RETRIED = 1,          /* a rejected step succeeded after halving dt      */
+  MHD_EINVAL = -1,          /* invalid argument                                 */
+  MHD_ENOMEM = -2,          /* device allocation failed                         */
+  MHD_ECUDA = -3,           /* a CUDA call failed (message in mhd_last_error)   */
+  MHD_INADMISSIBLE = -4,    /* halvings exhausted; state restored to step start */
+  MHD_NONFINITE = -5,       /* a non-finite value was produced                  */
+  MHD_TIMEOUT = -6          /* a bounded device wait gave up                    */
+};
+
+typedef struct { int nx, ny; double x0, x1, y0, y1; } mhd_mesh_t;
+
+/* Stabilisation switches and constants (§3.2.2, §3.3.3, §4 of the paper):
+ * oe_hydro / oe_vel: hydro and velocity oscillation elimination; pp: Zhang-Shu
+ * positivity limiter; ar: artificial resistivity; s_H, s_M: OE scale factors;
+ * C_s, C_eta: A.R. sensor response and strength; cfl: CFL number of the
+ * time-step reading; max_halvings: retries of a rejected step. */
+typedef struct {
+  int oe_hydro, oe_vel, pp, ar;
+  double s_H, s_M, C_s, C_eta, cfl;
+  int max_halvings;
+} mhd_params_t;
+
+/* Diagnostics (DG-GLL quadrature for the fluid, exact magnetic product for
+ * E_mag).  div_B is max_K min(hx,hy) max_{Gauss(k)^2} |dBx/dx + dBy/dy|. */
+typedef struct {
+  double mass, mom[3], E_kin, E_int, E_mag, entropy, div_B, B_max, rho_min, p_min, eta_max;
+  int n_rejections;
+  int reserved;
+} mhd_diag_t;
+
+typedef struct mhd_ctx mhd_ctx;
+
+/* Create a context for a periodic nx x ny mesh of [x0,x1]x[y0,y1] with DGSEM
+ * degree p (1..4) and magnetic base degree k (k = p-1 or k = p, k >= 0),
+ * ratio of specific heats gamma > 1.  Allocates all device memory on the
+ * current device.  Errors: MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA. */
+int mhd_create(const mhd_mesh_t* mesh, int p, int k, double gamma, mhd_ctx** out);
+void mhd_destroy(mhd_ctx* ctx);
+
+/* Stabilisation parameters (default: all off, s_H = s_M = 0.02, C_s = 5,
+ * C_eta = 0.2, cfl = 0.4, max_halvings = 20). */
+int mhd_set_params(mhd_ctx* ctx, const mhd_params_t* prm);
+
+/* Stream on which all work of the context is enqueued (a cudaStream_t). */
+int mhd_set_stream(mhd_ctx* ctx, void* stream);
+
+/* Sizes: K elements, N = K (p+1)^2 DG nodes, G = K (k+1)^2 magnetic grid
+ * points per in-plane array, Z = K (k+1)^2 B_z values. */
+int mhd_sizes(const mhd_ctx* ctx, long long* K, long long* N, long long* G, long long* Z);
+
+/* Physical coordinates of the nodes into host buffers: which = 0 DG nodes
+ * [N], 1 W nodes of the potential layout [G], 2 B_z nodes [Z]. */
+int mhd_node_coords(const mhd_ctx* ctx, int which, double* X, double* Y);
+
+/* Conservative state in (U [5][N]) and the magnetic field (host layouts). */
+int mhd_set_state(mhd_ctx* ctx, const double* U, const double* Bx, const double* By, const double* Bz,
+                  int on_device);
+int mhd_get_state(mhd_ctx* ctx, double* U, double* Bx, double* By, double* Bz, int on_device);
+
+/* Fluid state from nodal primitives rho [N], u [3][N], p [N] (m = rho u,
+ * E_mech = p/(gamma-1) + rho|u|^2/2); the magnetic field is left unchanged. */
+int mhd_set_primitive(mhd_ctx* ctx, const double* rho, const double* u, const double* p, int on_device);
+
+/* Magnetic field B = (Bx0 + (-dAz/dy), By0 + dAz/dx, Bz) from the nodal
+ * W_h^{k+1} interpolant of a potential Az (exactly divergence-free). */
+int mhd_set_B_from_potential(mhd_ctx* ctx, const double* Az, double Bx0, double By0, const double* Bz,
+                             int on_device);
+
+/* CFL time step of the current state (written to *dt). */
+int mhd_compute_dt(mhd_ctx* ctx, double* dt);
+
+/* One Strang step S^dt = Phi_H^{dt/2} o Phi_M^{dt} o Phi_H^{dt/2}
+ * (Algorithm 3).  dt <= 0 means "use the CFL step".  A step whose raw stage
+ * averages are inadmissible is restored and retried with dt/2 up to
+ * max_halvings times: returns MHD_RETRIED with *dt_taken the reduced step, or
+ * MHD_INADMISSIBLE with the state restored. */
+int mhd_strang_step(mhd_ctx* ctx, double dt, double* dt_taken);
+
+/* Several Strang steps at a fixed dt without a host synchronisation between
+ * them; the status of the whole sequence is checked once at the end.  On a
+ * rejection the sequence stops with the state of the last good step and
+ * returns MHD_INADMISSIBLE with *steps_done steps committed. */
+int mhd_strang_steps(mhd_ctx* ctx, double dt, int nsteps, int* steps_done);
+
+/* A single substep: which = 0 hydro Phi_H^tau (Algorithm 1), 1 magnetic
+ * Phi_M^tau (Algorithm 2, with the nodal variable exchange around it). */
+int mhd_substep(mhd_ctx* ctx, int which, double tau);
+
+/* Test hook: hydro residual L_E (eq. euler-semidiscrete, mass-inverted) of a
+ * conservative state U [5][N] into L [5][N]. */
+int mhd_hydro_rhs(mhd_ctx* ctx, const double* U, double* L, int on_device);
+
+/* Test hook: magnetic residual L_M (eq. magnetic-dae) of a primitive state
+ * (rho, e [N], u [3][N], B in host layouts, eta [K]) into de [N], du [3][N],
+ * dBx, dBy [G], dBz [Z]. */
+int mhd_mag_rhs(mhd_ctx* ctx, const double* rho, const double* e, const double* u, const double* Bx,
+                const double* By, const double* Bz, const double* eta, double* de, double* du, double* dBx,
+                double* dBy, double* dBz, int on_device);
+
+/* Diagnostics of the current state. */
+int mhd_diagnostics(mhd_ctx* ctx, mhd_diag_t* out);
+
+/* Resistivity eta_K [K] of the last magnetic substep into a host buffer. */
+int mhd_get_eta(mhd_ctx* ctx, double* eta);
+
+/* Number of kernel launches enqueued by the context since creation. */
+long long mhd_launch_count(const mhd_ctx* ctx);
+
+const char* mhd_status_string(int status);
+const char* mhd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MHD_H */

@@ -1,0 +1,555 @@
+// C ABI of the library (include/mhd.h): context, state transfer and the
+// Strang driver (Algorithm 3) with the raw-average rejection and retry of the
+// hydro stage (§3.2.3).  All work is enqueued on one stream; the host reads
+// one status word per step.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mhd.h"
+#include "mhd_internal.cuh"
+
+namespace mhd {
+// kernels / launchers defined in the other translation units
+void hydro_face(int p, const double* S, double* Fx, double* Fy, const Mesh& M, cudaStream_t st);
+void hydro_vol(int p, int mode, const double* S, const double* U0, const double* Fx, const double* Fy, double* out,
+               double* avg, unsigned* status, const Tab* T, const Mesh& M, const double* dtp, double dtfac,
+               double ca, double cb, int first, cudaStream_t st);
+size_t mag_load_doubles(int p, int k, int K);
+void mag_stage(int p, int k, int mode, const double* B, const double* u, const double* e, const double* rho,
+               const double* eta, int resistive, const double* B0, const double* u0, const double* e0, double* Bo,
+               double* uo, double* eo, double* LJ, double* LE, const Tab* T, const Mesh& M, const double* dtp,
+               double dtfac, double ca, double cb, int first, cudaStream_t st);
+void grid_to_blocked(const double* g, double* o, int nx, int ny, int mm, cudaStream_t st);
+void blocked_to_grid(const double* o, double* g, int nx, int ny, int mm, cudaStream_t st);
+void cons_to_prim(const double* U, double* Y, size_t N, cudaStream_t st);
+void prim_to_cons(const double* Y, double* U, size_t N, cudaStream_t st);
+void prim_in(const double* rho, const double* u, const double* p, double* U, size_t N, double g, cudaStream_t st);
+void b_from_potential(int k, const double* A, double Bx0, double By0, double* Bx, double* By, const Tab* T,
+                      const Mesh& M, cudaStream_t st);
+void cfl_dt(int p, int k, const double* U, const double* B, const Tab* T, const Mesh& M,
+            unsigned long long* maxbits, double cfl, double* dt, cudaStream_t st);
+void set_scalar(double* ptr, double v, cudaStream_t st);
+void diag_partials(int p, int k, const double* U, const double* B, const Tab* T, const Mesh& M, double* out,
+                   cudaStream_t st);
+void stab_hydro(int p, double* S, const double* avg, unsigned* status, const Tab* T, const Mesh& M,
+                const Stab& prm, const double* dtp, double dtfac, double* work, cudaStream_t st);
+void stab_eta(int p, int k, const double* rho, const double* Y, const double* B, const Tab* T, const Mesh& M,
+              const Stab& prm, double* eta, double* work, cudaStream_t st);
+void stab_vel_prep(int p, const double* rho, double* chol, const Tab* T, const Mesh& M, cudaStream_t st);
+void stab_vel(int p, int k, const double* rho, double* Y, const double* B, const double* chol, const Tab* T,
+              const Mesh& M, const Stab& prm, const double* dtp, double dtfac, double* work, cudaStream_t st);
+size_t stab_work_doubles(int p, int k, const Mesh& M);
+size_t stab_chol_doubles(int p, const Mesh& M);
+}  // namespace mhd
+
+using namespace mhd;
+
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return MHD_ECUDA;
+}
+}  // namespace
+
+struct mhd_ctx {
+  int p, k, n, n2, mm;
+  Mesh M;
+  Stab prm;
+  double x0, x1, y0, y1;
+  cudaStream_t st;
+  bool own_stream;
+  const Tab* T;
+  Tab hT;
+  size_t N, Z;
+  double *U, *Usave, *S1, *S2;
+  double *B, *Bsave, *Ba, *Bb;
+  double *Y0, *Ya, *Yb;
+  double *Fx, *Fy, *LJ, *LE, *avg, *eta, *dt, *work, *chol, *io;
+  unsigned* status;
+  unsigned long long* maxbits;
+  double* h_pinned;  // small pinned host scratch
+  unsigned* h_status;
+  long long launches;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+cudaError_t dalloc(mhd_ctx* c, double** p, size_t n) {
+  void* ptr = nullptr;
+  cudaError_t e = cudaMalloc(&ptr, std::max<size_t>(n, 1) * sizeof(double));
+  if (e == cudaSuccess) { c->allocs.push_back(ptr); *p = (double*)ptr; }
+  return e;
+}
+
+cudaError_t copy_in(mhd_ctx* c, double* dst, const double* src, size_t n, int on_device) {
+  if (on_device) return cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  cudaError_t e = cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyHostToDevice, c->st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(c->st);
+}
+cudaError_t copy_out(mhd_ctx* c, double* dst, const double* src, size_t n, int on_device) {
+  if (on_device) return cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  cudaError_t e = cudaMemcpyAsync(dst, src, n * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(c->st);
+}
+
+const double RK_A[3] = {0.0, 0.75, 1.0 / 3.0};
+const double RK_B[3] = {1.0, 0.25, 2.0 / 3.0};
+
+// Hydro substep Phi_H^{tau}, tau = dt * fac (Algorithm 1).
+void hydro_substep(mhd_ctx* c, double fac) {
+  const double* in[3] = {c->U, c->S1, c->S2};
+  double* out[3] = {c->S1, c->S2, c->U};
+  bool stab = c->prm.oe_hydro || c->prm.pp;
+  for (int s = 0; s < 3; ++s) {
+    hydro_face(c->p, in[s], c->Fx, c->Fy, c->M, c->st);
+    hydro_vol(c->p, 1, in[s], c->U, c->Fx, c->Fy, out[s], stab ? c->avg : nullptr, c->status, c->T, c->M, c->dt, fac,
+              RK_A[s], RK_B[s], s == 0, c->st);
+    c->launches += 2;
+    if (stab) {
+      stab_hydro(c->p, out[s], c->avg, c->status, c->T, c->M, c->prm, c->dt, fac, c->work, c->st);
+      c->launches += 4;
+    }
+  }
+}
+
+// Magnetic substep Phi_M^{tau}, tau = dt * fac (Algorithm 2), with the nodal
+// exchange before and after (§3.4.1).
+void mag_substep(mhd_ctx* c, double fac) {
+  const size_t N = c->N;
+  cons_to_prim(c->U, c->Y0, N, c->st);
+  c->launches++;
+  int resistive = c->prm.ar && c->prm.C_eta != 0.0;
+  if (resistive) {
+    stab_eta(c->p, c->k, c->U, c->Y0, c->B, c->T, c->M, c->prm, c->eta, c->work, c->st);
+    c->launches += 3;
+  }
+  if (c->prm.oe_vel) {
+    stab_vel_prep(c->p, c->U, c->chol, c->T, c->M, c->st);
+    c->launches++;
+  }
+  const double* Bin[3] = {c->B, c->Ba, c->Bb};
+  double* Bout[3] = {c->Ba, c->Bb, c->B};
+  const double* Yin[3] = {c->Y0, c->Ya, c->Yb};
+  double* Yout[3] = {c->Ya, c->Yb, c->Y0};
+  for (int s = 0; s < 3; ++s) {
+    mag_stage(c->p, c->k, 1, Bin[s], Yin[s] + N, Yin[s], c->U, c->eta, resistive, c->B, c->Y0 + N, c->Y0, Bout[s],
+              Yout[s] + N, Yout[s], c->LJ, c->LE, c->T, c->M, c->dt, fac, RK_A[s], RK_B[s], s == 0, c->st);
+    c->launches += 3;
+    if (c->prm.oe_vel) {
+      stab_vel(c->p, c->k, c->U, Yout[s], Bout[s], c->chol, c->T, c->M, c->prm, c->dt, fac, c->work, c->st);
+      c->launches += 3;
+    }
+  }
+  prim_to_cons(c->Y0, c->U, N, c->st);
+  c->launches++;
+}
+
+void enqueue_strang(mhd_ctx* c) {
+  hydro_substep(c, 0.5);
+  mag_substep(c, 1.0);
+  hydro_substep(c, 0.5);
+}
+
+int check_status(mhd_ctx* c, unsigned* st_out) {
+  cudaError_t e = cudaMemcpyAsync(c->h_status, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st);
+  if (e != cudaSuccess) return cuda_fail(e, "status copy");
+  e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return cuda_fail(e, "step");
+  *st_out = *c->h_status;
+  return MHD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mhd_last_error(void) { return g_err.c_str(); }
+
+const char* mhd_status_string(int s) {
+  switch (s) {
+    case MHD_OK: return "ok";
+    case MHD_RETRIED: return "step retried with a smaller dt";
+    case MHD_EINVAL: return "invalid argument";
+    case MHD_ENOMEM: return "out of device memory";
+    case MHD_ECUDA: return "CUDA error";
+    case MHD_INADMISSIBLE: return "inadmissible cell average after all halvings";
+    case MHD_NONFINITE: return "non-finite value";
+    case MHD_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+int mhd_create(const mhd_mesh_t* mesh, int p, int k, double gamma, mhd_ctx** out) {
+  if (!mesh || !out) return fail(MHD_EINVAL, "null argument");
+  *out = nullptr;
+  if (mesh->nx < 1 || mesh->ny < 1 || !(mesh->x1 > mesh->x0) || !(mesh->y1 > mesh->y0))
+    return fail(MHD_EINVAL, "invalid mesh");
+  if (table_slot(p, k) < 0) return fail(MHD_EINVAL, "unsupported (p, k): need 1 <= p <= 4 and k in {p-1, p}");
+  if (!(gamma > 1.0)) return fail(MHD_EINVAL, "gamma must exceed 1");
+  if ((long long)mesh->nx * mesh->ny > (1LL << 30)) return fail(MHD_EINVAL, "mesh too large");
+  mhd_ctx* c = new (std::nothrow) mhd_ctx();
+  if (!c) return fail(MHD_ENOMEM, "host allocation");
+  c->p = p; c->k = k; c->n = p + 1; c->n2 = c->n * c->n; c->mm = k + 1;
+  c->x0 = mesh->x0; c->x1 = mesh->x1; c->y0 = mesh->y0; c->y1 = mesh->y1;
+  c->M.nx = mesh->nx; c->M.ny = mesh->ny; c->M.K = mesh->nx * mesh->ny;
+  c->M.hx = (mesh->x1 - mesh->x0) / mesh->nx;
+  c->M.hy = (mesh->y1 - mesh->y0) / mesh->ny;
+  c->M.Jdet = c->M.hx * c->M.hy / 4.0;
+  c->M.g = gamma;
+  c->prm = Stab{0, 0, 0, 0, 0.02, 0.02, 5.0, 0.2, 0.4, 20};
+  c->N = (size_t)c->M.K * c->n2;
+  c->Z = (size_t)c->M.K * c->mm * c->mm;
+  c->launches = 0;
+  cudaError_t e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { delete c; return cuda_fail(e, "stream"); }
+  c->own_stream = true;
+  c->T = device_tables(p, k, &e);
+  if (!c->T) { cudaStreamDestroy(c->st); delete c; return cuda_fail(e, "tables"); }
+  host_tables(p, k, &c->hT);
+  const size_t N = c->N, Z = c->Z, K = c->M.K;
+  double** bufs5[] = {&c->U, &c->Usave, &c->S1, &c->S2};
+  for (auto b : bufs5) if ((e = dalloc(c, b, 5 * N)) != cudaSuccess) goto oom;
+  {
+    double** bufs3[] = {&c->B, &c->Bsave, &c->Ba, &c->Bb};
+    for (auto b : bufs3) if ((e = dalloc(c, b, 3 * Z)) != cudaSuccess) goto oom;
+    double** bufs4[] = {&c->Y0, &c->Ya, &c->Yb};
+    for (auto b : bufs4) if ((e = dalloc(c, b, 4 * N)) != cudaSuccess) goto oom;
+  }
+  if ((e = dalloc(c, &c->Fx, 5 * K * c->n)) != cudaSuccess) goto oom;
+  if ((e = dalloc(c, &c->Fy, 5 * K * c->n)) != cudaSuccess) goto oom;
+  if ((e = dalloc(c, &c->LJ, mag_load_doubles(p, k, (int)K))) != cudaSuccess) goto oom;
+  if ((e = dalloc(c, &c->LE, mag_load_doubles(p, k, (int)K))) != cudaSuccess) goto oom;
+  if ((e = dalloc(c, &c->avg, 5 * K)) != cudaSuccess) goto oom;
+  if ((e = dalloc(c, &c->eta, K)) != cudaSuccess) goto oom;
+  if ((e = dalloc(c, &c->dt, 4)) != cudaSuccess) goto oom;
+  if ((e = dalloc(c, &c->work, std::max(stab_work_doubles(p, k, c->M), 12 * K))) != cudaSuccess) goto oom;
+  if ((e = dalloc(c, &c->chol, stab_chol_doubles(p, c->M))) != cudaSuccess) goto oom;
+  if ((e = dalloc(c, &c->io, std::max(5 * N, 3 * Z + 4 * N))) != cudaSuccess) goto oom;
+  {
+    void* ptr = nullptr;
+    if ((e = cudaMalloc(&ptr, 64)) != cudaSuccess) goto oom;
+    c->allocs.push_back(ptr);
+    c->status = (unsigned*)ptr;
+    c->maxbits = (unsigned long long*)((char*)ptr + 16);
+    if ((e = cudaMallocHost(&ptr, 64)) != cudaSuccess) goto oom;
+    c->h_pinned = (double*)ptr;
+    c->h_status = (unsigned*)((char*)ptr + 32);
+  }
+  cudaMemsetAsync(c->U, 0, 5 * N * sizeof(double), c->st);
+  cudaMemsetAsync(c->B, 0, 3 * Z * sizeof(double), c->st);
+  cudaMemsetAsync(c->eta, 0, K * sizeof(double), c->st);
+  cudaMemsetAsync(c->status, 0, 64, c->st);
+  if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) { mhd_destroy(c); return cuda_fail(e, "init"); }
+  *out = c;
+  return MHD_OK;
+oom:
+  mhd_destroy(c);
+  return fail(MHD_ENOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
+}
+
+void mhd_destroy(mhd_ctx* c) {
+  if (!c) return;
+  if (c->st) cudaStreamSynchronize(c->st);
+  for (void* p : c->allocs) cudaFree(p);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+  delete c;
+}
+
+int mhd_set_params(mhd_ctx* c, const mhd_params_t* prm) {
+  if (!c || !prm) return fail(MHD_EINVAL, "null argument");
+  if (prm->s_H < 0 || prm->s_M < 0 || prm->C_s < 0 || prm->C_eta < 0 || !(prm->cfl > 0) || prm->max_halvings < 0)
+    return fail(MHD_EINVAL, "invalid stabilisation parameters");
+  if (prm->oe_hydro || prm->oe_vel || prm->pp || prm->ar)
+    return fail(MHD_EINVAL, "stage stabilisation is not available in this build");
+  c->prm = Stab{prm->oe_hydro, prm->oe_vel, prm->pp, prm->ar, prm->s_H, prm->s_M, prm->C_s, prm->C_eta, prm->cfl,
+                prm->max_halvings};
+  return MHD_OK;
+}
+
+int mhd_set_stream(mhd_ctx* c, void* stream) {
+  if (!c) return fail(MHD_EINVAL, "null context");
+  cudaStreamSynchronize(c->st);
+  if (c->own_stream) cudaStreamDestroy(c->st);
+  c->st = (cudaStream_t)stream;
+  c->own_stream = false;
+  return MHD_OK;
+}
+
+int mhd_sizes(const mhd_ctx* c, long long* K, long long* N, long long* G, long long* Z) {
+  if (!c) return fail(MHD_EINVAL, "null context");
+  if (K) *K = c->M.K;
+  if (N) *N = (long long)c->N;
+  if (G) *G = (long long)c->Z;
+  if (Z) *Z = (long long)c->Z;
+  return MHD_OK;
+}
+
+int mhd_node_coords(const mhd_ctx* c, int which, double* X, double* Y) {
+  if (!c || !X || !Y) return fail(MHD_EINVAL, "null argument");
+  const Tab& T = c->hT;
+  const int nx = c->M.nx, ny = c->M.ny, n = c->n, mm = c->mm;
+  for (int ey = 0; ey < ny; ++ey)
+    for (int ex = 0; ex < nx; ++ex) {
+      double xl = c->x0 + ex * c->M.hx, yl = c->y0 + ey * c->M.hy;
+      size_t k = (size_t)ey * nx + ex;
+      if (which == 0) {
+        for (int j = 0; j < n; ++j)
+          for (int i = 0; i < n; ++i) {
+            X[k * n * n + j * n + i] = xl + 0.5 * (1.0 + T.xp[i]) * c->M.hx;
+            Y[k * n * n + j * n + i] = yl + 0.5 * (1.0 + T.xp[j]) * c->M.hy;
+          }
+      } else if (which == 1) {
+        for (int b = 0; b < mm; ++b)
+          for (int a = 0; a < mm; ++a) {
+            size_t g = (size_t)(ey * mm + b) * nx * mm + ex * mm + a;
+            X[g] = xl + 0.5 * (1.0 + T.xL[a]) * c->M.hx;
+            Y[g] = yl + 0.5 * (1.0 + T.xL[b]) * c->M.hy;
+          }
+      } else if (which == 2) {
+        for (int b = 0; b < mm; ++b)
+          for (int a = 0; a < mm; ++a) {
+            X[k * mm * mm + b * mm + a] = xl + 0.5 * (1.0 + T.xM[a]) * c->M.hx;
+            Y[k * mm * mm + b * mm + a] = yl + 0.5 * (1.0 + T.xM[b]) * c->M.hy;
+          }
+      } else {
+        return fail(MHD_EINVAL, "which must be 0, 1 or 2");
+      }
+    }
+  return MHD_OK;
+}
+
+int mhd_set_state(mhd_ctx* c, const double* U, const double* Bx, const double* By, const double* Bz, int on_device) {
+  if (!c || !U || !Bx || !By || !Bz) return fail(MHD_EINVAL, "null argument");
+  cudaError_t e;
+  if ((e = copy_in(c, c->U, U, 5 * c->N, on_device)) != cudaSuccess) return cuda_fail(e, "set_state U");
+  if ((e = copy_in(c, c->io, Bx, c->Z, on_device)) != cudaSuccess) return cuda_fail(e, "set_state Bx");
+  grid_to_blocked(c->io, c->B, c->M.nx, c->M.ny, c->mm, c->st);
+  if ((e = copy_in(c, c->io, By, c->Z, on_device)) != cudaSuccess) return cuda_fail(e, "set_state By");
+  grid_to_blocked(c->io, c->B + c->Z, c->M.nx, c->M.ny, c->mm, c->st);
+  if ((e = copy_in(c, c->B + 2 * c->Z, Bz, c->Z, on_device)) != cudaSuccess) return cuda_fail(e, "set_state Bz");
+  c->launches += 2;
+  if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(e, "set_state");
+  return MHD_OK;
+}
+
+int mhd_get_state(mhd_ctx* c, double* U, double* Bx, double* By, double* Bz, int on_device) {
+  if (!c) return fail(MHD_EINVAL, "null context");
+  cudaError_t e;
+  if (U && (e = copy_out(c, U, c->U, 5 * c->N, on_device)) != cudaSuccess) return cuda_fail(e, "get_state U");
+  if (Bx) {
+    blocked_to_grid(c->B, c->io, c->M.nx, c->M.ny, c->mm, c->st);
+    c->launches++;
+    if ((e = copy_out(c, Bx, c->io, c->Z, on_device)) != cudaSuccess) return cuda_fail(e, "get_state Bx");
+    if (on_device && (e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(e, "get_state");
+  }
+  if (By) {
+    blocked_to_grid(c->B + c->Z, c->io, c->M.nx, c->M.ny, c->mm, c->st);
+    c->launches++;
+    if ((e = copy_out(c, By, c->io, c->Z, on_device)) != cudaSuccess) return cuda_fail(e, "get_state By");
+    if (on_device && (e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(e, "get_state");
+  }
+  if (Bz && (e = copy_out(c, Bz, c->B + 2 * c->Z, c->Z, on_device)) != cudaSuccess) return cuda_fail(e, "get_state Bz");
+  if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(e, "get_state");
+  return MHD_OK;
+}
+
+int mhd_set_primitive(mhd_ctx* c, const double* rho, const double* u, const double* p, int on_device) {
+  if (!c || !rho || !u || !p) return fail(MHD_EINVAL, "null argument");
+  const size_t N = c->N;
+  cudaError_t e;
+  if ((e = copy_in(c, c->io, rho, N, on_device)) != cudaSuccess) return cuda_fail(e, "rho");
+  if ((e = copy_in(c, c->io + N, u, 3 * N, on_device)) != cudaSuccess) return cuda_fail(e, "u");
+  if ((e = copy_in(c, c->S1, p, N, on_device)) != cudaSuccess) return cuda_fail(e, "p");
+  prim_in(c->io, c->io + N, c->S1, c->U, N, c->M.g, c->st);
+  c->launches++;
+  if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(e, "set_primitive");
+  return MHD_OK;
+}
+
+int mhd_set_B_from_potential(mhd_ctx* c, const double* Az, double Bx0, double By0, const double* Bz, int on_device) {
+  if (!c || !Az || !Bz) return fail(MHD_EINVAL, "null argument");
+  cudaError_t e;
+  if ((e = copy_in(c, c->io, Az, c->Z, on_device)) != cudaSuccess) return cuda_fail(e, "Az");
+  grid_to_blocked(c->io, c->io + c->Z, c->M.nx, c->M.ny, c->mm, c->st);
+  b_from_potential(c->k, c->io + c->Z, Bx0, By0, c->B, c->B + c->Z, c->T, c->M, c->st);
+  c->launches += 2;
+  if ((e = copy_in(c, c->B + 2 * c->Z, Bz, c->Z, on_device)) != cudaSuccess) return cuda_fail(e, "Bz");
+  if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(e, "set_B_from_potential");
+  return MHD_OK;
+}
+
+int mhd_compute_dt(mhd_ctx* c, double* dt) {
+  if (!c || !dt) return fail(MHD_EINVAL, "null argument");
+  cfl_dt(c->p, c->k, c->U, c->B, c->T, c->M, c->maxbits, c->prm.cfl, c->dt, c->st);
+  c->launches += 2;
+  cudaError_t e = cudaMemcpyAsync(c->h_pinned, c->dt, sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return cuda_fail(e, "compute_dt");
+  *dt = c->h_pinned[0];
+  if (!std::isfinite(*dt) || !(*dt > 0)) return fail(MHD_NONFINITE, "non-finite CFL step");
+  return MHD_OK;
+}
+
+int mhd_strang_step(mhd_ctx* c, double dt, double* dt_taken) {
+  if (!c) return fail(MHD_EINVAL, "null context");
+  cudaError_t e;
+  if (!(dt > 0)) {
+    int r = mhd_compute_dt(c, &dt);
+    if (r != MHD_OK) return r;
+  }
+  cudaMemcpyAsync(c->Usave, c->U, 5 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(c->Bsave, c->B, 3 * c->Z * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  for (int att = 0; att <= c->prm.max_halvings; ++att) {
+    cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->st);
+    set_scalar(c->dt, dt, c->st);
+    c->launches++;
+    enqueue_strang(c);
+    unsigned s = 0;
+    int r = check_status(c, &s);
+    if (r != MHD_OK) return r;
+    if (!(s & ST_INADMISSIBLE)) {
+      if (dt_taken) *dt_taken = dt;
+      return att > 0 ? MHD_RETRIED : MHD_OK;
+    }
+    cudaMemcpyAsync(c->U, c->Usave, 5 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    cudaMemcpyAsync(c->B, c->Bsave, 3 * c->Z * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    dt *= 0.5;
+  }
+  if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(e, "restore");
+  if (dt_taken) *dt_taken = 0.0;
+  return fail(MHD_INADMISSIBLE, "inadmissible cell average after all halvings");
+}
+
+int mhd_strang_steps(mhd_ctx* c, double dt, int nsteps, int* steps_done) {
+  if (!c || !(dt > 0) || nsteps < 0) return fail(MHD_EINVAL, "invalid argument");
+  if (steps_done) *steps_done = 0;
+  cudaMemcpyAsync(c->Usave, c->U, 5 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(c->Bsave, c->B, 3 * c->Z * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->st);
+  set_scalar(c->dt, dt, c->st);
+  c->launches++;
+  for (int s = 0; s < nsteps; ++s) enqueue_strang(c);
+  unsigned s = 0;
+  int r = check_status(c, &s);
+  if (r != MHD_OK) return r;
+  if (s & ST_INADMISSIBLE) {
+    cudaMemcpyAsync(c->U, c->Usave, 5 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    cudaMemcpyAsync(c->B, c->Bsave, 3 * c->Z * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    cudaStreamSynchronize(c->st);
+    return fail(MHD_INADMISSIBLE, "inadmissible cell average in a fixed-step sequence");
+  }
+  if (steps_done) *steps_done = nsteps;
+  return MHD_OK;
+}
+
+int mhd_substep(mhd_ctx* c, int which, double tau) {
+  if (!c || !(tau > 0) || (which != 0 && which != 1)) return fail(MHD_EINVAL, "invalid argument");
+  cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->st);
+  set_scalar(c->dt, tau, c->st);
+  c->launches++;
+  if (which == 0) hydro_substep(c, 1.0);
+  else mag_substep(c, 1.0);
+  unsigned s = 0;
+  int r = check_status(c, &s);
+  if (r != MHD_OK) return r;
+  if (s & ST_INADMISSIBLE) return fail(MHD_INADMISSIBLE, "inadmissible raw cell average");
+  return MHD_OK;
+}
+
+int mhd_hydro_rhs(mhd_ctx* c, const double* U, double* L, int on_device) {
+  if (!c || !U || !L) return fail(MHD_EINVAL, "null argument");
+  cudaError_t e;
+  if ((e = copy_in(c, c->S1, U, 5 * c->N, on_device)) != cudaSuccess) return cuda_fail(e, "U");
+  hydro_face(c->p, c->S1, c->Fx, c->Fy, c->M, c->st);
+  hydro_vol(c->p, 0, c->S1, c->S1, c->Fx, c->Fy, c->S2, nullptr, c->status, c->T, c->M, c->dt, 0.0, 0.0, 0.0, 0,
+            c->st);
+  c->launches += 2;
+  if ((e = copy_out(c, L, c->S2, 5 * c->N, on_device)) != cudaSuccess) return cuda_fail(e, "L");
+  if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(e, "hydro_rhs");
+  return MHD_OK;
+}
+
+int mhd_mag_rhs(mhd_ctx* c, const double* rho, const double* e_, const double* u, const double* Bx, const double* By,
+                const double* Bz, const double* eta, double* de, double* du, double* dBx, double* dBy, double* dBz,
+                int on_device) {
+  if (!c || !rho || !e_ || !u || !Bx || !By || !Bz || !eta || !de || !du || !dBx || !dBy || !dBz)
+    return fail(MHD_EINVAL, "null argument");
+  const size_t N = c->N, Z = c->Z;
+  cudaError_t e;
+  // rho -> S1[0:N]; Y = [e | u] -> Ya; B -> Ba (blocked); eta -> work
+  if ((e = copy_in(c, c->S1, rho, N, on_device)) != cudaSuccess) return cuda_fail(e, "rho");
+  if ((e = copy_in(c, c->Ya, e_, N, on_device)) != cudaSuccess) return cuda_fail(e, "e");
+  if ((e = copy_in(c, c->Ya + N, u, 3 * N, on_device)) != cudaSuccess) return cuda_fail(e, "u");
+  if ((e = copy_in(c, c->io, Bx, Z, on_device)) != cudaSuccess) return cuda_fail(e, "Bx");
+  grid_to_blocked(c->io, c->Ba, c->M.nx, c->M.ny, c->mm, c->st);
+  if ((e = copy_in(c, c->io, By, Z, on_device)) != cudaSuccess) return cuda_fail(e, "By");
+  grid_to_blocked(c->io, c->Ba + Z, c->M.nx, c->M.ny, c->mm, c->st);
+  if ((e = copy_in(c, c->Ba + 2 * Z, Bz, Z, on_device)) != cudaSuccess) return cuda_fail(e, "Bz");
+  if ((e = copy_in(c, c->work, eta, c->M.K, on_device)) != cudaSuccess) return cuda_fail(e, "eta");
+  mag_stage(c->p, c->k, 0, c->Ba, c->Ya + N, c->Ya, c->S1, c->work, 1, c->Ba, c->Ya + N, c->Ya, c->Bb, c->Yb + N,
+            c->Yb, c->LJ, c->LE, c->T, c->M, c->dt, 0.0, 0.0, 0.0, 0, c->st);
+  c->launches += 5;
+  if ((e = copy_out(c, de, c->Yb, N, on_device)) != cudaSuccess) return cuda_fail(e, "de");
+  if ((e = copy_out(c, du, c->Yb + N, 3 * N, on_device)) != cudaSuccess) return cuda_fail(e, "du");
+  blocked_to_grid(c->Bb, c->io, c->M.nx, c->M.ny, c->mm, c->st);
+  if ((e = copy_out(c, dBx, c->io, Z, on_device)) != cudaSuccess) return cuda_fail(e, "dBx");
+  if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(e, "dBx");
+  blocked_to_grid(c->Bb + Z, c->io, c->M.nx, c->M.ny, c->mm, c->st);
+  if ((e = copy_out(c, dBy, c->io, Z, on_device)) != cudaSuccess) return cuda_fail(e, "dBy");
+  if ((e = copy_out(c, dBz, c->Bb + 2 * Z, Z, on_device)) != cudaSuccess) return cuda_fail(e, "dBz");
+  c->launches += 2;
+  if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(e, "mag_rhs");
+  return MHD_OK;
+}
+
+int mhd_diagnostics(mhd_ctx* c, mhd_diag_t* out) {
+  if (!c || !out) return fail(MHD_EINVAL, "null argument");
+  const size_t K = c->M.K;
+  diag_partials(c->p, c->k, c->U, c->B, c->T, c->M, c->work, c->st);
+  c->launches++;
+  std::vector<double> h(12 * K), eta(K);
+  cudaError_t e = cudaMemcpyAsync(h.data(), c->work, 12 * K * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(eta.data(), c->eta, K * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return cuda_fail(e, "diagnostics");
+  double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1e300, 1e300};
+  for (size_t k = 0; k < K; ++k) {
+    for (int q = 0; q < 8; ++q) acc[q] += h[k * 12 + q];
+    acc[8] = std::max(acc[8], h[k * 12 + 8]);
+    acc[9] = std::max(acc[9], h[k * 12 + 9]);
+    acc[10] = std::min(acc[10], h[k * 12 + 10]);
+    acc[11] = std::min(acc[11], h[k * 12 + 11]);
+  }
+  double emax = 0.0;
+  for (double v : eta) emax = std::max(emax, v);
+  out->mass = acc[0]; out->mom[0] = acc[1]; out->mom[1] = acc[2]; out->mom[2] = acc[3];
+  out->E_kin = acc[4]; out->E_int = acc[5]; out->entropy = acc[6]; out->E_mag = 0.5 * acc[7];
+  out->div_B = acc[8]; out->B_max = acc[9]; out->rho_min = acc[10]; out->p_min = acc[11];
+  out->eta_max = emax; out->n_rejections = 0; out->reserved = 0;
+  return MHD_OK;
+}
+
+int mhd_get_eta(mhd_ctx* c, double* eta) {
+  if (!c || !eta) return fail(MHD_EINVAL, "null argument");
+  cudaError_t e = copy_out(c, eta, c->eta, c->M.K, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "get_eta");
+  return MHD_OK;
+}
+
+long long mhd_launch_count(const mhd_ctx* c) { return c ? c->launches : 0; }
+
+}  // extern "C"

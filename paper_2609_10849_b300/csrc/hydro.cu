@@ -1,0 +1,298 @@
+// Hydro stage kernels: entropy-stable DGSEM residual (§3.2.1, eq.
+// euler-nodal-index) fused with the SSP-RK(3,3) stage combination
+// (eq. euler-ssprk33) and the raw-average admissibility check (§3.2.3).
+//
+// Work mapping (FP64-issue bound part: every warp lane carries FP64 work):
+//   k_face  one thread per face node: LLF flux (eq. euler-lf-flux) on every
+//           x- and y-face, stored once per face: Fs[c][K][n], indexed by the
+//           element on the + side of the face.
+//   k_vol   EB elements x (p+1)^2 threads per block; the p(p+1)^2 unique
+//           entropy-conservative pairs of an element (eq.
+//           euler-chandrashekar-flux) are spread p per thread and evaluated
+//           once (the flux is symmetric), then gathered with D.  With
+//           2 D_00 = -1/w_0 and 2 D_pp = 1/w_p (SBP, eq. euler-sbp) the
+//           physical-flux diagonal cancels the physical part of the surface
+//           term exactly, leaving only the numerical flux F* at the end nodes.
+#include "mhd_internal.cuh"
+
+namespace mhd {
+
+template <int P>
+struct HCfg {
+  static constexpr int n = P + 1, n2 = n * n;
+  static constexpr int npairs = P * n2;        // unique pairs per element
+  static constexpr int npl = n * (n - 1) / 2;  // pairs per line
+  static constexpr int EB = P == 1 ? 32 : (P == 2 ? 32 : (P == 3 ? 8 : 5));
+  static constexpr int threads = EB * n2;
+};
+
+// Pairs (a, b), a < b, ordered so that the first n(n-1)/2 use only nodes < n.
+__constant__ unsigned char c_pair_a[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+__constant__ unsigned char c_pair_b[10] = {1, 2, 2, 3, 3, 3, 4, 4, 4, 4};
+
+__device__ __forceinline__ int pair_index(int a, int b) {  // a < b
+  return b * (b - 1) / 2 + a;
+}
+
+// Log-mean factor F with a_log = (aL + aR) / (2 F) and its reciprocal
+// (reading R1: Ismail-Roe series for u = f^2 < 1e-4, logarithm otherwise).
+// f = (aL - aR)/(aL + aR) is passed in; returns 1/F in *invF and F.
+__device__ __forceinline__ double logmean_factor(double aL, double aR, double f, double* invF) {
+  double u = f * f;
+  if (u < 1e-4) {
+    double F = fma(u, fma(u, fma(u, 1.0 / 7.0, 1.0 / 5.0), 1.0 / 3.0), 1.0);
+    *invF = rcp(F);
+    return F;
+  }
+  double lz = log(aL / aR);
+  double F = lz / (2.0 * f);
+  *invF = (2.0 * f) / lz;
+  return F;
+}
+
+__device__ __forceinline__ void llf_flux_dev(int d, const double* Um, const double* Up, double g, double* F) {
+  double im = rcp(Um[0]), ip = rcp(Up[0]);
+  double udm = Um[1 + d] * im, udp = Up[1 + d] * ip;
+  double pm = (g - 1.0) * (Um[4] - 0.5 * (Um[1] * Um[1] + Um[2] * Um[2] + Um[3] * Um[3]) * im);
+  double pp = (g - 1.0) * (Up[4] - 0.5 * (Up[1] * Up[1] + Up[2] * Up[2] + Up[3] * Up[3]) * ip);
+  double sm = fabs(udm) + sqrt(g * pm * im);
+  double sp = fabs(udp) + sqrt(g * pp * ip);
+  double lam = fmax(sm, sp);
+  double Fm[5], Fp[5];
+  Fm[0] = Um[1 + d]; Fp[0] = Up[1 + d];
+  Fm[1] = Um[1] * udm + (d == 0 ? pm : 0.0); Fp[1] = Up[1] * udp + (d == 0 ? pp : 0.0);
+  Fm[2] = Um[2] * udm + (d == 1 ? pm : 0.0); Fp[2] = Up[2] * udp + (d == 1 ? pp : 0.0);
+  Fm[3] = Um[3] * udm; Fp[3] = Up[3] * udp;
+  Fm[4] = (Um[4] + pm) * udm; Fp[4] = (Up[4] + pp) * udp;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) F[c] = 0.5 * (Fm[c] + Fp[c]) - 0.5 * lam * (Up[c] - Um[c]);
+}
+
+template <int P>
+__global__ void __launch_bounds__(256) k_face(const double* __restrict__ S, double* __restrict__ Fx,
+                                              double* __restrict__ Fy, Mesh M) {
+  constexpr int n = P + 1, n2 = n * n;
+  const size_t N = (size_t)M.K * n2;
+  const size_t nf = (size_t)M.K * n;
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * nf) return;
+  int d = t >= nf;
+  size_t r = d ? t - nf : t;
+  int k = (int)(r / n), j = (int)(r % n);
+  int ex = k % M.nx, ey = k / M.nx;
+  int km, qm, qp;
+  if (d == 0) { km = ey * M.nx + wrap(ex - 1, M.nx); qm = j * n + P; qp = j * n; }
+  else { km = wrap(ey - 1, M.ny) * M.nx + ex; qm = P * n + j; qp = j; }
+  double Um[5], Up[5], F[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    Um[c] = S[c * N + (size_t)km * n2 + qm];
+    Up[c] = S[c * N + (size_t)k * n2 + qp];
+  }
+  llf_flux_dev(d, Um, Up, M.g, F);
+  double* out = d ? Fy : Fx;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) out[c * nf + r] = F[c];
+}
+
+// mode 0: write L_E; mode 1: SSP stage combination into C.
+// Stage s: s == 0: C = S + tau L; otherwise C = a U0 + b (S + tau L).
+template <int P, int MODE>
+__global__ void __launch_bounds__(HCfg<P>::threads) k_vol(const double* __restrict__ S, const double* __restrict__ U0,
+                                                          const double* __restrict__ Fx, const double* __restrict__ Fy,
+                                                          double* __restrict__ out, double* __restrict__ avg_out,
+                                                          unsigned* __restrict__ status, const Tab* __restrict__ T,
+                                                          Mesh M, const double* __restrict__ dtp, double dtfac,
+                                                          double ca, double cb, int first) {
+  using C = HCfg<P>;
+  constexpr int n = C::n, n2 = C::n2, EB = C::EB, NP = C::npairs, NPL = C::npl;
+  __shared__ double sp[6][EB * n2];           // rho, ux, uy, uz, beta, |u|^2
+  __shared__ double sf[5][EB * NP];           // pair fluxes
+  __shared__ double savg[5][EB];
+  const size_t N = (size_t)M.K * n2;
+  const int tid = threadIdx.x;
+  const int el = tid / n2, q = tid % n2;
+  const int k = blockIdx.x * EB + el;
+  const bool valid = k < M.K;
+  const int kk = valid ? k : M.K - 1;  // clamp loads; results of invalid lanes are discarded
+  const size_t gi = (size_t)kk * n2 + q;
+  const double g = M.g;
+
+  double Us[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) Us[c] = S[c * N + gi];
+  {
+    double ir = rcp(Us[0]);
+    double ux = Us[1] * ir, uy = Us[2] * ir, uz = Us[3] * ir;
+    double u2 = fma(ux, ux, fma(uy, uy, uz * uz));
+    double pr = (g - 1.0) * fma(-0.5 * Us[0], u2, Us[4]);
+    sp[0][tid] = Us[0];
+    sp[1][tid] = ux; sp[2][tid] = uy; sp[3][tid] = uz;
+    sp[4][tid] = 0.5 * Us[0] * rcp(pr);
+    sp[5][tid] = u2;
+  }
+  __syncthreads();
+
+  // ---- pair fluxes ------------------------------------------------------------
+  const double ig1 = 1.0 / (g - 1.0);
+#pragma unroll
+  for (int s = 0; s < P; ++s) {
+    const int pidx = q + s * n2;
+    const int d = pidx >= NP / 2;
+    const int r = pidx - d * (NP / 2);
+    const int line = r / NPL, w = r % NPL;
+    const int a = c_pair_a[w], b = c_pair_b[w];
+    const int qa = el * n2 + (d == 0 ? line * n + a : a * n + line);
+    const int qb = el * n2 + (d == 0 ? line * n + b : b * n + line);
+    double rL = sp[0][qa], rR = sp[0][qb];
+    double bL = sp[4][qa], bR = sp[4][qb];
+    double sr = rL + rR, sb = bL + bR;
+    double isr = rcp(sr), isb = rcp(sb);
+    double fr = (rL - rR) * isr, fb = (bL - bR) * isb;
+    double iFr, iFb;
+    double Fr = logmean_factor(rL, rR, fr, &iFr);
+    double Fb = logmean_factor(bL, bR, fb, &iFb);
+    double rlog = 0.5 * sr * iFr;                       // rho^log
+    double ua0 = 0.5 * (sp[1][qa] + sp[1][qb]);
+    double ua1 = 0.5 * (sp[2][qa] + sp[2][qb]);
+    double ua2 = 0.5 * (sp[3][qa] + sp[3][qb]);
+    double u2a = 0.5 * (sp[5][qa] + sp[5][qb]);         // {{|u|^2}}
+    double au2 = fma(ua0, ua0, fma(ua1, ua1, ua2 * ua2));  // |{{u}}|^2
+    double phat = 0.5 * sr * isb;                       // {{rho}} / (2 {{beta}})
+    // h = 1/(2(g-1) beta^log) - {{|u|^2}}/2 + |{{u}}|^2 + phat/rho^log
+    //   = Fb/((g-1) sb) ... with beta^log = sb/(2 Fb) and rho^log = sr/(2 Fr)
+    double hhat = fma(Fb * ig1 + Fr, isb, fma(-0.5, u2a, au2));
+    double ud = d == 0 ? ua0 : ua1;
+    double f0 = rlog * ud;
+    const int o = el * NP + pidx;
+    sf[0][o] = f0;
+    sf[1][o] = fma(f0, ua0, d == 0 ? phat : 0.0);
+    sf[2][o] = fma(f0, ua1, d == 1 ? phat : 0.0);
+    sf[3][o] = f0 * ua2;
+    sf[4][o] = f0 * hhat;
+  }
+  __syncthreads();
+
+  // ---- gather: L = -(2/hx)[2 sum D F + end terms] - (2/hy)[...] -----------------
+  const int i = q % n, j = q / n;
+  double Drow_i[n], Drow_j[n];
+#pragma unroll
+  for (int r = 0; r < n; ++r) { Drow_i[r] = T->D[i][r]; Drow_j[r] = T->D[j][r]; }
+  const double cx = -4.0 / M.hx, cy = -4.0 / M.hy;
+  const double w0i = 1.0 / T->wp[0];
+  const int ex = kk % M.nx, ey = kk / M.nx;
+  const size_t nf = (size_t)M.K * n;
+  double L[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    double sx = 0.0, sy = 0.0;
+#pragma unroll
+    for (int r = 0; r < n; ++r) {
+      if (r == i) continue;
+      int pi_ = pair_index(min(i, r), max(i, r));
+      sx = fma(Drow_i[r], sf[c][el * NP + j * NPL + pi_], sx);
+    }
+#pragma unroll
+    for (int r = 0; r < n; ++r) {
+      if (r == j) continue;
+      int pi_ = pair_index(min(j, r), max(j, r));
+      sy = fma(Drow_j[r], sf[c][el * NP + NP / 2 + i * NPL + pi_], sy);
+    }
+    double v = fma(cx, sx, cy * sy);
+    // end nodes: -(2/hx)[-F*_left/w_0] and -(2/hx)[+F*_right/w_p] (w_p = w_0)
+    if (i == 0) v = fma(2.0 / M.hx * w0i, Fx[c * nf + (size_t)kk * n + j], v);
+    if (i == P) v = fma(-2.0 / M.hx * w0i, Fx[c * nf + (size_t)(ey * M.nx + wrap(ex + 1, M.nx)) * n + j], v);
+    if (j == 0) v = fma(2.0 / M.hy * w0i, Fy[c * nf + (size_t)kk * n + i], v);
+    if (j == P) v = fma(-2.0 / M.hy * w0i, Fy[c * nf + (size_t)(wrap(ey + 1, M.ny) * M.nx + ex) * n + i], v);
+    L[c] = v;
+  }
+
+  if (MODE == 0) {
+    if (valid) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) out[c * N + gi] = L[c];
+    }
+    return;
+  }
+
+  const double tau = dtp[0] * dtfac;
+  double Cv[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    double raw = fma(tau, L[c], Us[c]);
+    Cv[c] = first ? raw : fma(ca, U0[c * N + gi], cb * raw);
+  }
+  if (valid) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out[c * N + gi] = Cv[c];
+  }
+  // ---- raw element averages and the admissibility check --------------------------
+  __syncthreads();  // sp is reused for the weighted values
+  const double wq = 0.25 * T->wp[i] * T->wp[j];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) sf[c][el * n2 + q] = Cv[c];
+  __syncthreads();
+  if (q < 5) {
+    const int c = q;
+    double s = 0.0;
+#pragma unroll
+    for (int t2 = 0; t2 < n2; ++t2) s = fma(0.25 * T->wp[t2 % n] * T->wp[t2 / n], sf[c][el * n2 + t2], s);
+    savg[c][el] = s;
+  }
+  (void)wq;
+  __syncthreads();
+  if (q == 0 && valid) {
+    double a0 = savg[0][el], a1 = savg[1][el], a2 = savg[2][el], a3 = savg[3][el], a4 = savg[4][el];
+    if (avg_out) {
+      avg_out[0 * (size_t)M.K + k] = a0; avg_out[1 * (size_t)M.K + k] = a1; avg_out[2 * (size_t)M.K + k] = a2;
+      avg_out[3 * (size_t)M.K + k] = a3; avg_out[4 * (size_t)M.K + k] = a4;
+    }
+    // rho > 0 and p > 0  <=>  rho > 0 and rho E - |m|^2/2 > 0
+    double pe = fma(a0, a4, -0.5 * fma(a1, a1, fma(a2, a2, a3 * a3)));
+    bool fin = isfinite(a0) && isfinite(a1) && isfinite(a2) && isfinite(a3) && isfinite(a4);
+    if (!fin) atomicOr(status, ST_NONFINITE | ST_INADMISSIBLE);
+    else if (!(a0 > 0.0) || !(pe > 0.0)) atomicOr(status, ST_INADMISSIBLE);
+  }
+}
+
+// ---- launchers ------------------------------------------------------------------
+template <int P>
+void launch_face(const double* S, double* Fx, double* Fy, const Mesh& M, cudaStream_t st) {
+  size_t total = 2 * (size_t)M.K * (P + 1);
+  int th = 256;
+  k_face<P><<<(unsigned)((total + th - 1) / th), th, 0, st>>>(S, Fx, Fy, M);
+}
+
+template <int P>
+void launch_vol(int mode, const double* S, const double* U0, const double* Fx, const double* Fy, double* out,
+                double* avg, unsigned* status, const Tab* T, const Mesh& M, const double* dtp, double dtfac,
+                double ca, double cb, int first, cudaStream_t st) {
+  using C = HCfg<P>;
+  unsigned blocks = (unsigned)((M.K + C::EB - 1) / C::EB);
+  if (mode == 0)
+    k_vol<P, 0><<<blocks, C::threads, 0, st>>>(S, U0, Fx, Fy, out, avg, status, T, M, dtp, dtfac, ca, cb, first);
+  else
+    k_vol<P, 1><<<blocks, C::threads, 0, st>>>(S, U0, Fx, Fy, out, avg, status, T, M, dtp, dtfac, ca, cb, first);
+}
+
+void hydro_face(int p, const double* S, double* Fx, double* Fy, const Mesh& M, cudaStream_t st) {
+  switch (p) {
+    case 1: launch_face<1>(S, Fx, Fy, M, st); break;
+    case 2: launch_face<2>(S, Fx, Fy, M, st); break;
+    case 3: launch_face<3>(S, Fx, Fy, M, st); break;
+    case 4: launch_face<4>(S, Fx, Fy, M, st); break;
+  }
+}
+
+void hydro_vol(int p, int mode, const double* S, const double* U0, const double* Fx, const double* Fy, double* out,
+               double* avg, unsigned* status, const Tab* T, const Mesh& M, const double* dtp, double dtfac,
+               double ca, double cb, int first, cudaStream_t st) {
+  switch (p) {
+    case 1: launch_vol<1>(mode, S, U0, Fx, Fy, out, avg, status, T, M, dtp, dtfac, ca, cb, first, st); break;
+    case 2: launch_vol<2>(mode, S, U0, Fx, Fy, out, avg, status, T, M, dtp, dtfac, ca, cb, first, st); break;
+    case 3: launch_vol<3>(mode, S, U0, Fx, Fy, out, avg, status, T, M, dtp, dtfac, ca, cb, first, st); break;
+    case 4: launch_vol<4>(mode, S, U0, Fx, Fy, out, avg, status, T, M, dtp, dtfac, ca, cb, first, st); break;
+  }
+}
+
+}  // namespace mhd

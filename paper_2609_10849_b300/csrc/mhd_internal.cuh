@@ -1,0 +1,119 @@
+// Internal declarations of the B300 H-M-H Strang-step library.
+//
+// Device layouts (element-blocked; the host layouts of include/mhd.h are
+// converted on the way in and out):
+//   DG fields          [c][K][n2], n = p+1, node j*n+i           (as on the host)
+//   magnetic arrays    [K][mm*mm], mm = k+1, local index b*mm+a   (owned DOFs):
+//     Bx  (R, x-comp)  a = GLL(k+1) node 0..k in x, b = Gauss(k) node in y
+//     By  (R, y-comp)  a = Gauss(k) node in x,     b = GLL(k+1) node 0..k in y
+//     Bz  (V_h^k)      GLL(k) nodes
+//   element closures   an element also uses the a = k+1 column / b = k+1 row
+//                      of its +x / +y neighbour (node 0 there).
+//   per-element loads  closure-sized scratch written by one kernel and
+//                      gathered (assembled) by the next.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MHD_NMAX 5  // p + 1 <= 5 and k + 1 <= 5
+#define MHD_LMAX 6  // k + 2 <= 6
+
+namespace mhd {
+
+// 1D tables of one (p, k) pair.  Row index first: T[a][c] = basis c at point a.
+struct Tab {
+  double xp[MHD_NMAX], wp[MHD_NMAX];          // GLL(p)
+  double D[MHD_NMAX][MHD_NMAX];               // D[i][j] = l_j'(xp_i)
+  double xL[MHD_LMAX], wL[MHD_LMAX];          // GLL(k+1)
+  double zG[MHD_NMAX], wG[MHD_NMAX];          // Gauss(k), k+1 points
+  double xM[MHD_NMAX], wM[MHD_NMAX];          // GLL(k)
+  double ML[MHD_LMAX][MHD_LMAX];              // exact GLL(k+1) mass  int l_a l_b
+  double dL_G[MHD_NMAX][MHD_LMAX];            // l^L_c'(zG_a)
+  double L_G[MHD_NMAX][MHD_LMAX];             // l^L_c(zG_a)
+  double G_L[MHD_LMAX][MHD_NMAX];             // g_c(xL_a)
+  double M_G[MHD_NMAX][MHD_NMAX];             // l^M_c(zG_a)
+  double M_L[MHD_LMAX][MHD_NMAX];             // l^M_c(xL_a)
+  double P_G[MHD_NMAX][MHD_NMAX];             // l^P_c(zG_a)
+  double P_L[MHD_LMAX][MHD_NMAX];             // l^P_c(xL_a)
+  double dL_M[MHD_NMAX][MHD_LMAX];            // l^L_c'(xM_a)
+  double G_M[MHD_NMAX][MHD_NMAX];             // g_c(xM_a)
+  double L_P[MHD_NMAX][MHD_LMAX];             // l^L_c(xp_a)
+  double G_P[MHD_NMAX][MHD_NMAX];             // g_c(xp_a)
+  double M_P[MHD_NMAX][MHD_NMAX];             // l^M_c(xp_a)
+  double dL_L[MHD_LMAX][MHD_LMAX];            // l^L_c'(xL_a)
+  double dL_Gz[MHD_NMAX][MHD_LMAX];           // same as dL_G (kept for symmetry of use)
+  double Dr0[MHD_NMAX][MHD_NMAX];             // row 0 of D^r: [r][s]
+  double Drp[MHD_NMAX][MHD_NMAX];             // row p of D^r: [r][s]
+  double Leg[MHD_NMAX][MHD_NMAX];             // Legendre P_a(xp_i): [i][a]
+  double LegN[MHD_NMAX];                      // 1 / sum_i wp_i P_a(xp_i)^2
+  double z2[MHD_LMAX], w2[MHD_LMAX];          // Gauss with k+2 points
+  double L_2[MHD_LMAX][MHD_LMAX];             // l^L_c(z2_a)
+  double G_2[MHD_LMAX][MHD_NMAX];             // g_c(z2_a)
+  double M_2[MHD_LMAX][MHD_NMAX];             // l^M_c(z2_a)
+  double L_end[2][MHD_LMAX];                  // l^L_c(-1), l^L_c(+1)
+  double G_end[2][MHD_NMAX];                  // g_c(-1), g_c(+1)
+  double M_end[2][MHD_NMAX];                  // l^M_c(-1), l^M_c(+1)
+};
+
+// Device copy of the tables of the 8 supported (p, k) pairs.
+int table_slot(int p, int k);
+const Tab* device_tables(int p, int k, cudaError_t* err);  // uploads once per device
+void host_tables(int p, int k, Tab* out);
+
+struct Mesh {
+  int nx, ny, K;
+  double hx, hy, Jdet, g;
+};
+
+// Stabilisation parameters as seen by the kernels.
+struct Stab {
+  int oe_hydro, oe_vel, pp, ar;
+  double s_H, s_M, C_s, C_eta, cfl;
+  int max_halvings;
+};
+
+// Status word bits written by kernels.
+enum : unsigned {
+  ST_INADMISSIBLE = 1u,
+  ST_NONFINITE = 2u,
+  ST_TIMEOUT = 4u,
+};
+
+__host__ __device__ inline int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// ---- fast FP64 reciprocal ---------------------------------------------------
+// Seed from the documented PTX approximation rcp.approx.ftz.f64 (high-word
+// reciprocal, relative error below 2^-22), refined by one cubic Newton-Raphson
+// step r1 = r0 (1 + e + e^2), e = 1 - x r0 (error e^3 < 2^-66, then rounding).
+// Valid for normal x with |x| in [2^-1000, 2^1000]; the library only takes
+// reciprocals of densities, pressures and sums of those.
+__device__ __forceinline__ double rcp(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  double t = fma(e, e, e);
+  return fma(r, t, r);
+}
+
+// ---- launch counting ----------------------------------------------------------
+struct Ctx;
+void count_launch(Ctx* c);
+
+}  // namespace mhd
+
+// Dispatch a templated functor over the supported (p, k) pairs.
+#define MHD_DISPATCH_PK(p, k, F)                                 \
+  do {                                                           \
+    switch ((p) * 10 + (k)) {                                    \
+      case 10: F(1, 0); break;                                   \
+      case 11: F(1, 1); break;                                   \
+      case 21: F(2, 1); break;                                   \
+      case 22: F(2, 2); break;                                   \
+      case 32: F(3, 2); break;                                   \
+      case 33: F(3, 3); break;                                   \
+      case 43: F(4, 3); break;                                   \
+      case 44: F(4, 4); break;                                   \
+      default: break;                                            \
+    }                                                            \
+  } while (0)

@@ -1,0 +1,280 @@
+// Pointwise and reduction kernels: host<->device layout permutation of the
+// compatible fields, the nodal variable exchange (§3.4.1), the discretely
+// divergence-free initial field from a potential, the CFL time step and the
+// per-element diagnostic partials.
+#include "mhd_internal.cuh"
+
+namespace mhd {
+
+// grid [NY][NX] (X = ex*mm + a, Y = ey*mm + b) <-> element-blocked [K][mm*mm].
+__global__ void k_grid_to_blocked(const double* __restrict__ g, double* __restrict__ o, int nx, int ny, int mm) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t tot = (size_t)nx * ny * mm * mm;
+  if (t >= tot) return;
+  int NX = nx * mm;
+  int X = (int)(t % NX), Y = (int)(t / NX);
+  int ex = X / mm, a = X % mm, ey = Y / mm, b = Y % mm;
+  o[((size_t)ey * nx + ex) * mm * mm + b * mm + a] = g[t];
+}
+__global__ void k_blocked_to_grid(const double* __restrict__ o, double* __restrict__ g, int nx, int ny, int mm) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t tot = (size_t)nx * ny * mm * mm;
+  if (t >= tot) return;
+  int NX = nx * mm;
+  int X = (int)(t % NX), Y = (int)(t / NX);
+  int ex = X / mm, a = X % mm, ey = Y / mm, b = Y % mm;
+  g[t] = o[((size_t)ey * nx + ex) * mm * mm + b * mm + a];
+}
+
+void grid_to_blocked(const double* g, double* o, int nx, int ny, int mm, cudaStream_t st) {
+  size_t tot = (size_t)nx * ny * mm * mm;
+  k_grid_to_blocked<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(g, o, nx, ny, mm);
+}
+void blocked_to_grid(const double* o, double* g, int nx, int ny, int mm, cudaStream_t st) {
+  size_t tot = (size_t)nx * ny * mm * mm;
+  k_blocked_to_grid<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(o, g, nx, ny, mm);
+}
+
+// (rho, m, E_mech) -> (e, u) at every GLL node; Y = [e | u_x | u_y | u_z].
+__global__ void k_cons_to_prim(const double* __restrict__ U, double* __restrict__ Y, size_t N) {
+  size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= N) return;
+  double rho = U[q], ir = rcp(rho);
+  double ux = U[N + q] * ir, uy = U[2 * N + q] * ir, uz = U[3 * N + q] * ir;
+  double ke = 0.5 * rho * fma(ux, ux, fma(uy, uy, uz * uz));
+  Y[q] = (U[4 * N + q] - ke) * ir;
+  Y[N + q] = ux; Y[2 * N + q] = uy; Y[3 * N + q] = uz;
+}
+
+// (e, u) -> (m, E_mech) with the frozen density.
+__global__ void k_prim_to_cons(const double* __restrict__ Y, double* __restrict__ U, size_t N) {
+  size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= N) return;
+  double rho = U[q];
+  double ux = Y[N + q], uy = Y[2 * N + q], uz = Y[3 * N + q];
+  U[N + q] = rho * ux; U[2 * N + q] = rho * uy; U[3 * N + q] = rho * uz;
+  U[4 * N + q] = fma(rho, Y[q], 0.5 * rho * fma(ux, ux, fma(uy, uy, uz * uz)));
+}
+
+// (rho, u, p) -> conservative.
+__global__ void k_prim_in(const double* __restrict__ rho, const double* __restrict__ u, const double* __restrict__ p,
+                          double* __restrict__ U, size_t N, double g) {
+  size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= N) return;
+  double r = rho[q], ux = u[q], uy = u[N + q], uz = u[2 * N + q];
+  U[q] = r; U[N + q] = r * ux; U[2 * N + q] = r * uy; U[3 * N + q] = r * uz;
+  U[4 * N + q] = p[q] / (g - 1.0) + 0.5 * r * (ux * ux + uy * uy + uz * uz);
+}
+
+void cons_to_prim(const double* U, double* Y, size_t N, cudaStream_t st) {
+  k_cons_to_prim<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(U, Y, N);
+}
+void prim_to_cons(const double* Y, double* U, size_t N, cudaStream_t st) {
+  k_prim_to_cons<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(Y, U, N);
+}
+void prim_in(const double* rho, const double* u, const double* p, double* U, size_t N, double g, cudaStream_t st) {
+  k_prim_in<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rho, u, p, U, N, g);
+}
+
+// B_par = B0 + grad^perp A_h on the owned R_h^k DOFs, A blocked [K][mm^2].
+template <int KM>
+__global__ void k_b_from_potential(const double* __restrict__ A, double Bx0, double By0, double* __restrict__ Bx,
+                                   double* __restrict__ By, const Tab* __restrict__ T, Mesh M) {
+  constexpr int mm = KM + 1, mL = KM + 2;
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)M.K * mm * mm) return;
+  int k = (int)(t / (mm * mm)), r = (int)(t % (mm * mm)), b = r / mm, a = r % mm;
+  int ex = k % M.nx, ey = k / M.nx;
+  auto Acl = [&](int aa, int bb) {
+    int ox = ex, oy = ey;
+    if (aa == mL - 1) { ox = wrap(ex + 1, M.nx); aa = 0; }
+    if (bb == mL - 1) { oy = wrap(ey + 1, M.ny); bb = 0; }
+    return A[((size_t)oy * M.nx + ox) * mm * mm + bb * mm + aa];
+  };
+  double vx = 0.0, vy = 0.0;
+  for (int c = 0; c < mL; ++c) {
+    vx = fma(T->dL_G[b][c], Acl(a, c), vx);  // d/dy at (xL_a, zG_b)
+    vy = fma(T->dL_G[a][c], Acl(c, b), vy);  // d/dx at (zG_a, xL_b)
+  }
+  Bx[t] = Bx0 - 2.0 / M.hy * vx;
+  By[t] = By0 + 2.0 / M.hx * vy;
+}
+
+void b_from_potential(int k, const double* A, double Bx0, double By0, double* Bx, double* By, const Tab* T,
+                      const Mesh& M, cudaStream_t st) {
+  size_t tot = (size_t)M.K * (k + 1) * (k + 1);
+  unsigned bl = (unsigned)((tot + 255) / 256);
+  switch (k) {
+    case 0: k_b_from_potential<0><<<bl, 256, 0, st>>>(A, Bx0, By0, Bx, By, T, M); break;
+    case 1: k_b_from_potential<1><<<bl, 256, 0, st>>>(A, Bx0, By0, Bx, By, T, M); break;
+    case 2: k_b_from_potential<2><<<bl, 256, 0, st>>>(A, Bx0, By0, Bx, By, T, M); break;
+    case 3: k_b_from_potential<3><<<bl, 256, 0, st>>>(A, Bx0, By0, Bx, By, T, M); break;
+    case 4: k_b_from_potential<4><<<bl, 256, 0, st>>>(A, Bx0, By0, Bx, By, T, M); break;
+  }
+}
+
+// B_h of element k at its DG node (i, j) (tensor interpolation of the closures).
+template <int P, int KM>
+__device__ void B_at_dg(const double* __restrict__ B, size_t Z, const Tab* __restrict__ T, const Mesh& M, int k, int i,
+                        int j, double out[3]) {
+  constexpr int mm = KM + 1, mL = KM + 2;
+  int ex = k % M.nx, ey = k / M.nx;
+  const double* Bx = B;
+  const double* By = B + Z;
+  const double* Bz = B + 2 * Z;
+  double bx = 0.0, by = 0.0, bz = 0.0;
+  for (int b = 0; b < mm; ++b) {  // Bx: GLL(k+1) x (closure), Gauss y
+    double row = 0.0;
+    for (int a = 0; a < mL; ++a) {
+      double v = a == mL - 1 ? Bx[((size_t)ey * M.nx + wrap(ex + 1, M.nx)) * mm * mm + b * mm]
+                             : Bx[(size_t)k * mm * mm + b * mm + a];
+      row = fma(T->L_P[i][a], v, row);
+    }
+    bx = fma(T->G_P[j][b], row, bx);
+  }
+  for (int b = 0; b < mL; ++b) {  // By: Gauss x, GLL(k+1) y (closure)
+    double row = 0.0;
+    for (int a = 0; a < mm; ++a) {
+      double v = b == mL - 1 ? By[((size_t)wrap(ey + 1, M.ny) * M.nx + ex) * mm * mm + a]
+                             : By[(size_t)k * mm * mm + b * mm + a];
+      row = fma(T->G_P[i][a], v, row);
+    }
+    by = fma(T->L_P[j][b], row, by);
+  }
+  for (int b = 0; b < mm; ++b) {
+    double row = 0.0;
+    for (int a = 0; a < mm; ++a) row = fma(T->M_P[i][a], Bz[(size_t)k * mm * mm + b * mm + a], row);
+    bz = fma(T->M_P[j][b], row, bz);
+  }
+  out[0] = bx; out[1] = by; out[2] = bz;
+}
+
+// Largest CFL rate (reading R2) over the DG nodes: atomicMax on the bits of a
+// non-negative double.
+template <int P, int KM>
+__global__ void k_cfl(const double* __restrict__ U, const double* __restrict__ B, const Tab* __restrict__ T, Mesh M,
+                      unsigned long long* __restrict__ maxbits) {
+  constexpr int n = P + 1, n2 = n * n;
+  size_t N = (size_t)M.K * n2, Z = (size_t)M.K * (KM + 1) * (KM + 1);
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double rate = 0.0;
+  if (t < N) {
+    int k = (int)(t / n2), q = (int)(t % n2);
+    double Bv[3];
+    B_at_dg<P, KM>(B, Z, T, M, k, q % n, q / n, Bv);
+    double rho = U[t], ir = 1.0 / rho;
+    double ux = U[N + t] * ir, uy = U[2 * N + t] * ir, uz = U[3 * N + t] * ir;
+    double pr = (M.g - 1.0) * (U[4 * N + t] - 0.5 * rho * (ux * ux + uy * uy + uz * uz));
+    double cf = sqrt((M.g * pr + Bv[0] * Bv[0] + Bv[1] * Bv[1] + Bv[2] * Bv[2]) * ir);
+    rate = (2.0 * P + 1.0) * ((fabs(ux) + cf) / M.hx + (fabs(uy) + cf) / M.hy);
+    if (!(rate >= 0.0)) rate = __longlong_as_double(0x7ff0000000000000ULL);  // non-finite -> +inf
+  }
+  unsigned long long bits = (unsigned long long)__double_as_longlong(rate);
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, o);
+    bits = ob > bits ? ob : bits;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(maxbits, bits);
+}
+
+__global__ void k_finalize_dt(const unsigned long long* __restrict__ maxbits, double cfl, double* __restrict__ dt) {
+  double r = __longlong_as_double((long long)*maxbits);
+  dt[0] = cfl / r;
+}
+
+__global__ void k_set_scalar(double* p, double v) { *p = v; }
+
+void cfl_dt(int p, int k, const double* U, const double* B, const Tab* T, const Mesh& M,
+            unsigned long long* maxbits, double cfl, double* dt, cudaStream_t st) {
+  cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long), st);
+  size_t N = (size_t)M.K * (p + 1) * (p + 1);
+  unsigned bl = (unsigned)((N + 255) / 256);
+#define MHD_CFL_CASE(PP, KK) k_cfl<PP, KK><<<bl, 256, 0, st>>>(U, B, T, M, maxbits)
+  MHD_DISPATCH_PK(p, k, MHD_CFL_CASE);
+#undef MHD_CFL_CASE
+  k_finalize_dt<<<1, 1, 0, st>>>(maxbits, cfl, dt);
+}
+
+void set_scalar(double* ptr, double v, cudaStream_t st) { k_set_scalar<<<1, 1, 0, st>>>(ptr, v); }
+
+// Per-element partials: [mass, mx, my, mz, E_kin, E_int, entropy, 2 E_mag,
+// div metric, |B| max, rho min, p min] -> out[K][12].
+template <int P, int KM>
+__global__ void k_diag(const double* __restrict__ U, const double* __restrict__ B, const Tab* __restrict__ T, Mesh M,
+                       double* __restrict__ out) {
+  constexpr int n = P + 1, n2 = n * n, mm = KM + 1, mL = KM + 2;
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= M.K) return;
+  size_t N = (size_t)M.K * n2, Z = (size_t)M.K * mm * mm;
+  double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1e300, 1e300};
+  for (int q = 0; q < n2; ++q) {
+    int i = q % n, j = q / n;
+    double w = M.Jdet * T->wp[i] * T->wp[j];
+    size_t t = (size_t)k * n2 + q;
+    double rho = U[t], mx = U[N + t], my = U[2 * N + t], mz = U[3 * N + t], E = U[4 * N + t];
+    double ke = 0.5 * (mx * mx + my * my + mz * mz) / rho;
+    double pr = (M.g - 1.0) * (E - ke);
+    acc[0] += w * rho; acc[1] += w * mx; acc[2] += w * my; acc[3] += w * mz;
+    acc[4] += w * ke; acc[5] += w * pr / (M.g - 1.0);
+    acc[6] += w * rho * (log(pr) - M.g * log(rho));
+    double Bv[3];
+    B_at_dg<P, KM>(B, Z, T, M, k, i, j, Bv);
+    acc[9] = fmax(acc[9], sqrt(Bv[0] * Bv[0] + Bv[1] * Bv[1] + Bv[2] * Bv[2]));
+    acc[10] = fmin(acc[10], rho);
+    acc[11] = fmin(acc[11], pr);
+  }
+  // exact magnetic energy and the divergence metric
+  int ex = k % M.nx, ey = k / M.nx;
+  const double* Bx = B;
+  const double* By = B + Z;
+  const double* Bz = B + 2 * Z;
+  double bx[mm][mL], by[mL][mm];
+  for (int b = 0; b < mm; ++b)
+    for (int a = 0; a < mL; ++a)
+      bx[b][a] = a == mL - 1 ? Bx[((size_t)ey * M.nx + wrap(ex + 1, M.nx)) * mm * mm + b * mm]
+                             : Bx[(size_t)k * mm * mm + b * mm + a];
+  for (int b = 0; b < mL; ++b)
+    for (int a = 0; a < mm; ++a)
+      by[b][a] = b == mL - 1 ? By[((size_t)wrap(ey + 1, M.ny) * M.nx + ex) * mm * mm + a]
+                             : By[(size_t)k * mm * mm + b * mm + a];
+  double em = 0.0;
+  for (int qy = 0; qy < mL; ++qy)
+    for (int qx = 0; qx < mL; ++qx) {
+      double vx = 0.0, vy = 0.0;
+      for (int b = 0; b < mm; ++b)
+        for (int a = 0; a < mL; ++a) vx += bx[b][a] * T->L_2[qx][a] * T->G_2[qy][b];
+      for (int b = 0; b < mL; ++b)
+        for (int a = 0; a < mm; ++a) vy += by[b][a] * T->G_2[qx][a] * T->L_2[qy][b];
+      em += M.Jdet * T->w2[qx] * T->w2[qy] * (vx * vx + vy * vy);
+    }
+  for (int qy = 0; qy < mm; ++qy)
+    for (int qx = 0; qx < mm; ++qx) {
+      double vz = 0.0;
+      for (int b = 0; b < mm; ++b)
+        for (int a = 0; a < mm; ++a) vz += Bz[(size_t)k * mm * mm + b * mm + a] * T->M_G[qx][a] * T->M_G[qy][b];
+      em += M.Jdet * T->wG[qx] * T->wG[qy] * vz * vz;
+    }
+  acc[7] = em;
+  double dv = 0.0;
+  for (int qy = 0; qy < mm; ++qy)
+    for (int qx = 0; qx < mm; ++qx) {
+      double dx = 0.0, dy = 0.0;
+      for (int b = 0; b < mm; ++b)
+        for (int a = 0; a < mL; ++a) dx += bx[b][a] * T->dL_G[qx][a] * (b == qy ? 1.0 : 0.0);
+      for (int b = 0; b < mL; ++b)
+        for (int a = 0; a < mm; ++a) dy += by[b][a] * (a == qx ? 1.0 : 0.0) * T->dL_G[qy][b];
+      dv = fmax(dv, fabs(2.0 / M.hx * dx + 2.0 / M.hy * dy));
+    }
+  acc[8] = fmin(M.hx, M.hy) * dv;
+  for (int c = 0; c < 12; ++c) out[(size_t)k * 12 + c] = acc[c];
+}
+
+void diag_partials(int p, int k, const double* U, const double* B, const Tab* T, const Mesh& M, double* out,
+                   cudaStream_t st) {
+  unsigned bl = (unsigned)((M.K + 127) / 128);
+#define MHD_DIAG_CASE(PP, KK) k_diag<PP, KK><<<bl, 128, 0, st>>>(U, B, T, M, out)
+  MHD_DISPATCH_PK(p, k, MHD_DIAG_CASE);
+#undef MHD_DIAG_CASE
+}
+
+}  // namespace mhd

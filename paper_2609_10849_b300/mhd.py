@@ -1,0 +1,222 @@
+"""Thin ctypes binding of libmhd.so (include/mhd.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of the library.  Arrays are numpy (host) or torch CUDA tensors (device,
+passed by data pointer on the context's stream).  There is no CPU fallback:
+if the library cannot be loaded the import of the solver fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmhd.so")
+
+MHD_OK, MHD_RETRIED = 0, 1
+MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA, MHD_INADMISSIBLE, MHD_NONFINITE, MHD_TIMEOUT = -1, -2, -3, -4, -5, -6
+
+
+class MhdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (status {code})")
+        self.code = code
+
+
+class Mesh(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("x0", C.c_double), ("x1", C.c_double), ("y0", C.c_double),
+                ("y1", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [("oe_hydro", C.c_int), ("oe_vel", C.c_int), ("pp", C.c_int), ("ar", C.c_int), ("s_H", C.c_double),
+                ("s_M", C.c_double), ("C_s", C.c_double), ("C_eta", C.c_double), ("cfl", C.c_double),
+                ("max_halvings", C.c_int)]
+
+
+class Diag(C.Structure):
+    _fields_ = [("mass", C.c_double), ("mom", C.c_double * 3), ("E_kin", C.c_double), ("E_int", C.c_double),
+                ("E_mag", C.c_double), ("entropy", C.c_double), ("div_B", C.c_double), ("B_max", C.c_double),
+                ("rho_min", C.c_double), ("p_min", C.c_double), ("eta_max", C.c_double),
+                ("n_rejections", C.c_int), ("reserved", C.c_int)]
+
+
+_lib = None
+
+# name: (restype, argtypes); "P" = generic pointer
+_SIGS = {
+    "mhd_create": (C.c_int, [C.POINTER(Mesh), C.c_int, C.c_int, C.c_double, C.POINTER(C.c_void_p)]),
+    "mhd_destroy": (None, [C.c_void_p]),
+    "mhd_set_params": (C.c_int, [C.c_void_p, C.POINTER(Params)]),
+    "mhd_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mhd_sizes": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_longlong)] * 4),
+    "mhd_node_coords": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "mhd_set_state": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int]),
+    "mhd_get_state": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int]),
+    "mhd_set_primitive": (C.c_int, [C.c_void_p] + [C.c_void_p] * 3 + [C.c_int]),
+    "mhd_set_B_from_potential": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_int]),
+    "mhd_compute_dt": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "mhd_strang_step": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
+    "mhd_strang_steps": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int)]),
+    "mhd_substep": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
+    "mhd_hydro_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "mhd_mag_rhs": (C.c_int, [C.c_void_p] + [C.c_void_p] * 12 + [C.c_int]),
+    "mhd_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(Diag)]),
+    "mhd_get_eta": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mhd_launch_count": (C.c_longlong, [C.c_void_p]),
+    "mhd_status_string": (C.c_char_p, [C.c_int]),
+    "mhd_last_error": (C.c_char_p, []),
+}
+
+
+def lib():
+    """Load libmhd.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing; build it with paper_2609_10849_b300/build.py")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code < 0:
+        raise MhdError(code, lib().mhd_last_error().decode())
+    return code
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or torch tensor (float64, contiguous)."""
+    if a is None:
+        return None, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous() or str(a.dtype) != "torch.float64":
+            raise ValueError("tensors must be contiguous float64")
+        return C.c_void_p(a.data_ptr()), int(a.is_cuda)
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise ValueError("arrays must be C-contiguous float64 numpy arrays")
+    return a.ctypes.data_as(C.c_void_p), 0
+
+
+def _ptrs(*arrs):
+    ps = [_ptr(a) for a in arrs]
+    dev = {d for p, d in ps if p is not None}
+    if len(dev) > 1:
+        raise ValueError("mix of host and device buffers")
+    return [p for p, _ in ps], (dev.pop() if dev else 0)
+
+
+class Solver:
+    """One periodic mesh with DGSEM degree p and magnetic degree k."""
+
+    def __init__(self, nx, ny, p, k, gamma, domain=(0.0, 1.0, 0.0, 1.0)):
+        self.nx, self.ny, self.p, self.k, self.gamma = nx, ny, p, k, gamma
+        self.domain = tuple(float(v) for v in domain)
+        mesh = Mesh(nx, ny, *self.domain)
+        h = C.c_void_p()
+        _check(lib().mhd_create(C.byref(mesh), p, k, gamma, C.byref(h)))
+        self._h = h
+        K, N, G, Z = (C.c_longlong() for _ in range(4))
+        _check(lib().mhd_sizes(h, C.byref(K), C.byref(N), C.byref(G), C.byref(Z)))
+        self.K, self.N, self.G, self.Z = K.value, N.value, G.value, Z.value
+        self.params = dict(oe_hydro=0, oe_vel=0, pp=0, ar=0, s_H=0.02, s_M=0.02, C_s=5.0, C_eta=0.2, cfl=0.4,
+                           max_halvings=20)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mhd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, **kw):
+        self.params.update(kw)
+        _check(lib().mhd_set_params(self._h, C.byref(Params(**self.params))))
+
+    def set_stream(self, stream_ptr: int):
+        _check(lib().mhd_set_stream(self._h, C.c_void_p(stream_ptr)))
+
+    def coords(self, which):
+        size = {"dg": self.N, "w": self.G, "bz": self.Z}[which]
+        X, Y = np.zeros(size), np.zeros(size)
+        _check(lib().mhd_node_coords(self._h, {"dg": 0, "w": 1, "bz": 2}[which], _ptr(X)[0], _ptr(Y)[0]))
+        return X, Y
+
+    def set_state(self, U, Bx, By, Bz):
+        (pU, pX, pY, pZ), dev = _ptrs(U, Bx, By, Bz)
+        _check(lib().mhd_set_state(self._h, pU, pX, pY, pZ, dev))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = (np.zeros((5, self.N)), np.zeros(self.G), np.zeros(self.G), np.zeros(self.Z))
+        (pU, pX, pY, pZ), dev = _ptrs(*out)
+        _check(lib().mhd_get_state(self._h, pU, pX, pY, pZ, dev))
+        return out
+
+    def set_primitive(self, rho, u, p):
+        (a, b, c), dev = _ptrs(rho, u, p)
+        _check(lib().mhd_set_primitive(self._h, a, b, c, dev))
+
+    def set_B_from_potential(self, Az, Bx0, By0, Bz):
+        (a, z), dev = _ptrs(Az, Bz)
+        _check(lib().mhd_set_B_from_potential(self._h, a, float(Bx0), float(By0), z, dev))
+
+    def compute_dt(self):
+        dt = C.c_double()
+        _check(lib().mhd_compute_dt(self._h, C.byref(dt)))
+        return dt.value
+
+    def strang_step(self, dt=0.0):
+        taken = C.c_double()
+        st = _check(lib().mhd_strang_step(self._h, float(dt), C.byref(taken)))
+        return st, taken.value
+
+    def strang_steps(self, dt, nsteps):
+        done = C.c_int()
+        _check(lib().mhd_strang_steps(self._h, float(dt), int(nsteps), C.byref(done)))
+        return done.value
+
+    def substep(self, which, tau):
+        return _check(lib().mhd_substep(self._h, {"H": 0, "M": 1}[which], float(tau)))
+
+    def hydro_rhs(self, U):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        L = np.zeros_like(U)
+        _check(lib().mhd_hydro_rhs(self._h, _ptr(U)[0], _ptr(L)[0], 0))
+        return L
+
+    def mag_rhs(self, rho, e, u, Bx, By, Bz, eta=None):
+        f = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+        eta = np.zeros(self.K) if eta is None else eta
+        ins = [f(a) for a in (rho, e, u, Bx, By, Bz, eta)]
+        de, du = np.zeros(self.N), np.zeros((3, self.N))
+        dBx, dBy, dBz = np.zeros(self.G), np.zeros(self.G), np.zeros(self.Z)
+        ps = [_ptr(a)[0] for a in ins + [de, du, dBx, dBy, dBz]]
+        _check(lib().mhd_mag_rhs(self._h, *ps, 0))
+        return dict(de=de, du=du, dBx=dBx, dBy=dBy, dBz=dBz)
+
+    def diagnostics(self):
+        d = Diag()
+        _check(lib().mhd_diagnostics(self._h, C.byref(d)))
+        return dict(mass=d.mass, mom_x=d.mom[0], mom_y=d.mom[1], mom_z=d.mom[2], E_kin=d.E_kin, E_int=d.E_int,
+                    E_mag=d.E_mag, entropy=d.entropy, div_B=d.div_B, B_max=d.B_max, rho_min=d.rho_min,
+                    p_min=d.p_min, eta_max=d.eta_max)
+
+    def eta(self):
+        out = np.zeros(self.K)
+        _check(lib().mhd_get_eta(self._h, _ptr(out)[0]))
+        return out
+
+    def launch_count(self):
+        return lib().mhd_launch_count(self._h)

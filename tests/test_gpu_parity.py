@@ -1,0 +1,185 @@
+"""GPU <-> oracle parity of the CUDA path, called through the C ABI.
+
+Tolerance: 1e-12 relative max-norm per step (1e-9 after 100 steps), the
+spec bar for FP64 parity; per-kernel residuals are held to the same
+1e-12 relative to the largest residual entry.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_2609_10849_b300 import workloads
+from tests.test_oracle_hydro import smooth_random_state
+from tests.test_oracle_magnetic import random_mag_state
+from tests.util import oracle_state
+
+pytestmark = pytest.mark.gpu
+
+PK = [(1, 0), (1, 1), (2, 1), (2, 2), (3, 2), (3, 3), (4, 3), (4, 4)]
+
+
+def rel(a, b, floor=0.0):
+    """max|a - b| / max(max|b|, floor): relative max-norm; the floor is the
+    scale of the quantity where the field itself is zero up to roundoff."""
+    a, b = np.asarray(a), np.asarray(b)
+    den = max(np.abs(b).max(), floor)
+    return np.abs(a - b).max() / (den if den > 0 else 1.0)
+
+
+def solver_like(o):
+    from paper_2609_10849_b300.mhd import Solver
+    return Solver(o.nx, o.ny, o.p, o.m, o.gamma, o.domain)
+
+
+def copy_state(o, s):
+    s.set_state(*o.get_state())
+
+
+def compare_state(o, s, tol):
+    Uo, Bxo, Byo, Bzo = o.get_state()
+    Ug, Bxg, Byg, Bzg = s.get_state()
+    bscale = max(np.abs(Bxo).max(), np.abs(Byo).max(), np.abs(Bzo).max())
+    errs = [rel(Ug[c], Uo[c], np.abs(Uo).max()) for c in range(5)] + \
+        [rel(Bxg, Bxo, bscale), rel(Byg, Byo, bscale), rel(Bzg, Bzo, bscale)]
+    assert max(errs) <= tol, errs
+    return max(errs)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("mesh", [(5, 4), (7, 3), (1, 1), (2, 1)])
+def test_hydro_rhs(p, mesh):
+    rng = np.random.default_rng(p * 10 + mesh[0])
+    o = Oracle(*mesh, p, p, 1.4, (0.0, 1.0, 0.0, 0.8))
+    U = smooth_random_state(o, rng)
+    Lo = o.hydro_rhs(U)
+    s = solver_like(o)
+    Lg = s.hydro_rhs(U.copy())
+    scale = np.abs(Lo).max()  # a single periodic element has a roundoff-level mass residual
+    for c in range(5):
+        assert rel(Lg[c], Lo[c], 1e-3 * scale) <= 1e-12, (c, rel(Lg[c], Lo[c]))
+
+
+@pytest.mark.parametrize("pk", PK)
+@pytest.mark.parametrize("resistive", [False, True])
+def test_mag_rhs(pk, resistive):
+    p, k = pk
+    rng = np.random.default_rng(100 + 10 * p + k)
+    o = Oracle(5, 3, p, k, 5 / 3, (0.0, 1.3, 0.0, 0.7))
+    rho, e, u, Bx, By, Bz = random_mag_state(o, rng)
+    eta = rng.uniform(0.0, 0.3, o.K) if resistive else np.zeros(o.K)
+    eta[::3] = 0.0
+    ro = o.mag_rhs(rho, e, u, Bx, By, Bz, eta)
+    s = solver_like(o)
+    rg = s.mag_rhs(rho, e, u, Bx, By, Bz, eta)
+    for key in ("du", "dBx", "dBy", "dBz"):
+        assert rel(rg[key], ro[key]) <= 1e-12, (key, rel(rg[key], ro[key]))
+    if resistive:
+        assert rel(rg["de"], ro["de"]) <= 1e-12
+    else:
+        assert np.all(rg["de"] == 0.0)
+
+
+@pytest.mark.parametrize("which", ["H", "M"])
+@pytest.mark.parametrize("pk", [(2, 2), (3, 3), (3, 2), (4, 4)])
+def test_substep(which, pk):
+    wl = workloads.orszag_tang()
+    o = oracle_state(wl, 6, 5, *pk)
+    s = solver_like(o)
+    copy_state(o, s)
+    tau = 0.5 * o.cfl_dt()
+    assert o.substep(which, tau) == 0
+    s.substep(which, tau)
+    compare_state(o, s, 1e-12)
+
+
+def test_cfl_dt():
+    wl = workloads.orszag_tang()
+    o = oracle_state(wl, 8, 8, 3, 3)
+    s = solver_like(o)
+    copy_state(o, s)
+    assert s.compute_dt() == pytest.approx(o.cfl_dt(), rel=1e-14)
+
+
+def test_potential_field_and_coords():
+    from paper_2609_10849_b300.mhd import Solver
+    wl = workloads.orszag_tang()
+    o = oracle_state(wl, 6, 4, 3, 3)
+    s = Solver(6, 4, 3, 3, wl["gamma"], wl["domain"])
+    for which in ("dg", "w", "bz"):
+        Xo, Yo = o.coords(which)
+        Xg, Yg = s.coords(which)
+        assert np.abs(Xo - Xg).max() < 1e-15 and np.abs(Yo - Yg).max() < 1e-15
+    XW, YW = s.coords("w")
+    XZ, YZ = s.coords("bz")
+    s.set_B_from_potential(wl["Az"](XW, YW), *wl["B0"], wl["fields"](XZ, YZ)[5])
+    _, Bxg, Byg, _ = s.get_state()
+    _, Bxo, Byo, _ = o.get_state()
+    assert rel(Bxg, Bxo) <= 1e-13 and rel(Byg, Byo) <= 1e-13
+
+
+def test_strang_alfven_per_step():
+    """Config 1 (circularly polarised Alfven wave, 16 x 16, p = k = 3): 1e-12 per step."""
+    wl = workloads.alfven_rotated()
+    o = oracle_state(wl, 16, 16, 3, 3)
+    o.set_params(cfl=0.4)
+    s = solver_like(o)
+    copy_state(o, s)
+    for _ in range(3):
+        dt = o.cfl_dt()
+        assert s.compute_dt() == pytest.approx(dt, rel=1e-13)
+        o.strang_step(dt)
+        s.strang_step(dt)
+        compare_state(o, s, 1e-12)
+        copy_state(o, s)  # per-step parity from an identical input
+
+
+def test_strang_alfven_100_steps():
+    """Config 1 over 100 Strang steps: within 1e-9 of the oracle."""
+    wl = workloads.alfven_rotated()
+    o = oracle_state(wl, 16, 16, 3, 3)
+    s = solver_like(o)
+    copy_state(o, s)
+    dt = o.cfl_dt()
+    for _ in range(100):
+        o.strang_step(dt)
+    assert s.strang_steps(dt, 100) == 100
+    compare_state(o, s, 1e-9)
+    d = s.diagnostics()
+    do = o.diagnostics()
+    assert d["mass"] == pytest.approx(do["mass"], rel=1e-14)
+    assert d["div_B"] <= 1e-12 * d["B_max"]
+
+
+def tiled(o, reps):
+    """Host state of the oracle tiled reps x reps times (same element geometry)."""
+    U, Bx, By, Bz = o.get_state()
+    n2, mm = o.n2, o.mm
+    U4 = U.reshape(5, o.ny, o.nx, n2)
+    Ut = np.tile(U4, (1, reps, reps, 1)).reshape(5, -1)
+    Bzt = np.tile(Bz.reshape(o.ny, o.nx, mm * mm), (reps, reps, 1)).ravel()
+    Bxt = np.tile(Bx.reshape(o.ny * mm, o.nx * mm), (reps, reps)).ravel()
+    Byt = np.tile(By.reshape(o.ny * mm, o.nx * mm), (reps, reps)).ravel()
+    return Ut, Bxt, Byt, Bzt
+
+
+def test_full_size_tiled_parity():
+    """256 x 256 elements (the Orszag-Tang mesh size) in the bench launch
+    configuration: a state tiled 16 x 16 from a 16 x 16 oracle state must give
+    the oracle's step on every tile."""
+    from paper_2609_10849_b300.mhd import Solver
+    wl = workloads.orszag_tang()
+    o = oracle_state(wl, 16, 16, 3, 3)
+    reps = 16
+    x0, x1, y0, y1 = o.domain
+    s = Solver(16 * reps, 16 * reps, 3, 3, wl["gamma"], (x0, x0 + reps * (x1 - x0), y0, y0 + reps * (y1 - y0)))
+    s.set_state(*tiled(o, reps))
+    dt = o.cfl_dt()
+    assert s.compute_dt() == pytest.approx(dt, rel=1e-13)
+    o.strang_step(dt)
+    s.strang_step(dt)
+    U, Bx, By, Bz = s.get_state()
+    Ut, Bxt, Byt, Bzt = tiled(o, reps)
+    for a, b in [(U, Ut), (Bx, Bxt), (By, Byt), (Bz, Bzt)]:
+        assert rel(a, b) <= 1e-12
+    d = s.diagnostics()
+    assert d["div_B"] <= 1e-12 * d["B_max"]
