@@ -1,0 +1,306 @@
+#!/usr/bin/env python
+"""Throughput benchmark: FP64 DOF-updates/s of the H-M-H Strang step.
+
+Workload: the Orszag-Tang vortex on a 256 x 256 periodic mesh of [0,1]^2,
+DGSEM degree p = 3, magnetic degree k = 3, gamma = 5/3, synthetic analytic
+initial state, CFL 0.4 time step fixed at its t = 0 value.  One "step" is one
+full Strang step S^dt = Phi_H^{dt/2} o Phi_M^{dt} o Phi_H^{dt/2}.
+DOFs per element: 5 (p+1)^2 + 3 (k+1)^2 = 128.
+
+  python bench.py --gpus N --steps K --warmup W [--impl ours|reference]
+
+N > 1 runs under torchrun: every rank runs an independent replica (the
+method has no data-path collective; weak scaling), the timed region is
+bracketed by a barrier and synchronisation and the max over ranks is used.
+--impl reference times the CPU oracle (plain FP64, one core) on a bounded
+sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "FP64 DOF-updates/s per Strang step at p=3"
+UNIT = "DOF-updates/s"
+NOMINAL_FP64_TFLOPS = 1.25  # B300 dense FP64, nominal (profiling recipe table)
+
+
+def workload_config(stab, mesh=256):
+    return dict(workload=f"orszag_tang_{mesh}x{mesh}_p3k3", mesh=[mesh, mesh], domain=[0.0, 1.0, 0.0, 1.0], p=3, k=3,
+                gamma=5.0 / 3.0, dofs_per_element=128, cfl=0.4, stabilization=stab,
+                l2="working set per step > 126 MB L2 (state + stage buffers ~0.5 GB), no flush needed")
+
+
+def dofs_per_element(p, k):
+    return 5 * (p + 1) ** 2 + 3 * (k + 1) ** 2
+
+
+def vol_flops_per_element(p):
+    """Algorithmic FP64 flops of one launch of the volume kernel per element
+    (FMA = 2, add/mul/reciprocal = 1): 52 per entropy-conservative pair
+    (p (p+1)^2 pairs), 16 per node for the primitives, 5 (4p + 3) per node for
+    the gather with D, 8 per face node for the end terms, 4 per node-component
+    for the stage combination and 2 per node-component for the raw average."""
+    n = p + 1
+    n2 = n * n
+    return 52 * p * n2 + 16 * n2 + 5 * n2 * (4 * p + 3) + 5 * 4 * n * 2 + 5 * n2 * 4 + 5 * n2 * 2 + 8
+
+
+def make_solver(stab_params, mesh=256):
+    from paper_2609_10849_b300 import workloads
+    from paper_2609_10849_b300.mhd import Solver
+    wl = workloads.orszag_tang()
+    s = Solver(mesh, mesh, 3, 3, wl["gamma"], wl["domain"])
+    X, Y = s.coords("dg")
+    rho, ux, uy, uz, p, _ = wl["fields"](X, Y)
+    s.set_primitive(np.ascontiguousarray(rho), np.ascontiguousarray(np.stack([ux, uy, uz])),
+                    np.ascontiguousarray(p))
+    XW, YW = s.coords("w")
+    XZ, YZ = s.coords("bz")
+    s.set_B_from_potential(np.ascontiguousarray(wl["Az"](XW, YW)), *wl["B0"],
+                           np.ascontiguousarray(wl["fields"](XZ, YZ)[5]))
+    if stab_params:
+        s.set_params(**stab_params)
+    return s
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.device)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(steps=4, n=64):
+    """The oracle as it stands, single-threaded, on a bounded sample of the same
+    workload: the Orszag-Tang vortex on an n x n mesh, p = k = 3."""
+    import oracle
+    from paper_2609_10849_b300 import workloads
+    wl = workloads.orszag_tang()
+    o = oracle.Oracle(n, n, 3, 3, wl["gamma"], wl["domain"])
+    X, Y = o.coords("dg")
+    rho, ux, uy, uz, pr, _ = wl["fields"](X, Y)
+    XW, YW = o.coords("w")
+    XZ, YZ = o.coords("bz")
+    Bx, By = o.b_from_potential(wl["Az"](XW, YW), *wl["B0"])
+    o.set_primitive(rho, np.stack([ux, uy, uz]), pr, Bx, By, wl["fields"](XZ, YZ)[5])
+    dt = o.cfl_dt()
+    o.strang_step(dt)  # warm-up
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.strang_step(dt)
+    el = time.perf_counter() - t0
+    return dict(value=dofs_per_element(3, 3) * n * n * steps / el, unit=UNIT, cores=1, kind="oracle",
+                sample=f"{steps} Strang steps of the same Orszag-Tang workload on a {n}x{n} mesh (p=k=3), "
+                       f"serial C++ oracle, {el:.1f} s")
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    stab = {"oe_hydro": 0, "pp": 0, "ar": 0, "oe_vel": 0}
+    n = 32
+    import oracle
+    from paper_2609_10849_b300 import workloads
+    wl = workloads.orszag_tang()
+    o = oracle.Oracle(n, n, 3, 3, wl["gamma"], wl["domain"])
+    X, Y = o.coords("dg")
+    rho, ux, uy, uz, pr, _ = wl["fields"](X, Y)
+    XW, YW = o.coords("w")
+    XZ, YZ = o.coords("bz")
+    Bx, By = o.b_from_potential(wl["Az"](XW, YW), *wl["B0"])
+    o.set_primitive(rho, np.stack([ux, uy, uz]), pr, Bx, By, wl["fields"](XZ, YZ)[5])
+    dt = o.cfl_dt()
+    for _ in range(args.warmup):
+        o.strang_step(dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.strang_step(dt)
+    el = time.perf_counter() - t0
+    value = dofs_per_element(3, 3) * n * n * args.steps / el
+    sample = (f"each step: one Strang step of the Orszag-Tang workload on a {n}x{n} sample mesh (p=k=3), serial "
+              f"C++ oracle")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(stab, args.mesh),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mesh", type=int, default=256, help="elements per direction (256 is the benchmark workload)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2609_10849_b300 import mhd
+    stab = {"oe_hydro": 0, "pp": 0, "ar": 0, "oe_vel": 0}
+    s = make_solver(None, args.mesh)
+    stream = torch.cuda.current_stream()
+    s.set_stream(stream.cuda_stream)
+    dt = s.compute_dt()
+    dofs = dofs_per_element(3, 3) * s.K
+
+    s.strang_steps(dt, args.warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = s.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        e0.record(stream)
+        s.strang_steps(dt, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = s.launch_count() - l0
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * dofs * args.steps / (ms * 1e-3)
+
+    # per-kernel event timing of the same steps (separate pass) for the roofline
+    s.profile_kernels(True)
+    s.strang_steps(dt, args.steps)
+    kt = s.kernel_times()
+    s.profile_kernels(False)
+    vol_ms = kt["vol"][0] / kt["vol"][1]
+    vol_flops = vol_flops_per_element(3) * s.K
+    achieved = vol_flops / (vol_ms * 1e-3) / 1e12
+    measured_peak = mhd.fp64_peak_tflops()
+    step_ms_sum = sum(v[0] for v in kt.values())
+    roofline = {"bound": "alu", "kernel": "k_vol<3> (entropy-conservative volume term + SSP stage)",
+                "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None,
+                "peak_source": "nominal B300 dense FP64 (1.25 TFLOP/s, profiling recipe)",
+                "peak_measured_dfma_tflops": measured_peak, "frac_of_measured_dfma": achieved / measured_peak,
+                "flops_per_launch": vol_flops, "avg_launch_ms": vol_ms,
+                "kernel_share_of_step": {k: v[0] / step_ms_sum for k, v in kt.items()}}
+
+    # end-to-end through the public API with pinned host buffers
+    U, Bx, By, Bz = (torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+                     for n in (5 * s.N, s.G, s.G, s.Z))
+    host = (U.reshape(5, s.N), Bx, By, Bz)
+    s.get_state(host)
+    e2e_steps = max(5, args.steps // 5)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_state(*host)
+        s.strang_step(dt)
+        s.get_state(host)
+    e2e_el = time.perf_counter() - t0
+    nbytes = 8 * (5 * s.N + 2 * s.G + s.Z)
+    e2e = {"value": world * dofs * e2e_steps / e2e_el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (analytic Orszag-Tang initial state)",
+            "config": dict(workload_config(stab, args.mesh), parallelism=f"replicas{world}", dt=dt,
+                           stabilization_note="stage stabilisation kernels not built yet: OE/PP/A.R./velocity "
+                                              "filter off"),
+            "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

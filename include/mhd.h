@@ -147,6 +147,23 @@ int mhd_get_eta(mhd_ctx* ctx, double* eta);
 /* Number of kernel launches enqueued by the context since creation. */
 long long mhd_launch_count(const mhd_ctx* ctx);
 
+/* Instrumentation (no counterpart in the paper): with enable != 0 every
+ * subsequent launch group is bracketed by CUDA events on the context stream,
+ * grouped in classes 0 face flux, 1 volume + stage combination, 2-4 magnetic
+ * stage (one group per SSP stage: J loads, E loads + velocity, curl update),
+ * 5 nodal exchange, 6 hydro stabilisation, 7 A.R. coefficient, 8 velocity
+ * OE.  Enabling clears previous records. */
+int mhd_profile_kernels(mhd_ctx* ctx, int enable);
+
+/* Total event time in ms and number of groups per class since profiling was
+ * enabled (arrays of nclasses entries); returns the number of classes. */
+int mhd_kernel_times(mhd_ctx* ctx, double* ms, long long* counts, int nclasses);
+
+/* Instrumentation (no counterpart in the paper): measured FP64 FMA issue rate
+ * of the current device in TFLOP/s (FMA = 2 flops), from a probe kernel with
+ * every lane active.  Allocates and frees a small buffer. */
+int mhd_fp64_peak(double* tflops);
+
 const char* mhd_status_string(int status);
 const char* mhd_last_error(void);
 

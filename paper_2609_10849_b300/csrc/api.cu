@@ -81,6 +81,10 @@ struct mhd_ctx {
   unsigned* h_status;
   long long launches;
   std::vector<void*> allocs;
+  // optional per-kernel-class event timing (bench instrumentation)
+  bool profiling;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_rec;
 };
 
 namespace {
@@ -105,6 +109,32 @@ cudaError_t copy_out(mhd_ctx* c, double* dst, const double* src, size_t n, int o
   return cudaStreamSynchronize(c->st);
 }
 
+// Kernel classes of the event profiler.
+enum { KC_FACE = 0, KC_VOL, KC_MAG_J, KC_MAG_E, KC_MAG_B, KC_EXCH, KC_STAB_H, KC_STAB_ETA, KC_STAB_VEL, KC_COUNT };
+
+// Scoped event pair around the launches of one kernel class.
+struct Prof {
+  mhd_ctx* c;
+  int kc;
+  cudaEvent_t a, b;
+  Prof(mhd_ctx* c_, int kc_) : c(c_), kc(kc_), a(nullptr), b(nullptr) {
+    if (!c->profiling) return;
+    size_t used = 2 * c->ev_rec.size();
+    while (c->ev_pool.size() < used + 2) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      c->ev_pool.push_back(e);
+    }
+    a = c->ev_pool[used];
+    b = c->ev_pool[used + 1];
+    c->ev_rec.push_back({kc, {a, b}});
+    cudaEventRecord(a, c->st);
+  }
+  ~Prof() {
+    if (a) cudaEventRecord(b, c->st);
+  }
+};
+
 const double RK_A[3] = {0.0, 0.75, 1.0 / 3.0};
 const double RK_B[3] = {1.0, 0.25, 2.0 / 3.0};
 
@@ -114,11 +144,13 @@ void hydro_substep(mhd_ctx* c, double fac) {
   double* out[3] = {c->S1, c->S2, c->U};
   bool stab = c->prm.oe_hydro || c->prm.pp;
   for (int s = 0; s < 3; ++s) {
-    hydro_face(c->p, in[s], c->Fx, c->Fy, c->M, c->st);
-    hydro_vol(c->p, 1, in[s], c->U, c->Fx, c->Fy, out[s], stab ? c->avg : nullptr, c->status, c->T, c->M, c->dt, fac,
-              RK_A[s], RK_B[s], s == 0, c->st);
+    { Prof pr(c, KC_FACE); hydro_face(c->p, in[s], c->Fx, c->Fy, c->M, c->st); }
+    { Prof pr(c, KC_VOL);
+      hydro_vol(c->p, 1, in[s], c->U, c->Fx, c->Fy, out[s], stab ? c->avg : nullptr, c->status, c->T, c->M, c->dt,
+                fac, RK_A[s], RK_B[s], s == 0, c->st); }
     c->launches += 2;
     if (stab) {
+      Prof pr(c, KC_STAB_H);
       stab_hydro(c->p, out[s], c->avg, c->status, c->T, c->M, c->prm, c->dt, fac, c->work, c->st);
       c->launches += 4;
     }
@@ -129,14 +161,16 @@ void hydro_substep(mhd_ctx* c, double fac) {
 // exchange before and after (§3.4.1).
 void mag_substep(mhd_ctx* c, double fac) {
   const size_t N = c->N;
-  cons_to_prim(c->U, c->Y0, N, c->st);
+  { Prof pr(c, KC_EXCH); cons_to_prim(c->U, c->Y0, N, c->st); }
   c->launches++;
   int resistive = c->prm.ar && c->prm.C_eta != 0.0;
   if (resistive) {
+    Prof pr(c, KC_STAB_ETA);
     stab_eta(c->p, c->k, c->U, c->Y0, c->B, c->T, c->M, c->prm, c->eta, c->work, c->st);
     c->launches += 3;
   }
   if (c->prm.oe_vel) {
+    Prof pr(c, KC_STAB_VEL);
     stab_vel_prep(c->p, c->U, c->chol, c->T, c->M, c->st);
     c->launches++;
   }
@@ -145,14 +179,19 @@ void mag_substep(mhd_ctx* c, double fac) {
   const double* Yin[3] = {c->Y0, c->Ya, c->Yb};
   double* Yout[3] = {c->Ya, c->Yb, c->Y0};
   for (int s = 0; s < 3; ++s) {
-    mag_stage(c->p, c->k, 1, Bin[s], Yin[s] + N, Yin[s], c->U, c->eta, resistive, c->B, c->Y0 + N, c->Y0, Bout[s],
-              Yout[s] + N, Yout[s], c->LJ, c->LE, c->T, c->M, c->dt, fac, RK_A[s], RK_B[s], s == 0, c->st);
+    {
+      Prof pr(c, KC_MAG_E);
+      mag_stage(c->p, c->k, 1, Bin[s], Yin[s] + N, Yin[s], c->U, c->eta, resistive, c->B, c->Y0 + N, c->Y0,
+                Bout[s], Yout[s] + N, Yout[s], c->LJ, c->LE, c->T, c->M, c->dt, fac, RK_A[s], RK_B[s], s == 0, c->st);
+    }
     c->launches += 3;
     if (c->prm.oe_vel) {
+      Prof pr(c, KC_STAB_VEL);
       stab_vel(c->p, c->k, c->U, Yout[s], Bout[s], c->chol, c->T, c->M, c->prm, c->dt, fac, c->work, c->st);
       c->launches += 3;
     }
   }
+  Prof pr(c, KC_EXCH);
   prim_to_cons(c->Y0, c->U, N, c->st);
   c->launches++;
 }
@@ -263,6 +302,7 @@ oom:
 void mhd_destroy(mhd_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
+  for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   if (c->own_stream && c->st) cudaStreamDestroy(c->st);
@@ -551,5 +591,26 @@ int mhd_get_eta(mhd_ctx* c, double* eta) {
 }
 
 long long mhd_launch_count(const mhd_ctx* c) { return c ? c->launches : 0; }
+
+int mhd_profile_kernels(mhd_ctx* c, int enable) {
+  if (!c) return fail(MHD_EINVAL, "null context");
+  cudaStreamSynchronize(c->st);
+  c->profiling = enable != 0;
+  c->ev_rec.clear();
+  return MHD_OK;
+}
+
+int mhd_kernel_times(mhd_ctx* c, double* ms, long long* counts, int nclasses) {
+  if (!c || !ms || !counts) return fail(MHD_EINVAL, "null argument");
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return cuda_fail(e, "kernel_times");
+  for (int i = 0; i < nclasses; ++i) { ms[i] = 0.0; counts[i] = 0; }
+  for (auto& r : c->ev_rec) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.second.first, r.second.second) != cudaSuccess) continue;
+    if (r.first < nclasses) { ms[r.first] += t; counts[r.first]++; }
+  }
+  return KC_COUNT;
+}
 
 }  // extern "C"

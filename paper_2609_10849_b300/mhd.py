@@ -66,6 +66,9 @@ _SIGS = {
     "mhd_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(Diag)]),
     "mhd_get_eta": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mhd_launch_count": (C.c_longlong, [C.c_void_p]),
+    "mhd_profile_kernels": (C.c_int, [C.c_void_p, C.c_int]),
+    "mhd_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "mhd_fp64_peak": (C.c_int, [C.POINTER(C.c_double)]),
     "mhd_status_string": (C.c_char_p, [C.c_int]),
     "mhd_last_error": (C.c_char_p, []),
 }
@@ -111,6 +114,13 @@ def _ptrs(*arrs):
     if len(dev) > 1:
         raise ValueError("mix of host and device buffers")
     return [p for p, _ in ps], (dev.pop() if dev else 0)
+
+
+def fp64_peak_tflops():
+    """Measured FP64 FMA issue rate of the current device (TFLOP/s)."""
+    v = C.c_double()
+    _check(lib().mhd_fp64_peak(C.byref(v)))
+    return v.value
 
 
 class Solver:
@@ -220,3 +230,17 @@ class Solver:
 
     def launch_count(self):
         return lib().mhd_launch_count(self._h)
+
+    KERNEL_CLASSES = ("face", "vol", "mag_J", "mag_stage", "mag_B", "exchange", "stab_hydro", "stab_eta",
+                      "stab_vel")
+
+    def profile_kernels(self, enable=True):
+        _check(lib().mhd_profile_kernels(self._h, int(enable)))
+
+    def kernel_times(self):
+        """{class: (total ms, launch groups)} since profiling was enabled."""
+        n = len(self.KERNEL_CLASSES)
+        ms = np.zeros(n)
+        cnt = np.zeros(n, dtype=np.int64)
+        _check(lib().mhd_kernel_times(self._h, ms.ctypes.data_as(C.c_void_p), cnt.ctypes.data_as(C.c_void_p), n))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.KERNEL_CLASSES) if cnt[i]}
