@@ -159,6 +159,27 @@ int mhd_profile_kernels(mhd_ctx* ctx, int enable);
  * enabled (arrays of nclasses entries); returns the number of classes. */
 int mhd_kernel_times(mhd_ctx* ctx, double* ms, long long* counts, int nclasses);
 
+/* Hydro residual L_E of a conservative state without any device allocation.
+ * The paper has no counterpart: this exists for callers that cannot allocate
+ * device memory themselves, for example code running while all device memory
+ * belongs to a caching allocator or to a fixed budget of the host application,
+ * or a latency-critical loop where a cudaMalloc/cudaFree pair is not
+ * acceptable.  It computes what mhd_hydro_rhs computes, without a context: U
+ * and L are caller-owned DEVICE buffers [5][K (p+1)^2] in the DG layout above;
+ * the work is enqueued on `stream` (a cudaStream_t, 0 = legacy default stream)
+ * and the call returns without synchronising.
+ * Scratch: the face fluxes live in one file-scope device array of 2^20
+ * doubles (8 MiB) that every GPU using the library keeps until the process
+ * exits.  Meshes needing more than 10 K (p+1) <= 2^20 doubles are rejected
+ * with MHD_EINVAL (p = 3: K <= 26,214 elements).  All calls share the array:
+ * calls whose kernels overlap on the GPU race and must be serialised by the
+ * caller.  Nothing in it needs to start at zero (each call writes what it
+ * reads first).  Set-up: the first call on a device looks up the array's
+ * device address and uploads the 1D tables for degree p (synchronous copies
+ * to device symbols); make that first call before any stream capture.
+ * Errors: MHD_EINVAL, MHD_ECUDA (message in mhd_last_error). */
+int mhd_hydro_rhs_static(const mhd_mesh_t* mesh, int p, double gamma, const double* U, double* L, void* stream);
+
 /* Instrumentation (no counterpart in the paper): measured FP64 FMA issue rate
  * of the current device in TFLOP/s (FMA = 2 flops), from a probe kernel with
  * every lane active.  Allocates and frees a small buffer. */

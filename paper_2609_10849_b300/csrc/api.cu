@@ -44,12 +44,19 @@ void stab_vel(int p, int k, const double* rho, double* Y, const double* B, const
               const Mesh& M, const Stab& prm, const double* dtp, double dtfac, double* work, cudaStream_t st);
 size_t stab_work_doubles(int p, int k, const Mesh& M);
 size_t stab_chol_doubles(int p, const Mesh& M);
+void set_error_message(const char* msg);
 }  // namespace mhd
 
 using namespace mhd;
 
 namespace {
 thread_local std::string g_err;
+}  // namespace
+
+// Lets the allocation-free entry point report through mhd_last_error().
+void mhd::set_error_message(const char* msg) { g_err = msg; }
+
+namespace {
 
 int fail(int code, const std::string& msg) {
   g_err = msg;

@@ -69,6 +69,7 @@ _SIGS = {
     "mhd_profile_kernels": (C.c_int, [C.c_void_p, C.c_int]),
     "mhd_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "mhd_fp64_peak": (C.c_int, [C.POINTER(C.c_double)]),
+    "mhd_hydro_rhs_static": (C.c_int, [C.POINTER(Mesh), C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mhd_status_string": (C.c_char_p, [C.c_int]),
     "mhd_last_error": (C.c_char_p, []),
 }
@@ -121,6 +122,17 @@ def fp64_peak_tflops():
     v = C.c_double()
     _check(lib().mhd_fp64_peak(C.byref(v)))
     return v.value
+
+
+def hydro_rhs_static(nx, ny, p, gamma, domain, U, L, stream=0):
+    """Hydro residual of the device tensor U [5, K (p+1)^2] into the device
+    tensor L without any device allocation (fixed library scratch; calls that
+    overlap on the GPU race).  Enqueued on `stream`; does not synchronise."""
+    mesh = Mesh(nx, ny, *(float(v) for v in domain))
+    (pu, pl), dev = _ptrs(U, L)
+    if not dev:
+        raise ValueError("U and L must be device tensors")
+    _check(lib().mhd_hydro_rhs_static(C.byref(mesh), p, float(gamma), pu, pl, C.c_void_p(stream)))
 
 
 class Solver:
