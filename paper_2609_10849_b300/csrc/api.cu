@@ -159,7 +159,7 @@ void hydro_substep(mhd_ctx* c, double fac) {
     if (stab) {
       Prof pr(c, KC_STAB_H);
       stab_hydro(c->p, out[s], c->avg, c->status, c->T, c->M, c->prm, c->dt, fac, c->work, c->st);
-      c->launches += 4;
+      c->launches += c->prm.oe_hydro ? 4 : 1;
     }
   }
 }
@@ -175,6 +175,8 @@ void mag_substep(mhd_ctx* c, double fac) {
     Prof pr(c, KC_STAB_ETA);
     stab_eta(c->p, c->k, c->U, c->Y0, c->B, c->T, c->M, c->prm, c->eta, c->work, c->st);
     c->launches += 3;
+  } else {
+    cudaMemsetAsync(c->eta, 0, c->M.K * sizeof(double), c->st);
   }
   if (c->prm.oe_vel) {
     Prof pr(c, KC_STAB_VEL);
@@ -195,7 +197,7 @@ void mag_substep(mhd_ctx* c, double fac) {
     if (c->prm.oe_vel) {
       Prof pr(c, KC_STAB_VEL);
       stab_vel(c->p, c->k, c->U, Yout[s], Bout[s], c->chol, c->T, c->M, c->prm, c->dt, fac, c->work, c->st);
-      c->launches += 3;
+      c->launches += 4;
     }
   }
   Prof pr(c, KC_EXCH);
@@ -320,8 +322,6 @@ int mhd_set_params(mhd_ctx* c, const mhd_params_t* prm) {
   if (!c || !prm) return fail(MHD_EINVAL, "null argument");
   if (prm->s_H < 0 || prm->s_M < 0 || prm->C_s < 0 || prm->C_eta < 0 || !(prm->cfl > 0) || prm->max_halvings < 0)
     return fail(MHD_EINVAL, "invalid stabilisation parameters");
-  if (prm->oe_hydro || prm->oe_vel || prm->pp || prm->ar)
-    return fail(MHD_EINVAL, "stage stabilisation is not available in this build");
   c->prm = Stab{prm->oe_hydro, prm->oe_vel, prm->pp, prm->ar, prm->s_H, prm->s_M, prm->C_s, prm->C_eta, prm->cfl,
                 prm->max_halvings};
   return MHD_OK;

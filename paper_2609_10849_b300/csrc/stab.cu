@@ -1,15 +1,758 @@
-// Stage stabilisation kernels (hydro OE + positivity limiter, A.R.
-// coefficient, velocity OE).  Not built yet: the API rejects enabling them.
+// Stage stabilisation kernels.
+//
+//  * Hydro stage map P = P_PP o P_OE (§3.2.2): direction-resolved jump sensor
+//    with cross-line scaling (eqs. euler-oe-jump, euler-oe-amplitude,
+//    euler-oe-shared-amplitude, euler-oe-sigma), damping of the discrete
+//    Legendre shells (eqs. euler-oe-rate, euler-oe-factor, euler-oe-map) and
+//    the Zhang-Shu scaling limiter (eqs. euler-pp-*).
+//  * Artificial-resistivity coefficient (eqs. magnetic-ar-sensor,
+//    magnetic-ar-coefficient), once per magnetic substep.
+//  * Velocity OE (eqs. magnetic-oe-sensor, magnetic-oe-rate,
+//    magnetic-oe-factor, magnetic-oe-map): rho-weighted nested projections
+//    through Psi = Phi L^{-T} (G = Phi^T W Phi = L L^T), built once per substep.
+//
+// The sensor statistics are shared by both OE procedures: k_stats writes per
+// element and component the average, nodal max/min and the jump measures of
+// its -x and -y faces; k_lines reduces rows and columns in a fixed order;
+// k_global reduces the rows.  Readings R6-R9 of the design notes apply.
+#include <cfloat>
+
 #include "mhd_internal.cuh"
 
 namespace mhd {
-void stab_hydro(int, double*, const double*, unsigned*, const Tab*, const Mesh&, const Stab&, const double*, double,
-                double*, cudaStream_t) {}
-void stab_eta(int, int, const double*, const double*, const double*, const Tab*, const Mesh&, const Stab&, double*,
-              double*, cudaStream_t) {}
-void stab_vel_prep(int, const double*, double*, const Tab*, const Mesh&, cudaStream_t) {}
-void stab_vel(int, int, const double*, double*, const double*, const double*, const Tab*, const Mesh&, const Stab&,
-              const double*, double, double*, cudaStream_t) {}
-size_t stab_work_doubles(int, int, const Mesh& M) { return 16 * (size_t)M.K; }
-size_t stab_chol_doubles(int, const Mesh&) { return 1; }
+
+// ---- work-buffer layout ---------------------------------------------------------
+struct StatsView {
+  double* avg;   // [nc][K]
+  double* emax;  // [nc][K]
+  double* emin;  // [nc][K]
+  double* jx;    // [nc][n][K] jump measure of the -x face of element K
+  double* jy;    // [nc][n][K] jump measure of the -y face
+  double* line;  // [2][L][nc][3]: (sum of averages, max, min) per row (0) / column (1), L = max(nx, ny)
+  double* glob;  // [nc][4]: mean, amplitude Delta_Omega, L-inf norm, roundoff-constant flag
+  double* ar;    // [K][8] A.R. per-element partials
+  double* arg;   // [8] A.R. global values
+};
+
+static StatsView stats_view(double* work, int p, const Mesh& M) {
+  const size_t K = M.K, n = p + 1, L = M.nx > M.ny ? M.nx : M.ny;
+  const size_t NC = 5;
+  StatsView v;
+  v.avg = work;
+  v.emax = v.avg + NC * K;
+  v.emin = v.emax + NC * K;
+  v.jx = v.emin + NC * K;
+  v.jy = v.jx + NC * n * K;
+  v.line = v.jy + NC * n * K;
+  v.glob = v.line + 2 * L * NC * 3;
+  v.ar = v.glob + NC * 4;
+  v.arg = v.ar + 8 * K;
+  return v;
+}
+
+size_t stab_work_doubles(int p, int k, const Mesh& M) {
+  (void)k;
+  const size_t K = M.K, n = p + 1, L = M.nx > M.ny ? M.nx : M.ny;
+  return 3 * 5 * K + 2 * 5 * n * K + 2 * L * 5 * 3 + 5 * 4 + 8 * K + 8 + 64;
+}
+
+size_t stab_chol_doubles(int p, const Mesh& M) {
+  const size_t n2 = (size_t)(p + 1) * (p + 1);
+  return (size_t)M.K * n2 * n2;
+}
+
+// ---- k_stats: per element and component --------------------------------------------
+// Items (element innermost, so a warp shares one item type): for each component
+// c: [average, max, min] (1 item) and for each direction I and order r the jump
+// measure of the lower face (1 item each).
+template <int P>
+__global__ void k_stats(const double* __restrict__ F, size_t stride, int nc, StatsView V, const Tab* __restrict__ T,
+                        Mesh M) {
+  constexpr int n = P + 1, n2 = n * n;
+  const size_t K = M.K;
+  const size_t items = (size_t)nc * (1 + 2 * n);
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= items * K) return;
+  const int k = (int)(t % K);
+  const int it = (int)(t / K);
+  const int c = it / (1 + 2 * n), w = it % (1 + 2 * n);
+  const double* f = F + c * stride;
+  const int ex = k % M.nx, ey = k / M.nx;
+  if (w == 0) {
+    double s = 0.0, mx = -DBL_MAX, mn = DBL_MAX;
+#pragma unroll
+    for (int q = 0; q < n2; ++q) {
+      double v = f[(size_t)k * n2 + q];
+      s = fma(0.25 * T->wp[q % n] * T->wp[q / n], v, s);
+      mx = fmax(mx, v);
+      mn = fmin(mn, v);
+    }
+    V.avg[c * K + k] = s;
+    V.emax[c * K + k] = mx;
+    V.emin[c * K + k] = mn;
+    return;
+  }
+  const int I = (w - 1) / n, r = (w - 1) % n;
+  const int kA = I == 0 ? ey * M.nx + wrap(ex - 1, M.nx) : wrap(ey - 1, M.ny) * M.nx + ex;  // lower side
+  const double h = I == 0 ? M.hx : M.hy;
+  double scale = 1.0;
+  for (int i = 0; i < r; ++i) scale *= 2.0 / h;
+  double acc = 0.0;
+#pragma unroll
+  for (int tt = 0; tt < n; ++tt) {  // face GLL node
+    double dA = 0.0, dB = 0.0;
+#pragma unroll
+    for (int s = 0; s < n; ++s) {
+      double wA = I == 0 ? f[(size_t)kA * n2 + tt * n + s] : f[(size_t)kA * n2 + s * n + tt];
+      double wB = I == 0 ? f[(size_t)k * n2 + tt * n + s] : f[(size_t)k * n2 + s * n + tt];
+      dA = fma(T->Drp[r][s], wA, dA);
+      dB = fma(T->Dr0[r][s], wB, dB);
+    }
+    double jmp = scale * (dB - dA);
+    acc = fma(0.5 * T->wp[tt] * jmp, jmp, acc);
+  }
+  double* out = I == 0 ? V.jx : V.jy;
+  out[((size_t)c * n + r) * K + k] = sqrt(acc);
+}
+
+// ---- k_lines: row (blockIdx.y = 0) and column (1) reductions -----------------------
+// Fixed-order tree: thread t accumulates a strided subset, then a pairwise tree.
+__global__ void k_lines(int nc, StatsView V, Mesh M) {
+  const int dir = blockIdx.y, L = blockIdx.x;
+  const int nlines = dir == 0 ? M.ny : M.nx, len = dir == 0 ? M.nx : M.ny;
+  if (L >= nlines) return;
+  const size_t K = M.K;
+  const int Lmax = M.nx > M.ny ? M.nx : M.ny;
+  __shared__ double s_sum[256], s_max[256], s_min[256];
+  for (int c = 0; c < nc; ++c) {
+    double s = 0.0, mx = -DBL_MAX, mn = DBL_MAX;
+    for (int t = threadIdx.x; t < len; t += blockDim.x) {
+      int k = dir == 0 ? L * M.nx + t : t * M.nx + L;
+      s += V.avg[c * K + k];
+      mx = fmax(mx, V.emax[c * K + k]);
+      mn = fmin(mn, V.emin[c * K + k]);
+    }
+    s_sum[threadIdx.x] = s; s_max[threadIdx.x] = mx; s_min[threadIdx.x] = mn;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) {
+        s_sum[threadIdx.x] += s_sum[threadIdx.x + o];
+        s_max[threadIdx.x] = fmax(s_max[threadIdx.x], s_max[threadIdx.x + o]);
+        s_min[threadIdx.x] = fmin(s_min[threadIdx.x], s_min[threadIdx.x + o]);
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      double* o = V.line + (((size_t)dir * Lmax + L) * nc + c) * 3;
+      o[0] = s_sum[0]; o[1] = s_max[0]; o[2] = s_min[0];
+    }
+    __syncthreads();
+  }
+}
+
+// ---- k_global: from the row reductions --------------------------------------------
+__global__ void k_global(int nc, StatsView V, Mesh M) {
+  __shared__ double s_sum[256], s_max[256], s_min[256];
+  const int Lmax = M.nx > M.ny ? M.nx : M.ny;
+  for (int c = 0; c < nc; ++c) {
+    double s = 0.0, mx = -DBL_MAX, mn = DBL_MAX;
+    for (int L = threadIdx.x; L < M.ny; L += blockDim.x) {
+      const double* o = V.line + ((size_t)L * nc + c) * 3;
+      s += o[0]; mx = fmax(mx, o[1]); mn = fmin(mn, o[2]);
+    }
+    s_sum[threadIdx.x] = s; s_max[threadIdx.x] = mx; s_min[threadIdx.x] = mn;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) {
+        s_sum[threadIdx.x] += s_sum[threadIdx.x + o];
+        s_max[threadIdx.x] = fmax(s_max[threadIdx.x], s_max[threadIdx.x + o]);
+        s_min[threadIdx.x] = fmin(s_min[threadIdx.x], s_min[threadIdx.x + o]);
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      double mean = s_sum[0] / M.K;
+      double amp = fmax(s_max[0] - mean, mean - s_min[0]);
+      double linf = fmax(fabs(s_max[0]), fabs(s_min[0]));
+      double* g = V.glob + c * 4;
+      g[0] = mean; g[1] = amp; g[2] = linf;
+      g[3] = amp <= 1024.0 * DBL_EPSILON * fmax(linf, 1e-300) ? 1.0 : 0.0;  // reading R8
+    }
+    __syncthreads();
+  }
+  (void)Lmax;
+}
+
+// Shared amplitude Delta_{I,K} (eq. euler-oe-shared-amplitude) of the line of element (ex, ey).
+__device__ __forceinline__ double shared_amp(const StatsView& V, int nc, int I, int ex, int ey, const Mesh& M) {
+  const int Lmax = M.nx > M.ny ? M.nx : M.ny;
+  const int L = I == 0 ? ey : ex, len = I == 0 ? M.nx : M.ny;
+  double D = 0.0;
+  for (int c = 0; c < nc; ++c) {
+    const double* o = V.line + (((size_t)I * Lmax + L) * nc + c) * 3;
+    double mean = o[0] / len;
+    double amp = fmax(o[1] - mean, mean - o[2]);
+    D = fmax(D, fmax(amp, 1e-6 * V.glob[c * 4 + 1]));
+  }
+  return D;
+}
+
+// sigma_{r,I,K} (eq. euler-oe-sigma / magnetic-oe-sensor).
+__device__ __forceinline__ double sigma_rI(const StatsView& V, int nc, int n, int I, int r, int k, int kB, double Delta,
+                                           double h, const Mesh& M) {
+  const size_t K = M.K;
+  const double* J = I == 0 ? V.jx : V.jy;
+  double fac = 2.0 * r + 1.0;
+  double hr = 1.0, fact = 1.0;
+  for (int i = 0; i < r; ++i) { hr *= h; fact *= (i + 1); }
+  fac = fac * hr / (2.0 * fact);
+  double s = 0.0;
+  for (int c = 0; c < nc; ++c) {
+    if (V.glob[c * 4 + 3] != 0.0) continue;
+    double Jr = J[((size_t)c * n + r) * K + k] + J[((size_t)c * n + r) * K + kB];
+    s = fmax(s, fac * Jr / Delta);
+  }
+  return s;
+}
+
+// ---- k_oe_pp: hydro OE map then the positivity limiter, one element per n2 threads ----
+template <int P>
+struct OCfg {
+  static constexpr int n = P + 1, n2 = n * n, EB = P == 1 ? 32 : (P == 2 ? 32 : (P == 3 ? 8 : 5));
+  static constexpr int threads = EB * n2;
+};
+
+template <int P>
+__global__ void __launch_bounds__(OCfg<P>::threads) k_oe_pp(double* __restrict__ S, StatsView V,
+                                                            const Tab* __restrict__ T, Mesh M, Stab prm,
+                                                            const double* __restrict__ dtp, double dtfac,
+                                                            unsigned* __restrict__ status) {
+  using C = OCfg<P>;
+  constexpr int n = C::n, n2 = C::n2, EB = C::EB;
+  __shared__ double su[5][EB * n2];
+  __shared__ double st[5][EB * n2];
+  __shared__ double sD[EB][n];
+  __shared__ double sa[EB][6];
+  __shared__ double sth[EB][2];
+  const size_t N = (size_t)M.K * n2, K = M.K;
+  const int tid = threadIdx.x, el = tid / n2, q = tid % n2;
+  const int k = blockIdx.x * EB + el;
+  const bool valid = k < M.K;
+  const int kk = valid ? k : M.K - 1;
+  const int ex = kk % M.nx, ey = kk / M.nx;
+  const int i = q % n, j = q / n;
+  const double g = M.g;
+  for (int c = 0; c < 5; ++c) su[c][tid] = S[c * N + (size_t)kk * n2 + q];
+
+  if (prm.oe_hydro) {
+    // damping factors D_l (one thread per l); sigma from the face jump measures
+    if (q <= P) {
+      const int l = q;
+      double Theta = 0.0;
+      const double a0 = V.avg[kk], a1 = V.avg[K + kk], a2 = V.avg[2 * K + kk], a3 = V.avg[3 * K + kk],
+                   a4 = V.avg[4 * K + kk];
+      const double ir = 1.0 / a0;
+      const double pb = (g - 1.0) * (a4 - 0.5 * (a1 * a1 + a2 * a2 + a3 * a3) * ir);
+      const double cb = sqrt(g * pb * ir);
+      for (int I = 0; I < 2; ++I) {
+        const double h = I == 0 ? M.hx : M.hy;
+        const double lam = (2.0 * P + 1.0) * (fabs((I == 0 ? a1 : a2) * ir) + cb) / h;
+        const double Delta = shared_amp(V, 5, I, ex, ey, M);
+        const int kB = I == 0 ? ey * M.nx + wrap(ex + 1, M.nx) : wrap(ey + 1, M.ny) * M.nx + ex;
+        double ss = 0.0;
+        for (int r = 0; r <= l; ++r) ss += sigma_rI(V, 5, n, I, r, kk, kB, Delta, h, M);
+        Theta += lam * ss;
+      }
+      sD[el][l] = l == 0 ? 1.0 : exp(-prm.s_H * dtp[0] * dtfac * Theta);
+    }
+    __syncthreads();
+    // modal transform: forward y then x, damp, inverse x then y (5 comps x n2 items per element)
+    for (int c = 0; c < 5; ++c) {  // T[b][i] = sum_j w_j P_b(x_j) U[j][i]
+      const int b = j;
+      double v = 0.0;
+#pragma unroll
+      for (int jj = 0; jj < n; ++jj) v = fma(T->wp[jj] * T->Leg[jj][b], su[c][el * n2 + jj * n + i], v);
+      st[c][tid] = v;
+    }
+    __syncthreads();
+    for (int c = 0; c < 5; ++c) {  // coef[b][a] = N_a N_b sum_i w_i P_a(x_i) T[b][i], damped by D_max(a,b)
+      const int b = j, a = i;
+      double v = 0.0;
+#pragma unroll
+      for (int ii = 0; ii < n; ++ii) v = fma(T->wp[ii] * T->Leg[ii][a], st[c][el * n2 + b * n + ii], v);
+      su[c][tid] = v * T->LegN[a] * T->LegN[b] * sD[el][a > b ? a : b];
+    }
+    __syncthreads();
+    for (int c = 0; c < 5; ++c) {  // V[b][i] = sum_a P_a(x_i) coef[b][a]
+      double v = 0.0;
+#pragma unroll
+      for (int a = 0; a < n; ++a) v = fma(T->Leg[i][a], su[c][el * n2 + j * n + a], v);
+      st[c][tid] = v;
+    }
+    __syncthreads();
+    for (int c = 0; c < 5; ++c) {  // U[j][i] = sum_b P_b(x_j) V[b][i]
+      double v = 0.0;
+#pragma unroll
+      for (int b = 0; b < n; ++b) v = fma(T->Leg[j][b], st[c][el * n2 + b * n + i], v);
+      su[c][tid] = v;
+    }
+    __syncthreads();
+  }
+
+  if (prm.pp) {
+    const double eps = DBL_EPSILON, eps_rho = 64.0 * eps;
+    __syncthreads();
+    if (q < 5) {  // average of U* (eq. euler-pp-average)
+      double s = 0.0;
+      for (int t2 = 0; t2 < n2; ++t2) s = fma(0.25 * T->wp[t2 % n] * T->wp[t2 / n], su[q][el * n2 + t2], s);
+      sa[el][q] = s;
+    }
+    __syncthreads();
+    if (q == 0) {
+      double a[5] = {sa[el][0], sa[el][1], sa[el][2], sa[el][3], sa[el][4]};
+      double rbar = a[0];
+      double pbar = (g - 1.0) * (a[4] - (a[1] * a[1] + a[2] * a[2] + a[3] * a[3]) / (2.0 * a[0]));
+      double th_r = 1.0, th_p = 1.0, collapse = 0.0;
+      if (!(rbar > 0.0) || !(pbar > 0.0) || !isfinite(rbar) || !isfinite(pbar)) {
+        if (valid) atomicOr(status, ST_INADMISSIBLE);
+      } else if (rbar <= eps_rho) {
+        collapse = 1.0;
+      } else {
+        double rmin = DBL_MAX;
+        for (int t2 = 0; t2 < n2; ++t2) rmin = fmin(rmin, su[0][el * n2 + t2]);
+        if (rmin < eps_rho) {
+          double den = rbar - rmin;
+          th_r = den > 0.0 ? fmin(1.0, fmax(0.0, (rbar - eps_rho) / den)) : 1.0;
+        }
+        auto Sp = [&](double r_, double m1, double m2, double m3, double E) {
+          return fabs(E) + (m1 * m1 + m2 * m2 + m3 * m3) / (2.0 * fmax(r_, eps_rho));
+        };
+        double Smax = Sp(a[0], a[1], a[2], a[3], a[4]);
+        double pmin = DBL_MAX;
+        for (int t2 = 0; t2 < n2; ++t2) {
+          double r_ = su[0][el * n2 + t2];
+          if (th_r < 1.0) r_ = rbar + th_r * (r_ - rbar);
+          double m1 = su[1][el * n2 + t2], m2 = su[2][el * n2 + t2], m3 = su[3][el * n2 + t2], E = su[4][el * n2 + t2];
+          Smax = fmax(Smax, Sp(r_, m1, m2, m3, E));
+          pmin = fmin(pmin, (g - 1.0) * (E - (m1 * m1 + m2 * m2 + m3 * m3) / (2.0 * r_)));
+        }
+        double eps_p = fmax(64.0 * eps, 8192.0 * eps * Smax);
+        if (pbar <= eps_p) collapse = 1.0;
+        else if (pmin < eps_p) {
+          double den = pbar - pmin;
+          th_p = den > 0.0 ? fmin(1.0, fmax(0.0, (pbar - eps_p) / den)) : 1.0;
+        }
+      }
+      sth[el][0] = collapse ? -1.0 : th_r;
+      sth[el][1] = th_p;
+      for (int c = 0; c < 5; ++c) sa[el][c] = a[c];
+    }
+    __syncthreads();
+    double th_r = sth[el][0], th_p = sth[el][1];
+    if (th_r < 0.0) {
+      for (int c = 0; c < 5; ++c) su[c][tid] = sa[el][c];
+    } else {
+      if (th_r < 1.0) su[0][tid] = sa[el][0] + th_r * (su[0][tid] - sa[el][0]);
+      if (th_p < 1.0)
+        for (int c = 0; c < 5; ++c) su[c][tid] = sa[el][c] + th_p * (su[c][tid] - sa[el][c]);
+    }
+  }
+  if (valid)
+    for (int c = 0; c < 5; ++c) S[c * N + (size_t)k * n2 + q] = su[c][tid];
+}
+
+// ---- launchers: hydro stage map -----------------------------------------------------
+template <int P>
+static void launch_stats(const double* F, size_t stride, int nc, const StatsView& V, const Tab* T, const Mesh& M,
+                         cudaStream_t st) {
+  constexpr int n = P + 1;
+  size_t total = (size_t)nc * (1 + 2 * n) * M.K;
+  k_stats<P><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(F, stride, nc, V, T, M);
+  dim3 grid(M.nx > M.ny ? M.nx : M.ny, 2);
+  k_lines<<<grid, 256, 0, st>>>(nc, V, M);
+  k_global<<<1, 256, 0, st>>>(nc, V, M);
+}
+
+template <int P>
+static void stab_hydro_impl(double* S, unsigned* status, const Tab* T, const Mesh& M, const Stab& prm,
+                            const double* dtp, double dtfac, double* work, cudaStream_t st) {
+  StatsView V = stats_view(work, P, M);
+  if (prm.oe_hydro) launch_stats<P>(S, (size_t)M.K * (P + 1) * (P + 1), 5, V, T, M, st);
+  using C = OCfg<P>;
+  k_oe_pp<P><<<(unsigned)((M.K + C::EB - 1) / C::EB), C::threads, 0, st>>>(S, V, T, M, prm, dtp, dtfac, status);
+}
+
+void stab_hydro(int p, double* S, const double* avg, unsigned* status, const Tab* T, const Mesh& M, const Stab& prm,
+                const double* dtp, double dtfac, double* work, cudaStream_t st) {
+  (void)avg;
+  switch (p) {
+    case 1: stab_hydro_impl<1>(S, status, T, M, prm, dtp, dtfac, work, st); break;
+    case 2: stab_hydro_impl<2>(S, status, T, M, prm, dtp, dtfac, work, st); break;
+    case 3: stab_hydro_impl<3>(S, status, T, M, prm, dtp, dtfac, work, st); break;
+    case 4: stab_hydro_impl<4>(S, status, T, M, prm, dtp, dtfac, work, st); break;
+  }
+}
+
+// ============================ artificial resistivity =============================
+// B closure helpers (element-blocked owned DOFs, see mhd_internal.cuh).
+template <int KM>
+__device__ __forceinline__ double bx_cl(const double* Bx, int ex, int ey, int a, int b, const Mesh& M) {
+  constexpr int mm = KM + 1, mL = KM + 2;
+  if (a == mL - 1) return Bx[((size_t)ey * M.nx + wrap(ex + 1, M.nx)) * mm * mm + b * mm];
+  return Bx[((size_t)ey * M.nx + ex) * mm * mm + b * mm + a];
+}
+template <int KM>
+__device__ __forceinline__ double by_cl(const double* By, int ex, int ey, int a, int b, const Mesh& M) {
+  constexpr int mm = KM + 1, mL = KM + 2;
+  if (b == mL - 1) return By[((size_t)wrap(ey + 1, M.ny) * M.nx + ex) * mm * mm + a];
+  return By[((size_t)ey * M.nx + ex) * mm * mm + b * mm + a];
+}
+
+// Component d of B_h of element (ex, ey) at reference point (x, y) given as 1D
+// basis values: LX = l^L(x) [mL], GX = g(x) [mm], MX = l^M(x) [mm], likewise Y.
+template <int KM>
+__device__ double B_eval(const double* B, size_t Z, int d, int ex, int ey, const double* LX, const double* GX,
+                         const double* MX, const double* LY, const double* GY, const double* MY, const Mesh& M) {
+  constexpr int mm = KM + 1, mL = KM + 2;
+  double v = 0.0;
+  if (d == 0) {
+    for (int b = 0; b < mm; ++b) {
+      double row = 0.0;
+      for (int a = 0; a < mL; ++a) row = fma(LX[a], bx_cl<KM>(B, ex, ey, a, b, M), row);
+      v = fma(GY[b], row, v);
+    }
+  } else if (d == 1) {
+    for (int b = 0; b < mL; ++b) {
+      double row = 0.0;
+      for (int a = 0; a < mm; ++a) row = fma(GX[a], by_cl<KM>(B + Z, ex, ey, a, b, M), row);
+      v = fma(LY[b], row, v);
+    }
+  } else {
+    const double* Bz = B + 2 * Z + ((size_t)ey * M.nx + ex) * mm * mm;
+    for (int b = 0; b < mm; ++b) {
+      double row = 0.0;
+      for (int a = 0; a < mm; ++a) row = fma(MX[a], Bz[b * mm + a], row);
+      v = fma(MY[b], row, v);
+    }
+  }
+  return v;
+}
+
+// Per element: exact integrals of Bx, By, Bz (global means), max/min of the
+// owned DOFs, the tangential jump measures J_0 of the -x face (B_y, B_z) and
+// the -y face (B_x, B_z), and the directional speeds a_{I,K}.
+// ar[K][16]: 0-2 integrals, 3-5 max, 6-8 min, 9-10 -x face (By, Bz), 11-12 -y face (Bx, Bz), 13-14 a_x, a_y
+template <int P, int KM>
+__global__ void k_ar_elem(const double* __restrict__ rho, const double* __restrict__ Y, const double* __restrict__ B,
+                          const Tab* __restrict__ T, Mesh M, double* __restrict__ ar) {
+  constexpr int n = P + 1, n2 = n * n, mm = KM + 1, mL = KM + 2, q2 = KM + 2;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= M.K) return;
+  const size_t Z = (size_t)M.K * mm * mm, N = (size_t)M.K * n2;
+  const int ex = k % M.nx, ey = k / M.nx;
+  double out[16];
+  // integrals with the exact magnetic product rules
+  double ix = 0.0, iy = 0.0, iz = 0.0;
+  for (int qy = 0; qy < q2; ++qy)
+    for (int qx = 0; qx < q2; ++qx) {
+      double w = M.Jdet * T->w2[qx] * T->w2[qy];
+      ix = fma(w, B_eval<KM>(B, Z, 0, ex, ey, T->L_2[qx], T->G_2[qx], T->M_2[qx], T->L_2[qy], T->G_2[qy], T->M_2[qy], M), ix);
+      iy = fma(w, B_eval<KM>(B, Z, 1, ex, ey, T->L_2[qx], T->G_2[qx], T->M_2[qx], T->L_2[qy], T->G_2[qy], T->M_2[qy], M), iy);
+    }
+  for (int qy = 0; qy < mm; ++qy)
+    for (int qx = 0; qx < mm; ++qx) {
+      double w = M.Jdet * T->wG[qx] * T->wG[qy];
+      double s = 0.0;
+      const double* Bz = B + 2 * Z + (size_t)k * mm * mm;
+      for (int b = 0; b < mm; ++b)
+        for (int a = 0; a < mm; ++a) s = fma(T->M_G[qx][a] * T->M_G[qy][b], Bz[b * mm + a], s);
+      iz = fma(w, s, iz);
+    }
+  out[0] = ix; out[1] = iy; out[2] = iz;
+  for (int d = 0; d < 3; ++d) {
+    double mx = -DBL_MAX, mn = DBL_MAX;
+    const double* A = B + d * Z + (size_t)k * mm * mm;
+    for (int t = 0; t < mm * mm; ++t) { mx = fmax(mx, A[t]); mn = fmin(mn, A[t]); }
+    out[3 + d] = mx; out[6 + d] = mn;
+  }
+  // tangential jumps on the lower faces, Gauss(k+2) face rule (reading R6)
+  for (int I = 0; I < 2; ++I) {
+    const int exA = I == 0 ? wrap(ex - 1, M.nx) : ex, eyA = I == 0 ? ey : wrap(ey - 1, M.ny);
+    const int dcomp[2] = {I == 0 ? 1 : 0, 2};
+    for (int tc = 0; tc < 2; ++tc) {
+      const int d = dcomp[tc];
+      double acc = 0.0;
+      for (int t = 0; t < q2; ++t) {
+        // upper face of A at +1, lower face of this element at -1; face coordinate z2_t
+        double vA, vB;
+        if (I == 0) {
+          vA = B_eval<KM>(B, Z, d, exA, eyA, T->L_end[1], T->G_end[1], T->M_end[1], T->L_2[t], T->G_2[t], T->M_2[t], M);
+          vB = B_eval<KM>(B, Z, d, ex, ey, T->L_end[0], T->G_end[0], T->M_end[0], T->L_2[t], T->G_2[t], T->M_2[t], M);
+        } else {
+          vA = B_eval<KM>(B, Z, d, exA, eyA, T->L_2[t], T->G_2[t], T->M_2[t], T->L_end[1], T->G_end[1], T->M_end[1], M);
+          vB = B_eval<KM>(B, Z, d, ex, ey, T->L_2[t], T->G_2[t], T->M_2[t], T->L_end[0], T->G_end[0], T->M_end[0], M);
+        }
+        double jmp = vB - vA;
+        acc = fma(0.5 * T->w2[t] * jmp, jmp, acc);
+      }
+      out[9 + 2 * I + tc] = sqrt(acc);
+    }
+  }
+  // a_{I,K} = max over DG nodes of |u_I| + |B_h| / sqrt(rho)
+  double ax = 0.0, ay = 0.0;
+  for (int q = 0; q < n2; ++q) {
+    int i = q % n, j = q / n;
+    double Bv[3];
+    for (int d = 0; d < 3; ++d)
+      Bv[d] = B_eval<KM>(B, Z, d, ex, ey, T->L_P[i], T->G_P[i], T->M_P[i], T->L_P[j], T->G_P[j], T->M_P[j], M);
+    double bn = sqrt(Bv[0] * Bv[0] + Bv[1] * Bv[1] + Bv[2] * Bv[2]);
+    double r = rho[(size_t)k * n2 + q];
+    double va = bn / sqrt(r);
+    ax = fmax(ax, fabs(Y[N + (size_t)k * n2 + q]) + va);
+    ay = fmax(ay, fabs(Y[2 * N + (size_t)k * n2 + q]) + va);
+  }
+  out[13] = ax; out[14] = ay; out[15] = 0.0;
+  for (int c = 0; c < 16; ++c) ar[(size_t)k * 16 + c] = out[c];
+}
+
+// Global reduction of the A.R. partials (one block, fixed order).
+__global__ void k_ar_global(const double* __restrict__ ar, Mesh M, double* __restrict__ g) {
+  __shared__ double sm[256][9];
+  double acc[9] = {0, 0, 0, -DBL_MAX, -DBL_MAX, -DBL_MAX, DBL_MAX, DBL_MAX, DBL_MAX};
+  for (int k = threadIdx.x; k < M.K; k += blockDim.x) {
+    const double* a = ar + (size_t)k * 16;
+    for (int c = 0; c < 3; ++c) acc[c] += a[c];
+    for (int c = 3; c < 6; ++c) acc[c] = fmax(acc[c], a[c]);
+    for (int c = 6; c < 9; ++c) acc[c] = fmin(acc[c], a[c]);
+  }
+  for (int c = 0; c < 9; ++c) sm[threadIdx.x][c] = acc[c];
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int c = 0; c < 9; ++c) {
+        double x = sm[threadIdx.x][c], y = sm[threadIdx.x + o][c];
+        sm[threadIdx.x][c] = c < 3 ? x + y : (c < 6 ? fmax(x, y) : fmin(x, y));
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double area = M.K * 4.0 * M.Jdet;
+    double amp[3], linf[3];
+    for (int d = 0; d < 3; ++d) {
+      double mean = sm[0][d] / area;
+      amp[d] = fmax(sm[0][3 + d] - mean, mean - sm[0][6 + d]);
+      linf[d] = fmax(fabs(sm[0][3 + d]), fabs(sm[0][6 + d]));
+    }
+    // Delta^B_I over T_x = {y, z}, T_y = {x, z}; roundoff-constant directions off (reading R8)
+    double Dx = fmax(amp[1], amp[2]), Dy = fmax(amp[0], amp[2]);
+    g[0] = Dx; g[1] = Dy;
+    g[2] = Dx <= 1024.0 * DBL_EPSILON * fmax(fmax(linf[1], linf[2]), 1e-300) ? 1.0 : 0.0;
+    g[3] = Dy <= 1024.0 * DBL_EPSILON * fmax(fmax(linf[0], linf[2]), 1e-300) ? 1.0 : 0.0;
+  }
+}
+
+// eta_K = C_eta max_I h_I a_I R_I / (2p+1), R_I = min(C_s sigma^B_I, 1).
+__global__ void k_ar_eta(const double* __restrict__ ar, const double* __restrict__ g, Mesh M, Stab prm, int p,
+                         double* __restrict__ eta) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= M.K) return;
+  const int ex = k % M.nx, ey = k / M.nx;
+  const int kE = ey * M.nx + wrap(ex + 1, M.nx), kN = wrap(ey + 1, M.ny) * M.nx + ex;
+  const double* a = ar + (size_t)k * 16;
+  double e = 0.0;
+  for (int I = 0; I < 2; ++I) {
+    double sig = 0.0;
+    if (g[2 + I] == 0.0) {
+      const double* b = ar + (size_t)(I == 0 ? kE : kN) * 16;
+      for (int tc = 0; tc < 2; ++tc) {
+        double J0 = a[9 + 2 * I + tc] + b[9 + 2 * I + tc];
+        sig = fmax(sig, J0 / (2.0 * g[I]));
+      }
+    }
+    double R = fmin(prm.C_s * sig, 1.0);
+    double h = I == 0 ? M.hx : M.hy;
+    e = fmax(e, h / (2.0 * p + 1.0) * a[13 + I] * R);
+  }
+  eta[k] = prm.C_eta * e;
+}
+
+void stab_eta(int p, int k, const double* rho, const double* Y, const double* B, const Tab* T, const Mesh& M,
+              const Stab& prm, double* eta, double* work, cudaStream_t st) {
+  StatsView V = stats_view(work, p, M);
+  double* ar = V.jx;  // the A.R. partials reuse the sensor area: [K][16] <= 2 * 5 * n * K
+  double* g = V.glob;
+  unsigned bl = (unsigned)((M.K + 127) / 128);
+#define MHD_AR_CASE(PP, KK) k_ar_elem<PP, KK><<<bl, 128, 0, st>>>(rho, Y, B, T, M, ar)
+  MHD_DISPATCH_PK(p, k, MHD_AR_CASE);
+#undef MHD_AR_CASE
+  k_ar_global<<<1, 256, 0, st>>>(ar, M, g);
+  k_ar_eta<<<bl, 128, 0, st>>>(ar, g, M, prm, p, eta);
+}
+
+// ============================ velocity OE ==========================================
+// Psi = Phi L^{-T} per element (n2 x n2, row q = node, column alpha = basis in shell order).
+template <int P>
+__global__ void k_vel_prep(const double* __restrict__ rho, double* __restrict__ Psi, const Tab* __restrict__ T, Mesh M) {
+  constexpr int n = P + 1, n2 = n * n;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= M.K) return;
+  // shell-ordered Legendre indices
+  int ia[n2], ib[n2];
+  {
+    int t = 0;
+    for (int l = 0; l <= P; ++l)
+      for (int b = 0; b <= l; ++b)
+        for (int a = 0; a <= l; ++a)
+          if ((a > b ? a : b) == l) { ia[t] = a; ib[t] = b; ++t; }
+  }
+  double* out = Psi + (size_t)k * n2 * n2;
+  // Gram matrix G = Phi^T W Phi, W = diag(Jdet w_i w_j rho_q); Cholesky in place (lower)
+  double L[n2 * (n2 + 1) / 2];
+  auto li = [](int r, int c) { return r * (r + 1) / 2 + c; };
+  for (int al = 0; al < n2; ++al)
+    for (int be = 0; be <= al; ++be) {
+      double s = 0.0;
+      for (int q = 0; q < n2; ++q) {
+        int i = q % n, j = q / n;
+        double W = M.Jdet * T->wp[i] * T->wp[j] * rho[(size_t)k * n2 + q];
+        s = fma(W * T->Leg[i][ia[al]] * T->Leg[j][ib[al]], T->Leg[i][ia[be]] * T->Leg[j][ib[be]], s);
+      }
+      L[li(al, be)] = s;
+    }
+  for (int r = 0; r < n2; ++r) {
+    for (int c = 0; c <= r; ++c) {
+      double s = L[li(r, c)];
+      for (int t = 0; t < c; ++t) s -= L[li(r, t)] * L[li(c, t)];
+      L[li(r, c)] = (r == c) ? sqrt(s) : s / L[li(c, c)];
+    }
+  }
+  // Psi[q][al] = (Phi L^{-T})[q][al]: forward sweep over columns
+  for (int q = 0; q < n2; ++q) {
+    int i = q % n, j = q / n;
+    double row[n2];
+    for (int al = 0; al < n2; ++al) {
+      double s = T->Leg[i][ia[al]] * T->Leg[j][ib[al]];
+      for (int b = 0; b < al; ++b) s -= row[b] * L[li(al, b)];
+      row[al] = s / L[li(al, al)];
+    }
+    for (int al = 0; al < n2; ++al) out[q * n2 + al] = row[al];
+  }
+}
+
+void stab_vel_prep(int p, const double* rho, double* chol, const Tab* T, const Mesh& M, cudaStream_t st) {
+  unsigned bl = (unsigned)((M.K + 63) / 64);
+  switch (p) {
+    case 1: k_vel_prep<1><<<bl, 64, 0, st>>>(rho, chol, T, M); break;
+    case 2: k_vel_prep<2><<<bl, 64, 0, st>>>(rho, chol, T, M); break;
+    case 3: k_vel_prep<3><<<bl, 64, 0, st>>>(rho, chol, T, M); break;
+    case 4: k_vel_prep<4><<<bl, 64, 0, st>>>(rho, chol, T, M); break;
+  }
+}
+
+// Velocity OE map with heating of e, one element per n2 threads.
+template <int P, int KM>
+__global__ void __launch_bounds__(OCfg<P>::threads) k_vel_oe(const double* __restrict__ rho, double* __restrict__ Y,
+                                                             const double* __restrict__ B,
+                                                             const double* __restrict__ Psi, StatsView V,
+                                                             const Tab* __restrict__ T, Mesh M, Stab prm,
+                                                             const double* __restrict__ dtp, double dtfac) {
+  using C = OCfg<P>;
+  constexpr int n = C::n, n2 = C::n2, EB = C::EB;
+  __shared__ double su[3][EB * n2];
+  __shared__ double sc[3][EB * n2];
+  __shared__ double sD[EB][n];
+  __shared__ double sv[EB * n2][2];
+  const size_t N = (size_t)M.K * n2, Z = (size_t)M.K * (KM + 1) * (KM + 1);
+  const int tid = threadIdx.x, el = tid / n2, q = tid % n2;
+  const int k = blockIdx.x * EB + el;
+  const bool valid = k < M.K;
+  const int kk = valid ? k : M.K - 1;
+  const int ex = kk % M.nx, ey = kk / M.nx;
+  const int i = q % n, j = q / n;
+  const double r_ = rho[(size_t)kk * n2 + q];
+  for (int d = 0; d < 3; ++d) su[d][tid] = Y[(1 + d) * N + (size_t)kk * n2 + q];
+  {  // |u_I| + |B_h|/sqrt(rho) at this node
+    double Bv[3];
+    for (int d = 0; d < 3; ++d)
+      Bv[d] = B_eval<KM>(B, Z, d, ex, ey, T->L_P[i], T->G_P[i], T->M_P[i], T->L_P[j], T->G_P[j], T->M_P[j], M);
+    double va = sqrt(Bv[0] * Bv[0] + Bv[1] * Bv[1] + Bv[2] * Bv[2]) / sqrt(r_);
+    sv[tid][0] = fabs(su[0][tid]) + va;
+    sv[tid][1] = fabs(su[1][tid]) + va;
+  }
+  __syncthreads();
+  if (q <= P) {
+    const int l = q;
+    double Theta = 0.0;
+    for (int I = 0; I < 2; ++I) {
+      double amax = 0.0;
+      for (int t2 = 0; t2 < n2; ++t2) amax = fmax(amax, sv[el * n2 + t2][I]);
+      const double h = I == 0 ? M.hx : M.hy;
+      const double lam = (2.0 * P + 1.0) / h * amax;
+      const double Delta = shared_amp(V, 3, I, ex, ey, M);
+      const int kB = I == 0 ? ey * M.nx + wrap(ex + 1, M.nx) : wrap(ey + 1, M.ny) * M.nx + ex;
+      double ss = 0.0;
+      for (int r = 0; r <= l; ++r) ss += sigma_rI(V, 3, n, I, r, kk, kB, Delta, h, M);
+      Theta += lam * ss;
+    }
+    sD[el][l] = l == 0 ? 1.0 : exp(-prm.s_M * dtp[0] * dtfac * Theta);
+  }
+  // coefficients c_alpha = sum_q Psi[q][alpha] M_q rho_q u_q (thread q plays alpha)
+  const double* Ps = Psi + (size_t)kk * n2 * n2;
+  {
+    const int al = q;
+    for (int d = 0; d < 3; ++d) {
+      double s = 0.0;
+      for (int t2 = 0; t2 < n2; ++t2) {
+        double W = M.Jdet * T->wp[t2 % n] * T->wp[t2 / n] * rho[(size_t)kk * n2 + t2];
+        s = fma(Ps[t2 * n2 + al] * W, su[d][el * n2 + t2], s);
+      }
+      sc[d][tid] = s;
+    }
+  }
+  __syncthreads();
+  // shell values w_l at this node, damped velocity and heating
+  int shell[n2];
+  {
+    int t = 0;
+    for (int l = 0; l <= P; ++l)
+      for (int b = 0; b <= l; ++b)
+        for (int a = 0; a <= l; ++a)
+          if ((a > b ? a : b) == l) shell[t++] = l;
+  }
+  double de = 0.0, unew[3];
+  for (int d = 0; d < 3; ++d) {
+    double wl[n];
+    for (int l = 0; l < n; ++l) wl[l] = 0.0;
+    for (int al = 0; al < n2; ++al) wl[shell[al]] = fma(sc[d][el * n2 + al], Ps[q * n2 + al], wl[shell[al]]);
+    double s = wl[0];
+    for (int l = 1; l <= P; ++l) {
+      double Dl = sD[el][l];
+      s = fma(Dl, wl[l], s);
+      de = fma(0.5 * (1.0 - Dl * Dl) * wl[l], wl[l], de);
+    }
+    unew[d] = s;
+  }
+  if (valid) {
+    for (int d = 0; d < 3; ++d) Y[(1 + d) * N + (size_t)k * n2 + q] = unew[d];
+    Y[(size_t)k * n2 + q] += de;
+  }
+}
+
+void stab_vel(int p, int k, const double* rho, double* Y, const double* B, const double* chol, const Tab* T,
+              const Mesh& M, const Stab& prm, const double* dtp, double dtfac, double* work, cudaStream_t st) {
+  StatsView V = stats_view(work, p, M);
+  const size_t N = (size_t)M.K * (p + 1) * (p + 1);
+  switch (p) {
+    case 1: launch_stats<1>(Y + N, N, 3, V, T, M, st); break;
+    case 2: launch_stats<2>(Y + N, N, 3, V, T, M, st); break;
+    case 3: launch_stats<3>(Y + N, N, 3, V, T, M, st); break;
+    case 4: launch_stats<4>(Y + N, N, 3, V, T, M, st); break;
+  }
+#define MHD_VOE_CASE(PP, KK)                                                                            \
+  k_vel_oe<PP, KK><<<(unsigned)((M.K + OCfg<PP>::EB - 1) / OCfg<PP>::EB), OCfg<PP>::threads, 0, st>>>( \
+      rho, Y, B, chol, V, T, M, prm, dtp, dtfac)
+  MHD_DISPATCH_PK(p, k, MHD_VOE_CASE);
+#undef MHD_VOE_CASE
+}
+
 }  // namespace mhd
