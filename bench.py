@@ -33,6 +33,9 @@ import numpy as np  # noqa: E402
 METRIC = "FP64 DOF-updates/s per Strang step at p=3"
 UNIT = "DOF-updates/s"
 NOMINAL_FP64_TFLOPS = 1.25  # B300 dense FP64, nominal (profiling recipe table)
+# Config 2 of the workload: OE (both stages), positivity limiter, artificial
+# resistivity and velocity filter active, with the paper's constants.
+STAB = dict(oe_hydro=1, oe_vel=1, pp=1, ar=1, s_H=0.02, s_M=0.02, C_s=5.0, C_eta=0.2)
 
 
 def workload_config(stab, mesh=256):
@@ -70,7 +73,7 @@ def make_solver(stab_params, mesh=256):
     s.set_B_from_potential(np.ascontiguousarray(wl["Az"](XW, YW)), *wl["B0"],
                            np.ascontiguousarray(wl["fields"](XZ, YZ)[5]))
     if stab_params:
-        s.set_params(**stab_params)
+        s.set_params(cfl=0.4, **stab_params)
     return s
 
 
@@ -132,7 +135,7 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_baseline(steps=4, n=64):
+def cpu_baseline(steps=3, n=64):
     """The oracle as it stands, single-threaded, on a bounded sample of the same
     workload: the Orszag-Tang vortex on an n x n mesh, p = k = 3."""
     import oracle
@@ -145,6 +148,7 @@ def cpu_baseline(steps=4, n=64):
     XZ, YZ = o.coords("bz")
     Bx, By = o.b_from_potential(wl["Az"](XW, YW), *wl["B0"])
     o.set_primitive(rho, np.stack([ux, uy, uz]), pr, Bx, By, wl["fields"](XZ, YZ)[5])
+    o.set_params(cfl=0.4, **STAB)
     dt = o.cfl_dt()
     o.strang_step(dt)  # warm-up
     t0 = time.perf_counter()
@@ -159,7 +163,7 @@ def cpu_baseline(steps=4, n=64):
 def run_reference(args, rank):
     if rank != 0:
         return
-    stab = {"oe_hydro": 0, "pp": 0, "ar": 0, "oe_vel": 0}
+    stab = STAB
     n = 32
     import oracle
     from paper_2609_10849_b300 import workloads
@@ -171,6 +175,7 @@ def run_reference(args, rank):
     XZ, YZ = o.coords("bz")
     Bx, By = o.b_from_potential(wl["Az"](XW, YW), *wl["B0"])
     o.set_primitive(rho, np.stack([ux, uy, uz]), pr, Bx, By, wl["fields"](XZ, YZ)[5])
+    o.set_params(cfl=0.4, **STAB)
     dt = o.cfl_dt()
     for _ in range(args.warmup):
         o.strang_step(dt)
@@ -218,8 +223,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     from paper_2609_10849_b300 import mhd
-    stab = {"oe_hydro": 0, "pp": 0, "ar": 0, "oe_vel": 0}
-    s = make_solver(None, args.mesh)
+    stab = STAB
+    s = make_solver(stab, args.mesh)
     stream = torch.cuda.current_stream()
     s.set_stream(stream.cuda_stream)
     dt = s.compute_dt()
@@ -289,9 +294,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (analytic Orszag-Tang initial state)",
-            "config": dict(workload_config(stab, args.mesh), parallelism=f"replicas{world}", dt=dt,
-                           stabilization_note="stage stabilisation kernels not built yet: OE/PP/A.R./velocity "
-                                              "filter off"),
+            "config": dict(workload_config(stab, args.mesh), parallelism=f"replicas{world}", dt=dt),
             "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
         }
         if not args.no_cpu_baseline:

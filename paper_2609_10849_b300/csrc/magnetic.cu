@@ -19,9 +19,22 @@
 //             magnetic-divergence).
 // Shared DOFs are assembled by every element that needs them in one canonical
 // order (south-west contribution first), so all copies agree bitwise.
+//
+// Work mapping (the FP64 pipe is the bound: keep every lane busy, keep table
+// reads uniform): a block holds EB = 16 elements; shared memory is laid out
+// element-innermost ([quantity][item][element]) and a flat loop index is
+// item * EB + element, so each half-warp evaluates one item for 16 elements.
+// All lanes of a half-warp take the same branch and read the same table
+// entries, which live in constant memory (broadcast reads).
 #include "mhd_internal.cuh"
 
 namespace mhd {
+
+__constant__ Tab c_mtab[8];
+
+void upload_mag_tables(int slot, const Tab* h, cudaError_t* err) {
+  *err = cudaMemcpyToSymbol(c_mtab, h, sizeof(Tab), slot * sizeof(Tab));
+}
 
 template <int P, int KM>
 struct MD {
@@ -32,14 +45,19 @@ struct MD {
   static constexpr int NZ = mm * mm;   // owned DOFs / B_z
   static constexpr int EB = 16;        // elements per block
   static constexpr int TH = 256;       // threads per block
+  static constexpr int SLOT = P - 1 + KM;
 };
+
+#define FLAT(ITEMS) for (int idx = threadIdx.x; idx < D::EB * (ITEMS); idx += blockDim.x)
+#define SM(off, it) sm[(size_t)((off) + (it)) * D::EB + e]
 
 // ---- assembly of closure values from element loads ----------------------------
 // W-type closure node (a, b), a, b < mL, of element (ex, ey).
 template <int P, int KM>
 __device__ __forceinline__ double assemble_W(const double* __restrict__ Lz, int ex, int ey, int a, int b,
-                                             const Mesh& M, double iJ, const Tab* T) {
+                                             const Mesh& M, double iJ) {
   using D = MD<P, KM>;
+  const Tab& T = c_mtab[D::SLOT];
   int ox = ex, oy = ey, ao = a, bo = b;
   if (a == D::mL - 1) { ox = wrap(ex + 1, M.nx); ao = 0; }
   if (b == D::mL - 1) { oy = wrap(ey + 1, M.ny); bo = 0; }
@@ -49,39 +67,41 @@ __device__ __forceinline__ double assemble_W(const double* __restrict__ Lz, int 
   if (bo == 0) v += Lz[(size_t)(sy * M.nx + ox) * D::NW + (D::mL - 1) * D::mL + ao];
   if (ao == 0) v += Lz[(size_t)(oy * M.nx + wx) * D::NW + bo * D::mL + (D::mL - 1)];
   v += Lz[(size_t)(oy * M.nx + ox) * D::NW + bo * D::mL + ao];
-  double wa = ao == 0 ? 2.0 * T->wL[0] : T->wL[ao];
-  double wb = bo == 0 ? 2.0 * T->wL[0] : T->wL[bo];
+  double wa = ao == 0 ? 2.0 * T.wL[0] : T.wL[ao];
+  double wb = bo == 0 ? 2.0 * T.wL[0] : T.wL[bo];
   return v / (wa * wb) * iJ;
 }
 
 // Y-type (N_x) closure node (a < mm, b < mL).
 template <int P, int KM>
 __device__ __forceinline__ double assemble_Nx(const double* __restrict__ Lx, int ex, int ey, int a, int b,
-                                              const Mesh& M, double iJ, const Tab* T) {
+                                              const Mesh& M, double iJ) {
   using D = MD<P, KM>;
+  const Tab& T = c_mtab[D::SLOT];
   int oy = ey, bo = b;
   if (b == D::mL - 1) { oy = wrap(ey + 1, M.ny); bo = 0; }
   const int sy = wrap(oy - 1, M.ny);
   double v = 0.0;
   if (bo == 0) v += Lx[(size_t)(sy * M.nx + ex) * D::NX + (D::mL - 1) * D::mm + a];
   v += Lx[(size_t)(oy * M.nx + ex) * D::NX + bo * D::mm + a];
-  double wb = bo == 0 ? 2.0 * T->wL[0] : T->wL[bo];
-  return v / (T->wG[a] * wb) * iJ;
+  double wb = bo == 0 ? 2.0 * T.wL[0] : T.wL[bo];
+  return v / (T.wG[a] * wb) * iJ;
 }
 
 // X-type (N_y) closure node (a < mL, b < mm).
 template <int P, int KM>
 __device__ __forceinline__ double assemble_Ny(const double* __restrict__ Ly, int ex, int ey, int a, int b,
-                                              const Mesh& M, double iJ, const Tab* T) {
+                                              const Mesh& M, double iJ) {
   using D = MD<P, KM>;
+  const Tab& T = c_mtab[D::SLOT];
   int ox = ex, ao = a;
   if (a == D::mL - 1) { ox = wrap(ex + 1, M.nx); ao = 0; }
   const int wx = wrap(ox - 1, M.nx);
   double v = 0.0;
   if (ao == 0) v += Ly[(size_t)(ey * M.nx + wx) * D::NY + b * D::mL + (D::mL - 1)];
   v += Ly[(size_t)(ey * M.nx + ox) * D::NY + b * D::mL + ao];
-  double wa = ao == 0 ? 2.0 * T->wL[0] : T->wL[ao];
-  return v / (wa * T->wG[b]) * iJ;
+  double wa = ao == 0 ? 2.0 * T.wL[0] : T.wL[ao];
+  return v / (wa * T.wG[b]) * iJ;
 }
 
 // B closure loads: Bx (X-type, [b < mm][a < mL]) and By (Y-type, [b < mL][a < mm]).
@@ -100,77 +120,73 @@ __device__ __forceinline__ double closure_By(const double* __restrict__ By, int 
   return By[(size_t)(ey * M.nx + ex) * D::NZ + b * D::mm + a];
 }
 
-#define FLAT_LOOP(ITEMS) for (int idx = threadIdx.x; idx < D::EB * (ITEMS); idx += blockDim.x)
-
 // ============================ k_mag_J ==========================================
 template <int P, int KM>
-struct SJ {
+struct LJ_ {  // per-element shared-memory offsets (doubles)
   using D = MD<P, KM>;
-  double bx[D::NY], by[D::NX], bz[D::NZ];
-  double t1[D::mm * D::mL];   // [j < mm][a < mL]  sum_i Bx[j][i] ML[i][a]
-  double t2[D::mL * D::mm];   // [b < mL][i < mm]  sum_j ML[j][b] By[j][i]
-  double ta[D::NZ];           // Bz rows to Gauss x
-  double bzg[D::NZ];          // Bz at Gauss(k)^2: [d][a]
+  static constexpr int BX = 0, BY = BX + D::NY, BZ = BY + D::NX;
+  static constexpr int T1 = BZ + D::NZ;          // [j < mm][a < mL]
+  static constexpr int T2 = T1 + D::mm * D::mL;  // [b < mL][i < mm]
+  static constexpr int TA = T2 + D::mL * D::mm;  // Bz rows to Gauss x
+  static constexpr int BZG = TA + D::NZ;         // Bz at Gauss(k)^2: [d][a]
+  static constexpr int SIZE = BZG + D::NZ;
 };
 
 template <int P, int KM>
 __global__ void __launch_bounds__(256) k_mag_J(const double* __restrict__ Bx, const double* __restrict__ By,
                                                const double* __restrict__ Bz, double* __restrict__ LJx,
-                                               double* __restrict__ LJy, double* __restrict__ LJz,
-                                               const Tab* __restrict__ T, Mesh M) {
+                                               double* __restrict__ LJy, double* __restrict__ LJz, Mesh M) {
   using D = MD<P, KM>;
-  extern __shared__ double smem_raw[];
-  SJ<P, KM>* S = reinterpret_cast<SJ<P, KM>*>(smem_raw);
+  using O = LJ_<P, KM>;
+  const Tab& T = c_mtab[D::SLOT];
+  extern __shared__ double sm[];
   const int k0 = blockIdx.x * D::EB;
-  // stage 1: closures
   constexpr int I1 = D::NY + D::NX + D::NZ;
-  FLAT_LOOP(I1) {
-    int e = idx / I1, it = idx % I1, k = min(k0 + e, M.K - 1);
+  FLAT(I1) {
+    int it = idx / D::EB, e = idx % D::EB, k = min(k0 + e, M.K - 1);
     int ex = k % M.nx, ey = k / M.nx;
-    if (it < D::NY) { int a = it % D::mL, b = it / D::mL; S[e].bx[it] = closure_Bx<P, KM>(Bx, ex, ey, a, b, M); }
-    else if (it < D::NY + D::NX) { it -= D::NY; int a = it % D::mm, b = it / D::mm; S[e].by[it] = closure_By<P, KM>(By, ex, ey, a, b, M); }
-    else { it -= D::NY + D::NX; S[e].bz[it] = Bz[(size_t)k * D::NZ + it]; }
+    if (it < D::NY) SM(O::BX, it) = closure_Bx<P, KM>(Bx, ex, ey, it % D::mL, it / D::mL, M);
+    else if (it < D::NY + D::NX) { it -= D::NY; SM(O::BY, it) = closure_By<P, KM>(By, ex, ey, it % D::mm, it / D::mm, M); }
+    else { it -= D::NY + D::NX; SM(O::BZ, it) = Bz[(size_t)k * D::NZ + it]; }
   }
   __syncthreads();
-  // stage 2: t1, t2 (mass contractions) and the x-pass of Bz to Gauss points
   constexpr int I2 = D::mm * D::mL + D::mL * D::mm + D::NZ;
-  FLAT_LOOP(I2) {
-    int e = idx / I2, it = idx % I2;
+  FLAT(I2) {
+    int it = idx / D::EB, e = idx % D::EB;
     if (it < D::mm * D::mL) {
       int j = it / D::mL, a = it % D::mL;
       double s = 0.0;
 #pragma unroll
-      for (int i = 0; i < D::mL; ++i) s = fma(S[e].bx[j * D::mL + i], T->ML[i][a], s);
-      S[e].t1[it] = s;
+      for (int i = 0; i < D::mL; ++i) s = fma(SM(O::BX, j * D::mL + i), T.ML[i][a], s);
+      SM(O::T1, it) = s;
     } else if (it < 2 * D::mm * D::mL) {
       it -= D::mm * D::mL;
       int b = it / D::mm, i = it % D::mm;
       double s = 0.0;
 #pragma unroll
-      for (int j = 0; j < D::mL; ++j) s = fma(T->ML[j][b], S[e].by[j * D::mm + i], s);
-      S[e].t2[it] = s;
+      for (int j = 0; j < D::mL; ++j) s = fma(T.ML[j][b], SM(O::BY, j * D::mm + i), s);
+      SM(O::T2, it) = s;
     } else {
       it -= 2 * D::mm * D::mL;
-      int r = it / D::mm, a = it % D::mm;  // Bz row r (GLL(k) y), Gauss x point a
+      int r = it / D::mm, a = it % D::mm;
       double s = 0.0;
 #pragma unroll
-      for (int c = 0; c < D::mm; ++c) s = fma(T->M_G[a][c], S[e].bz[r * D::mm + c], s);
-      S[e].ta[it] = s;
+      for (int c = 0; c < D::mm; ++c) s = fma(T.M_G[a][c], SM(O::BZ, r * D::mm + c), s);
+      SM(O::TA, it) = s;
     }
   }
   __syncthreads();
-  // stage 3: W loads and the y-pass of Bz
   const double cy = 2.0 / M.hy * M.Jdet, cx = 2.0 / M.hx * M.Jdet;
   constexpr int I3 = D::NW + D::NZ;
-  FLAT_LOOP(I3) {
-    int e = idx / I3, it = idx % I3, k = k0 + e;
+  FLAT(I3) {
+    int it = idx / D::EB, e = idx % D::EB, k = k0 + e;
     if (it < D::NW) {
       int b = it / D::mL, a = it % D::mL;
       double z1 = 0.0, z2 = 0.0;
 #pragma unroll
       for (int j = 0; j < D::mm; ++j) {
-        z1 = fma(T->wG[j] * T->dL_G[j][b], S[e].t1[j * D::mL + a], z1);
-        z2 = fma(T->wG[j] * T->dL_G[j][a], S[e].t2[b * D::mm + j], z2);
+        z1 = fma(T.wG[j] * T.dL_G[j][b], SM(O::T1, j * D::mL + a), z1);
+        z2 = fma(T.wG[j] * T.dL_G[j][a], SM(O::T2, b * D::mm + j), z2);
       }
       if (k < M.K) LJz[(size_t)k * D::NW + it] = fma(cy, z1, -cx * z2);
     } else {
@@ -178,53 +194,58 @@ __global__ void __launch_bounds__(256) k_mag_J(const double* __restrict__ Bx, co
       int d = it / D::mm, a = it % D::mm;
       double s = 0.0;
 #pragma unroll
-      for (int r = 0; r < D::mm; ++r) s = fma(T->M_G[d][r], S[e].ta[r * D::mm + a], s);
-      S[e].bzg[it] = s;
+      for (int r = 0; r < D::mm; ++r) s = fma(T.M_G[d][r], SM(O::TA, r * D::mm + a), s);
+      SM(O::BZG, it) = s;
     }
   }
   __syncthreads();
-  // stage 4: N loads
   constexpr int I4 = D::NX + D::NY;
-  FLAT_LOOP(I4) {
-    int e = idx / I4, it = idx % I4, k = k0 + e;
+  FLAT(I4) {
+    int it = idx / D::EB, e = idx % D::EB, k = k0 + e;
     if (k >= M.K) continue;
     if (it < D::NX) {  // J_x: a < mm (Gauss x), b < mL
       int b = it / D::mm, a = it % D::mm;
       double s = 0.0;
 #pragma unroll
-      for (int d = 0; d < D::mm; ++d) s = fma(T->wG[d] * T->dL_G[d][b], S[e].bzg[d * D::mm + a], s);
-      LJx[(size_t)k * D::NX + it] = -cy * T->wG[a] * s;
+      for (int d = 0; d < D::mm; ++d) s = fma(T.wG[d] * T.dL_G[d][b], SM(O::BZG, d * D::mm + a), s);
+      LJx[(size_t)k * D::NX + it] = -cy * T.wG[a] * s;
     } else {  // J_y: a < mL (GLL x), b < mm
       it -= D::NX;
       int b = it / D::mL, a = it % D::mL;
       double s = 0.0;
 #pragma unroll
-      for (int c = 0; c < D::mm; ++c) s = fma(T->wG[c] * T->dL_G[c][a], S[e].bzg[b * D::mm + c], s);
-      LJy[(size_t)k * D::NY + it] = cx * T->wG[b] * s;
+      for (int c = 0; c < D::mm; ++c) s = fma(T.wG[c] * T.dL_G[c][a], SM(O::BZG, b * D::mm + c), s);
+      LJy[(size_t)k * D::NY + it] = cx * T.wG[b] * s;
     }
   }
 }
 
 // ============================ k_mag_E ==========================================
 template <int P, int KM>
-struct SE {
+struct LE_ {  // per-element shared-memory offsets (doubles), with region reuse
   using D = MD<P, KM>;
-  double jx[D::NX], jy[D::NY], jz[D::NW];
-  double bx[D::NY], by[D::NX], bz[D::NZ];
-  double u[3][D::n2], rho[D::n2];
-  double ug[2][D::n * D::mm];    // u_y, u_z rows to Gauss x: [j][a]
-  double ul[3][D::n * D::mL];    // u_x, u_y, u_z rows to GLL(k+1) x
-  double bxg[D::NZ];             // Bx rows (Gauss y) to Gauss x
-  double byl[D::NW];             // By rows (GLL y) to GLL x  (= By at W nodes)
-  double bzg[D::NZ];             // Bz rows to Gauss x
-  double bzl[D::mm * D::mL];     // Bz rows to GLL(k+1) x
-  double unx[2][D::NX], uny[2][D::NY], uw[2][D::NW];
-  double bxnx[D::NX], bznx[D::NX], byny[D::NY], bzny[D::NY], bxw[D::NW], bzw[D::NW];
-  double ay_nx[D::NX], az_nx[D::NX], ax_ny[D::NY], az_ny[D::NY], ax_w[D::NW], ay_w[D::NW];
-  double vx[D::n * D::mL], vy1[D::n * D::mm], vy2[D::n * D::mL], vz1[D::n * D::mm], vz2[D::n * D::mL];
-  double jq[3][D::n2];           // J_h at the DG nodes (resistive part)
-  double tq[3][D::n * D::mL];    // x-pass scratch of the resistive part
-  double eta;
+  // region A: closures (live through the pointwise stage; J also in the resistive stage)
+  static constexpr int JX = 0, JY = JX + D::NX, JZ = JY + D::NY, BX = JZ + D::NW, BY = BX + D::NY, BZ = BY + D::NX;
+  static constexpr int ETA = BZ + D::NZ;
+  static constexpr int RB = ETA + 1;
+  // region B: x-passes (dead after the y-passes), then the transposed y-pass
+  static constexpr int UG = RB;                          // u_y, u_z rows to Gauss x: [d][j][a]
+  static constexpr int UL = UG + 2 * D::n * D::mm;       // u_x, u_y, u_z rows to GLL(k+1) x
+  static constexpr int BXG = UL + 3 * D::n * D::mL;      // Bx rows (Gauss y) to Gauss x
+  static constexpr int BYL = BXG + D::NZ;                // By rows (GLL y) to GLL x (= By at W)
+  static constexpr int BZG = BYL + D::NW;                // Bz rows to Gauss x
+  static constexpr int BZL = BZG + D::NZ;                // Bz rows to GLL(k+1) x
+  static constexpr int RB_END = BZL + D::mm * D::mL;
+  static constexpr int VX = RB, VY1 = VX + D::n * D::mL, VY2 = VY1 + D::n * D::mm, VZ1 = VY2 + D::n * D::mL,
+                       VZ2 = VZ1 + D::n * D::mm, V_END = VZ2 + D::n * D::mL;
+  static constexpr int RC = RB_END > V_END ? RB_END : V_END;
+  // region C: values at the auxiliary families; Lorentz products overwrite them in place;
+  // the resistive stage reuses it afterwards
+  static constexpr int UNX = RC, UNY = UNX + 2 * D::NX, UW = UNY + 2 * D::NY;
+  static constexpr int BXNX = UW + 2 * D::NW, BZNX = BXNX + D::NX, BYNY = BZNX + D::NX, BZNY = BYNY + D::NY;
+  static constexpr int BXW = BZNY + D::NY, BZW = BXW + D::NW, RC_END = BZW + D::NW;
+  static constexpr int TQ = RC, JQ = TQ + 3 * D::n * D::mL, RQ_END = JQ + 3 * D::n2;
+  static constexpr int SIZE = RC_END > RQ_END ? RC_END : RQ_END;
 };
 
 // mode 0: write du, de (residual test hook); mode 1: SSP combination into (uo, eo).
@@ -232,61 +253,58 @@ template <int P, int KM, int MODE>
 __global__ void __launch_bounds__(256) k_mag_E(
     const double* __restrict__ LJx, const double* __restrict__ LJy, const double* __restrict__ LJz,
     const double* __restrict__ Bx, const double* __restrict__ By, const double* __restrict__ Bz,
-    const double* __restrict__ u, const double* __restrict__ e, const double* __restrict__ rho,
-    const double* __restrict__ eta, const double* __restrict__ u0, const double* __restrict__ e0,
-    double* __restrict__ uo, double* __restrict__ eo, double* __restrict__ LEx, double* __restrict__ LEy,
-    double* __restrict__ LEz, const Tab* __restrict__ T, Mesh M, const double* __restrict__ dtp, double dtfac,
-    double ca, double cb, int first, int resistive) {
+    const double* __restrict__ u, const double* __restrict__ e_in, const double* __restrict__ rho,
+    const double* __restrict__ eta, const double* u0, const double* e0, double* uo, double* eo,
+    double* __restrict__ LEx, double* __restrict__ LEy, double* __restrict__ LEz, Mesh M,
+    const double* __restrict__ dtp, double dtfac, double ca, double cb, int first, int resistive) {
   using D = MD<P, KM>;
-  extern __shared__ double smem_raw[];
-  SE<P, KM>* S = reinterpret_cast<SE<P, KM>*>(smem_raw);
+  using O = LE_<P, KM>;
+  const Tab& T = c_mtab[D::SLOT];
+  extern __shared__ double sm[];
   const int k0 = blockIdx.x * D::EB;
   const size_t N = (size_t)M.K * D::n2;
   const double iJ = 1.0 / M.Jdet;
-  // stage 1: J closure (assembled), B closure, u, rho, eta
-  constexpr int I1 = D::NX + D::NY + D::NW + D::NY + D::NX + D::NZ + 4 * D::n2 + 1;
-  FLAT_LOOP(I1) {
-    int el = idx / I1, it = idx % I1, k = min(k0 + el, M.K - 1);
+  // stage 1: J closure (assembled), B closure, eta
+  constexpr int I1 = D::NX + D::NY + D::NW + D::NY + D::NX + D::NZ + 1;
+  FLAT(I1) {
+    int it = idx / D::EB, e = idx % D::EB, k = min(k0 + e, M.K - 1);
     int ex = k % M.nx, ey = k / M.nx;
-    if (it < D::NX) { S[el].jx[it] = assemble_Nx<P, KM>(LJx, ex, ey, it % D::mm, it / D::mm, M, iJ, T); continue; }
+    if (it < D::NX) { SM(O::JX, it) = assemble_Nx<P, KM>(LJx, ex, ey, it % D::mm, it / D::mm, M, iJ); continue; }
     it -= D::NX;
-    if (it < D::NY) { S[el].jy[it] = assemble_Ny<P, KM>(LJy, ex, ey, it % D::mL, it / D::mL, M, iJ, T); continue; }
+    if (it < D::NY) { SM(O::JY, it) = assemble_Ny<P, KM>(LJy, ex, ey, it % D::mL, it / D::mL, M, iJ); continue; }
     it -= D::NY;
-    if (it < D::NW) { S[el].jz[it] = assemble_W<P, KM>(LJz, ex, ey, it % D::mL, it / D::mL, M, iJ, T); continue; }
+    if (it < D::NW) { SM(O::JZ, it) = assemble_W<P, KM>(LJz, ex, ey, it % D::mL, it / D::mL, M, iJ); continue; }
     it -= D::NW;
-    if (it < D::NY) { S[el].bx[it] = closure_Bx<P, KM>(Bx, ex, ey, it % D::mL, it / D::mL, M); continue; }
+    if (it < D::NY) { SM(O::BX, it) = closure_Bx<P, KM>(Bx, ex, ey, it % D::mL, it / D::mL, M); continue; }
     it -= D::NY;
-    if (it < D::NX) { S[el].by[it] = closure_By<P, KM>(By, ex, ey, it % D::mm, it / D::mm, M); continue; }
+    if (it < D::NX) { SM(O::BY, it) = closure_By<P, KM>(By, ex, ey, it % D::mm, it / D::mm, M); continue; }
     it -= D::NX;
-    if (it < D::NZ) { S[el].bz[it] = Bz[(size_t)k * D::NZ + it]; continue; }
-    it -= D::NZ;
-    if (it < 3 * D::n2) { int d = it / D::n2, q = it % D::n2; S[el].u[d][q] = u[d * N + (size_t)k * D::n2 + q]; continue; }
-    it -= 3 * D::n2;
-    if (it < D::n2) { S[el].rho[it] = rho[(size_t)k * D::n2 + it]; continue; }
-    S[el].eta = resistive ? eta[k] : 0.0;
+    if (it < D::NZ) { SM(O::BZ, it) = Bz[(size_t)k * D::NZ + it]; continue; }
+    SM(O::ETA, 0) = resistive ? eta[k] : 0.0;
   }
   __syncthreads();
-  // stage 2: x-passes
+  // stage 2: x-passes (u read straight from global memory)
   constexpr int NUG = 2 * D::n * D::mm, NUL = 3 * D::n * D::mL;
   constexpr int I2 = NUG + NUL + D::NZ + D::NW + D::NZ + D::mm * D::mL;
-  FLAT_LOOP(I2) {
-    int el = idx / I2, it = idx % I2;
-    auto& s = S[el];
+  FLAT(I2) {
+    int it = idx / D::EB, e = idx % D::EB, k = min(k0 + e, M.K - 1);
     if (it < NUG) {  // u_y, u_z to Gauss x
       int d = it / (D::n * D::mm), r = it % (D::n * D::mm), j = r / D::mm, a = r % D::mm;
+      const double* ur = u + (1 + d) * N + (size_t)k * D::n2 + j * D::n;
       double v = 0.0;
 #pragma unroll
-      for (int i = 0; i < D::n; ++i) v = fma(T->P_G[a][i], s.u[1 + d][j * D::n + i], v);
-      s.ug[d][r] = v;
+      for (int i = 0; i < D::n; ++i) v = fma(T.P_G[a][i], ur[i], v);
+      SM(O::UG, it) = v;
       continue;
     }
     it -= NUG;
     if (it < NUL) {  // u_x, u_y, u_z to GLL(k+1) x
       int d = it / (D::n * D::mL), r = it % (D::n * D::mL), j = r / D::mL, a = r % D::mL;
+      const double* ur = u + d * N + (size_t)k * D::n2 + j * D::n;
       double v = 0.0;
 #pragma unroll
-      for (int i = 0; i < D::n; ++i) v = fma(T->P_L[a][i], s.u[d][j * D::n + i], v);
-      s.ul[d][r] = v;
+      for (int i = 0; i < D::n; ++i) v = fma(T.P_L[a][i], ur[i], v);
+      SM(O::UL, it) = v;
       continue;
     }
     it -= NUL;
@@ -294,8 +312,8 @@ __global__ void __launch_bounds__(256) k_mag_E(
       int j = it / D::mm, a = it % D::mm;
       double v = 0.0;
 #pragma unroll
-      for (int i = 0; i < D::mL; ++i) v = fma(T->L_G[a][i], s.bx[j * D::mL + i], v);
-      s.bxg[it] = v;
+      for (int i = 0; i < D::mL; ++i) v = fma(T.L_G[a][i], SM(O::BX, j * D::mL + i), v);
+      SM(O::BXG, it) = v;
       continue;
     }
     it -= D::NZ;
@@ -303,8 +321,8 @@ __global__ void __launch_bounds__(256) k_mag_E(
       int j = it / D::mL, a = it % D::mL;
       double v = 0.0;
 #pragma unroll
-      for (int i = 0; i < D::mm; ++i) v = fma(T->G_L[a][i], s.by[j * D::mm + i], v);
-      s.byl[it] = v;
+      for (int i = 0; i < D::mm; ++i) v = fma(T.G_L[a][i], SM(O::BY, j * D::mm + i), v);
+      SM(O::BYL, it) = v;
       continue;
     }
     it -= D::NW;
@@ -312,8 +330,8 @@ __global__ void __launch_bounds__(256) k_mag_E(
       int j = it / D::mm, a = it % D::mm;
       double v = 0.0;
 #pragma unroll
-      for (int i = 0; i < D::mm; ++i) v = fma(T->M_G[a][i], s.bz[j * D::mm + i], v);
-      s.bzg[it] = v;
+      for (int i = 0; i < D::mm; ++i) v = fma(T.M_G[a][i], SM(O::BZ, j * D::mm + i), v);
+      SM(O::BZG, it) = v;
       continue;
     }
     it -= D::NZ;
@@ -321,32 +339,31 @@ __global__ void __launch_bounds__(256) k_mag_E(
       int j = it / D::mL, a = it % D::mL;
       double v = 0.0;
 #pragma unroll
-      for (int i = 0; i < D::mm; ++i) v = fma(T->M_L[a][i], s.bz[j * D::mm + i], v);
-      s.bzl[it] = v;
+      for (int i = 0; i < D::mm; ++i) v = fma(T.M_L[a][i], SM(O::BZ, j * D::mm + i), v);
+      SM(O::BZL, it) = v;
     }
   }
   __syncthreads();
   // stage 3: y-passes to the auxiliary families
   constexpr int I3 = 2 * D::NX + 2 * D::NY + 2 * D::NW + D::NX + D::NX + D::NY + D::NY + D::NW + D::NW;
-  FLAT_LOOP(I3) {
-    int el = idx / I3, it = idx % I3;
-    auto& s = S[el];
+  FLAT(I3) {
+    int it = idx / D::EB, e = idx % D::EB;
     if (it < 2 * D::NX) {  // u_y, u_z at N_x: GLL(k+1) y from GLL(p)
       int d = it / D::NX, r = it % D::NX, b = r / D::mm, a = r % D::mm;
       double v = 0.0;
 #pragma unroll
-      for (int j = 0; j < D::n; ++j) v = fma(T->P_L[b][j], s.ug[d][j * D::mm + a], v);
-      s.unx[d][r] = v;
+      for (int j = 0; j < D::n; ++j) v = fma(T.P_L[b][j], SM(O::UG, d * D::n * D::mm + j * D::mm + a), v);
+      SM(O::UNX, it) = v;
       continue;
     }
     it -= 2 * D::NX;
     if (it < 2 * D::NY) {  // u_x, u_z at N_y: Gauss y
       int d = it / D::NY, r = it % D::NY, b = r / D::mL, a = r % D::mL;
-      const double* src = d == 0 ? s.ul[0] : s.ul[2];
+      const int src = (d == 0 ? 0 : 2) * D::n * D::mL;
       double v = 0.0;
 #pragma unroll
-      for (int j = 0; j < D::n; ++j) v = fma(T->P_G[b][j], src[j * D::mL + a], v);
-      s.uny[d][r] = v;
+      for (int j = 0; j < D::n; ++j) v = fma(T.P_G[b][j], SM(O::UL, src + j * D::mL + a), v);
+      SM(O::UNY, it) = v;
       continue;
     }
     it -= 2 * D::NY;
@@ -354,8 +371,8 @@ __global__ void __launch_bounds__(256) k_mag_E(
       int d = it / D::NW, r = it % D::NW, b = r / D::mL, a = r % D::mL;
       double v = 0.0;
 #pragma unroll
-      for (int j = 0; j < D::n; ++j) v = fma(T->P_L[b][j], s.ul[d][j * D::mL + a], v);
-      s.uw[d][r] = v;
+      for (int j = 0; j < D::n; ++j) v = fma(T.P_L[b][j], SM(O::UL, d * D::n * D::mL + j * D::mL + a), v);
+      SM(O::UW, it) = v;
       continue;
     }
     it -= 2 * D::NW;
@@ -363,8 +380,8 @@ __global__ void __launch_bounds__(256) k_mag_E(
       int b = it / D::mm, a = it % D::mm;
       double v = 0.0;
 #pragma unroll
-      for (int j = 0; j < D::mm; ++j) v = fma(T->G_L[b][j], s.bxg[j * D::mm + a], v);
-      s.bxnx[it] = v;
+      for (int j = 0; j < D::mm; ++j) v = fma(T.G_L[b][j], SM(O::BXG, j * D::mm + a), v);
+      SM(O::BXNX, it) = v;
       continue;
     }
     it -= D::NX;
@@ -372,8 +389,8 @@ __global__ void __launch_bounds__(256) k_mag_E(
       int b = it / D::mm, a = it % D::mm;
       double v = 0.0;
 #pragma unroll
-      for (int j = 0; j < D::mm; ++j) v = fma(T->M_L[b][j], s.bzg[j * D::mm + a], v);
-      s.bznx[it] = v;
+      for (int j = 0; j < D::mm; ++j) v = fma(T.M_L[b][j], SM(O::BZG, j * D::mm + a), v);
+      SM(O::BZNX, it) = v;
       continue;
     }
     it -= D::NX;
@@ -381,8 +398,8 @@ __global__ void __launch_bounds__(256) k_mag_E(
       int b = it / D::mL, a = it % D::mL;
       double v = 0.0;
 #pragma unroll
-      for (int j = 0; j < D::mL; ++j) v = fma(T->L_G[b][j], s.byl[j * D::mL + a], v);
-      s.byny[it] = v;
+      for (int j = 0; j < D::mL; ++j) v = fma(T.L_G[b][j], SM(O::BYL, j * D::mL + a), v);
+      SM(O::BYNY, it) = v;
       continue;
     }
     it -= D::NY;
@@ -390,8 +407,8 @@ __global__ void __launch_bounds__(256) k_mag_E(
       int b = it / D::mL, a = it % D::mL;
       double v = 0.0;
 #pragma unroll
-      for (int j = 0; j < D::mm; ++j) v = fma(T->M_G[b][j], s.bzl[j * D::mL + a], v);
-      s.bzny[it] = v;
+      for (int j = 0; j < D::mm; ++j) v = fma(T.M_G[b][j], SM(O::BZL, j * D::mL + a), v);
+      SM(O::BZNY, it) = v;
       continue;
     }
     it -= D::NY;
@@ -399,8 +416,8 @@ __global__ void __launch_bounds__(256) k_mag_E(
       int b = it / D::mL, a = it % D::mL;
       double v = 0.0;
 #pragma unroll
-      for (int j = 0; j < D::mm; ++j) v = fma(T->G_L[b][j], s.bx[j * D::mL + a], v);
-      s.bxw[it] = v;
+      for (int j = 0; j < D::mm; ++j) v = fma(T.G_L[b][j], SM(O::BX, j * D::mL + a), v);
+      SM(O::BXW, it) = v;
       continue;
     }
     it -= D::NW;
@@ -408,56 +425,57 @@ __global__ void __launch_bounds__(256) k_mag_E(
       int b = it / D::mL, a = it % D::mL;
       double v = 0.0;
 #pragma unroll
-      for (int j = 0; j < D::mm; ++j) v = fma(T->M_L[b][j], s.bzl[j * D::mL + a], v);
-      s.bzw[it] = v;
+      for (int j = 0; j < D::mm; ++j) v = fma(T.M_L[b][j], SM(O::BZL, j * D::mL + a), v);
+      SM(O::BZW, it) = v;
     }
   }
   __syncthreads();
-  // stage 4: pointwise E loads (lumped weights) and Lorentz products
+  // stage 4: pointwise E loads (lumped weights); Lorentz products overwrite the u values in place
   const double Jd = M.Jdet;
   constexpr int I4 = D::NX + D::NY + D::NW;
-  FLAT_LOOP(I4) {
-    int el = idx / I4, it = idx % I4, k = k0 + el;
-    auto& s = S[el];
+  FLAT(I4) {
+    int it = idx / D::EB, e = idx % D::EB, k = k0 + e;
     if (it < D::NX) {
       int b = it / D::mm, a = it % D::mm;
-      double w = Jd * T->wG[a] * T->wL[b];
-      double by_ = s.by[it], bz_ = s.bznx[it], jx_ = s.jx[it];
-      if (k < M.K) LEx[(size_t)k * D::NX + it] = w * fma(s.unx[1][it], by_, -s.unx[0][it] * bz_);
-      s.ay_nx[it] = -w * bz_ * jx_;
-      s.az_nx[it] = w * by_ * jx_;
+      double w = Jd * T.wG[a] * T.wL[b];
+      double by_ = SM(O::BY, it), bz_ = SM(O::BZNX, it), jx_ = SM(O::JX, it);
+      double uy = SM(O::UNX, it), uz = SM(O::UNX, D::NX + it);
+      if (k < M.K) LEx[(size_t)k * D::NX + it] = w * fma(uz, by_, -uy * bz_);
+      SM(O::UNX, it) = -w * bz_ * jx_;         // s_y contribution
+      SM(O::UNX, D::NX + it) = w * by_ * jx_;  // s_z contribution
     } else if (it < D::NX + D::NY) {
       it -= D::NX;
       int b = it / D::mL, a = it % D::mL;
-      double w = Jd * T->wL[a] * T->wG[b];
-      double bx_ = s.bx[it], bz_ = s.bzny[it], jy_ = s.jy[it];
-      if (k < M.K) LEy[(size_t)k * D::NY + it] = w * fma(s.uny[0][it], bz_, -s.uny[1][it] * bx_);
-      s.ax_ny[it] = w * bz_ * jy_;
-      s.az_ny[it] = -w * bx_ * jy_;
+      double w = Jd * T.wL[a] * T.wG[b];
+      double bx_ = SM(O::BX, it), bz_ = SM(O::BZNY, it), jy_ = SM(O::JY, it);
+      double ux = SM(O::UNY, it), uz = SM(O::UNY, D::NY + it);
+      if (k < M.K) LEy[(size_t)k * D::NY + it] = w * fma(ux, bz_, -uz * bx_);
+      SM(O::UNY, it) = w * bz_ * jy_;           // s_x
+      SM(O::UNY, D::NY + it) = -w * bx_ * jy_;  // s_z
     } else {
       it -= D::NX + D::NY;
       int b = it / D::mL, a = it % D::mL;
-      double w = Jd * T->wL[a] * T->wL[b];
-      double bx_ = s.bxw[it], by_ = s.byl[it], jz_ = s.jz[it];
-      if (k < M.K) LEz[(size_t)k * D::NW + it] = w * fma(s.uw[1][it], bx_, -s.uw[0][it] * by_);
-      s.ax_w[it] = -w * by_ * jz_;
-      s.ay_w[it] = w * bx_ * jz_;
+      double w = Jd * T.wL[a] * T.wL[b];
+      double bx_ = SM(O::BXW, it), by_ = SM(O::BYL, it), jz_ = SM(O::JZ, it);
+      double ux = SM(O::UW, it), uy = SM(O::UW, D::NW + it);
+      if (k < M.K) LEz[(size_t)k * D::NW + it] = w * fma(uy, bx_, -ux * by_);
+      SM(O::UW, it) = -w * by_ * jz_;          // s_x
+      SM(O::UW, D::NW + it) = w * bx_ * jz_;   // s_y
     }
   }
   __syncthreads();
-  // stage 5: transposed y-pass onto the DG y-nodes
+  // stage 5: transposed y-pass onto the DG y-nodes (into region B)
   constexpr int I5 = D::n * D::mL + D::n * D::mm + D::n * D::mL + D::n * D::mm + D::n * D::mL;
-  FLAT_LOOP(I5) {
-    int el = idx / I5, it = idx % I5;
-    auto& s = S[el];
+  FLAT(I5) {
+    int it = idx / D::EB, e = idx % D::EB;
     if (it < D::n * D::mL) {
       int j = it / D::mL, a = it % D::mL;
       double v = 0.0;
 #pragma unroll
-      for (int b = 0; b < D::mm; ++b) v = fma(T->P_G[b][j], s.ax_ny[b * D::mL + a], v);
+      for (int b = 0; b < D::mm; ++b) v = fma(T.P_G[b][j], SM(O::UNY, b * D::mL + a), v);
 #pragma unroll
-      for (int b = 0; b < D::mL; ++b) v = fma(T->P_L[b][j], s.ax_w[b * D::mL + a], v);
-      s.vx[it] = v;
+      for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UW, b * D::mL + a), v);
+      SM(O::VX, it) = v;
       continue;
     }
     it -= D::n * D::mL;
@@ -465,8 +483,8 @@ __global__ void __launch_bounds__(256) k_mag_E(
       int j = it / D::mm, a = it % D::mm;
       double v = 0.0;
 #pragma unroll
-      for (int b = 0; b < D::mL; ++b) v = fma(T->P_L[b][j], s.ay_nx[b * D::mm + a], v);
-      s.vy1[it] = v;
+      for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UNX, b * D::mm + a), v);
+      SM(O::VY1, it) = v;
       continue;
     }
     it -= D::n * D::mm;
@@ -474,8 +492,8 @@ __global__ void __launch_bounds__(256) k_mag_E(
       int j = it / D::mL, a = it % D::mL;
       double v = 0.0;
 #pragma unroll
-      for (int b = 0; b < D::mL; ++b) v = fma(T->P_L[b][j], s.ay_w[b * D::mL + a], v);
-      s.vy2[it] = v;
+      for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UW, D::NW + b * D::mL + a), v);
+      SM(O::VY2, it) = v;
       continue;
     }
     it -= D::n * D::mL;
@@ -483,8 +501,8 @@ __global__ void __launch_bounds__(256) k_mag_E(
       int j = it / D::mm, a = it % D::mm;
       double v = 0.0;
 #pragma unroll
-      for (int b = 0; b < D::mL; ++b) v = fma(T->P_L[b][j], s.az_nx[b * D::mm + a], v);
-      s.vz1[it] = v;
+      for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UNX, D::NX + b * D::mm + a), v);
+      SM(O::VZ1, it) = v;
       continue;
     }
     it -= D::n * D::mm;
@@ -492,133 +510,127 @@ __global__ void __launch_bounds__(256) k_mag_E(
       int j = it / D::mL, a = it % D::mL;
       double v = 0.0;
 #pragma unroll
-      for (int b = 0; b < D::mm; ++b) v = fma(T->P_G[b][j], s.az_ny[b * D::mL + a], v);
-      s.vz2[it] = v;
+      for (int b = 0; b < D::mm; ++b) v = fma(T.P_G[b][j], SM(O::UNY, D::NY + b * D::mL + a), v);
+      SM(O::VZ2, it) = v;
     }
   }
   __syncthreads();
-  // stage 5b (resistive only): J_h at the DG nodes, x-pass then y-pass
-  bool any_res = false;
+  // stage 5b (resistive only): J_h at the DG nodes and the resistive loads
   if (resistive) {
-    // x-pass: Jx rows (GLL y, b < mL) Gauss->DG x; Jy rows (Gauss y) GLL->DG x; Jz rows GLL->DG x
     constexpr int IR1 = D::mL * D::n + D::mm * D::n + D::mL * D::n;
-    FLAT_LOOP(IR1) {
-      int el = idx / IR1, it = idx % IR1;
-      auto& s = S[el];
-      if (s.eta == 0.0) continue;
+    FLAT(IR1) {
+      int it = idx / D::EB, e = idx % D::EB;
+      if (SM(O::ETA, 0) == 0.0) continue;
       if (it < D::mL * D::n) {
         int b = it / D::n, i = it % D::n;
         double v = 0.0;
 #pragma unroll
-        for (int a = 0; a < D::mm; ++a) v = fma(T->G_P[i][a], s.jx[b * D::mm + a], v);
-        s.tq[0][it] = v;
+        for (int a = 0; a < D::mm; ++a) v = fma(T.G_P[i][a], SM(O::JX, b * D::mm + a), v);
+        SM(O::TQ, it) = v;
       } else if (it < D::mL * D::n + D::mm * D::n) {
         it -= D::mL * D::n;
         int b = it / D::n, i = it % D::n;
         double v = 0.0;
 #pragma unroll
-        for (int a = 0; a < D::mL; ++a) v = fma(T->L_P[i][a], s.jy[b * D::mL + a], v);
-        s.tq[1][it] = v;
+        for (int a = 0; a < D::mL; ++a) v = fma(T.L_P[i][a], SM(O::JY, b * D::mL + a), v);
+        SM(O::TQ, D::n * D::mL + it) = v;
       } else {
         it -= D::mL * D::n + D::mm * D::n;
         int b = it / D::n, i = it % D::n;
         double v = 0.0;
 #pragma unroll
-        for (int a = 0; a < D::mL; ++a) v = fma(T->L_P[i][a], s.jz[b * D::mL + a], v);
-        s.tq[2][it] = v;
+        for (int a = 0; a < D::mL; ++a) v = fma(T.L_P[i][a], SM(O::JZ, b * D::mL + a), v);
+        SM(O::TQ, 2 * D::n * D::mL + it) = v;
       }
     }
     __syncthreads();
     constexpr int IR2 = 3 * D::n2;
-    FLAT_LOOP(IR2) {
-      int el = idx / IR2, it = idx % IR2;
-      auto& s = S[el];
-      if (s.eta == 0.0) continue;
+    FLAT(IR2) {
+      int it = idx / D::EB, e = idx % D::EB;
+      if (SM(O::ETA, 0) == 0.0) continue;
       int d = it / D::n2, q = it % D::n2, j = q / D::n, i = q % D::n;
       double v = 0.0;
       if (d == 0) {
 #pragma unroll
-        for (int b = 0; b < D::mL; ++b) v = fma(T->L_P[j][b], s.tq[0][b * D::n + i], v);
+        for (int b = 0; b < D::mL; ++b) v = fma(T.L_P[j][b], SM(O::TQ, b * D::n + i), v);
       } else if (d == 1) {
 #pragma unroll
-        for (int b = 0; b < D::mm; ++b) v = fma(T->G_P[j][b], s.tq[1][b * D::n + i], v);
+        for (int b = 0; b < D::mm; ++b) v = fma(T.G_P[j][b], SM(O::TQ, D::n * D::mL + b * D::n + i), v);
       } else {
 #pragma unroll
-        for (int b = 0; b < D::mL; ++b) v = fma(T->L_P[j][b], s.tq[2][b * D::n + i], v);
+        for (int b = 0; b < D::mL; ++b) v = fma(T.L_P[j][b], SM(O::TQ, 2 * D::n * D::mL + b * D::n + i), v);
       }
-      s.jq[d][q] = v;
+      SM(O::JQ, it) = v;
     }
     __syncthreads();
-    // resistive loads R_n = eta sum_q Jdet w_q J(x_q) phi_n(x_q), added to the E loads
-    // (each element adds only to its own closure loads)
+    // R_n = eta sum_q Jdet w_q J(x_q) phi_n(x_q), added to this element's own closure loads
     constexpr int IR3 = D::NX + D::NY + D::NW;
-    FLAT_LOOP(IR3) {
-      int el = idx / IR3, it = idx % IR3, k = k0 + el;
-      auto& s = S[el];
-      if (s.eta == 0.0 || k >= M.K) continue;
+    FLAT(IR3) {
+      int it = idx / D::EB, e = idx % D::EB, k = k0 + e;
+      const double et = SM(O::ETA, 0);
+      if (et == 0.0 || k >= M.K) continue;
       double r = 0.0;
       if (it < D::NX) {
         int b = it / D::mm, a = it % D::mm;
         for (int j = 0; j < D::n; ++j) {
           double t = 0.0;
 #pragma unroll
-          for (int i = 0; i < D::n; ++i) t = fma(T->wp[i] * T->G_P[i][a], s.jq[0][j * D::n + i], t);
-          r = fma(T->wp[j] * T->L_P[j][b], t, r);
+          for (int i = 0; i < D::n; ++i) t = fma(T.wp[i] * T.G_P[i][a], SM(O::JQ, j * D::n + i), t);
+          r = fma(T.wp[j] * T.L_P[j][b], t, r);
         }
-        LEx[(size_t)k * D::NX + it] += s.eta * Jd * r;
+        LEx[(size_t)k * D::NX + it] += et * Jd * r;
       } else if (it < D::NX + D::NY) {
         it -= D::NX;
         int b = it / D::mL, a = it % D::mL;
         for (int j = 0; j < D::n; ++j) {
           double t = 0.0;
 #pragma unroll
-          for (int i = 0; i < D::n; ++i) t = fma(T->wp[i] * T->L_P[i][a], s.jq[1][j * D::n + i], t);
-          r = fma(T->wp[j] * T->G_P[j][b], t, r);
+          for (int i = 0; i < D::n; ++i) t = fma(T.wp[i] * T.L_P[i][a], SM(O::JQ, D::n2 + j * D::n + i), t);
+          r = fma(T.wp[j] * T.G_P[j][b], t, r);
         }
-        LEy[(size_t)k * D::NY + it] += s.eta * Jd * r;
+        LEy[(size_t)k * D::NY + it] += et * Jd * r;
       } else {
         it -= D::NX + D::NY;
         int b = it / D::mL, a = it % D::mL;
         for (int j = 0; j < D::n; ++j) {
           double t = 0.0;
 #pragma unroll
-          for (int i = 0; i < D::n; ++i) t = fma(T->wp[i] * T->L_P[i][a], s.jq[2][j * D::n + i], t);
-          r = fma(T->wp[j] * T->L_P[j][b], t, r);
+          for (int i = 0; i < D::n; ++i) t = fma(T.wp[i] * T.L_P[i][a], SM(O::JQ, 2 * D::n2 + j * D::n + i), t);
+          r = fma(T.wp[j] * T.L_P[j][b], t, r);
         }
-        LEz[(size_t)k * D::NW + it] += s.eta * Jd * r;
+        LEz[(size_t)k * D::NW + it] += et * Jd * r;
       }
     }
-    any_res = true;
   }
   // stage 6: x-pass onto DG nodes, velocity and energy rates, SSP combination
   const double tau = MODE ? dtp[0] * dtfac : 0.0;
   constexpr int I6 = D::n2;
-  FLAT_LOOP(I6) {
-    int el = idx / I6, q = idx % I6, k = k0 + el;
+  FLAT(I6) {
+    int q = idx / D::EB, e = idx % D::EB, k = k0 + e;
     if (k >= M.K) continue;
-    auto& s = S[el];
     int j = q / D::n, i = q % D::n;
     double sx = 0.0, sy = 0.0, sz = 0.0;
 #pragma unroll
     for (int a = 0; a < D::mL; ++a) {
-      sx = fma(T->P_L[a][i], s.vx[j * D::mL + a], sx);
-      sy = fma(T->P_L[a][i], s.vy2[j * D::mL + a], sy);
-      sz = fma(T->P_L[a][i], s.vz2[j * D::mL + a], sz);
+      sx = fma(T.P_L[a][i], SM(O::VX, j * D::mL + a), sx);
+      sy = fma(T.P_L[a][i], SM(O::VY2, j * D::mL + a), sy);
+      sz = fma(T.P_L[a][i], SM(O::VZ2, j * D::mL + a), sz);
     }
 #pragma unroll
     for (int a = 0; a < D::mm; ++a) {
-      sy = fma(T->P_G[a][i], s.vy1[j * D::mm + a], sy);
-      sz = fma(T->P_G[a][i], s.vz1[j * D::mm + a], sz);
-    }
-    double r_ = s.rho[q];
-    double im = rcp(r_ * Jd * T->wp[i] * T->wp[j]);
-    double du[3] = {sx * im, sy * im, sz * im};
-    double de = 0.0;
-    if (any_res && s.eta != 0.0) {
-      double jx = s.jq[0][q], jy = s.jq[1][q], jz = s.jq[2][q];
-      de = s.eta * fma(jx, jx, fma(jy, jy, jz * jz)) * rcp(r_);
+      sy = fma(T.P_G[a][i], SM(O::VY1, j * D::mm + a), sy);
+      sz = fma(T.P_G[a][i], SM(O::VZ1, j * D::mm + a), sz);
     }
     size_t gq = (size_t)k * D::n2 + q;
+    double r_ = rho[gq];
+    double im = rcp(r_ * Jd * T.wp[i] * T.wp[j]);
+    double du[3] = {sx * im, sy * im, sz * im};
+    double de = 0.0;
+    const double et = SM(O::ETA, 0);
+    if (resistive && et != 0.0) {
+      double jx = SM(O::JQ, q), jy = SM(O::JQ, D::n2 + q), jz = SM(O::JQ, 2 * D::n2 + q);
+      de = et * fma(jx, jx, fma(jy, jy, jz * jz)) * rcp(r_);
+    }
     if (MODE == 0) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) uo[d * N + gq] = du[d];
@@ -626,10 +638,10 @@ __global__ void __launch_bounds__(256) k_mag_E(
     } else {
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        double raw = fma(tau, du[d], s.u[d][q]);
+        double raw = fma(tau, du[d], u[d * N + gq]);
         uo[d * N + gq] = first ? raw : fma(ca, u0[d * N + gq], cb * raw);
       }
-      double raw = fma(tau, de, e[gq]);
+      double raw = fma(tau, de, e_in[gq]);
       eo[gq] = first ? raw : fma(ca, e0[gq], cb * raw);
     }
   }
@@ -637,79 +649,79 @@ __global__ void __launch_bounds__(256) k_mag_E(
 
 // ============================ k_mag_B ==========================================
 template <int P, int KM>
-struct SB {
+struct LB_ {
   using D = MD<P, KM>;
-  double ex[D::NX], ey[D::NY], ez[D::NW];
-  double ty[D::mm * D::mm];   // d/dx of E_y rows at GLL(k) x: [b < mm][a < mm]
-  double tx[D::mL * D::mm];   // E_x rows (GLL y) to GLL(k) x: [b < mL][a < mm]
+  static constexpr int EX = 0, EY = EX + D::NX, EZ = EY + D::NY;
+  static constexpr int TY = EZ + D::NW;          // d/dx of E_y rows at GLL(k) x: [b < mm][a < mm]
+  static constexpr int TX = TY + D::NZ;          // E_x rows (GLL y) to GLL(k) x: [b < mL][a < mm]
+  static constexpr int SIZE = TX + D::mL * D::mm;
 };
 
 // mode 0: write dB; mode 1: SSP combination into Bo.
 template <int P, int KM, int MODE>
-__global__ void __launch_bounds__(256) k_mag_B(
-    const double* __restrict__ LEx, const double* __restrict__ LEy, const double* __restrict__ LEz,
-    const double* __restrict__ B, const double* __restrict__ B0, double* __restrict__ Bo, const Tab* __restrict__ T,
-    Mesh M, const double* __restrict__ dtp, double dtfac, double ca, double cb, int first) {
+__global__ void __launch_bounds__(256) k_mag_B(const double* __restrict__ LEx, const double* __restrict__ LEy,
+                                               const double* __restrict__ LEz, const double* B, const double* B0,
+                                               double* Bo, Mesh M, const double* __restrict__ dtp, double dtfac,
+                                               double ca, double cb, int first) {
   using D = MD<P, KM>;
-  extern __shared__ double smem_raw[];
-  SB<P, KM>* S = reinterpret_cast<SB<P, KM>*>(smem_raw);
+  using O = LB_<P, KM>;
+  const Tab& T = c_mtab[D::SLOT];
+  extern __shared__ double sm[];
   const int k0 = blockIdx.x * D::EB;
   const double iJ = 1.0 / M.Jdet;
   const size_t Z = (size_t)M.K * D::NZ;
   constexpr int I1 = D::NX + D::NY + D::NW;
-  FLAT_LOOP(I1) {
-    int el = idx / I1, it = idx % I1, k = min(k0 + el, M.K - 1);
+  FLAT(I1) {
+    int it = idx / D::EB, e = idx % D::EB, k = min(k0 + e, M.K - 1);
     int ex = k % M.nx, ey = k / M.nx;
-    if (it < D::NX) S[el].ex[it] = assemble_Nx<P, KM>(LEx, ex, ey, it % D::mm, it / D::mm, M, iJ, T);
-    else if (it < D::NX + D::NY) { it -= D::NX; S[el].ey[it] = assemble_Ny<P, KM>(LEy, ex, ey, it % D::mL, it / D::mL, M, iJ, T); }
-    else { it -= D::NX + D::NY; S[el].ez[it] = assemble_W<P, KM>(LEz, ex, ey, it % D::mL, it / D::mL, M, iJ, T); }
+    if (it < D::NX) SM(O::EX, it) = assemble_Nx<P, KM>(LEx, ex, ey, it % D::mm, it / D::mm, M, iJ);
+    else if (it < D::NX + D::NY) { it -= D::NX; SM(O::EY, it) = assemble_Ny<P, KM>(LEy, ex, ey, it % D::mL, it / D::mL, M, iJ); }
+    else { it -= D::NX + D::NY; SM(O::EZ, it) = assemble_W<P, KM>(LEz, ex, ey, it % D::mL, it / D::mL, M, iJ); }
   }
   __syncthreads();
   constexpr int I2 = D::NZ + D::mL * D::mm;
-  FLAT_LOOP(I2) {
-    int el = idx / I2, it = idx % I2;
-    auto& s = S[el];
+  FLAT(I2) {
+    int it = idx / D::EB, e = idx % D::EB;
     if (it < D::NZ) {  // d/dx E_y at GLL(k) x, rows Gauss y
       int b = it / D::mm, a = it % D::mm;
       double v = 0.0;
 #pragma unroll
-      for (int c = 0; c < D::mL; ++c) v = fma(T->dL_M[a][c], s.ey[b * D::mL + c], v);
-      s.ty[it] = v;
+      for (int c = 0; c < D::mL; ++c) v = fma(T.dL_M[a][c], SM(O::EY, b * D::mL + c), v);
+      SM(O::TY, it) = v;
     } else {
       it -= D::NZ;
       int b = it / D::mm, a = it % D::mm;  // E_x rows (GLL y) to GLL(k) x
       double v = 0.0;
 #pragma unroll
-      for (int c = 0; c < D::mm; ++c) v = fma(T->G_M[a][c], s.ex[b * D::mm + c], v);
-      s.tx[it] = v;
+      for (int c = 0; c < D::mm; ++c) v = fma(T.G_M[a][c], SM(O::EX, b * D::mm + c), v);
+      SM(O::TX, it) = v;
     }
   }
   __syncthreads();
   const double tau = MODE ? dtp[0] * dtfac : 0.0;
   const double ax = 2.0 / M.hx, ay = 2.0 / M.hy;
   constexpr int I3 = 3 * D::NZ;
-  FLAT_LOOP(I3) {
-    int el = idx / I3, it = idx % I3, k = k0 + el;
+  FLAT(I3) {
+    int it = idx / D::EB, e = idx % D::EB, k = k0 + e;
     if (k >= M.K) continue;
-    auto& s = S[el];
     int comp = it / D::NZ, r = it % D::NZ, b = r / D::mm, a = r % D::mm;
     double dB;
     if (comp == 0) {  // Bx at (xL_a, zG_b): -d_y E_z
       double v = 0.0;
 #pragma unroll
-      for (int c = 0; c < D::mL; ++c) v = fma(T->dL_G[b][c], s.ez[c * D::mL + a], v);
+      for (int c = 0; c < D::mL; ++c) v = fma(T.dL_G[b][c], SM(O::EZ, c * D::mL + a), v);
       dB = -ay * v;
     } else if (comp == 1) {  // By at (zG_a, xL_b): d_x E_z
       double v = 0.0;
 #pragma unroll
-      for (int c = 0; c < D::mL; ++c) v = fma(T->dL_G[a][c], s.ez[b * D::mL + c], v);
+      for (int c = 0; c < D::mL; ++c) v = fma(T.dL_G[a][c], SM(O::EZ, b * D::mL + c), v);
       dB = ax * v;
     } else {  // Bz at (xM_a, xM_b): -(d_x E_y - d_y E_x)
       double vy = 0.0, vx = 0.0;
 #pragma unroll
-      for (int c = 0; c < D::mm; ++c) vy = fma(T->G_M[b][c], s.ty[c * D::mm + a], vy);
+      for (int c = 0; c < D::mm; ++c) vy = fma(T.G_M[b][c], SM(O::TY, c * D::mm + a), vy);
 #pragma unroll
-      for (int c = 0; c < D::mL; ++c) vx = fma(T->dL_M[b][c], s.tx[c * D::mm + a], vx);
+      for (int c = 0; c < D::mL; ++c) vx = fma(T.dL_M[b][c], SM(O::TX, c * D::mm + a), vx);
       dB = -fma(ax, vy, -ay * vx);
     }
     size_t gi = comp * Z + (size_t)k * D::NZ + r;
@@ -723,39 +735,36 @@ __global__ void __launch_bounds__(256) k_mag_B(
 
 // ---- launchers ------------------------------------------------------------------
 template <int P, int KM>
-static void set_smem(const void* f, size_t bytes) {
-  cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-template <int P, int KM>
 void mag_stage_impl(int mode, const double* B, const double* u, const double* e, const double* rho,
                     const double* eta, int resistive, const double* B0, const double* u0, const double* e0,
-                    double* Bo, double* uo, double* eo, double* LJ, double* LE, const Tab* T, const Mesh& M,
-                    const double* dtp, double dtfac, double ca, double cb, int first, cudaStream_t st) {
+                    double* Bo, double* uo, double* eo, double* LJ, double* LE, const Mesh& M, const double* dtp,
+                    double dtfac, double ca, double cb, int first, cudaStream_t st) {
   using D = MD<P, KM>;
   const size_t Z = (size_t)M.K * D::NZ;
   double* LJx = LJ; double* LJy = LJ + (size_t)M.K * D::NX; double* LJz = LJy + (size_t)M.K * D::NY;
   double* LEx = LE; double* LEy = LE + (size_t)M.K * D::NX; double* LEz = LEy + (size_t)M.K * D::NY;
   unsigned blocks = (unsigned)((M.K + D::EB - 1) / D::EB);
-  size_t sj = sizeof(SJ<P, KM>) * D::EB, se = sizeof(SE<P, KM>) * D::EB, sb = sizeof(SB<P, KM>) * D::EB;
+  const size_t sj = sizeof(double) * LJ_<P, KM>::SIZE * D::EB;
+  const size_t se = sizeof(double) * LE_<P, KM>::SIZE * D::EB;
+  const size_t sb = sizeof(double) * LB_<P, KM>::SIZE * D::EB;
   static bool init = false;
   if (!init) {
-    set_smem<P, KM>((const void*)k_mag_J<P, KM>, sj);
-    set_smem<P, KM>((const void*)k_mag_E<P, KM, 0>, se);
-    set_smem<P, KM>((const void*)k_mag_E<P, KM, 1>, se);
-    set_smem<P, KM>((const void*)k_mag_B<P, KM, 0>, sb);
-    set_smem<P, KM>((const void*)k_mag_B<P, KM, 1>, sb);
+    cudaFuncSetAttribute((const void*)k_mag_J<P, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sj);
+    cudaFuncSetAttribute((const void*)k_mag_E<P, KM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se);
+    cudaFuncSetAttribute((const void*)k_mag_E<P, KM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se);
+    cudaFuncSetAttribute((const void*)k_mag_B<P, KM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+    cudaFuncSetAttribute((const void*)k_mag_B<P, KM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
     init = true;
   }
-  k_mag_J<P, KM><<<blocks, D::TH, sj, st>>>(B, B + Z, B + 2 * Z, LJx, LJy, LJz, T, M);
+  k_mag_J<P, KM><<<blocks, D::TH, sj, st>>>(B, B + Z, B + 2 * Z, LJx, LJy, LJz, M);
   if (mode == 0) {
     k_mag_E<P, KM, 0><<<blocks, D::TH, se, st>>>(LJx, LJy, LJz, B, B + Z, B + 2 * Z, u, e, rho, eta, u0, e0, uo, eo,
-                                                  LEx, LEy, LEz, T, M, dtp, dtfac, ca, cb, first, resistive);
-    k_mag_B<P, KM, 0><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, T, M, dtp, dtfac, ca, cb, first);
+                                                  LEx, LEy, LEz, M, dtp, dtfac, ca, cb, first, resistive);
+    k_mag_B<P, KM, 0><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, M, dtp, dtfac, ca, cb, first);
   } else {
     k_mag_E<P, KM, 1><<<blocks, D::TH, se, st>>>(LJx, LJy, LJz, B, B + Z, B + 2 * Z, u, e, rho, eta, u0, e0, uo, eo,
-                                                  LEx, LEy, LEz, T, M, dtp, dtfac, ca, cb, first, resistive);
-    k_mag_B<P, KM, 1><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, T, M, dtp, dtfac, ca, cb, first);
+                                                  LEx, LEy, LEz, M, dtp, dtfac, ca, cb, first, resistive);
+    k_mag_B<P, KM, 1><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, M, dtp, dtfac, ca, cb, first);
   }
 }
 
@@ -769,8 +778,9 @@ void mag_stage(int p, int k, int mode, const double* B, const double* u, const d
                const double* eta, int resistive, const double* B0, const double* u0, const double* e0, double* Bo,
                double* uo, double* eo, double* LJ, double* LE, const Tab* T, const Mesh& M, const double* dtp,
                double dtfac, double ca, double cb, int first, cudaStream_t st) {
-#define MHD_MAG_CASE(PP, KK)                                                                                     \
-  mag_stage_impl<PP, KK>(mode, B, u, e, rho, eta, resistive, B0, u0, e0, Bo, uo, eo, LJ, LE, T, M, dtp, dtfac, ca, \
+  (void)T;  // the magnetic kernels read the constant-memory copy of the tables
+#define MHD_MAG_CASE(PP, KK)                                                                                  \
+  mag_stage_impl<PP, KK>(mode, B, u, e, rho, eta, resistive, B0, u0, e0, Bo, uo, eo, LJ, LE, M, dtp, dtfac, ca, \
                          cb, first, st)
   MHD_DISPATCH_PK(p, k, MHD_MAG_CASE);
 #undef MHD_MAG_CASE

@@ -215,12 +215,65 @@ __device__ __forceinline__ double sigma_rI(const StatsView& V, int nc, int n, in
   return s;
 }
 
-// ---- k_oe_pp: hydro OE map then the positivity limiter, one element per n2 threads ----
+// ---- k_oe_pp: hydro OE map then the positivity limiter ----------------------------
+// Each element owns a segment of SW lanes (SW = smallest power of two >= (p+1)^2,
+// a divisor of 32), so per-element minima, maxima and sums are shuffle trees and
+// every lane of the segment carries its node's share of the limiter; the
+// scalar per-element quantities are evaluated by all lanes of the segment.
 template <int P>
 struct OCfg {
-  static constexpr int n = P + 1, n2 = n * n, EB = P == 1 ? 32 : (P == 2 ? 32 : (P == 3 ? 8 : 5));
-  static constexpr int threads = EB * n2;
+  static constexpr int n = P + 1, n2 = n * n;
+  static constexpr int SW = n2 <= 4 ? 4 : (n2 <= 16 ? 16 : 32);
+  static constexpr int EB = 128 / SW;
+  static constexpr int threads = EB * SW;
 };
+
+template <int SW>
+__device__ __forceinline__ double seg_min(double v) {
+#pragma unroll
+  for (int o = SW / 2; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+template <int SW>
+__device__ __forceinline__ double seg_max(double v) {
+#pragma unroll
+  for (int o = SW / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+template <int SW>
+__device__ __forceinline__ double seg_sum(double v) {
+#pragma unroll
+  for (int o = SW / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Per-element OE damping factors D_l (eq. euler-oe-factor / magnetic-oe-factor):
+// lanes q < 2n evaluate sigma_{r,I} (I = q / n, r = q % n); lanes q < n sum
+// Theta_l and take the exponential.  lam[I] must be valid in every lane.
+template <int P>
+__device__ __forceinline__ void oe_factors(const StatsView& V, int nc, int q, int el, int kk, int ex, int ey,
+                                           const double lam[2], double s_tau, const Mesh& M,
+                                           double (*ssig)[2 * (P + 1)], double (*sD)[P + 1]) {
+  constexpr int n = P + 1;
+  if (q < 2 * n) {
+    const int I = q / n, r = q % n;
+    const double h = I == 0 ? M.hx : M.hy;
+    const double Delta = shared_amp(V, nc, I, ex, ey, M);
+    const int kB = I == 0 ? ey * M.nx + wrap(ex + 1, M.nx) : wrap(ey + 1, M.ny) * M.nx + ex;
+    ssig[el][q] = sigma_rI(V, nc, n, I, r, kk, kB, Delta, h, M);
+  }
+  __syncthreads();
+  if (q < n) {
+    double Theta = 0.0;
+    for (int I = 0; I < 2; ++I) {
+      double ss = 0.0;
+      for (int r = 0; r <= q; ++r) ss += ssig[el][I * n + r];
+      Theta = fma(lam[I], ss, Theta);
+    }
+    sD[el][q] = q == 0 ? 1.0 : exp(-s_tau * Theta);
+  }
+  __syncthreads();
+}
 
 template <int P>
 __global__ void __launch_bounds__(OCfg<P>::threads) k_oe_pp(double* __restrict__ S, StatsView V,
@@ -228,137 +281,133 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_oe_pp(double* __restrict__
                                                             const double* __restrict__ dtp, double dtfac,
                                                             unsigned* __restrict__ status) {
   using C = OCfg<P>;
-  constexpr int n = C::n, n2 = C::n2, EB = C::EB;
-  __shared__ double su[5][EB * n2];
-  __shared__ double st[5][EB * n2];
+  constexpr int n = C::n, n2 = C::n2, EB = C::EB, SW = C::SW;
+  __shared__ double su[5][EB * SW];
+  __shared__ double st[5][EB * SW];
+  __shared__ double ssig[EB][2 * n];
   __shared__ double sD[EB][n];
-  __shared__ double sa[EB][6];
-  __shared__ double sth[EB][2];
   const size_t N = (size_t)M.K * n2, K = M.K;
-  const int tid = threadIdx.x, el = tid / n2, q = tid % n2;
+  const int tid = threadIdx.x, el = tid / SW, q = tid % SW;
+  const bool node = q < n2;
   const int k = blockIdx.x * EB + el;
-  const bool valid = k < M.K;
-  const int kk = valid ? k : M.K - 1;
+  const bool valid = k < M.K && node;
+  const int kk = k < M.K ? k : M.K - 1;
   const int ex = kk % M.nx, ey = kk / M.nx;
-  const int i = q % n, j = q / n;
+  const int qq = node ? q : 0;
+  const int i = qq % n, j = qq / n;
   const double g = M.g;
-  for (int c = 0; c < 5; ++c) su[c][tid] = S[c * N + (size_t)kk * n2 + q];
+  double u[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) u[c] = node ? S[c * N + (size_t)kk * n2 + q] : 0.0;
 
   if (prm.oe_hydro) {
-    // damping factors D_l (one thread per l); sigma from the face jump measures
-    if (q <= P) {
-      const int l = q;
-      double Theta = 0.0;
+    double lam[2];
+    {
       const double a0 = V.avg[kk], a1 = V.avg[K + kk], a2 = V.avg[2 * K + kk], a3 = V.avg[3 * K + kk],
                    a4 = V.avg[4 * K + kk];
-      const double ir = 1.0 / a0;
-      const double pb = (g - 1.0) * (a4 - 0.5 * (a1 * a1 + a2 * a2 + a3 * a3) * ir);
+      const double ir = rcp(a0);
+      const double pb = (g - 1.0) * fma(-0.5 * ir, fma(a1, a1, fma(a2, a2, a3 * a3)), a4);
       const double cb = sqrt(g * pb * ir);
-      for (int I = 0; I < 2; ++I) {
-        const double h = I == 0 ? M.hx : M.hy;
-        const double lam = (2.0 * P + 1.0) * (fabs((I == 0 ? a1 : a2) * ir) + cb) / h;
-        const double Delta = shared_amp(V, 5, I, ex, ey, M);
-        const int kB = I == 0 ? ey * M.nx + wrap(ex + 1, M.nx) : wrap(ey + 1, M.ny) * M.nx + ex;
-        double ss = 0.0;
-        for (int r = 0; r <= l; ++r) ss += sigma_rI(V, 5, n, I, r, kk, kB, Delta, h, M);
-        Theta += lam * ss;
+      lam[0] = (2.0 * P + 1.0) * (fabs(a1 * ir) + cb) / M.hx;
+      lam[1] = (2.0 * P + 1.0) * (fabs(a2 * ir) + cb) / M.hy;
+    }
+    oe_factors<P>(V, 5, q, el, kk, ex, ey, lam, prm.s_H * dtp[0] * dtfac, M, ssig, sD);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) su[c][tid] = u[c];
+    __syncthreads();
+    if (node) {  // T[b][i] = sum_j w_j P_b(x_j) U[j][i]   (b = j of this lane)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        double v = 0.0;
+#pragma unroll
+        for (int jj = 0; jj < n; ++jj) v = fma(T->wp[jj] * T->Leg[jj][j], su[c][el * SW + jj * n + i], v);
+        st[c][tid] = v;
       }
-      sD[el][l] = l == 0 ? 1.0 : exp(-prm.s_H * dtp[0] * dtfac * Theta);
     }
     __syncthreads();
-    // modal transform: forward y then x, damp, inverse x then y (5 comps x n2 items per element)
-    for (int c = 0; c < 5; ++c) {  // T[b][i] = sum_j w_j P_b(x_j) U[j][i]
-      const int b = j;
-      double v = 0.0;
+    if (node) {  // coef[b][a] = N_a N_b sum_i w_i P_a(x_i) T[b][i], damped by D_max(a,b)   (a = i, b = j)
+      const double f = T->LegN[i] * T->LegN[j] * sD[el][i > j ? i : j];
 #pragma unroll
-      for (int jj = 0; jj < n; ++jj) v = fma(T->wp[jj] * T->Leg[jj][b], su[c][el * n2 + jj * n + i], v);
-      st[c][tid] = v;
-    }
-    __syncthreads();
-    for (int c = 0; c < 5; ++c) {  // coef[b][a] = N_a N_b sum_i w_i P_a(x_i) T[b][i], damped by D_max(a,b)
-      const int b = j, a = i;
-      double v = 0.0;
+      for (int c = 0; c < 5; ++c) {
+        double v = 0.0;
 #pragma unroll
-      for (int ii = 0; ii < n; ++ii) v = fma(T->wp[ii] * T->Leg[ii][a], st[c][el * n2 + b * n + ii], v);
-      su[c][tid] = v * T->LegN[a] * T->LegN[b] * sD[el][a > b ? a : b];
+        for (int ii = 0; ii < n; ++ii) v = fma(T->wp[ii] * T->Leg[ii][i], st[c][el * SW + j * n + ii], v);
+        su[c][tid] = v * f;
+      }
     }
     __syncthreads();
-    for (int c = 0; c < 5; ++c) {  // V[b][i] = sum_a P_a(x_i) coef[b][a]
-      double v = 0.0;
+    if (node) {  // V[b][i] = sum_a P_a(x_i) coef[b][a]
 #pragma unroll
-      for (int a = 0; a < n; ++a) v = fma(T->Leg[i][a], su[c][el * n2 + j * n + a], v);
-      st[c][tid] = v;
-    }
-    __syncthreads();
-    for (int c = 0; c < 5; ++c) {  // U[j][i] = sum_b P_b(x_j) V[b][i]
-      double v = 0.0;
+      for (int c = 0; c < 5; ++c) {
+        double v = 0.0;
 #pragma unroll
-      for (int b = 0; b < n; ++b) v = fma(T->Leg[j][b], st[c][el * n2 + b * n + i], v);
-      su[c][tid] = v;
+        for (int a = 0; a < n; ++a) v = fma(T->Leg[i][a], su[c][el * SW + j * n + a], v);
+        st[c][tid] = v;
+      }
     }
     __syncthreads();
+    if (node) {  // U[j][i] = sum_b P_b(x_j) V[b][i]
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        double v = 0.0;
+#pragma unroll
+        for (int b = 0; b < n; ++b) v = fma(T->Leg[j][b], st[c][el * SW + b * n + i], v);
+        u[c] = v;
+      }
+    }
   }
 
   if (prm.pp) {
+    // Every shuffle below runs in all lanes (no per-element branch around it);
+    // the element decisions are taken afterwards from segment-uniform values.
     const double eps = DBL_EPSILON, eps_rho = 64.0 * eps;
-    __syncthreads();
-    if (q < 5) {  // average of U* (eq. euler-pp-average)
-      double s = 0.0;
-      for (int t2 = 0; t2 < n2; ++t2) s = fma(0.25 * T->wp[t2 % n] * T->wp[t2 / n], su[q][el * n2 + t2], s);
-      sa[el][q] = s;
+    const double wq = node ? 0.25 * T->wp[i] * T->wp[j] : 0.0;
+    const int lead = (threadIdx.x & 31) & ~(SW - 1);
+    double a[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c)  // average of U* (eq. euler-pp-average), identical in every lane of the segment
+      a[c] = __shfl_sync(0xffffffffu, seg_sum<SW>(wq * u[c]), lead);
+    const double rbar = a[0];
+    const double pbar = (g - 1.0) * (a[4] - (a[1] * a[1] + a[2] * a[2] + a[3] * a[3]) / (2.0 * a[0]));
+    const bool bad = !(rbar > 0.0) || !(pbar > 0.0) || !isfinite(rbar) || !isfinite(pbar);
+    // density scaling (eq. euler-pp-density)
+    const double rmin = seg_min<SW>(node ? u[0] : DBL_MAX);
+    double th_r = 1.0;
+    if (rmin < eps_rho) {
+      const double den = rbar - rmin;
+      th_r = den > 0.0 ? fmin(1.0, fmax(0.0, (rbar - eps_rho) / den)) : 1.0;
     }
-    __syncthreads();
-    if (q == 0) {
-      double a[5] = {sa[el][0], sa[el][1], sa[el][2], sa[el][3], sa[el][4]};
-      double rbar = a[0];
-      double pbar = (g - 1.0) * (a[4] - (a[1] * a[1] + a[2] * a[2] + a[3] * a[3]) / (2.0 * a[0]));
-      double th_r = 1.0, th_p = 1.0, collapse = 0.0;
-      if (!(rbar > 0.0) || !(pbar > 0.0) || !isfinite(rbar) || !isfinite(pbar)) {
-        if (valid) atomicOr(status, ST_INADMISSIBLE);
-      } else if (rbar <= eps_rho) {
-        collapse = 1.0;
-      } else {
-        double rmin = DBL_MAX;
-        for (int t2 = 0; t2 < n2; ++t2) rmin = fmin(rmin, su[0][el * n2 + t2]);
-        if (rmin < eps_rho) {
-          double den = rbar - rmin;
-          th_r = den > 0.0 ? fmin(1.0, fmax(0.0, (rbar - eps_rho) / den)) : 1.0;
-        }
-        auto Sp = [&](double r_, double m1, double m2, double m3, double E) {
-          return fabs(E) + (m1 * m1 + m2 * m2 + m3 * m3) / (2.0 * fmax(r_, eps_rho));
-        };
-        double Smax = Sp(a[0], a[1], a[2], a[3], a[4]);
-        double pmin = DBL_MAX;
-        for (int t2 = 0; t2 < n2; ++t2) {
-          double r_ = su[0][el * n2 + t2];
-          if (th_r < 1.0) r_ = rbar + th_r * (r_ - rbar);
-          double m1 = su[1][el * n2 + t2], m2 = su[2][el * n2 + t2], m3 = su[3][el * n2 + t2], E = su[4][el * n2 + t2];
-          Smax = fmax(Smax, Sp(r_, m1, m2, m3, E));
-          pmin = fmin(pmin, (g - 1.0) * (E - (m1 * m1 + m2 * m2 + m3 * m3) / (2.0 * r_)));
-        }
-        double eps_p = fmax(64.0 * eps, 8192.0 * eps * Smax);
-        if (pbar <= eps_p) collapse = 1.0;
-        else if (pmin < eps_p) {
-          double den = pbar - pmin;
-          th_p = den > 0.0 ? fmin(1.0, fmax(0.0, (pbar - eps_p) / den)) : 1.0;
+    double r0 = u[0];
+    if (th_r < 1.0) r0 = rbar + th_r * (u[0] - rbar);
+    // pressure-cancellation scale and floor (eq. euler-pp-floors), pressure scaling (eq. euler-pp-pressure)
+    const double m2 = fma(u[1], u[1], fma(u[2], u[2], u[3] * u[3]));
+    const double Sq = node ? fabs(u[4]) + m2 / (2.0 * fmax(r0, eps_rho)) : 0.0;
+    const double pq = node ? (g - 1.0) * (u[4] - m2 / (2.0 * r0)) : DBL_MAX;
+    const double Sa = fabs(a[4]) + (a[1] * a[1] + a[2] * a[2] + a[3] * a[3]) / (2.0 * fmax(a[0], eps_rho));
+    const double Smax = fmax(Sa, seg_max<SW>(Sq));
+    const double pmin = seg_min<SW>(pq);
+    const double eps_p = fmax(64.0 * eps, 8192.0 * eps * Smax);
+    if (bad) {
+      if (q == 0 && k < M.K) atomicOr(status, ST_INADMISSIBLE);
+    } else if (rbar <= eps_rho || pbar <= eps_p) {  // vacuum-like average: collapse (reading R9)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) u[c] = a[c];
+    } else {
+      u[0] = r0;
+      if (pmin < eps_p) {
+        const double den = pbar - pmin;
+        const double th_p = den > 0.0 ? fmin(1.0, fmax(0.0, (pbar - eps_p) / den)) : 1.0;
+        if (th_p < 1.0) {
+#pragma unroll
+          for (int c = 0; c < 5; ++c) u[c] = a[c] + th_p * (u[c] - a[c]);
         }
       }
-      sth[el][0] = collapse ? -1.0 : th_r;
-      sth[el][1] = th_p;
-      for (int c = 0; c < 5; ++c) sa[el][c] = a[c];
-    }
-    __syncthreads();
-    double th_r = sth[el][0], th_p = sth[el][1];
-    if (th_r < 0.0) {
-      for (int c = 0; c < 5; ++c) su[c][tid] = sa[el][c];
-    } else {
-      if (th_r < 1.0) su[0][tid] = sa[el][0] + th_r * (su[0][tid] - sa[el][0]);
-      if (th_p < 1.0)
-        for (int c = 0; c < 5; ++c) su[c][tid] = sa[el][c] + th_p * (su[c][tid] - sa[el][c]);
     }
   }
-  if (valid)
-    for (int c = 0; c < 5; ++c) S[c * N + (size_t)k * n2 + q] = su[c][tid];
+  if (valid) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) S[c * N + (size_t)k * n2 + q] = u[c];
+  }
 }
 
 // ---- launchers: hydro stage map -----------------------------------------------------
@@ -649,7 +698,7 @@ void stab_vel_prep(int p, const double* rho, double* chol, const Tab* T, const M
   }
 }
 
-// Velocity OE map with heating of e, one element per n2 threads.
+// Velocity OE map with heating of e; one element per segment of SW lanes.
 template <int P, int KM>
 __global__ void __launch_bounds__(OCfg<P>::threads) k_vel_oe(const double* __restrict__ rho, double* __restrict__ Y,
                                                              const double* __restrict__ B,
@@ -657,83 +706,70 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_vel_oe(const double* __res
                                                              const Tab* __restrict__ T, Mesh M, Stab prm,
                                                              const double* __restrict__ dtp, double dtfac) {
   using C = OCfg<P>;
-  constexpr int n = C::n, n2 = C::n2, EB = C::EB;
-  __shared__ double su[3][EB * n2];
-  __shared__ double sc[3][EB * n2];
+  constexpr int n = C::n, n2 = C::n2, EB = C::EB, SW = C::SW;
+  __shared__ double sPsi[EB][n2 * n2];
+  __shared__ double sWu[3][EB * SW];
+  __shared__ double sc[3][EB * SW];
+  __shared__ double ssig[EB][2 * n];
   __shared__ double sD[EB][n];
-  __shared__ double sv[EB * n2][2];
   const size_t N = (size_t)M.K * n2, Z = (size_t)M.K * (KM + 1) * (KM + 1);
-  const int tid = threadIdx.x, el = tid / n2, q = tid % n2;
+  const int tid = threadIdx.x, el = tid / SW, q = tid % SW;
+  const bool node = q < n2;
   const int k = blockIdx.x * EB + el;
-  const bool valid = k < M.K;
-  const int kk = valid ? k : M.K - 1;
+  const bool valid = k < M.K && node;
+  const int kk = k < M.K ? k : M.K - 1;
   const int ex = kk % M.nx, ey = kk / M.nx;
-  const int i = q % n, j = q / n;
-  const double r_ = rho[(size_t)kk * n2 + q];
-  for (int d = 0; d < 3; ++d) su[d][tid] = Y[(1 + d) * N + (size_t)kk * n2 + q];
-  {  // |u_I| + |B_h|/sqrt(rho) at this node
+  const int qq = node ? q : 0;
+  const int i = qq % n, j = qq / n;
+  double u[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) u[d] = node ? Y[(1 + d) * N + (size_t)kk * n2 + q] : 0.0;
+  const double r_ = node ? rho[(size_t)kk * n2 + q] : 1.0;
+  for (int t = q; t < n2 * n2; t += SW) sPsi[el][t] = Psi[(size_t)kk * n2 * n2 + t];
+  // rate lambda_M from the nodal max of |u_I| + |B_h| / sqrt(rho) (eq. magnetic-oe-rate)
+  double lam[2];
+  {
     double Bv[3];
+#pragma unroll
     for (int d = 0; d < 3; ++d)
       Bv[d] = B_eval<KM>(B, Z, d, ex, ey, T->L_P[i], T->G_P[i], T->M_P[i], T->L_P[j], T->G_P[j], T->M_P[j], M);
-    double va = sqrt(Bv[0] * Bv[0] + Bv[1] * Bv[1] + Bv[2] * Bv[2]) / sqrt(r_);
-    sv[tid][0] = fabs(su[0][tid]) + va;
-    sv[tid][1] = fabs(su[1][tid]) + va;
+    const double va = sqrt(fma(Bv[0], Bv[0], fma(Bv[1], Bv[1], Bv[2] * Bv[2])) * rcp(r_));
+    const double ax = seg_max<SW>(node ? fabs(u[0]) + va : 0.0);
+    const double ay = seg_max<SW>(node ? fabs(u[1]) + va : 0.0);
+    lam[0] = (2.0 * P + 1.0) / M.hx * ax;
+    lam[1] = (2.0 * P + 1.0) / M.hy * ay;
   }
-  __syncthreads();
-  if (q <= P) {
-    const int l = q;
-    double Theta = 0.0;
-    for (int I = 0; I < 2; ++I) {
-      double amax = 0.0;
-      for (int t2 = 0; t2 < n2; ++t2) amax = fmax(amax, sv[el * n2 + t2][I]);
-      const double h = I == 0 ? M.hx : M.hy;
-      const double lam = (2.0 * P + 1.0) / h * amax;
-      const double Delta = shared_amp(V, 3, I, ex, ey, M);
-      const int kB = I == 0 ? ey * M.nx + wrap(ex + 1, M.nx) : wrap(ey + 1, M.ny) * M.nx + ex;
-      double ss = 0.0;
-      for (int r = 0; r <= l; ++r) ss += sigma_rI(V, 3, n, I, r, kk, kB, Delta, h, M);
-      Theta += lam * ss;
-    }
-    sD[el][l] = l == 0 ? 1.0 : exp(-prm.s_M * dtp[0] * dtfac * Theta);
-  }
-  // coefficients c_alpha = sum_q Psi[q][alpha] M_q rho_q u_q (thread q plays alpha)
-  const double* Ps = Psi + (size_t)kk * n2 * n2;
-  {
-    const int al = q;
+  const double W = node ? M.Jdet * T->wp[i] * T->wp[j] * r_ : 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) sWu[d][tid] = W * u[d];
+  oe_factors<P>(V, 3, q, el, kk, ex, ey, lam, prm.s_M * dtp[0] * dtfac, M, ssig, sD);  // syncs
+  // coefficients c_alpha = sum_t Psi[t][alpha] W_t u_t (lane q plays alpha)
+  if (node) {
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
       double s = 0.0;
-      for (int t2 = 0; t2 < n2; ++t2) {
-        double W = M.Jdet * T->wp[t2 % n] * T->wp[t2 / n] * rho[(size_t)kk * n2 + t2];
-        s = fma(Ps[t2 * n2 + al] * W, su[d][el * n2 + t2], s);
-      }
+#pragma unroll
+      for (int t = 0; t < n2; ++t) s = fma(sPsi[el][t * n2 + q], sWu[d][el * SW + t], s);
       sc[d][tid] = s;
     }
   }
   __syncthreads();
-  // shell values w_l at this node, damped velocity and heating
-  int shell[n2];
-  {
-    int t = 0;
-    for (int l = 0; l <= P; ++l)
-      for (int b = 0; b <= l; ++b)
-        for (int a = 0; a <= l; ++a)
-          if ((a > b ? a : b) == l) shell[t++] = l;
-  }
-  double de = 0.0, unew[3];
-  for (int d = 0; d < 3; ++d) {
-    double wl[n];
-    for (int l = 0; l < n; ++l) wl[l] = 0.0;
-    for (int al = 0; al < n2; ++al) wl[shell[al]] = fma(sc[d][el * n2 + al], Ps[q * n2 + al], wl[shell[al]]);
-    double s = wl[0];
-    for (int l = 1; l <= P; ++l) {
-      double Dl = sD[el][l];
-      s = fma(Dl, wl[l], s);
-      de = fma(0.5 * (1.0 - Dl * Dl) * wl[l], wl[l], de);
-    }
-    unew[d] = s;
-  }
   if (valid) {
-    for (int d = 0; d < 3; ++d) Y[(1 + d) * N + (size_t)k * n2 + q] = unew[d];
+    double de = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double unew = 0.0;
+#pragma unroll
+      for (int l = 0; l <= P; ++l) {  // shell l holds basis indices [l^2, (l+1)^2)
+        double wl = 0.0;
+#pragma unroll
+        for (int al = l * l; al < (l + 1) * (l + 1); ++al) wl = fma(sc[d][el * SW + al], sPsi[el][q * n2 + al], wl);
+        const double Dl = sD[el][l];
+        unew = fma(Dl, wl, unew);
+        if (l > 0) de = fma(0.5 * (1.0 - Dl * Dl) * wl, wl, de);
+      }
+      Y[(1 + d) * N + (size_t)k * n2 + q] = unew;
+    }
     Y[(size_t)k * n2 + q] += de;
   }
 }

@@ -243,6 +243,7 @@ int table_slot(int p, int k) {
 }
 
 __device__ Tab g_tables[8];
+void upload_mag_tables(int slot, const Tab* h, cudaError_t* err);  // constant-memory copy (magnetic.cu)
 
 const Tab* device_tables(int p, int k, cudaError_t* err) {
   static std::mutex mu;
@@ -258,6 +259,8 @@ const Tab* device_tables(int p, int k, cudaError_t* err) {
     Tab h;
     host_tables(p, k, &h);
     if ((*err = cudaMemcpyToSymbol(g_tables, &h, sizeof(Tab), slot * sizeof(Tab))) != cudaSuccess) return nullptr;
+    upload_mag_tables(slot, &h, err);
+    if (*err != cudaSuccess) return nullptr;
     filled[dev][slot] = true;
   }
   void* base = nullptr;
