@@ -32,6 +32,7 @@ struct StatsView {
   double* glob;  // [nc][4]: mean, amplitude Delta_Omega, L-inf norm, roundoff-constant flag
   double* ar;    // [K][8] A.R. per-element partials
   double* arg;   // [8] A.R. global values
+  double* part;  // [ceil(K/256)][9] A.R. chunk partials
 };
 
 static StatsView stats_view(double* work, int p, const Mesh& M) {
@@ -47,13 +48,14 @@ static StatsView stats_view(double* work, int p, const Mesh& M) {
   v.glob = v.line + 2 * L * NC * 3;
   v.ar = v.glob + NC * 4;
   v.arg = v.ar + 8 * K;
+  v.part = v.arg + 8;
   return v;
 }
 
 size_t stab_work_doubles(int p, int k, const Mesh& M) {
   (void)k;
   const size_t K = M.K, n = p + 1, L = M.nx > M.ny ? M.nx : M.ny;
-  return 3 * 5 * K + 2 * 5 * n * K + 2 * L * 5 * 3 + 5 * 4 + 8 * K + 8 + 64;
+  return 3 * 5 * K + 2 * 5 * n * K + 2 * L * 5 * 3 + 5 * 4 + 8 * K + 8 + 9 * (K / 256 + 1) + 64;
 }
 
 size_t stab_chol_doubles(int p, const Mesh& M) {
@@ -188,9 +190,10 @@ __device__ __forceinline__ double shared_amp(const StatsView& V, int nc, int I, 
   const int Lmax = M.nx > M.ny ? M.nx : M.ny;
   const int L = I == 0 ? ey : ex, len = I == 0 ? M.nx : M.ny;
   double D = 0.0;
+  const double ilen = 1.0 / len;
   for (int c = 0; c < nc; ++c) {
     const double* o = V.line + (((size_t)I * Lmax + L) * nc + c) * 3;
-    double mean = o[0] / len;
+    double mean = o[0] * ilen;
     double amp = fmax(o[1] - mean, mean - o[2]);
     D = fmax(D, fmax(amp, 1e-6 * V.glob[c * 4 + 1]));
   }
@@ -210,9 +213,9 @@ __device__ __forceinline__ double sigma_rI(const StatsView& V, int nc, int n, in
   for (int c = 0; c < nc; ++c) {
     if (V.glob[c * 4 + 3] != 0.0) continue;
     double Jr = J[((size_t)c * n + r) * K + k] + J[((size_t)c * n + r) * K + kB];
-    s = fmax(s, fac * Jr / Delta);
+    s = fmax(s, fac * Jr);
   }
-  return s;
+  return s / Delta;
 }
 
 // ---- k_oe_pp: hydro OE map then the positivity limiter ----------------------------
@@ -564,26 +567,41 @@ __global__ void k_ar_elem(const double* __restrict__ rho, const double* __restri
   for (int c = 0; c < 16; ++c) ar[(size_t)k * 16 + c] = out[c];
 }
 
-// Global reduction of the A.R. partials (one block, fixed order).
-__global__ void k_ar_global(const double* __restrict__ ar, Mesh M, double* __restrict__ g) {
-  __shared__ double sm[256][9];
-  double acc[9] = {0, 0, 0, -DBL_MAX, -DBL_MAX, -DBL_MAX, DBL_MAX, DBL_MAX, DBL_MAX};
-  for (int k = threadIdx.x; k < M.K; k += blockDim.x) {
-    const double* a = ar + (size_t)k * 16;
-    for (int c = 0; c < 3; ++c) acc[c] += a[c];
-    for (int c = 3; c < 6; ++c) acc[c] = fmax(acc[c], a[c]);
-    for (int c = 6; c < 9; ++c) acc[c] = fmin(acc[c], a[c]);
-  }
+// Global reduction of the A.R. partials in two fixed-order levels: k_ar_part
+// reduces 256-element chunks (one block each), k_ar_global the chunk results.
+__device__ __forceinline__ void ar_combine(double* x, const double* y) {
+  for (int c = 0; c < 3; ++c) x[c] += y[c];
+  for (int c = 3; c < 6; ++c) x[c] = fmax(x[c], y[c]);
+  for (int c = 6; c < 9; ++c) x[c] = fmin(x[c], y[c]);
+}
+
+__device__ void ar_block_reduce(double acc[9], double (*sm)[9]) {
   for (int c = 0; c < 9; ++c) sm[threadIdx.x][c] = acc[c];
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o)
-      for (int c = 0; c < 9; ++c) {
-        double x = sm[threadIdx.x][c], y = sm[threadIdx.x + o][c];
-        sm[threadIdx.x][c] = c < 3 ? x + y : (c < 6 ? fmax(x, y) : fmin(x, y));
-      }
+    if (threadIdx.x < o) ar_combine(sm[threadIdx.x], sm[threadIdx.x + o]);
     __syncthreads();
   }
+}
+
+__global__ void k_ar_part(const double* __restrict__ ar, Mesh M, double* __restrict__ part) {
+  __shared__ double sm[256][9];
+  double acc[9] = {0, 0, 0, -DBL_MAX, -DBL_MAX, -DBL_MAX, DBL_MAX, DBL_MAX, DBL_MAX};
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < M.K) {
+    const double* a = ar + (size_t)k * 16;
+    for (int c = 0; c < 9; ++c) acc[c] = a[c];
+  }
+  ar_block_reduce(acc, sm);
+  if (threadIdx.x == 0)
+    for (int c = 0; c < 9; ++c) part[(size_t)blockIdx.x * 9 + c] = sm[0][c];
+}
+
+__global__ void k_ar_global(const double* __restrict__ part, int nparts, Mesh M, double* __restrict__ g) {
+  __shared__ double sm[256][9];
+  double acc[9] = {0, 0, 0, -DBL_MAX, -DBL_MAX, -DBL_MAX, DBL_MAX, DBL_MAX, DBL_MAX};
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) ar_combine(acc, part + (size_t)b * 9);
+  ar_block_reduce(acc, sm);
   if (threadIdx.x == 0) {
     double area = M.K * 4.0 * M.Jdet;
     double amp[3], linf[3];
@@ -634,67 +652,133 @@ void stab_eta(int p, int k, const double* rho, const double* Y, const double* B,
 #define MHD_AR_CASE(PP, KK) k_ar_elem<PP, KK><<<bl, 128, 0, st>>>(rho, Y, B, T, M, ar)
   MHD_DISPATCH_PK(p, k, MHD_AR_CASE);
 #undef MHD_AR_CASE
-  k_ar_global<<<1, 256, 0, st>>>(ar, M, g);
+  const int nparts = (M.K + 255) / 256;
+  double* part = V.part;
+  k_ar_part<<<nparts, 256, 0, st>>>(ar, M, part);
+  k_ar_global<<<1, 256, 0, st>>>(part, nparts, M, g);
   k_ar_eta<<<bl, 128, 0, st>>>(ar, g, M, prm, p, eta);
 }
 
 // ============================ velocity OE ==========================================
-// Psi = Phi L^{-T} per element (n2 x n2, row q = node, column alpha = basis in shell order).
+// Psi = Phi L^{-T} per element (n2 x n2, row q = node, column alpha = basis in
+// shell order), G = Phi^T W Phi = L L^T.  One thread per element (32 elements per
+// block); the Gram matrix is sum-factorised,
+//   G[(a,b),(a',b')] = sum_j P_b(x_j) P_b'(x_j) H_j[a][a'],
+//   H_j[a][a'] = sum_i W_ij P_a(x_i) P_a'(x_i),
+// and L is kept in shared memory laid out element-innermost.
 template <int P>
-__global__ void k_vel_prep(const double* __restrict__ rho, double* __restrict__ Psi, const Tab* __restrict__ T, Mesh M) {
-  constexpr int n = P + 1, n2 = n * n;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= M.K) return;
-  // shell-ordered Legendre indices
+struct VPrep {
+  static constexpr int n = P + 1, n2 = n * n, NL = n2 * (n2 + 1) / 2, NA = n * (n + 1) / 2, NH = n * NA;
+  static constexpr int SIZE = NL + NH;
+};
+
+__device__ __forceinline__ int tri(int r, int c) { return r * (r + 1) / 2 + c; }  // c <= r
+
+template <int P>
+__global__ void __launch_bounds__(32) k_vel_prep(const double* __restrict__ rho, double* __restrict__ Psi,
+                                                 const Tab* __restrict__ T, Mesh M) {
+  using V = VPrep<P>;
+  constexpr int n = V::n, n2 = V::n2;
+  extern __shared__ double smp[];
+  const int lane = threadIdx.x;
+  const int k = blockIdx.x * 32 + lane;
+  const int kk = k < M.K ? k : M.K - 1;
+#define LS(idx) smp[(size_t)(idx) * 32 + lane]
+#define HS(idx) smp[(size_t)(V::NL + (idx)) * 32 + lane]
+  // shell-ordered Legendre index pairs (a, b) of the basis: shell l = max(a, b) holds [l^2, (l+1)^2)
   int ia[n2], ib[n2];
   {
     int t = 0;
+#pragma unroll
     for (int l = 0; l <= P; ++l)
+#pragma unroll
       for (int b = 0; b <= l; ++b)
+#pragma unroll
         for (int a = 0; a <= l; ++a)
           if ((a > b ? a : b) == l) { ia[t] = a; ib[t] = b; ++t; }
   }
-  double* out = Psi + (size_t)k * n2 * n2;
-  // Gram matrix G = Phi^T W Phi, W = diag(Jdet w_i w_j rho_q); Cholesky in place (lower)
-  double L[n2 * (n2 + 1) / 2];
-  auto li = [](int r, int c) { return r * (r + 1) / 2 + c; };
-  for (int al = 0; al < n2; ++al)
-    for (int be = 0; be <= al; ++be) {
-      double s = 0.0;
-      for (int q = 0; q < n2; ++q) {
-        int i = q % n, j = q / n;
-        double W = M.Jdet * T->wp[i] * T->wp[j] * rho[(size_t)k * n2 + q];
-        s = fma(W * T->Leg[i][ia[al]] * T->Leg[j][ib[al]], T->Leg[i][ia[be]] * T->Leg[j][ib[be]], s);
+  double W[n2];
+#pragma unroll
+  for (int q = 0; q < n2; ++q) W[q] = M.Jdet * T->wp[q % n] * T->wp[q / n] * rho[(size_t)kk * n2 + q];
+#pragma unroll
+  for (int j = 0; j < n; ++j)
+#pragma unroll
+    for (int a = 0; a < n; ++a)
+#pragma unroll
+      for (int a2 = 0; a2 <= a; ++a2) {
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < n; ++i) s = fma(W[j * n + i] * T->Leg[i][a], T->Leg[i][a2], s);
+        HS(j * V::NA + tri(a, a2)) = s;
       }
-      L[li(al, be)] = s;
+#pragma unroll
+  for (int al = 0; al < n2; ++al)
+#pragma unroll
+    for (int be = 0; be <= al; ++be) {
+      const int a = ia[al], b = ib[al], a2 = ia[be], b2 = ib[be];
+      const int pa = a >= a2 ? tri(a, a2) : tri(a2, a);
+      double s = 0.0;
+#pragma unroll
+      for (int j = 0; j < n; ++j) s = fma(T->Leg[j][b] * T->Leg[j][b2], HS(j * V::NA + pa), s);
+      LS(tri(al, be)) = s;
     }
+  // Cholesky G = L L^T in place (row by row)
+  double rdiag[n2];
+#pragma unroll
   for (int r = 0; r < n2; ++r) {
+#pragma unroll
     for (int c = 0; c <= r; ++c) {
-      double s = L[li(r, c)];
-      for (int t = 0; t < c; ++t) s -= L[li(r, t)] * L[li(c, t)];
-      L[li(r, c)] = (r == c) ? sqrt(s) : s / L[li(c, c)];
+      double s = LS(tri(r, c));
+#pragma unroll
+      for (int t = 0; t < c; ++t) s = fma(-LS(tri(r, t)), LS(tri(c, t)), s);
+      if (r == c) {
+        const double d = sqrt(s);
+        LS(tri(r, r)) = d;
+        rdiag[r] = rcp(d);
+      } else {
+        LS(tri(r, c)) = s * rdiag[c];
+      }
     }
   }
-  // Psi[q][al] = (Phi L^{-T})[q][al]: forward sweep over columns
+  // rows of Psi: psi_q L^T = phi_q (forward substitution)
+  double* out = Psi + (size_t)kk * n2 * n2;
+#pragma unroll 1
   for (int q = 0; q < n2; ++q) {
-    int i = q % n, j = q / n;
+    const int i = q % n, j = q / n;
     double row[n2];
+#pragma unroll
     for (int al = 0; al < n2; ++al) {
       double s = T->Leg[i][ia[al]] * T->Leg[j][ib[al]];
-      for (int b = 0; b < al; ++b) s -= row[b] * L[li(al, b)];
-      row[al] = s / L[li(al, al)];
+#pragma unroll
+      for (int b = 0; b < al; ++b) s = fma(-row[b], LS(tri(al, b)), s);
+      row[al] = s * rdiag[al];
     }
-    for (int al = 0; al < n2; ++al) out[q * n2 + al] = row[al];
+    if (k < M.K) {
+#pragma unroll
+      for (int al = 0; al < n2; ++al) out[q * n2 + al] = row[al];
+    }
   }
+#undef LS
+#undef HS
+}
+
+template <int P>
+static void launch_vel_prep(const double* rho, double* chol, const Tab* T, const Mesh& M, cudaStream_t st) {
+  const size_t smem = sizeof(double) * VPrep<P>::SIZE * 32;
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute((const void*)k_vel_prep<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    init = true;
+  }
+  k_vel_prep<P><<<(unsigned)((M.K + 31) / 32), 32, smem, st>>>(rho, chol, T, M);
 }
 
 void stab_vel_prep(int p, const double* rho, double* chol, const Tab* T, const Mesh& M, cudaStream_t st) {
-  unsigned bl = (unsigned)((M.K + 63) / 64);
   switch (p) {
-    case 1: k_vel_prep<1><<<bl, 64, 0, st>>>(rho, chol, T, M); break;
-    case 2: k_vel_prep<2><<<bl, 64, 0, st>>>(rho, chol, T, M); break;
-    case 3: k_vel_prep<3><<<bl, 64, 0, st>>>(rho, chol, T, M); break;
-    case 4: k_vel_prep<4><<<bl, 64, 0, st>>>(rho, chol, T, M); break;
+    case 1: launch_vel_prep<1>(rho, chol, T, M, st); break;
+    case 2: launch_vel_prep<2>(rho, chol, T, M, st); break;
+    case 3: launch_vel_prep<3>(rho, chol, T, M, st); break;
+    case 4: launch_vel_prep<4>(rho, chol, T, M, st); break;
   }
 }
 

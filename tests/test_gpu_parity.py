@@ -238,3 +238,30 @@ def test_stabilised_strang_steps(wl_name):
     d = s.diagnostics()
     assert d["rho_min"] > 0 and d["p_min"] > 0
     assert d["div_B"] <= 1e-12 * d["B_max"]
+
+
+def test_full_size_tiled_parity_stabilised():
+    """The benchmark configuration (256 x 256, p = k = 3, OE + PP + A.R. + velocity
+    filter): tiling a 16 x 16 oracle state 16 x 16 times keeps every row, column
+    and global statistic of the sensors, so each tile must reproduce the
+    oracle's stabilised Strang step."""
+    from paper_2609_10849_b300.mhd import Solver
+    wl = workloads.orszag_tang()
+    o = oracle_state(wl, 16, 16, 3, 3)
+    o.set_params(cfl=0.4, **STAB)
+    reps = 16
+    x0, x1, y0, y1 = o.domain
+    s = Solver(16 * reps, 16 * reps, 3, 3, wl["gamma"], (x0, x0 + reps * (x1 - x0), y0, y0 + reps * (y1 - y0)))
+    s.set_params(cfl=0.4, **STAB)
+    s.set_state(*tiled(o, reps))
+    dt = o.cfl_dt()
+    o.strang_step(dt)
+    s.strang_step(dt)
+    U, Bx, By, Bz = s.get_state()
+    Ut, Bxt, Byt, Bzt = tiled(o, reps)
+    bscale = max(np.abs(Bxt).max(), np.abs(Byt).max())
+    assert rel(U, Ut) <= 1e-12
+    for a, b in [(Bx, Bxt), (By, Byt), (Bz, Bzt)]:
+        assert rel(a, b, bscale) <= 1e-12
+    eta_t = np.tile(o.eta().reshape(16, 16), (reps, reps)).ravel()
+    assert rel(s.eta(), eta_t) <= 1e-9
