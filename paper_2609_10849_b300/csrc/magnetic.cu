@@ -67,9 +67,7 @@ __device__ __forceinline__ double assemble_W(const double* __restrict__ Lz, int 
   if (bo == 0) v += Lz[(size_t)(sy * M.nx + ox) * D::NW + (D::mL - 1) * D::mL + ao];
   if (ao == 0) v += Lz[(size_t)(oy * M.nx + wx) * D::NW + bo * D::mL + (D::mL - 1)];
   v += Lz[(size_t)(oy * M.nx + ox) * D::NW + bo * D::mL + ao];
-  double wa = ao == 0 ? 2.0 * T.wL[0] : T.wL[ao];
-  double wb = bo == 0 ? 2.0 * T.wL[0] : T.wL[bo];
-  return v / (wa * wb) * iJ;
+  return v * (iJ * T.iwLs[ao] * T.iwLs[bo]);
 }
 
 // Y-type (N_x) closure node (a < mm, b < mL).
@@ -84,8 +82,7 @@ __device__ __forceinline__ double assemble_Nx(const double* __restrict__ Lx, int
   double v = 0.0;
   if (bo == 0) v += Lx[(size_t)(sy * M.nx + ex) * D::NX + (D::mL - 1) * D::mm + a];
   v += Lx[(size_t)(oy * M.nx + ex) * D::NX + bo * D::mm + a];
-  double wb = bo == 0 ? 2.0 * T.wL[0] : T.wL[bo];
-  return v / (T.wG[a] * wb) * iJ;
+  return v * (iJ * T.iwG[a] * T.iwLs[bo]);
 }
 
 // X-type (N_y) closure node (a < mL, b < mm).
@@ -100,8 +97,7 @@ __device__ __forceinline__ double assemble_Ny(const double* __restrict__ Ly, int
   double v = 0.0;
   if (ao == 0) v += Ly[(size_t)(ey * M.nx + wx) * D::NY + b * D::mL + (D::mL - 1)];
   v += Ly[(size_t)(ey * M.nx + ox) * D::NY + b * D::mL + ao];
-  double wa = ao == 0 ? 2.0 * T.wL[0] : T.wL[ao];
-  return v / (wa * T.wG[b]) * iJ;
+  return v * (iJ * T.iwLs[ao] * T.iwG[b]);
 }
 
 // B closure loads: Bx (X-type, [b < mm][a < mL]) and By (Y-type, [b < mL][a < mm]).
@@ -563,42 +559,60 @@ __global__ void __launch_bounds__(256) k_mag_E(
       SM(O::JQ, it) = v;
     }
     __syncthreads();
-    // R_n = eta sum_q Jdet w_q J(x_q) phi_n(x_q), added to this element's own closure loads
-    constexpr int IR3 = D::NX + D::NY + D::NW;
+    // R_n = eta sum_q Jdet w_q J(x_q) phi_n(x_q), sum-factorised: x-pass of the
+    // weighted DG-node values onto the basis in x (into the dead TQ area), then
+    // y-pass, added to this element's own closure loads
+    constexpr int IR3 = D::n * D::mm + D::n * D::mL + D::n * D::mL;
     FLAT(IR3) {
+      int it = idx / D::EB, e = idx % D::EB;
+      if (SM(O::ETA, 0) == 0.0) continue;
+      if (it < D::n * D::mm) {  // N_x: basis g_a in x; rows j
+        int j = it / D::mm, a = it % D::mm;
+        double t = 0.0;
+#pragma unroll
+        for (int i = 0; i < D::n; ++i) t = fma(T.WG_P[i][a], SM(O::JQ, j * D::n + i), t);
+        SM(O::TQ, it) = t;
+      } else if (it < D::n * D::mm + D::n * D::mL) {  // N_y: basis l^L_a in x
+        it -= D::n * D::mm;
+        int j = it / D::mL, a = it % D::mL;
+        double t = 0.0;
+#pragma unroll
+        for (int i = 0; i < D::n; ++i) t = fma(T.WL_P[i][a], SM(O::JQ, D::n2 + j * D::n + i), t);
+        SM(O::TQ, D::n * D::mm + it) = t;
+      } else {  // W: basis l^L_a in x
+        it -= D::n * D::mm + D::n * D::mL;
+        int j = it / D::mL, a = it % D::mL;
+        double t = 0.0;
+#pragma unroll
+        for (int i = 0; i < D::n; ++i) t = fma(T.WL_P[i][a], SM(O::JQ, 2 * D::n2 + j * D::n + i), t);
+        SM(O::TQ, D::n * D::mm + D::n * D::mL + it) = t;
+      }
+    }
+    __syncthreads();
+    constexpr int IR4 = D::NX + D::NY + D::NW;
+    FLAT(IR4) {
       int it = idx / D::EB, e = idx % D::EB, k = k0 + e;
       const double et = SM(O::ETA, 0);
       if (et == 0.0 || k >= M.K) continue;
+      const double f = et * Jd;
       double r = 0.0;
-      if (it < D::NX) {
+      if (it < D::NX) {  // (a < mm, b < mL): y basis l^L_b
         int b = it / D::mm, a = it % D::mm;
-        for (int j = 0; j < D::n; ++j) {
-          double t = 0.0;
 #pragma unroll
-          for (int i = 0; i < D::n; ++i) t = fma(T.wp[i] * T.G_P[i][a], SM(O::JQ, j * D::n + i), t);
-          r = fma(T.wp[j] * T.L_P[j][b], t, r);
-        }
-        LEx[(size_t)k * D::NX + it] += et * Jd * r;
-      } else if (it < D::NX + D::NY) {
+        for (int j = 0; j < D::n; ++j) r = fma(T.WL_P[j][b], SM(O::TQ, j * D::mm + a), r);
+        LEx[(size_t)k * D::NX + it] += f * r;
+      } else if (it < D::NX + D::NY) {  // (a < mL, b < mm): y basis g_b
         it -= D::NX;
         int b = it / D::mL, a = it % D::mL;
-        for (int j = 0; j < D::n; ++j) {
-          double t = 0.0;
 #pragma unroll
-          for (int i = 0; i < D::n; ++i) t = fma(T.wp[i] * T.L_P[i][a], SM(O::JQ, D::n2 + j * D::n + i), t);
-          r = fma(T.wp[j] * T.G_P[j][b], t, r);
-        }
-        LEy[(size_t)k * D::NY + it] += et * Jd * r;
-      } else {
+        for (int j = 0; j < D::n; ++j) r = fma(T.WG_P[j][b], SM(O::TQ, D::n * D::mm + j * D::mL + a), r);
+        LEy[(size_t)k * D::NY + it] += f * r;
+      } else {  // W: y basis l^L_b
         it -= D::NX + D::NY;
         int b = it / D::mL, a = it % D::mL;
-        for (int j = 0; j < D::n; ++j) {
-          double t = 0.0;
 #pragma unroll
-          for (int i = 0; i < D::n; ++i) t = fma(T.wp[i] * T.L_P[i][a], SM(O::JQ, 2 * D::n2 + j * D::n + i), t);
-          r = fma(T.wp[j] * T.L_P[j][b], t, r);
-        }
-        LEz[(size_t)k * D::NW + it] += et * Jd * r;
+        for (int j = 0; j < D::n; ++j) r = fma(T.WL_P[j][b], SM(O::TQ, D::n * D::mm + D::n * D::mL + j * D::mL + a), r);
+        LEz[(size_t)k * D::NW + it] += f * r;
       }
     }
   }

@@ -54,6 +54,10 @@ struct Tab {
   double L_end[2][MHD_LMAX];                  // l^L_c(-1), l^L_c(+1)
   double G_end[2][MHD_NMAX];                  // g_c(-1), g_c(+1)
   double M_end[2][MHD_NMAX];                  // l^M_c(-1), l^M_c(+1)
+  double WG_P[MHD_NMAX][MHD_NMAX];            // wp_a g_c(xp_a)
+  double WL_P[MHD_NMAX][MHD_LMAX];            // wp_a l^L_c(xp_a)
+  double iwLs[MHD_LMAX];                      // 1 / assembled GLL(k+1) weight (2 wL_0 at a = 0)
+  double iwG[MHD_NMAX];                       // 1 / wG
 };
 
 // Device copy of the tables of the 8 supported (p, k) pairs.

@@ -97,21 +97,32 @@ __global__ void k_stats(const double* __restrict__ F, size_t stride, int nc, Sta
   const int I = (w - 1) / n, r = (w - 1) % n;
   const int kA = I == 0 ? ey * M.nx + wrap(ex - 1, M.nx) : wrap(ey - 1, M.ny) * M.nx + ex;  // lower side
   const double h = I == 0 ? M.hx : M.hy;
-  double scale = 1.0;
+  double scale = 1.0;  // (2/h)^r, applied once to the averaged square
   for (int i = 0; i < r; ++i) scale *= 2.0 / h;
   double acc = 0.0;
+  if (r == 0) {  // the traces themselves: end nodes of the two elements
 #pragma unroll
-  for (int tt = 0; tt < n; ++tt) {  // face GLL node
-    double dA = 0.0, dB = 0.0;
-#pragma unroll
-    for (int s = 0; s < n; ++s) {
-      double wA = I == 0 ? f[(size_t)kA * n2 + tt * n + s] : f[(size_t)kA * n2 + s * n + tt];
-      double wB = I == 0 ? f[(size_t)k * n2 + tt * n + s] : f[(size_t)k * n2 + s * n + tt];
-      dA = fma(T->Drp[r][s], wA, dA);
-      dB = fma(T->Dr0[r][s], wB, dB);
+    for (int tt = 0; tt < n; ++tt) {
+      double wA = I == 0 ? f[(size_t)kA * n2 + tt * n + P] : f[(size_t)kA * n2 + P * n + tt];
+      double wB = I == 0 ? f[(size_t)k * n2 + tt * n] : f[(size_t)k * n2 + tt];
+      double jmp = wB - wA;
+      acc = fma(0.5 * T->wp[tt] * jmp, jmp, acc);
     }
-    double jmp = scale * (dB - dA);
-    acc = fma(0.5 * T->wp[tt] * jmp, jmp, acc);
+  } else {
+#pragma unroll
+    for (int tt = 0; tt < n; ++tt) {  // face GLL node
+      double dA = 0.0, dB = 0.0;
+#pragma unroll
+      for (int s = 0; s < n; ++s) {
+        double wA = I == 0 ? f[(size_t)kA * n2 + tt * n + s] : f[(size_t)kA * n2 + s * n + tt];
+        double wB = I == 0 ? f[(size_t)k * n2 + tt * n + s] : f[(size_t)k * n2 + s * n + tt];
+        dA = fma(T->Drp[r][s], wA, dA);
+        dB = fma(T->Dr0[r][s], wB, dB);
+      }
+      double jmp = dB - dA;
+      acc = fma(0.5 * T->wp[tt] * jmp, jmp, acc);
+    }
+    acc *= scale * scale;
   }
   double* out = I == 0 ? V.jx : V.jy;
   out[((size_t)c * n + r) * K + k] = sqrt(acc);
@@ -311,8 +322,8 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_oe_pp(double* __restrict__
       const double ir = rcp(a0);
       const double pb = (g - 1.0) * fma(-0.5 * ir, fma(a1, a1, fma(a2, a2, a3 * a3)), a4);
       const double cb = sqrt(g * pb * ir);
-      lam[0] = (2.0 * P + 1.0) * (fabs(a1 * ir) + cb) / M.hx;
-      lam[1] = (2.0 * P + 1.0) * (fabs(a2 * ir) + cb) / M.hy;
+      lam[0] = (2.0 * P + 1.0) * (fabs(a1 * ir) + cb) * (1.0 / M.hx);
+      lam[1] = (2.0 * P + 1.0) * (fabs(a2 * ir) + cb) * (1.0 / M.hy);
     }
     oe_factors<P>(V, 5, q, el, kk, ex, ey, lam, prm.s_H * dtp[0] * dtfac, M, ssig, sD);
 #pragma unroll
@@ -371,7 +382,9 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_oe_pp(double* __restrict__
     for (int c = 0; c < 5; ++c)  // average of U* (eq. euler-pp-average), identical in every lane of the segment
       a[c] = __shfl_sync(0xffffffffu, seg_sum<SW>(wq * u[c]), lead);
     const double rbar = a[0];
-    const double pbar = (g - 1.0) * (a[4] - (a[1] * a[1] + a[2] * a[2] + a[3] * a[3]) / (2.0 * a[0]));
+    const double ira = rcp(fmax(a[0], eps_rho));  // only used when rbar > eps_rho
+    const double ma2 = fma(a[1], a[1], fma(a[2], a[2], a[3] * a[3]));
+    const double pbar = (g - 1.0) * fma(-0.5 * ma2, a[0] > eps_rho ? ira : 1.0 / a[0], a[4]);
     const bool bad = !(rbar > 0.0) || !(pbar > 0.0) || !isfinite(rbar) || !isfinite(pbar);
     // density scaling (eq. euler-pp-density)
     const double rmin = seg_min<SW>(node ? u[0] : DBL_MAX);
@@ -384,9 +397,10 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_oe_pp(double* __restrict__
     if (th_r < 1.0) r0 = rbar + th_r * (u[0] - rbar);
     // pressure-cancellation scale and floor (eq. euler-pp-floors), pressure scaling (eq. euler-pp-pressure)
     const double m2 = fma(u[1], u[1], fma(u[2], u[2], u[3] * u[3]));
-    const double Sq = node ? fabs(u[4]) + m2 / (2.0 * fmax(r0, eps_rho)) : 0.0;
-    const double pq = node ? (g - 1.0) * (u[4] - m2 / (2.0 * r0)) : DBL_MAX;
-    const double Sa = fabs(a[4]) + (a[1] * a[1] + a[2] * a[2] + a[3] * a[3]) / (2.0 * fmax(a[0], eps_rho));
+    const double ir0 = rcp(fmax(r0, eps_rho));  // nodes are >= eps_rho after the density scaling
+    const double Sq = node ? fma(0.5 * m2, ir0, fabs(u[4])) : 0.0;
+    const double pq = node ? (g - 1.0) * fma(-0.5 * m2, r0 >= eps_rho ? ir0 : 1.0 / r0, u[4]) : DBL_MAX;
+    const double Sa = fma(0.5 * ma2, ira, fabs(a[4]));
     const double Smax = fmax(Sa, seg_max<SW>(Sq));
     const double pmin = seg_min<SW>(pq);
     const double eps_p = fmax(64.0 * eps, 8192.0 * eps * Smax);

@@ -185,6 +185,12 @@ void host_tables(int p, int k, Tab* T) {
   fill_interp(T->L_end, 2, ends, mL, xL, false);
   fill_interp(T->G_end, 2, ends, mm, zG, false);
   fill_interp(T->M_end, 2, ends, mm, xM, false);
+  for (int a = 0; a < n; ++a) {
+    for (int c = 0; c < mm; ++c) T->WG_P[a][c] = (double)(wp[a] * (ld)T->G_P[a][c]);
+    for (int c = 0; c < mL; ++c) T->WL_P[a][c] = (double)(wp[a] * (ld)T->L_P[a][c]);
+  }
+  for (int a = 0; a < mL; ++a) T->iwLs[a] = (double)(1.0L / (a == 0 ? 2.0L * wL[0] : wL[a]));
+  for (int a = 0; a < mm; ++a) T->iwG[a] = (double)(1.0L / wG[a]);
   // exact GLL(k+1) mass with the (k+2)-point Gauss rule
   for (int a = 0; a < mL; ++a)
     for (int b = 0; b < mL; ++b) {
