@@ -117,11 +117,34 @@ int mhd_compute_dt(mhd_ctx* ctx, double* dt);
  * MHD_INADMISSIBLE with the state restored. */
 int mhd_strang_step(mhd_ctx* ctx, double dt, double* dt_taken);
 
-/* Several Strang steps at a fixed dt without a host synchronisation between
- * them; the status of the whole sequence is checked once at the end.  On a
- * rejection the sequence stops with the state of the last good step and
- * returns MHD_INADMISSIBLE with *steps_done steps committed. */
+/* Several Strang steps at a fixed dt as one CUDA-graph launch (captured on the
+ * first call for a given nsteps and replayed afterwards; parameter or stream
+ * changes invalidate it); the status of the whole sequence is checked once at
+ * the end.  If a raw average became inadmissible the state is restored to the
+ * start of the sequence and MHD_INADMISSIBLE is returned with *steps_done = 0. */
 int mhd_strang_steps(mhd_ctx* ctx, double dt, int nsteps, int* steps_done);
+
+/* Batches of independent runs (spec batching pattern; the paper has no
+ * counterpart): every run has its own context (mesh, p, k, gamma, parameters
+ * and state) and stream.  mhd_batch_step advances every run by nsteps Strang
+ * steps with its own fixed dt (dt[i]) as ONE CUDA-graph launch holding a
+ * parallel branch per run, then checks every run's status once.  The graph
+ * is captured on the first call and re-captured when nsteps or a run's
+ * parameters change; each run's result is bitwise that of mhd_strang_steps on
+ * the run alone.  A run whose raw averages become inadmissible is restored to
+ * the start of the call and reported MHD_INADMISSIBLE in status[i] (may be
+ * NULL); the other runs keep their results. */
+typedef struct mhd_batch mhd_batch;
+int mhd_batch_create(int nruns, const mhd_mesh_t* meshes, const int* p, const int* k, const double* gamma,
+                     mhd_batch** out);
+void mhd_batch_destroy(mhd_batch* batch);
+int mhd_batch_size(const mhd_batch* batch);
+/* Context of run i (owned by the batch): use it to set states and parameters
+ * and to read states and diagnostics. */
+mhd_ctx* mhd_batch_run(mhd_batch* batch, int i);
+int mhd_batch_step(mhd_batch* batch, const double* dt, int nsteps, int* status);
+/* Kernel launches enqueued by the batch and its runs since creation. */
+long long mhd_batch_launch_count(const mhd_batch* batch);
 
 /* A single substep: which = 0 hydro Phi_H^tau (Algorithm 1), 1 magnetic
  * Phi_M^tau (Algorithm 2, with the nodal variable exchange around it). */

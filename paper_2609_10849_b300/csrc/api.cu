@@ -45,6 +45,8 @@ void stab_vel(int p, int k, const double* rho, double* Y, const double* B, const
 size_t stab_work_doubles(int p, int k, const Mesh& M);
 size_t stab_chol_doubles(int p, const Mesh& M);
 void set_error_message(const char* msg);
+cudaError_t mag_prepare(int p, int k);
+cudaError_t stab_prepare(int p);
 }  // namespace mhd
 
 using namespace mhd;
@@ -90,6 +92,10 @@ struct mhd_ctx {
   std::vector<void*> allocs;
   // optional per-kernel-class event timing (bench instrumentation)
   bool profiling;
+  // cached CUDA graph of a fixed-dt sequence of Strang steps (mhd_strang_steps)
+  cudaGraphExec_t graph;
+  int graph_steps;
+  long long graph_launches;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_rec;
 };
@@ -266,6 +272,11 @@ int mhd_create(const mhd_mesh_t* mesh, int p, int k, double gamma, mhd_ctx** out
   c->own_stream = true;
   c->T = device_tables(p, k, &e);
   if (!c->T) { cudaStreamDestroy(c->st); delete c; return cuda_fail(e, "tables"); }
+  if ((e = mag_prepare(p, k)) != cudaSuccess || (e = stab_prepare(p)) != cudaSuccess) {
+    cudaStreamDestroy(c->st);
+    delete c;
+    return cuda_fail(e, "kernel attributes");
+  }
   host_tables(p, k, &c->hT);
   const size_t N = c->N, Z = c->Z, K = c->M.K;
   double** bufs5[] = {&c->U, &c->Usave, &c->S1, &c->S2};
@@ -311,6 +322,7 @@ oom:
 void mhd_destroy(mhd_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
   for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
   for (void* p : c->allocs) cudaFree(p);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -324,6 +336,7 @@ int mhd_set_params(mhd_ctx* c, const mhd_params_t* prm) {
     return fail(MHD_EINVAL, "invalid stabilisation parameters");
   c->prm = Stab{prm->oe_hydro, prm->oe_vel, prm->pp, prm->ar, prm->s_H, prm->s_M, prm->C_s, prm->C_eta, prm->cfl,
                 prm->max_halvings};
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
   return MHD_OK;
 }
 
@@ -333,6 +346,7 @@ int mhd_set_stream(mhd_ctx* c, void* stream) {
   if (c->own_stream) cudaStreamDestroy(c->st);
   c->st = (cudaStream_t)stream;
   c->own_stream = false;
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
   return MHD_OK;
 }
 
@@ -481,17 +495,62 @@ int mhd_strang_step(mhd_ctx* c, double dt, double* dt_taken) {
   return fail(MHD_INADMISSIBLE, "inadmissible cell average after all halvings");
 }
 
+// Capture `nsteps` Strang steps (state save included) on stream `st` of the
+// context; the step length is read from the device word c->dt at run time.
+static void enqueue_sequence(mhd_ctx* c, int nsteps) {
+  cudaMemcpyAsync(c->Usave, c->U, 5 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  cudaMemcpyAsync(c->Bsave, c->B, 3 * c->Z * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  for (int s = 0; s < nsteps; ++s) enqueue_strang(c);
+}
+
+// Instantiated graph of a fixed-dt sequence of nsteps Strang steps (cached).
+static int sequence_graph(mhd_ctx* c, int nsteps) {
+  if (c->graph && c->graph_steps == nsteps) return MHD_OK;
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  cudaGraph_t g = nullptr;
+  long long l0 = c->launches;
+  cudaError_t e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+  enqueue_sequence(c, nsteps);
+  e = cudaStreamEndCapture(c->st, &g);
+  if (e != cudaSuccess) return cuda_fail(e, "end capture");
+  e = cudaGraphInstantiate(&c->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { c->graph = nullptr; return cuda_fail(e, "graph instantiate"); }
+  c->graph_steps = nsteps;
+  c->graph_launches = c->launches - l0;
+  c->launches = l0;
+  return MHD_OK;
+}
+
+static bool capturable(cudaStream_t s) {
+  return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+}
+
 int mhd_strang_steps(mhd_ctx* c, double dt, int nsteps, int* steps_done) {
   if (!c || !(dt > 0) || nsteps < 0) return fail(MHD_EINVAL, "invalid argument");
   if (steps_done) *steps_done = 0;
-  cudaMemcpyAsync(c->Usave, c->U, 5 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
-  cudaMemcpyAsync(c->Bsave, c->B, 3 * c->Z * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  if (nsteps == 0) return MHD_OK;
+  // the legacy default stream cannot be captured, and the event profiler needs
+  // the eager launches: run eagerly in both cases
+  const bool graph = capturable(c->st) && !c->profiling;
+  if (graph) {
+    int r = sequence_graph(c, nsteps);
+    if (r != MHD_OK) return r;
+  }
   cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->st);
   set_scalar(c->dt, dt, c->st);
   c->launches++;
-  for (int s = 0; s < nsteps; ++s) enqueue_strang(c);
+  if (graph) {
+    cudaError_t e = cudaGraphLaunch(c->graph, c->st);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    c->launches += c->graph_launches;
+  } else {
+    enqueue_sequence(c, nsteps);
+  }
+  int r;
   unsigned s = 0;
-  int r = check_status(c, &s);
+  r = check_status(c, &s);
   if (r != MHD_OK) return r;
   if (s & ST_INADMISSIBLE) {
     cudaMemcpyAsync(c->U, c->Usave, 5 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
@@ -501,6 +560,152 @@ int mhd_strang_steps(mhd_ctx* c, double dt, int nsteps, int* steps_done) {
   }
   if (steps_done) *steps_done = nsteps;
   return MHD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batch of independent runs (uneven meshes and degrees): every run keeps its
+// own context and stream; one CUDA graph holds a parallel branch per run, so a
+// batch step is a single graph launch and small runs overlap on the GPU.
+// ---------------------------------------------------------------------------
+struct mhd_batch {
+  std::vector<mhd_ctx*> runs;
+  cudaStream_t root;
+  std::vector<cudaEvent_t> ev;  // ev[0] fork, ev[1 + i] join of run i, ev[1 + n + i] set-up of run i
+  cudaGraphExec_t exec;
+  int exec_steps;
+  long long launches_per_replay;
+  long long launches_total;
+  unsigned* h_status;
+};
+
+extern "C" {
+
+int mhd_batch_create(int nruns, const mhd_mesh_t* meshes, const int* p, const int* k, const double* gamma,
+                     mhd_batch** out) {
+  if (!out || nruns < 1 || !meshes || !p || !k || !gamma) return fail(MHD_EINVAL, "invalid argument");
+  *out = nullptr;
+  mhd_batch* b = new (std::nothrow) mhd_batch();
+  if (!b) return fail(MHD_ENOMEM, "host allocation");
+  cudaError_t e = cudaStreamCreateWithFlags(&b->root, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { delete b; return cuda_fail(e, "stream"); }
+  for (int i = 0; i < nruns; ++i) {
+    mhd_ctx* c = nullptr;
+    int r = mhd_create(&meshes[i], p[i], k[i], gamma[i], &c);
+    if (r != MHD_OK) { mhd_batch_destroy(b); return r; }
+    b->runs.push_back(c);
+  }
+  b->ev.resize(1 + 2 * nruns);
+  for (auto& ev : b->ev)
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+      mhd_batch_destroy(b);
+      return cuda_fail(e, "events");
+    }
+  if ((e = cudaMallocHost(&b->h_status, sizeof(unsigned) * nruns)) != cudaSuccess) {
+    mhd_batch_destroy(b);
+    return cuda_fail(e, "pinned status");
+  }
+  *out = b;
+  return MHD_OK;
+}
+
+void mhd_batch_destroy(mhd_batch* b) {
+  if (!b) return;
+  if (b->root) cudaStreamSynchronize(b->root);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto ev : b->ev)
+    if (ev) cudaEventDestroy(ev);
+  for (auto c : b->runs) mhd_destroy(c);
+  if (b->h_status) cudaFreeHost(b->h_status);
+  if (b->root) cudaStreamDestroy(b->root);
+  delete b;
+}
+
+int mhd_batch_size(const mhd_batch* b) { return b ? (int)b->runs.size() : 0; }
+
+mhd_ctx* mhd_batch_run(mhd_batch* b, int i) {
+  if (!b || i < 0 || i >= (int)b->runs.size()) return nullptr;
+  return b->runs[i];
+}
+
+int mhd_batch_step(mhd_batch* b, const double* dt, int nsteps, int* status) {
+  if (!b || !dt || nsteps < 1) return fail(MHD_EINVAL, "invalid argument");
+  const int n = (int)b->runs.size();
+  for (int i = 0; i < n; ++i)
+    if (!(dt[i] > 0)) return fail(MHD_EINVAL, "dt must be positive");
+  cudaError_t e;
+  // (re)capture the batch graph: fork from the root stream into every run's stream
+  bool stale = !b->exec || b->exec_steps != nsteps;
+  for (auto c : b->runs) stale = stale || !c->graph || c->graph_steps != nsteps;
+  if (stale) {
+    if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+    for (auto c : b->runs) {  // per-run graphs also serve as the validity marker of the parameters
+      int r = sequence_graph(c, nsteps);
+      if (r != MHD_OK) return r;
+    }
+    cudaGraph_t g = nullptr;
+    std::vector<long long> l0(n);
+    for (int i = 0; i < n; ++i) l0[i] = b->runs[i]->launches;
+    if ((e = cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+      return cuda_fail(e, "begin capture");
+    cudaEventRecord(b->ev[0], b->root);
+    for (int i = 0; i < n; ++i) {
+      mhd_ctx* c = b->runs[i];
+      cudaStreamWaitEvent(c->st, b->ev[0], 0);
+      enqueue_sequence(c, nsteps);
+      cudaEventRecord(b->ev[1 + i], c->st);
+      cudaStreamWaitEvent(b->root, b->ev[1 + i], 0);
+    }
+    e = cudaStreamEndCapture(b->root, &g);
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { b->exec = nullptr; return cuda_fail(e, "graph instantiate"); }
+    b->launches_per_replay = 0;
+    for (int i = 0; i < n; ++i) {  // captured launches count at replay, not at capture
+      b->launches_per_replay += b->runs[i]->launches - l0[i];
+      b->runs[i]->launches = l0[i];
+    }
+    b->exec_steps = nsteps;
+  }
+  // per-run step length and status words, then the graph on the root stream
+  for (int i = 0; i < n; ++i) {
+    mhd_ctx* c = b->runs[i];
+    cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->st);
+    set_scalar(c->dt, dt[i], c->st);
+    c->launches++;
+    cudaEventRecord(b->ev[1 + n + i], c->st);
+    cudaStreamWaitEvent(b->root, b->ev[1 + n + i], 0);
+  }
+  if ((e = cudaGraphLaunch(b->exec, b->root)) != cudaSuccess) return cuda_fail(e, "graph launch");
+  b->launches_total += b->launches_per_replay;
+  for (int i = 0; i < n; ++i)
+    if ((e = cudaMemcpyAsync(&b->h_status[i], b->runs[i]->status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                             b->root)) != cudaSuccess)
+      return cuda_fail(e, "status copy");
+  if ((e = cudaStreamSynchronize(b->root)) != cudaSuccess) return cuda_fail(e, "batch step");
+  int worst = MHD_OK;
+  for (int i = 0; i < n; ++i) {
+    mhd_ctx* c = b->runs[i];
+    int st = MHD_OK;
+    if (b->h_status[i] & ST_INADMISSIBLE) {  // restore this run; the caller may retry it with a smaller dt
+      cudaMemcpyAsync(c->U, c->Usave, 5 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+      cudaMemcpyAsync(c->B, c->Bsave, 3 * c->Z * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+      cudaStreamSynchronize(c->st);
+      st = MHD_INADMISSIBLE;
+      worst = MHD_INADMISSIBLE;
+    }
+    if (status) status[i] = st;
+  }
+  return worst == MHD_OK ? MHD_OK : fail(worst, "a run of the batch had an inadmissible cell average");
+}
+
+long long mhd_batch_launch_count(const mhd_batch* b) {
+  if (!b) return 0;
+  long long t = b->launches_total;
+  for (auto c : b->runs) t += c->launches;
+  return t;
 }
 
 int mhd_substep(mhd_ctx* c, int which, double tau) {

@@ -761,15 +761,6 @@ void mag_stage_impl(int mode, const double* B, const double* u, const double* e,
   const size_t sj = sizeof(double) * LJ_<P, KM>::SIZE * D::EB;
   const size_t se = sizeof(double) * LE_<P, KM>::SIZE * D::EB;
   const size_t sb = sizeof(double) * LB_<P, KM>::SIZE * D::EB;
-  static bool init = false;
-  if (!init) {
-    cudaFuncSetAttribute((const void*)k_mag_J<P, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sj);
-    cudaFuncSetAttribute((const void*)k_mag_E<P, KM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se);
-    cudaFuncSetAttribute((const void*)k_mag_E<P, KM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)se);
-    cudaFuncSetAttribute((const void*)k_mag_B<P, KM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-    cudaFuncSetAttribute((const void*)k_mag_B<P, KM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
-    init = true;
-  }
   k_mag_J<P, KM><<<blocks, D::TH, sj, st>>>(B, B + Z, B + 2 * Z, LJx, LJy, LJz, M);
   if (mode == 0) {
     k_mag_E<P, KM, 0><<<blocks, D::TH, se, st>>>(LJx, LJy, LJz, B, B + Z, B + 2 * Z, u, e, rho, eta, u0, e0, uo, eo,
@@ -780,6 +771,31 @@ void mag_stage_impl(int mode, const double* B, const double* u, const double* e,
                                                   LEx, LEy, LEz, M, dtp, dtfac, ca, cb, first, resistive);
     k_mag_B<P, KM, 1><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, M, dtp, dtfac, ca, cb, first);
   }
+}
+
+// Opt-in dynamic shared memory of the magnetic kernels of one (p, k) pair on the
+// current device (done at context creation, never during stream capture).
+template <int P, int KM>
+static cudaError_t mag_prepare_impl() {
+  using D = MD<P, KM>;
+  const int sj = (int)(sizeof(double) * LJ_<P, KM>::SIZE * D::EB);
+  const int se = (int)(sizeof(double) * LE_<P, KM>::SIZE * D::EB);
+  const int sb = (int)(sizeof(double) * LB_<P, KM>::SIZE * D::EB);
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_J<P, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sj);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_E<P, KM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, se);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_E<P, KM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, se);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_B<P, KM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_B<P, KM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+  return e;
+}
+
+cudaError_t mag_prepare(int p, int k) {
+  cudaError_t e = cudaErrorInvalidValue;
+#define MHD_MAG_PREP(PP, KK) e = mag_prepare_impl<PP, KK>()
+  MHD_DISPATCH_PK(p, k, MHD_MAG_PREP);
+#undef MHD_MAG_PREP
+  return e;
 }
 
 size_t mag_load_doubles(int p, int k, int K) {

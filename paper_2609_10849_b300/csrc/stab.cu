@@ -779,12 +779,18 @@ __global__ void __launch_bounds__(32) k_vel_prep(const double* __restrict__ rho,
 template <int P>
 static void launch_vel_prep(const double* rho, double* chol, const Tab* T, const Mesh& M, cudaStream_t st) {
   const size_t smem = sizeof(double) * VPrep<P>::SIZE * 32;
-  static bool init = false;
-  if (!init) {
-    cudaFuncSetAttribute((const void*)k_vel_prep<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    init = true;
-  }
   k_vel_prep<P><<<(unsigned)((M.K + 31) / 32), 32, smem, st>>>(rho, chol, T, M);
+}
+
+// Opt-in dynamic shared memory of the velocity-projector kernel (context creation).
+cudaError_t stab_prepare(int p) {
+  switch (p) {
+    case 1: return cudaFuncSetAttribute((const void*)k_vel_prep<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * VPrep<1>::SIZE * 32));
+    case 2: return cudaFuncSetAttribute((const void*)k_vel_prep<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * VPrep<2>::SIZE * 32));
+    case 3: return cudaFuncSetAttribute((const void*)k_vel_prep<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * VPrep<3>::SIZE * 32));
+    case 4: return cudaFuncSetAttribute((const void*)k_vel_prep<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * VPrep<4>::SIZE * 32));
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 void stab_vel_prep(int p, const double* rho, double* chol, const Tab* T, const Mesh& M, cudaStream_t st) {

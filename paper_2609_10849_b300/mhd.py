@@ -70,6 +70,13 @@ _SIGS = {
     "mhd_kernel_times": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "mhd_fp64_peak": (C.c_int, [C.POINTER(C.c_double)]),
     "mhd_hydro_rhs_static": (C.c_int, [C.POINTER(Mesh), C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mhd_batch_create": (C.c_int, [C.c_int, C.POINTER(Mesh), C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.POINTER(C.c_void_p)]),
+    "mhd_batch_destroy": (None, [C.c_void_p]),
+    "mhd_batch_size": (C.c_int, [C.c_void_p]),
+    "mhd_batch_run": (C.c_void_p, [C.c_void_p, C.c_int]),
+    "mhd_batch_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "mhd_batch_launch_count": (C.c_longlong, [C.c_void_p]),
     "mhd_status_string": (C.c_char_p, [C.c_int]),
     "mhd_last_error": (C.c_char_p, []),
 }
@@ -138,12 +145,16 @@ def hydro_rhs_static(nx, ny, p, gamma, domain, U, L, stream=0):
 class Solver:
     """One periodic mesh with DGSEM degree p and magnetic degree k."""
 
-    def __init__(self, nx, ny, p, k, gamma, domain=(0.0, 1.0, 0.0, 1.0)):
+    def __init__(self, nx, ny, p, k, gamma, domain=(0.0, 1.0, 0.0, 1.0), _handle=None):
         self.nx, self.ny, self.p, self.k, self.gamma = nx, ny, p, k, gamma
         self.domain = tuple(float(v) for v in domain)
-        mesh = Mesh(nx, ny, *self.domain)
-        h = C.c_void_p()
-        _check(lib().mhd_create(C.byref(mesh), p, k, gamma, C.byref(h)))
+        self._owned = _handle is None
+        if _handle is None:
+            mesh = Mesh(nx, ny, *self.domain)
+            h = C.c_void_p()
+            _check(lib().mhd_create(C.byref(mesh), p, k, gamma, C.byref(h)))
+        else:
+            h = C.c_void_p(_handle)
         self._h = h
         K, N, G, Z = (C.c_longlong() for _ in range(4))
         _check(lib().mhd_sizes(h, C.byref(K), C.byref(N), C.byref(G), C.byref(Z)))
@@ -153,7 +164,8 @@ class Solver:
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().mhd_destroy(self._h)
+            if self._owned:
+                lib().mhd_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -256,3 +268,48 @@ class Solver:
         cnt = np.zeros(n, dtype=np.int64)
         _check(lib().mhd_kernel_times(self._h, ms.ctypes.data_as(C.c_void_p), cnt.ctypes.data_as(C.c_void_p), n))
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.KERNEL_CLASSES) if cnt[i]}
+
+
+class Batch:
+    """Independent runs advanced together by one CUDA-graph launch per call.
+
+    ``specs`` is a list of (nx, ny, p, k, gamma, domain); ``runs[i]`` is a
+    :class:`Solver` view of run i (owned by the batch)."""
+
+    def __init__(self, specs):
+        n = len(specs)
+        meshes = (Mesh * n)(*[Mesh(s[0], s[1], *(float(v) for v in s[5])) for s in specs])
+        p = np.array([s[2] for s in specs], dtype=np.int32)
+        k = np.array([s[3] for s in specs], dtype=np.int32)
+        g = np.array([s[4] for s in specs], dtype=np.float64)
+        h = C.c_void_p()
+        _check(lib().mhd_batch_create(n, meshes, p.ctypes.data_as(C.c_void_p), k.ctypes.data_as(C.c_void_p),
+                                      g.ctypes.data_as(C.c_void_p), C.byref(h)))
+        self._h = h
+        self.runs = [Solver(s[0], s[1], s[2], s[3], s[4], s[5], _handle=lib().mhd_batch_run(h, i))
+                     for i, s in enumerate(specs)]
+
+    def step(self, dt, nsteps=1):
+        """Advance every run by nsteps Strang steps of its own dt; returns per-run status."""
+        dt = np.ascontiguousarray(dt, dtype=np.float64)
+        st = np.zeros(len(self.runs), dtype=np.int32)
+        code = lib().mhd_batch_step(self._h, dt.ctypes.data_as(C.c_void_p), int(nsteps), st.ctypes.data_as(C.c_void_p))
+        if code < 0 and code != MHD_INADMISSIBLE:
+            raise MhdError(code, lib().mhd_last_error().decode())
+        return st
+
+    def launch_count(self):
+        return lib().mhd_batch_launch_count(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for r in self.runs:
+                r._h = None
+            lib().mhd_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -207,6 +207,23 @@ def density_wave(amp=0.2, u=(1.0, 0.5, 0.3), p0=1.0, gamma=1.4):
                 gamma=gamma)
 
 
+BATCH_MESHES = (32, 48, 64, 96, 128, 192, 256)
+BATCH_DEGREES = (2, 3, 4)
+
+
+def batch_specs(nruns: int, seed: int = SEED):
+    """Seeded (N, p) of the batched workload: N from BATCH_MESHES (an N x N
+    mesh), p = k from BATCH_DEGREES, drawn uniformly; run i is the Orszag-Tang
+    variant orszag_tang_variant(i)."""
+    r = Rng(seed ^ 0xB47C4)
+    out = []
+    for _ in range(nruns):
+        N = BATCH_MESHES[min(int(r.uniform() * len(BATCH_MESHES)), len(BATCH_MESHES) - 1)]
+        p = BATCH_DEGREES[min(int(r.uniform() * len(BATCH_DEGREES)), len(BATCH_DEGREES) - 1)]
+        out.append((N, p))
+    return out
+
+
 WORKLOADS = {
     "alfven": alfven_rotated,
     "alfven_diag": alfven_diagonal,
