@@ -29,21 +29,39 @@
 #include <cstring>
 #include <vector>
 
+#ifdef ORACLE_TANGENT
+// Forward-mode tangent build (liboracle_tangent.so): the same source with the
+// scalar type replaced by a dual number; the values it computes are those of
+// the plain build bit for bit, the tangents are directional derivatives.
+#include "dual.h"
+typedef Dual real;
+#else
+typedef double real;
+inline double val(double x) { return x; }
+inline double tan_of(double) { return 0.0; }
+#endif
+using std::exp;
+using std::fabs;
+using std::isfinite;
+using std::log;
+using std::pow;
+using std::sqrt;
+
 namespace {
 
-typedef std::vector<double> vec;
+typedef std::vector<real> vec;
 
 // ---------------------------------------------------------------------------
 // O1. One-dimensional rules and Lagrange bases (§3.1.3)
 // ---------------------------------------------------------------------------
 
 // Legendre P_n(x) and P_n'(x): Bonnet recurrence, P_k' = P_{k-2}' + (2k-1) P_{k-1}.
-void legendre(int n, double x, double* P, double* dP) {
+void legendre(int n, real x, real* P, real* dP) {
   if (n == 0) { *P = 1.0; *dP = 0.0; return; }
-  double p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0;
+  real p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0;
   for (int k = 2; k <= n; ++k) {
-    double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
-    double d2 = d0 + (2.0 * k - 1.0) * p1;
+    real p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+    real d2 = d0 + (2.0 * k - 1.0) * p1;
     p0 = p1; p1 = p2; d0 = d1; d1 = d2;
   }
   *P = p1; *dP = d1;
@@ -53,15 +71,15 @@ void legendre(int n, double x, double* P, double* dP) {
 void gauss_rule(int npts, vec& x, vec& w) {
   x.assign(npts, 0.0); w.assign(npts, 0.0);
   for (int i = 0; i < (npts + 1) / 2; ++i) {
-    double z = std::cos(M_PI * (i + 0.75) / (npts + 0.5));
+    real z = std::cos(M_PI * (i + 0.75) / (npts + 0.5));
     for (int it = 0; it < 100; ++it) {
-      double P, dP; legendre(npts, z, &P, &dP);
-      double dz = P / dP;
+      real P, dP; legendre(npts, z, &P, &dP);
+      real dz = P / dP;
       z -= dz;
-      if (std::fabs(dz) <= 1e-16) break;
+      if (fabs(dz) <= 1e-16) break;
     }
-    double P, dP; legendre(npts, z, &P, &dP);
-    double wt = 2.0 / ((1.0 - z * z) * dP * dP);
+    real P, dP; legendre(npts, z, &P, &dP);
+    real wt = 2.0 / ((1.0 - z * z) * dP * dP);
     x[npts - 1 - i] = z; x[i] = -z;
     w[npts - 1 - i] = wt; w[i] = wt;
   }
@@ -75,37 +93,37 @@ void gll_rule(int r, vec& x, vec& w) {
   x.assign(r + 1, 0.0); w.assign(r + 1, 0.0);
   x[0] = -1.0; x[r] = 1.0;
   for (int i = 1; i <= r / 2; ++i) {
-    double z = std::cos(M_PI * i / r);
+    real z = std::cos(M_PI * i / r);
     for (int it = 0; it < 100; ++it) {
-      double P, dP; legendre(r, z, &P, &dP);
-      double d2P = (2.0 * z * dP - r * (r + 1.0) * P) / (1.0 - z * z);  // Legendre ODE
-      double dz = dP / d2P;
+      real P, dP; legendre(r, z, &P, &dP);
+      real d2P = (2.0 * z * dP - r * (r + 1.0) * P) / (1.0 - z * z);  // Legendre ODE
+      real dz = dP / d2P;
       z -= dz;
-      if (std::fabs(dz) <= 1e-16) break;
+      if (fabs(dz) <= 1e-16) break;
     }
     x[r - i] = z; x[i] = -z;
   }
   if (r % 2 == 0) x[r / 2] = 0.0;
   for (int i = 0; i <= r; ++i) {
-    double P, dP; legendre(r, x[i], &P, &dP);
+    real P, dP; legendre(r, x[i], &P, &dP);
     w[i] = 2.0 / (r * (r + 1.0) * P * P);
   }
 }
 
 // Lagrange basis l_j on `nodes` evaluated at x (product formula).
-double lag(const vec& nodes, int j, double x) {
-  double v = 1.0;
+real lag(const vec& nodes, int j, real x) {
+  real v = 1.0;
   for (int k = 0; k < (int)nodes.size(); ++k)
     if (k != j) v *= (x - nodes[k]) / (nodes[j] - nodes[k]);
   return v;
 }
 
 // Derivative of l_j at x (product rule written out).
-double dlag(const vec& nodes, int j, double x) {
-  double s = 0.0;
+real dlag(const vec& nodes, int j, real x) {
+  real s = 0.0;
   for (int l = 0; l < (int)nodes.size(); ++l) {
     if (l == j) continue;
-    double t = 1.0 / (nodes[j] - nodes[l]);
+    real t = 1.0 / (nodes[j] - nodes[l]);
     for (int k = 0; k < (int)nodes.size(); ++k)
       if (k != j && k != l) t *= (x - nodes[k]) / (nodes[j] - nodes[k]);
     s += t;
@@ -118,15 +136,15 @@ double dlag(const vec& nodes, int j, double x) {
 // ---------------------------------------------------------------------------
 
 // Pressure from the mechanical-energy variables (§3.2, p = (g-1)(E - |m|^2/(2 rho))).
-double pressure(const double U[5], double g) {
+real pressure(const real U[5], real g) {
   return (g - 1.0) * (U[4] - (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / (2.0 * U[0]));
 }
 
 // Physical Euler flux F_d(U), d = 0 (x) or 1 (y) (§3.2).
-void phys_flux(int d, const double U[5], double g, double F[5]) {
-  double rho = U[0], ux = U[1] / rho, uy = U[2] / rho;
-  double p = pressure(U, g);
-  double ud = d == 0 ? ux : uy;
+void phys_flux(int d, const real U[5], real g, real F[5]) {
+  real rho = U[0], ux = U[1] / rho, uy = U[2] / rho;
+  real p = pressure(U, g);
+  real ud = d == 0 ? ux : uy;
   F[0] = U[1 + d];
   F[1] = U[1] * ud + (d == 0 ? p : 0.0);
   F[2] = U[2] * ud + (d == 1 ? p : 0.0);
@@ -136,39 +154,39 @@ void phys_flux(int d, const double U[5], double g, double F[5]) {
 
 // Logarithmic mean with the continuous extension a_L = a_R (reading R1:
 // series for small (a_L-a_R)/(a_L+a_R), Ismail & Roe 2009, switch at u = 1e-4).
-double log_mean(double aL, double aR) {
-  double zeta = aL / aR;
-  double f = (zeta - 1.0) / (zeta + 1.0);
-  double u = f * f;
-  double F;
+real log_mean(real aL, real aR) {
+  real zeta = aL / aR;
+  real f = (zeta - 1.0) / (zeta + 1.0);
+  real u = f * f;
+  real F;
   if (u < 1e-4)
     F = 1.0 + u / 3.0 + u * u / 5.0 + u * u * u / 7.0;
   else
-    F = std::log(zeta) / (2.0 * f);
+    F = log(zeta) / (2.0 * f);
   return (aL + aR) / (2.0 * F);
 }
 
 // Chandrashekar's entropy-conservative two-point flux, 2.5D form
 // (eq. euler-chandrashekar-flux), beta = rho/(2p).
-void ec_flux(int d, const double UL[5], const double UR[5], double g, double F[5]) {
-  double rL = UL[0], rR = UR[0];
-  double uL[3] = {UL[1] / rL, UL[2] / rL, UL[3] / rL};
-  double uR[3] = {UR[1] / rR, UR[2] / rR, UR[3] / rR};
-  double pL = pressure(UL, g), pR = pressure(UR, g);
-  double bL = rL / (2.0 * pL), bR = rR / (2.0 * pR);
-  double r_avg = 0.5 * (rL + rR);
-  double b_avg = 0.5 * (bL + bR);
-  double u_avg[3];
+void ec_flux(int d, const real UL[5], const real UR[5], real g, real F[5]) {
+  real rL = UL[0], rR = UR[0];
+  real uL[3] = {UL[1] / rL, UL[2] / rL, UL[3] / rL};
+  real uR[3] = {UR[1] / rR, UR[2] / rR, UR[3] / rR};
+  real pL = pressure(UL, g), pR = pressure(UR, g);
+  real bL = rL / (2.0 * pL), bR = rR / (2.0 * pR);
+  real r_avg = 0.5 * (rL + rR);
+  real b_avg = 0.5 * (bL + bR);
+  real u_avg[3];
   for (int c = 0; c < 3; ++c) u_avg[c] = 0.5 * (uL[c] + uR[c]);
-  double u2L = uL[0] * uL[0] + uL[1] * uL[1] + uL[2] * uL[2];
-  double u2R = uR[0] * uR[0] + uR[1] * uR[1] + uR[2] * uR[2];
-  double u2_avg = 0.5 * (u2L + u2R);                                        // {{|u|^2}}
-  double avg_u_sq = u_avg[0] * u_avg[0] + u_avg[1] * u_avg[1] + u_avg[2] * u_avg[2];  // |{{u}}|^2
-  double r_log = log_mean(rL, rR);
-  double b_log = log_mean(bL, bR);
-  double p_hat = r_avg / (2.0 * b_avg);
-  double h_hat = 1.0 / (2.0 * (g - 1.0) * b_log) - 0.5 * u2_avg + avg_u_sq + p_hat / r_log;
-  double ud = u_avg[d];
+  real u2L = uL[0] * uL[0] + uL[1] * uL[1] + uL[2] * uL[2];
+  real u2R = uR[0] * uR[0] + uR[1] * uR[1] + uR[2] * uR[2];
+  real u2_avg = 0.5 * (u2L + u2R);                                        // {{|u|^2}}
+  real avg_u_sq = u_avg[0] * u_avg[0] + u_avg[1] * u_avg[1] + u_avg[2] * u_avg[2];  // |{{u}}|^2
+  real r_log = log_mean(rL, rR);
+  real b_log = log_mean(bL, bR);
+  real p_hat = r_avg / (2.0 * b_avg);
+  real h_hat = 1.0 / (2.0 * (g - 1.0) * b_log) - 0.5 * u2_avg + avg_u_sq + p_hat / r_log;
+  real ud = u_avg[d];
   F[0] = r_log * ud;
   F[1] = r_log * u_avg[0] * ud + (d == 0 ? p_hat : 0.0);
   F[2] = r_log * u_avg[1] * ud + (d == 1 ? p_hat : 0.0);
@@ -177,19 +195,19 @@ void ec_flux(int d, const double UL[5], const double UR[5], double g, double F[5
 }
 
 // Local Lax-Friedrichs flux (eq. euler-lf-flux) with acoustic c = sqrt(g p / rho).
-void llf_flux(int d, const double Um[5], const double Up[5], double g, double F[5]) {
-  double Fm[5], Fp[5];
+void llf_flux(int d, const real Um[5], const real Up[5], real g, real F[5]) {
+  real Fm[5], Fp[5];
   phys_flux(d, Um, g, Fm);
   phys_flux(d, Up, g, Fp);
-  double sm = std::fabs(Um[1 + d] / Um[0]) + std::sqrt(g * pressure(Um, g) / Um[0]);
-  double sp = std::fabs(Up[1 + d] / Up[0]) + std::sqrt(g * pressure(Up, g) / Up[0]);
-  double lam = std::max(sm, sp);
+  real sm = fabs(Um[1 + d] / Um[0]) + sqrt(g * pressure(Um, g) / Um[0]);
+  real sp = fabs(Up[1 + d] / Up[0]) + sqrt(g * pressure(Up, g) / Up[0]);
+  real lam = std::max(sm, sp);
   for (int c = 0; c < 5; ++c) F[c] = 0.5 * (Fm[c] + Fp[c]) - 0.5 * lam * (Up[c] - Um[c]);
 }
 
 struct Params {
   int oe_hydro, oe_vel, pp, ar;
-  double s_H, s_M, C_s, C_eta, cfl;
+  real s_H, s_M, C_s, C_eta, cfl;
   int max_halvings;
   int ec_faces;  // test hook: entropy-conservative flux on faces instead of LLF
 };
@@ -201,7 +219,7 @@ enum { OR_OK = 0, OR_RETRIED = 1, OR_REJECT = -10, OR_INADMISSIBLE = -11 };
 // ---------------------------------------------------------------------------
 struct Oracle {
   int nx, ny, K, p, m, n, n2, mm, mL, NX, NY;
-  double x0, x1, y0, y1, hx, hy, Jdet, g;
+  real x0, x1, y0, y1, hx, hy, Jdet, g;
   Params prm;
   vec xp, wp;  // GLL(p): DG nodes
   vec xL, wL;  // GLL(m+1): W nodes, continuous direction of N and R
@@ -217,9 +235,9 @@ struct Oracle {
   int emod(int e, int N) const { return ((e % N) + N) % N; }
   int kid(int ex, int ey) const { return emod(ey, ny) * nx + emod(ex, nx); }
   int gidx(int X, int Y) const { return emod(Y, NY) * NX + emod(X, NX); }
-  double Q(int i, int r) const { return wp[i] * D[i * n + r]; }  // Q = M D
+  real Q(int i, int r) const { return wp[i] * D[i * n + r]; }  // Q = M D
 
-  void init(int nx_, int ny_, double x0_, double x1_, double y0_, double y1_, int p_, int m_, double g_) {
+  void init(int nx_, int ny_, real x0_, real x1_, real y0_, real y1_, int p_, int m_, real g_) {
     nx = nx_; ny = ny_; K = nx * ny; p = p_; m = m_; n = p + 1; n2 = n * n;
     mm = m + 1; mL = m + 2; NX = nx * mm; NY = ny * mm;
     x0 = x0_; x1 = x1_; y0 = y0_; y1 = y1_;
@@ -241,52 +259,52 @@ struct Oracle {
 
   // ---- element closures of the compatible fields --------------------------
   // "X-type": GLL(m+1) in x (a = 0..m+1), Gauss(m) in y (b = 0..m): B_x, E_y, J_y
-  void clX(const vec& A, int ex, int ey, double* c) const {
+  void clX(const vec& A, int ex, int ey, real* c) const {
     for (int b = 0; b < mm; ++b)
       for (int a = 0; a < mL; ++a) c[b * mL + a] = A[gidx(ex * mm + a, ey * mm + b)];
   }
   // "Y-type": Gauss(m) in x (a = 0..m), GLL(m+1) in y (b = 0..m+1): B_y, E_x, J_x
-  void clY(const vec& A, int ex, int ey, double* c) const {
+  void clY(const vec& A, int ex, int ey, real* c) const {
     for (int b = 0; b < mL; ++b)
       for (int a = 0; a < mm; ++a) c[b * mm + a] = A[gidx(ex * mm + a, ey * mm + b)];
   }
   // "W-type": GLL(m+1) in both directions: E_z, J_z, potentials
-  void clW(const vec& A, int ex, int ey, double* c) const {
+  void clW(const vec& A, int ex, int ey, real* c) const {
     for (int b = 0; b < mL; ++b)
       for (int a = 0; a < mL; ++a) c[b * mL + a] = A[gidx(ex * mm + a, ey * mm + b)];
   }
 
   // Tensor-product evaluation sum_{a,b} c[b][a] phi_a(x) psi_b(y); dx/dy select
   // reference derivatives.
-  static double ev(const double* c, const vec& nx_, const vec& ny_, double x, double y, int dx, int dy) {
-    double s = 0.0;
+  static real ev(const real* c, const vec& nx_, const vec& ny_, real x, real y, int dx, int dy) {
+    real s = 0.0;
     int na = nx_.size(), nb = ny_.size();
-    double fx[16];
+    real fx[16];
     for (int a = 0; a < na; ++a) fx[a] = dx ? dlag(nx_, a, x) : lag(nx_, a, x);
     for (int b = 0; b < nb; ++b) {
-      double fy = dy ? dlag(ny_, b, y) : lag(ny_, b, y);
+      real fy = dy ? dlag(ny_, b, y) : lag(ny_, b, y);
       for (int a = 0; a < na; ++a) s += c[b * na + a] * fx[a] * fy;
     }
     return s;
   }
-  double evX(const double* c, double x, double y, int dx = 0, int dy = 0) const { return ev(c, xL, zG, x, y, dx, dy); }
-  double evY(const double* c, double x, double y, int dx = 0, int dy = 0) const { return ev(c, zG, xL, x, y, dx, dy); }
-  double evW(const double* c, double x, double y, int dx = 0, int dy = 0) const { return ev(c, xL, xL, x, y, dx, dy); }
-  double evZ(const double* c, double x, double y, int dx = 0, int dy = 0) const { return ev(c, xM, xM, x, y, dx, dy); }
-  double evDG(const double* c, double x, double y) const { return ev(c, xp, xp, x, y, 0, 0); }
+  real evX(const real* c, real x, real y, int dx = 0, int dy = 0) const { return ev(c, xL, zG, x, y, dx, dy); }
+  real evY(const real* c, real x, real y, int dx = 0, int dy = 0) const { return ev(c, zG, xL, x, y, dx, dy); }
+  real evW(const real* c, real x, real y, int dx = 0, int dy = 0) const { return ev(c, xL, xL, x, y, dx, dy); }
+  real evZ(const real* c, real x, real y, int dx = 0, int dy = 0) const { return ev(c, xM, xM, x, y, dx, dy); }
+  real evDG(const real* c, real x, real y) const { return ev(c, xp, xp, x, y, 0, 0); }
 
   // B_h of element (ex,ey) at reference point (x,y).
-  void B_at(const double* bx, const double* by, const double* bz, double x, double y, double B[3]) const {
+  void B_at(const real* bx, const real* by, const real* bz, real x, real y, real B[3]) const {
     B[0] = evX(bx, x, y); B[1] = evY(by, x, y); B[2] = evZ(bz, x, y);
   }
 
   // ------------------------------------------------------------------------
   // Hydro residual L_E (eq. euler-nodal-index with eq. euler-volume-residual)
   // ------------------------------------------------------------------------
-  void node_state(const vec* S, int k, int i, int j, double u[5]) const {
+  void node_state(const vec* S, int k, int i, int j, real u[5]) const {
     for (int c = 0; c < 5; ++c) u[c] = S[c][(size_t)k * n2 + j * n + i];
   }
-  void face_flux(int d, const double Um[5], const double Up[5], double F[5]) const {
+  void face_flux(int d, const real Um[5], const real Up[5], real F[5]) const {
     if (prm.ec_faces) ec_flux(d, Um, Up, g, F);
     else llf_flux(d, Um, Up, g, F);
   }
@@ -297,7 +315,7 @@ struct Oracle {
         int k = kid(ex, ey);
         for (int j = 0; j < n; ++j)
           for (int i = 0; i < n; ++i) {
-            double Ui[5], Ur[5], F[5], Fs[5], R[5] = {0, 0, 0, 0, 0};
+            real Ui[5], Ur[5], F[5], Fs[5], R[5] = {0, 0, 0, 0, 0};
             node_state(S, k, i, j, Ui);
             for (int r = 0; r < n; ++r) {  // x-direction volume term
               node_state(S, k, r, j, Ur);
@@ -311,35 +329,35 @@ struct Oracle {
             }
             // interface terms: Delta F~ = F~ - F~*, traces ordered in +x / +y
             if (i == 0) {
-              double Um[5]; node_state(S, kid(ex - 1, ey), p, j, Um);
+              real Um[5]; node_state(S, kid(ex - 1, ey), p, j, Um);
               face_flux(0, Um, Ui, Fs); phys_flux(0, Ui, g, F);
               for (int c = 0; c < 5; ++c) R[c] += wp[j] * (hy / 2.0) * (F[c] - Fs[c]);
             }
             if (i == p) {
-              double Up[5]; node_state(S, kid(ex + 1, ey), 0, j, Up);
+              real Up[5]; node_state(S, kid(ex + 1, ey), 0, j, Up);
               face_flux(0, Ui, Up, Fs); phys_flux(0, Ui, g, F);
               for (int c = 0; c < 5; ++c) R[c] -= wp[j] * (hy / 2.0) * (F[c] - Fs[c]);
             }
             if (j == 0) {
-              double Um[5]; node_state(S, kid(ex, ey - 1), i, p, Um);
+              real Um[5]; node_state(S, kid(ex, ey - 1), i, p, Um);
               face_flux(1, Um, Ui, Fs); phys_flux(1, Ui, g, F);
               for (int c = 0; c < 5; ++c) R[c] += wp[i] * (hx / 2.0) * (F[c] - Fs[c]);
             }
             if (j == p) {
-              double Up[5]; node_state(S, kid(ex, ey + 1), i, 0, Up);
+              real Up[5]; node_state(S, kid(ex, ey + 1), i, 0, Up);
               face_flux(1, Ui, Up, Fs); phys_flux(1, Ui, g, F);
               for (int c = 0; c < 5; ++c) R[c] -= wp[i] * (hx / 2.0) * (F[c] - Fs[c]);
             }
-            double M = Jdet * wp[i] * wp[j];
+            real M = Jdet * wp[i] * wp[j];
             for (int c = 0; c < 5; ++c) L[c][(size_t)k * n2 + j * n + i] = -R[c] / M;
           }
       }
   }
 
   // Quadrature-weighted element average (eq. euler-pp-average): sum M U / |K|.
-  void element_average(const vec* S, int k, double avg[5]) const {
+  void element_average(const vec* S, int k, real avg[5]) const {
     for (int c = 0; c < 5; ++c) {
-      double s = 0.0;
+      real s = 0.0;
       for (int j = 0; j < n; ++j)
         for (int i = 0; i < n; ++i) s += Jdet * wp[i] * wp[j] * S[c][(size_t)k * n2 + j * n + i];
       avg[c] = s / (4.0 * Jdet);
@@ -349,27 +367,27 @@ struct Oracle {
   // Raw-average admissibility check before the stage map (§3.2.3, reading R9).
   bool averages_admissible(const vec* S) const {
     for (int k = 0; k < K; ++k) {
-      double a[5]; element_average(S, k, a);
+      real a[5]; element_average(S, k, a);
       bool finite = true;
-      for (int c = 0; c < 5; ++c) finite = finite && std::isfinite(a[c]);
+      for (int c = 0; c < 5; ++c) finite = finite && isfinite(a[c]);
       if (!finite || !(a[0] > 0.0) || !(pressure(a, g) > 0.0)) return false;
     }
     return true;
   }
 
   // Stage map P = P_PP o P_OE (eq. euler-stage-map); the pieces are below.
-  void hydro_stage_map(vec* S, double tau);
+  void hydro_stage_map(vec* S, real tau);
 
   // Hydro substep Phi_H^tau (Algorithm 1, eq. euler-ssprk33).
-  int hydro_substep(double tau) {
+  int hydro_substep(real tau) {
     vec U0[5], S[5], L[5], C[5];
     for (int c = 0; c < 5; ++c) { U0[c] = U[c]; S[c] = U[c]; L[c].assign(U[c].size(), 0.0); C[c] = U[c]; }
-    const double a[3] = {0.0, 0.75, 1.0 / 3.0}, b[3] = {1.0, 0.25, 2.0 / 3.0};
+    const real a[3] = {0.0, 0.75, 1.0 / 3.0}, b[3] = {1.0, 0.25, 2.0 / 3.0};
     for (int s = 0; s < 3; ++s) {
       hydro_rhs(S, L);
       for (int c = 0; c < 5; ++c)
         for (size_t q = 0; q < C[c].size(); ++q) {
-          double raw = S[c][q] + tau * L[c][q];
+          real raw = S[c][q] + tau * L[c][q];
           C[c][q] = (s == 0) ? raw : a[s] * U0[c][q] + b[s] * raw;
         }
       if (!averages_admissible(C)) return OR_REJECT;
@@ -391,14 +409,14 @@ struct Oracle {
   void compute_J(const vec& bX, const vec& bY, const vec& bZ, vec& Jx, vec& Jy, vec& Jz) const {
     size_t G = (size_t)NX * NY;
     vec lx(G, 0.0), ly(G, 0.0), lz(G, 0.0), mx(G, 0.0), my(G, 0.0), mz(G, 0.0);
-    std::vector<double> bx(mL * mm), by(mm * mL);
+    std::vector<real> bx(mL * mm), by(mm * mL);
     for (int ey = 0; ey < ny; ++ey)
       for (int ex = 0; ex < nx; ++ex) {
         int k = kid(ex, ey);
         clX(bX, ex, ey, bx.data()); clY(bY, ex, ey, by.data());
-        const double* bz = &bZ[(size_t)k * mm * mm];
+        const real* bz = &bZ[(size_t)k * mm * mm];
         // W block: (J_z, phi)_W = (B_x, d_y phi)_B - (B_y, d_x phi)_B
-        std::vector<double> bxq(mL * mL), byq(mL * mL), bzq(mm * mm);
+        std::vector<real> bxq(mL * mL), byq(mL * mL), bzq(mm * mm);
         for (int qy = 0; qy < mL; ++qy)
           for (int qx = 0; qx < mL; ++qx) {
             bxq[qy * mL + qx] = evX(bx.data(), z2[qx], z2[qy]);
@@ -407,16 +425,16 @@ struct Oracle {
         for (int qy = 0; qy < mm; ++qy)
           for (int qx = 0; qx < mm; ++qx) bzq[qy * mm + qx] = evZ(bz, zG[qx], zG[qy]);
         // GLL(m+1) basis and derivative at the Gauss(m+2) points
-        std::vector<double> Lq(mL * mL), dLq(mL * mL);
+        std::vector<real> Lq(mL * mL), dLq(mL * mL);
         for (int a = 0; a < mL; ++a)
           for (int q = 0; q < mL; ++q) { Lq[a * mL + q] = lag(xL, a, z2[q]); dLq[a * mL + q] = dlag(xL, a, z2[q]); }
         for (int b = 0; b < mL; ++b)
           for (int a = 0; a < mL; ++a) {
-            double s = 0.0;
+            real s = 0.0;
             for (int qy = 0; qy < mL; ++qy)
               for (int qx = 0; qx < mL; ++qx) {
-                double dyphi = (2.0 / hy) * Lq[a * mL + qx] * dLq[b * mL + qy];
-                double dxphi = (2.0 / hx) * dLq[a * mL + qx] * Lq[b * mL + qy];
+                real dyphi = (2.0 / hy) * Lq[a * mL + qx] * dLq[b * mL + qy];
+                real dxphi = (2.0 / hx) * dLq[a * mL + qx] * Lq[b * mL + qy];
                 s += Jdet * w2[qx] * w2[qy] * (bxq[qy * mL + qx] * dyphi - byq[qy * mL + qx] * dxphi);
               }
             size_t gi = gidx(ex * mm + a, ey * mm + b);
@@ -425,11 +443,11 @@ struct Oracle {
         // N block, x-component: DOF g_a(x) l_b(y) e_x; (J_x, phi)_N = (B_z, -d_y phi)_B
         for (int b = 0; b < mL; ++b)
           for (int a = 0; a < mm; ++a) {
-            double s = 0.0;
+            real s = 0.0;
             for (int qy = 0; qy < mm; ++qy)
               for (int qx = 0; qx < mm; ++qx) {
-                double X = zG[qx], Y = zG[qy];
-                double dyphi = (2.0 / hy) * lag(zG, a, X) * dlag(xL, b, Y);
+                real X = zG[qx], Y = zG[qy];
+                real dyphi = (2.0 / hy) * lag(zG, a, X) * dlag(xL, b, Y);
                 s += Jdet * wG[qx] * wG[qy] * bzq[qy * mm + qx] * (-dyphi);
               }
             size_t gi = gidx(ex * mm + a, ey * mm + b);
@@ -438,11 +456,11 @@ struct Oracle {
         // N block, y-component: DOF l_a(x) g_b(y) e_y; (J_y, phi)_N = (B_z, d_x phi)_B
         for (int b = 0; b < mm; ++b)
           for (int a = 0; a < mL; ++a) {
-            double s = 0.0;
+            real s = 0.0;
             for (int qy = 0; qy < mm; ++qy)
               for (int qx = 0; qx < mm; ++qx) {
-                double X = zG[qx], Y = zG[qy];
-                double dxphi = (2.0 / hx) * dlag(xL, a, X) * lag(zG, b, Y);
+                real X = zG[qx], Y = zG[qy];
+                real dxphi = (2.0 / hx) * dlag(xL, a, X) * lag(zG, b, Y);
                 s += Jdet * wG[qx] * wG[qy] * bzq[qy * mm + qx] * dxphi;
               }
             size_t gi = gidx(ex * mm + a, ey * mm + b);
@@ -461,19 +479,19 @@ struct Oracle {
                  const vec& Jx, const vec& Jy, const vec& Jz, vec& Ex, vec& Ey, vec& Ez) const {
     size_t G = (size_t)NX * NY;
     vec lx(G, 0.0), ly(G, 0.0), lz(G, 0.0), mx(G, 0.0), my(G, 0.0), mz(G, 0.0);
-    std::vector<double> bx(mL * mm), by(mm * mL), jx(mm * mL), jy(mL * mm), jz(mL * mL);
+    std::vector<real> bx(mL * mm), by(mm * mL), jx(mm * mL), jy(mL * mm), jz(mL * mL);
     for (int ey = 0; ey < ny; ++ey)
       for (int ex = 0; ex < nx; ++ex) {
         int k = kid(ex, ey);
         clX(bX, ex, ey, bx.data()); clY(bY, ex, ey, by.data());
         clY(Jx, ex, ey, jx.data()); clX(Jy, ex, ey, jy.data()); clW(Jz, ex, ey, jz.data());
-        const double* bz = &bZ[(size_t)k * mm * mm];
-        const double* ux = &u[0][(size_t)k * n2];
-        const double* uy = &u[1][(size_t)k * n2];
-        const double* uz = &u[2][(size_t)k * n2];
-        double ek = etaK[k];
+        const real* bz = &bZ[(size_t)k * mm * mm];
+        const real* ux = &u[0][(size_t)k * n2];
+        const real* uy = &u[1][(size_t)k * n2];
+        const real* uz = &u[2][(size_t)k * n2];
+        real ek = etaK[k];
         // resistive field J_h at the DG-GLL(p) nodes of this element
-        std::vector<double> Jq(3 * n2);
+        std::vector<real> Jq(3 * n2);
         for (int j = 0; j < n; ++j)
           for (int i = 0; i < n; ++i) {
             Jq[0 * n2 + j * n + i] = evY(jx.data(), xp[i], xp[j]);
@@ -483,14 +501,14 @@ struct Oracle {
         // x-component at N_x nodes (zeta_a, xi^L_b)
         for (int b = 0; b < mL; ++b)
           for (int a = 0; a < mm; ++a) {
-            double X = zG[a], Y = xL[b], B[3];
+            real X = zG[a], Y = xL[b], B[3];
             B_at(bx.data(), by.data(), bz, X, Y, B);
-            double vy = evDG(uy, X, Y), vz = evDG(uz, X, Y);
-            double val = -(vy * B[2] - vz * B[1]);
-            double w = Jdet * wG[a] * wL[b];
-            double load = w * val;
+            real vy = evDG(uy, X, Y), vz = evDG(uz, X, Y);
+            real val = -(vy * B[2] - vz * B[1]);
+            real w = Jdet * wG[a] * wL[b];
+            real load = w * val;
             if (ek != 0.0) {
-              double r = 0.0;
+              real r = 0.0;
               for (int j = 0; j < n; ++j)
                 for (int i = 0; i < n; ++i)
                   r += Jdet * wp[i] * wp[j] * Jq[0 * n2 + j * n + i] * lag(zG, a, xp[i]) * lag(xL, b, xp[j]);
@@ -502,14 +520,14 @@ struct Oracle {
         // y-component at N_y nodes (xi^L_a, zeta_b)
         for (int b = 0; b < mm; ++b)
           for (int a = 0; a < mL; ++a) {
-            double X = xL[a], Y = zG[b], B[3];
+            real X = xL[a], Y = zG[b], B[3];
             B_at(bx.data(), by.data(), bz, X, Y, B);
-            double vx = evDG(ux, X, Y), vz = evDG(uz, X, Y);
-            double val = -(vz * B[0] - vx * B[2]);
-            double w = Jdet * wL[a] * wG[b];
-            double load = w * val;
+            real vx = evDG(ux, X, Y), vz = evDG(uz, X, Y);
+            real val = -(vz * B[0] - vx * B[2]);
+            real w = Jdet * wL[a] * wG[b];
+            real load = w * val;
             if (ek != 0.0) {
-              double r = 0.0;
+              real r = 0.0;
               for (int j = 0; j < n; ++j)
                 for (int i = 0; i < n; ++i)
                   r += Jdet * wp[i] * wp[j] * Jq[1 * n2 + j * n + i] * lag(xL, a, xp[i]) * lag(zG, b, xp[j]);
@@ -521,14 +539,14 @@ struct Oracle {
         // z-component at W nodes (xi^L_a, xi^L_b)
         for (int b = 0; b < mL; ++b)
           for (int a = 0; a < mL; ++a) {
-            double X = xL[a], Y = xL[b], B[3];
+            real X = xL[a], Y = xL[b], B[3];
             B_at(bx.data(), by.data(), bz, X, Y, B);
-            double vx = evDG(ux, X, Y), vy = evDG(uy, X, Y);
-            double val = -(vx * B[1] - vy * B[0]);
-            double w = Jdet * wL[a] * wL[b];
-            double load = w * val;
+            real vx = evDG(ux, X, Y), vy = evDG(uy, X, Y);
+            real val = -(vx * B[1] - vy * B[0]);
+            real w = Jdet * wL[a] * wL[b];
+            real load = w * val;
             if (ek != 0.0) {
-              double r = 0.0;
+              real r = 0.0;
               for (int j = 0; j < n; ++j)
                 for (int i = 0; i < n; ++i)
                   r += Jdet * wp[i] * wp[j] * Jq[2 * n2 + j * n + i] * lag(xL, a, xp[i]) * lag(xL, b, xp[j]);
@@ -553,7 +571,7 @@ struct Oracle {
     dY.e.assign((size_t)K * n2, 0.0);
     for (int d = 0; d < 3; ++d) dY.u[d].assign((size_t)K * n2, 0.0);
     dY.Bx.assign(G, 0.0); dY.By.assign(G, 0.0); dY.Bz.assign((size_t)K * mm * mm, 0.0);
-    std::vector<double> bx(mL * mm), by(mm * mL), jx(mm * mL), jy(mL * mm), jz(mL * mL),
+    std::vector<real> bx(mL * mm), by(mm * mL), jx(mm * mL), jy(mL * mm), jz(mL * mL),
         exc(mm * mL), eyc(mL * mm), ezc(mL * mL);
     for (int ey = 0; ey < ny; ++ey)
       for (int ex = 0; ex < nx; ++ex) {
@@ -561,19 +579,19 @@ struct Oracle {
         clX(Y.Bx, ex, ey, bx.data()); clY(Y.By, ex, ey, by.data());
         clY(Jx, ex, ey, jx.data()); clX(Jy, ex, ey, jy.data()); clW(Jz, ex, ey, jz.data());
         clY(Ex, ex, ey, exc.data()); clX(Ey, ex, ey, eyc.data()); clW(Ez, ex, ey, ezc.data());
-        const double* bz = &Y.Bz[(size_t)k * mm * mm];
+        const real* bz = &Y.Bz[(size_t)k * mm * mm];
         // -curl E on the DOFs owned by this element: dB_par = grad^perp E_z
         for (int b = 0; b < mm; ++b)
           for (int a = 0; a < mm; ++a) {
             dY.Bx[gidx(ex * mm + a, ey * mm + b)] = -(2.0 / hy) * evW(ezc.data(), xL[a], zG[b], 0, 1);
             dY.By[gidx(ex * mm + a, ey * mm + b)] = (2.0 / hx) * evW(ezc.data(), zG[a], xL[b], 1, 0);
-            double dEy_dx = (2.0 / hx) * evX(eyc.data(), xM[a], xM[b], 1, 0);
-            double dEx_dy = (2.0 / hy) * evY(exc.data(), xM[a], xM[b], 0, 1);
+            real dEy_dx = (2.0 / hx) * evX(eyc.data(), xM[a], xM[b], 1, 0);
+            real dEx_dy = (2.0 / hy) * evY(exc.data(), xM[a], xM[b], 0, 1);
             dY.Bz[(size_t)k * mm * mm + b * mm + a] = -(dEy_dx - dEx_dy);
           }
         // Lorentz load: algebraic transpose of C_h (eq. semi-vel), Ohmic heating (eq. ohmic-heating)
         // B_h of this element at its auxiliary nodes (N_x, N_y and W families)
-        std::vector<double> Bnx(3 * mL * mm), Bny(3 * mL * mm), Bw(3 * mL * mL);
+        std::vector<real> Bnx(3 * mL * mm), Bny(3 * mL * mm), Bw(3 * mL * mL);
         for (int b = 0; b < mL; ++b)
           for (int a = 0; a < mm; ++a) B_at(bx.data(), by.data(), bz, zG[a], xL[b], &Bnx[3 * (b * mm + a)]);
         for (int b = 0; b < mm; ++b)
@@ -582,55 +600,55 @@ struct Oracle {
           for (int a = 0; a < mL; ++a) B_at(bx.data(), by.data(), bz, xL[a], xL[b], &Bw[3 * (b * mL + a)]);
         for (int j = 0; j < n; ++j)
           for (int i = 0; i < n; ++i) {
-            double sx = 0.0, sy = 0.0, sz = 0.0;
+            real sx = 0.0, sy = 0.0, sz = 0.0;
             for (int b = 0; b < mL; ++b)  // N_x nodes
               for (int a = 0; a < mm; ++a) {
-                double X = zG[a], Yq = xL[b];
-                const double* B = &Bnx[3 * (b * mm + a)];
-                double w = Jdet * wG[a] * wL[b] * lag(xp, i, X) * lag(xp, j, Yq);
-                double jv = jx[b * mm + a];
+                real X = zG[a], Yq = xL[b];
+                const real* B = &Bnx[3 * (b * mm + a)];
+                real w = Jdet * wG[a] * wL[b] * lag(xp, i, X) * lag(xp, j, Yq);
+                real jv = jx[b * mm + a];
                 sy += -w * B[2] * jv;
                 sz += w * B[1] * jv;
               }
             for (int b = 0; b < mm; ++b)  // N_y nodes
               for (int a = 0; a < mL; ++a) {
-                double X = xL[a], Yq = zG[b];
-                const double* B = &Bny[3 * (b * mL + a)];
-                double w = Jdet * wL[a] * wG[b] * lag(xp, i, X) * lag(xp, j, Yq);
-                double jv = jy[b * mL + a];
+                real X = xL[a], Yq = zG[b];
+                const real* B = &Bny[3 * (b * mL + a)];
+                real w = Jdet * wL[a] * wG[b] * lag(xp, i, X) * lag(xp, j, Yq);
+                real jv = jy[b * mL + a];
                 sx += w * B[2] * jv;
                 sz += -w * B[0] * jv;
               }
             for (int b = 0; b < mL; ++b)  // W nodes
               for (int a = 0; a < mL; ++a) {
-                double X = xL[a], Yq = xL[b];
-                const double* B = &Bw[3 * (b * mL + a)];
-                double w = Jdet * wL[a] * wL[b] * lag(xp, i, X) * lag(xp, j, Yq);
-                double jv = jz[b * mL + a];
+                real X = xL[a], Yq = xL[b];
+                const real* B = &Bw[3 * (b * mL + a)];
+                real w = Jdet * wL[a] * wL[b] * lag(xp, i, X) * lag(xp, j, Yq);
+                real jv = jz[b * mL + a];
                 sx += -w * B[1] * jv;
                 sy += w * B[0] * jv;
               }
             size_t q = (size_t)k * n2 + j * n + i;
-            double M = Jdet * wp[i] * wp[j];
+            real M = Jdet * wp[i] * wp[j];
             dY.u[0][q] = sx / (rho[q] * M);
             dY.u[1][q] = sy / (rho[q] * M);
             dY.u[2][q] = sz / (rho[q] * M);
-            double jxq = evY(jx.data(), xp[i], xp[j]);
-            double jyq = evX(jy.data(), xp[i], xp[j]);
-            double jzq = evW(jz.data(), xp[i], xp[j]);
+            real jxq = evY(jx.data(), xp[i], xp[j]);
+            real jyq = evX(jy.data(), xp[i], xp[j]);
+            real jzq = evW(jz.data(), xp[i], xp[j]);
             dY.e[q] = etaK[k] * (jxq * jxq + jyq * jyq + jzq * jzq) / rho[q];
           }
       }
   }
 
   // Stabilisation pieces of the magnetic stage (velocity OE and A.R.).
-  void B_at_dg_state(const Mag& Y, int ex, int ey, int i, int j, double B[3]) const;
+  void B_at_dg_state(const Mag& Y, int ex, int ey, int i, int j, real B[3]) const;
   void ar_coefficient(const vec& rho, const Mag& Y, vec& etaK) const;
   struct VelProj;
-  void vel_oe(const vec& rho, Mag& Y, double tau, const VelProj* P) const;
+  void vel_oe(const vec& rho, Mag& Y, real tau, const VelProj* P) const;
 
   // Magnetic substep Phi_M^tau (Algorithm 2, eq. magnetic-ssprk33).
-  int mag_substep(const vec& rho, Mag& Y, double tau);
+  int mag_substep(const vec& rho, Mag& Y, real tau);
 
   // Nodal exchange (§3.4.1).
   void cons_to_prim(Mag& Y) const {
@@ -638,8 +656,8 @@ struct Oracle {
     Y.e.assign(N, 0.0);
     for (int d = 0; d < 3; ++d) Y.u[d].assign(N, 0.0);
     for (size_t q = 0; q < N; ++q) {
-      double rho = U[0][q];
-      double ux = U[1][q] / rho, uy = U[2][q] / rho, uz = U[3][q] / rho;
+      real rho = U[0][q];
+      real ux = U[1][q] / rho, uy = U[2][q] / rho, uz = U[3][q] / rho;
       Y.u[0][q] = ux; Y.u[1][q] = uy; Y.u[2][q] = uz;
       Y.e[q] = (U[4][q] - 0.5 * rho * (ux * ux + uy * uy + uz * uz)) / rho;
     }
@@ -648,15 +666,15 @@ struct Oracle {
   void prim_to_cons(const Mag& Y) {
     size_t N = (size_t)K * n2;
     for (size_t q = 0; q < N; ++q) {
-      double rho = U[0][q];
-      double ux = Y.u[0][q], uy = Y.u[1][q], uz = Y.u[2][q];
+      real rho = U[0][q];
+      real ux = Y.u[0][q], uy = Y.u[1][q], uz = Y.u[2][q];
       U[1][q] = rho * ux; U[2][q] = rho * uy; U[3][q] = rho * uz;
       U[4][q] = rho * Y.e[q] + 0.5 * rho * (ux * ux + uy * uy + uz * uz);
     }
     Bx = Y.Bx; By = Y.By; Bz = Y.Bz;
   }
 
-  int run_mag(double tau) {
+  int run_mag(real tau) {
     Mag Y; cons_to_prim(Y);
     vec rho = U[0];
     int st = mag_substep(rho, Y, tau);
@@ -666,7 +684,7 @@ struct Oracle {
 
   // One Strang step (Algorithm 3, eq. strang-composition) with the rejection
   // and retry of reading R3.
-  int strang_step(double dt, double* dt_taken) {
+  int strang_step(real dt, real* dt_taken) {
     vec U0[5]; for (int c = 0; c < 5; ++c) U0[c] = U[c];
     vec B0x = Bx, B0y = By, B0z = Bz;
     last_rejections = 0;
@@ -688,25 +706,25 @@ struct Oracle {
   }
 
   // B_h at the DG node (i,j) of element (ex,ey).
-  void B_at_dg(int ex, int ey, int i, int j, double B[3]) const {
-    std::vector<double> bx(mL * mm), by(mm * mL);
+  void B_at_dg(int ex, int ey, int i, int j, real B[3]) const {
+    std::vector<real> bx(mL * mm), by(mm * mL);
     clX(Bx, ex, ey, bx.data()); clY(By, ex, ey, by.data());
     B_at(bx.data(), by.data(), &Bz[(size_t)kid(ex, ey) * mm * mm], xp[i], xp[j], B);
   }
 
   // CFL time step (reading R2).
-  double cfl_dt() const {
-    double mx = 0.0;
+  real cfl_dt() const {
+    real mx = 0.0;
     for (int ey = 0; ey < ny; ++ey)
       for (int ex = 0; ex < nx; ++ex) {
         int k = kid(ex, ey);
         for (int j = 0; j < n; ++j)
           for (int i = 0; i < n; ++i) {
-            double Ui[5]; node_state(U, k, i, j, Ui);
-            double B[3]; B_at_dg(ex, ey, i, j, B);
-            double rho = Ui[0], pr = pressure(Ui, g);
-            double cf = std::sqrt((g * pr + B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) / rho);
-            double r = (2.0 * p + 1.0) * ((std::fabs(Ui[1] / rho) + cf) / hx + (std::fabs(Ui[2] / rho) + cf) / hy);
+            real Ui[5]; node_state(U, k, i, j, Ui);
+            real B[3]; B_at_dg(ex, ey, i, j, B);
+            real rho = Ui[0], pr = pressure(Ui, g);
+            real cf = sqrt((g * pr + B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) / rho);
+            real r = (2.0 * p + 1.0) * ((fabs(Ui[1] / rho) + cf) / hx + (fabs(Ui[2] / rho) + cf) / hy);
             mx = std::max(mx, r);
           }
       }
@@ -715,30 +733,30 @@ struct Oracle {
 
   // B_h||_{Gauss(m)^2} divergence metric (reading R16): max over elements of
   // min(hx,hy) * max |dBx/dx + dBy/dy| at the Gauss(m) points.
-  double div_metric() const {
-    double mx = 0.0;
-    std::vector<double> bx(mL * mm), by(mm * mL);
+  real div_metric() const {
+    real mx = 0.0;
+    std::vector<real> bx(mL * mm), by(mm * mL);
     for (int ey = 0; ey < ny; ++ey)
       for (int ex = 0; ex < nx; ++ex) {
         clX(Bx, ex, ey, bx.data()); clY(By, ex, ey, by.data());
         for (int b = 0; b < mm; ++b)
           for (int a = 0; a < mm; ++a) {
-            double dv = (2.0 / hx) * evX(bx.data(), zG[a], zG[b], 1, 0) + (2.0 / hy) * evY(by.data(), zG[a], zG[b], 0, 1);
-            mx = std::max(mx, std::min(hx, hy) * std::fabs(dv));
+            real dv = (2.0 / hx) * evX(bx.data(), zG[a], zG[b], 1, 0) + (2.0 / hy) * evY(by.data(), zG[a], zG[b], 0, 1);
+            mx = std::max(mx, std::min(hx, hy) * fabs(dv));
           }
       }
     return mx;
   }
 
   // Magnetic energy 1/2 (B,B)_B with the exact product (eq. magnetic-inner-product).
-  double mag_energy(const vec& bX, const vec& bY, const vec& bZ, const vec* cX = nullptr, const vec* cY = nullptr,
+  real mag_energy(const vec& bX, const vec& bY, const vec& bZ, const vec* cX = nullptr, const vec* cY = nullptr,
                     const vec* cZ = nullptr) const {
     // returns (B, C)_B; with C = B it is twice the magnetic energy
     const vec& CX = cX ? *cX : bX;
     const vec& CY = cY ? *cY : bY;
     const vec& CZ = cZ ? *cZ : bZ;
-    double s = 0.0;
-    std::vector<double> bx(mL * mm), by(mm * mL), cx(mL * mm), cy(mm * mL);
+    real s = 0.0;
+    std::vector<real> bx(mL * mm), by(mm * mL), cx(mL * mm), cy(mm * mL);
     for (int ey = 0; ey < ny; ++ey)
       for (int ex = 0; ex < nx; ++ex) {
         int k = kid(ex, ey);
@@ -746,21 +764,28 @@ struct Oracle {
         clX(CX, ex, ey, cx.data()); clY(CY, ex, ey, cy.data());
         for (int qy = 0; qy < mL; ++qy)
           for (int qx = 0; qx < mL; ++qx) {
-            double X = z2[qx], Y = z2[qy];
+            real X = z2[qx], Y = z2[qy];
             s += Jdet * w2[qx] * w2[qy] *
                  (evX(bx.data(), X, Y) * evX(cx.data(), X, Y) + evY(by.data(), X, Y) * evY(cy.data(), X, Y));
           }
-        const double* bz = &bZ[(size_t)k * mm * mm];
-        const double* cz = &CZ[(size_t)k * mm * mm];
+        const real* bz = &bZ[(size_t)k * mm * mm];
+        const real* cz = &CZ[(size_t)k * mm * mm];
         for (int qy = 0; qy < mm; ++qy)
           for (int qx = 0; qx < mm; ++qx) {
-            double X = zG[qx], Y = zG[qy];
+            real X = zG[qx], Y = zG[qy];
             s += Jdet * wG[qx] * wG[qy] * evZ(bz, X, Y) * evZ(cz, X, Y);
           }
       }
     return s;
   }
 };
+
+// Host-array conversion of the C interface (values only; the tangent build
+// exchanges tangents through or_set_tangent / or_get_tangent).
+void to_host(double* out, const vec& v) {
+  for (size_t i = 0; i < v.size(); ++i) out[i] = val(v[i]);
+}
+vec from_host(const double* p, size_t n) { return vec(p, p + n); }
 
 }  // namespace
 
@@ -775,20 +800,33 @@ int or_rule(int kind, int r, double* x, double* w) {
   vec X, W;
   if (kind == 0) gauss_rule(r + 1, X, W);  // Gauss(r): r+1 points
   else gll_rule(r, X, W);                  // GLL(r): r+1 points
-  for (size_t i = 0; i < X.size(); ++i) { x[i] = X[i]; w[i] = W[i]; }
+  to_host(x, X);
+  to_host(w, W);
   return (int)X.size();
 }
 
 double or_lagrange(const double* nodes, int nn, int j, double x, int deriv) {
   vec v(nodes, nodes + nn);
-  return deriv ? dlag(v, j, x) : lag(v, j, x);
+  return val(deriv ? dlag(v, j, x) : lag(v, j, x));
 }
 
-double or_log_mean(double a, double b) { return log_mean(a, b); }
+double or_log_mean(double a, double b) { return val(log_mean(a, b)); }
 
-void or_ec_flux(int d, const double* UL, const double* UR, double g, double* F) { ec_flux(d, UL, UR, g, F); }
-void or_llf_flux(int d, const double* Um, const double* Up, double g, double* F) { llf_flux(d, Um, Up, g, F); }
-void or_phys_flux(int d, const double* U, double g, double* F) { phys_flux(d, U, g, F); }
+void or_ec_flux(int d, const double* UL, const double* UR, double g, double* F) {
+  vec l = from_host(UL, 5), r = from_host(UR, 5), f(5);
+  ec_flux(d, l.data(), r.data(), g, f.data());
+  to_host(F, f);
+}
+void or_llf_flux(int d, const double* Um, const double* Up, double g, double* F) {
+  vec l = from_host(Um, 5), r = from_host(Up, 5), f(5);
+  llf_flux(d, l.data(), r.data(), g, f.data());
+  to_host(F, f);
+}
+void or_phys_flux(int d, const double* U, double g, double* F) {
+  vec u = from_host(U, 5), f(5);
+  phys_flux(d, u.data(), g, f.data());
+  to_host(F, f);
+}
 
 void* or_create(int nx, int ny, double x0, double x1, double y0, double y1, int p, int m, double g) {
   if (nx < 1 || ny < 1 || p < 1 || m < 0 || m > p) return nullptr;
@@ -810,28 +848,28 @@ void or_coords(void* h, int which, double* X, double* Y) {
   Oracle* o = (Oracle*)h;
   for (int ey = 0; ey < o->ny; ++ey)
     for (int ex = 0; ex < o->nx; ++ex) {
-      double xl = o->x0 + ex * o->hx, yl = o->y0 + ey * o->hy;
+      real xl = o->x0 + ex * o->hx, yl = o->y0 + ey * o->hy;
       int k = o->kid(ex, ey);
       if (which == 0) {
         for (int j = 0; j < o->n; ++j)
           for (int i = 0; i < o->n; ++i) {
             size_t q = (size_t)k * o->n2 + j * o->n + i;
-            X[q] = xl + (1.0 + o->xp[i]) * o->hx / 2.0;
-            Y[q] = yl + (1.0 + o->xp[j]) * o->hy / 2.0;
+            X[q] = val(xl + (1.0 + o->xp[i]) * o->hx / 2.0);
+            Y[q] = val(yl + (1.0 + o->xp[j]) * o->hy / 2.0);
           }
       } else if (which == 1) {
         for (int b = 0; b < o->mm; ++b)
           for (int a = 0; a < o->mm; ++a) {
             size_t q = o->gidx(ex * o->mm + a, ey * o->mm + b);
-            X[q] = xl + (1.0 + o->xL[a]) * o->hx / 2.0;
-            Y[q] = yl + (1.0 + o->xL[b]) * o->hy / 2.0;
+            X[q] = val(xl + (1.0 + o->xL[a]) * o->hx / 2.0);
+            Y[q] = val(yl + (1.0 + o->xL[b]) * o->hy / 2.0);
           }
       } else {
         for (int b = 0; b < o->mm; ++b)
           for (int a = 0; a < o->mm; ++a) {
             size_t q = (size_t)k * o->mm * o->mm + b * o->mm + a;
-            X[q] = xl + (1.0 + o->xM[a]) * o->hx / 2.0;
-            Y[q] = yl + (1.0 + o->xM[b]) * o->hy / 2.0;
+            X[q] = val(xl + (1.0 + o->xM[a]) * o->hx / 2.0);
+            Y[q] = val(yl + (1.0 + o->xM[b]) * o->hy / 2.0);
           }
       }
     }
@@ -842,14 +880,14 @@ void or_coords(void* h, int which, double* X, double* Y) {
 void or_b_from_potential(void* h, const double* Az, double Bx0, double By0, double* BxOut, double* ByOut) {
   Oracle* o = (Oracle*)h;
   vec A(Az, Az + (size_t)o->NX * o->NY);
-  std::vector<double> c(o->mL * o->mL);
+  std::vector<real> c(o->mL * o->mL);
   for (int ey = 0; ey < o->ny; ++ey)
     for (int ex = 0; ex < o->nx; ++ex) {
       o->clW(A, ex, ey, c.data());
       for (int b = 0; b < o->mm; ++b)
         for (int a = 0; a < o->mm; ++a) {
-          BxOut[o->gidx(ex * o->mm + a, ey * o->mm + b)] = Bx0 - (2.0 / o->hy) * o->evW(c.data(), o->xL[a], o->zG[b], 0, 1);
-          ByOut[o->gidx(ex * o->mm + a, ey * o->mm + b)] = By0 + (2.0 / o->hx) * o->evW(c.data(), o->zG[a], o->xL[b], 1, 0);
+          BxOut[o->gidx(ex * o->mm + a, ey * o->mm + b)] = val(Bx0 - (2.0 / o->hy) * o->evW(c.data(), o->xL[a], o->zG[b], 0, 1));
+          ByOut[o->gidx(ex * o->mm + a, ey * o->mm + b)] = val(By0 + (2.0 / o->hx) * o->evW(c.data(), o->zG[a], o->xL[b], 1, 0));
         }
     }
 }
@@ -866,11 +904,10 @@ void or_set_state(void* h, const double* U5, const double* bx, const double* by,
 void or_get_state(void* h, double* U5, double* bx, double* by, double* bz) {
   Oracle* o = (Oracle*)h;
   size_t N = (size_t)o->K * o->n2;
-  for (int c = 0; c < 5; ++c) std::memcpy(U5 + c * N, o->U[c].data(), N * sizeof(double));
-  size_t G = (size_t)o->NX * o->NY;
-  std::memcpy(bx, o->Bx.data(), G * sizeof(double));
-  std::memcpy(by, o->By.data(), G * sizeof(double));
-  std::memcpy(bz, o->Bz.data(), (size_t)o->K * o->mm * o->mm * sizeof(double));
+  for (int c = 0; c < 5; ++c) to_host(U5 + c * N, o->U[c]);
+  to_host(bx, o->Bx);
+  to_host(by, o->By);
+  to_host(bz, o->Bz);
 }
 
 void or_hydro_rhs(void* h, const double* U5, double* L5) {
@@ -879,7 +916,7 @@ void or_hydro_rhs(void* h, const double* U5, double* L5) {
   vec S[5], L[5];
   for (int c = 0; c < 5; ++c) { S[c].assign(U5 + c * N, U5 + (c + 1) * N); L[c].assign(N, 0.0); }
   o->hydro_rhs(S, L);
-  for (int c = 0; c < 5; ++c) std::memcpy(L5 + c * N, L[c].data(), N * sizeof(double));
+  for (int c = 0; c < 5; ++c) to_host(L5 + c * N, L[c]);
 }
 
 // Magnetic residual on a primitive state: inputs rho, e, u (3 x N), B, etaK;
@@ -896,13 +933,13 @@ void or_mag_rhs(void* h, const double* rho, const double* e, const double* u, co
   vec R(rho, rho + N), E(etaK, etaK + o->K);
   vec Jv[3], Ev[3];
   o->mag_rhs(R, E, Y, dY, Jv, Ev);
-  std::memcpy(de, dY.e.data(), N * sizeof(double));
-  for (int d = 0; d < 3; ++d) std::memcpy(du + d * N, dY.u[d].data(), N * sizeof(double));
-  std::memcpy(dbx, dY.Bx.data(), G * sizeof(double));
-  std::memcpy(dby, dY.By.data(), G * sizeof(double));
-  std::memcpy(dbz, dY.Bz.data(), Z * sizeof(double));
-  if (Jo) for (int d = 0; d < 3; ++d) std::memcpy(Jo + d * G, Jv[d].data(), G * sizeof(double));
-  if (Eo) for (int d = 0; d < 3; ++d) std::memcpy(Eo + d * G, Ev[d].data(), G * sizeof(double));
+  to_host(de, dY.e);
+  for (int d = 0; d < 3; ++d) to_host(du + d * N, dY.u[d]);
+  to_host(dbx, dY.Bx);
+  to_host(dby, dY.By);
+  to_host(dbz, dY.Bz);
+  if (Jo) for (int d = 0; d < 3; ++d) to_host(Jo + d * G, Jv[d]);
+  if (Eo) for (int d = 0; d < 3; ++d) to_host(Eo + d * G, Ev[d]);
 }
 
 // (B, C)_B with the exact magnetic product.
@@ -911,7 +948,7 @@ double or_mag_product(void* h, const double* bx, const double* by, const double*
   Oracle* o = (Oracle*)h;
   size_t G = (size_t)o->NX * o->NY, Z = (size_t)o->K * o->mm * o->mm;
   vec BX(bx, bx + G), BY(by, by + G), BZ(bz, bz + Z), CX(cx, cx + G), CY(cy, cy + G), CZ(cz, cz + Z);
-  return o->mag_energy(BX, BY, BZ, &CX, &CY, &CZ);
+  return val(o->mag_energy(BX, BY, BZ, &CX, &CY, &CZ));
 }
 
 // which = 0: hydro substep Phi_H^tau; which = 1: magnetic substep Phi_M^tau.
@@ -922,52 +959,54 @@ int or_substep(void* h, int which, double tau) {
 
 int or_strang_step(void* h, double dt, double* dt_taken, int* nrej) {
   Oracle* o = (Oracle*)h;
-  int st = o->strang_step(dt, dt_taken);
+  real taken = 0.0;
+  int st = o->strang_step(dt, &taken);
+  if (dt_taken) *dt_taken = val(taken);
   if (nrej) *nrej = o->last_rejections;
   return st;
 }
 
-double or_cfl_dt(void* h) { return ((Oracle*)h)->cfl_dt(); }
-double or_div_metric(void* h) { return ((Oracle*)h)->div_metric(); }
+double or_cfl_dt(void* h) { return val(((Oracle*)h)->cfl_dt()); }
+double or_div_metric(void* h) { return val(((Oracle*)h)->div_metric()); }
 
 void or_get_eta(void* h, double* out) {
   Oracle* o = (Oracle*)h;
-  std::memcpy(out, o->eta.data(), o->K * sizeof(double));
+  to_host(out, o->eta);
 }
 
 // Diagnostics: [mass, mom_x, mom_y, mom_z, E_kin, E_int, E_mag, entropy S_h,
 // div metric, max|B|, rho_min, p_min, eta_max].
 void or_diagnostics(void* h, double* out) {
   Oracle* o = (Oracle*)h;
-  double mass = 0, mom[3] = {0, 0, 0}, ekin = 0, eint = 0, S = 0, rmin = 1e300, pmin = 1e300, bmax = 0;
+  real mass = 0, mom[3] = {0, 0, 0}, ekin = 0, eint = 0, S = 0, rmin = 1e300, pmin = 1e300, bmax = 0;
   for (int ey = 0; ey < o->ny; ++ey)
     for (int ex = 0; ex < o->nx; ++ex) {
       int k = o->kid(ex, ey);
       for (int j = 0; j < o->n; ++j)
         for (int i = 0; i < o->n; ++i) {
-          double Ui[5]; o->node_state(o->U, k, i, j, Ui);
-          double M = o->Jdet * o->wp[i] * o->wp[j];
-          double pr = pressure(Ui, o->g);
+          real Ui[5]; o->node_state(o->U, k, i, j, Ui);
+          real M = o->Jdet * o->wp[i] * o->wp[j];
+          real pr = pressure(Ui, o->g);
           mass += M * Ui[0];
           for (int d = 0; d < 3; ++d) mom[d] += M * Ui[1 + d];
           ekin += M * 0.5 * (Ui[1] * Ui[1] + Ui[2] * Ui[2] + Ui[3] * Ui[3]) / Ui[0];
           eint += M * pr / (o->g - 1.0);
-          S += M * Ui[0] * (std::log(pr) - o->g * std::log(Ui[0]));
+          S += M * Ui[0] * (log(pr) - o->g * log(Ui[0]));
           rmin = std::min(rmin, Ui[0]); pmin = std::min(pmin, pr);
-          double B[3]; o->B_at_dg(ex, ey, i, j, B);
-          bmax = std::max(bmax, std::sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
+          real B[3]; o->B_at_dg(ex, ey, i, j, B);
+          bmax = std::max(bmax, sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
         }
     }
-  double emax = 0; for (int k = 0; k < o->K; ++k) emax = std::max(emax, o->eta[k]);
-  out[0] = mass; out[1] = mom[0]; out[2] = mom[1]; out[3] = mom[2];
-  out[4] = ekin; out[5] = eint; out[6] = 0.5 * o->mag_energy(o->Bx, o->By, o->Bz);
-  out[7] = S; out[8] = o->div_metric(); out[9] = bmax; out[10] = rmin; out[11] = pmin; out[12] = emax;
+  real emax = 0; for (int k = 0; k < o->K; ++k) emax = std::max(emax, o->eta[k]);
+  const real r[13] = {mass, mom[0], mom[1], mom[2], ekin, eint, 0.5 * o->mag_energy(o->Bx, o->By, o->Bz),
+                      S, o->div_metric(), bmax, rmin, pmin, emax};
+  for (int i = 0; i < 13; ++i) out[i] = val(r[i]);
 }
 
 // Sample a field at the nq x nq Gauss points of every element (for L2 errors).
 // field: 0..4 conserved, 5..7 u, 8 p, 9..11 B, 12..14 E_h, 15..17 J_h
 // (E_h with the element resistivity of the last magnetic substep).
-void or_sample(void* h, int field, int nq, double* val, double* X, double* Y, double* W) {
+void or_sample(void* h, int field, int nq, double* val_out, double* X, double* Y, double* W) {
   Oracle* o = (Oracle*)h;
   vec zq, wq; gauss_rule(nq, zq, wq);
   vec Jv[3], Ev[3];
@@ -978,18 +1017,18 @@ void or_sample(void* h, int field, int nq, double* val, double* X, double* Y, do
       o->compute_E(Y0.u, o->Bx, o->By, o->Bz, o->eta, Jv[0], Jv[1], Jv[2], Ev[0], Ev[1], Ev[2]);
     }
   }
-  std::vector<double> c(std::max(o->n2, o->mL * o->mL)), c2(o->n2);
+  std::vector<real> c(std::max(o->n2, o->mL * o->mL)), c2(o->n2);
   size_t idx = 0;
   for (int ey = 0; ey < o->ny; ++ey)
     for (int ex = 0; ex < o->nx; ++ex) {
       int k = o->kid(ex, ey);
       for (int qy = 0; qy < nq; ++qy)
         for (int qx = 0; qx < nq; ++qx, ++idx) {
-          double xr = zq[qx], yr = zq[qy];
-          X[idx] = o->x0 + ex * o->hx + (1.0 + xr) * o->hx / 2.0;
-          Y[idx] = o->y0 + ey * o->hy + (1.0 + yr) * o->hy / 2.0;
-          W[idx] = o->Jdet * wq[qx] * wq[qy];
-          double v = 0.0;
+          real xr = zq[qx], yr = zq[qy];
+          X[idx] = val(o->x0 + ex * o->hx + (1.0 + xr) * o->hx / 2.0);
+          Y[idx] = val(o->y0 + ey * o->hy + (1.0 + yr) * o->hy / 2.0);
+          W[idx] = val(o->Jdet * wq[qx] * wq[qy]);
+          real v = 0.0;
           if (field <= 4) {
             v = o->evDG(&o->U[field][(size_t)k * o->n2], xr, yr);
           } else if (field <= 7) {
@@ -997,7 +1036,7 @@ void or_sample(void* h, int field, int nq, double* val, double* X, double* Y, do
             v = o->evDG(c2.data(), xr, yr);
           } else if (field == 8) {
             for (int q = 0; q < o->n2; ++q) {
-              double Ui[5]; for (int cc = 0; cc < 5; ++cc) Ui[cc] = o->U[cc][(size_t)k * o->n2 + q];
+              real Ui[5]; for (int cc = 0; cc < 5; ++cc) Ui[cc] = o->U[cc][(size_t)k * o->n2 + q];
               c2[q] = pressure(Ui, o->g);
             }
             v = o->evDG(c2.data(), xr, yr);
@@ -1011,9 +1050,84 @@ void or_sample(void* h, int field, int nq, double* val, double* X, double* Y, do
             else if (comp == 1) { o->clX(F[1], ex, ey, c.data()); v = o->evX(c.data(), xr, yr); }
             else { o->clW(F[2], ex, ey, c.data()); v = o->evW(c.data(), xr, yr); }
           }
-          val[idx] = v;
+          val_out[idx] = val(v);
         }
     }
 }
 
 }  // extern "C"
+
+#ifdef ORACLE_TANGENT
+// ---------------------------------------------------------------------------
+// Tangent interface (liboracle_tangent.so only): directional derivatives of the
+// oracle's maps by forward-mode dual numbers.  The test-suite uses them as the
+// exact tangent J dx against which the adjoint's J^T lam is checked.
+// ---------------------------------------------------------------------------
+namespace {
+void seed(vec& v, const double* d) {
+  for (size_t i = 0; i < v.size(); ++i) v[i].d = d ? d[i] : 0.0;
+}
+void tangent_out(double* out, const vec& v) {
+  for (size_t i = 0; i < v.size(); ++i) out[i] = v[i].d;
+}
+}  // namespace
+
+extern "C" {
+
+// Tangent parts of the current state (values unchanged).
+void or_set_tangent(void* h, const double* dU5, const double* dbx, const double* dby, const double* dbz) {
+  Oracle* o = (Oracle*)h;
+  size_t N = (size_t)o->K * o->n2;
+  for (int c = 0; c < 5; ++c) seed(o->U[c], dU5 + c * N);
+  seed(o->Bx, dbx); seed(o->By, dby); seed(o->Bz, dbz);
+}
+
+void or_get_tangent(void* h, double* dU5, double* dbx, double* dby, double* dbz) {
+  Oracle* o = (Oracle*)h;
+  size_t N = (size_t)o->K * o->n2;
+  for (int c = 0; c < 5; ++c) tangent_out(dU5 + c * N, o->U[c]);
+  tangent_out(dbx, o->Bx); tangent_out(dby, o->By); tangent_out(dbz, o->Bz);
+}
+
+// L = L_E(U) and its tangent dL = L_E'(U) dU.
+void or_hydro_rhs_tangent(void* h, const double* U5, const double* dU5, double* L5, double* dL5) {
+  Oracle* o = (Oracle*)h;
+  size_t N = (size_t)o->K * o->n2;
+  vec S[5], L[5];
+  for (int c = 0; c < 5; ++c) {
+    S[c] = from_host(U5 + c * N, N);
+    seed(S[c], dU5 + c * N);
+    L[c].assign(N, 0.0);
+  }
+  o->hydro_rhs(S, L);
+  for (int c = 0; c < 5; ++c) { to_host(L5 + c * N, L[c]); tangent_out(dL5 + c * N, L[c]); }
+}
+
+// Magnetic residual (de, du, dB) of (rho, e, u, B) at fixed eta and its tangent
+// for the input tangents (t_*); outputs out[0..4] = de, du, dBx, dBy, dBz and
+// tout[0..4] their tangents.
+void or_mag_rhs_tangent(void* h, const double* rho, const double* t_rho, const double* e, const double* t_e,
+                        const double* u, const double* t_u, const double* bx, const double* t_bx,
+                        const double* by, const double* t_by, const double* bz, const double* t_bz,
+                        const double* etaK, double* de, double* du, double* dbx, double* dby, double* dbz,
+                        double* t_de, double* t_du, double* t_dbx, double* t_dby, double* t_dbz) {
+  Oracle* o = (Oracle*)h;
+  size_t N = (size_t)o->K * o->n2, G = (size_t)o->NX * o->NY, Z = (size_t)o->K * o->mm * o->mm;
+  Oracle::Mag Y, dY;
+  Y.e = from_host(e, N); seed(Y.e, t_e);
+  for (int d = 0; d < 3; ++d) { Y.u[d] = from_host(u + d * N, N); seed(Y.u[d], t_u + d * N); }
+  Y.Bx = from_host(bx, G); seed(Y.Bx, t_bx);
+  Y.By = from_host(by, G); seed(Y.By, t_by);
+  Y.Bz = from_host(bz, Z); seed(Y.Bz, t_bz);
+  vec R = from_host(rho, N), E = from_host(etaK, o->K);
+  seed(R, t_rho);
+  o->mag_rhs(R, E, Y, dY);
+  to_host(de, dY.e); tangent_out(t_de, dY.e);
+  for (int d = 0; d < 3; ++d) { to_host(du + d * N, dY.u[d]); tangent_out(t_du + d * N, dY.u[d]); }
+  to_host(dbx, dY.Bx); tangent_out(t_dbx, dY.Bx);
+  to_host(dby, dY.By); tangent_out(t_dby, dY.By);
+  to_host(dbz, dY.Bz); tangent_out(t_dbz, dY.Bz);
+}
+
+}  // extern "C"
+#endif
