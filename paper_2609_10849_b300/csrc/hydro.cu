@@ -232,8 +232,8 @@ __global__ void __launch_bounds__(HCfg<P>::threads) k_vol(const double* __restri
 #pragma unroll
   for (int c = 0; c < 5; ++c) sf[c][el * n2 + q] = Cv[c];
   __syncthreads();
-  if (q < 5) {
-    const int c = q;
+  // component c is reduced by node thread c mod n2 (p = 1 has only 4 nodes per element)
+  for (int c = q; c < 5; c += n2) {
     double s = 0.0;
 #pragma unroll
     for (int t2 = 0; t2 < n2; ++t2) s = fma(0.25 * T->wp[t2 % n] * T->wp[t2 / n], sf[c][el * n2 + t2], s);
