@@ -161,6 +161,41 @@ int mhd_mag_rhs(mhd_ctx* ctx, const double* rho, const double* e, const double* 
                 const double* By, const double* Bz, const double* eta, double* de, double* du, double* dBx,
                 double* dBy, double* dBz, int on_device);
 
+/* ---- Adjoint (spec differentiation pattern; the paper has none) ----
+ * Packed state vector of a context: [U 5N | Bx G | By G | Bz Z] in the host
+ * layouts above (G = Z); its length is mhd_state_size().  An adjoint vector
+ * lam has the same packing and holds dJ/d(state) of a scalar objective J. */
+long long mhd_state_size(const mhd_ctx* ctx);
+
+/* Vector-Jacobian product of one Strang step S^dt (Algorithm 3) at fixed dt:
+ * lam_n = (dS^dt/dx)(state_n)^T lam_np1, written by hand in reverse mode
+ * (transposed flux differencing with the Jacobians of the entropy-conservative
+ * two-point flux and of the LLF flux, the adjoint SSP-RK(3,3) stages, the
+ * transposed discrete curl, the adjoint lumped reconstructions of E_h and
+ * J_h, and the adjoint nodal exchange).  The step's intermediate states are
+ * recomputed from state_n on the device; the context's own state is not
+ * touched.  The derivative is that of the step with every stabilisation map
+ * off: if hydro OE, the limiter, the artificial resistivity or the velocity
+ * OE is enabled, *flags (may be NULL) gets bits 1, 2, 4, 8 respectively and
+ * the call returns MHD_EINVAL.  lam_n may alias lam_np1.  The first call
+ * allocates the adjoint's device buffers (about 14 state-sized vectors).
+ * Errors: MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA, MHD_INADMISSIBLE or
+ * MHD_NONFINITE if the recomputed step leaves the admissible set. */
+int mhd_adjoint_step(mhd_ctx* ctx, const double* state_n, const double* lam_np1, double* lam_n, double dt,
+                     int on_device, int* flags);
+
+/* Test hook: (dL_E/dU)(U)^T nu for the hydro residual of mhd_hydro_rhs
+ * (U, nu, out [5][N]). */
+int mhd_hydro_rhs_vjp(mhd_ctx* ctx, const double* U, const double* nu, double* out, int on_device);
+
+/* Test hook: vector-Jacobian product of the ideal magnetic residual of
+ * mhd_mag_rhs (eta = 0, where de/dt = 0 and nothing depends on e) with
+ * respect to (rho [N], u [3][N], B): inputs w_u [3][N] and w_B (host layouts)
+ * weight (du/dt, dB/dt); outputs g_rho [N], g_u [3][N], g_B. */
+int mhd_mag_rhs_vjp(mhd_ctx* ctx, const double* rho, const double* u, const double* Bx, const double* By,
+                    const double* Bz, const double* w_u, const double* w_Bx, const double* w_By, const double* w_Bz,
+                    double* g_rho, double* g_u, double* g_Bx, double* g_By, double* g_Bz, int on_device);
+
 /* Diagnostics of the current state. */
 int mhd_diagnostics(mhd_ctx* ctx, mhd_diag_t* out);
 

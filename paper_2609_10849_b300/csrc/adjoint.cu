@@ -1,0 +1,305 @@
+// Adjoint of one H-M-H Strang step (Algorithm 3, eq. strang-composition) with
+// the stabilisation maps switched off and dt fixed.
+//
+// Reverse mode written out by hand: the step's intermediate states are
+// recomputed from its start state (the hydro stage inputs of both hydro
+// substeps, the state after the first one and the magnetic stage states),
+// then the adjoint runs backwards through
+//   Phi_H^{dt/2}  <-  exchange back  <-  Phi_M^{dt}  <-  exchange  <-  Phi_H^{dt/2}.
+// Each SSP-RK(3,3) substep (eq. euler-ssprk33, eq. magnetic-ssprk33) is
+//   S1 = S0 + tau F(S0),  S2 = 3/4 S0 + 1/4 (S1 + tau F(S1)),
+//   S3 = 1/3 S0 + 2/3 (S2 + tau F(S2)),
+// whose adjoint for lam3 is, with a = (0, 3/4, 1/3), b = (1, 1/4, 2/3):
+//   w = b2 lam3, lam2 = w + tau F'(S2)^T w, lam0  = a2 lam3,
+//   w = b1 lam2, lam1 = w + tau F'(S1)^T w, lam0 += a1 lam2,
+//   lam0 += lam1 + tau F'(S0)^T lam1.
+// The magnetic substep freezes the density, so its adjoint also accumulates
+// the density adjoint, which the two exchanges pass on to the conservative
+// variables.
+#include <algorithm>
+#include <string>
+
+#include "../../include/mhd.h"
+#include "context.cuh"
+
+using namespace mhd;
+
+namespace {
+
+const double RK_A[3] = {0.0, 0.75, 1.0 / 3.0};
+const double RK_B[3] = {1.0, 0.25, 2.0 / 3.0};
+
+int afail(int code, const std::string& msg) {
+  set_error_message(msg.c_str());
+  return code;
+}
+int acuda(cudaError_t e, const char* where) {
+  return afail(MHD_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+cudaError_t aalloc(mhd_ctx* c, double** p, size_t n) {
+  void* ptr = nullptr;
+  cudaError_t e = cudaMalloc(&ptr, std::max<size_t>(n, 1) * sizeof(double));
+  if (e == cudaSuccess) { c->allocs.push_back(ptr); *p = (double*)ptr; }
+  return e;
+}
+
+cudaError_t acopy(mhd_ctx* c, double* dst, const double* src, size_t n, cudaMemcpyKind host_kind, int on_device) {
+  return cudaMemcpyAsync(dst, src, n * sizeof(double), on_device ? cudaMemcpyDeviceToDevice : host_kind, c->st);
+}
+
+// L0 = a lam (+ L0 if acc), W = b lam.
+__global__ void k_lin2(const double* __restrict__ lam, double a, double b, int acc, double* __restrict__ L0,
+                       double* __restrict__ W, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double l = lam[i];
+  L0[i] = acc ? fma(a, l, L0[i]) : a * l;
+  W[i] = b * l;
+}
+
+// out = W + tau G (acc: out += W + tau G).
+__global__ void k_fin(const double* __restrict__ W, const double* __restrict__ G, double tau, int acc,
+                      double* __restrict__ out, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = fma(tau, G[i], W[i]);
+  out[i] = acc ? out[i] + v : v;
+}
+
+unsigned nblk(size_t n) { return (unsigned)((n + 255) / 256); }
+
+int ensure_adjoint(mhd_ctx* c) {
+  AdjBufs& A = c->adj;
+  if (A.ready) return MHD_OK;
+  const size_t N = c->N, Z = c->Z, K = c->M.K;
+  const size_t VM = 4 * N + 3 * Z, VX = std::max(5 * N, VM);
+  cudaError_t e = cudaSuccess;
+  for (int h = 0; h < 2 && e == cudaSuccess; ++h)
+    for (int s = 0; s < 3 && e == cudaSuccess; ++s) e = aalloc(c, &A.hS[h][s], 5 * N);
+  if (e == cudaSuccess) e = aalloc(c, &A.Ua, 5 * N);
+  for (int s = 0; s < 4 && e == cudaSuccess; ++s) e = aalloc(c, &A.Y[s], VM);
+  if (e == cudaSuccess) e = aalloc(c, &A.lamU, 5 * N);
+  if (e == cudaSuccess) e = aalloc(c, &A.lamM, VM);
+  if (e == cudaSuccess) e = aalloc(c, &A.W, VX);
+  if (e == cudaSuccess) e = aalloc(c, &A.L0, VX);
+  if (e == cudaSuccess) e = aalloc(c, &A.G, VX);
+  if (e == cudaSuccess) e = aalloc(c, &A.lamR, N);
+  if (e == cudaSuccess) e = aalloc(c, &A.FA, 20 * K * c->n);
+  if (e == cudaSuccess) e = aalloc(c, &A.io, 5 * N + 3 * Z);
+  if (e == cudaSuccess) e = aalloc(c, &A.ms.mu, 3 * N);
+  if (e == cudaSuccess) e = aalloc(c, &A.ms.s, 3 * N);
+  if (e == cudaSuccess) e = aalloc(c, &A.ms.LT, mag_load_doubles(c->p, c->k, (int)K));
+  if (e == cudaSuccess) e = aalloc(c, &A.ms.LJ, mag_load_doubles(c->p, c->k, (int)K));
+  if (e == cudaSuccess) e = aalloc(c, &A.ms.LE, mag_load_doubles(c->p, c->k, (int)K));
+  if (e == cudaSuccess) e = aalloc(c, &A.ms.V, 3 * Z);
+  if (e == cudaSuccess) e = aalloc(c, &A.ms.LB, mag_adj_load_doubles(c->p, c->k, (int)K));
+  if (e != cudaSuccess) return afail(MHD_ENOMEM, std::string("adjoint buffers: ") + cudaGetErrorString(e));
+  A.ready = true;
+  return MHD_OK;
+}
+
+// ---- forward recomputation ---------------------------------------------------------
+// Hydro substep tau = dt * fac from S[0] (filled by the caller), keeping the
+// stage inputs S[1], S[2]; the result goes to out.
+void hydro_fwd(mhd_ctx* c, double* const S[3], double* out, double fac) {
+  const double* in[3] = {S[0], S[1], S[2]};
+  double* o[3] = {S[1], S[2], out};
+  for (int s = 0; s < 3; ++s) {
+    hydro_face(c->p, in[s], c->Fx, c->Fy, c->M, c->st);
+    hydro_vol(c->p, 1, in[s], S[0], c->Fx, c->Fy, o[s], nullptr, c->status, c->T, c->M, c->dt, fac, RK_A[s],
+              RK_B[s], s == 0, c->st);
+  }
+  c->launches += 6;
+}
+
+// Magnetic substep tau = dt * fac from Y[0] (e, u, B) with density rho,
+// keeping the stage states Y[1], Y[2]; the result goes to Y[3].
+void mag_fwd(mhd_ctx* c, const double* rho, double fac) {
+  AdjBufs& A = c->adj;
+  const size_t N = c->N;
+  for (int s = 0; s < 3; ++s) {
+    double* in = A.Y[s];
+    double* out = A.Y[s + 1];
+    mag_stage(c->p, c->k, 1, in + 4 * N, in + N, in, rho, c->eta, 0, A.Y[0] + 4 * N, A.Y[0] + N, A.Y[0],
+              out + 4 * N, out + N, out, c->LJ, c->LE, c->T, c->M, c->dt, fac, RK_A[s], RK_B[s], s == 0, c->st);
+  }
+  c->launches += 9;
+}
+
+// ---- adjoint substeps --------------------------------------------------------------
+void hydro_adj(mhd_ctx* c, double* const S[3], double* lam, double tau) {
+  AdjBufs& A = c->adj;
+  const size_t n = 5 * c->N;
+  for (int s = 2; s >= 0; --s) {
+    const double* w = lam;
+    if (s > 0) {
+      k_lin2<<<nblk(n), 256, 0, c->st>>>(lam, RK_A[s], RK_B[s], s == 1, A.L0, A.W, n);
+      w = A.W;
+    }
+    hydro_rhs_vjp(c->p, S[s], w, A.FA, A.G, c->M, c->T, c->st);
+    k_fin<<<nblk(n), 256, 0, c->st>>>(w, A.G, tau, s == 0, s > 0 ? lam : A.L0, n);
+    c->launches += s > 0 ? 4 : 3;
+  }
+  cudaMemcpyAsync(lam, A.L0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+}
+
+void mag_adj(mhd_ctx* c, const double* rho, double* lam, double tau) {
+  AdjBufs& A = c->adj;
+  const size_t N = c->N, n = 4 * N + 3 * c->Z;
+  for (int s = 2; s >= 0; --s) {
+    const double* w = lam;
+    if (s > 0) {
+      k_lin2<<<nblk(n), 256, 0, c->st>>>(lam, RK_A[s], RK_B[s], s == 1, A.L0, A.W, n);
+      w = A.W;
+    }
+    cudaMemsetAsync(A.G, 0, N * sizeof(double), c->st);  // the ideal residual has de/dt = 0
+    const double* Ys = A.Y[s];
+    mag_rhs_vjp(c->p, c->k, rho, Ys + N, Ys + 4 * N, w + N, w + 4 * N, A.G + N, A.G + 4 * N, A.lamR, tau, A.ms,
+                c->M, c->st);
+    k_fin<<<nblk(n), 256, 0, c->st>>>(w, A.G, tau, s == 0, s > 0 ? lam : A.L0, n);
+    c->launches += (s > 0 ? 2 : 1) + 9;
+  }
+  cudaMemcpyAsync(lam, A.L0, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+}
+
+int read_status(mhd_ctx* c, unsigned* st) {
+  cudaError_t e = cudaMemcpyAsync(c->h_status, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return acuda(e, "adjoint");
+  *st = *c->h_status;
+  return MHD_OK;
+}
+
+int stab_flags(const mhd_ctx* c) {
+  return (c->prm.oe_hydro ? 1 : 0) | (c->prm.pp ? 2 : 0) | (c->prm.ar && c->prm.C_eta != 0.0 ? 4 : 0) |
+         (c->prm.oe_vel ? 8 : 0);
+}
+
+}  // namespace
+
+extern "C" {
+
+long long mhd_state_size(const mhd_ctx* c) { return c ? (long long)(5 * c->N + 3 * c->Z) : 0; }
+
+int mhd_adjoint_step(mhd_ctx* c, const double* state_n, const double* lam_np1, double* lam_n, double dt,
+                     int on_device, int* flags) {
+  if (!c || !state_n || !lam_np1 || !lam_n) return afail(MHD_EINVAL, "null argument");
+  const int fl = stab_flags(c);
+  if (flags) *flags = fl;
+  if (fl) return afail(MHD_EINVAL, "the adjoint differentiates the step with every stabilisation map off");
+  if (!(dt > 0.0)) return afail(MHD_EINVAL, "dt must be positive");
+  int r = ensure_adjoint(c);
+  if (r != MHD_OK) return r;
+  AdjBufs& A = c->adj;
+  const size_t N = c->N, Z = c->Z;
+  const int nx = c->M.nx, ny = c->M.ny, mm = c->mm;
+  cudaError_t e;
+  // inputs: state -> hS[0][0] and Y[0] (B part), adjoint -> lamU and lamM (B part)
+  if ((e = acopy(c, A.io, state_n, 5 * N + 3 * Z, cudaMemcpyHostToDevice, on_device)) != cudaSuccess)
+    return acuda(e, "adjoint state");
+  cudaMemcpyAsync(A.hS[0][0], A.io, 5 * N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  grid_to_blocked(A.io + 5 * N, A.Y[0] + 4 * N, nx, ny, mm, c->st);
+  grid_to_blocked(A.io + 5 * N + Z, A.Y[0] + 4 * N + Z, nx, ny, mm, c->st);
+  cudaMemcpyAsync(A.Y[0] + 4 * N + 2 * Z, A.io + 5 * N + 2 * Z, Z * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  // recompute the step
+  set_scalar(c->dt, dt, c->st);
+  cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->st);
+  hydro_fwd(c, A.hS[0], A.Ua, 0.5);
+  cons_to_prim(A.Ua, A.Y[0], N, c->st);
+  mag_fwd(c, A.Ua, 1.0);
+  cudaMemcpyAsync(A.hS[1][0], A.Ua, 5 * N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  prim_to_cons(A.Y[3], A.hS[1][0], N, c->st);
+  hydro_fwd(c, A.hS[1], A.G, 0.5);
+  c->launches += 6;
+  unsigned st = 0;
+  if ((r = read_status(c, &st)) != MHD_OK) return r;
+  if (st & ST_NONFINITE) return afail(MHD_NONFINITE, "non-finite value in the recomputed step");
+  if (st & ST_INADMISSIBLE) return afail(MHD_INADMISSIBLE, "inadmissible cell average in the recomputed step");
+  // adjoint input
+  if ((e = acopy(c, A.io, lam_np1, 5 * N + 3 * Z, cudaMemcpyHostToDevice, on_device)) != cudaSuccess)
+    return acuda(e, "adjoint input");
+  cudaMemcpyAsync(A.lamU, A.io, 5 * N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  grid_to_blocked(A.io + 5 * N, A.lamM + 4 * N, nx, ny, mm, c->st);
+  grid_to_blocked(A.io + 5 * N + Z, A.lamM + 4 * N + Z, nx, ny, mm, c->st);
+  cudaMemcpyAsync(A.lamM + 4 * N + 2 * Z, A.io + 5 * N + 2 * Z, Z * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  // backwards through the step
+  hydro_adj(c, A.hS[1], A.lamU, 0.5 * dt);
+  adj_prim_to_cons(A.hS[1][0], A.Y[3], A.lamU, A.lamM, A.lamR, N, c->st);
+  mag_adj(c, A.Ua, A.lamM, dt);
+  adj_cons_to_prim(A.Ua, A.lamM, A.lamR, A.lamU, N, c->st);
+  hydro_adj(c, A.hS[0], A.lamU, 0.5 * dt);
+  c->launches += 6;
+  // output
+  cudaMemcpyAsync(A.io, A.lamU, 5 * N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  blocked_to_grid(A.lamM + 4 * N, A.io + 5 * N, nx, ny, mm, c->st);
+  blocked_to_grid(A.lamM + 4 * N + Z, A.io + 5 * N + Z, nx, ny, mm, c->st);
+  cudaMemcpyAsync(A.io + 5 * N + 2 * Z, A.lamM + 4 * N + 2 * Z, Z * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  if ((e = acopy(c, lam_n, A.io, 5 * N + 3 * Z, cudaMemcpyDeviceToHost, on_device)) != cudaSuccess)
+    return acuda(e, "adjoint output");
+  if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return acuda(e, "adjoint");
+  return MHD_OK;
+}
+
+int mhd_hydro_rhs_vjp(mhd_ctx* c, const double* U, const double* nu, double* out, int on_device) {
+  if (!c || !U || !nu || !out) return afail(MHD_EINVAL, "null argument");
+  int r = ensure_adjoint(c);
+  if (r != MHD_OK) return r;
+  AdjBufs& A = c->adj;
+  const size_t n = 5 * c->N;
+  cudaError_t e;
+  if ((e = acopy(c, A.hS[0][0], U, n, cudaMemcpyHostToDevice, on_device)) != cudaSuccess) return acuda(e, "U");
+  if ((e = acopy(c, A.W, nu, n, cudaMemcpyHostToDevice, on_device)) != cudaSuccess) return acuda(e, "nu");
+  hydro_rhs_vjp(c->p, A.hS[0][0], A.W, A.FA, A.G, c->M, c->T, c->st);
+  c->launches += 2;
+  if ((e = acopy(c, out, A.G, n, cudaMemcpyDeviceToHost, on_device)) != cudaSuccess) return acuda(e, "out");
+  if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return acuda(e, "hydro_rhs_vjp");
+  return MHD_OK;
+}
+
+int mhd_mag_rhs_vjp(mhd_ctx* c, const double* rho, const double* u, const double* Bx, const double* By,
+                    const double* Bz, const double* wu, const double* wBx, const double* wBy, const double* wBz,
+                    double* g_rho, double* g_u, double* g_Bx, double* g_By, double* g_Bz, int on_device) {
+  if (!c || !rho || !u || !Bx || !By || !Bz || !wu || !wBx || !wBy || !wBz || !g_rho || !g_u || !g_Bx || !g_By ||
+      !g_Bz)
+    return afail(MHD_EINVAL, "null argument");
+  int r = ensure_adjoint(c);
+  if (r != MHD_OK) return r;
+  AdjBufs& A = c->adj;
+  const size_t N = c->N, Z = c->Z;
+  const int nx = c->M.nx, ny = c->M.ny, mm = c->mm;
+  const cudaMemcpyKind h2d = cudaMemcpyHostToDevice, d2h = cudaMemcpyDeviceToHost;
+  double* Y = A.Y[0];
+  double* io = A.io;
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = acopy(c, A.Ua, rho, N, h2d, on_device);
+  if (e == cudaSuccess) e = acopy(c, Y + N, u, 3 * N, h2d, on_device);
+  if (e == cudaSuccess) e = acopy(c, io, Bx, Z, h2d, on_device);
+  if (e == cudaSuccess) e = acopy(c, io + Z, By, Z, h2d, on_device);
+  if (e == cudaSuccess) e = acopy(c, Y + 4 * N + 2 * Z, Bz, Z, h2d, on_device);
+  if (e == cudaSuccess) e = acopy(c, A.W + N, wu, 3 * N, h2d, on_device);
+  if (e == cudaSuccess) e = acopy(c, io + 2 * Z, wBx, Z, h2d, on_device);
+  if (e == cudaSuccess) e = acopy(c, io + 3 * Z, wBy, Z, h2d, on_device);
+  if (e == cudaSuccess) e = acopy(c, A.W + 4 * N + 2 * Z, wBz, Z, h2d, on_device);
+  if (e != cudaSuccess) return acuda(e, "mag_rhs_vjp inputs");
+  grid_to_blocked(io, Y + 4 * N, nx, ny, mm, c->st);
+  grid_to_blocked(io + Z, Y + 4 * N + Z, nx, ny, mm, c->st);
+  grid_to_blocked(io + 2 * Z, A.W + 4 * N, nx, ny, mm, c->st);
+  grid_to_blocked(io + 3 * Z, A.W + 4 * N + Z, nx, ny, mm, c->st);
+  cudaMemsetAsync(A.lamR, 0, N * sizeof(double), c->st);
+  mag_rhs_vjp(c->p, c->k, A.Ua, Y + N, Y + 4 * N, A.W + N, A.W + 4 * N, A.G + N, A.G + 4 * N, A.lamR, 1.0, A.ms,
+              c->M, c->st);
+  blocked_to_grid(A.G + 4 * N, io, nx, ny, mm, c->st);
+  blocked_to_grid(A.G + 4 * N + Z, io + Z, nx, ny, mm, c->st);
+  c->launches += 15;
+  if (e == cudaSuccess) e = acopy(c, g_rho, A.lamR, N, d2h, on_device);
+  if (e == cudaSuccess) e = acopy(c, g_u, A.G + N, 3 * N, d2h, on_device);
+  if (e == cudaSuccess) e = acopy(c, g_Bx, io, Z, d2h, on_device);
+  if (e == cudaSuccess) e = acopy(c, g_By, io + Z, Z, d2h, on_device);
+  if (e == cudaSuccess) e = acopy(c, g_Bz, A.G + 4 * N + 2 * Z, Z, d2h, on_device);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return acuda(e, "mag_rhs_vjp");
+  return MHD_OK;
+}
+
+}  // extern "C"

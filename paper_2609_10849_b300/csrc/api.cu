@@ -10,44 +10,8 @@
 #include <vector>
 
 #include "../../include/mhd.h"
-#include "mhd_internal.cuh"
+#include "context.cuh"
 
-namespace mhd {
-// kernels / launchers defined in the other translation units
-void hydro_face(int p, const double* S, double* Fx, double* Fy, const Mesh& M, cudaStream_t st);
-void hydro_vol(int p, int mode, const double* S, const double* U0, const double* Fx, const double* Fy, double* out,
-               double* avg, unsigned* status, const Tab* T, const Mesh& M, const double* dtp, double dtfac,
-               double ca, double cb, int first, cudaStream_t st);
-size_t mag_load_doubles(int p, int k, int K);
-void mag_stage(int p, int k, int mode, const double* B, const double* u, const double* e, const double* rho,
-               const double* eta, int resistive, const double* B0, const double* u0, const double* e0, double* Bo,
-               double* uo, double* eo, double* LJ, double* LE, const Tab* T, const Mesh& M, const double* dtp,
-               double dtfac, double ca, double cb, int first, cudaStream_t st);
-void grid_to_blocked(const double* g, double* o, int nx, int ny, int mm, cudaStream_t st);
-void blocked_to_grid(const double* o, double* g, int nx, int ny, int mm, cudaStream_t st);
-void cons_to_prim(const double* U, double* Y, size_t N, cudaStream_t st);
-void prim_to_cons(const double* Y, double* U, size_t N, cudaStream_t st);
-void prim_in(const double* rho, const double* u, const double* p, double* U, size_t N, double g, cudaStream_t st);
-void b_from_potential(int k, const double* A, double Bx0, double By0, double* Bx, double* By, const Tab* T,
-                      const Mesh& M, cudaStream_t st);
-void cfl_dt(int p, int k, const double* U, const double* B, const Tab* T, const Mesh& M,
-            unsigned long long* maxbits, double cfl, double* dt, cudaStream_t st);
-void set_scalar(double* ptr, double v, cudaStream_t st);
-void diag_partials(int p, int k, const double* U, const double* B, const Tab* T, const Mesh& M, double* out,
-                   cudaStream_t st);
-void stab_hydro(int p, double* S, const double* avg, unsigned* status, const Tab* T, const Mesh& M,
-                const Stab& prm, const double* dtp, double dtfac, double* work, cudaStream_t st);
-void stab_eta(int p, int k, const double* rho, const double* Y, const double* B, const Tab* T, const Mesh& M,
-              const Stab& prm, double* eta, double* work, cudaStream_t st);
-void stab_vel_prep(int p, const double* rho, double* chol, const Tab* T, const Mesh& M, cudaStream_t st);
-void stab_vel(int p, int k, const double* rho, double* Y, const double* B, const double* chol, const Tab* T,
-              const Mesh& M, const Stab& prm, const double* dtp, double dtfac, double* work, cudaStream_t st);
-size_t stab_work_doubles(int p, int k, const Mesh& M);
-size_t stab_chol_doubles(int p, const Mesh& M);
-void set_error_message(const char* msg);
-cudaError_t mag_prepare(int p, int k);
-cudaError_t stab_prepare(int p);
-}  // namespace mhd
 
 using namespace mhd;
 
@@ -70,35 +34,6 @@ int cuda_fail(cudaError_t e, const char* where) {
 }
 }  // namespace
 
-struct mhd_ctx {
-  int p, k, n, n2, mm;
-  Mesh M;
-  Stab prm;
-  double x0, x1, y0, y1;
-  cudaStream_t st;
-  bool own_stream;
-  const Tab* T;
-  Tab hT;
-  size_t N, Z;
-  double *U, *Usave, *S1, *S2;
-  double *B, *Bsave, *Ba, *Bb;
-  double *Y0, *Ya, *Yb;
-  double *Fx, *Fy, *LJ, *LE, *avg, *eta, *dt, *work, *chol, *io;
-  unsigned* status;
-  unsigned long long* maxbits;
-  double* h_pinned;  // small pinned host scratch
-  unsigned* h_status;
-  long long launches;
-  std::vector<void*> allocs;
-  // optional per-kernel-class event timing (bench instrumentation)
-  bool profiling;
-  // cached CUDA graph of a fixed-dt sequence of Strang steps (mhd_strang_steps)
-  cudaGraphExec_t graph;
-  int graph_steps;
-  long long graph_launches;
-  std::vector<cudaEvent_t> ev_pool;
-  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_rec;
-};
 
 namespace {
 
@@ -272,7 +207,8 @@ int mhd_create(const mhd_mesh_t* mesh, int p, int k, double gamma, mhd_ctx** out
   c->own_stream = true;
   c->T = device_tables(p, k, &e);
   if (!c->T) { cudaStreamDestroy(c->st); delete c; return cuda_fail(e, "tables"); }
-  if ((e = mag_prepare(p, k)) != cudaSuccess || (e = stab_prepare(p)) != cudaSuccess) {
+  if ((e = mag_prepare(p, k)) != cudaSuccess || (e = stab_prepare(p)) != cudaSuccess ||
+      (e = mag_adj_prepare(p, k)) != cudaSuccess) {
     cudaStreamDestroy(c->st);
     delete c;
     return cuda_fail(e, "kernel attributes");

@@ -244,7 +244,8 @@ struct LE_ {  // per-element shared-memory offsets (doubles), with region reuse
   static constexpr int SIZE = RC_END > RQ_END ? RC_END : RQ_END;
 };
 
-// mode 0: write du, de (residual test hook); mode 1: SSP combination into (uo, eo).
+// mode 0: write du, de (residual test hook); mode 1: SSP combination into (uo, eo);
+// mode 2: raw Lorentz load only (adjoint, see magnetic_adjoint.inc).
 template <int P, int KM, int MODE>
 __global__ void __launch_bounds__(256) k_mag_E(
     const double* __restrict__ LJx, const double* __restrict__ LJy, const double* __restrict__ LJz,
@@ -617,7 +618,8 @@ __global__ void __launch_bounds__(256) k_mag_E(
     }
   }
   // stage 6: x-pass onto DG nodes, velocity and energy rates, SSP combination
-  const double tau = MODE ? dtp[0] * dtfac : 0.0;
+  // (mode 2: the raw Lorentz load C_B^T J, no mass or density division)
+  const double tau = MODE == 1 ? dtp[0] * dtfac : 0.0;
   constexpr int I6 = D::n2;
   FLAT(I6) {
     int q = idx / D::EB, e = idx % D::EB, k = k0 + e;
@@ -636,6 +638,12 @@ __global__ void __launch_bounds__(256) k_mag_E(
       sz = fma(T.P_G[a][i], SM(O::VZ1, j * D::mm + a), sz);
     }
     size_t gq = (size_t)k * D::n2 + q;
+    if (MODE == 2) {
+      uo[gq] = sx;
+      uo[N + gq] = sy;
+      uo[2 * N + gq] = sz;
+      continue;
+    }
     double r_ = rho[gq];
     double im = rcp(r_ * Jd * T.wp[i] * T.wp[j]);
     double du[3] = {sx * im, sy * im, sz * im};
@@ -797,6 +805,8 @@ cudaError_t mag_prepare(int p, int k) {
 #undef MHD_MAG_PREP
   return e;
 }
+
+#include "magnetic_adjoint.inc"
 
 size_t mag_load_doubles(int p, int k, int K) {
   (void)p;

@@ -77,6 +77,12 @@ struct Stab {
   int max_halvings;
 };
 
+// Scratch of the magnetic-residual adjoint (doubles): mu, s [3N]; LT, LJ, LE
+// [element loads of the magnetic stage]; V [3Z]; LB [closure loads of B].
+struct MagAdjScratch {
+  double *mu, *s, *LT, *LJ, *LE, *V, *LB;
+};
+
 // Status word bits written by kernels.
 enum : unsigned {
   ST_INADMISSIBLE = 1u,

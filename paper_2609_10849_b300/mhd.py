@@ -77,6 +77,11 @@ _SIGS = {
     "mhd_batch_run": (C.c_void_p, [C.c_void_p, C.c_int]),
     "mhd_batch_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "mhd_batch_launch_count": (C.c_longlong, [C.c_void_p]),
+    "mhd_state_size": (C.c_longlong, [C.c_void_p]),
+    "mhd_adjoint_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
+                                   C.POINTER(C.c_int)]),
+    "mhd_hydro_rhs_vjp": (C.c_int, [C.c_void_p] + [C.c_void_p] * 3 + [C.c_int]),
+    "mhd_mag_rhs_vjp": (C.c_int, [C.c_void_p] + [C.c_void_p] * 14 + [C.c_int]),
     "mhd_status_string": (C.c_char_p, [C.c_int]),
     "mhd_last_error": (C.c_char_p, []),
 }
@@ -239,6 +244,53 @@ class Solver:
         ps = [_ptr(a)[0] for a in ins + [de, du, dBx, dBy, dBz]]
         _check(lib().mhd_mag_rhs(self._h, *ps, 0))
         return dict(de=de, du=du, dBx=dBx, dBy=dBy, dBz=dBz)
+
+    # -- packed state and adjoint ------------------------------------------
+    def state_size(self):
+        """Length of the packed state [U 5N | Bx G | By G | Bz Z] (host layouts)."""
+        return int(lib().mhd_state_size(self._h))
+
+    def _split(self, x):
+        N5, G, Z = 5 * self.N, self.G, self.Z
+        return x[:N5], x[N5:N5 + G], x[N5 + G:N5 + 2 * G], x[N5 + 2 * G:N5 + 2 * G + Z]
+
+    def set_packed(self, x):
+        """Set the state from a packed vector (numpy array or CUDA tensor)."""
+        self.set_state(*self._split(x))
+
+    def get_packed(self, out):
+        """Write the packed state into ``out`` (numpy array or CUDA tensor)."""
+        self.get_state(self._split(out))
+        return out
+
+    def adjoint_step(self, state, lam, dt, out=None):
+        """lam_n = (dS^dt/dx)(state)^T lam for one Strang step at fixed dt.
+
+        ``state``, ``lam`` and ``out`` are packed vectors, all numpy arrays or
+        all CUDA tensors; ``out`` may be ``lam``."""
+        if out is None:
+            out = np.zeros_like(lam) if isinstance(lam, np.ndarray) else lam.clone()
+        (ps, pl, po), dev = _ptrs(state, lam, out)
+        flags = C.c_int(0)
+        code = lib().mhd_adjoint_step(self._h, ps, pl, po, float(dt), dev, C.byref(flags))
+        if code < 0:
+            raise MhdError(code, lib().mhd_last_error().decode() + f" (flags {flags.value})")
+        return out
+
+    def hydro_rhs_vjp(self, U, nu):
+        f = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+        U, nu = f(U), f(nu)
+        out = np.zeros_like(U)
+        _check(lib().mhd_hydro_rhs_vjp(self._h, _ptr(U)[0], _ptr(nu)[0], _ptr(out)[0], 0))
+        return out
+
+    def mag_rhs_vjp(self, rho, u, Bx, By, Bz, w_u, w_Bx, w_By, w_Bz):
+        """VJP of the ideal magnetic residual: returns g_rho, g_u [3,N], g_Bx, g_By, g_Bz."""
+        f = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+        ins = [f(a) for a in (rho, u, Bx, By, Bz, w_u, w_Bx, w_By, w_Bz)]
+        outs = [np.zeros(self.N), np.zeros((3, self.N)), np.zeros(self.G), np.zeros(self.G), np.zeros(self.Z)]
+        _check(lib().mhd_mag_rhs_vjp(self._h, *[_ptr(a)[0] for a in ins + outs], 0))
+        return outs
 
     def diagnostics(self):
         d = Diag()

@@ -1,0 +1,252 @@
+"""Adjoint of the CUDA path (hand-written vector-Jacobian products through the
+C ABI) against the oracle's forward-mode tangent and against central finite
+differences of the CUDA forward.
+
+* residual VJPs: the full Jacobian on tiny meshes element by element
+  (rows from the GPU VJP with unit adjoints, columns from the oracle tangent
+  with unit directions), and the dot-product test <lam, J dx> = <J^T lam, dx>
+  on larger meshes for every (p, k);
+* one Strang step: the dot-product test against the oracle tangent of the
+  whole step;
+* a differentiable sequence of steps with checkpointing (torch.autograd):
+  directional derivatives of an objective against central differences.
+
+Tolerances: Jacobian entries 1e-11 of the largest entry; dot products 1e-12 of
+sum |lam_i (J dx)_i| (both sides are exact up to rounding); finite differences
+1e-6 relative (the spec bar for the adjoint).
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle, Tangent
+from tests.test_oracle_magnetic import random_mag_state
+from tests.test_oracle_tangent import generic_state
+
+pytestmark = pytest.mark.gpu
+
+PK = [(1, 0), (1, 1), (2, 1), (2, 2), (3, 2), (3, 3), (4, 3), (4, 4)]
+
+
+def solver_like(o):
+    from paper_2609_10849_b300.mhd import Solver
+    return Solver(o.nx, o.ny, o.p, o.m, o.gamma, o.domain)
+
+
+def dot_check(lam, Jdx, JTlam, dx, tol=1e-12):
+    a = sum(float((l * j).sum()) for l, j in zip(lam, Jdx))
+    b = sum(float((g * d).sum()) for g, d in zip(JTlam, dx))
+    scale = sum(float(np.abs(l * j).sum()) for l, j in zip(lam, Jdx))
+    assert abs(a - b) <= tol * scale, (a, b, abs(a - b) / scale)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_hydro_vjp_full_jacobian(p):
+    rng = np.random.default_rng(800 + p)
+    dom = (0.0, 1.0, 0.0, 0.8)
+    t = Tangent(2, 2, p, p, 1.4, dom)
+    U = generic_state(t, rng)
+    n = U.size
+    Jt = np.zeros((n, n))  # columns from the tangent
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        Jt[:, j] = t.hydro_rhs_tangent(U, e.reshape(U.shape))[1].ravel()
+    s = solver_like(t)
+    Jg = np.zeros((n, n))  # rows from the VJP
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        Jg[i, :] = s.hydro_rhs_vjp(U, e.reshape(U.shape)).ravel()
+    assert np.abs(Jg - Jt).max() <= 1e-11 * np.abs(Jt).max()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("mesh", [(5, 4), (3, 7)])
+def test_hydro_vjp_dot(p, mesh):
+    rng = np.random.default_rng(810 + 10 * p + mesh[0])
+    t = Tangent(*mesh, p, p, 1.4, (0.0, 1.0, 0.0, 0.8))
+    U = generic_state(t, rng)
+    dU = rng.standard_normal(U.shape)
+    lam = rng.standard_normal(U.shape)
+    dL = t.hydro_rhs_tangent(U, dU)[1]
+    g = solver_like(t).hydro_rhs_vjp(U, lam)
+    dot_check([lam], [dL], [g], [dU])
+
+
+def mag_inputs(o, rng):
+    rho, e, u, Bx, By, Bz = random_mag_state(o, rng)
+    return dict(rho=rho, e=e, u=u, Bx=Bx, By=By, Bz=Bz)
+
+
+@pytest.mark.parametrize("pk", [(1, 0), (1, 1), (2, 1)])
+def test_mag_vjp_full_jacobian(pk):
+    p, k = pk
+    rng = np.random.default_rng(830 + 10 * p + k)
+    t = Tangent(2, 2, p, k, 5 / 3, (0.0, 1.3, 0.0, 0.7))
+    st = mag_inputs(t, rng)
+    keys_in = ("rho", "u", "Bx", "By", "Bz")
+    sizes_in = [np.size(st[k_]) for k_ in keys_in]
+    keys_out = ("du", "dBx", "dBy", "dBz")
+    zero = {k_: np.zeros(np.shape(v)) for k_, v in st.items()}
+    n_in = sum(sizes_in)
+    cols = []
+    for j in range(n_in):
+        tang = {k_: v.copy() for k_, v in zero.items()}
+        off = j
+        for k_, sz in zip(keys_in, sizes_in):
+            if off < sz:
+                tang[k_].reshape(-1)[off] = 1.0
+                break
+            off -= sz
+        r, dr = t.mag_rhs_tangent(st, tang)
+        cols.append(np.concatenate([np.ravel(dr[k_]) for k_ in keys_out]))
+    Jt = np.stack(cols, axis=1)
+    s = solver_like(t)
+    n_out = Jt.shape[0]
+    N = t.K * t.n2
+    Jg = np.zeros_like(Jt)
+    for i in range(n_out):
+        w = np.zeros(n_out)
+        w[i] = 1.0
+        wu, wBx, wBy, wBz = np.split(w, np.cumsum([3 * N, t.G, t.G]))
+        g = s.mag_rhs_vjp(st["rho"], st["u"], st["Bx"], st["By"], st["Bz"], wu.reshape(3, N), wBx, wBy, wBz)
+        Jg[i, :] = np.concatenate([np.ravel(a) for a in g])
+    assert np.abs(Jg - Jt).max() <= 1e-11 * np.abs(Jt).max()
+
+
+@pytest.mark.parametrize("pk", PK)
+def test_mag_vjp_dot(pk):
+    p, k = pk
+    rng = np.random.default_rng(850 + 10 * p + k)
+    t = Tangent(5, 3, p, k, 5 / 3, (0.0, 1.3, 0.0, 0.7))
+    st = mag_inputs(t, rng)
+    tang = {k_: rng.standard_normal(np.shape(v)) for k_, v in st.items()}
+    tang["e"][:] = 0.0  # the ideal residual does not depend on e
+    _, dr = t.mag_rhs_tangent(st, tang)
+    w = {k_: rng.standard_normal(np.shape(dr[k_])) for k_ in ("du", "dBx", "dBy", "dBz")}
+    s = solver_like(t)
+    g = s.mag_rhs_vjp(st["rho"], st["u"], st["Bx"], st["By"], st["Bz"], w["du"], w["dBx"], w["dBy"], w["dBz"])
+    dot_check([w["du"], w["dBx"], w["dBy"], w["dBz"]], [dr["du"], dr["dBx"], dr["dBy"], dr["dBz"]], g,
+              [tang["rho"], tang["u"], tang["Bx"], tang["By"], tang["Bz"]])
+    assert np.abs(dr["de"]).max() == 0.0
+
+
+def packed(o, U, Bx, By, Bz):
+    return np.concatenate([np.ravel(U), Bx, By, Bz])
+
+
+@pytest.mark.parametrize("pk", [(1, 1), (2, 2), (3, 2), (3, 3), (4, 4)])
+def test_adjoint_step_dot(pk):
+    p, k = pk
+    rng = np.random.default_rng(870 + 10 * p + k)
+    dom = (0.0, 1.0, 0.0, 1.0)
+    t = Tangent(4, 3, p, k, 5 / 3, dom)
+    U = generic_state(t, rng)
+    Bx, By = rng.uniform(-0.5, 0.5, t.G), rng.uniform(-0.5, 0.5, t.G)
+    Bz = rng.uniform(-0.5, 0.5, t.Z)
+    x = [U, Bx, By, Bz]
+    dx = [rng.standard_normal(np.shape(a)) for a in x]
+    dt = 1e-3
+    t.set_state(*x)
+    t.set_tangent(*dx)
+    assert t.strang_step(dt)[0] == 0
+    Jdx = t.get_tangent()
+    s = solver_like(t)
+    lam = [rng.standard_normal(np.shape(a)) for a in x]
+    g = s.adjoint_step(packed(t, *x), packed(t, *lam), dt)
+    gs = np.split(g, np.cumsum([U.size, t.G, t.G]))
+    dot_check([np.ravel(a) for a in lam], [np.ravel(a) for a in Jdx], gs, [np.ravel(a) for a in dx])
+
+
+def test_adjoint_refuses_stabilisation():
+    from paper_2609_10849_b300.mhd import MhdError
+    rng = np.random.default_rng(890)
+    t = Tangent(3, 3, 2, 2, 5 / 3)
+    U = generic_state(t, rng)
+    s = solver_like(t)
+    x = packed(t, U, np.zeros(t.G), np.zeros(t.G), np.zeros(t.Z))
+    s.set_params(pp=1)
+    with pytest.raises(MhdError, match="flags 2"):
+        s.adjoint_step(x, x.copy(), 1e-3)
+    s.set_params(pp=0)
+    s.adjoint_step(x, x.copy(), 1e-3)
+
+
+def vortex_problem(n, p, dt_steps_cfl=True):
+    """Advected MHD vortex (§4.2) on an n x n mesh: solver, packed magnetic part,
+    nodal rho0, u0, p0 and the CFL step at t = 0."""
+    import torch
+    from paper_2609_10849_b300 import workloads
+    from paper_2609_10849_b300.mhd import Solver
+    wl = workloads.balsara_vortex()
+    s = Solver(n, n, p, p, wl["gamma"], wl["domain"])
+    X, Y = s.coords("dg")
+    rho, ux, uy, uz, pr, _ = wl["fields"](X, Y)
+    XW, YW = s.coords("w")
+    XZ, YZ = s.coords("bz")
+    s.set_primitive(rho, np.stack([ux, uy, uz]), pr)
+    s.set_B_from_potential(wl["Az"](XW, YW), *wl["B0"], wl["fields"](XZ, YZ)[5])
+    dt = s.compute_dt()
+    x = torch.zeros(s.state_size(), dtype=torch.float64, device="cuda")
+    s.get_packed(x)
+    B = x[5 * s.N:].clone()
+    t = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
+    return s, B, t(rho), t(np.stack([ux, uy, uz])), t(pr), dt, (X, Y)
+
+
+def target_density(X, Y, seed=20260910):
+    """Seeded perturbed initial density of the adjoint workload:
+    rho* = 1 + 0.01 sum_k a_k sin(2 pi (kx x + ky y)/10 + phi_k)."""
+    from paper_2609_10849_b300.workloads import Rng
+    r = Rng(seed + 5)
+    out = np.ones_like(X)
+    for _ in range(4):
+        a = r.uniform(-1, 1)
+        kx = 1 + int(r.uniform() * 2)
+        ky = 1 + int(r.uniform() * 2)
+        ph = r.uniform(0, 2 * np.pi)
+        out += 0.01 * a * np.sin(2 * np.pi * (kx * X + ky * Y) / 10 + ph)
+    return out
+
+
+def objective_setup(n, p, nsteps, every):
+    import torch
+    from paper_2609_10849_b300.adjoint import pack_primitive, strang_steps
+    s, B, rho0, u0, p0, dt, (X, Y) = vortex_problem(n, p)
+    g = s.gamma
+    # target: the end state of the run started from the perturbed density
+    rs = torch.tensor(target_density(X, Y), dtype=torch.float64, device="cuda")
+    with torch.no_grad():
+        xt = strang_steps(s, pack_primitive(rs, u0, p0, g, B), dt, nsteps, every)
+    rho_t = xt[:s.N].clone()
+    from oracle import rule
+    _, w = rule("gll", p)
+    hx = 10.0 / n
+    Mq = torch.tensor(np.tile(np.outer(w, w).ravel() * hx * hx / 4, s.K), device="cuda")
+
+    def J(rho, u):
+        x = strang_steps(s, pack_primitive(rho, u, p0, g, B), dt, nsteps, every)
+        return 0.5 * (Mq * (x[:s.N] - rho_t) ** 2).sum()
+
+    return J, rho0, u0
+
+
+@pytest.mark.parametrize("nsteps,every", [(6, 4), (5, 5)])
+def test_autograd_gradient_fd(nsteps, every):
+    import torch
+    J, rho0, u0 = objective_setup(8, 3, nsteps, every)
+    rho = rho0.clone().requires_grad_(True)
+    u = u0.clone().requires_grad_(True)
+    val = J(rho, u)
+    val.backward()
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    for _ in range(2):
+        dr = torch.randn(rho.shape, generator=gen, device="cuda", dtype=torch.float64)
+        du = torch.randn(u.shape, generator=gen, device="cuda", dtype=torch.float64)
+        eps = 1e-5
+        with torch.no_grad():
+            jp = J(rho0 + eps * dr, u0 + eps * du).item()
+            jm = J(rho0 - eps * dr, u0 - eps * du).item()
+        fd = (jp - jm) / (2 * eps)
+        ad = float((rho.grad * dr).sum() + (u.grad * du).sum())
+        assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
