@@ -42,69 +42,6 @@ __device__ __forceinline__ void prim_adjoint(const Prim& q, double g, double gr,
   out[0] += dr;
 }
 
-// Log-mean factor F(aL, aR) with a_log = (aL + aR)/(2F) (reading R1) and its
-// partial derivatives dF/daL, dF/daR.
-__device__ __forceinline__ double logmean_F(double aL, double aR, double* dFL, double* dFR) {
-  const double s = aL + aR, d = aL - aR;
-  const double f = d / s, u = f * f;
-  const double dfL = 2.0 * aR / (s * s), dfR = -2.0 * aL / (s * s);
-  if (u < 1e-4) {
-    const double F = 1.0 + u / 3.0 + u * u / 5.0 + u * u * u / 7.0;
-    const double dFdf = 2.0 * f * (1.0 / 3.0 + 2.0 * u / 5.0 + 3.0 * u * u / 7.0);
-    *dFL = dFdf * dfL;
-    *dFR = dFdf * dfR;
-    return F;
-  }
-  const double lz = log(aL / aR);
-  const double F = lz / (2.0 * f);
-  *dFL = (1.0 / aL) / (2.0 * f) - lz / (2.0 * f * f) * dfL;
-  *dFR = (-1.0 / aR) / (2.0 * f) - lz / (2.0 * f * f) * dfR;
-  return F;
-}
-
-// dL += (dF_ec/dUL)^T gF, dR += (dF_ec/dUR)^T gF (direction d).
-__device__ void ec_flux_vjp(int d, const double UL[5], const double UR[5], double g, const double gF[5], double dL[5],
-                            double dR[5]) {
-  const Prim L = prim_of(UL, g), R = prim_of(UR, g);
-  const double bL = L.r / (2.0 * L.p), bR = R.r / (2.0 * R.p);
-  double dFrL, dFrR, dFbL, dFbR;
-  const double Fr = logmean_F(L.r, R.r, &dFrL, &dFrR);
-  const double Fb = logmean_F(bL, bR, &dFbL, &dFbR);
-  const double sr = L.r + R.r, sb = bL + bR;
-  const double rlog = 0.5 * sr / Fr;
-  double ua[3];
-  for (int c = 0; c < 3; ++c) ua[c] = 0.5 * (L.u[c] + R.u[c]);
-  const double ig1 = 1.0 / (g - 1.0);
-  const double hhat = (Fb * ig1 + Fr) / sb - 0.25 * (L.u2 + R.u2) + ua[0] * ua[0] + ua[1] * ua[1] + ua[2] * ua[2];
-  const double ud = ua[d];
-  const double f0 = rlog * ud;
-  // reverse sweep
-  const double gf0 = gF[0] + gF[1] * ua[0] + gF[2] * ua[1] + gF[3] * ua[2] + gF[4] * hhat;
-  double gua[3] = {gF[1] * f0, gF[2] * f0, gF[3] * f0};
-  gua[d] += gf0 * rlog;
-  const double gphat = d == 0 ? gF[1] : gF[2];
-  const double ghhat = gF[4] * f0;
-  const double grlog = gf0 * ud;
-  double gFb = ghhat * ig1 / sb, gFr = ghhat / sb;
-  double gsb = -ghhat * (Fb * ig1 + Fr) / (sb * sb);
-  const double gu2a = -0.5 * ghhat;  // u2a = (|uL|^2 + |uR|^2)/2
-  for (int c = 0; c < 3; ++c) gua[c] += 2.0 * ua[c] * ghhat;
-  double gsr = 0.5 * gphat / sb;  // phat = sr / (2 sb)
-  gsb -= 0.5 * gphat * sr / (sb * sb);
-  gsr += 0.5 * grlog / Fr;  // rlog = sr / (2 Fr)
-  gFr -= 0.5 * grlog * sr / (Fr * Fr);
-  double guL[3], guR[3];
-  for (int c = 0; c < 3; ++c) {
-    guL[c] = 0.5 * gua[c] + gu2a * L.u[c];
-    guR[c] = 0.5 * gua[c] + gu2a * R.u[c];
-  }
-  const double grL = gsr + gFr * dFrL, grR = gsr + gFr * dFrR;
-  const double gbL = gsb + gFb * dFbL, gbR = gsb + gFb * dFbR;
-  // beta = rho / (2 p)
-  prim_adjoint(L, g, grL + gbL / (2.0 * L.p), guL, -gbL * bL / L.p, dL);
-  prim_adjoint(R, g, grR + gbR / (2.0 * R.p), guR, -gbR * bR / R.p, dR);
-}
-
 // out += (dF_d/dU)^T h for the physical flux F_d.
 __device__ void phys_flux_vjp(int d, const double U[5], double g, const double h[5], double out[5]) {
   const Prim q = prim_of(U, g);
@@ -182,61 +119,215 @@ __global__ void k_adj_face(const double* __restrict__ S, const double* __restric
   }
 }
 
-// Volume part and assembly: one thread per element.  out = (dL_E/dU)^T nu.
+// Pair tables of the forward volume kernel (hydro.cu): pair w of a line is
+// (c_pair_a[w], c_pair_b[w]) with w = b (b - 1) / 2 + a.
+__constant__ unsigned char c_apair_a[10] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3};
+__constant__ unsigned char c_apair_b[10] = {1, 2, 2, 3, 3, 3, 4, 4, 4, 4};
+
 template <int P>
-__global__ void k_adj_vol(const double* __restrict__ S, const double* __restrict__ nu, const double* __restrict__ FA,
-                          double* __restrict__ out, Mesh M, const Tab* __restrict__ T) {
-  constexpr int n = P + 1, n2 = n * n;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= M.K) return;
-  const size_t N = (size_t)M.K * n2, nf = (size_t)M.K * n;
-  const int ex = k % M.nx, ey = k / M.nx;
-  double lam[5][n2];
-  for (int c = 0; c < 5; ++c)
-    for (int q = 0; q < n2; ++q) lam[c][q] = 0.0;
-  for (int dir = 0; dir < 2; ++dir) {
-    const double cs = -4.0 / (dir == 0 ? M.hx : M.hy);
-    for (int line = 0; line < n; ++line)
-      for (int a = 0; a < n; ++a)
-        for (int b = a + 1; b < n; ++b) {
-          const int qa = dir == 0 ? line * n + a : a * n + line;
-          const int qb = dir == 0 ? line * n + b : b * n + line;
-          double Ua[5], Ub[5], gF[5], da[5] = {0, 0, 0, 0, 0}, db[5] = {0, 0, 0, 0, 0};
-          for (int c = 0; c < 5; ++c) {
-            Ua[c] = S[c * N + (size_t)k * n2 + qa];
-            Ub[c] = S[c * N + (size_t)k * n2 + qb];
-            gF[c] = cs * (T->D[a][b] * nu[c * N + (size_t)k * n2 + qa] + T->D[b][a] * nu[c * N + (size_t)k * n2 + qb]);
-          }
-          ec_flux_vjp(dir, Ua, Ub, M.g, gF, da, db);
-          for (int c = 0; c < 5; ++c) { lam[c][qa] += da[c]; lam[c][qb] += db[c]; }
-        }
+struct ACfg {
+  static constexpr int n = P + 1, n2 = n * n;
+  static constexpr int npairs = P * n2;        // unique pairs per element (both directions)
+  static constexpr int npl = n * (n - 1) / 2;  // pairs per line
+  static constexpr int EB = P == 1 ? 32 : (P == 2 ? 16 : (P == 3 ? 8 : 4));
+  static constexpr int threads = EB * n2;
+};
+
+// F(f) = atanh(f)/f with a_log = (aL + aR)/(2F), f = (aL - aR)/(aL + aR), and
+// F'(f): the Taylor series sum_k f^2k/(2k+1) for f^2 < 1e-2 (eight terms,
+// truncation below 1e-17), otherwise from per-node logarithms, lz = log aL -
+// log aR = 2 atanh(f): F = lz/(2f), F' = (1/(1 - f^2) - F)/f.
+__device__ __forceinline__ double logmean_FdF(double f, double lz, double* dF, double* iF) {
+  const double u = f * f;
+  if (u < 1e-2) {
+    const double c[8] = {1.0, 1.0 / 3.0, 1.0 / 5.0, 1.0 / 7.0, 1.0 / 9.0, 1.0 / 11.0, 1.0 / 13.0, 1.0 / 15.0};
+    double F = c[7], G = 7.0 * 2.0 * c[7];
+#pragma unroll
+    for (int k = 6; k >= 1; --k) {
+      F = fma(F, u, c[k]);
+      G = fma(G, u, 2.0 * k * c[k]);
+    }
+    F = fma(F, u, c[0]);
+    *dF = G * f;
+    *iF = rcp(F);
+    return F;
   }
-  // interface parts: node 0 of a line is the plus trace of the lower face of this
-  // element, node p the minus trace of the lower face of the upper neighbour
-  const int kE = ey * M.nx + wrap(ex + 1, M.nx), kN = wrap(ey + 1, M.ny) * M.nx + ex;
+  const double i2f = rcp(2.0 * f);
+  const double F = lz * i2f;
+  *dF = (rcp(1.0 - u) - F) * (2.0 * i2f);
+  *iF = (2.0 * f) / lz;
+  return F;
+}
+
+// Volume part and assembly: EB elements x (p+1)^2 threads, p pairs per
+// thread as in the forward kernel.  Each pair's reverse sweep yields the
+// adjoints of (rho, u, beta) of its two nodes (shared memory); each node then
+// sums its 2p pair contributions, converts them to the conservative adjoint
+// once, and adds the interface contributions of k_adj_face.
+template <int P>
+__global__ void __launch_bounds__(ACfg<P>::threads) k_adj_vol(const double* __restrict__ S,
+                                                              const double* __restrict__ nu,
+                                                              const double* __restrict__ FA,
+                                                              double* __restrict__ out, Mesh M,
+                                                              const Tab* __restrict__ T) {
+  using C = ACfg<P>;
+  constexpr int n = C::n, n2 = C::n2, EB = C::EB, NP = C::npairs, NPL = C::npl;
+  __shared__ double sp[8][EB * n2];   // rho, ux, uy, uz, beta, |u|^2, log rho, log beta
+  __shared__ double sn[5][EB * n2];   // nu
+  __shared__ double sg[10][EB * NP];  // pair outputs: (g_rho, g_u, g_beta) of node a, then of node b
+  const size_t N = (size_t)M.K * n2;
+  const int tid = threadIdx.x;
+  const int el = tid / n2, q = tid % n2;
+  const int k = blockIdx.x * EB + el;
+  const bool valid = k < M.K;
+  const int kk = valid ? k : M.K - 1;
+  const size_t gi = (size_t)kk * n2 + q;
+  const double g = M.g, ig1 = 1.0 / (g - 1.0);
+  double r0, u0[3], b0, u20;
+  {
+    double Us[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      Us[c] = S[c * N + gi];
+      sn[c][tid] = nu[c * N + gi];
+    }
+    const double ir = rcp(Us[0]);
+    u0[0] = Us[1] * ir; u0[1] = Us[2] * ir; u0[2] = Us[3] * ir;
+    u20 = fma(u0[0], u0[0], fma(u0[1], u0[1], u0[2] * u0[2]));
+    const double pr = (g - 1.0) * fma(-0.5 * Us[0], u20, Us[4]);
+    r0 = Us[0];
+    b0 = 0.5 * Us[0] * rcp(pr);
+    sp[0][tid] = r0; sp[1][tid] = u0[0]; sp[2][tid] = u0[1]; sp[3][tid] = u0[2];
+    sp[4][tid] = b0; sp[5][tid] = u20; sp[6][tid] = log(r0); sp[7][tid] = log(b0);
+  }
+  __syncthreads();
+  const double cs[2] = {-4.0 / M.hx, -4.0 / M.hy};
+#pragma unroll
+  for (int s = 0; s < P; ++s) {
+    const int pidx = q + s * n2;
+    const int d = pidx >= NP / 2;
+    const int r = pidx - d * (NP / 2);
+    const int line = r / NPL, w = r % NPL;
+    const int a = c_apair_a[w], b = c_apair_b[w];
+    const int qa = el * n2 + (d == 0 ? line * n + a : a * n + line);
+    const int qb = el * n2 + (d == 0 ? line * n + b : b * n + line);
+    // adjoint of the pair flux: it enters L_a with -(4/h) D_ab and L_b with -(4/h) D_ba
+    const double Dab = cs[d] * T->D[a][b], Dba = cs[d] * T->D[b][a];
+    double gF[5];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) gF[c] = fma(Dab, sn[c][qa], Dba * sn[c][qb]);
+    const double rL = sp[0][qa], rR = sp[0][qb], bL = sp[4][qa], bR = sp[4][qb];
+    const double sr = rL + rR, sb = bL + bR;
+    const double isr = rcp(sr), isb = rcp(sb);
+    const double fr = (rL - rR) * isr, fb = (bL - bR) * isb;
+    double dFr, dFb, iFr, iFb;
+    const double Fr = logmean_FdF(fr, sp[6][qa] - sp[6][qb], &dFr, &iFr);
+    const double Fb = logmean_FdF(fb, sp[7][qa] - sp[7][qb], &dFb, &iFb);
+    const double rlog = 0.5 * sr * iFr;
+    double ua[3];
+    ua[0] = 0.5 * (sp[1][qa] + sp[1][qb]);
+    ua[1] = 0.5 * (sp[2][qa] + sp[2][qb]);
+    ua[2] = 0.5 * (sp[3][qa] + sp[3][qb]);
+    const double u2a = 0.5 * (sp[5][qa] + sp[5][qb]);
+    const double au2 = fma(ua[0], ua[0], fma(ua[1], ua[1], ua[2] * ua[2]));
+    const double hnum = fma(Fb, ig1, Fr);
+    const double hhat = fma(hnum, isb, fma(-0.5, u2a, au2));
+    const double ud = d == 0 ? ua[0] : ua[1];
+    const double f0 = rlog * ud;
+    // reverse sweep
+    const double gf0 = fma(gF[1], ua[0], fma(gF[2], ua[1], fma(gF[3], ua[2], fma(gF[4], hhat, gF[0]))));
+    double gua[3] = {gF[1] * f0, gF[2] * f0, gF[3] * f0};
+    gua[d] = fma(gf0, rlog, gua[d]);
+    const double gphat = gF[1 + d];
+    const double ghhat = gF[4] * f0;
+    const double grlog = gf0 * ud;
+    const double gFb = ghhat * ig1 * isb;
+    double gFr = ghhat * isb;
+    double gsb = -ghhat * hnum * isb * isb;
+    const double gu2a = -0.5 * ghhat;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gua[c] = fma(2.0 * ua[c], ghhat, gua[c]);
+    double gsr = 0.5 * gphat * isb;
+    gsb -= 0.5 * gphat * sr * isb * isb;
+    gsr = fma(0.5 * grlog, iFr, gsr);
+    gFr -= grlog * rlog * iFr;
+    const double gfr = gFr * dFr, gfb = gFb * dFb;
+    const int o = el * NP + pidx;
+    sg[0][o] = fma(gfr * (1.0 - fr), isr, gsr);
+    sg[5][o] = fma(-gfr * (1.0 + fr), isr, gsr);
+    sg[4][o] = fma(gfb * (1.0 - fb), isb, gsb);
+    sg[9][o] = fma(-gfb * (1.0 + fb), isb, gsb);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      sg[1 + c][o] = fma(gu2a, sp[1 + c][qa], 0.5 * gua[c]);
+      sg[6 + c][o] = fma(gu2a, sp[1 + c][qb], 0.5 * gua[c]);
+    }
+  }
+  __syncthreads();
+  // gather the pair outputs of this node: x-pairs on row j, y-pairs on column i
+  const int i = q % n, j = q / n;
+  double gr = 0.0, gu[3] = {0.0, 0.0, 0.0}, gb = 0.0;
+#pragma unroll
+  for (int rr = 0; rr < n; ++rr) {
+    if (rr == i) continue;
+    const int o = el * NP + j * NPL + (i < rr ? rr * (rr - 1) / 2 + i : i * (i - 1) / 2 + rr);
+    const int side = i < rr ? 0 : 5;
+    gr += sg[side][o]; gu[0] += sg[side + 1][o]; gu[1] += sg[side + 2][o]; gu[2] += sg[side + 3][o];
+    gb += sg[side + 4][o];
+  }
+#pragma unroll
+  for (int rr = 0; rr < n; ++rr) {
+    if (rr == j) continue;
+    const int o = el * NP + NP / 2 + i * NPL + (j < rr ? rr * (rr - 1) / 2 + j : j * (j - 1) / 2 + rr);
+    const int side = j < rr ? 0 : 5;
+    gr += sg[side][o]; gu[0] += sg[side + 1][o]; gu[1] += sg[side + 2][o]; gu[2] += sg[side + 3][o];
+    gb += sg[side + 4][o];
+  }
+  // (rho, u, beta) -> conservative: beta = rho/(2p), p = (g-1)(E - rho |u|^2/2)
+  const double ir = rcp(r0);
+  const double gp = -2.0 * gb * b0 * b0 * ir;  // dbeta/dp = -beta/p, 1/p = 2 beta/rho
+  gr = fma(gb * b0, ir, gr);                  // dbeta/drho at fixed p = 1/(2p)
+  double res[5];
+  res[4] = (g - 1.0) * gp;
+  double dr = fma(0.5 * u20, res[4], gr);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    res[1 + c] = fma(gu[c], ir, -res[4] * u0[c]);
+    dr -= gu[c] * u0[c] * ir;
+  }
+  res[0] = dr;
+  // interface parts: node 0 of a line is the plus trace of the element's lower
+  // face, node p the minus trace of the lower face of the next element
+  const size_t nf = (size_t)M.K * n;
+  const int ex = kk % M.nx, ey = kk / M.nx;
   const double* FAx = FA;
   const double* FAy = FA + 2 * 5 * nf;
-  for (int j = 0; j < n; ++j)
-    for (int c = 0; c < 5; ++c) {
-      lam[c][j * n + 0] += FAx[(1 * 5 + c) * nf + (size_t)k * n + j];
-      lam[c][j * n + P] += FAx[(0 * 5 + c) * nf + (size_t)kE * n + j];
-      lam[c][0 * n + j] += FAy[(1 * 5 + c) * nf + (size_t)k * n + j];
-      lam[c][P * n + j] += FAy[(0 * 5 + c) * nf + (size_t)kN * n + j];
-    }
-  for (int c = 0; c < 5; ++c)
-    for (int q = 0; q < n2; ++q) out[c * N + (size_t)k * n2 + q] = lam[c][q];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    double v = res[c];
+    if (i == 0) v += FAx[(5 + c) * nf + (size_t)kk * n + j];
+    if (i == P) v += FAx[c * nf + (size_t)(ey * M.nx + wrap(ex + 1, M.nx)) * n + j];
+    if (j == 0) v += FAy[(5 + c) * nf + (size_t)kk * n + i];
+    if (j == P) v += FAy[c * nf + (size_t)(wrap(ey + 1, M.ny) * M.nx + ex) * n + i];
+    if (valid) out[c * N + gi] = v;
+  }
 }
 
 void hydro_rhs_vjp(int p, const double* S, const double* nu, double* FA, double* out, const Mesh& M, const Tab* T,
                    cudaStream_t st) {
   const size_t nf = (size_t)M.K * (p + 1);
-  const unsigned bf = (unsigned)((2 * nf + 127) / 128), bv = (unsigned)((M.K + 63) / 64);
+  const unsigned bf = (unsigned)((2 * nf + 127) / 128);
+#define MHD_ADJ_H(PP)                                                                                   \
+  k_adj_face<PP><<<bf, 128, 0, st>>>(S, nu, FA, M, T);                                                 \
+  k_adj_vol<PP><<<(unsigned)((M.K + ACfg<PP>::EB - 1) / ACfg<PP>::EB), ACfg<PP>::threads, 0, st>>>(S, nu, FA, \
+                                                                                                    out, M, T)
   switch (p) {
-    case 1: k_adj_face<1><<<bf, 128, 0, st>>>(S, nu, FA, M, T); k_adj_vol<1><<<bv, 64, 0, st>>>(S, nu, FA, out, M, T); break;
-    case 2: k_adj_face<2><<<bf, 128, 0, st>>>(S, nu, FA, M, T); k_adj_vol<2><<<bv, 64, 0, st>>>(S, nu, FA, out, M, T); break;
-    case 3: k_adj_face<3><<<bf, 128, 0, st>>>(S, nu, FA, M, T); k_adj_vol<3><<<bv, 64, 0, st>>>(S, nu, FA, out, M, T); break;
-    case 4: k_adj_face<4><<<bf, 128, 0, st>>>(S, nu, FA, M, T); k_adj_vol<4><<<bv, 64, 0, st>>>(S, nu, FA, out, M, T); break;
+    case 1: MHD_ADJ_H(1); break;
+    case 2: MHD_ADJ_H(2); break;
+    case 3: MHD_ADJ_H(3); break;
+    case 4: MHD_ADJ_H(4); break;
   }
+#undef MHD_ADJ_H
 }
 
 // ---- pointwise adjoint pieces -------------------------------------------------
