@@ -196,14 +196,14 @@ def run_reference(args, rank):
     }), flush=True)
 
 
-def run_batch(args):
+def batch_leg(nruns, steps):
     """Batched workload: nruns independent Orszag-Tang variants with seeded
     uneven meshes and degrees, all stabilisation on, advanced by one CUDA-graph
     launch per call, against the same runs advanced one at a time."""
     import torch
     from paper_2609_10849_b300 import workloads
     from paper_2609_10849_b300.mhd import Batch
-    specs = workloads.batch_specs(args.batch)
+    specs = workloads.batch_specs(nruns)
     wls = [workloads.orszag_tang_variant(i) for i in range(len(specs))]
     full = [(N, N, p, p, wl["gamma"], wl["domain"]) for (N, p), wl in zip(specs, wls)]
     t0 = time.perf_counter()
@@ -220,27 +220,95 @@ def run_batch(args):
     dts = np.array([r.compute_dt() for r in batch.runs])
     setup = time.perf_counter() - t0
     dofs = sum(dofs_per_element(p, p) * N * N for N, p in specs)
-    batch.step(dts, args.steps)  # capture + warm-up
+    batch.step(dts, steps)  # capture + warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    batch.step(dts, args.steps)
+    batch.step(dts, steps)
     torch.cuda.synchronize()
     tb = time.perf_counter() - t0
     for r, dt in zip(batch.runs, dts):  # sequential: one run at a time through the plain path
-        r.strang_steps(dt, args.steps)
+        r.strang_steps(dt, steps)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for r, dt in zip(batch.runs, dts):
-        r.strang_steps(dt, args.steps)
+        r.strang_steps(dt, steps)
     torch.cuda.synchronize()
     ts = time.perf_counter() - t0
-    print(json.dumps({
+    out = {
         "metric": "FP64 DOF-updates/s, batched vs sequential", "unit": UNIT, "runs": len(specs),
-        "elements": int(sum(N * N for N, _ in specs)), "steps": args.steps,
-        "batched": dofs * args.steps / tb, "sequential": dofs * args.steps / ts, "speedup": ts / tb,
+        "elements": int(sum(N * N for N, _ in specs)), "steps": steps,
+        "batched": dofs * steps / tb, "sequential": dofs * steps / ts, "speedup": ts / tb,
         "setup_s": setup, "degrees": {str(p): sum(1 for _, q in specs if q == p) for p in (2, 3, 4)},
-        "config": {"workload": "orszag_tang_variants_batch", "stabilization": STAB, "seed": workloads.SEED}}),
-        flush=True)
+        "config": {"workload": "orszag_tang_variants_batch", "stabilization": STAB, "seed": workloads.SEED}}
+    batch.close()
+    return out
+
+
+def gll_weights(p):
+    """GLL(p) quadrature weights 2/(p(p+1) P_p(x_i)^2) (nodes: +-1 and the roots
+    of P_p'), for the objective's mass weights."""
+    from numpy.polynomial import legendre as L
+    x = np.concatenate([[-1.0], np.sort(L.Legendre.basis(p).deriv().roots().real), [1.0]])
+    return 2.0 / (p * (p + 1) * L.legval(x, [0] * p + [1]) ** 2)
+
+
+def adjoint_leg(steps=20, every=20, n=128, p=4):
+    """Adjoint workload: the advected MHD vortex (§4.2) on n x n elements of
+    [-5,5]^2, p = k = 4, fixed dt (CFL at t = 0), stabilisation off.  Times
+    `steps` forward Strang steps and the checkpointed backward pass of the
+    objective 1/2 sum_q M_q (rho_q(T) - rho*_q(T))^2 (a seeded perturbed run
+    gives rho*), against the plain forward of the same steps."""
+    import torch
+    from paper_2609_10849_b300 import workloads
+    from paper_2609_10849_b300.adjoint import pack_primitive, strang_steps
+    from paper_2609_10849_b300.mhd import Solver
+    wl = workloads.balsara_vortex()
+    s = Solver(n, n, p, p, wl["gamma"], wl["domain"])
+    X, Y = s.coords("dg")
+    rho, ux, uy, uz, pr, _ = wl["fields"](X, Y)
+    XW, YW = s.coords("w")
+    XZ, YZ = s.coords("bz")
+    s.set_primitive(rho, np.stack([ux, uy, uz]), pr)
+    s.set_B_from_potential(wl["Az"](XW, YW), *wl["B0"], wl["fields"](XZ, YZ)[5])
+    dt = s.compute_dt()
+    x = torch.zeros(s.state_size(), dtype=torch.float64, device="cuda")
+    s.get_packed(x)
+    dev = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    B, r0, u0, p0 = x[5 * s.N:].clone(), dev(rho), dev(np.stack([ux, uy, uz])), dev(pr)
+    rs = dev(workloads.vortex_target_density(X, Y))
+    with torch.no_grad():
+        target = strang_steps(s, pack_primitive(rs, u0, p0, s.gamma, B), dt, steps, every)[:s.N].clone()
+    Mq = dev(np.tile(np.outer(gll_weights(p), gll_weights(p)).ravel() * (10.0 / n) ** 2 / 4, s.K))
+    rho_v = r0.clone().requires_grad_(True)
+    u_v = u0.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    xT = strang_steps(s, pack_primitive(rho_v, u_v, p0, s.gamma, B), dt, steps, every)
+    J = 0.5 * (Mq * (xT[:s.N] - target) ** 2).sum()
+    torch.cuda.synchronize()
+    tf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    J.backward()
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    s.set_packed(x)
+    s.strang_steps(dt, steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.strang_steps(dt, steps)
+    torch.cuda.synchronize()
+    tp = time.perf_counter() - t0
+    dofs = dofs_per_element(p, p) * s.K
+    return {"workload": f"balsara_vortex_{n}x{n}_p{p}k{p}", "steps": steps, "checkpoint_every": every, "dt": dt,
+            "plain_ms_per_step": 1e3 * tp / steps, "forward_ms_per_step": 1e3 * tf / steps,
+            "backward_ms_per_step": 1e3 * tb / steps, "backward_over_plain": tb / tp,
+            "plain_dof_updates_per_s": dofs * steps / tp, "adjoint_dof_updates_per_s": dofs * steps / tb,
+            "note": "backward = segment recomputation + one mhd_adjoint_step per step (which recomputes its "
+                    "stage states); forward includes checkpoint copies"}
+
+
+def run_batch(args):
+    print(json.dumps(batch_leg(args.batch, args.steps)), flush=True)
 
 
 def main():
@@ -252,6 +320,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mesh", type=int, default=256, help="elements per direction (256 is the benchmark workload)")
     ap.add_argument("--batch", type=int, default=0, help="run the batched workload with this many runs instead")
+    ap.add_argument("--no-side-legs", action="store_true", help="skip the adjoint and batched side measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -349,6 +418,9 @@ def main():
             "config": dict(workload_config(stab, args.mesh), parallelism=f"replicas{world}", dt=dt),
             "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
         }
+        if not args.no_side_legs and world == 1:
+            line["adjoint"] = adjoint_leg()
+            line["batched"] = batch_leg(256, 2)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

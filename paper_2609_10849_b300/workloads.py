@@ -207,6 +207,21 @@ def density_wave(amp=0.2, u=(1.0, 0.5, 0.3), p0=1.0, gamma=1.4):
                 gamma=gamma)
 
 
+def vortex_target_density(X, Y, seed: int = SEED):
+    """Seeded perturbed initial density of the adjoint workload (a target run
+    starts from it): rho* = 1 + 0.01 sum_{k=1..4} a_k sin(2 pi (kx_k x + ky_k y)/10
+    + phi_k), a_k ~ U(-1, 1), kx_k, ky_k in {1, 2}, phi_k ~ U(0, 2 pi)."""
+    r = Rng(seed + 5)
+    out = np.ones_like(X)
+    for _ in range(4):
+        a = r.uniform(-1, 1)
+        kx = 1 + min(int(r.uniform() * 2), 1)
+        ky = 1 + min(int(r.uniform() * 2), 1)
+        ph = r.uniform(0, 2 * math.pi)
+        out = out + 0.01 * a * np.sin(2 * np.pi * (kx * X + ky * Y) / 10 + ph)
+    return out
+
+
 BATCH_MESHES = (32, 48, 64, 96, 128, 192, 256)
 BATCH_DEGREES = (2, 3, 4)
 

@@ -194,28 +194,14 @@ def vortex_problem(n, p, dt_steps_cfl=True):
     return s, B, t(rho), t(np.stack([ux, uy, uz])), t(pr), dt, (X, Y)
 
 
-def target_density(X, Y, seed=20260910):
-    """Seeded perturbed initial density of the adjoint workload:
-    rho* = 1 + 0.01 sum_k a_k sin(2 pi (kx x + ky y)/10 + phi_k)."""
-    from paper_2609_10849_b300.workloads import Rng
-    r = Rng(seed + 5)
-    out = np.ones_like(X)
-    for _ in range(4):
-        a = r.uniform(-1, 1)
-        kx = 1 + int(r.uniform() * 2)
-        ky = 1 + int(r.uniform() * 2)
-        ph = r.uniform(0, 2 * np.pi)
-        out += 0.01 * a * np.sin(2 * np.pi * (kx * X + ky * Y) / 10 + ph)
-    return out
-
-
 def objective_setup(n, p, nsteps, every):
     import torch
     from paper_2609_10849_b300.adjoint import pack_primitive, strang_steps
     s, B, rho0, u0, p0, dt, (X, Y) = vortex_problem(n, p)
     g = s.gamma
     # target: the end state of the run started from the perturbed density
-    rs = torch.tensor(target_density(X, Y), dtype=torch.float64, device="cuda")
+    from paper_2609_10849_b300.workloads import vortex_target_density
+    rs = torch.tensor(vortex_target_density(X, Y), dtype=torch.float64, device="cuda")
     with torch.no_grad():
         xt = strang_steps(s, pack_primitive(rs, u0, p0, g, B), dt, nsteps, every)
     rho_t = xt[:s.N].clone()
@@ -250,3 +236,22 @@ def test_autograd_gradient_fd(nsteps, every):
         fd = (jp - jm) / (2 * eps)
         ad = float((rho.grad * dr).sum() + (u.grad * du).sum())
         assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+
+
+def test_vortex_adjoint_full_size():
+    """The adjoint workload at full size: 128 x 128 elements, p = k = 4, 200
+    Strang steps at the t = 0 CFL step, checkpoints every 20; the gradient with
+    respect to the initial density and velocity against central differences."""
+    import torch
+    J, rho0, u0 = objective_setup(128, 4, 200, 20)
+    rho = rho0.clone().requires_grad_(True)
+    u = u0.clone().requires_grad_(True)
+    J(rho, u).backward()
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    dr = torch.randn(rho.shape, generator=gen, device="cuda", dtype=torch.float64)
+    du = torch.randn(u.shape, generator=gen, device="cuda", dtype=torch.float64)
+    eps = 1e-5
+    with torch.no_grad():
+        fd = (J(rho0 + eps * dr, u0 + eps * du).item() - J(rho0 - eps * dr, u0 - eps * du).item()) / (2 * eps)
+    ad = float((rho.grad * dr).sum() + (u.grad * du).sum())
+    assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
