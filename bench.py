@@ -321,6 +321,7 @@ def main():
     ap.add_argument("--mesh", type=int, default=256, help="elements per direction (256 is the benchmark workload)")
     ap.add_argument("--batch", type=int, default=0, help="run the batched workload with this many runs instead")
     ap.add_argument("--no-side-legs", action="store_true", help="skip the adjoint and batched side measurements")
+    ap.add_argument("--leg", default="", choices=["", "adjoint"], help="run only this side measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -333,6 +334,9 @@ def main():
         return
     if args.batch:
         run_batch(args)
+        return
+    if args.leg == "adjoint":
+        print(json.dumps(adjoint_leg()), flush=True)
         return
 
     import torch

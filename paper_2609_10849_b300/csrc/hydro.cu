@@ -36,13 +36,14 @@ __device__ __forceinline__ int pair_index(int a, int b) {  // a < b
 
 // Log-mean factor F with a_log = (aL + aR) / (2 F) and its reciprocal
 // (reading R1: Ismail-Roe series for u = f^2 < 1e-4, logarithm otherwise).
-// f = (aL - aR)/(aL + aR) is passed in; returns 1/F in *invF and F.
+// f = (aL - aR)/(aL + aR) is passed in; returns 1/F in *invF and F.  On the
+// series branch 1/F is the reciprocal series 1 - u/3 - 4u^2/45 - 44u^3/945
+// (from F (1/F) = 1 term by term; the first omitted term is below 1e-17).
 __device__ __forceinline__ double logmean_factor(double aL, double aR, double f, double* invF) {
   double u = f * f;
   if (u < 1e-4) {
-    double F = fma(u, fma(u, fma(u, 1.0 / 7.0, 1.0 / 5.0), 1.0 / 3.0), 1.0);
-    *invF = rcp(F);
-    return F;
+    *invF = fma(u, fma(u, fma(u, -44.0 / 945.0, -4.0 / 45.0), -1.0 / 3.0), 1.0);
+    return fma(u, fma(u, fma(u, 1.0 / 7.0, 1.0 / 5.0), 1.0 / 3.0), 1.0);
   }
   double lz = log(aL / aR);
   double F = lz / (2.0 * f);
@@ -106,7 +107,7 @@ __global__ void __launch_bounds__(HCfg<P>::threads) k_vol(const double* __restri
                                                           double ca, double cb, int first) {
   using C = HCfg<P>;
   constexpr int n = C::n, n2 = C::n2, EB = C::EB, NP = C::npairs, NPL = C::npl;
-  __shared__ double sp[6][EB * n2];           // rho, ux, uy, uz, beta, |u|^2
+  __shared__ double sp[6][EB * n2];           // rho/2, ux/2, uy/2, uz/2, beta, |u|^2/2
   __shared__ double sf[5][EB * NP];           // pair fluxes
   __shared__ double savg[5][EB];
   const size_t N = (size_t)M.K * n2;
@@ -126,10 +127,11 @@ __global__ void __launch_bounds__(HCfg<P>::threads) k_vol(const double* __restri
     double ux = Us[1] * ir, uy = Us[2] * ir, uz = Us[3] * ir;
     double u2 = fma(ux, ux, fma(uy, uy, uz * uz));
     double pr = (g - 1.0) * fma(-0.5 * Us[0], u2, Us[4]);
-    sp[0][tid] = Us[0];
-    sp[1][tid] = ux; sp[2][tid] = uy; sp[3][tid] = uz;
+    // halves: the pair means {{.}} become plain sums (scaling by 1/2 is exact)
+    sp[0][tid] = 0.5 * Us[0];
+    sp[1][tid] = 0.5 * ux; sp[2][tid] = 0.5 * uy; sp[3][tid] = 0.5 * uz;
     sp[4][tid] = 0.5 * Us[0] * rcp(pr);
-    sp[5][tid] = u2;
+    sp[5][tid] = 0.5 * u2;
   }
   __syncthreads();
 
@@ -144,21 +146,21 @@ __global__ void __launch_bounds__(HCfg<P>::threads) k_vol(const double* __restri
     const int a = c_pair_a[w], b = c_pair_b[w];
     const int qa = el * n2 + (d == 0 ? line * n + a : a * n + line);
     const int qb = el * n2 + (d == 0 ? line * n + b : b * n + line);
-    double rL = sp[0][qa], rR = sp[0][qb];
+    double rL = sp[0][qa], rR = sp[0][qb];              // rho/2 of both nodes
     double bL = sp[4][qa], bR = sp[4][qb];
-    double sr = rL + rR, sb = bL + bR;
-    double isr = rcp(sr), isb = rcp(sb);
+    double hr = rL + rR, sb = bL + bR;                  // {{rho}}, 2 {{beta}}
+    double isr = rcp(hr), isb = rcp(sb);
     double fr = (rL - rR) * isr, fb = (bL - bR) * isb;
     double iFr, iFb;
     double Fr = logmean_factor(rL, rR, fr, &iFr);
     double Fb = logmean_factor(bL, bR, fb, &iFb);
-    double rlog = 0.5 * sr * iFr;                       // rho^log
-    double ua0 = 0.5 * (sp[1][qa] + sp[1][qb]);
-    double ua1 = 0.5 * (sp[2][qa] + sp[2][qb]);
-    double ua2 = 0.5 * (sp[3][qa] + sp[3][qb]);
-    double u2a = 0.5 * (sp[5][qa] + sp[5][qb]);         // {{|u|^2}}
+    double rlog = hr * iFr;                             // rho^log
+    double ua0 = sp[1][qa] + sp[1][qb];
+    double ua1 = sp[2][qa] + sp[2][qb];
+    double ua2 = sp[3][qa] + sp[3][qb];
+    double u2a = sp[5][qa] + sp[5][qb];                 // {{|u|^2}}
     double au2 = fma(ua0, ua0, fma(ua1, ua1, ua2 * ua2));  // |{{u}}|^2
-    double phat = 0.5 * sr * isb;                       // {{rho}} / (2 {{beta}})
+    double phat = hr * isb;                             // {{rho}} / (2 {{beta}})
     // h = 1/(2(g-1) beta^log) - {{|u|^2}}/2 + |{{u}}|^2 + phat/rho^log
     //   = Fb/((g-1) sb) ... with beta^log = sb/(2 Fb) and rho^log = sr/(2 Fr)
     double hhat = fma(Fb * ig1 + Fr, isb, fma(-0.5, u2a, au2));
@@ -227,22 +229,34 @@ __global__ void __launch_bounds__(HCfg<P>::threads) k_vol(const double* __restri
     for (int c = 0; c < 5; ++c) out[c * N + gi] = Cv[c];
   }
   // ---- raw element averages and the admissibility check --------------------------
-  __syncthreads();  // sp is reused for the weighted values
-  const double wq = 0.25 * T->wp[i] * T->wp[j];
+  double a0, a1, a2, a3, a4;
+  if constexpr (n2 == 4 || n2 == 16) {
+    // an element is an aligned power-of-two lane segment: xor-shuffle sums
+    const double wq = 0.25 * T->wp[i] * T->wp[j];
+    double w[5];
 #pragma unroll
-  for (int c = 0; c < 5; ++c) sf[c][el * n2 + q] = Cv[c];
-  __syncthreads();
-  // component c is reduced by node thread c mod n2 (p = 1 has only 4 nodes per element)
-  for (int c = q; c < 5; c += n2) {
-    double s = 0.0;
+    for (int c = 0; c < 5; ++c) w[c] = wq * Cv[c];
 #pragma unroll
-    for (int t2 = 0; t2 < n2; ++t2) s = fma(0.25 * T->wp[t2 % n] * T->wp[t2 / n], sf[c][el * n2 + t2], s);
-    savg[c][el] = s;
+    for (int o = n2 / 2; o > 0; o >>= 1)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) w[c] += __shfl_xor_sync(0xffffffffu, w[c], o);
+    a0 = w[0]; a1 = w[1]; a2 = w[2]; a3 = w[3]; a4 = w[4];
+  } else {
+    __syncthreads();  // sf is reused for the stage values
+#pragma unroll
+    for (int c = 0; c < 5; ++c) sf[c][el * n2 + q] = Cv[c];
+    __syncthreads();
+    // component c is reduced by node thread c mod n2
+    for (int c = q; c < 5; c += n2) {
+      double s = 0.0;
+#pragma unroll
+      for (int t2 = 0; t2 < n2; ++t2) s = fma(0.25 * T->wp[t2 % n] * T->wp[t2 / n], sf[c][el * n2 + t2], s);
+      savg[c][el] = s;
+    }
+    __syncthreads();
+    a0 = savg[0][el]; a1 = savg[1][el]; a2 = savg[2][el]; a3 = savg[3][el]; a4 = savg[4][el];
   }
-  (void)wq;
-  __syncthreads();
   if (q == 0 && valid) {
-    double a0 = savg[0][el], a1 = savg[1][el], a2 = savg[2][el], a3 = savg[3][el], a4 = savg[4][el];
     if (avg_out) {
       avg_out[0 * (size_t)M.K + k] = a0; avg_out[1 * (size_t)M.K + k] = a1; avg_out[2 * (size_t)M.K + k] = a2;
       avg_out[3 * (size_t)M.K + k] = a3; avg_out[4 * (size_t)M.K + k] = a4;

@@ -14,7 +14,9 @@
 // The sensor statistics are shared by both OE procedures: k_stats writes per
 // element and component the average, nodal max/min and the jump measures of
 // its -x and -y faces; k_lines reduces rows and columns in a fixed order;
-// k_global reduces the rows.  Readings R6-R9 of the design notes apply.
+// k_global reduces the rows and tabulates the reciprocal shared amplitude of
+// every row and column and the order factors of the sensor.  Readings R6-R9 of
+// the design notes apply.
 #include <cfloat>
 
 #include "mhd_internal.cuh"
@@ -33,6 +35,8 @@ struct StatsView {
   double* ar;    // [K][8] A.R. per-element partials
   double* arg;   // [8] A.R. global values
   double* part;  // [ceil(K/256)][9] A.R. chunk partials
+  double* lineD; // [2][L] 1 / Delta_{I,line} (eq. euler-oe-shared-amplitude), from k_global
+  double* rfac;  // [2][8] (2r + 1) h_I^r / (2 r!) of eq. euler-oe-sigma, from k_global
 };
 
 static StatsView stats_view(double* work, int p, const Mesh& M) {
@@ -49,13 +53,15 @@ static StatsView stats_view(double* work, int p, const Mesh& M) {
   v.ar = v.glob + NC * 4;
   v.arg = v.ar + 8 * K;
   v.part = v.arg + 8;
+  v.lineD = v.part + 9 * (K / 256 + 1);
+  v.rfac = v.lineD + 2 * L;
   return v;
 }
 
 size_t stab_work_doubles(int p, int k, const Mesh& M) {
   (void)k;
   const size_t K = M.K, n = p + 1, L = M.nx > M.ny ? M.nx : M.ny;
-  return 3 * 5 * K + 2 * 5 * n * K + 2 * L * 5 * 3 + 5 * 4 + 8 * K + 8 + 9 * (K / 256 + 1) + 64;
+  return 3 * 5 * K + 2 * 5 * n * K + 2 * L * 5 * 3 + 5 * 4 + 8 * K + 8 + 9 * (K / 256 + 1) + 2 * L + 16 + 64;
 }
 
 size_t stab_chol_doubles(int p, const Mesh& M) {
@@ -97,8 +103,9 @@ __global__ void k_stats(const double* __restrict__ F, size_t stride, int nc, Sta
   const int I = (w - 1) / n, r = (w - 1) % n;
   const int kA = I == 0 ? ey * M.nx + wrap(ex - 1, M.nx) : wrap(ey - 1, M.ny) * M.nx + ex;  // lower side
   const double h = I == 0 ? M.hx : M.hy;
+  const double ih = rcp(0.5 * h);
   double scale = 1.0;  // (2/h)^r, applied once to the averaged square
-  for (int i = 0; i < r; ++i) scale *= 2.0 / h;
+  for (int i = 0; i < r; ++i) scale *= ih;
   double acc = 0.0;
   if (r == 0) {  // the traces themselves: end nodes of the two elements
 #pragma unroll
@@ -164,7 +171,7 @@ __global__ void k_lines(int nc, StatsView V, Mesh M) {
 }
 
 // ---- k_global: from the row reductions --------------------------------------------
-__global__ void k_global(int nc, StatsView V, Mesh M) {
+__global__ void k_global(int nc, int n, StatsView V, Mesh M) {
   __shared__ double s_sum[256], s_max[256], s_min[256];
   const int Lmax = M.nx > M.ny ? M.nx : M.ny;
   for (int c = 0; c < nc; ++c) {
@@ -193,40 +200,46 @@ __global__ void k_global(int nc, StatsView V, Mesh M) {
     }
     __syncthreads();
   }
-  (void)Lmax;
-}
-
-// Shared amplitude Delta_{I,K} (eq. euler-oe-shared-amplitude) of the line of element (ex, ey).
-__device__ __forceinline__ double shared_amp(const StatsView& V, int nc, int I, int ex, int ey, const Mesh& M) {
-  const int Lmax = M.nx > M.ny ? M.nx : M.ny;
-  const int L = I == 0 ? ey : ex, len = I == 0 ? M.nx : M.ny;
-  double D = 0.0;
-  const double ilen = 1.0 / len;
-  for (int c = 0; c < nc; ++c) {
-    const double* o = V.line + (((size_t)I * Lmax + L) * nc + c) * 3;
-    double mean = o[0] * ilen;
-    double amp = fmax(o[1] - mean, mean - o[2]);
-    D = fmax(D, fmax(amp, 1e-6 * V.glob[c * 4 + 1]));
+  // 1 / Delta_{I,L} of every row (I = 0) and column (I = 1), with the global
+  // amplitude floor, and the order factors of the sensor
+  for (int t = threadIdx.x; t < 2 * Lmax; t += blockDim.x) {
+    const int I = t / Lmax, L = t % Lmax;
+    const int nl = I == 0 ? M.ny : M.nx, len = I == 0 ? M.nx : M.ny;
+    if (L >= nl) continue;
+    const double ilen = 1.0 / len;
+    double D = 0.0;
+    for (int c = 0; c < nc; ++c) {
+      const double* o = V.line + (((size_t)I * Lmax + L) * nc + c) * 3;
+      const double mean = o[0] * ilen;
+      const double amp = fmax(o[1] - mean, mean - o[2]);
+      D = fmax(D, fmax(amp, 1e-6 * V.glob[c * 4 + 1]));
+    }
+    V.lineD[t] = 1.0 / D;
   }
-  return D;
+  if (threadIdx.x < 2 * n) {
+    const int I = threadIdx.x / n, r = threadIdx.x % n;
+    const double h = I == 0 ? M.hx : M.hy;
+    double hr = 1.0, fact = 1.0;
+    for (int i = 0; i < r; ++i) { hr *= h; fact *= (i + 1); }
+    V.rfac[I * 8 + r] = (2.0 * r + 1.0) * hr / (2.0 * fact);
+  }
 }
 
-// sigma_{r,I,K} (eq. euler-oe-sigma / magnetic-oe-sensor).
-__device__ __forceinline__ double sigma_rI(const StatsView& V, int nc, int n, int I, int r, int k, int kB, double Delta,
-                                           double h, const Mesh& M) {
-  const size_t K = M.K;
+// sigma_{r,I,K} (eq. euler-oe-sigma / magnetic-oe-sensor): max over the
+// components not constant to roundoff (reading R8; the flag is tested on its
+// bit pattern) of the order factor times the face jump measures of the two
+// faces, over the shared amplitude of the element's line.
+__device__ __forceinline__ double sigma_rI(const StatsView& V, int nc, int n, int I, int r, int k, int kB,
+                                           double iDelta, size_t K) {
   const double* J = I == 0 ? V.jx : V.jy;
-  double fac = 2.0 * r + 1.0;
-  double hr = 1.0, fact = 1.0;
-  for (int i = 0; i < r; ++i) { hr *= h; fact *= (i + 1); }
-  fac = fac * hr / (2.0 * fact);
+  const double fac = V.rfac[I * 8 + r];
   double s = 0.0;
   for (int c = 0; c < nc; ++c) {
-    if (V.glob[c * 4 + 3] != 0.0) continue;
-    double Jr = J[((size_t)c * n + r) * K + k] + J[((size_t)c * n + r) * K + kB];
-    s = fmax(s, fac * Jr);
+    if (__double_as_longlong(V.glob[c * 4 + 3]) != 0) continue;
+    const double Jr = J[((size_t)c * n + r) * K + k] + J[((size_t)c * n + r) * K + kB];
+    s = fmax(s, Jr);
   }
-  return s / Delta;
+  return fac * s * iDelta;
 }
 
 // ---- k_oe_pp: hydro OE map then the positivity limiter ----------------------------
@@ -271,10 +284,10 @@ __device__ __forceinline__ void oe_factors(const StatsView& V, int nc, int q, in
   constexpr int n = P + 1;
   if (q < 2 * n) {
     const int I = q / n, r = q % n;
-    const double h = I == 0 ? M.hx : M.hy;
-    const double Delta = shared_amp(V, nc, I, ex, ey, M);
+    const int Lmax = M.nx > M.ny ? M.nx : M.ny;
+    const double iDelta = V.lineD[I * Lmax + (I == 0 ? ey : ex)];
     const int kB = I == 0 ? ey * M.nx + wrap(ex + 1, M.nx) : wrap(ey + 1, M.ny) * M.nx + ex;
-    ssig[el][q] = sigma_rI(V, nc, n, I, r, kk, kB, Delta, h, M);
+    ssig[el][q] = sigma_rI(V, nc, n, I, r, kk, kB, iDelta, M.K);
   }
   __syncthreads();
   if (q < n) {
@@ -322,31 +335,37 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_oe_pp(double* __restrict__
       const double ir = rcp(a0);
       const double pb = (g - 1.0) * fma(-0.5 * ir, fma(a1, a1, fma(a2, a2, a3 * a3)), a4);
       const double cb = sqrt(g * pb * ir);
-      lam[0] = (2.0 * P + 1.0) * (fabs(a1 * ir) + cb) * (1.0 / M.hx);
-      lam[1] = (2.0 * P + 1.0) * (fabs(a2 * ir) + cb) * (1.0 / M.hy);
+      lam[0] = (2.0 * P + 1.0) * (fabs(a1 * ir) + cb) * rcp(M.hx);
+      lam[1] = (2.0 * P + 1.0) * (fabs(a2 * ir) + cb) * rcp(M.hy);
     }
     oe_factors<P>(V, 5, q, el, kk, ex, ey, lam, prm.s_H * dtp[0] * dtfac, M, ssig, sD);
 #pragma unroll
     for (int c = 0; c < 5; ++c) su[c][tid] = u[c];
     __syncthreads();
     if (node) {  // T[b][i] = sum_j w_j P_b(x_j) U[j][i]   (b = j of this lane)
+      double wl[n];
+#pragma unroll
+      for (int jj = 0; jj < n; ++jj) wl[jj] = T->wp[jj] * T->Leg[jj][j];
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
         double v = 0.0;
 #pragma unroll
-        for (int jj = 0; jj < n; ++jj) v = fma(T->wp[jj] * T->Leg[jj][j], su[c][el * SW + jj * n + i], v);
+        for (int jj = 0; jj < n; ++jj) v = fma(wl[jj], su[c][el * SW + jj * n + i], v);
         st[c][tid] = v;
       }
     }
     __syncthreads();
     if (node) {  // coef[b][a] = N_a N_b sum_i w_i P_a(x_i) T[b][i], damped by D_max(a,b)   (a = i, b = j)
       const double f = T->LegN[i] * T->LegN[j] * sD[el][i > j ? i : j];
+      double wl[n];
+#pragma unroll
+      for (int ii = 0; ii < n; ++ii) wl[ii] = f * T->wp[ii] * T->Leg[ii][i];
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
         double v = 0.0;
 #pragma unroll
-        for (int ii = 0; ii < n; ++ii) v = fma(T->wp[ii] * T->Leg[ii][i], st[c][el * SW + j * n + ii], v);
-        su[c][tid] = v * f;
+        for (int ii = 0; ii < n; ++ii) v = fma(wl[ii], st[c][el * SW + j * n + ii], v);
+        su[c][tid] = v;
       }
     }
     __syncthreads();
@@ -436,7 +455,7 @@ static void launch_stats(const double* F, size_t stride, int nc, const StatsView
   k_stats<P><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(F, stride, nc, V, T, M);
   dim3 grid(M.nx > M.ny ? M.nx : M.ny, 2);
   k_lines<<<grid, 256, 0, st>>>(nc, V, M);
-  k_global<<<1, 256, 0, st>>>(nc, V, M);
+  k_global<<<1, 256, 0, st>>>(nc, P + 1, V, M);
 }
 
 template <int P>
@@ -840,8 +859,8 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_vel_oe(const double* __res
     const double va = sqrt(fma(Bv[0], Bv[0], fma(Bv[1], Bv[1], Bv[2] * Bv[2])) * rcp(r_));
     const double ax = seg_max<SW>(node ? fabs(u[0]) + va : 0.0);
     const double ay = seg_max<SW>(node ? fabs(u[1]) + va : 0.0);
-    lam[0] = (2.0 * P + 1.0) / M.hx * ax;
-    lam[1] = (2.0 * P + 1.0) / M.hy * ay;
+    lam[0] = (2.0 * P + 1.0) * rcp(M.hx) * ax;
+    lam[1] = (2.0 * P + 1.0) * rcp(M.hy) * ay;
   }
   const double W = node ? M.Jdet * T->wp[i] * T->wp[j] * r_ : 0.0;
 #pragma unroll
