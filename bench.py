@@ -33,6 +33,10 @@ import numpy as np  # noqa: E402
 METRIC = "FP64 DOF-updates/s per Strang step at p=3"
 UNIT = "DOF-updates/s"
 NOMINAL_FP64_TFLOPS = 1.25  # B300 dense FP64, nominal (profiling recipe table)
+# DRAM bytes (read + write) of one k_vol<3> launch from the ncu capture summarised in
+# profiles/kernels_orszag_tang_256_full.md (same kernel source as this bench); must be reset
+# to None whenever the volume kernel changes until it is captured again.
+K_VOL_TRAFFIC_BYTES = 105.0e6 + 11.37e6
 # Config 2 of the workload: OE (both stages), positivity limiter, artificial
 # resistivity and velocity filter active, with the paper's constants.
 STAB = dict(oe_hydro=1, oe_vel=1, pp=1, ar=1, s_H=0.02, s_M=0.02, C_s=5.0, C_eta=0.2)
@@ -391,7 +395,8 @@ def main():
     step_ms_sum = sum(v[0] for v in kt.values())
     roofline = {"bound": "alu", "kernel": "k_vol<3> (entropy-conservative volume term + SSP stage)",
                 "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": None,
+                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": K_VOL_TRAFFIC_BYTES,
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "peak_source": "nominal B300 dense FP64 (1.25 TFLOP/s, profiling recipe)",
                 "peak_measured_dfma_tflops": measured_peak, "frac_of_measured_dfma": achieved / measured_peak,
                 "flops_per_launch": vol_flops, "avg_launch_ms": vol_ms,
