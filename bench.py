@@ -223,6 +223,9 @@ def batch_leg(nruns, steps):
         r.set_params(cfl=0.4, **STAB)
     dts = np.array([r.compute_dt() for r in batch.runs])
     setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    batch.autotune()  # per-run tiles, used by the batched and the sequential runs alike
+    tune = time.perf_counter() - t0
     dofs = sum(dofs_per_element(p, p) * N * N for N, p in specs)
     batch.step(dts, steps)  # capture + warm-up
     torch.cuda.synchronize()
@@ -242,7 +245,7 @@ def batch_leg(nruns, steps):
         "metric": "FP64 DOF-updates/s, batched vs sequential", "unit": UNIT, "runs": len(specs),
         "elements": int(sum(N * N for N, _ in specs)), "steps": steps,
         "batched": dofs * steps / tb, "sequential": dofs * steps / ts, "speedup": ts / tb,
-        "setup_s": setup, "degrees": {str(p): sum(1 for _, q in specs if q == p) for p in (2, 3, 4)},
+        "setup_s": setup, "autotune_s": tune, "degrees": {str(p): sum(1 for _, q in specs if q == p) for p in (2, 3, 4)},
         "config": {"workload": "orszag_tang_variants_batch", "stabilization": STAB, "seed": workloads.SEED}}
     batch.close()
     return out
@@ -356,6 +359,7 @@ def main():
     stream = torch.cuda.Stream()  # a capturable stream (the legacy default stream is not)
     torch.cuda.set_stream(stream)
     s.set_stream(stream.cuda_stream)
+    tiles = s.autotune()  # elements per CTA of the volume and magnetic kernels
     dt = s.compute_dt()
     dofs = dofs_per_element(3, 3) * s.K
 
@@ -424,7 +428,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (analytic Orszag-Tang initial state)",
-            "config": dict(workload_config(stab, args.mesh), parallelism=f"replicas{world}", dt=dt),
+            "config": dict(workload_config(stab, args.mesh), parallelism=f"replicas{world}", dt=dt,
+                           tiles={"vol_elements_per_cta": tiles[0], "mag_elements_per_cta": tiles[1]}),
             "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
         }
         if not args.no_side_legs and world == 1:

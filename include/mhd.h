@@ -146,6 +146,18 @@ int mhd_batch_step(mhd_batch* batch, const double* dt, int nsteps, int* status);
 /* Kernel launches enqueued by the batch and its runs since creation. */
 long long mhd_batch_launch_count(const mhd_batch* batch);
 
+/* Tile autotuner (spec batching pattern; the paper has none): times the
+ * elements-per-CTA variants of the volume kernel and of the magnetic-stage
+ * kernels on the context's own mesh and CURRENT state (set a state first) and
+ * keeps the fastest for every later launch (cached graphs are re-captured).
+ * choices (may be NULL) receives [volume elements per CTA, magnetic elements
+ * per CTA].  Synchronises; leaves the state unchanged. */
+int mhd_autotune(mhd_ctx* ctx, int* choices);
+/* Set the tile variants directly (0 = default, 1, 2; see mhd_autotune). */
+int mhd_set_tiles(mhd_ctx* ctx, int vol_variant, int mag_variant);
+/* mhd_autotune for every run of a batch (each run keeps its own choice). */
+int mhd_batch_autotune(mhd_batch* batch);
+
 /* A single substep: which = 0 hydro Phi_H^tau (Algorithm 1), 1 magnetic
  * Phi_M^tau (Algorithm 2, with the nodal variable exchange around it). */
 int mhd_substep(mhd_ctx* ctx, int which, double tau);

@@ -2,6 +2,7 @@
 // Strang driver (Algorithm 3) with the raw-average rejection and retry of the
 // hydro stage (§3.2.3).  All work is enqueued on one stream; the host reads
 // one status word per step.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -501,6 +502,90 @@ int mhd_strang_steps(mhd_ctx* c, double dt, int nsteps, int* steps_done) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Tile autotuner: elements per CTA of the volume kernel and of the magnetic
+// stage kernels, timed on the context's own mesh and state.
+// ---------------------------------------------------------------------------
+namespace {
+
+// Mean time of `reps` launches of fn() on the context stream (ms).
+template <class F>
+float time_launches(mhd_ctx* c, int reps, F fn, cudaEvent_t a, cudaEvent_t b) {
+  fn();  // warm-up
+  cudaEventRecord(a, c->st);
+  for (int r = 0; r < reps; ++r) fn();
+  cudaEventRecord(b, c->st);
+  cudaEventSynchronize(b);
+  float ms = 0.0f;
+  cudaEventElapsedTime(&ms, a, b);
+  return ms / reps;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mhd_autotune(mhd_ctx* c, int* choices) {
+  if (!c) return fail(MHD_EINVAL, "null context");
+  const size_t N = c->N;
+  const int reps = (int)std::min<long long>(100, std::max<long long>(3, 262144LL / c->M.K));
+  cudaEvent_t a, b;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune events");
+  set_scalar(c->dt, 0.0, c->st);  // tau = 0: the timed stages leave their inputs unchanged
+  hydro_face(c->p, c->U, c->Fx, c->Fy, c->M, c->st);
+  float best = 1e30f;
+  int bv = 0;
+  for (int v = 0; v < kTileVariants; ++v) {
+    Mesh Mv = c->M;
+    Mv.tile_vol = v;
+    float t = time_launches(c, reps, [&] {
+      hydro_vol(c->p, 1, c->U, c->U, c->Fx, c->Fy, c->S1, nullptr, c->status, c->T, Mv, c->dt, 1.0, 0.0, 1.0, 1,
+                c->st);
+    }, a, b);
+    if (t < best) { best = t; bv = v; }
+  }
+  cons_to_prim(c->U, c->Y0, N, c->st);
+  best = 1e30f;
+  int bm = 0;
+  for (int v = 0; v < kTileVariants; ++v) {
+    if (!mag_tile_ok(c->p, c->k, v)) continue;
+    Mesh Mv = c->M;
+    Mv.tile_mag = v;
+    float t = time_launches(c, reps, [&] {
+      mag_stage(c->p, c->k, 0, c->B, c->Y0 + N, c->Y0, c->U, c->eta, 0, c->B, c->Y0 + N, c->Y0, c->Ba, c->Ya + N,
+                c->Ya, c->LJ, c->LE, c->T, Mv, c->dt, 1.0, 0.0, 1.0, 1, c->st);
+    }, a, b);
+    if (t < best) { best = t; bm = v; }
+  }
+  cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->st);
+  e = cudaStreamSynchronize(c->st);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune");
+  c->M.tile_vol = bv;
+  c->M.tile_mag = bm;
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  if (choices) {
+    choices[0] = vol_tile_eb(c->p, bv);
+    choices[1] = mag_tile_eb(bm);
+  }
+  return MHD_OK;
+}
+
+int mhd_set_tiles(mhd_ctx* c, int vol_variant, int mag_variant) {
+  if (!c) return fail(MHD_EINVAL, "null context");
+  if (vol_variant < 0 || vol_variant >= kTileVariants || !mag_tile_ok(c->p, c->k, mag_variant))
+    return fail(MHD_EINVAL, "invalid tile variant");
+  c->M.tile_vol = vol_variant;
+  c->M.tile_mag = mag_variant;
+  if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+  return MHD_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
 // Batch of independent runs (uneven meshes and degrees): every run keeps its
 // own context and stream; one CUDA graph holds a parallel branch per run, so a
 // batch step is a single graph launch and small runs overlap on the GPU.
@@ -563,6 +648,16 @@ int mhd_batch_size(const mhd_batch* b) { return b ? (int)b->runs.size() : 0; }
 mhd_ctx* mhd_batch_run(mhd_batch* b, int i) {
   if (!b || i < 0 || i >= (int)b->runs.size()) return nullptr;
   return b->runs[i];
+}
+
+int mhd_batch_autotune(mhd_batch* b) {
+  if (!b) return fail(MHD_EINVAL, "null batch");
+  for (auto c : b->runs) {
+    int r = mhd_autotune(c, nullptr);
+    if (r != MHD_OK) return r;
+  }
+  if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+  return MHD_OK;
 }
 
 int mhd_batch_step(mhd_batch* b, const double* dt, int nsteps, int* status) {

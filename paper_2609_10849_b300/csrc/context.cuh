@@ -54,6 +54,7 @@ void adj_prim_to_cons(const double* U, const double* Y, const double* lamU, doub
 void adj_cons_to_prim(const double* U, const double* lamY, const double* lamR, double* lamU, size_t N,
                       cudaStream_t st);
 cudaError_t mag_adj_prepare(int p, int k);
+bool mag_tile_ok(int p, int k, int v);
 size_t mag_adj_load_doubles(int p, int k, int K);
 void mag_rhs_vjp(int p, int k, const double* rho, const double* u, const double* B, const double* wu,
                  const double* wB, double* gu, double* gB, double* grho, double rho_scale, const MagAdjScratch& S,

@@ -17,12 +17,12 @@
 
 namespace mhd {
 
-template <int P>
+template <int P, int EBv = vol_tile_eb(P, 0)>
 struct HCfg {
   static constexpr int n = P + 1, n2 = n * n;
   static constexpr int npairs = P * n2;        // unique pairs per element
   static constexpr int npl = n * (n - 1) / 2;  // pairs per line
-  static constexpr int EB = P == 1 ? 32 : (P == 2 ? 32 : (P == 3 ? 8 : 5));
+  static constexpr int EB = EBv;               // elements per CTA (autotuned variant)
   static constexpr int threads = EB * n2;
 };
 
@@ -98,14 +98,14 @@ __global__ void __launch_bounds__(256) k_face(const double* __restrict__ S, doub
 
 // mode 0: write L_E; mode 1: SSP stage combination into C.
 // Stage s: s == 0: C = S + tau L; otherwise C = a U0 + b (S + tau L).
-template <int P, int MODE>
-__global__ void __launch_bounds__(HCfg<P>::threads) k_vol(const double* __restrict__ S, const double* __restrict__ U0,
+template <int P, int MODE, int EBv>
+__global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __restrict__ S, const double* __restrict__ U0,
                                                           const double* __restrict__ Fx, const double* __restrict__ Fy,
                                                           double* __restrict__ out, double* __restrict__ avg_out,
                                                           unsigned* __restrict__ status, const Tab* __restrict__ T,
                                                           Mesh M, const double* __restrict__ dtp, double dtfac,
                                                           double ca, double cb, int first) {
-  using C = HCfg<P>;
+  using C = HCfg<P, EBv>;
   constexpr int n = C::n, n2 = C::n2, EB = C::EB, NP = C::npairs, NPL = C::npl;
   __shared__ double sp[6][EB * n2];           // rho/2, ux/2, uy/2, uz/2, beta, |u|^2/2
   __shared__ double sf[5][EB * NP];           // pair fluxes
@@ -277,16 +277,29 @@ void launch_face(const double* S, double* Fx, double* Fy, const Mesh& M, cudaStr
   k_face<P><<<(unsigned)((total + th - 1) / th), th, 0, st>>>(S, Fx, Fy, M);
 }
 
+template <int P, int EBv>
+void launch_vol_eb(int mode, const double* S, const double* U0, const double* Fx, const double* Fy, double* out,
+                   double* avg, unsigned* status, const Tab* T, const Mesh& M, const double* dtp, double dtfac,
+                   double ca, double cb, int first, cudaStream_t st) {
+  using C = HCfg<P, EBv>;
+  unsigned blocks = (unsigned)((M.K + C::EB - 1) / C::EB);
+  if (mode == 0)
+    k_vol<P, 0, EBv><<<blocks, C::threads, 0, st>>>(S, U0, Fx, Fy, out, avg, status, T, M, dtp, dtfac, ca, cb,
+                                                   first);
+  else
+    k_vol<P, 1, EBv><<<blocks, C::threads, 0, st>>>(S, U0, Fx, Fy, out, avg, status, T, M, dtp, dtfac, ca, cb,
+                                                   first);
+}
+
 template <int P>
 void launch_vol(int mode, const double* S, const double* U0, const double* Fx, const double* Fy, double* out,
                 double* avg, unsigned* status, const Tab* T, const Mesh& M, const double* dtp, double dtfac,
                 double ca, double cb, int first, cudaStream_t st) {
-  using C = HCfg<P>;
-  unsigned blocks = (unsigned)((M.K + C::EB - 1) / C::EB);
-  if (mode == 0)
-    k_vol<P, 0><<<blocks, C::threads, 0, st>>>(S, U0, Fx, Fy, out, avg, status, T, M, dtp, dtfac, ca, cb, first);
-  else
-    k_vol<P, 1><<<blocks, C::threads, 0, st>>>(S, U0, Fx, Fy, out, avg, status, T, M, dtp, dtfac, ca, cb, first);
+  switch (M.tile_vol) {
+    case 1: launch_vol_eb<P, vol_tile_eb(P, 1)>(mode, S, U0, Fx, Fy, out, avg, status, T, M, dtp, dtfac, ca, cb, first, st); break;
+    case 2: launch_vol_eb<P, vol_tile_eb(P, 2)>(mode, S, U0, Fx, Fy, out, avg, status, T, M, dtp, dtfac, ca, cb, first, st); break;
+    default: launch_vol_eb<P, vol_tile_eb(P, 0)>(mode, S, U0, Fx, Fy, out, avg, status, T, M, dtp, dtfac, ca, cb, first, st); break;
+  }
 }
 
 void hydro_face(int p, const double* S, double* Fx, double* Fy, const Mesh& M, cudaStream_t st) {

@@ -36,14 +36,14 @@ void upload_mag_tables(int slot, const Tab* h, cudaError_t* err) {
   *err = cudaMemcpyToSymbol(c_mtab, h, sizeof(Tab), slot * sizeof(Tab));
 }
 
-template <int P, int KM>
+template <int P, int KM, int EBv = mag_tile_eb(0)>
 struct MD {
   static constexpr int n = P + 1, n2 = n * n, mm = KM + 1, mL = KM + 2;
   static constexpr int NX = mm * mL;   // N_x family / Y-type arrays: a < mm (Gauss x), b < mL (GLL y)
   static constexpr int NY = mL * mm;   // N_y family / X-type arrays: a < mL (GLL x), b < mm (Gauss y)
   static constexpr int NW = mL * mL;   // W family
   static constexpr int NZ = mm * mm;   // owned DOFs / B_z
-  static constexpr int EB = 16;        // elements per block
+  static constexpr int EB = EBv;       // elements per block (autotuned variant)
   static constexpr int TH = 256;       // threads per block
   static constexpr int SLOT = P - 1 + KM;
 };
@@ -128,11 +128,11 @@ struct LJ_ {  // per-element shared-memory offsets (doubles)
   static constexpr int SIZE = BZG + D::NZ;
 };
 
-template <int P, int KM>
+template <int P, int KM, int EBv = mag_tile_eb(0)>
 __global__ void __launch_bounds__(256) k_mag_J(const double* __restrict__ Bx, const double* __restrict__ By,
                                                const double* __restrict__ Bz, double* __restrict__ LJx,
                                                double* __restrict__ LJy, double* __restrict__ LJz, Mesh M) {
-  using D = MD<P, KM>;
+  using D = MD<P, KM, EBv>;
   using O = LJ_<P, KM>;
   const Tab& T = c_mtab[D::SLOT];
   extern __shared__ double sm[];
@@ -246,7 +246,7 @@ struct LE_ {  // per-element shared-memory offsets (doubles), with region reuse
 
 // mode 0: write du, de (residual test hook); mode 1: SSP combination into (uo, eo);
 // mode 2: raw Lorentz load only (adjoint, see magnetic_adjoint.inc).
-template <int P, int KM, int MODE>
+template <int P, int KM, int MODE, int EBv = mag_tile_eb(0)>
 __global__ void __launch_bounds__(256) k_mag_E(
     const double* __restrict__ LJx, const double* __restrict__ LJy, const double* __restrict__ LJz,
     const double* __restrict__ Bx, const double* __restrict__ By, const double* __restrict__ Bz,
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
     const double* __restrict__ eta, const double* u0, const double* e0, double* uo, double* eo,
     double* __restrict__ LEx, double* __restrict__ LEy, double* __restrict__ LEz, Mesh M,
     const double* __restrict__ dtp, double dtfac, double ca, double cb, int first, int resistive) {
-  using D = MD<P, KM>;
+  using D = MD<P, KM, EBv>;
   using O = LE_<P, KM>;
   const Tab& T = c_mtab[D::SLOT];
   extern __shared__ double sm[];
@@ -680,12 +680,12 @@ struct LB_ {
 };
 
 // mode 0: write dB; mode 1: SSP combination into Bo.
-template <int P, int KM, int MODE>
+template <int P, int KM, int MODE, int EBv = mag_tile_eb(0)>
 __global__ void __launch_bounds__(256) k_mag_B(const double* __restrict__ LEx, const double* __restrict__ LEy,
                                                const double* __restrict__ LEz, const double* B, const double* B0,
                                                double* Bo, Mesh M, const double* __restrict__ dtp, double dtfac,
                                                double ca, double cb, int first) {
-  using D = MD<P, KM>;
+  using D = MD<P, KM, EBv>;
   using O = LB_<P, KM>;
   const Tab& T = c_mtab[D::SLOT];
   extern __shared__ double sm[];
@@ -756,12 +756,12 @@ __global__ void __launch_bounds__(256) k_mag_B(const double* __restrict__ LEx, c
 }
 
 // ---- launchers ------------------------------------------------------------------
-template <int P, int KM>
-void mag_stage_impl(int mode, const double* B, const double* u, const double* e, const double* rho,
-                    const double* eta, int resistive, const double* B0, const double* u0, const double* e0,
-                    double* Bo, double* uo, double* eo, double* LJ, double* LE, const Mesh& M, const double* dtp,
-                    double dtfac, double ca, double cb, int first, cudaStream_t st) {
-  using D = MD<P, KM>;
+template <int P, int KM, int EBv>
+void mag_stage_eb(int mode, const double* B, const double* u, const double* e, const double* rho, const double* eta,
+                  int resistive, const double* B0, const double* u0, const double* e0, double* Bo, double* uo,
+                  double* eo, double* LJ, double* LE, const Mesh& M, const double* dtp, double dtfac, double ca,
+                  double cb, int first, cudaStream_t st) {
+  using D = MD<P, KM, EBv>;
   const size_t Z = (size_t)M.K * D::NZ;
   double* LJx = LJ; double* LJy = LJ + (size_t)M.K * D::NX; double* LJz = LJy + (size_t)M.K * D::NY;
   double* LEx = LE; double* LEy = LE + (size_t)M.K * D::NX; double* LEz = LEy + (size_t)M.K * D::NY;
@@ -769,33 +769,75 @@ void mag_stage_impl(int mode, const double* B, const double* u, const double* e,
   const size_t sj = sizeof(double) * LJ_<P, KM>::SIZE * D::EB;
   const size_t se = sizeof(double) * LE_<P, KM>::SIZE * D::EB;
   const size_t sb = sizeof(double) * LB_<P, KM>::SIZE * D::EB;
-  k_mag_J<P, KM><<<blocks, D::TH, sj, st>>>(B, B + Z, B + 2 * Z, LJx, LJy, LJz, M);
+  k_mag_J<P, KM, EBv><<<blocks, D::TH, sj, st>>>(B, B + Z, B + 2 * Z, LJx, LJy, LJz, M);
   if (mode == 0) {
-    k_mag_E<P, KM, 0><<<blocks, D::TH, se, st>>>(LJx, LJy, LJz, B, B + Z, B + 2 * Z, u, e, rho, eta, u0, e0, uo, eo,
-                                                  LEx, LEy, LEz, M, dtp, dtfac, ca, cb, first, resistive);
-    k_mag_B<P, KM, 0><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, M, dtp, dtfac, ca, cb, first);
+    k_mag_E<P, KM, 0, EBv><<<blocks, D::TH, se, st>>>(LJx, LJy, LJz, B, B + Z, B + 2 * Z, u, e, rho, eta, u0, e0, uo,
+                                                       eo, LEx, LEy, LEz, M, dtp, dtfac, ca, cb, first, resistive);
+    k_mag_B<P, KM, 0, EBv><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, M, dtp, dtfac, ca, cb, first);
   } else {
-    k_mag_E<P, KM, 1><<<blocks, D::TH, se, st>>>(LJx, LJy, LJz, B, B + Z, B + 2 * Z, u, e, rho, eta, u0, e0, uo, eo,
-                                                  LEx, LEy, LEz, M, dtp, dtfac, ca, cb, first, resistive);
-    k_mag_B<P, KM, 1><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, M, dtp, dtfac, ca, cb, first);
+    k_mag_E<P, KM, 1, EBv><<<blocks, D::TH, se, st>>>(LJx, LJy, LJz, B, B + Z, B + 2 * Z, u, e, rho, eta, u0, e0, uo,
+                                                       eo, LEx, LEy, LEz, M, dtp, dtfac, ca, cb, first, resistive);
+    k_mag_B<P, KM, 1, EBv><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, M, dtp, dtfac, ca, cb, first);
   }
+}
+
+// Tile variants whose shared memory fits the device (set at context creation).
+static bool g_mag_tile_ok[8][kTileVariants] = {};
+
+template <int P, int KM>
+void mag_stage_impl(int mode, const double* B, const double* u, const double* e, const double* rho,
+                    const double* eta, int resistive, const double* B0, const double* u0, const double* e0,
+                    double* Bo, double* uo, double* eo, double* LJ, double* LE, const Mesh& M, const double* dtp,
+                    double dtfac, double ca, double cb, int first, cudaStream_t st) {
+  const int v = (M.tile_mag > 0 && M.tile_mag < kTileVariants && g_mag_tile_ok[P - 1 + KM][M.tile_mag]) ? M.tile_mag : 0;
+#define MHD_MAG_EB(V)                                                                                            \
+  mag_stage_eb<P, KM, mag_tile_eb(V)>(mode, B, u, e, rho, eta, resistive, B0, u0, e0, Bo, uo, eo, LJ, LE, M, dtp, \
+                                      dtfac, ca, cb, first, st)
+  switch (v) {
+    case 1: MHD_MAG_EB(1); break;
+    case 2: MHD_MAG_EB(2); break;
+    default: MHD_MAG_EB(0); break;
+  }
+#undef MHD_MAG_EB
 }
 
 // Opt-in dynamic shared memory of the magnetic kernels of one (p, k) pair on the
 // current device (done at context creation, never during stream capture).
-template <int P, int KM>
-static cudaError_t mag_prepare_impl() {
-  using D = MD<P, KM>;
+template <int P, int KM, int EBv>
+static cudaError_t mag_prepare_eb() {
+  using D = MD<P, KM, EBv>;
   const int sj = (int)(sizeof(double) * LJ_<P, KM>::SIZE * D::EB);
   const int se = (int)(sizeof(double) * LE_<P, KM>::SIZE * D::EB);
   const int sb = (int)(sizeof(double) * LB_<P, KM>::SIZE * D::EB);
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_J<P, KM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sj);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_E<P, KM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, se);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_E<P, KM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, se);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_B<P, KM, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_B<P, KM, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_J<P, KM, EBv>, cudaFuncAttributeMaxDynamicSharedMemorySize, sj);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_E<P, KM, 0, EBv>, cudaFuncAttributeMaxDynamicSharedMemorySize, se);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_E<P, KM, 1, EBv>, cudaFuncAttributeMaxDynamicSharedMemorySize, se);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_B<P, KM, 0, EBv>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_B<P, KM, 1, EBv>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
   return e;
+}
+
+// The default variant must fit; the others are marked usable when they do.
+template <int P, int KM>
+static cudaError_t mag_prepare_impl() {
+  using D = MD<P, KM>;
+  int maxsm = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t per = sizeof(double) * (size_t)(LE_<P, KM>::SIZE > LJ_<P, KM>::SIZE
+                                                    ? (LE_<P, KM>::SIZE > LB_<P, KM>::SIZE ? LE_<P, KM>::SIZE : LB_<P, KM>::SIZE)
+                                                    : (LJ_<P, KM>::SIZE > LB_<P, KM>::SIZE ? LJ_<P, KM>::SIZE : LB_<P, KM>::SIZE));
+  (void)D::EB;
+  cudaError_t e = mag_prepare_eb<P, KM, mag_tile_eb(0)>();
+  if (e != cudaSuccess) return e;
+  g_mag_tile_ok[P - 1 + KM][0] = true;
+  if (per * mag_tile_eb(1) <= (size_t)maxsm && mag_prepare_eb<P, KM, mag_tile_eb(1)>() == cudaSuccess)
+    g_mag_tile_ok[P - 1 + KM][1] = true;
+  if (per * mag_tile_eb(2) <= (size_t)maxsm && mag_prepare_eb<P, KM, mag_tile_eb(2)>() == cudaSuccess)
+    g_mag_tile_ok[P - 1 + KM][2] = true;
+  cudaGetLastError();  // a refused opt-in only disables that variant
+  return cudaSuccess;
 }
 
 cudaError_t mag_prepare(int p, int k) {
@@ -807,6 +849,12 @@ cudaError_t mag_prepare(int p, int k) {
 }
 
 #include "magnetic_adjoint.inc"
+
+// Whether tile variant v of the magnetic kernels is usable for (p, k) on this device.
+bool mag_tile_ok(int p, int k, int v) {
+  const int slot = table_slot(p, k);
+  return slot >= 0 && v >= 0 && v < kTileVariants && g_mag_tile_ok[slot][v];
+}
 
 size_t mag_load_doubles(int p, int k, int K) {
   (void)p;

@@ -68,7 +68,20 @@ void host_tables(int p, int k, Tab* out);
 struct Mesh {
   int nx, ny, K;
   double hx, hy, Jdet, g;
+  // tile variants chosen by the autotuner (0 = default elements per CTA):
+  // volume kernel and magnetic-stage kernels
+  int tile_vol, tile_mag;
 };
+
+// Elements per CTA of the tile variants (index 0 is the default).
+constexpr int vol_tile_eb(int p, int v) {
+  return p == 1 ? (v == 0 ? 32 : v == 1 ? 16 : 64)
+       : p == 2 ? (v == 0 ? 32 : v == 1 ? 16 : 8)
+       : p == 3 ? (v == 0 ? 8 : v == 1 ? 4 : 16)
+                : (v == 0 ? 5 : v == 1 ? 3 : 8);
+}
+constexpr int mag_tile_eb(int v) { return v == 0 ? 16 : v == 1 ? 8 : 32; }
+constexpr int kTileVariants = 3;
 
 // Stabilisation parameters as seen by the kernels.
 struct Stab {

@@ -82,6 +82,9 @@ _SIGS = {
                                    C.POINTER(C.c_int)]),
     "mhd_hydro_rhs_vjp": (C.c_int, [C.c_void_p] + [C.c_void_p] * 3 + [C.c_int]),
     "mhd_mag_rhs_vjp": (C.c_int, [C.c_void_p] + [C.c_void_p] * 14 + [C.c_int]),
+    "mhd_autotune": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "mhd_set_tiles": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "mhd_batch_autotune": (C.c_int, [C.c_void_p]),
     "mhd_status_string": (C.c_char_p, [C.c_int]),
     "mhd_last_error": (C.c_char_p, []),
 }
@@ -245,6 +248,17 @@ class Solver:
         _check(lib().mhd_mag_rhs(self._h, *ps, 0))
         return dict(de=de, du=du, dBx=dBx, dBy=dBy, dBz=dBz)
 
+    # -- tiles ---------------------------------------------------------------
+    def autotune(self):
+        """Time the elements-per-CTA variants on the current state and keep the
+        fastest; returns (volume elements per CTA, magnetic elements per CTA)."""
+        ch = np.zeros(2, dtype=np.int32)
+        _check(lib().mhd_autotune(self._h, ch.ctypes.data_as(C.c_void_p)))
+        return int(ch[0]), int(ch[1])
+
+    def set_tiles(self, vol_variant, mag_variant):
+        _check(lib().mhd_set_tiles(self._h, int(vol_variant), int(mag_variant)))
+
     # -- packed state and adjoint ------------------------------------------
     def state_size(self):
         """Length of the packed state [U 5N | Bx G | By G | Bz Z] (host layouts)."""
@@ -352,6 +366,10 @@ class Batch:
 
     def launch_count(self):
         return lib().mhd_batch_launch_count(self._h)
+
+    def autotune(self):
+        """Autotune the tiles of every run (each run keeps its own choice)."""
+        _check(lib().mhd_batch_autotune(self._h))
 
     def close(self):
         if getattr(self, "_h", None):

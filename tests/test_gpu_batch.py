@@ -60,3 +60,45 @@ def test_graph_and_eager_paths_agree():
         b.strang_steps(dt, 3)
     for x, y in zip(a.get_state(), b.get_state()):
         assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("pk", [(1, 1), (2, 2), (3, 3), (4, 4), (4, 3)])
+def test_tile_variants_bitwise(pk):
+    """Every elements-per-CTA variant of the volume and magnetic kernels gives
+    the same state bit for bit (the per-element arithmetic does not depend on
+    the tiling, and shared DOFs are assembled in one canonical order)."""
+    from paper_2609_10849_b300.mhd import Solver
+    from tests.util import oracle_state
+    p, k = pk
+    wl = workloads.orszag_tang_variant(3)
+    o = oracle_state(wl, 9, 7, p, k)
+    ref = None
+    for v in range(3):
+        s = Solver(9, 7, p, k, wl["gamma"], wl["domain"])
+        s.set_params(**STAB)
+        s.set_state(*o.get_state())
+        dt = s.compute_dt()
+        s.set_tiles(v, v)
+        for _ in range(2):
+            st, _ = s.strang_step(dt)
+            assert st == 0
+        out = s.get_state()
+        if ref is None:
+            ref = out
+        else:
+            for a, b in zip(out, ref):
+                assert np.array_equal(a, b), (pk, v)
+
+
+def test_autotune_keeps_state():
+    from paper_2609_10849_b300.mhd import Solver
+    from tests.util import oracle_state
+    wl = workloads.orszag_tang()
+    o = oracle_state(wl, 24, 24, 3, 3)
+    s = Solver(24, 24, 3, 3, wl["gamma"], wl["domain"])
+    s.set_state(*o.get_state())
+    before = s.get_state()
+    vol_eb, mag_eb = s.autotune()
+    assert vol_eb in (4, 8, 16) and mag_eb in (8, 16, 32)
+    for a, b in zip(s.get_state(), before):
+        assert np.array_equal(a, b)
