@@ -186,13 +186,16 @@ long long mhd_state_size(const mhd_ctx* ctx);
  * transposed discrete curl, the adjoint lumped reconstructions of E_h and
  * J_h, and the adjoint nodal exchange).  The step's intermediate states are
  * recomputed from state_n on the device; the context's own state is not
- * touched.  The derivative is that of the step with every stabilisation map
- * off: if hydro OE, the limiter, the artificial resistivity or the velocity
- * OE is enabled, *flags (may be NULL) gets bits 1, 2, 4, 8 respectively and
- * the call returns MHD_EINVAL.  lam_n may alias lam_np1.  The first call
- * allocates the adjoint's device buffers (about 14 state-sized vectors).
- * Errors: MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA, MHD_INADMISSIBLE or
- * MHD_NONFINITE if the recomputed step leaves the admissible set. */
+ * touched.  Stabilisation: the hydro OE and the limiter, when enabled, are
+ * differentiated with their coefficients (the OE factors D_l and the limiter
+ * factors theta) frozen at the values of the recomputed step, and *flags (may
+ * be NULL) reports them (bit 1 hydro OE, bit 2 limiter) with MHD_OK; the
+ * artificial resistivity (bit 4) and the velocity OE (bit 8) are not
+ * supported and make the call return MHD_EINVAL.  lam_n may alias lam_np1.
+ * The first call allocates the adjoint's device buffers (about 14
+ * state-sized vectors).  Errors: MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA,
+ * MHD_INADMISSIBLE or MHD_NONFINITE if the recomputed step leaves the
+ * admissible set. */
 int mhd_adjoint_step(mhd_ctx* ctx, const double* state_n, const double* lam_np1, double* lam_n, double dt,
                      int on_device, int* flags);
 

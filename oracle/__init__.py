@@ -86,6 +86,7 @@ def _load(path):
     L.or_oe_sensor.argtypes = [C.c_void_p, _dp, C.c_int, _dp]
     L.or_ar_coefficient.argtypes = [C.c_void_p] + [_dp] * 6
     L.or_vel_oe.argtypes = [C.c_void_p] + [_dp] * 6 + [C.c_double]
+    L.or_set_frozen.argtypes = [C.c_void_p, C.c_int]
     return L
 
 
@@ -321,6 +322,12 @@ class Tangent(Oracle):
     def set_tangent(self, dU, dBx, dBy, dBz):
         f = lambda a: np.ascontiguousarray(a, dtype=np.float64).ravel()
         self._L.or_set_tangent(self._h, f(dU), f(dBx), f(dBy), f(dBz))
+
+    def set_frozen(self, frozen=True):
+        """Hold the stabilisation coefficients (OE factors D_l, limiter theta,
+        A.R. eta) at their values: the tangent of the frozen-coefficient
+        linearisation."""
+        self._L.or_set_frozen(self._h, int(frozen))
 
     def get_tangent(self):
         dU = np.zeros(5 * self.K * self.n2)

@@ -72,5 +72,9 @@ inline Dual pow(const Dual& a, const Dual& b) {
 }
 inline bool isfinite(const Dual& a) { return std::isfinite(a.v); }
 
+// Holds a coefficient at its value: the tangent through it is dropped (the
+// "frozen coefficient" linearisation of the stabilisation maps).
+inline void freeze(Dual& a) { a.d = 0.0; }
+
 inline double val(const Dual& a) { return a.v; }
 inline double tan_of(const Dual& a) { return a.d; }

@@ -39,6 +39,7 @@ typedef Dual real;
 typedef double real;
 inline double val(double x) { return x; }
 inline double tan_of(double) { return 0.0; }
+inline void freeze(double&) {}
 #endif
 using std::exp;
 using std::fabs;
@@ -210,6 +211,7 @@ struct Params {
   real s_H, s_M, C_s, C_eta, cfl;
   int max_halvings;
   int ec_faces;  // test hook: entropy-conservative flux on faces instead of LLF
+  int frozen;    // tangent build: hold the stabilisation coefficients (D_l, theta, eta) at their values
 };
 
 enum { OR_OK = 0, OR_RETRIED = 1, OR_REJECT = -10, OR_INADMISSIBLE = -11 };
@@ -253,7 +255,7 @@ struct Oracle {
     for (int c = 0; c < 5; ++c) U[c].assign((size_t)K * n2, 0.0);
     Bx.assign((size_t)NX * NY, 0.0); By = Bx; Bz.assign((size_t)K * mm * mm, 0.0);
     eta.assign(K, 0.0);
-    prm = Params{0, 0, 0, 0, 0.02, 0.02, 5.0, 0.0, 0.4, 20, 0};
+    prm = Params{0, 0, 0, 0, 0.02, 0.02, 5.0, 0.0, 0.4, 20, 0, 0};
     last_rejections = 0;
   }
 
@@ -839,8 +841,13 @@ void or_destroy(void* h) { delete (Oracle*)h; }
 void or_set_params(void* h, int oe_hydro, int oe_vel, int pp, int ar, double s_H, double s_M, double C_s,
                    double C_eta, double cfl, int max_halvings, int ec_faces) {
   Oracle* o = (Oracle*)h;
-  o->prm = Params{oe_hydro, oe_vel, pp, ar, s_H, s_M, C_s, C_eta, cfl, max_halvings, ec_faces};
+  const int frozen = o->prm.frozen;
+  o->prm = Params{oe_hydro, oe_vel, pp, ar, s_H, s_M, C_s, C_eta, cfl, max_halvings, ec_faces, frozen};
 }
+
+// Tangent build: hold the stabilisation coefficients at their forward values
+// (the linearisation that the library's adjoint differentiates).
+void or_set_frozen(void* h, int frozen) { ((Oracle*)h)->prm.frozen = frozen; }
 
 // Physical coordinates of the DG nodes [K][n2], of the W nodes
 // [NY][NX] (GLL(m+1) nodes 0..m of each element) and of the B_z nodes [K][mm^2].

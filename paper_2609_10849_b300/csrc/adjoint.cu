@@ -1,5 +1,7 @@
-// Adjoint of one H-M-H Strang step (Algorithm 3, eq. strang-composition) with
-// the stabilisation maps switched off and dt fixed.
+// Adjoint of one H-M-H Strang step (Algorithm 3, eq. strang-composition) at
+// fixed dt.  The hydro stage maps (OE and limiter) are differentiated with
+// their coefficients (D_l, theta) frozen at the values of the recomputed
+// forward step; the A.R. and the velocity OE must be off.
 //
 // Reverse mode written out by hand: the step's intermediate states are
 // recomputed from its start state (the hydro stage inputs of both hydro
@@ -87,6 +89,7 @@ int ensure_adjoint(mhd_ctx* c) {
   if (e == cudaSuccess) e = aalloc(c, &A.lamR, N);
   if (e == cudaSuccess) e = aalloc(c, &A.FA, 20 * K * c->n);
   if (e == cudaSuccess) e = aalloc(c, &A.io, 5 * N + 3 * Z);
+  if (e == cudaSuccess) e = aalloc(c, &A.frz, 6 * K * (c->n + 2));
   if (e == cudaSuccess) e = aalloc(c, &A.ms.mu, 3 * N);
   if (e == cudaSuccess) e = aalloc(c, &A.ms.s, 3 * N);
   if (e == cudaSuccess) e = aalloc(c, &A.ms.LT, mag_load_doubles(c->p, c->k, (int)K));
@@ -100,17 +103,26 @@ int ensure_adjoint(mhd_ctx* c) {
 }
 
 // ---- forward recomputation ---------------------------------------------------------
-// Hydro substep tau = dt * fac from S[0] (filled by the caller), keeping the
-// stage inputs S[1], S[2]; the result goes to out.
-void hydro_fwd(mhd_ctx* c, double* const S[3], double* out, double fac) {
+bool stab_on(const mhd_ctx* c) { return c->prm.oe_hydro || c->prm.pp; }
+
+double* frz_slot(mhd_ctx* c, int h, int s) { return c->adj.frz + (size_t)(3 * h + s) * c->M.K * (c->n + 2); }
+
+// Hydro substep h (0 or 1) of tau = dt * fac from S[0] (filled by the caller),
+// keeping the stage inputs S[1], S[2] and, with stabilisation on, the frozen
+// coefficients of every stage map; the result goes to out.
+void hydro_fwd(mhd_ctx* c, double* const S[3], double* out, double fac, int h) {
   const double* in[3] = {S[0], S[1], S[2]};
   double* o[3] = {S[1], S[2], out};
   for (int s = 0; s < 3; ++s) {
     hydro_face(c->p, in[s], c->Fx, c->Fy, c->M, c->st);
     hydro_vol(c->p, 1, in[s], S[0], c->Fx, c->Fy, o[s], nullptr, c->status, c->T, c->M, c->dt, fac, RK_A[s],
               RK_B[s], s == 0, c->st);
+    c->launches += 2;
+    if (stab_on(c)) {
+      stab_hydro(c->p, o[s], c->status, c->T, c->M, c->prm, c->dt, fac, c->work, frz_slot(c, h, s), c->st);
+      c->launches += c->prm.oe_hydro ? 4 : 1;
+    }
   }
-  c->launches += 6;
 }
 
 // Magnetic substep tau = dt * fac from Y[0] (e, u, B) with density rho,
@@ -128,10 +140,14 @@ void mag_fwd(mhd_ctx* c, const double* rho, double fac) {
 }
 
 // ---- adjoint substeps --------------------------------------------------------------
-void hydro_adj(mhd_ctx* c, double* const S[3], double* lam, double tau) {
+void hydro_adj(mhd_ctx* c, double* const S[3], double* lam, double tau, int h) {
   AdjBufs& A = c->adj;
   const size_t n = 5 * c->N;
   for (int s = 2; s >= 0; --s) {
+    if (stab_on(c)) {  // stage map with frozen coefficients: lam <- P^T lam
+      stab_hydro_adjoint(c->p, lam, frz_slot(c, h, s), c->T, c->M, c->prm.oe_hydro, c->prm.pp, c->st);
+      c->launches++;
+    }
     const double* w = lam;
     if (s > 0) {
       k_lin2<<<nblk(n), 256, 0, c->st>>>(lam, RK_A[s], RK_B[s], s == 1, A.L0, A.W, n);
@@ -175,6 +191,7 @@ int stab_flags(const mhd_ctx* c) {
   return (c->prm.oe_hydro ? 1 : 0) | (c->prm.pp ? 2 : 0) | (c->prm.ar && c->prm.C_eta != 0.0 ? 4 : 0) |
          (c->prm.oe_vel ? 8 : 0);
 }
+const int kFrozenSupported = 1 | 2;  // hydro OE and limiter: differentiated with frozen coefficients
 
 }  // namespace
 
@@ -187,7 +204,8 @@ int mhd_adjoint_step(mhd_ctx* c, const double* state_n, const double* lam_np1, d
   if (!c || !state_n || !lam_np1 || !lam_n) return afail(MHD_EINVAL, "null argument");
   const int fl = stab_flags(c);
   if (flags) *flags = fl;
-  if (fl) return afail(MHD_EINVAL, "the adjoint differentiates the step with every stabilisation map off");
+  if (fl & ~kFrozenSupported)
+    return afail(MHD_EINVAL, "the adjoint supports the magnetic stage with A.R. and velocity OE off");
   if (!(dt > 0.0)) return afail(MHD_EINVAL, "dt must be positive");
   int r = ensure_adjoint(c);
   if (r != MHD_OK) return r;
@@ -205,13 +223,13 @@ int mhd_adjoint_step(mhd_ctx* c, const double* state_n, const double* lam_np1, d
   // recompute the step
   set_scalar(c->dt, dt, c->st);
   cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->st);
-  hydro_fwd(c, A.hS[0], A.Ua, 0.5);
+  hydro_fwd(c, A.hS[0], A.Ua, 0.5, 0);
   cons_to_prim(A.Ua, A.Y[0], N, c->st);
   mag_fwd(c, A.Ua, 1.0);
   cudaMemcpyAsync(A.hS[1][0], A.Ua, 5 * N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
   prim_to_cons(A.Y[3], A.hS[1][0], N, c->st);
-  hydro_fwd(c, A.hS[1], A.G, 0.5);
-  c->launches += 6;
+  hydro_fwd(c, A.hS[1], A.G, 0.5, 1);
+  c->launches += 2;
   unsigned st = 0;
   if ((r = read_status(c, &st)) != MHD_OK) return r;
   if (st & ST_NONFINITE) return afail(MHD_NONFINITE, "non-finite value in the recomputed step");
@@ -224,11 +242,11 @@ int mhd_adjoint_step(mhd_ctx* c, const double* state_n, const double* lam_np1, d
   grid_to_blocked(A.io + 5 * N + Z, A.lamM + 4 * N + Z, nx, ny, mm, c->st);
   cudaMemcpyAsync(A.lamM + 4 * N + 2 * Z, A.io + 5 * N + 2 * Z, Z * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
   // backwards through the step
-  hydro_adj(c, A.hS[1], A.lamU, 0.5 * dt);
+  hydro_adj(c, A.hS[1], A.lamU, 0.5 * dt, 1);
   adj_prim_to_cons(A.hS[1][0], A.Y[3], A.lamU, A.lamM, A.lamR, N, c->st);
   mag_adj(c, A.Ua, A.lamM, dt);
   adj_cons_to_prim(A.Ua, A.lamM, A.lamR, A.lamU, N, c->st);
-  hydro_adj(c, A.hS[0], A.lamU, 0.5 * dt);
+  hydro_adj(c, A.hS[0], A.lamU, 0.5 * dt, 0);
   c->launches += 6;
   // output
   cudaMemcpyAsync(A.io, A.lamU, 5 * N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);

@@ -100,7 +100,7 @@ void hydro_substep(mhd_ctx* c, double fac) {
     c->launches += 2;
     if (stab) {
       Prof pr(c, KC_STAB_H);
-      stab_hydro(c->p, out[s], c->avg, c->status, c->T, c->M, c->prm, c->dt, fac, c->work, c->st);
+      stab_hydro(c->p, out[s], c->status, c->T, c->M, c->prm, c->dt, fac, c->work, nullptr, c->st);
       c->launches += c->prm.oe_hydro ? 4 : 1;
     }
   }

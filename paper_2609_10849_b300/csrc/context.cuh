@@ -33,8 +33,10 @@ void cfl_dt(int p, int k, const double* U, const double* B, const Tab* T, const 
 void set_scalar(double* ptr, double v, cudaStream_t st);
 void diag_partials(int p, int k, const double* U, const double* B, const Tab* T, const Mesh& M, double* out,
                    cudaStream_t st);
-void stab_hydro(int p, double* S, const double* avg, unsigned* status, const Tab* T, const Mesh& M,
-                const Stab& prm, const double* dtp, double dtfac, double* work, cudaStream_t st);
+void stab_hydro(int p, double* S, unsigned* status, const Tab* T, const Mesh& M, const Stab& prm, const double* dtp,
+                double dtfac, double* work, double* frz, cudaStream_t st);
+void stab_hydro_adjoint(int p, double* lam, const double* frz, const Tab* T, const Mesh& M, int oe, int pp,
+                        cudaStream_t st);
 void stab_eta(int p, int k, const double* rho, const double* Y, const double* B, const Tab* T, const Mesh& M,
               const Stab& prm, double* eta, double* work, cudaStream_t st);
 void stab_vel_prep(int p, const double* rho, double* chol, const Tab* T, const Mesh& M, cudaStream_t st);
@@ -75,6 +77,7 @@ struct AdjBufs {
   double* lamR = nullptr;  // adjoint of the frozen density [N]
   double* FA = nullptr;    // face adjoints [2][2][5][K (p+1)]
   double* io = nullptr;    // packed host-layout staging [5N + 3Z]
+  double* frz = nullptr;   // frozen stage-map coefficients [2][3][K][p+3]
   mhd::MagAdjScratch ms{};
 };
 

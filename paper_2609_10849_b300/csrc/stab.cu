@@ -302,11 +302,15 @@ __device__ __forceinline__ void oe_factors(const StatsView& V, int nc, int q, in
   __syncthreads();
 }
 
+// frz (may be null): per element the frozen coefficients of the map, [K][p+3]:
+// D_0..D_p of the OE and the limiter factors t_rho (density) and t (others),
+// U'' = t U* + (1 - t) avg(U*), for the adjoint.
 template <int P>
 __global__ void __launch_bounds__(OCfg<P>::threads) k_oe_pp(double* __restrict__ S, StatsView V,
                                                             const Tab* __restrict__ T, Mesh M, Stab prm,
                                                             const double* __restrict__ dtp, double dtfac,
-                                                            unsigned* __restrict__ status) {
+                                                            unsigned* __restrict__ status,
+                                                            double* __restrict__ frz) {
   using C = OCfg<P>;
   constexpr int n = C::n, n2 = C::n2, EB = C::EB, SW = C::SW;
   __shared__ double su[5][EB * SW];
@@ -390,6 +394,7 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_oe_pp(double* __restrict__
     }
   }
 
+  double t_rho = 1.0, t_all = 1.0;  // frozen limiter factors (adjoint)
   if (prm.pp) {
     // Every shuffle below runs in all lanes (no per-element branch around it);
     // the element decisions are taken afterwards from segment-uniform values.
@@ -428,17 +433,28 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_oe_pp(double* __restrict__
     } else if (rbar <= eps_rho || pbar <= eps_p) {  // vacuum-like average: collapse (reading R9)
 #pragma unroll
       for (int c = 0; c < 5; ++c) u[c] = a[c];
+      t_rho = t_all = 0.0;
     } else {
       u[0] = r0;
+      if (th_r < 1.0) t_rho = th_r;
       if (pmin < eps_p) {
         const double den = pbar - pmin;
         const double th_p = den > 0.0 ? fmin(1.0, fmax(0.0, (pbar - eps_p) / den)) : 1.0;
         if (th_p < 1.0) {
 #pragma unroll
           for (int c = 0; c < 5; ++c) u[c] = a[c] + th_p * (u[c] - a[c]);
+          t_rho *= th_p;
+          t_all = th_p;
         }
       }
     }
+  }
+  if (frz && q == 0 && k < M.K) {
+    double* f = frz + (size_t)k * (n + 2);
+#pragma unroll
+    for (int l = 0; l < n; ++l) f[l] = prm.oe_hydro ? sD[el][l] : 1.0;
+    f[n] = t_rho;
+    f[n + 1] = t_all;
   }
   if (valid) {
 #pragma unroll
@@ -460,21 +476,123 @@ static void launch_stats(const double* F, size_t stride, int nc, const StatsView
 
 template <int P>
 static void stab_hydro_impl(double* S, unsigned* status, const Tab* T, const Mesh& M, const Stab& prm,
-                            const double* dtp, double dtfac, double* work, cudaStream_t st) {
+                            const double* dtp, double dtfac, double* work, double* frz, cudaStream_t st) {
   StatsView V = stats_view(work, P, M);
   if (prm.oe_hydro) launch_stats<P>(S, (size_t)M.K * (P + 1) * (P + 1), 5, V, T, M, st);
   using C = OCfg<P>;
-  k_oe_pp<P><<<(unsigned)((M.K + C::EB - 1) / C::EB), C::threads, 0, st>>>(S, V, T, M, prm, dtp, dtfac, status);
+  k_oe_pp<P><<<(unsigned)((M.K + C::EB - 1) / C::EB), C::threads, 0, st>>>(S, V, T, M, prm, dtp, dtfac, status,
+                                                                             frz);
 }
 
-void stab_hydro(int p, double* S, const double* avg, unsigned* status, const Tab* T, const Mesh& M, const Stab& prm,
-                const double* dtp, double dtfac, double* work, cudaStream_t st) {
-  (void)avg;
+// Adjoint of the hydro stage map with its coefficients frozen at the values
+// the forward map recorded in frz: lam <- P_OE^T P_PP^T lam, in place.
+//   P_PP: U'' = t U* + (1 - t) avg(U*), avg = sum_q (w_q / 4) U*_q
+//         -> lam* = t lam'' + (w_q / 4)(1 - t) sum_q' lam''_q'
+//   P_OE: U' = Phi diag(D) N Phi^T W U (Legendre modes, quadrature W, norms N)
+//         -> lam = W Phi N diag(D) Phi^T lam'
+template <int P>
+__global__ void __launch_bounds__(OCfg<P>::threads) k_adj_stage_map(double* __restrict__ lam,
+                                                                    const double* __restrict__ frz,
+                                                                    const Tab* __restrict__ T, Mesh M, int oe,
+                                                                    int pp) {
+  using C = OCfg<P>;
+  constexpr int n = C::n, n2 = C::n2, EB = C::EB, SW = C::SW;
+  __shared__ double su[5][EB * SW];
+  __shared__ double st[5][EB * SW];
+  const size_t N = (size_t)M.K * n2;
+  const int tid = threadIdx.x, el = tid / SW, q = tid % SW;
+  const bool node = q < n2;
+  const int k = blockIdx.x * EB + el;
+  const bool valid = k < M.K && node;
+  const int kk = k < M.K ? k : M.K - 1;
+  const int qq = node ? q : 0;
+  const int i = qq % n, j = qq / n;
+  const double* f = frz + (size_t)kk * (n + 2);
+  double l5[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) l5[c] = node ? lam[c * N + (size_t)kk * n2 + q] : 0.0;
+  if (pp) {
+    const double wq = node ? 0.25 * T->wp[i] * T->wp[j] : 0.0;
+    const int lead = (threadIdx.x & 31) & ~(SW - 1);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      const double sum = __shfl_sync(0xffffffffu, seg_sum<SW>(l5[c]), lead);
+      const double t = c == 0 ? f[n] : f[n + 1];
+      l5[c] = fma(t, l5[c], wq * (1.0 - t) * sum);
+    }
+  }
+  if (oe) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) su[c][tid] = l5[c];
+    __syncthreads();
+    if (node) {  // Vb[b][i] = sum_j P_b(x_j) lam[j][i]   (b = j of this lane)
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        double v = 0.0;
+#pragma unroll
+        for (int jj = 0; jj < n; ++jj) v = fma(T->Leg[jj][j], su[c][el * SW + jj * n + i], v);
+        st[c][tid] = v;
+      }
+    }
+    __syncthreads();
+    if (node) {  // s[b][a] = N_a N_b D_max(a,b) sum_i P_a(x_i) Vb[b][i]   (a = i, b = j)
+      const double fs = T->LegN[i] * T->LegN[j] * f[i > j ? i : j];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        double v = 0.0;
+#pragma unroll
+        for (int ii = 0; ii < n; ++ii) v = fma(T->Leg[ii][i], st[c][el * SW + j * n + ii], v);
+        su[c][tid] = fs * v;
+      }
+    }
+    __syncthreads();
+    if (node) {  // Tb[b][i] = w_i sum_a P_a(x_i) s[b][a]
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        double v = 0.0;
+#pragma unroll
+        for (int a = 0; a < n; ++a) v = fma(T->Leg[i][a], su[c][el * SW + j * n + a], v);
+        st[c][tid] = T->wp[i] * v;
+      }
+    }
+    __syncthreads();
+    if (node) {  // lam[j][i] = w_j sum_b P_b(x_j) Tb[b][i]
+#pragma unroll
+      for (int c = 0; c < 5; ++c) {
+        double v = 0.0;
+#pragma unroll
+        for (int b = 0; b < n; ++b) v = fma(T->Leg[j][b], st[c][el * SW + b * n + i], v);
+        l5[c] = T->wp[j] * v;
+      }
+    }
+  }
+  if (valid) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) lam[c * N + (size_t)k * n2 + q] = l5[c];
+  }
+}
+
+void stab_hydro_adjoint(int p, double* lam, const double* frz, const Tab* T, const Mesh& M, int oe, int pp,
+                        cudaStream_t st) {
+#define MHD_ADJ_MAP(PP)                                                                                       \
+  k_adj_stage_map<PP><<<(unsigned)((M.K + OCfg<PP>::EB - 1) / OCfg<PP>::EB), OCfg<PP>::threads, 0, st>>>( \
+      lam, frz, T, M, oe, pp)
   switch (p) {
-    case 1: stab_hydro_impl<1>(S, status, T, M, prm, dtp, dtfac, work, st); break;
-    case 2: stab_hydro_impl<2>(S, status, T, M, prm, dtp, dtfac, work, st); break;
-    case 3: stab_hydro_impl<3>(S, status, T, M, prm, dtp, dtfac, work, st); break;
-    case 4: stab_hydro_impl<4>(S, status, T, M, prm, dtp, dtfac, work, st); break;
+    case 1: MHD_ADJ_MAP(1); break;
+    case 2: MHD_ADJ_MAP(2); break;
+    case 3: MHD_ADJ_MAP(3); break;
+    case 4: MHD_ADJ_MAP(4); break;
+  }
+#undef MHD_ADJ_MAP
+}
+
+void stab_hydro(int p, double* S, unsigned* status, const Tab* T, const Mesh& M, const Stab& prm, const double* dtp,
+                double dtfac, double* work, double* frz, cudaStream_t st) {
+  switch (p) {
+    case 1: stab_hydro_impl<1>(S, status, T, M, prm, dtp, dtfac, work, frz, st); break;
+    case 2: stab_hydro_impl<2>(S, status, T, M, prm, dtp, dtfac, work, frz, st); break;
+    case 3: stab_hydro_impl<3>(S, status, T, M, prm, dtp, dtfac, work, frz, st); break;
+    case 4: stab_hydro_impl<4>(S, status, T, M, prm, dtp, dtfac, work, frz, st); break;
   }
 }
 

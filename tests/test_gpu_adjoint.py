@@ -158,18 +158,57 @@ def test_adjoint_step_dot(pk):
     dot_check([np.ravel(a) for a in lam], [np.ravel(a) for a in Jdx], gs, [np.ravel(a) for a in dx])
 
 
-def test_adjoint_refuses_stabilisation():
+def test_adjoint_refuses_magnetic_stabilisation():
     from paper_2609_10849_b300.mhd import MhdError
     rng = np.random.default_rng(890)
     t = Tangent(3, 3, 2, 2, 5 / 3)
     U = generic_state(t, rng)
     s = solver_like(t)
     x = packed(t, U, np.zeros(t.G), np.zeros(t.G), np.zeros(t.Z))
-    s.set_params(pp=1)
-    with pytest.raises(MhdError, match="flags 2"):
+    s.set_params(ar=1, C_eta=0.2)
+    with pytest.raises(MhdError, match="flags 4"):
         s.adjoint_step(x, x.copy(), 1e-3)
-    s.set_params(pp=0)
+    s.set_params(ar=0, oe_vel=1)
+    with pytest.raises(MhdError, match="flags 8"):
+        s.adjoint_step(x, x.copy(), 1e-3)
+    s.set_params(oe_vel=0, oe_hydro=1, pp=1)  # supported with frozen coefficients
     s.adjoint_step(x, x.copy(), 1e-3)
+
+
+@pytest.mark.parametrize("pk,oe", [((2, 2), 1), ((3, 3), 1), ((4, 3), 1), ((2, 2), 0), ((4, 3), 0)])
+def test_adjoint_step_frozen_stage_maps_dot(pk, oe):
+    """Hydro OE (oe = 1) and limiter on: the adjoint with frozen D_l and theta
+    against the oracle tangent with the same coefficients held at their values.
+    A few nodes of the state are near vacuum in pressure; with the OE off the
+    limiter acts on them (without it the step would be rejected)."""
+    p, k = pk
+    rng = np.random.default_rng(900 + 10 * p + k)
+    dom = (0.0, 1.0, 0.0, 1.0)
+    t = Tangent(5, 4, p, k, 5 / 3, dom)
+    prm = dict(oe_hydro=oe, pp=1, s_H=0.5)
+    t.set_params(**prm)
+    t.set_frozen(True)
+    U = generic_state(t, rng)
+    for q in (7, 40, 63):  # E = kinetic energy + a tiny internal energy
+        kin = 0.5 * (U[1, q] ** 2 + U[2, q] ** 2 + U[3, q] ** 2) / U[0, q]
+        U[4, q] = kin + 1e-9
+    Bx, By = rng.uniform(-0.5, 0.5, t.G), rng.uniform(-0.5, 0.5, t.G)
+    Bz = rng.uniform(-0.5, 0.5, t.Z)
+    x = [U, Bx, By, Bz]
+    dx = [rng.standard_normal(np.shape(a)) for a in x]
+    dt = 2e-3
+    t.set_state(*x)
+    t.set_tangent(*dx)
+    assert t.strang_step(dt)[0] == 0
+    Jdx = t.get_tangent()
+    s = solver_like(t)
+    s.set_params(**prm)
+    lam = [rng.standard_normal(np.shape(a)) for a in x]
+    g = s.adjoint_step(packed(t, *x), packed(t, *lam), dt)
+    gs = np.split(g, np.cumsum([U.size, t.G, t.G]))
+    # the frozen coefficients of the two sides agree to rounding, amplified
+    # through the sensor's quotients
+    dot_check([np.ravel(a) for a in lam], [np.ravel(a) for a in Jdx], gs, [np.ravel(a) for a in dx], tol=1e-9)
 
 
 def vortex_problem(n, p, dt_steps_cfl=True):
