@@ -186,12 +186,14 @@ long long mhd_state_size(const mhd_ctx* ctx);
  * transposed discrete curl, the adjoint lumped reconstructions of E_h and
  * J_h, and the adjoint nodal exchange).  The step's intermediate states are
  * recomputed from state_n on the device; the context's own state is not
- * touched.  Stabilisation: the hydro OE and the limiter, when enabled, are
- * differentiated with their coefficients (the OE factors D_l and the limiter
- * factors theta) frozen at the values of the recomputed step, and *flags (may
- * be NULL) reports them (bit 1 hydro OE, bit 2 limiter) with MHD_OK; the
- * artificial resistivity (bit 4) and the velocity OE (bit 8) are not
- * supported and make the call return MHD_EINVAL.  lam_n may alias lam_np1.
+ * touched.  Stabilisation: the maps that are enabled are differentiated
+ * with their coefficients frozen at the values of the recomputed step (the
+ * OE factors D_l and limiter factors theta of the hydro stage maps, the
+ * factors and rho-weighted projector of the velocity OE, the A.R.
+ * coefficient eta; the resistive Ohm load and the Ohmic heating themselves
+ * are differentiated), and *flags (may be NULL) reports which are active (bit
+ * 1 hydro OE, bit 2 limiter, bit 4 A.R., bit 8 velocity OE); the call returns
+ * MHD_OK.  lam_n may alias lam_np1.
  * The first call allocates the adjoint's device buffers (about 14
  * state-sized vectors).  Errors: MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA,
  * MHD_INADMISSIBLE or MHD_NONFINITE if the recomputed step leaves the

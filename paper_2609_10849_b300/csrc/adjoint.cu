@@ -1,7 +1,9 @@
 // Adjoint of one H-M-H Strang step (Algorithm 3, eq. strang-composition) at
-// fixed dt.  The hydro stage maps (OE and limiter) are differentiated with
-// their coefficients (D_l, theta) frozen at the values of the recomputed
-// forward step; the A.R. and the velocity OE must be off.
+// fixed dt.  The stabilisation maps are differentiated with their
+// coefficients frozen at the values of the recomputed forward step: the OE
+// factors D_l and limiter factors theta of the hydro stage maps, the factors
+// and the rho-weighted projector of the velocity OE, and the A.R. coefficient
+// eta (whose resistive Ohm load and Ohmic heating are differentiated).
 //
 // Reverse mode written out by hand: the step's intermediate states are
 // recomputed from its start state (the hydro stage inputs of both hydro
@@ -90,6 +92,9 @@ int ensure_adjoint(mhd_ctx* c) {
   if (e == cudaSuccess) e = aalloc(c, &A.FA, 20 * K * c->n);
   if (e == cudaSuccess) e = aalloc(c, &A.io, 5 * N + 3 * Z);
   if (e == cudaSuccess) e = aalloc(c, &A.frz, 6 * K * (c->n + 2));
+  if (e == cudaSuccess) e = aalloc(c, &A.vfrz, 3 * K * c->n);
+  if (e == cudaSuccess) e = aalloc(c, &A.vstar, 9 * N);
+  if (e == cudaSuccess) e = aalloc(c, &A.eta, K);
   if (e == cudaSuccess) e = aalloc(c, &A.ms.mu, 3 * N);
   if (e == cudaSuccess) e = aalloc(c, &A.ms.s, 3 * N);
   if (e == cudaSuccess) e = aalloc(c, &A.ms.LT, mag_load_doubles(c->p, c->k, (int)K));
@@ -126,17 +131,36 @@ void hydro_fwd(mhd_ctx* c, double* const S[3], double* out, double fac, int h) {
 }
 
 // Magnetic substep tau = dt * fac from Y[0] (e, u, B) with density rho,
-// keeping the stage states Y[1], Y[2]; the result goes to Y[3].
+// keeping the stage states Y[1], Y[2]; the result goes to Y[3].  With the
+// velocity OE on, the velocity of every stage candidate before the filter and
+// the filter's damping factors are kept as well (frozen coefficients).
+bool resistive(const mhd_ctx* c) { return c->prm.ar && c->prm.C_eta != 0.0; }
+
 void mag_fwd(mhd_ctx* c, const double* rho, double fac) {
   AdjBufs& A = c->adj;
   const size_t N = c->N;
+  const int res = resistive(c);
+  if (res) {  // A.R. coefficient from the state entering the substep (frozen for the adjoint)
+    stab_eta(c->p, c->k, rho, A.Y[0], A.Y[0] + 4 * N, c->T, c->M, c->prm, A.eta, c->work, c->st);
+    c->launches += 3;
+  }
+  if (c->prm.oe_vel) {
+    stab_vel_prep(c->p, rho, c->chol, c->T, c->M, c->st);
+    c->launches++;
+  }
   for (int s = 0; s < 3; ++s) {
     double* in = A.Y[s];
     double* out = A.Y[s + 1];
-    mag_stage(c->p, c->k, 1, in + 4 * N, in + N, in, rho, c->eta, 0, A.Y[0] + 4 * N, A.Y[0] + N, A.Y[0],
+    mag_stage(c->p, c->k, 1, in + 4 * N, in + N, in, rho, A.eta, res, A.Y[0] + 4 * N, A.Y[0] + N, A.Y[0],
               out + 4 * N, out + N, out, c->LJ, c->LE, c->T, c->M, c->dt, fac, RK_A[s], RK_B[s], s == 0, c->st);
+    c->launches += 3;
+    if (c->prm.oe_vel) {
+      cudaMemcpyAsync(A.vstar + 3 * N * s, out + N, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+      stab_vel(c->p, c->k, rho, out, out + 4 * N, c->chol, c->T, c->M, c->prm, c->dt, fac, c->work,
+               A.vfrz + (size_t)s * c->M.K * c->n, c->st);
+      c->launches += 4;
+    }
   }
-  c->launches += 9;
 }
 
 // ---- adjoint substeps --------------------------------------------------------------
@@ -164,6 +188,11 @@ void mag_adj(mhd_ctx* c, const double* rho, double* lam, double tau) {
   AdjBufs& A = c->adj;
   const size_t N = c->N, n = 4 * N + 3 * c->Z;
   for (int s = 2; s >= 0; --s) {
+    if (c->prm.oe_vel) {  // velocity OE with frozen coefficients: lam <- V^T lam
+      stab_vel_adjoint(c->p, rho, lam, A.vstar + 3 * N * s, c->chol, A.vfrz + (size_t)s * c->M.K * c->n, c->T,
+                       c->M, c->st);
+      c->launches++;
+    }
     const double* w = lam;
     if (s > 0) {
       k_lin2<<<nblk(n), 256, 0, c->st>>>(lam, RK_A[s], RK_B[s], s == 1, A.L0, A.W, n);
@@ -171,8 +200,8 @@ void mag_adj(mhd_ctx* c, const double* rho, double* lam, double tau) {
     }
     cudaMemsetAsync(A.G, 0, N * sizeof(double), c->st);  // the ideal residual has de/dt = 0
     const double* Ys = A.Y[s];
-    mag_rhs_vjp(c->p, c->k, rho, Ys + N, Ys + 4 * N, w + N, w + 4 * N, A.G + N, A.G + 4 * N, A.lamR, tau, A.ms,
-                c->M, c->st);
+    mag_rhs_vjp(c->p, c->k, rho, Ys + N, Ys + 4 * N, w, w + N, w + 4 * N, resistive(c) ? A.eta : nullptr, A.G + N,
+                A.G + 4 * N, A.lamR, tau, A.ms, c->M, c->st);
     k_fin<<<nblk(n), 256, 0, c->st>>>(w, A.G, tau, s == 0, s > 0 ? lam : A.L0, n);
     c->launches += (s > 0 ? 2 : 1) + 9;
   }
@@ -191,7 +220,7 @@ int stab_flags(const mhd_ctx* c) {
   return (c->prm.oe_hydro ? 1 : 0) | (c->prm.pp ? 2 : 0) | (c->prm.ar && c->prm.C_eta != 0.0 ? 4 : 0) |
          (c->prm.oe_vel ? 8 : 0);
 }
-const int kFrozenSupported = 1 | 2;  // hydro OE and limiter: differentiated with frozen coefficients
+const int kFrozenSupported = 1 | 2 | 4 | 8;  // every stabilisation map, with frozen coefficients
 
 }  // namespace
 
@@ -204,8 +233,7 @@ int mhd_adjoint_step(mhd_ctx* c, const double* state_n, const double* lam_np1, d
   if (!c || !state_n || !lam_np1 || !lam_n) return afail(MHD_EINVAL, "null argument");
   const int fl = stab_flags(c);
   if (flags) *flags = fl;
-  if (fl & ~kFrozenSupported)
-    return afail(MHD_EINVAL, "the adjoint supports the magnetic stage with A.R. and velocity OE off");
+  if (fl & ~kFrozenSupported) return afail(MHD_EINVAL, "unsupported stabilisation map");
   if (!(dt > 0.0)) return afail(MHD_EINVAL, "dt must be positive");
   int r = ensure_adjoint(c);
   if (r != MHD_OK) return r;
@@ -305,8 +333,8 @@ int mhd_mag_rhs_vjp(mhd_ctx* c, const double* rho, const double* u, const double
   grid_to_blocked(io + 2 * Z, A.W + 4 * N, nx, ny, mm, c->st);
   grid_to_blocked(io + 3 * Z, A.W + 4 * N + Z, nx, ny, mm, c->st);
   cudaMemsetAsync(A.lamR, 0, N * sizeof(double), c->st);
-  mag_rhs_vjp(c->p, c->k, A.Ua, Y + N, Y + 4 * N, A.W + N, A.W + 4 * N, A.G + N, A.G + 4 * N, A.lamR, 1.0, A.ms,
-              c->M, c->st);
+  mag_rhs_vjp(c->p, c->k, A.Ua, Y + N, Y + 4 * N, nullptr, A.W + N, A.W + 4 * N, nullptr, A.G + N, A.G + 4 * N,
+              A.lamR, 1.0, A.ms, c->M, c->st);
   blocked_to_grid(A.G + 4 * N, io, nx, ny, mm, c->st);
   blocked_to_grid(A.G + 4 * N + Z, io + Z, nx, ny, mm, c->st);
   c->launches += 15;

@@ -138,7 +138,8 @@ void mag_substep(mhd_ctx* c, double fac) {
     c->launches += 3;
     if (c->prm.oe_vel) {
       Prof pr(c, KC_STAB_VEL);
-      stab_vel(c->p, c->k, c->U, Yout[s], Bout[s], c->chol, c->T, c->M, c->prm, c->dt, fac, c->work, c->st);
+      stab_vel(c->p, c->k, c->U, Yout[s], Bout[s], c->chol, c->T, c->M, c->prm, c->dt, fac, c->work, nullptr,
+               c->st);
       c->launches += 4;
     }
   }

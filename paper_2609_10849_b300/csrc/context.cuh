@@ -41,7 +41,10 @@ void stab_eta(int p, int k, const double* rho, const double* Y, const double* B,
               const Stab& prm, double* eta, double* work, cudaStream_t st);
 void stab_vel_prep(int p, const double* rho, double* chol, const Tab* T, const Mesh& M, cudaStream_t st);
 void stab_vel(int p, int k, const double* rho, double* Y, const double* B, const double* chol, const Tab* T,
-              const Mesh& M, const Stab& prm, const double* dtp, double dtfac, double* work, cudaStream_t st);
+              const Mesh& M, const Stab& prm, const double* dtp, double dtfac, double* work, double* frz,
+              cudaStream_t st);
+void stab_vel_adjoint(int p, const double* rho, double* lam, const double* ustar, const double* chol,
+                      const double* frzD, const Tab* T, const Mesh& M, cudaStream_t st);
 size_t stab_work_doubles(int p, int k, const Mesh& M);
 size_t stab_chol_doubles(int p, const Mesh& M);
 void set_error_message(const char* msg);
@@ -58,9 +61,9 @@ void adj_cons_to_prim(const double* U, const double* lamY, const double* lamR, d
 cudaError_t mag_adj_prepare(int p, int k);
 bool mag_tile_ok(int p, int k, int v);
 size_t mag_adj_load_doubles(int p, int k, int K);
-void mag_rhs_vjp(int p, int k, const double* rho, const double* u, const double* B, const double* wu,
-                 const double* wB, double* gu, double* gB, double* grho, double rho_scale, const MagAdjScratch& S,
-                 const Mesh& M, cudaStream_t st);
+void mag_rhs_vjp(int p, int k, const double* rho, const double* u, const double* B, const double* we,
+                 const double* wu, const double* wB, const double* eta, double* gu, double* gB, double* grho,
+                 double rho_scale, const MagAdjScratch& S, const Mesh& M, cudaStream_t st);
 }  // namespace mhd
 
 // Device buffers of the adjoint, allocated on the first adjoint call.
@@ -78,6 +81,9 @@ struct AdjBufs {
   double* FA = nullptr;    // face adjoints [2][2][5][K (p+1)]
   double* io = nullptr;    // packed host-layout staging [5N + 3Z]
   double* frz = nullptr;   // frozen stage-map coefficients [2][3][K][p+3]
+  double* vfrz = nullptr;  // frozen velocity-OE factors [3][K][p+1]
+  double* vstar = nullptr; // velocity before the velocity OE, per magnetic stage [3][3N]
+  double* eta = nullptr;   // frozen A.R. coefficient of the recomputed magnetic substep [K]
   mhd::MagAdjScratch ms{};
 };
 

@@ -940,12 +940,15 @@ void stab_vel_prep(int p, const double* rho, double* chol, const Tab* T, const M
 }
 
 // Velocity OE map with heating of e; one element per segment of SW lanes.
+// frz (may be null): the damping factors D_0..D_p of every element, [K][p+1],
+// for the adjoint (frozen coefficients).
 template <int P, int KM>
 __global__ void __launch_bounds__(OCfg<P>::threads) k_vel_oe(const double* __restrict__ rho, double* __restrict__ Y,
                                                              const double* __restrict__ B,
                                                              const double* __restrict__ Psi, StatsView V,
                                                              const Tab* __restrict__ T, Mesh M, Stab prm,
-                                                             const double* __restrict__ dtp, double dtfac) {
+                                                             const double* __restrict__ dtp, double dtfac,
+                                                             double* __restrict__ frz) {
   using C = OCfg<P>;
   constexpr int n = C::n, n2 = C::n2, EB = C::EB, SW = C::SW;
   __shared__ double sPsi[EB][n2 * n2];
@@ -984,6 +987,7 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_vel_oe(const double* __res
 #pragma unroll
   for (int d = 0; d < 3; ++d) sWu[d][tid] = W * u[d];
   oe_factors<P>(V, 3, q, el, kk, ex, ey, lam, prm.s_M * dtp[0] * dtfac, M, ssig, sD);  // syncs
+  if (frz && q < n && k < M.K) frz[(size_t)k * n + q] = sD[el][q];
   // coefficients c_alpha = sum_t Psi[t][alpha] W_t u_t (lane q plays alpha)
   if (node) {
 #pragma unroll
@@ -1016,7 +1020,8 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_vel_oe(const double* __res
 }
 
 void stab_vel(int p, int k, const double* rho, double* Y, const double* B, const double* chol, const Tab* T,
-              const Mesh& M, const Stab& prm, const double* dtp, double dtfac, double* work, cudaStream_t st) {
+              const Mesh& M, const Stab& prm, const double* dtp, double dtfac, double* work, double* frz,
+              cudaStream_t st) {
   StatsView V = stats_view(work, p, M);
   const size_t N = (size_t)M.K * (p + 1) * (p + 1);
   switch (p) {
@@ -1027,9 +1032,116 @@ void stab_vel(int p, int k, const double* rho, double* Y, const double* B, const
   }
 #define MHD_VOE_CASE(PP, KK)                                                                            \
   k_vel_oe<PP, KK><<<(unsigned)((M.K + OCfg<PP>::EB - 1) / OCfg<PP>::EB), OCfg<PP>::threads, 0, st>>>( \
-      rho, Y, B, chol, V, T, M, prm, dtp, dtfac)
+      rho, Y, B, chol, V, T, M, prm, dtp, dtfac, frz)
   MHD_DISPATCH_PK(p, k, MHD_VOE_CASE);
 #undef MHD_VOE_CASE
+}
+
+// Adjoint of the velocity OE map (eq. magnetic-oe-map) with the damping
+// factors D_l and the rho-weighted projector Psi frozen.  Per element and
+// component, with W_q = Jdet w_q rho_q and shells l of the modal basis:
+//   c = Psi^T W u*,  w_l = Psi_l c_l,  u' = sum_l D_l w_l,
+//   e' = e + sum_{l >= 1} (1 - D_l^2)/2 sum_d w_{l,d}^2.
+// For adjoints (lam_u', lam_e'): mu_l = D_l lam_u' + [l >= 1](1 - D_l^2) w_l lam_e',
+// lam_c[alpha] = sum_q Psi[q][alpha] mu_{l(alpha)}[q], lam_u = W Psi lam_c, and
+// lam_e = lam_e'.  lam holds (e, u) and is updated in place (u part).
+template <int P>
+__global__ void __launch_bounds__(OCfg<P>::threads) k_adj_vel_oe(const double* __restrict__ rho,
+                                                                 double* __restrict__ lam,
+                                                                 const double* __restrict__ ustar,
+                                                                 const double* __restrict__ Psi,
+                                                                 const double* __restrict__ frzD,
+                                                                 const Tab* __restrict__ T, Mesh M) {
+  using C = OCfg<P>;
+  constexpr int n = C::n, n2 = C::n2, EB = C::EB, SW = C::SW;
+  __shared__ double sPsi[EB][n2 * n2];
+  __shared__ double sWu[3][EB * SW];
+  __shared__ double sc[3][EB * SW];
+  __shared__ double smu[3][n][EB * SW];
+  const size_t N = (size_t)M.K * n2;
+  const int tid = threadIdx.x, el = tid / SW, q = tid % SW;
+  const bool node = q < n2;
+  const int k = blockIdx.x * EB + el;
+  const bool valid = k < M.K && node;
+  const int kk = k < M.K ? k : M.K - 1;
+  const int qq = node ? q : 0;
+  const int i = qq % n, j = qq / n;
+  for (int t = q; t < n2 * n2; t += SW) sPsi[el][t] = Psi[(size_t)kk * n2 * n2 + t];
+  const size_t gq = (size_t)kk * n2 + qq;
+  const double W = node ? M.Jdet * T->wp[i] * T->wp[j] * rho[gq] : 0.0;
+  double lu[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    sWu[d][tid] = node ? W * ustar[d * N + gq] : 0.0;
+    lu[d] = node ? lam[(1 + d) * N + gq] : 0.0;
+  }
+  const double le = node ? lam[gq] : 0.0;
+  double D[n];
+#pragma unroll
+  for (int l = 0; l < n; ++l) D[l] = frzD[(size_t)kk * n + l];
+  __syncthreads();
+  if (node) {  // c_alpha (lane q plays alpha)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double s = 0.0;
+#pragma unroll
+      for (int t = 0; t < n2; ++t) s = fma(sPsi[el][t * n2 + q], sWu[d][el * SW + t], s);
+      sc[d][tid] = s;
+    }
+  }
+  __syncthreads();
+  if (node) {  // mu_l at node q
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+      for (int l = 0; l <= P; ++l) {
+        double wl = 0.0;
+#pragma unroll
+        for (int al = l * l; al < (l + 1) * (l + 1); ++al) wl = fma(sc[d][el * SW + al], sPsi[el][q * n2 + al], wl);
+        double mu = D[l] * lu[d];
+        if (l > 0) mu = fma(fma(-D[l], D[l], 1.0) * wl, le, mu);
+        smu[d][l][tid] = mu;
+      }
+    }
+  }
+  __syncthreads();
+  if (node) {  // lam_c[alpha] (lane q plays alpha, in shell l)
+    int l = 0;
+#pragma unroll
+    for (int ll = 1; ll <= P; ++ll)
+      if (q >= ll * ll) l = ll;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double s = 0.0;
+#pragma unroll
+      for (int t = 0; t < n2; ++t) s = fma(sPsi[el][t * n2 + q], smu[d][l][el * SW + t], s);
+      sc[d][tid] = s;
+    }
+  }
+  __syncthreads();
+  if (valid) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double s = 0.0;
+#pragma unroll
+      for (int al = 0; al < n2; ++al) s = fma(sPsi[el][q * n2 + al], sc[d][el * SW + al], s);
+      lam[(1 + d) * N + gq] = W * s;
+    }
+  }
+}
+
+void stab_vel_adjoint(int p, const double* rho, double* lam, const double* ustar, const double* chol,
+                      const double* frzD, const Tab* T, const Mesh& M, cudaStream_t st) {
+#define MHD_ADJ_VOE(PP)                                                                                    \
+  k_adj_vel_oe<PP><<<(unsigned)((M.K + OCfg<PP>::EB - 1) / OCfg<PP>::EB), OCfg<PP>::threads, 0, st>>>( \
+      rho, lam, ustar, chol, frzD, T, M)
+  switch (p) {
+    case 1: MHD_ADJ_VOE(1); break;
+    case 2: MHD_ADJ_VOE(2); break;
+    case 3: MHD_ADJ_VOE(3); break;
+    case 4: MHD_ADJ_VOE(4); break;
+  }
+#undef MHD_ADJ_VOE
 }
 
 }  // namespace mhd

@@ -287,6 +287,7 @@ class Solver:
         (ps, pl, po), dev = _ptrs(state, lam, out)
         flags = C.c_int(0)
         code = lib().mhd_adjoint_step(self._h, ps, pl, po, float(dt), dev, C.byref(flags))
+        self.last_adjoint_flags = flags.value  # stabilisation maps differentiated with frozen coefficients
         if code < 0:
             raise MhdError(code, lib().mhd_last_error().decode() + f" (flags {flags.value})")
         return out

@@ -158,21 +158,17 @@ def test_adjoint_step_dot(pk):
     dot_check([np.ravel(a) for a in lam], [np.ravel(a) for a in Jdx], gs, [np.ravel(a) for a in dx])
 
 
-def test_adjoint_refuses_magnetic_stabilisation():
-    from paper_2609_10849_b300.mhd import MhdError
+def test_adjoint_reports_frozen_maps():
     rng = np.random.default_rng(890)
     t = Tangent(3, 3, 2, 2, 5 / 3)
     U = generic_state(t, rng)
     s = solver_like(t)
     x = packed(t, U, np.zeros(t.G), np.zeros(t.G), np.zeros(t.Z))
-    s.set_params(ar=1, C_eta=0.2)
-    with pytest.raises(MhdError, match="flags 4"):
-        s.adjoint_step(x, x.copy(), 1e-3)
-    s.set_params(ar=0, oe_vel=1)
-    with pytest.raises(MhdError, match="flags 8"):
-        s.adjoint_step(x, x.copy(), 1e-3)
-    s.set_params(oe_vel=0, oe_hydro=1, pp=1)  # supported with frozen coefficients
     s.adjoint_step(x, x.copy(), 1e-3)
+    assert s.last_adjoint_flags == 0
+    s.set_params(oe_hydro=1, pp=1, ar=1, C_eta=0.2, oe_vel=1)
+    s.adjoint_step(x, x.copy(), 1e-3)
+    assert s.last_adjoint_flags == 1 | 2 | 4 | 8
 
 
 @pytest.mark.parametrize("pk,oe", [((2, 2), 1), ((3, 3), 1), ((4, 3), 1), ((2, 2), 0), ((4, 3), 0)])
@@ -294,3 +290,64 @@ def test_vortex_adjoint_full_size():
         fd = (J(rho0 + eps * dr, u0 + eps * du).item() - J(rho0 - eps * dr, u0 - eps * du).item()) / (2 * eps)
     ad = float((rho.grad * dr).sum() + (u.grad * du).sum())
     assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+
+
+@pytest.mark.parametrize("pk", [(1, 1), (2, 2), (3, 3), (4, 4)])
+def test_adjoint_step_frozen_velocity_oe_dot(pk):
+    """Velocity OE on (and hydro OE, limiter): the adjoint with frozen D_l and
+    rho-weighted projector against the oracle tangent holding the same
+    coefficients at their values."""
+    p, k = pk
+    rng = np.random.default_rng(950 + 10 * p + k)
+    dom = (0.0, 1.0, 0.0, 1.0)
+    t = Tangent(4, 5, p, k, 5 / 3, dom)
+    prm = dict(oe_hydro=1, pp=1, oe_vel=1, s_H=0.2, s_M=0.5)
+    t.set_params(**prm)
+    t.set_frozen(True)
+    U = generic_state(t, rng)
+    Bx, By = rng.uniform(-0.5, 0.5, t.G), rng.uniform(-0.5, 0.5, t.G)
+    Bz = rng.uniform(-0.5, 0.5, t.Z)
+    x = [U, Bx, By, Bz]
+    dx = [rng.standard_normal(np.shape(a)) for a in x]
+    dt = 2e-3
+    t.set_state(*x)
+    t.set_tangent(*dx)
+    assert t.strang_step(dt)[0] == 0
+    Jdx = t.get_tangent()
+    s = solver_like(t)
+    s.set_params(**prm)
+    lam = [rng.standard_normal(np.shape(a)) for a in x]
+    g = s.adjoint_step(packed(t, *x), packed(t, *lam), dt)
+    gs = np.split(g, np.cumsum([U.size, t.G, t.G]))
+    dot_check([np.ravel(a) for a in lam], [np.ravel(a) for a in Jdx], gs, [np.ravel(a) for a in dx], tol=1e-9)
+
+
+@pytest.mark.parametrize("pk", [(1, 0), (2, 1), (3, 3), (4, 4)])
+def test_adjoint_step_frozen_resistivity_dot(pk):
+    """Every stabilisation map on, A.R. included: the adjoint with eta frozen
+    (resistive Ohm load and Ohmic heating differentiated) against the oracle
+    tangent holding the same coefficients at their values."""
+    p, k = pk
+    rng = np.random.default_rng(970 + 10 * p + k)
+    dom = (0.0, 1.0, 0.0, 1.0)
+    t = Tangent(4, 5, p, k, 5 / 3, dom)
+    prm = dict(oe_hydro=1, pp=1, oe_vel=1, ar=1, C_eta=0.2, s_H=0.2, s_M=0.5)
+    t.set_params(**prm)
+    t.set_frozen(True)
+    U = generic_state(t, rng)
+    Bx, By = rng.uniform(-0.5, 0.5, t.G), rng.uniform(-0.5, 0.5, t.G)
+    Bz = rng.uniform(-0.5, 0.5, t.Z)
+    x = [U, Bx, By, Bz]
+    dx = [rng.standard_normal(np.shape(a)) for a in x]
+    dt = 2e-3
+    t.set_state(*x)
+    t.set_tangent(*dx)
+    assert t.strang_step(dt)[0] == 0
+    assert t.eta().max() > 0
+    Jdx = t.get_tangent()
+    s = solver_like(t)
+    s.set_params(**prm)
+    lam = [rng.standard_normal(np.shape(a)) for a in x]
+    g = s.adjoint_step(packed(t, *x), packed(t, *lam), dt)
+    gs = np.split(g, np.cumsum([U.size, t.G, t.G]))
+    dot_check([np.ravel(a) for a in lam], [np.ravel(a) for a in Jdx], gs, [np.ravel(a) for a in dx], tol=1e-9)
