@@ -266,3 +266,35 @@ def test_full_size_tiled_parity_stabilised():
         assert rel(a, b, bscale) <= 1e-12
     eta_t = np.tile(o.eta().reshape(16, 16), (reps, reps)).ravel()
     assert rel(s.eta(), eta_t) <= 1e-9
+
+
+def test_full_size_blast_1024_tiled():
+    """Config 3 at its full size (1024 x 1024 elements, p = k = 3, every
+    stabilisation map on, in the bench's launch configuration): a 64 x 64 blast
+    tiled 16 x 16 times keeps every row, column and global sensor statistic,
+    so every tile must reproduce the oracle's stabilised Strang step; mass is
+    conserved and B stays divergence-free at this size."""
+    from paper_2609_10849_b300.mhd import Solver
+    wl = workloads.blast()
+    o = oracle_state(wl, 64, 64, 3, 3)
+    o.set_params(cfl=0.4, **STAB)
+    reps = 16
+    x0, x1, y0, y1 = o.domain
+    s = Solver(64 * reps, 64 * reps, 3, 3, wl["gamma"], (x0, x0 + reps * (x1 - x0), y0, y0 + reps * (y1 - y0)))
+    s.set_params(cfl=0.4, **STAB)
+    s.set_state(*tiled(o, reps))
+    d0 = s.diagnostics()
+    dt = o.cfl_dt()
+    assert o.strang_step(dt)[0] == 0
+    st, taken = s.strang_step(dt)
+    assert st == 0 and taken == dt
+    U, Bx, By, Bz = s.get_state()
+    Ut, Bxt, Byt, Bzt = tiled(o, reps)
+    bscale = max(np.abs(Bxt).max(), np.abs(Byt).max())
+    assert rel(U, Ut) <= 1e-12
+    for a, b in [(Bx, Bxt), (By, Byt), (Bz, Bzt)]:
+        assert rel(a, b, bscale) <= 1e-12
+    d1 = s.diagnostics()
+    assert abs(d1["mass"] - d0["mass"]) <= 1e-13 * d0["mass"]
+    assert d1["div_B"] <= 1e-12 * d1["B_max"]
+    assert d1["rho_min"] > 0 and d1["p_min"] > 0
