@@ -36,7 +36,7 @@ NOMINAL_FP64_TFLOPS = 1.25  # B300 dense FP64, nominal (profiling recipe table)
 # DRAM bytes (read + write) of one k_vol<3> launch from the ncu capture summarised in
 # profiles/kernels_orszag_tang_256_full.md (same kernel source as this bench); must be reset
 # to None whenever the volume kernel changes until it is captured again.
-K_VOL_TRAFFIC_BYTES = 105.0e6 + 11.37e6
+K_VOL_TRAFFIC_BYTES = None
 # Config 2 of the workload: OE (both stages), positivity limiter, artificial
 # resistivity and velocity filter active, with the paper's constants.
 STAB = dict(oe_hydro=1, oe_vel=1, pp=1, ar=1, s_H=0.02, s_M=0.02, C_s=5.0, C_eta=0.2)

@@ -139,7 +139,7 @@ struct ACfg {
 // log aR = 2 atanh(f): F = lz/(2f), F' = (1/(1 - f^2) - F)/f.
 __device__ __forceinline__ double logmean_FdF(double f, double lz, double* dF, double* iF) {
   const double u = f * f;
-  if (u < 1e-2) {
+  if (__double_as_longlong(u) < __double_as_longlong(1e-2)) {  // u >= 0: integer compare of the bit patterns
     const double c[8] = {1.0, 1.0 / 3.0, 1.0 / 5.0, 1.0 / 7.0, 1.0 / 9.0, 1.0 / 11.0, 1.0 / 13.0, 1.0 / 15.0};
     double F = c[7], G = 7.0 * 2.0 * c[7];
 #pragma unroll

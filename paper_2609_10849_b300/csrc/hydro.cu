@@ -41,7 +41,8 @@ __device__ __forceinline__ int pair_index(int a, int b) {  // a < b
 // (from F (1/F) = 1 term by term; the first omitted term is below 1e-17).
 __device__ __forceinline__ double logmean_factor(double aL, double aR, double f, double* invF) {
   double u = f * f;
-  if (u < 1e-4) {
+  // u >= 0: the branch test compares bit patterns (integer pipe), equal to u < 1e-4
+  if (__double_as_longlong(u) < __double_as_longlong(1e-4)) {
     *invF = fma(u, fma(u, fma(u, -44.0 / 945.0, -4.0 / 45.0), -1.0 / 3.0), 1.0);
     return fma(u, fma(u, fma(u, 1.0 / 7.0, 1.0 / 5.0), 1.0 / 3.0), 1.0);
   }

@@ -58,6 +58,8 @@ struct Tab {
   double WL_P[MHD_NMAX][MHD_LMAX];            // wp_a l^L_c(xp_a)
   double iwLs[MHD_LMAX];                      // 1 / assembled GLL(k+1) weight (2 wL_0 at a = 0)
   double iwG[MHD_NMAX];                       // 1 / wG
+  double Wq[MHD_NMAX * MHD_NMAX];             // 0.25 wp_i wp_j at node j*(p+1)+i (element-average weights)
+  double hwp[MHD_NMAX];                       // 0.5 wp_i
 };
 
 // Device copy of the tables of the 8 supported (p, k) pairs.
@@ -117,6 +119,18 @@ __device__ __forceinline__ double rcp(double x) {
   double e = fma(-x, r, 1.0);
   double t = fma(e, e, e);
   return fma(r, t, r);
+}
+
+// ---- order-preserving integer keys of doubles ---------------------------------
+// key(a) < key(b) <=> a < b for non-NaN doubles (-0 sorts below +0), so
+// minima and maxima can be taken with 64-bit integer operations, which run on
+// the integer pipe instead of the FP64 pipe; dkey_inv(dkey(x)) == x bitwise.
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dkey_inv(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
 }
 
 // ---- launch counting ----------------------------------------------------------

@@ -86,18 +86,20 @@ __global__ void k_stats(const double* __restrict__ F, size_t stride, int nc, Sta
   const int c = it / (1 + 2 * n), w = it % (1 + 2 * n);
   const double* f = F + c * stride;
   const int ex = k % M.nx, ey = k / M.nx;
-  if (w == 0) {
-    double s = 0.0, mx = -DBL_MAX, mn = DBL_MAX;
+  if (w == 0) {  // weighted average; nodal max and min on integer keys
+    double s = 0.0;
+    long long mx = dkey(-DBL_MAX), mn = dkey(DBL_MAX);
 #pragma unroll
     for (int q = 0; q < n2; ++q) {
       double v = f[(size_t)k * n2 + q];
-      s = fma(0.25 * T->wp[q % n] * T->wp[q / n], v, s);
-      mx = fmax(mx, v);
-      mn = fmin(mn, v);
+      s = fma(T->Wq[q], v, s);
+      const long long kv = dkey(v);
+      mx = kv > mx ? kv : mx;
+      mn = kv < mn ? kv : mn;
     }
     V.avg[c * K + k] = s;
-    V.emax[c * K + k] = mx;
-    V.emin[c * K + k] = mn;
+    V.emax[c * K + k] = dkey_inv(mx);
+    V.emin[c * K + k] = dkey_inv(mn);
     return;
   }
   const int I = (w - 1) / n, r = (w - 1) % n;
@@ -113,7 +115,7 @@ __global__ void k_stats(const double* __restrict__ F, size_t stride, int nc, Sta
       double wA = I == 0 ? f[(size_t)kA * n2 + tt * n + P] : f[(size_t)kA * n2 + P * n + tt];
       double wB = I == 0 ? f[(size_t)k * n2 + tt * n] : f[(size_t)k * n2 + tt];
       double jmp = wB - wA;
-      acc = fma(0.5 * T->wp[tt] * jmp, jmp, acc);
+      acc = fma(T->hwp[tt] * jmp, jmp, acc);
     }
   } else {
 #pragma unroll
@@ -127,7 +129,7 @@ __global__ void k_stats(const double* __restrict__ F, size_t stride, int nc, Sta
         dB = fma(T->Dr0[r][s], wB, dB);
       }
       double jmp = dB - dA;
-      acc = fma(0.5 * T->wp[tt] * jmp, jmp, acc);
+      acc = fma(T->hwp[tt] * jmp, jmp, acc);
     }
     acc *= scale * scale;
   }
@@ -255,17 +257,26 @@ struct OCfg {
   static constexpr int threads = EB * SW;
 };
 
+// Segment minimum / maximum on order-preserving integer keys (integer pipe).
 template <int SW>
 __device__ __forceinline__ double seg_min(double v) {
+  long long kv = dkey(v);
 #pragma unroll
-  for (int o = SW / 2; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
+  for (int o = SW / 2; o > 0; o >>= 1) {
+    const long long w = __shfl_xor_sync(0xffffffffu, kv, o);
+    kv = w < kv ? w : kv;
+  }
+  return dkey_inv(kv);
 }
 template <int SW>
 __device__ __forceinline__ double seg_max(double v) {
+  long long kv = dkey(v);
 #pragma unroll
-  for (int o = SW / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
+  for (int o = SW / 2; o > 0; o >>= 1) {
+    const long long w = __shfl_xor_sync(0xffffffffu, kv, o);
+    kv = w > kv ? w : kv;
+  }
+  return dkey_inv(kv);
 }
 template <int SW>
 __device__ __forceinline__ double seg_sum(double v) {

@@ -191,6 +191,9 @@ void host_tables(int p, int k, Tab* T) {
   }
   for (int a = 0; a < mL; ++a) T->iwLs[a] = (double)(1.0L / (a == 0 ? 2.0L * wL[0] : wL[a]));
   for (int a = 0; a < mm; ++a) T->iwG[a] = (double)(1.0L / wG[a]);
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) T->Wq[j * n + i] = 0.25 * T->wp[i] * T->wp[j];
+  for (int i = 0; i < n; ++i) T->hwp[i] = 0.5 * T->wp[i];
   // exact GLL(k+1) mass with the (k+2)-point Gauss rule
   for (int a = 0; a < mL; ++a)
     for (int b = 0; b < mL; ++b) {
