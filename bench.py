@@ -295,18 +295,21 @@ def adjoint_leg(steps=20, every=20, n=128, p=4):
     with torch.no_grad():
         target = strang_steps(s, pack_primitive(rs, u0, p0, s.gamma, B), dt, steps, every)[:s.N].clone()
     Mq = dev(np.tile(np.outer(gll_weights(p), gll_weights(p)).ravel() * (10.0 / n) ** 2 / 4, s.K))
-    rho_v = r0.clone().requires_grad_(True)
-    u_v = u0.clone().requires_grad_(True)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    xT = strang_steps(s, pack_primitive(rho_v, u_v, p0, s.gamma, B), dt, steps, every)
-    J = 0.5 * (Mq * (xT[:s.N] - target) ** 2).sum()
-    torch.cuda.synchronize()
-    tf = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    J.backward()
-    torch.cuda.synchronize()
-    tb = time.perf_counter() - t0
+    def forward_backward():
+        rho_v = r0.clone().requires_grad_(True)
+        u_v = u0.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        xT = strang_steps(s, pack_primitive(rho_v, u_v, p0, s.gamma, B), dt, steps, every)
+        J = 0.5 * (Mq * (xT[:s.N] - target) ** 2).sum()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        J.backward()
+        torch.cuda.synchronize()
+        return t1 - t0, time.perf_counter() - t1
+
+    forward_backward()  # warm-up: first-use costs and the adjoint's tape allocation
+    tf, tb = forward_backward()
     s.set_packed(x)
     s.strang_steps(dt, steps)
     torch.cuda.synchronize()
@@ -319,8 +322,9 @@ def adjoint_leg(steps=20, every=20, n=128, p=4):
             "plain_ms_per_step": 1e3 * tp / steps, "forward_ms_per_step": 1e3 * tf / steps,
             "backward_ms_per_step": 1e3 * tb / steps, "backward_over_plain": tb / tp,
             "plain_dof_updates_per_s": dofs * steps / tp, "adjoint_dof_updates_per_s": dofs * steps / tb,
-            "note": "backward = segment recomputation + one mhd_adjoint_step per step (which recomputes its "
-                    "stage states); forward includes checkpoint copies"}
+            "note": "backward = one mhd_adjoint_segment per checkpoint segment (recomputes the segment once, "
+                    "recording every stage state, then the step adjoints); forward includes checkpoint copies; "
+                    "second of two forward/backward passes"}
 
 
 def run_batch(args):

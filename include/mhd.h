@@ -201,6 +201,16 @@ long long mhd_state_size(const mhd_ctx* ctx);
 int mhd_adjoint_step(mhd_ctx* ctx, const double* state_n, const double* lam_np1, double* lam_n, double dt,
                      int on_device, int* flags);
 
+/* Adjoint of a checkpoint segment of nsteps fixed-dt Strang steps from the
+ * packed state_0: one forward pass records the stage states of every step of
+ * the segment in device memory (about 60 state-sized vectors per step; the
+ * tapes stay allocated for later calls), then the step adjoints run from the
+ * last step to the first: lam_0 = (d(S^dt)^nsteps/dx)(state_0)^T lam_end.
+ * mhd_adjoint_step is the nsteps = 1 case.  Flags, frozen coefficients,
+ * aliasing and errors as for mhd_adjoint_step. */
+int mhd_adjoint_segment(mhd_ctx* ctx, const double* state_0, int nsteps, const double* lam_end, double* lam_0,
+                        double dt, int on_device, int* flags);
+
 /* Test hook: (dL_E/dU)(U)^T nu for the hydro residual of mhd_hydro_rhs
  * (U, nu, out [5][N]). */
 int mhd_hydro_rhs_vjp(mhd_ctx* ctx, const double* U, const double* nu, double* out, int on_device);

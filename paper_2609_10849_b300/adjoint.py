@@ -3,20 +3,22 @@
 The paper has no adjoint; this is the library's differentiation pattern.  The
 forward pass runs ``nsteps`` Strang steps S^dt (Algorithm 3) through the C ABI
 and keeps a checkpoint of the packed state every ``checkpoint_every`` steps.
-The backward pass walks the checkpoints in reverse: it recomputes the
-step-start states of one segment from its checkpoint, then applies
-``mhd_adjoint_step`` (the hand-written vector-Jacobian product of one step)
-from the last step of the segment to the first.  All arithmetic runs in the
-library's CUDA kernels; torch provides device memory and the autograd graph.
+The backward pass walks the checkpoints in reverse: for each segment,
+``mhd_adjoint_segment`` recomputes the segment once from its checkpoint,
+recording every stage state in device memory, and applies the hand-written
+step adjoints from the last step of the segment to the first.  All arithmetic
+runs in the library's CUDA kernels; torch provides device memory and the
+autograd graph.
 
-The derivative is that of the step with every stabilisation map off
-(``mhd_adjoint_step`` refuses otherwise) at the fixed ``dt``.
+The derivative is taken at the fixed ``dt``; enabled stabilisation maps are
+differentiated with their coefficients frozen at the recomputed forward
+values (see ``mhd_adjoint_step``).
 """
 from __future__ import annotations
 
 import torch
 
-from .mhd import MHD_OK, MhdError, Solver
+from .mhd import Solver
 
 
 class StrangSteps(torch.autograd.Function):
@@ -48,15 +50,7 @@ class StrangSteps(torch.autograd.Function):
         torch.cuda.current_stream().synchronize()
         for si in reversed(range(len(ctx.ckpts))):
             m = min(every, ctx.nsteps - si * every)
-            states = [ctx.ckpts[si]]
-            solver.set_packed(ctx.ckpts[si])
-            for _ in range(m - 1):
-                st, _taken = solver.strang_step(dt)
-                if st != MHD_OK:
-                    raise MhdError(st, "recomputed step was retried with a smaller dt")
-                states.append(solver.get_packed(torch.empty_like(lam)))
-            for i in reversed(range(m)):
-                solver.adjoint_step(states[i], lam, dt, out=lam)
+            solver.adjoint_segment(ctx.ckpts[si], m, lam, dt, out=lam)
         ctx.ckpts = None
         return lam, None, None, None, None
 

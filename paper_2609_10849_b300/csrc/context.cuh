@@ -66,24 +66,31 @@ void mag_rhs_vjp(int p, int k, const double* rho, const double* u, const double*
                  double rho_scale, const MagAdjScratch& S, const Mesh& M, cudaStream_t st);
 }  // namespace mhd
 
-// Device buffers of the adjoint, allocated on the first adjoint call.
+// Stage states of one recomputed Strang step (the adjoint's tape).
+struct StepTape {
+  double* hS[2][3] = {};     // stage inputs of the two hydro substeps [5N]
+  double* Ua = nullptr;      // state after the first hydro substep [5N]
+  double* Y[4] = {};         // magnetic stage states (e [N], u [3N], B [3Z] contiguous)
+  double* frz = nullptr;     // frozen stage-map coefficients [2][3][K][p+3]
+  double* vfrz = nullptr;    // frozen velocity-OE factors [3][K][p+1]
+  double* vstar = nullptr;   // velocity before the velocity OE, per magnetic stage [3][3N]
+  double* eta = nullptr;     // frozen A.R. coefficient of the magnetic substep [K]
+  double* chol = nullptr;    // velocity-OE projectors of the step [K][(p+1)^4] (velocity OE only)
+};
+
+// Device buffers of the adjoint, allocated on the first adjoint call; tapes
+// grow to the longest segment requested.
 struct AdjBufs {
   bool ready = false;
-  double* hS[2][3] = {};  // stage inputs of the two hydro substeps [5N]
-  double* Ua = nullptr;   // state after the first hydro substep [5N]
-  double* Y[4] = {};      // magnetic stage states (e [N], u [3N], B [3Z] contiguous)
+  std::vector<StepTape> tapes;
   double* lamU = nullptr;  // [5N]
   double* lamM = nullptr;  // magnetic adjoint (e, u, B) [4N + 3Z]
   double* W = nullptr;     // stage adjoint input [max(5N, 4N + 3Z)]
   double* L0 = nullptr;    // accumulated adjoint of the substep input
-  double* G = nullptr;     // residual VJP
+  double* G = nullptr;     // residual VJP; also the scratch end state of a recomputed step
   double* lamR = nullptr;  // adjoint of the frozen density [N]
   double* FA = nullptr;    // face adjoints [2][2][5][K (p+1)]
   double* io = nullptr;    // packed host-layout staging [5N + 3Z]
-  double* frz = nullptr;   // frozen stage-map coefficients [2][3][K][p+3]
-  double* vfrz = nullptr;  // frozen velocity-OE factors [3][K][p+1]
-  double* vstar = nullptr; // velocity before the velocity OE, per magnetic stage [3][3N]
-  double* eta = nullptr;   // frozen A.R. coefficient of the recomputed magnetic substep [K]
   mhd::MagAdjScratch ms{};
 };
 

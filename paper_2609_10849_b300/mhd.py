@@ -80,6 +80,8 @@ _SIGS = {
     "mhd_state_size": (C.c_longlong, [C.c_void_p]),
     "mhd_adjoint_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                                    C.POINTER(C.c_int)]),
+    "mhd_adjoint_segment": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
+                                      C.POINTER(C.c_int)]),
     "mhd_hydro_rhs_vjp": (C.c_int, [C.c_void_p] + [C.c_void_p] * 3 + [C.c_int]),
     "mhd_mag_rhs_vjp": (C.c_int, [C.c_void_p] + [C.c_void_p] * 14 + [C.c_int]),
     "mhd_autotune": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -288,6 +290,19 @@ class Solver:
         flags = C.c_int(0)
         code = lib().mhd_adjoint_step(self._h, ps, pl, po, float(dt), dev, C.byref(flags))
         self.last_adjoint_flags = flags.value  # stabilisation maps differentiated with frozen coefficients
+        if code < 0:
+            raise MhdError(code, lib().mhd_last_error().decode() + f" (flags {flags.value})")
+        return out
+
+    def adjoint_segment(self, state, nsteps, lam, dt, out=None):
+        """lam_0 for nsteps fixed-dt steps from ``state`` (one checkpoint segment,
+        recorded in device memory in one forward pass); ``out`` may be ``lam``."""
+        if out is None:
+            out = np.zeros_like(lam) if isinstance(lam, np.ndarray) else lam.clone()
+        (ps, pl, po), dev = _ptrs(state, lam, out)
+        flags = C.c_int(0)
+        code = lib().mhd_adjoint_segment(self._h, ps, int(nsteps), pl, po, float(dt), dev, C.byref(flags))
+        self.last_adjoint_flags = flags.value
         if code < 0:
             raise MhdError(code, lib().mhd_last_error().decode() + f" (flags {flags.value})")
         return out
