@@ -49,6 +49,19 @@ def workload_config(stab, mesh=256):
                 l2="working set per step > 126 MB L2 (state + stage buffers ~0.5 GB), no flush needed")
 
 
+def max_over_ranks(ms, dist, device):
+    """Slowest rank's time (ms): every rank gets the maximum (replicas, weak scaling)."""
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(world, dofs_per_rank, steps, ms):
+    """DOF-updates/s of the whole job: every rank advances its own replica."""
+    return world * dofs_per_rank * steps / (ms * 1e-3)
+
+
 def dofs_per_element(p, k):
     return 5 * (p + 1) ** 2 + 3 * (k + 1) ** 2
 
@@ -395,11 +408,9 @@ def main():
     ms = e0.elapsed_time(e1)
     launches = s.launch_count() - l0
     if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, "cuda")
     ms_per_step = ms / args.steps
-    value = world * dofs * args.steps / (ms * 1e-3)
+    value = whole_job_value(world, dofs, args.steps, ms)
 
     # per-kernel event timing of the same steps (separate pass) for the roofline
     s.profile_kernels(True)

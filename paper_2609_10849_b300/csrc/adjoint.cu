@@ -119,8 +119,9 @@ int ensure_tapes(mhd_ctx* c, int m) {
   AdjBufs& A = c->adj;
   cudaError_t e = cudaSuccess;
   while ((int)A.tapes.size() < m && e == cudaSuccess) {
-    A.tapes.emplace_back();
-    e = alloc_tape(c, A.tapes.back());
+    StepTape t;
+    e = alloc_tape(c, t);  // buffers already taken stay owned by the context
+    if (e == cudaSuccess) A.tapes.push_back(t);
   }
   if (c->prm.oe_vel)
     for (int i = 0; i < m && e == cudaSuccess; ++i)
