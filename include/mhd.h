@@ -62,11 +62,16 @@ typedef struct {
 } mhd_params_t;
 
 /* Diagnostics (DG-GLL quadrature for the fluid, exact magnetic product for
- * E_mag).  div_B is max_K min(hx,hy) max_{Gauss(k)^2} |dBx/dx + dBy/dy|. */
+ * E_mag).  div_B is max_K min(hx,hy) max_{Gauss(k)^2} |dBx/dx + dBy/dy|.
+ * n_rejections: rejected step attempts since the context was created.
+ * stab_active: which stabilisation maps acted since the previous diagnostics
+ * call (bit 1 a hydro OE factor D_p below 0.99, 2 the limiter scaled or
+ * collapsed an element, 4 a positive A.R. coefficient, 8 a velocity-OE factor
+ * below 0.99); reading clears it. */
 typedef struct {
   double mass, mom[3], E_kin, E_int, E_mag, entropy, div_B, B_max, rho_min, p_min, eta_max;
   int n_rejections;
-  int reserved;
+  int stab_active;
 } mhd_diag_t;
 
 typedef struct mhd_ctx mhd_ctx;

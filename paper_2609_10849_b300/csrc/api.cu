@@ -240,6 +240,7 @@ int mhd_create(const mhd_mesh_t* mesh, int p, int k, double gamma, mhd_ctx** out
     if ((e = cudaMalloc(&ptr, 64)) != cudaSuccess) goto oom;
     c->allocs.push_back(ptr);
     c->status = (unsigned*)ptr;
+    c->prm.activity = c->status + 1;
     c->maxbits = (unsigned long long*)((char*)ptr + 16);
     if ((e = cudaMallocHost(&ptr, 64)) != cudaSuccess) goto oom;
     c->h_pinned = (double*)ptr;
@@ -273,7 +274,7 @@ int mhd_set_params(mhd_ctx* c, const mhd_params_t* prm) {
   if (prm->s_H < 0 || prm->s_M < 0 || prm->C_s < 0 || prm->C_eta < 0 || !(prm->cfl > 0) || prm->max_halvings < 0)
     return fail(MHD_EINVAL, "invalid stabilisation parameters");
   c->prm = Stab{prm->oe_hydro, prm->oe_vel, prm->pp, prm->ar, prm->s_H, prm->s_M, prm->C_s, prm->C_eta, prm->cfl,
-                prm->max_halvings};
+                prm->max_halvings, c->status + 1};
   if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
   return MHD_OK;
 }
@@ -426,6 +427,7 @@ int mhd_strang_step(mhd_ctx* c, double dt, double* dt_taken) {
     }
     cudaMemcpyAsync(c->U, c->Usave, 5 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
     cudaMemcpyAsync(c->B, c->Bsave, 3 * c->Z * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+    c->rejections++;
     dt *= 0.5;
   }
   if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(e, "restore");
@@ -494,6 +496,7 @@ int mhd_strang_steps(mhd_ctx* c, double dt, int nsteps, int* steps_done) {
     cudaMemcpyAsync(c->U, c->Usave, 5 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
     cudaMemcpyAsync(c->B, c->Bsave, 3 * c->Z * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
     cudaStreamSynchronize(c->st);
+    c->rejections++;
     return fail(MHD_INADMISSIBLE, "inadmissible cell average in a fixed-step sequence");
   }
   if (steps_done) *steps_done = nsteps;
@@ -808,6 +811,9 @@ int mhd_diagnostics(mhd_ctx* c, mhd_diag_t* out) {
   std::vector<double> h(12 * K), eta(K);
   cudaError_t e = cudaMemcpyAsync(h.data(), c->work, 12 * K * sizeof(double), cudaMemcpyDeviceToHost, c->st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(eta.data(), c->eta, K * sizeof(double), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_status + 1, c->prm.activity, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->prm.activity, 0, sizeof(unsigned), c->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) return cuda_fail(e, "diagnostics");
   double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1e300, 1e300};
@@ -823,7 +829,9 @@ int mhd_diagnostics(mhd_ctx* c, mhd_diag_t* out) {
   out->mass = acc[0]; out->mom[0] = acc[1]; out->mom[1] = acc[2]; out->mom[2] = acc[3];
   out->E_kin = acc[4]; out->E_int = acc[5]; out->entropy = acc[6]; out->E_mag = 0.5 * acc[7];
   out->div_B = acc[8]; out->B_max = acc[9]; out->rho_min = acc[10]; out->p_min = acc[11];
-  out->eta_max = emax; out->n_rejections = 0; out->reserved = 0;
+  out->eta_max = emax;
+  out->n_rejections = (int)c->rejections;
+  out->stab_active = (int)c->h_status[1];
   return MHD_OK;
 }
 

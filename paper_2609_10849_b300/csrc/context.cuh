@@ -113,6 +113,7 @@ struct mhd_ctx {
   double* h_pinned;  // small pinned host scratch
   unsigned* h_status;
   long long launches;
+  long long rejections;  // rejected step attempts since creation
   std::vector<void*> allocs;
   // optional per-kernel-class event timing (bench instrumentation)
   bool profiling;

@@ -90,7 +90,23 @@ struct Stab {
   int oe_hydro, oe_vel, pp, ar;
   double s_H, s_M, C_s, C_eta, cfl;
   int max_halvings;
+  unsigned* activity;  // device word: which maps acted (ACT_* bits), may be null
 };
+
+// Activity bits of the stabilisation maps (mhd_diag_t.stab_active).
+enum : unsigned {
+  ACT_OE_HYDRO = 1u,  // a hydro OE factor D_p below 0.99
+  ACT_PP = 2u,        // the limiter scaled or collapsed an element
+  ACT_AR = 4u,        // a positive A.R. coefficient
+  ACT_OE_VEL = 8u,    // a velocity-OE factor D_p below 0.99
+};
+
+// OR `bits` of the calling lanes of a warp into *word with one atomic per warp.
+__device__ __forceinline__ void warp_or(unsigned* word, unsigned bits) {
+  const unsigned m = __activemask();
+  const unsigned all = __reduce_or_sync(m, bits);
+  if (word && all && (threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) atomicOr(word, all);
+}
 
 // Scratch of the magnetic-residual adjoint (doubles): mu, s [3N]; LT, LJ, LE
 // [element loads of the magnetic stage]; V [3Z]; LB [closure loads of B].

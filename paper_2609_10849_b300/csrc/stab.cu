@@ -460,6 +460,12 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_oe_pp(double* __restrict__
       }
     }
   }
+  {
+    unsigned act = 0u;
+    if (prm.oe_hydro && sD[el][P] < 0.99) act |= ACT_OE_HYDRO;
+    if (t_rho < 1.0 || t_all < 1.0) act |= ACT_PP;
+    warp_or(prm.activity, act);
+  }
   if (frz && q == 0 && k < M.K) {
     double* f = frz + (size_t)k * (n + 2);
 #pragma unroll
@@ -803,6 +809,7 @@ __global__ void k_ar_eta(const double* __restrict__ ar, const double* __restrict
     e = fmax(e, h / (2.0 * p + 1.0) * a[13 + I] * R);
   }
   eta[k] = prm.C_eta * e;
+  warp_or(prm.activity, prm.C_eta * e > 0.0 ? ACT_AR : 0u);
 }
 
 void stab_eta(int p, int k, const double* rho, const double* Y, const double* B, const Tab* T, const Mesh& M,
@@ -999,6 +1006,7 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_vel_oe(const double* __res
   for (int d = 0; d < 3; ++d) sWu[d][tid] = W * u[d];
   oe_factors<P>(V, 3, q, el, kk, ex, ey, lam, prm.s_M * dtp[0] * dtfac, M, ssig, sD);  // syncs
   if (frz && q < n && k < M.K) frz[(size_t)k * n + q] = sD[el][q];
+  warp_or(prm.activity, sD[el][P] < 0.99 ? ACT_OE_VEL : 0u);
   // coefficients c_alpha = sum_t Psi[t][alpha] W_t u_t (lane q plays alpha)
   if (node) {
 #pragma unroll

@@ -40,7 +40,7 @@ class Diag(C.Structure):
     _fields_ = [("mass", C.c_double), ("mom", C.c_double * 3), ("E_kin", C.c_double), ("E_int", C.c_double),
                 ("E_mag", C.c_double), ("entropy", C.c_double), ("div_B", C.c_double), ("B_max", C.c_double),
                 ("rho_min", C.c_double), ("p_min", C.c_double), ("eta_max", C.c_double),
-                ("n_rejections", C.c_int), ("reserved", C.c_int)]
+                ("n_rejections", C.c_int), ("stab_active", C.c_int)]
 
 
 _lib = None
@@ -327,7 +327,7 @@ class Solver:
         _check(lib().mhd_diagnostics(self._h, C.byref(d)))
         return dict(mass=d.mass, mom_x=d.mom[0], mom_y=d.mom[1], mom_z=d.mom[2], E_kin=d.E_kin, E_int=d.E_int,
                     E_mag=d.E_mag, entropy=d.entropy, div_B=d.div_B, B_max=d.B_max, rho_min=d.rho_min,
-                    p_min=d.p_min, eta_max=d.eta_max)
+                    p_min=d.p_min, eta_max=d.eta_max, n_rejections=d.n_rejections, stab_active=d.stab_active)
 
     def eta(self):
         out = np.zeros(self.K)

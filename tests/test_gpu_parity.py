@@ -298,3 +298,24 @@ def test_full_size_blast_1024_tiled():
     assert abs(d1["mass"] - d0["mass"]) <= 1e-13 * d0["mass"]
     assert d1["div_B"] <= 1e-12 * d1["B_max"]
     assert d1["rho_min"] > 0 and d1["p_min"] > 0
+
+
+def test_diagnostics_activity_and_rejections():
+    """stab_active reports the maps that acted since the previous diagnostics
+    call (and is cleared by reading it); n_rejections counts retried attempts."""
+    wl = workloads.blast()
+    o = oracle_state(wl, 16, 16, 3, 3)
+    s = solver_like(o)
+    s.set_params(cfl=0.4, **STAB)
+    copy_state(o, s)
+    assert s.diagnostics()["stab_active"] == 0
+    dt = o.cfl_dt()
+    for _ in range(2):
+        assert s.strang_step(dt)[0] == 0
+    d = s.diagnostics()
+    assert d["stab_active"] & 1  # the hydro OE damps the blast's jump
+    assert d["n_rejections"] == 0
+    assert s.diagnostics()["stab_active"] == 0
+    st, taken = s.strang_step(200 * dt)  # far beyond the CFL step: rejected and halved
+    assert st == 1 and taken < 200 * dt
+    assert s.diagnostics()["n_rejections"] >= 1
