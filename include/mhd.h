@@ -54,11 +54,17 @@ typedef struct { int nx, ny; double x0, x1, y0, y1; } mhd_mesh_t;
  * oe_hydro / oe_vel: hydro and velocity oscillation elimination; pp: Zhang-Shu
  * positivity limiter; ar: artificial resistivity; s_H, s_M: OE scale factors;
  * C_s, C_eta: A.R. sensor response and strength; cfl: CFL number of the
- * time-step reading; max_halvings: retries of a rejected step. */
+ * time-step reading; max_halvings: retries of a rejected step.
+ * strang_order: 0 (default) the H-M-H composition of eq. strang-composition
+ * and Algorithm 3, Phi_H^{dt/2} Phi_M^{dt} Phi_H^{dt/2}; 1 the M-H-M
+ * composition Phi_M^{dt/2} Phi_H^{dt} Phi_M^{dt/2}, which reproduces the
+ * printed temporal Cauchy differences of the paper's Table 3 digit for digit
+ * (not supported by the adjoint). */
 typedef struct {
   int oe_hydro, oe_vel, pp, ar;
   double s_H, s_M, C_s, C_eta, cfl;
   int max_halvings;
+  int strang_order;
 } mhd_params_t;
 
 /* Diagnostics (DG-GLL quadrature for the fluid, exact magnetic product for
@@ -84,7 +90,7 @@ int mhd_create(const mhd_mesh_t* mesh, int p, int k, double gamma, mhd_ctx** out
 void mhd_destroy(mhd_ctx* ctx);
 
 /* Stabilisation parameters (default: all off, s_H = s_M = 0.02, C_s = 5,
- * C_eta = 0.2, cfl = 0.4, max_halvings = 20). */
+ * C_eta = 0.2, cfl = 0.4, max_halvings = 20, strang_order = 0). */
 int mhd_set_params(mhd_ctx* ctx, const mhd_params_t* prm);
 
 /* Stream on which all work of the context is enqueued (a cudaStream_t). */

@@ -87,6 +87,7 @@ def _load(path):
     L.or_ar_coefficient.argtypes = [C.c_void_p] + [_dp] * 6
     L.or_vel_oe.argtypes = [C.c_void_p] + [_dp] * 6 + [C.c_double]
     L.or_set_frozen.argtypes = [C.c_void_p, C.c_int]
+    L.or_set_strang_order.argtypes = [C.c_void_p, C.c_int]
     return L
 
 
@@ -181,6 +182,10 @@ class Oracle:
                    cfl=0.4, max_halvings=20, ec_faces=0):
         self._L.or_set_params(self._h, oe_hydro, oe_vel, pp, ar, s_H, s_M, C_s, C_eta, cfl,
                             max_halvings, ec_faces)
+
+    def set_strang_order(self, order):
+        """0: H-M-H (eq. strang-composition, Algorithm 3); 1: M-H-M."""
+        self._L.or_set_strang_order(self._h, int(order))
 
     def coords(self, which):
         """Node coordinates: 'dg' [K,n2], 'w' [NY,NX], 'bz' [K,mm^2]."""

@@ -212,6 +212,7 @@ struct Params {
   int max_halvings;
   int ec_faces;  // test hook: entropy-conservative flux on faces instead of LLF
   int frozen;    // tangent build: hold the stabilisation coefficients (D_l, theta, eta) at their values
+  int strang_order;  // 0: H-M-H (eq. strang-composition, Algorithm 3); 1: M-H-M (reading R20)
 };
 
 enum { OR_OK = 0, OR_RETRIED = 1, OR_REJECT = -10, OR_INADMISSIBLE = -11 };
@@ -255,7 +256,7 @@ struct Oracle {
     for (int c = 0; c < 5; ++c) U[c].assign((size_t)K * n2, 0.0);
     Bx.assign((size_t)NX * NY, 0.0); By = Bx; Bz.assign((size_t)K * mm * mm, 0.0);
     eta.assign(K, 0.0);
-    prm = Params{0, 0, 0, 0, 0.02, 0.02, 5.0, 0.0, 0.4, 20, 0, 0};
+    prm = Params{0, 0, 0, 0, 0.02, 0.02, 5.0, 0.0, 0.4, 20, 0, 0, 0};
     last_rejections = 0;
   }
 
@@ -691,9 +692,16 @@ struct Oracle {
     vec B0x = Bx, B0y = By, B0z = Bz;
     last_rejections = 0;
     for (int att = 0; att <= prm.max_halvings; ++att) {
-      int st = hydro_substep(0.5 * dt);
-      if (st == OR_OK) st = run_mag(dt);
-      if (st == OR_OK) st = hydro_substep(0.5 * dt);
+      int st;
+      if (prm.strang_order == 1) {  // Phi_M^{dt/2} o Phi_H^{dt} o Phi_M^{dt/2} (reading R20)
+        st = run_mag(0.5 * dt);
+        if (st == OR_OK) st = hydro_substep(dt);
+        if (st == OR_OK) st = run_mag(0.5 * dt);
+      } else {  // Phi_H^{dt/2} o Phi_M^{dt} o Phi_H^{dt/2}
+        st = hydro_substep(0.5 * dt);
+        if (st == OR_OK) st = run_mag(dt);
+        if (st == OR_OK) st = hydro_substep(0.5 * dt);
+      }
       if (st == OR_OK) {
         if (dt_taken) *dt_taken = dt;
         return att > 0 ? OR_RETRIED : OR_OK;
@@ -841,9 +849,12 @@ void or_destroy(void* h) { delete (Oracle*)h; }
 void or_set_params(void* h, int oe_hydro, int oe_vel, int pp, int ar, double s_H, double s_M, double C_s,
                    double C_eta, double cfl, int max_halvings, int ec_faces) {
   Oracle* o = (Oracle*)h;
-  const int frozen = o->prm.frozen;
-  o->prm = Params{oe_hydro, oe_vel, pp, ar, s_H, s_M, C_s, C_eta, cfl, max_halvings, ec_faces, frozen};
+  const int frozen = o->prm.frozen, order = o->prm.strang_order;
+  o->prm = Params{oe_hydro, oe_vel, pp, ar, s_H, s_M, C_s, C_eta, cfl, max_halvings, ec_faces, frozen, order};
 }
+
+// Ordering of the Strang composition: 0 H-M-H (default), 1 M-H-M (reading R20).
+void or_set_strang_order(void* h, int order) { ((Oracle*)h)->prm.strang_order = order; }
 
 // Tangent build: hold the stabilisation coefficients at their forward values
 // (the linearisation that the library's adjoint differentiates).

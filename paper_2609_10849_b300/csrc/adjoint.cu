@@ -307,6 +307,7 @@ long long mhd_state_size(const mhd_ctx* c) { return c ? (long long)(5 * c->N + 3
 static int adjoint_begin(mhd_ctx* c, double dt, int* flags) {
   const int fl = stab_flags(c);
   if (flags) *flags = fl;
+  if (c->prm.strang_order != 0) return afail(MHD_EINVAL, "the adjoint differentiates the H-M-H step");
   if (fl & ~kFrozenSupported) return afail(MHD_EINVAL, "unsupported stabilisation map");
   if (!(dt > 0.0)) return afail(MHD_EINVAL, "dt must be positive");
   return ensure_adjoint(c);

@@ -148,7 +148,15 @@ void mag_substep(mhd_ctx* c, double fac) {
   c->launches++;
 }
 
+// One Strang step (Algorithm 3, eq. strang-composition): H-M-H, or the
+// M-H-M ordering when requested.
 void enqueue_strang(mhd_ctx* c) {
+  if (c->prm.strang_order == 1) {
+    mag_substep(c, 0.5);
+    hydro_substep(c, 1.0);
+    mag_substep(c, 0.5);
+    return;
+  }
   hydro_substep(c, 0.5);
   mag_substep(c, 1.0);
   hydro_substep(c, 0.5);
@@ -271,10 +279,11 @@ void mhd_destroy(mhd_ctx* c) {
 
 int mhd_set_params(mhd_ctx* c, const mhd_params_t* prm) {
   if (!c || !prm) return fail(MHD_EINVAL, "null argument");
-  if (prm->s_H < 0 || prm->s_M < 0 || prm->C_s < 0 || prm->C_eta < 0 || !(prm->cfl > 0) || prm->max_halvings < 0)
+  if (prm->s_H < 0 || prm->s_M < 0 || prm->C_s < 0 || prm->C_eta < 0 || !(prm->cfl > 0) || prm->max_halvings < 0 ||
+      (prm->strang_order != 0 && prm->strang_order != 1))
     return fail(MHD_EINVAL, "invalid stabilisation parameters");
   c->prm = Stab{prm->oe_hydro, prm->oe_vel, prm->pp, prm->ar, prm->s_H, prm->s_M, prm->C_s, prm->C_eta, prm->cfl,
-                prm->max_halvings, c->status + 1};
+                prm->max_halvings, c->status + 1, prm->strang_order};
   if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
   return MHD_OK;
 }

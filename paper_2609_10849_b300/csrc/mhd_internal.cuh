@@ -91,6 +91,7 @@ struct Stab {
   double s_H, s_M, C_s, C_eta, cfl;
   int max_halvings;
   unsigned* activity;  // device word: which maps acted (ACT_* bits), may be null
+  int strang_order;    // 0: H-M-H (Algorithm 3), 1: M-H-M
 };
 
 // Activity bits of the stabilisation maps (mhd_diag_t.stab_active).

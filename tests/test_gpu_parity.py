@@ -319,3 +319,19 @@ def test_diagnostics_activity_and_rejections():
     st, taken = s.strang_step(200 * dt)  # far beyond the CFL step: rejected and halved
     assert st == 1 and taken < 200 * dt
     assert s.diagnostics()["n_rejections"] >= 1
+
+
+@pytest.mark.parametrize("pk", [(1, 1), (2, 2), (3, 3), (4, 4)])
+def test_strang_mhm_order_parity(pk):
+    """The M-H-M composition (reading R20), every stabilisation map on: per-step
+    parity with the oracle's M-H-M step."""
+    o, s = stab_pair(workloads.orszag_tang(), 8, 8, *pk)
+    o.set_strang_order(1)
+    s.set_params(strang_order=1)
+    for _ in range(2):
+        dt = o.cfl_dt()
+        st_o, taken_o, _ = o.strang_step(dt)
+        st_g, taken_g = s.strang_step(dt)
+        assert st_o == 0 and st_g == 0 and taken_g == taken_o
+        compare_state(o, s, 1e-12)
+        copy_state(o, s)
