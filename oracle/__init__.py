@@ -80,6 +80,7 @@ def _load(path):
     L.or_div_metric.argtypes = [C.c_void_p]
     L.or_div_metric.restype = C.c_double
     L.or_get_eta.argtypes = [C.c_void_p, _dp]
+    L.or_set_eta.argtypes = [C.c_void_p, _dp]
     L.or_diagnostics.argtypes = [C.c_void_p, _dp]
     L.or_sample.argtypes = [C.c_void_p, C.c_int, C.c_int, _dp, _dp, _dp, _dp]
     L.or_hydro_stage_map.argtypes = [C.c_void_p, _dp, C.c_double]
@@ -296,6 +297,10 @@ class Oracle:
         out = np.zeros(self.K)
         self._L.or_get_eta(self._h, out)
         return out
+
+    def set_eta(self, eta):
+        """Set the element resistivity that :meth:`sample` uses for E_h."""
+        self._L.or_set_eta(self._h, np.ascontiguousarray(eta, dtype=np.float64))
 
     def diagnostics(self):
         out = np.zeros(13)

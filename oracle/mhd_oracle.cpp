@@ -992,6 +992,13 @@ void or_get_eta(void* h, double* out) {
   to_host(out, o->eta);
 }
 
+// Element resistivity used by or_sample's E_h (normally the one the last
+// magnetic substep computed); an input here, e.g. taken from another solver.
+void or_set_eta(void* h, const double* in) {
+  Oracle* o = (Oracle*)h;
+  o->eta = from_host(in, (size_t)o->K);
+}
+
 // Diagnostics: [mass, mom_x, mom_y, mom_z, E_kin, E_int, E_mag, entropy S_h,
 // div metric, max|B|, rho_min, p_min, eta_max].
 void or_diagnostics(void* h, double* out) {
