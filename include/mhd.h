@@ -135,8 +135,7 @@ int mhd_strang_step(mhd_ctx* ctx, double dt, double* dt_taken);
  * start of the sequence and MHD_INADMISSIBLE is returned with *steps_done = 0. */
 int mhd_strang_steps(mhd_ctx* ctx, double dt, int nsteps, int* steps_done);
 
-/* Batches of independent runs (spec batching pattern; the paper has no
- * counterpart): every run has its own context (mesh, p, k, gamma, parameters
+/* Batches of independent runs (the paper has no counterpart): every run has its own context (mesh, p, k, gamma, parameters
  * and state) and stream.  mhd_batch_step advances every run by nsteps Strang
  * steps with its own fixed dt (dt[i]) as ONE CUDA-graph launch holding a
  * parallel branch per run, then checks every run's status once.  The graph
@@ -157,7 +156,7 @@ int mhd_batch_step(mhd_batch* batch, const double* dt, int nsteps, int* status);
 /* Kernel launches enqueued by the batch and its runs since creation. */
 long long mhd_batch_launch_count(const mhd_batch* batch);
 
-/* Tile autotuner (spec batching pattern; the paper has none): times the
+/* Tile autotuner (batching of independent problems; the paper has none): times the
  * elements-per-CTA variants of the volume kernel and of the magnetic-stage
  * kernels on the context's own mesh and CURRENT state (set a state first) and
  * keeps the fastest for every later launch (cached graphs are re-captured).
@@ -184,7 +183,7 @@ int mhd_mag_rhs(mhd_ctx* ctx, const double* rho, const double* e, const double* 
                 const double* By, const double* Bz, const double* eta, double* de, double* du, double* dBx,
                 double* dBy, double* dBz, int on_device);
 
-/* ---- Adjoint (spec differentiation pattern; the paper has none) ----
+/* ---- Adjoint (differentiation of the step; the paper has none) ----
  * Packed state vector of a context: [U 5N | Bx G | By G | Bz Z] in the host
  * layouts above (G = Z); its length is mhd_state_size().  An adjoint vector
  * lam has the same packing and holds dJ/d(state) of a scalar objective J. */

@@ -8,7 +8,7 @@
 // carries the derivative).  Reverse mode is written out by hand below, one
 // adjoint statement per forward statement in reverse order.  Only the
 // unstabilised residual is differentiated: the OE map and the limiter are
-// outside the adjoint (the driver flags them when they are on).
+// outside this residual adjoint (the step adjoint reports them in its flags).
 #include "mhd_internal.cuh"
 
 namespace mhd {

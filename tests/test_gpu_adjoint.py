@@ -13,7 +13,7 @@ differences of the CUDA forward.
 
 Tolerances: Jacobian entries 1e-11 of the largest entry; dot products 1e-12 of
 sum |lam_i (J dx)_i| (both sides are exact up to rounding); finite differences
-1e-6 relative (the spec bar for the adjoint).
+1e-6 relative (the accuracy bar of the adjoint).
 """
 import numpy as np
 import pytest

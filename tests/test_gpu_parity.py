@@ -1,7 +1,7 @@
 """GPU <-> oracle parity of the CUDA path, called through the C ABI.
 
 Tolerance: 1e-12 relative max-norm per step (1e-9 after 100 steps), the
-spec bar for FP64 parity; per-kernel residuals are held to the same
+parity bar of the FP64 path; per-kernel residuals are held to the same
 1e-12 relative to the largest residual entry.
 """
 import numpy as np
