@@ -118,6 +118,22 @@ int mhd_set_primitive(mhd_ctx* ctx, const double* rho, const double* u, const do
 int mhd_set_B_from_potential(mhd_ctx* ctx, const double* Az, double Bx0, double By0, const double* Bz,
                              int on_device);
 
+/* Physical coordinates of the nq x nq Gauss-Legendre points of every element
+ * into host buffers X, Y [K][nq][nq] (x fastest, element K = ey*nx + ex),
+ * 1 <= nq <= 16.  These are the points at which mhd_set_Bz_projected takes
+ * its data. */
+int mhd_quad_coords(const mhd_ctx* ctx, int nq, double* X, double* Y);
+
+/* Out-of-plane field B_z set to the element-wise L2 projection onto V_h^k
+ * (Q^k in the GLL(k) nodal basis of §3.1.3) of values fq [K][nq][nq] given at
+ * the points of mhd_quad_coords (host or device memory per on_device).  The
+ * element mass is exact for nq >= k+1; the data integral uses the nq-point
+ * rule, exact when the data are polynomials of degree <= 2 nq - 1 - k.  The
+ * paper does not state its initial B_z; this projection reproduces its
+ * Table 1 (§4.1).  k+1 <= nq <= 16, else MHD_EINVAL.  The in-plane field and
+ * the fluid state are unchanged. */
+int mhd_set_Bz_projected(mhd_ctx* ctx, const double* fq, int nq, int on_device);
+
 /* CFL time step of the current state (written to *dt). */
 int mhd_compute_dt(mhd_ctx* ctx, double* dt);
 

@@ -83,6 +83,8 @@ def _load(path):
     L.or_set_eta.argtypes = [C.c_void_p, _dp]
     L.or_diagnostics.argtypes = [C.c_void_p, _dp]
     L.or_sample.argtypes = [C.c_void_p, C.c_int, C.c_int, _dp, _dp, _dp, _dp]
+    L.or_quad_coords.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
+    L.or_project_Bz.argtypes = [C.c_void_p, _dp, C.c_int]
     L.or_hydro_stage_map.argtypes = [C.c_void_p, _dp, C.c_double]
     L.or_oe_sensor.argtypes = [C.c_void_p, _dp, C.c_int, _dp]
     L.or_ar_coefficient.argtypes = [C.c_void_p] + [_dp] * 6
@@ -311,6 +313,17 @@ class Oracle:
 
     FIELDS = {"rho": 0, "mx": 1, "my": 2, "mz": 3, "E": 4, "ux": 5, "uy": 6, "uz": 7, "p": 8,
               "Bx": 9, "By": 10, "Bz": 11, "Ex": 12, "Ey": 13, "Ez": 14, "Jx": 15, "Jy": 16, "Jz": 17}
+
+    def quad_coords(self, nq):
+        """Coordinates of the nq x nq Gauss points of every element, [K*nq*nq]."""
+        X, Y = np.zeros(self.K * nq * nq), np.zeros(self.K * nq * nq)
+        self._L.or_quad_coords(self._h, nq, X, Y)
+        return X, Y
+
+    def project_Bz(self, fq, nq):
+        """Set B_z to the L2 projection onto V_h^m of values at the points of
+        :meth:`quad_coords` (the rest of the state is unchanged)."""
+        self._L.or_project_Bz(self._h, np.ascontiguousarray(fq, dtype=np.float64).ravel(), nq)
 
     def sample(self, field, nq):
         """Values of a field at nq x nq Gauss points per element, with coordinates and weights."""

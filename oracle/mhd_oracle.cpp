@@ -1028,6 +1028,73 @@ void or_diagnostics(void* h, double* out) {
   for (int i = 0; i < 13; ++i) out[i] = val(r[i]);
 }
 
+// Physical coordinates of the nq x nq Gauss-Legendre points of every element,
+// [K][qy][qx] with K = ey*nx + ex (the layout of or_sample).
+void or_quad_coords(void* h, int nq, double* X, double* Y) {
+  Oracle* o = (Oracle*)h;
+  vec zq, wq; gauss_rule(nq, zq, wq);
+  size_t idx = 0;
+  for (int ey = 0; ey < o->ny; ++ey)
+    for (int ex = 0; ex < o->nx; ++ex)
+      for (int qy = 0; qy < nq; ++qy)
+        for (int qx = 0; qx < nq; ++qx, ++idx) {
+          X[idx] = val(o->x0 + ex * o->hx + (1.0 + zq[qx]) * o->hx / 2.0);
+          Y[idx] = val(o->y0 + ey * o->hy + (1.0 + zq[qy]) * o->hy / 2.0);
+        }
+}
+
+// Initial out-of-plane field as the L2(K) projection onto V_h^m (Q^m in the
+// GLL(m) nodal basis of §3.1.3) of data given at the nq x nq Gauss points of
+// every element (layout of or_quad_coords).  The paper does not state its
+// initial B_z; this projection is the reading under which its Table 1 is
+// reproduced.  For each element the (m+1)^2 normal equations
+//   sum_b c_b (phi_b, phi_a)_K = (f, phi_a)_K  for every basis function a
+// are assembled with the nq-point tensor rule (exact for the mass when
+// nq >= m+1) and solved by Gaussian elimination with partial pivoting.
+void or_project_Bz(void* h, const double* fq, int nq) {
+  Oracle* o = (Oracle*)h;
+  vec zq, wq; gauss_rule(nq, zq, wq);
+  const int mm = o->mm, nb = mm * mm;
+  std::vector<real> A((size_t)nb * nb), r(nb), phi((size_t)nb * nq * nq);
+  for (int b = 0; b < nb; ++b)  // basis function b = (bx, by) at every point
+    for (int qy = 0; qy < nq; ++qy)
+      for (int qx = 0; qx < nq; ++qx)
+        phi[((size_t)b * nq + qy) * nq + qx] = lag(o->xM, b % mm, zq[qx]) * lag(o->xM, b / mm, zq[qy]);
+  for (int k = 0; k < o->K; ++k) {
+    const double* f = fq + (size_t)k * nq * nq;
+    for (int a = 0; a < nb; ++a) {
+      r[a] = 0.0;
+      for (int b = 0; b < nb; ++b) A[(size_t)a * nb + b] = 0.0;
+      for (int qy = 0; qy < nq; ++qy)
+        for (int qx = 0; qx < nq; ++qx) {
+          real w = o->Jdet * wq[qx] * wq[qy];
+          real pa = phi[((size_t)a * nq + qy) * nq + qx];
+          r[a] += w * f[qy * nq + qx] * pa;
+          for (int b = 0; b < nb; ++b) A[(size_t)a * nb + b] += w * pa * phi[((size_t)b * nq + qy) * nq + qx];
+        }
+    }
+    for (int col = 0; col < nb; ++col) {  // forward elimination
+      int piv = col;
+      for (int i = col + 1; i < nb; ++i)
+        if (fabs(A[(size_t)i * nb + col]) > fabs(A[(size_t)piv * nb + col])) piv = i;
+      if (piv != col) {
+        for (int j = 0; j < nb; ++j) std::swap(A[(size_t)col * nb + j], A[(size_t)piv * nb + j]);
+        std::swap(r[col], r[piv]);
+      }
+      for (int i = col + 1; i < nb; ++i) {
+        real l = A[(size_t)i * nb + col] / A[(size_t)col * nb + col];
+        for (int j = col; j < nb; ++j) A[(size_t)i * nb + j] -= l * A[(size_t)col * nb + j];
+        r[i] -= l * r[col];
+      }
+    }
+    for (int i = nb - 1; i >= 0; --i) {  // back substitution
+      real sum = r[i];
+      for (int j = i + 1; j < nb; ++j) sum -= A[(size_t)i * nb + j] * o->Bz[(size_t)k * nb + j];
+      o->Bz[(size_t)k * nb + i] = sum / A[(size_t)i * nb + i];
+    }
+  }
+}
+
 // Sample a field at the nq x nq Gauss points of every element (for L2 errors).
 // field: 0..4 conserved, 5..7 u, 8 p, 9..11 B, 12..14 E_h, 15..17 J_h
 // (E_h with the element resistivity of the last magnetic substep).

@@ -401,6 +401,48 @@ int mhd_set_B_from_potential(mhd_ctx* c, const double* Az, double Bx0, double By
   return MHD_OK;
 }
 
+int mhd_quad_coords(const mhd_ctx* c, int nq, double* X, double* Y) {
+  if (!c || !X || !Y) return fail(MHD_EINVAL, "null argument");
+  if (nq < 1 || nq > MHD_QMAX) return fail(MHD_EINVAL, "nq must be in [1, 16]");
+  double z[MHD_QMAX];
+  gauss_points(nq, z);
+  const int nx = c->M.nx, ny = c->M.ny;
+  for (int ey = 0; ey < ny; ++ey)
+    for (int ex = 0; ex < nx; ++ex) {
+      double xl = c->x0 + ex * c->M.hx, yl = c->y0 + ey * c->M.hy;
+      size_t base = ((size_t)ey * nx + ex) * nq * nq;
+      for (int qy = 0; qy < nq; ++qy)
+        for (int qx = 0; qx < nq; ++qx) {
+          X[base + qy * nq + qx] = xl + 0.5 * (1.0 + z[qx]) * c->M.hx;
+          Y[base + qy * nq + qx] = yl + 0.5 * (1.0 + z[qy]) * c->M.hy;
+        }
+    }
+  return MHD_OK;
+}
+
+int mhd_set_Bz_projected(mhd_ctx* c, const double* fq, int nq, int on_device) {
+  if (!c || !fq) return fail(MHD_EINVAL, "null argument");
+  if (nq < c->k + 1 || nq > MHD_QMAX) return fail(MHD_EINVAL, "nq must be in [k+1, 16]");
+  const size_t n = (size_t)c->M.K * nq * nq;
+  cudaError_t e;
+  double* tmp = nullptr;
+  const double* src = fq;
+  if (!on_device) {
+    if ((e = cudaMalloc(&tmp, n * sizeof(double))) != cudaSuccess) return cuda_fail(e, "B_z data");
+    if ((e = copy_in(c, tmp, fq, n, 0)) != cudaSuccess) {
+      cudaFree(tmp);
+      return cuda_fail(e, "B_z data");
+    }
+    src = tmp;
+  }
+  l2_project(c->k, nq, src, c->B + 2 * c->Z, (size_t)c->M.K, c->st);
+  c->launches++;
+  e = cudaStreamSynchronize(c->st);
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) return cuda_fail(e, "set_Bz_projected");
+  return MHD_OK;
+}
+
 int mhd_compute_dt(mhd_ctx* c, double* dt) {
   if (!c || !dt) return fail(MHD_EINVAL, "null argument");
   cfl_dt(c->p, c->k, c->U, c->B, c->T, c->M, c->maxbits, c->prm.cfl, c->dt, c->st);

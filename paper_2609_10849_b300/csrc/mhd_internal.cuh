@@ -18,6 +18,7 @@
 
 #define MHD_NMAX 5  // p + 1 <= 5 and k + 1 <= 5
 #define MHD_LMAX 6  // k + 2 <= 6
+#define MHD_QMAX 16  // points per direction of element data given at Gauss points
 
 namespace mhd {
 
@@ -66,6 +67,8 @@ struct Tab {
 int table_slot(int p, int k);
 const Tab* device_tables(int p, int k, cudaError_t* err);  // uploads once per device
 void host_tables(int p, int k, Tab* out);
+void gauss_points(int nq, double* z);
+void l2_projection_table(int k, int nq, double* P);
 
 struct Mesh {
   int nx, ny, K;

@@ -113,6 +113,35 @@ void b_from_potential(int k, const double* A, double Bx0, double By0, double* Bx
   }
 }
 
+// Element-wise L2 projection onto Q^k of data at the nq x nq Gauss points:
+// C[b][a] = sum_{j,i} P[b][j] P[a][i] F[j][i], one thread per output node.
+struct ProjTab {
+  double P[MHD_NMAX * MHD_QMAX];
+};
+
+__global__ void k_l2_project(const double* __restrict__ fq, int nq, int mm, ProjTab T, double* __restrict__ out,
+                             size_t K) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= K * mm * mm) return;
+  size_t k = t / (mm * mm);
+  int r = (int)(t % (mm * mm)), b = r / mm, a = r % mm;
+  const double* F = fq + k * nq * nq;
+  double c = 0.0;
+  for (int j = 0; j < nq; ++j) {
+    double row = 0.0;
+    for (int i = 0; i < nq; ++i) row = fma(T.P[a * nq + i], F[j * nq + i], row);
+    c = fma(T.P[b * nq + j], row, c);
+  }
+  out[t] = c;
+}
+
+void l2_project(int k, int nq, const double* fq, double* out, size_t K, cudaStream_t st) {
+  ProjTab T;
+  l2_projection_table(k, nq, T.P);
+  size_t tot = K * (k + 1) * (k + 1);
+  k_l2_project<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(fq, nq, k + 1, T, out, K);
+}
+
 // B_h of element k at its DG node (i, j) (tensor interpolation of the closures).
 template <int P, int KM>
 __device__ void B_at_dg(const double* __restrict__ B, size_t Z, const Tab* __restrict__ T, const Mesh& M, int k, int i,

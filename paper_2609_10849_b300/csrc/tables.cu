@@ -146,6 +146,48 @@ void fill_interp(double (&T)[R][C], int npts, const ld* pts, int nb, const ld* n
 
 }  // namespace
 
+void gauss_points(int nq, double* z) {
+  ld x[MHD_QMAX], w[MHD_QMAX];
+  gauss_ld(nq, x, w);
+  for (int i = 0; i < nq; ++i) z[i] = (double)x[i];
+}
+
+// One-dimensional factor of the L2(K) projection onto Q^k (GLL(k) nodal basis)
+// from values at the nq-point Gauss rule: P = M^{-1} L^T W with
+// L[g][a] = l_a(zeta_g), W = diag(varpi_g) and M = L^T W L, exact for
+// nq >= k + 1.  On a rectangle the element projection of data F[qy][qx] is
+// C = P F P^T (the Jacobian cancels).  P is row-major [k+1][nq].
+void l2_projection_table(int k, int nq, double* P) {
+  const int mm = k + 1;
+  ld zq[MHD_QMAX], wq[MHD_QMAX], xM[MHD_NMAX], wM[MHD_NMAX], L[MHD_QMAX][MHD_LMAX + 2];
+  gauss_ld(nq, zq, wq);
+  gll_ld(k, xM, wM);
+  for (int g = 0; g < nq; ++g) lagrange_values(mm, xM, zq[g], L[g]);
+  ld A[MHD_NMAX][2 * MHD_NMAX];  // [M | I] -> [I | M^{-1}] by Gauss-Jordan
+  for (int a = 0; a < mm; ++a)
+    for (int b = 0; b < mm; ++b) {
+      ld s = 0.0L;
+      for (int g = 0; g < nq; ++g) s += wq[g] * L[g][a] * L[g][b];
+      A[a][b] = s;
+      A[a][mm + b] = (a == b) ? 1.0L : 0.0L;
+    }
+  for (int c = 0; c < mm; ++c) {  // M is symmetric positive definite: no pivoting
+    ld d = A[c][c];
+    for (int j = 0; j < 2 * mm; ++j) A[c][j] /= d;
+    for (int r = 0; r < mm; ++r)
+      if (r != c) {
+        ld f = A[r][c];
+        for (int j = 0; j < 2 * mm; ++j) A[r][j] -= f * A[c][j];
+      }
+  }
+  for (int a = 0; a < mm; ++a)
+    for (int g = 0; g < nq; ++g) {
+      ld s = 0.0L;
+      for (int b = 0; b < mm; ++b) s += A[a][mm + b] * L[g][b];
+      P[a * nq + g] = (double)(s * wq[g]);
+    }
+}
+
 void host_tables(int p, int k, Tab* T) {
   std::memset(T, 0, sizeof(Tab));
   const int n = p + 1, mm = k + 1, mL = k + 2;

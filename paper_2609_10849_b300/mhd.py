@@ -57,6 +57,8 @@ _SIGS = {
     "mhd_get_state": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int]),
     "mhd_set_primitive": (C.c_int, [C.c_void_p] + [C.c_void_p] * 3 + [C.c_int]),
     "mhd_set_B_from_potential": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_int]),
+    "mhd_quad_coords": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "mhd_set_Bz_projected": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "mhd_compute_dt": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "mhd_strang_step": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_double)]),
     "mhd_strang_steps": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int)]),
@@ -215,6 +217,18 @@ class Solver:
     def set_B_from_potential(self, Az, Bx0, By0, Bz):
         (a, z), dev = _ptrs(Az, Bz)
         _check(lib().mhd_set_B_from_potential(self._h, a, float(Bx0), float(By0), z, dev))
+
+    def quad_coords(self, nq):
+        """Coordinates of the nq x nq Gauss points of every element, [K*nq*nq]."""
+        size = self.K * nq * nq
+        X, Y = np.zeros(size), np.zeros(size)
+        _check(lib().mhd_quad_coords(self._h, int(nq), _ptr(X)[0], _ptr(Y)[0]))
+        return X, Y
+
+    def set_Bz_projected(self, fq, nq):
+        """B_z as the L2 projection onto V_h^k of values at :meth:`quad_coords`."""
+        (a,), dev = _ptrs(fq)
+        _check(lib().mhd_set_Bz_projected(self._h, a, int(nq), dev))
 
     def compute_dt(self):
         dt = C.c_double()

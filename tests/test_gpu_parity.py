@@ -119,6 +119,33 @@ def test_potential_field_and_coords():
     assert rel(Bxg, Bxo) <= 1e-13 and rel(Byg, Byo) <= 1e-13
 
 
+@pytest.mark.parametrize("pk", PK)
+@pytest.mark.parametrize("nq", [None, 16])
+def test_bz_projection(pk, nq):
+    """Initial B_z as the L2 projection onto V_h^k (reading R10): the GPU's
+    tensor-factored projection against the oracle's element normal equations,
+    with the Gauss points of both sides."""
+    from paper_2609_10849_b300.mhd import Solver
+    p, k = pk
+    nq = k + 3 if nq is None else nq
+    wl = workloads.alfven_diagonal()
+    o = oracle_state(wl, 5, 3, p, k)
+    s = Solver(5, 3, p, k, wl["gamma"], wl["domain"])
+    copy_state(o, s)
+    Xo, Yo = o.quad_coords(nq)
+    Xg, Yg = s.quad_coords(nq)
+    assert np.abs(Xo - Xg).max() < 1e-14 and np.abs(Yo - Yg).max() < 1e-14
+    f = np.sin(1.3 * Xg - 0.7) * np.cos(0.9 * Yg) + 0.1 * Xg
+    o.project_Bz(f, nq)
+    s.set_Bz_projected(f, nq)
+    compare_state(o, s, 1e-13)
+    import torch  # device input
+    s.set_state(*o.get_state())
+    s.set_Bz_projected(torch.tensor(2.0 * f, device="cuda"), nq)
+    o.project_Bz(2.0 * f, nq)
+    compare_state(o, s, 1e-13)
+
+
 def test_strang_alfven_per_step():
     """Config 1 (circularly polarised Alfven wave, 16 x 16, p = k = 3): 1e-12 per step."""
     wl = workloads.alfven_rotated()
