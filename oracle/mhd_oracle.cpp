@@ -734,7 +734,7 @@ struct Oracle {
             real B[3]; B_at_dg(ex, ey, i, j, B);
             real rho = Ui[0], pr = pressure(Ui, g);
             real cf = sqrt((g * pr + B[0] * B[0] + B[1] * B[1] + B[2] * B[2]) / rho);
-            real r = (2.0 * p + 1.0) * ((fabs(Ui[1] / rho) + cf) / hx + (fabs(Ui[2] / rho) + cf) / hy);
+            real r = (2.0 * p + 1.0) * std::max((fabs(Ui[1] / rho) + cf) / hx, (fabs(Ui[2] / rho) + cf) / hy);
             mx = std::max(mx, r);
           }
       }

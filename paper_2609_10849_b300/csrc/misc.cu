@@ -195,7 +195,7 @@ __global__ void k_cfl(const double* __restrict__ U, const double* __restrict__ B
     double ux = U[N + t] * ir, uy = U[2 * N + t] * ir, uz = U[3 * N + t] * ir;
     double pr = (M.g - 1.0) * (U[4 * N + t] - 0.5 * rho * (ux * ux + uy * uy + uz * uz));
     double cf = sqrt((M.g * pr + Bv[0] * Bv[0] + Bv[1] * Bv[1] + Bv[2] * Bv[2]) * ir);
-    rate = (2.0 * P + 1.0) * ((fabs(ux) + cf) / M.hx + (fabs(uy) + cf) / M.hy);
+    rate = (2.0 * P + 1.0) * fmax((fabs(ux) + cf) / M.hx, (fabs(uy) + cf) / M.hy);
     if (!(rate >= 0.0)) rate = __longlong_as_double(0x7ff0000000000000ULL);  // non-finite -> +inf
   }
   unsigned long long bits = (unsigned long long)__double_as_longlong(rate);

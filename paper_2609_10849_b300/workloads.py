@@ -155,6 +155,66 @@ def blast(gamma=1.4, p_in=1000.0, p_out=0.1, r0=0.1, B=100.0):
     return dict(name="blast", fields=fields, Az=Az, B0=(b, b), domain=(-0.5, 0.5, -0.5, 0.5), gamma=gamma)
 
 
+def orszag_tang_2pi(gamma=5.0 / 3.0):
+    """Orszag-Tang vortex of §4.4 on the periodic [0, 2 pi]^2: rho = gamma^2,
+    p = gamma, u = (-sin y, sin x, 0), B = (-sin y, sin 2x, 0) = curl(A e_z)
+    with A = cos y + cos(2x)/2; ``Az`` is the potential of the library's
+    grad-perp convention B = (-dAz/dy, dAz/dx), i.e. Az = -A."""
+    def fields(x, y):
+        one = np.ones_like(x)
+        return gamma * gamma * one, -np.sin(y), np.sin(x), 0.0 * one, gamma * one, 0.0 * one
+
+    def Az(x, y):
+        return -(np.cos(y) + 0.5 * np.cos(2.0 * x))
+
+    return dict(name="orszag_tang_2pi", fields=fields, Az=Az, B0=(0.0, 0.0),
+                domain=(0.0, 2 * math.pi, 0.0, 2 * math.pi), gamma=gamma)
+
+
+def blast_oblique(gamma=5.0 / 3.0, p_in=10.0, p_out=0.1, r0=0.1):
+    """Oblique MHD blast wave of §4.6 on the periodic [0, 1]^2: rho = 1, u = 0,
+    B = (cos pi/4, sin pi/4, 0), p = p_in in the disk of radius r0 about
+    (1/2, 1/2) and p_out outside it."""
+    def fields(x, y):
+        one = np.ones_like(x)
+        r = np.sqrt((x - 0.5) ** 2 + (y - 0.5) ** 2)
+        return one, 0.0 * one, 0.0 * one, 0.0 * one, np.where(r < r0, p_in, p_out), 0.0 * one
+
+    def Az(x, y):
+        return 0.0 * x
+
+    c = math.cos(math.pi / 4)
+    return dict(name="blast_oblique", fields=fields, Az=Az, B0=(c, c), domain=(0.0, 1.0, 0.0, 1.0), gamma=gamma)
+
+
+def field_loop(A0=1e-3, R=0.3, u=(2.0, 1.0), gamma=5.0 / 3.0):
+    """Weak-field loop of §4.3 on the periodic [-1, 1] x [-1/2, 1/2]: rho = p = 1,
+    u = (2, 1, 0), B = curl(A e_z) with A = A0 max(R - r, 0) (``Az`` = -A in
+    the library's convention B = (-dAz/dy, dAz/dx)).  ``exact_B`` is the loop
+    translated by u t (periodically): |B| = A0 inside r < R."""
+    Lx, Ly = 2.0, 1.0
+
+    def fields(x, y):
+        one = np.ones_like(x)
+        return one, u[0] * one, u[1] * one, 0.0 * one, one, 0.0 * one
+
+    def Az(x, y):
+        return -A0 * np.maximum(R - np.sqrt(x * x + y * y), 0.0)
+
+    def exact_B(x, y, t=0.0):
+        xd = x - u[0] * t
+        yd = y - u[1] * t
+        xd = xd - Lx * np.round(xd / Lx)
+        yd = yd - Ly * np.round(yd / Ly)
+        r = np.sqrt(xd * xd + yd * yd)
+        inside = (r < R) & (r > 0)
+        rs = np.where(r > 0, r, 1.0)
+        return np.where(inside, -A0 * yd / rs, 0.0), np.where(inside, A0 * xd / rs, 0.0), 0.0 * x
+
+    return dict(name="field_loop", fields=fields, Az=Az, B0=(0.0, 0.0), domain=(-1.0, 1.0, -0.5, 0.5),
+                gamma=gamma, exact_B=exact_B, A0=A0)
+
+
 def balsara_vortex(L=5.0, gamma=5.0 / 3.0, ubar=(1.0, 1.0)):
     """Isodensity MHD vortex (§4.2) on the periodic box [-L, L]^2 with
     minimum-image displacement: rho = 1, u = ubar + g/(2 pi)(-y, x),
