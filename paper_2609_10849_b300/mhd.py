@@ -187,8 +187,11 @@ class Solver:
             pass
 
     def set_params(self, **kw):
-        self.params.update(kw)
-        _check(lib().mhd_set_params(self._h, C.byref(Params(**self.params))))
+        """Update stabilisation / stepping parameters; on MHD_EINVAL the previous
+        parameters stay in force (here and in the library)."""
+        new = dict(self.params, **kw)
+        _check(lib().mhd_set_params(self._h, C.byref(Params(**new))))
+        self.params = new
 
     def set_stream(self, stream_ptr: int):
         _check(lib().mhd_set_stream(self._h, C.c_void_p(stream_ptr)))

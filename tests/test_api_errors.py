@@ -1,0 +1,111 @@
+"""Error behaviour of the C ABI as the header states it: invalid arguments are
+refused with MHD_EINVAL and a message (mhd_last_error), nothing is changed,
+and a context stays usable after a refused call.
+
+The creation checks run on the CPU: mhd_create and mhd_batch_create validate
+their arguments before any CUDA call.  The rest need a context (a GPU).
+"""
+import numpy as np
+import pytest
+
+from paper_2609_10849_b300 import workloads
+from paper_2609_10849_b300.mhd import MhdError, Solver
+
+MHD_EINVAL = -1
+
+
+@pytest.mark.parametrize("args,msg", [
+    ((0, 4, 2, 2, 5 / 3), "invalid mesh"),
+    ((4, 0, 2, 2, 5 / 3), "invalid mesh"),
+    ((4, 4, 0, 0, 5 / 3), "unsupported"),
+    ((4, 4, 5, 5, 5 / 3), "unsupported"),
+    ((4, 4, 3, 1, 5 / 3), "unsupported"),
+    ((4, 4, 2, 3, 5 / 3), "unsupported"),
+    ((4, 4, 2, 2, 1.0), "gamma"),
+    ((4, 4, 2, 2, float("nan")), "gamma"),
+    ((40000, 40000, 1, 1, 5 / 3), "too large"),
+])
+def test_create_rejects(args, msg):
+    with pytest.raises(MhdError, match=msg) as e:
+        Solver(*args)
+    assert e.value.code == MHD_EINVAL
+
+
+@pytest.mark.parametrize("domain", [(1.0, 1.0, 0.0, 1.0), (0.0, 1.0, 0.5, -0.5)])
+def test_create_rejects_empty_domain(domain):
+    with pytest.raises(MhdError, match="invalid mesh"):
+        Solver(4, 4, 2, 2, 5 / 3, domain)
+
+
+def test_batch_create_rejects_no_runs():
+    from paper_2609_10849_b300.mhd import Batch
+    with pytest.raises(MhdError, match="invalid argument"):
+        Batch([])
+
+
+def _small():
+    wl = workloads.orszag_tang()
+    s = Solver(4, 3, 2, 2, wl["gamma"], wl["domain"])
+    X, Y = s.coords("dg")
+    rho, ux, uy, uz, pr, _ = wl["fields"](X, Y)
+    s.set_primitive(rho, np.stack([ux, uy, uz]), pr)
+    XW, YW = s.coords("w")
+    XZ, YZ = s.coords("bz")
+    s.set_B_from_potential(wl["Az"](XW, YW), *wl["B0"], wl["fields"](XZ, YZ)[5])
+    return s
+
+
+@pytest.mark.gpu
+def test_refused_calls_leave_the_context_usable():
+    s = _small()
+    ref = _small()
+    before = [a.copy() for a in s.get_state()]
+    for kw in (dict(cfl=0.0), dict(s_H=-1.0), dict(C_eta=-0.1), dict(max_halvings=-1), dict(strang_order=2)):
+        with pytest.raises(MhdError, match="invalid stabilisation parameters"):
+            s.set_params(**kw)
+    assert s.params == ref.params  # the refused values were not kept
+    with pytest.raises(MhdError, match="invalid argument"):
+        s.substep("M", 0.0)
+    with pytest.raises(MhdError, match="invalid argument"):
+        s.strang_steps(-1e-3, 2)
+    with pytest.raises(MhdError, match="invalid argument"):
+        s.strang_steps(1e-3, -1)
+    assert s.strang_steps(1e-3, 0) == 0
+    with pytest.raises(MhdError, match="invalid tile variant"):
+        s.set_tiles(9, 0)
+    with pytest.raises(MhdError, match="nq"):
+        s.quad_coords(0)
+    with pytest.raises(MhdError, match="nq"):
+        s.quad_coords(17)
+    X, Y = s.quad_coords(2)
+    with pytest.raises(MhdError, match="nq"):
+        s.set_Bz_projected(np.zeros_like(X), 2)  # k = 2 needs nq >= 3
+    x = np.zeros(s.state_size())
+    with pytest.raises(MhdError, match="invalid argument"):
+        s.adjoint_segment(x, 0, x, 1e-3)
+    for a, b in zip(s.get_state(), before):
+        assert np.array_equal(a, b)
+    # the context still steps exactly like a fresh one
+    assert s.strang_steps(1e-3, 3) == 3
+    assert ref.strang_steps(1e-3, 3) == 3
+    for a, b in zip(s.get_state(), ref.get_state()):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.gpu
+def test_adjoint_refuses_mhm_order():
+    s = _small()
+    s.set_params(strang_order=1)
+    with pytest.raises(MhdError):
+        s.adjoint_segment(np.ones(s.state_size()), 1, np.ones(s.state_size()), 1e-3)
+
+
+@pytest.mark.gpu
+def test_host_and_device_buffers_do_not_mix():
+    import torch
+    s = _small()
+    U, Bx, By, Bz = s.get_state()
+    with pytest.raises(ValueError, match="mix of host and device"):
+        s.set_state(torch.tensor(U, device="cuda"), Bx, By, Bz)
+    with pytest.raises(ValueError, match="float64"):
+        s.set_state(U.astype(np.float32), Bx, By, Bz)
