@@ -32,13 +32,13 @@ import numpy as np  # noqa: E402
 
 METRIC = "FP64 DOF-updates/s per Strang step at p=3"
 UNIT = "DOF-updates/s"
-NOMINAL_FP64_TFLOPS = 1.25  # B300 dense FP64, nominal (profiling recipe table)
+NOMINAL_FP64_TFLOPS = 1.25  # B300 dense FP64, nominal
 # DRAM bytes (read + write) of one k_vol<3> launch, mean over the three SSP stages (stage 1
 # does not read U^n), from the ncu capture summarised in profiles/kernels_orszag_tang_256_full.md
 # (same kernel source as this bench); reset to None whenever the volume kernel changes until it
 # is captured again.
 K_VOL_TRAFFIC_BYTES = (63.02e6 + 8.06e6 + 104.97e6 + 20.15e6 + 104.97e6 + 11.17e6) / 3.0
-# Config 2 of the workload: OE (both stages), positivity limiter, artificial
+# The stabilised benchmark workload: OE (both stages), positivity limiter, artificial
 # resistivity and velocity filter active, with the paper's constants.
 STAB = dict(oe_hydro=1, oe_vel=1, pp=1, ar=1, s_H=0.02, s_M=0.02, C_s=5.0, C_eta=0.2)
 
@@ -66,7 +66,7 @@ def dofs_per_element(p, k):
     return 5 * (p + 1) ** 2 + 3 * (k + 1) ** 2
 
 
-def vol_flops_per_element(p):
+def vol_flops_per_element_pairs(p):
     """Algorithmic work of one volume-kernel launch per element: ~117 FP64
     op-equivalents per unique entropy-conservative pair (means 12, two log means 2 x 22, p-hat 9, h-hat
     21, flux 6, accumulation into both nodes 20; FMA = 2, division = 8) times
@@ -74,7 +74,7 @@ def vol_flops_per_element(p):
     return 117 * p * (p + 1) ** 2
 
 
-def vol_flops_per_element(p):
+def vol_flops_per_element_minimal(p):
     """Algorithmic FP64 flops of one launch of the volume kernel per element
     (FMA = 2, add/mul/reciprocal = 1): 52 per entropy-conservative pair
     (p (p+1)^2 pairs), 16 per node for the primitives, 5 (4p + 3) per node for
@@ -417,7 +417,7 @@ def main():
     kt = s.kernel_times()
     s.profile_kernels(False)
     vol_ms = kt["vol"][0] / kt["vol"][1]
-    vol_flops = vol_flops_per_element(3) * s.K
+    vol_flops = vol_flops_per_element_pairs(3) * s.K
     achieved = vol_flops / (vol_ms * 1e-3) / 1e12
     measured_peak = mhd.fp64_peak_tflops()
     step_ms_sum = sum(v[0] for v in kt.values())
@@ -430,6 +430,8 @@ def main():
                 "flops_per_launch": vol_flops, "avg_launch_ms": vol_ms,
                 "flops_definition": "117 op-equivalents per unique EC pair x p(p+1)^2 pairs per element "
                                     "(FMA = 2, div = 8)",
+                "frac_minimal_count": vol_flops_per_element_minimal(3) * s.K / (vol_ms * 1e-3) / 1e12
+                / NOMINAL_FP64_TFLOPS,
                 "fp64_pipe_busy_ncu": 0.877,
                 "kernel_share_of_step": {k: v[0] / step_ms_sum for k, v in kt.items()}}
 

@@ -147,7 +147,7 @@ def test_bz_projection(pk, nq):
 
 
 def test_strang_alfven_per_step():
-    """Config 1 (circularly polarised Alfven wave, 16 x 16, p = k = 3): 1e-12 per step."""
+    """Circularly polarised Alfven wave (16 x 16, p = k = 3): 1e-12 per step."""
     wl = workloads.alfven_rotated()
     o = oracle_state(wl, 16, 16, 3, 3)
     o.set_params(cfl=0.4)
@@ -163,7 +163,7 @@ def test_strang_alfven_per_step():
 
 
 def test_strang_alfven_100_steps():
-    """Config 1 over 100 Strang steps: within 1e-9 of the oracle."""
+    """The circularly polarised Alfven wave over 100 Strang steps: within 1e-9 of the oracle."""
     wl = workloads.alfven_rotated()
     o = oracle_state(wl, 16, 16, 3, 3)
     s = solver_like(o)
@@ -296,7 +296,7 @@ def test_full_size_tiled_parity_stabilised():
 
 
 def test_full_size_blast_1024_tiled():
-    """Config 3 at its full size (1024 x 1024 elements, p = k = 3, every
+    """The blast wave at its full size (1024 x 1024 elements, p = k = 3, every
     stabilisation map on, in the bench's launch configuration): a 64 x 64 blast
     tiled 16 x 16 times keeps every row, column and global sensor statistic,
     so every tile must reproduce the oracle's stabilised Strang step; mass is
