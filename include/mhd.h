@@ -59,12 +59,18 @@ typedef struct { int nx, ny; double x0, x1, y0, y1; } mhd_mesh_t;
  * and Algorithm 3, Phi_H^{dt/2} Phi_M^{dt} Phi_H^{dt/2}; 1 the M-H-M
  * composition Phi_M^{dt/2} Phi_H^{dt} Phi_M^{dt/2}, which reproduces the
  * printed temporal Cauchy differences of the paper's Table 3 digit for digit
- * (not supported by the adjoint). */
+ * (not supported by the adjoint).
+ * reduced_2d2v: 1 selects the reduced magnetic stage of 2D2V configurations
+ * (§4: u_z = B_z = 0, so the in-plane components of E_h and J_h vanish and are
+ * not formed); the caller asserts u_z = B_z = 0, which every step then keeps
+ * exactly.  On such states the result equals that of the full stage (0,
+ * default).  The adjoint recomputes with the full stage. */
 typedef struct {
   int oe_hydro, oe_vel, pp, ar;
   double s_H, s_M, C_s, C_eta, cfl;
   int max_halvings;
   int strang_order;
+  int reduced_2d2v;
 } mhd_params_t;
 
 /* Diagnostics (DG-GLL quadrature for the fluid, exact magnetic product for

@@ -175,7 +175,7 @@ void mag_fwd(mhd_ctx* c, StepTape& t, const double* rho, double fac) {
     double* in = t.Y[s];
     double* out = t.Y[s + 1];
     mag_stage(c->p, c->k, 1, in + 4 * N, in + N, in, rho, t.eta, res, t.Y[0] + 4 * N, t.Y[0] + N, t.Y[0],
-              out + 4 * N, out + N, out, c->LJ, c->LE, c->T, c->M, c->dt, fac, RK_A[s], RK_B[s], s == 0, c->st);
+              out + 4 * N, out + N, out, c->LJ, c->LE, c->T, c->M, c->dt, fac, RK_A[s], RK_B[s], s == 0, 0, c->st);
     c->launches += 3;
     if (c->prm.oe_vel) {
       cudaMemcpyAsync(t.vstar + 3 * N * s, out + N, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);

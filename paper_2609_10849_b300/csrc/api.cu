@@ -133,7 +133,8 @@ void mag_substep(mhd_ctx* c, double fac) {
     {
       Prof pr(c, KC_MAG_E);
       mag_stage(c->p, c->k, 1, Bin[s], Yin[s] + N, Yin[s], c->U, c->eta, resistive, c->B, c->Y0 + N, c->Y0,
-                Bout[s], Yout[s] + N, Yout[s], c->LJ, c->LE, c->T, c->M, c->dt, fac, RK_A[s], RK_B[s], s == 0, c->st);
+                Bout[s], Yout[s] + N, Yout[s], c->LJ, c->LE, c->T, c->M, c->dt, fac, RK_A[s], RK_B[s], s == 0,
+                c->prm.reduced, c->st);
     }
     c->launches += 3;
     if (c->prm.oe_vel) {
@@ -280,10 +281,10 @@ void mhd_destroy(mhd_ctx* c) {
 int mhd_set_params(mhd_ctx* c, const mhd_params_t* prm) {
   if (!c || !prm) return fail(MHD_EINVAL, "null argument");
   if (prm->s_H < 0 || prm->s_M < 0 || prm->C_s < 0 || prm->C_eta < 0 || !(prm->cfl > 0) || prm->max_halvings < 0 ||
-      (prm->strang_order != 0 && prm->strang_order != 1))
+      (prm->strang_order != 0 && prm->strang_order != 1) || (prm->reduced_2d2v != 0 && prm->reduced_2d2v != 1))
     return fail(MHD_EINVAL, "invalid stabilisation parameters");
   c->prm = Stab{prm->oe_hydro, prm->oe_vel, prm->pp, prm->ar, prm->s_H, prm->s_M, prm->C_s, prm->C_eta, prm->cfl,
-                prm->max_halvings, c->status + 1, prm->strang_order};
+                prm->max_halvings, c->status + 1, prm->strang_order, prm->reduced_2d2v};
   if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
   return MHD_OK;
 }
@@ -609,7 +610,7 @@ int mhd_autotune(mhd_ctx* c, int* choices) {
     Mv.tile_mag = v;
     float t = time_launches(c, reps, [&] {
       mag_stage(c->p, c->k, 0, c->B, c->Y0 + N, c->Y0, c->U, c->eta, 0, c->B, c->Y0 + N, c->Y0, c->Ba, c->Ya + N,
-                c->Ya, c->LJ, c->LE, c->T, Mv, c->dt, 1.0, 0.0, 1.0, 1, c->st);
+                c->Ya, c->LJ, c->LE, c->T, Mv, c->dt, 1.0, 0.0, 1.0, 1, c->prm.reduced, c->st);
     }, a, b);
     if (t < best) { best = t; bm = v; }
   }
@@ -839,7 +840,7 @@ int mhd_mag_rhs(mhd_ctx* c, const double* rho, const double* e_, const double* u
   if ((e = copy_in(c, c->Ba + 2 * Z, Bz, Z, on_device)) != cudaSuccess) return cuda_fail(e, "Bz");
   if ((e = copy_in(c, c->work, eta, c->M.K, on_device)) != cudaSuccess) return cuda_fail(e, "eta");
   mag_stage(c->p, c->k, 0, c->Ba, c->Ya + N, c->Ya, c->S1, c->work, 1, c->Ba, c->Ya + N, c->Ya, c->Bb, c->Yb + N,
-            c->Yb, c->LJ, c->LE, c->T, c->M, c->dt, 0.0, 0.0, 0.0, 0, c->st);
+            c->Yb, c->LJ, c->LE, c->T, c->M, c->dt, 0.0, 0.0, 0.0, 0, 0, c->st);
   c->launches += 5;
   if ((e = copy_out(c, de, c->Yb, N, on_device)) != cudaSuccess) return cuda_fail(e, "de");
   if ((e = copy_out(c, du, c->Yb + N, 3 * N, on_device)) != cudaSuccess) return cuda_fail(e, "du");

@@ -20,7 +20,7 @@ size_t mag_load_doubles(int p, int k, int K);
 void mag_stage(int p, int k, int mode, const double* B, const double* u, const double* e, const double* rho,
                const double* eta, int resistive, const double* B0, const double* u0, const double* e0, double* Bo,
                double* uo, double* eo, double* LJ, double* LE, const Tab* T, const Mesh& M, const double* dtp,
-               double dtfac, double ca, double cb, int first, cudaStream_t st);
+               double dtfac, double ca, double cb, int first, int reduced, cudaStream_t st);
 void grid_to_blocked(const double* g, double* o, int nx, int ny, int mm, cudaStream_t st);
 void l2_project(int k, int nq, const double* fq, double* out, size_t K, cudaStream_t st);
 void blocked_to_grid(const double* o, double* g, int nx, int ny, int mm, cudaStream_t st);

@@ -128,7 +128,7 @@ struct LJ_ {  // per-element shared-memory offsets (doubles)
   static constexpr int SIZE = BZG + D::NZ;
 };
 
-template <int P, int KM, int EBv = mag_tile_eb(0)>
+template <int P, int KM, int EBv = mag_tile_eb(0), bool R2 = false>
 __global__ void __launch_bounds__(256) k_mag_J(const double* __restrict__ Bx, const double* __restrict__ By,
                                                const double* __restrict__ Bz, double* __restrict__ LJx,
                                                double* __restrict__ LJy, double* __restrict__ LJz, Mesh M) {
@@ -137,7 +137,8 @@ __global__ void __launch_bounds__(256) k_mag_J(const double* __restrict__ Bx, co
   const Tab& T = c_mtab[D::SLOT];
   extern __shared__ double sm[];
   const int k0 = blockIdx.x * D::EB;
-  constexpr int I1 = D::NY + D::NX + D::NZ;
+  // 2D2V (R2): B_z = 0, so only the W loads of J_z are formed
+  constexpr int I1 = D::NY + D::NX + (R2 ? 0 : D::NZ);
   FLAT(I1) {
     int it = idx / D::EB, e = idx % D::EB, k = min(k0 + e, M.K - 1);
     int ex = k % M.nx, ey = k / M.nx;
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(256) k_mag_J(const double* __restrict__ Bx, co
     else { it -= D::NY + D::NX; SM(O::BZ, it) = Bz[(size_t)k * D::NZ + it]; }
   }
   __syncthreads();
-  constexpr int I2 = D::mm * D::mL + D::mL * D::mm + D::NZ;
+  constexpr int I2 = D::mm * D::mL + D::mL * D::mm + (R2 ? 0 : D::NZ);
   FLAT(I2) {
     int it = idx / D::EB, e = idx % D::EB;
     if (it < D::mm * D::mL) {
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(256) k_mag_J(const double* __restrict__ Bx, co
   }
   __syncthreads();
   const double cy = 2.0 / M.hy * M.Jdet, cx = 2.0 / M.hx * M.Jdet;
-  constexpr int I3 = D::NW + D::NZ;
+  constexpr int I3 = D::NW + (R2 ? 0 : D::NZ);
   FLAT(I3) {
     int it = idx / D::EB, e = idx % D::EB, k = k0 + e;
     if (it < D::NW) {
@@ -195,7 +196,7 @@ __global__ void __launch_bounds__(256) k_mag_J(const double* __restrict__ Bx, co
     }
   }
   __syncthreads();
-  constexpr int I4 = D::NX + D::NY;
+  constexpr int I4 = R2 ? 0 : D::NX + D::NY;
   FLAT(I4) {
     int it = idx / D::EB, e = idx % D::EB, k = k0 + e;
     if (k >= M.K) continue;
@@ -246,7 +247,7 @@ struct LE_ {  // per-element shared-memory offsets (doubles), with region reuse
 
 // mode 0: write du, de (residual test hook); mode 1: SSP combination into (uo, eo);
 // mode 2: raw Lorentz load only (adjoint, see magnetic_adjoint.inc).
-template <int P, int KM, int MODE, int EBv = mag_tile_eb(0)>
+template <int P, int KM, int MODE, int EBv = mag_tile_eb(0), bool R2 = false>
 __global__ void __launch_bounds__(256) k_mag_E(
     const double* __restrict__ LJx, const double* __restrict__ LJy, const double* __restrict__ LJz,
     const double* __restrict__ Bx, const double* __restrict__ By, const double* __restrict__ Bz,
@@ -261,41 +262,49 @@ __global__ void __launch_bounds__(256) k_mag_E(
   const int k0 = blockIdx.x * D::EB;
   const size_t N = (size_t)M.K * D::n2;
   const double iJ = 1.0 / M.Jdet;
-  // stage 1: J closure (assembled), B closure, eta
-  constexpr int I1 = D::NX + D::NY + D::NW + D::NY + D::NX + D::NZ + 1;
+  // stage 1: J closure (assembled), B closure, eta (2D2V: J_z, B_x, B_y and eta only)
+  constexpr int I1 = (R2 ? 0 : D::NX + D::NY) + D::NW + D::NY + D::NX + (R2 ? 0 : D::NZ) + 1;
   FLAT(I1) {
     int it = idx / D::EB, e = idx % D::EB, k = min(k0 + e, M.K - 1);
     int ex = k % M.nx, ey = k / M.nx;
-    if (it < D::NX) { SM(O::JX, it) = assemble_Nx<P, KM>(LJx, ex, ey, it % D::mm, it / D::mm, M, iJ); continue; }
-    it -= D::NX;
-    if (it < D::NY) { SM(O::JY, it) = assemble_Ny<P, KM>(LJy, ex, ey, it % D::mL, it / D::mL, M, iJ); continue; }
-    it -= D::NY;
+    if constexpr (!R2) {
+      if (it < D::NX) { SM(O::JX, it) = assemble_Nx<P, KM>(LJx, ex, ey, it % D::mm, it / D::mm, M, iJ); continue; }
+      it -= D::NX;
+      if (it < D::NY) { SM(O::JY, it) = assemble_Ny<P, KM>(LJy, ex, ey, it % D::mL, it / D::mL, M, iJ); continue; }
+      it -= D::NY;
+    }
     if (it < D::NW) { SM(O::JZ, it) = assemble_W<P, KM>(LJz, ex, ey, it % D::mL, it / D::mL, M, iJ); continue; }
     it -= D::NW;
     if (it < D::NY) { SM(O::BX, it) = closure_Bx<P, KM>(Bx, ex, ey, it % D::mL, it / D::mL, M); continue; }
     it -= D::NY;
     if (it < D::NX) { SM(O::BY, it) = closure_By<P, KM>(By, ex, ey, it % D::mm, it / D::mm, M); continue; }
     it -= D::NX;
-    if (it < D::NZ) { SM(O::BZ, it) = Bz[(size_t)k * D::NZ + it]; continue; }
+    if constexpr (!R2) {
+      if (it < D::NZ) { SM(O::BZ, it) = Bz[(size_t)k * D::NZ + it]; continue; }
+    }
     SM(O::ETA, 0) = resistive ? eta[k] : 0.0;
   }
   __syncthreads();
-  // stage 2: x-passes (u read straight from global memory)
-  constexpr int NUG = 2 * D::n * D::mm, NUL = 3 * D::n * D::mL;
-  constexpr int I2 = NUG + NUL + D::NZ + D::NW + D::NZ + D::mm * D::mL;
+  // stage 2: x-passes (u read straight from global memory); only what the
+  // cross products need: E_x = -(u_y B_z - u_z B_y) at N_x, E_y = -(u_z B_x -
+  // u_x B_z) at N_y, E_z = -(u_x B_y - u_y B_x) at W
+  constexpr int NUG = R2 ? 0 : 2 * D::n * D::mm, NUL = (R2 ? 2 : 3) * D::n * D::mL;
+  constexpr int I2 = NUG + NUL + D::NW + (R2 ? 0 : D::NZ + D::mm * D::mL);
   FLAT(I2) {
     int it = idx / D::EB, e = idx % D::EB, k = min(k0 + e, M.K - 1);
-    if (it < NUG) {  // u_y, u_z to Gauss x
-      int d = it / (D::n * D::mm), r = it % (D::n * D::mm), j = r / D::mm, a = r % D::mm;
-      const double* ur = u + (1 + d) * N + (size_t)k * D::n2 + j * D::n;
-      double v = 0.0;
+    if constexpr (!R2) {
+      if (it < NUG) {  // u_y, u_z to Gauss x
+        int d = it / (D::n * D::mm), r = it % (D::n * D::mm), j = r / D::mm, a = r % D::mm;
+        const double* ur = u + (1 + d) * N + (size_t)k * D::n2 + j * D::n;
+        double v = 0.0;
 #pragma unroll
-      for (int i = 0; i < D::n; ++i) v = fma(T.P_G[a][i], ur[i], v);
-      SM(O::UG, it) = v;
-      continue;
+        for (int i = 0; i < D::n; ++i) v = fma(T.P_G[a][i], ur[i], v);
+        SM(O::UG, it) = v;
+        continue;
+      }
+      it -= NUG;
     }
-    it -= NUG;
-    if (it < NUL) {  // u_x, u_y, u_z to GLL(k+1) x
+    if (it < NUL) {  // u_x, u_y (and u_z) to GLL(k+1) x
       int d = it / (D::n * D::mL), r = it % (D::n * D::mL), j = r / D::mL, a = r % D::mL;
       const double* ur = u + d * N + (size_t)k * D::n2 + j * D::n;
       double v = 0.0;
@@ -305,15 +314,6 @@ __global__ void __launch_bounds__(256) k_mag_E(
       continue;
     }
     it -= NUL;
-    if (it < D::NZ) {  // Bx rows (Gauss y) to Gauss x
-      int j = it / D::mm, a = it % D::mm;
-      double v = 0.0;
-#pragma unroll
-      for (int i = 0; i < D::mL; ++i) v = fma(T.L_G[a][i], SM(O::BX, j * D::mL + i), v);
-      SM(O::BXG, it) = v;
-      continue;
-    }
-    it -= D::NZ;
     if (it < D::NW) {  // By rows (GLL y) to GLL x
       int j = it / D::mL, a = it % D::mL;
       double v = 0.0;
@@ -323,47 +323,51 @@ __global__ void __launch_bounds__(256) k_mag_E(
       continue;
     }
     it -= D::NW;
-    if (it < D::NZ) {  // Bz rows to Gauss x
-      int j = it / D::mm, a = it % D::mm;
-      double v = 0.0;
+    if constexpr (!R2) {
+      if (it < D::NZ) {  // Bz rows to Gauss x
+        int j = it / D::mm, a = it % D::mm;
+        double v = 0.0;
 #pragma unroll
-      for (int i = 0; i < D::mm; ++i) v = fma(T.M_G[a][i], SM(O::BZ, j * D::mm + i), v);
-      SM(O::BZG, it) = v;
-      continue;
-    }
-    it -= D::NZ;
-    {  // Bz rows to GLL(k+1) x
-      int j = it / D::mL, a = it % D::mL;
-      double v = 0.0;
+        for (int i = 0; i < D::mm; ++i) v = fma(T.M_G[a][i], SM(O::BZ, j * D::mm + i), v);
+        SM(O::BZG, it) = v;
+        continue;
+      }
+      it -= D::NZ;
+      {  // Bz rows to GLL(k+1) x
+        int j = it / D::mL, a = it % D::mL;
+        double v = 0.0;
 #pragma unroll
-      for (int i = 0; i < D::mm; ++i) v = fma(T.M_L[a][i], SM(O::BZ, j * D::mm + i), v);
-      SM(O::BZL, it) = v;
+        for (int i = 0; i < D::mm; ++i) v = fma(T.M_L[a][i], SM(O::BZ, j * D::mm + i), v);
+        SM(O::BZL, it) = v;
+      }
     }
   }
   __syncthreads();
   // stage 3: y-passes to the auxiliary families
-  constexpr int I3 = 2 * D::NX + 2 * D::NY + 2 * D::NW + D::NX + D::NX + D::NY + D::NY + D::NW + D::NW;
+  constexpr int I3 = (R2 ? 0 : 2 * D::NX + 2 * D::NY) + 2 * D::NW + (R2 ? 0 : D::NX + D::NY) + D::NW;
   FLAT(I3) {
     int it = idx / D::EB, e = idx % D::EB;
-    if (it < 2 * D::NX) {  // u_y, u_z at N_x: GLL(k+1) y from GLL(p)
-      int d = it / D::NX, r = it % D::NX, b = r / D::mm, a = r % D::mm;
-      double v = 0.0;
+    if constexpr (!R2) {
+      if (it < 2 * D::NX) {  // u_y, u_z at N_x: GLL(k+1) y from GLL(p)
+        int d = it / D::NX, r = it % D::NX, b = r / D::mm, a = r % D::mm;
+        double v = 0.0;
 #pragma unroll
-      for (int j = 0; j < D::n; ++j) v = fma(T.P_L[b][j], SM(O::UG, d * D::n * D::mm + j * D::mm + a), v);
-      SM(O::UNX, it) = v;
-      continue;
-    }
-    it -= 2 * D::NX;
-    if (it < 2 * D::NY) {  // u_x, u_z at N_y: Gauss y
-      int d = it / D::NY, r = it % D::NY, b = r / D::mL, a = r % D::mL;
-      const int src = (d == 0 ? 0 : 2) * D::n * D::mL;
-      double v = 0.0;
+        for (int j = 0; j < D::n; ++j) v = fma(T.P_L[b][j], SM(O::UG, d * D::n * D::mm + j * D::mm + a), v);
+        SM(O::UNX, it) = v;
+        continue;
+      }
+      it -= 2 * D::NX;
+      if (it < 2 * D::NY) {  // u_x, u_z at N_y: Gauss y
+        int d = it / D::NY, r = it % D::NY, b = r / D::mL, a = r % D::mL;
+        const int src = (d == 0 ? 0 : 2) * D::n * D::mL;
+        double v = 0.0;
 #pragma unroll
-      for (int j = 0; j < D::n; ++j) v = fma(T.P_G[b][j], SM(O::UL, src + j * D::mL + a), v);
-      SM(O::UNY, it) = v;
-      continue;
+        for (int j = 0; j < D::n; ++j) v = fma(T.P_G[b][j], SM(O::UL, src + j * D::mL + a), v);
+        SM(O::UNY, it) = v;
+        continue;
+      }
+      it -= 2 * D::NY;
     }
-    it -= 2 * D::NY;
     if (it < 2 * D::NW) {  // u_x, u_y at W
       int d = it / D::NW, r = it % D::NW, b = r / D::mL, a = r % D::mL;
       double v = 0.0;
@@ -373,66 +377,41 @@ __global__ void __launch_bounds__(256) k_mag_E(
       continue;
     }
     it -= 2 * D::NW;
-    if (it < D::NX) {  // Bx at N_x: Gauss y -> GLL y
-      int b = it / D::mm, a = it % D::mm;
-      double v = 0.0;
+    if constexpr (!R2) {
+      if (it < D::NX) {  // Bz at N_x: GLL(k) y -> GLL(k+1) y
+        int b = it / D::mm, a = it % D::mm;
+        double v = 0.0;
 #pragma unroll
-      for (int j = 0; j < D::mm; ++j) v = fma(T.G_L[b][j], SM(O::BXG, j * D::mm + a), v);
-      SM(O::BXNX, it) = v;
-      continue;
-    }
-    it -= D::NX;
-    if (it < D::NX) {  // Bz at N_x: GLL(k) y -> GLL(k+1) y
-      int b = it / D::mm, a = it % D::mm;
-      double v = 0.0;
+        for (int j = 0; j < D::mm; ++j) v = fma(T.M_L[b][j], SM(O::BZG, j * D::mm + a), v);
+        SM(O::BZNX, it) = v;
+        continue;
+      }
+      it -= D::NX;
+      if (it < D::NY) {  // Bz at N_y: GLL(k) y -> Gauss y
+        int b = it / D::mL, a = it % D::mL;
+        double v = 0.0;
 #pragma unroll
-      for (int j = 0; j < D::mm; ++j) v = fma(T.M_L[b][j], SM(O::BZG, j * D::mm + a), v);
-      SM(O::BZNX, it) = v;
-      continue;
+        for (int j = 0; j < D::mm; ++j) v = fma(T.M_G[b][j], SM(O::BZL, j * D::mL + a), v);
+        SM(O::BZNY, it) = v;
+        continue;
+      }
+      it -= D::NY;
     }
-    it -= D::NX;
-    if (it < D::NY) {  // By at N_y: GLL y -> Gauss y
-      int b = it / D::mL, a = it % D::mL;
-      double v = 0.0;
-#pragma unroll
-      for (int j = 0; j < D::mL; ++j) v = fma(T.L_G[b][j], SM(O::BYL, j * D::mL + a), v);
-      SM(O::BYNY, it) = v;
-      continue;
-    }
-    it -= D::NY;
-    if (it < D::NY) {  // Bz at N_y: GLL(k) y -> Gauss y
-      int b = it / D::mL, a = it % D::mL;
-      double v = 0.0;
-#pragma unroll
-      for (int j = 0; j < D::mm; ++j) v = fma(T.M_G[b][j], SM(O::BZL, j * D::mL + a), v);
-      SM(O::BZNY, it) = v;
-      continue;
-    }
-    it -= D::NY;
-    if (it < D::NW) {  // Bx at W: Gauss y -> GLL y
+    {  // Bx at W: Gauss y -> GLL y
       int b = it / D::mL, a = it % D::mL;
       double v = 0.0;
 #pragma unroll
       for (int j = 0; j < D::mm; ++j) v = fma(T.G_L[b][j], SM(O::BX, j * D::mL + a), v);
       SM(O::BXW, it) = v;
-      continue;
-    }
-    it -= D::NW;
-    {  // Bz at W
-      int b = it / D::mL, a = it % D::mL;
-      double v = 0.0;
-#pragma unroll
-      for (int j = 0; j < D::mm; ++j) v = fma(T.M_L[b][j], SM(O::BZL, j * D::mL + a), v);
-      SM(O::BZW, it) = v;
     }
   }
   __syncthreads();
   // stage 4: pointwise E loads (lumped weights); Lorentz products overwrite the u values in place
   const double Jd = M.Jdet;
-  constexpr int I4 = D::NX + D::NY + D::NW;
+  constexpr int I4 = (R2 ? 0 : D::NX + D::NY) + D::NW;
   FLAT(I4) {
     int it = idx / D::EB, e = idx % D::EB, k = k0 + e;
-    if (it < D::NX) {
+    if (!R2 && it < D::NX) {
       int b = it / D::mm, a = it % D::mm;
       double w = Jd * T.wG[a] * T.wL[b];
       double by_ = SM(O::BY, it), bz_ = SM(O::BZNX, it), jx_ = SM(O::JX, it);
@@ -440,7 +419,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
       if (k < M.K) LEx[(size_t)k * D::NX + it] = w * fma(uz, by_, -uy * bz_);
       SM(O::UNX, it) = -w * bz_ * jx_;         // s_y contribution
       SM(O::UNX, D::NX + it) = w * by_ * jx_;  // s_z contribution
-    } else if (it < D::NX + D::NY) {
+    } else if (!R2 && it < D::NX + D::NY) {
       it -= D::NX;
       int b = it / D::mL, a = it % D::mL;
       double w = Jd * T.wL[a] * T.wG[b];
@@ -450,7 +429,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
       SM(O::UNY, it) = w * bz_ * jy_;           // s_x
       SM(O::UNY, D::NY + it) = -w * bx_ * jy_;  // s_z
     } else {
-      it -= D::NX + D::NY;
+      if constexpr (!R2) it -= D::NX + D::NY;
       int b = it / D::mL, a = it % D::mL;
       double w = Jd * T.wL[a] * T.wL[b];
       double bx_ = SM(O::BXW, it), by_ = SM(O::BYL, it), jz_ = SM(O::JZ, it);
@@ -462,29 +441,33 @@ __global__ void __launch_bounds__(256) k_mag_E(
   }
   __syncthreads();
   // stage 5: transposed y-pass onto the DG y-nodes (into region B)
-  constexpr int I5 = D::n * D::mL + D::n * D::mm + D::n * D::mL + D::n * D::mm + D::n * D::mL;
+  constexpr int I5 = R2 ? 2 * D::n * D::mL : 3 * D::n * D::mL + 2 * D::n * D::mm;
   FLAT(I5) {
     int it = idx / D::EB, e = idx % D::EB;
     if (it < D::n * D::mL) {
       int j = it / D::mL, a = it % D::mL;
       double v = 0.0;
+      if constexpr (!R2) {
 #pragma unroll
-      for (int b = 0; b < D::mm; ++b) v = fma(T.P_G[b][j], SM(O::UNY, b * D::mL + a), v);
+        for (int b = 0; b < D::mm; ++b) v = fma(T.P_G[b][j], SM(O::UNY, b * D::mL + a), v);
+      }
 #pragma unroll
       for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UW, b * D::mL + a), v);
       SM(O::VX, it) = v;
       continue;
     }
     it -= D::n * D::mL;
-    if (it < D::n * D::mm) {
-      int j = it / D::mm, a = it % D::mm;
-      double v = 0.0;
+    if constexpr (!R2) {
+      if (it < D::n * D::mm) {
+        int j = it / D::mm, a = it % D::mm;
+        double v = 0.0;
 #pragma unroll
-      for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UNX, b * D::mm + a), v);
-      SM(O::VY1, it) = v;
-      continue;
+        for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UNX, b * D::mm + a), v);
+        SM(O::VY1, it) = v;
+        continue;
+      }
+      it -= D::n * D::mm;
     }
-    it -= D::n * D::mm;
     if (it < D::n * D::mL) {
       int j = it / D::mL, a = it % D::mL;
       double v = 0.0;
@@ -494,30 +477,33 @@ __global__ void __launch_bounds__(256) k_mag_E(
       continue;
     }
     it -= D::n * D::mL;
-    if (it < D::n * D::mm) {
-      int j = it / D::mm, a = it % D::mm;
-      double v = 0.0;
+    if constexpr (!R2) {
+      if (it < D::n * D::mm) {
+        int j = it / D::mm, a = it % D::mm;
+        double v = 0.0;
 #pragma unroll
-      for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UNX, D::NX + b * D::mm + a), v);
-      SM(O::VZ1, it) = v;
-      continue;
-    }
-    it -= D::n * D::mm;
-    {
-      int j = it / D::mL, a = it % D::mL;
-      double v = 0.0;
+        for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UNX, D::NX + b * D::mm + a), v);
+        SM(O::VZ1, it) = v;
+        continue;
+      }
+      it -= D::n * D::mm;
+      {
+        int j = it / D::mL, a = it % D::mL;
+        double v = 0.0;
 #pragma unroll
-      for (int b = 0; b < D::mm; ++b) v = fma(T.P_G[b][j], SM(O::UNY, D::NY + b * D::mL + a), v);
-      SM(O::VZ2, it) = v;
+        for (int b = 0; b < D::mm; ++b) v = fma(T.P_G[b][j], SM(O::UNY, D::NY + b * D::mL + a), v);
+        SM(O::VZ2, it) = v;
+      }
     }
   }
   __syncthreads();
   // stage 5b (resistive only): J_h at the DG nodes and the resistive loads
   if (resistive) {
-    constexpr int IR1 = D::mL * D::n + D::mm * D::n + D::mL * D::n;
+    constexpr int IR1 = (R2 ? 0 : D::mL * D::n + D::mm * D::n) + D::mL * D::n;
     FLAT(IR1) {
       int it = idx / D::EB, e = idx % D::EB;
       if (SM(O::ETA, 0) == 0.0) continue;
+      if constexpr (R2) it += D::mL * D::n + D::mm * D::n;  // J_z only
       if (it < D::mL * D::n) {
         int b = it / D::n, i = it % D::n;
         double v = 0.0;
@@ -541,10 +527,11 @@ __global__ void __launch_bounds__(256) k_mag_E(
       }
     }
     __syncthreads();
-    constexpr int IR2 = 3 * D::n2;
+    constexpr int IR2 = (R2 ? 1 : 3) * D::n2;
     FLAT(IR2) {
       int it = idx / D::EB, e = idx % D::EB;
       if (SM(O::ETA, 0) == 0.0) continue;
+      if constexpr (R2) it += 2 * D::n2;  // J_z only
       int d = it / D::n2, q = it % D::n2, j = q / D::n, i = q % D::n;
       double v = 0.0;
       if (d == 0) {
@@ -563,10 +550,11 @@ __global__ void __launch_bounds__(256) k_mag_E(
     // R_n = eta sum_q Jdet w_q J(x_q) phi_n(x_q), sum-factorised: x-pass of the
     // weighted DG-node values onto the basis in x (into the dead TQ area), then
     // y-pass, added to this element's own closure loads
-    constexpr int IR3 = D::n * D::mm + D::n * D::mL + D::n * D::mL;
+    constexpr int IR3 = (R2 ? 0 : D::n * D::mm + D::n * D::mL) + D::n * D::mL;
     FLAT(IR3) {
       int it = idx / D::EB, e = idx % D::EB;
       if (SM(O::ETA, 0) == 0.0) continue;
+      if constexpr (R2) it += D::n * D::mm + D::n * D::mL;  // W loads only
       if (it < D::n * D::mm) {  // N_x: basis g_a in x; rows j
         int j = it / D::mm, a = it % D::mm;
         double t = 0.0;
@@ -590,11 +578,12 @@ __global__ void __launch_bounds__(256) k_mag_E(
       }
     }
     __syncthreads();
-    constexpr int IR4 = D::NX + D::NY + D::NW;
+    constexpr int IR4 = (R2 ? 0 : D::NX + D::NY) + D::NW;
     FLAT(IR4) {
       int it = idx / D::EB, e = idx % D::EB, k = k0 + e;
       const double et = SM(O::ETA, 0);
       if (et == 0.0 || k >= M.K) continue;
+      if constexpr (R2) it += D::NX + D::NY;  // LEz only
       const double f = et * Jd;
       double r = 0.0;
       if (it < D::NX) {  // (a < mm, b < mL): y basis l^L_b
@@ -630,12 +619,14 @@ __global__ void __launch_bounds__(256) k_mag_E(
     for (int a = 0; a < D::mL; ++a) {
       sx = fma(T.P_L[a][i], SM(O::VX, j * D::mL + a), sx);
       sy = fma(T.P_L[a][i], SM(O::VY2, j * D::mL + a), sy);
-      sz = fma(T.P_L[a][i], SM(O::VZ2, j * D::mL + a), sz);
+      if constexpr (!R2) sz = fma(T.P_L[a][i], SM(O::VZ2, j * D::mL + a), sz);
     }
+    if constexpr (!R2) {
 #pragma unroll
-    for (int a = 0; a < D::mm; ++a) {
-      sy = fma(T.P_G[a][i], SM(O::VY1, j * D::mm + a), sy);
-      sz = fma(T.P_G[a][i], SM(O::VZ1, j * D::mm + a), sz);
+      for (int a = 0; a < D::mm; ++a) {
+        sy = fma(T.P_G[a][i], SM(O::VY1, j * D::mm + a), sy);
+        sz = fma(T.P_G[a][i], SM(O::VZ1, j * D::mm + a), sz);
+      }
     }
     size_t gq = (size_t)k * D::n2 + q;
     if (MODE == 2) {
@@ -650,7 +641,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
     double de = 0.0;
     const double et = SM(O::ETA, 0);
     if (resistive && et != 0.0) {
-      double jx = SM(O::JQ, q), jy = SM(O::JQ, D::n2 + q), jz = SM(O::JQ, 2 * D::n2 + q);
+      double jx = R2 ? 0.0 : SM(O::JQ, q), jy = R2 ? 0.0 : SM(O::JQ, D::n2 + q), jz = SM(O::JQ, 2 * D::n2 + q);
       de = et * fma(jx, jx, fma(jy, jy, jz * jz)) * rcp(r_);
     }
     if (MODE == 0) {
@@ -680,7 +671,7 @@ struct LB_ {
 };
 
 // mode 0: write dB; mode 1: SSP combination into Bo.
-template <int P, int KM, int MODE, int EBv = mag_tile_eb(0)>
+template <int P, int KM, int MODE, int EBv = mag_tile_eb(0), bool R2 = false>
 __global__ void __launch_bounds__(256) k_mag_B(const double* __restrict__ LEx, const double* __restrict__ LEy,
                                                const double* __restrict__ LEz, const double* B, const double* B0,
                                                double* Bo, Mesh M, const double* __restrict__ dtp, double dtfac,
@@ -692,16 +683,18 @@ __global__ void __launch_bounds__(256) k_mag_B(const double* __restrict__ LEx, c
   const int k0 = blockIdx.x * D::EB;
   const double iJ = 1.0 / M.Jdet;
   const size_t Z = (size_t)M.K * D::NZ;
-  constexpr int I1 = D::NX + D::NY + D::NW;
+  // 2D2V (R2): E_x = E_y = 0, so only E_z is assembled and dB_z = 0
+  constexpr int I1 = (R2 ? 0 : D::NX + D::NY) + D::NW;
   FLAT(I1) {
     int it = idx / D::EB, e = idx % D::EB, k = min(k0 + e, M.K - 1);
     int ex = k % M.nx, ey = k / M.nx;
+    if constexpr (R2) it += D::NX + D::NY;
     if (it < D::NX) SM(O::EX, it) = assemble_Nx<P, KM>(LEx, ex, ey, it % D::mm, it / D::mm, M, iJ);
     else if (it < D::NX + D::NY) { it -= D::NX; SM(O::EY, it) = assemble_Ny<P, KM>(LEy, ex, ey, it % D::mL, it / D::mL, M, iJ); }
     else { it -= D::NX + D::NY; SM(O::EZ, it) = assemble_W<P, KM>(LEz, ex, ey, it % D::mL, it / D::mL, M, iJ); }
   }
   __syncthreads();
-  constexpr int I2 = D::NZ + D::mL * D::mm;
+  constexpr int I2 = R2 ? 0 : D::NZ + D::mL * D::mm;
   FLAT(I2) {
     int it = idx / D::EB, e = idx % D::EB;
     if (it < D::NZ) {  // d/dx E_y at GLL(k) x, rows Gauss y
@@ -738,6 +731,8 @@ __global__ void __launch_bounds__(256) k_mag_B(const double* __restrict__ LEx, c
 #pragma unroll
       for (int c = 0; c < D::mL; ++c) v = fma(T.dL_G[a][c], SM(O::EZ, b * D::mL + c), v);
       dB = ax * v;
+    } else if (R2) {
+      dB = 0.0;
     } else {  // Bz at (xM_a, xM_b): -(d_x E_y - d_y E_x)
       double vy = 0.0, vx = 0.0;
 #pragma unroll
@@ -760,7 +755,7 @@ template <int P, int KM, int EBv>
 void mag_stage_eb(int mode, const double* B, const double* u, const double* e, const double* rho, const double* eta,
                   int resistive, const double* B0, const double* u0, const double* e0, double* Bo, double* uo,
                   double* eo, double* LJ, double* LE, const Mesh& M, const double* dtp, double dtfac, double ca,
-                  double cb, int first, cudaStream_t st) {
+                  double cb, int first, int reduced, cudaStream_t st) {
   using D = MD<P, KM, EBv>;
   const size_t Z = (size_t)M.K * D::NZ;
   double* LJx = LJ; double* LJy = LJ + (size_t)M.K * D::NX; double* LJz = LJy + (size_t)M.K * D::NY;
@@ -769,6 +764,23 @@ void mag_stage_eb(int mode, const double* B, const double* u, const double* e, c
   const size_t sj = sizeof(double) * LJ_<P, KM>::SIZE * D::EB;
   const size_t se = sizeof(double) * LE_<P, KM>::SIZE * D::EB;
   const size_t sb = sizeof(double) * LB_<P, KM>::SIZE * D::EB;
+  if (reduced) {  // 2D2V: u_z = B_z = 0, in-plane E and J vanish
+    k_mag_J<P, KM, EBv, true><<<blocks, D::TH, sj, st>>>(B, B + Z, B + 2 * Z, LJx, LJy, LJz, M);
+    if (mode == 0) {
+      k_mag_E<P, KM, 0, EBv, true><<<blocks, D::TH, se, st>>>(LJx, LJy, LJz, B, B + Z, B + 2 * Z, u, e, rho, eta, u0,
+                                                               e0, uo, eo, LEx, LEy, LEz, M, dtp, dtfac, ca, cb,
+                                                               first, resistive);
+      k_mag_B<P, KM, 0, EBv, true><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, M, dtp, dtfac, ca, cb,
+                                                               first);
+    } else {
+      k_mag_E<P, KM, 1, EBv, true><<<blocks, D::TH, se, st>>>(LJx, LJy, LJz, B, B + Z, B + 2 * Z, u, e, rho, eta, u0,
+                                                               e0, uo, eo, LEx, LEy, LEz, M, dtp, dtfac, ca, cb,
+                                                               first, resistive);
+      k_mag_B<P, KM, 1, EBv, true><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, M, dtp, dtfac, ca, cb,
+                                                               first);
+    }
+    return;
+  }
   k_mag_J<P, KM, EBv><<<blocks, D::TH, sj, st>>>(B, B + Z, B + 2 * Z, LJx, LJy, LJz, M);
   if (mode == 0) {
     k_mag_E<P, KM, 0, EBv><<<blocks, D::TH, se, st>>>(LJx, LJy, LJz, B, B + Z, B + 2 * Z, u, e, rho, eta, u0, e0, uo,
@@ -788,11 +800,11 @@ template <int P, int KM>
 void mag_stage_impl(int mode, const double* B, const double* u, const double* e, const double* rho,
                     const double* eta, int resistive, const double* B0, const double* u0, const double* e0,
                     double* Bo, double* uo, double* eo, double* LJ, double* LE, const Mesh& M, const double* dtp,
-                    double dtfac, double ca, double cb, int first, cudaStream_t st) {
+                    double dtfac, double ca, double cb, int first, int reduced, cudaStream_t st) {
   const int v = (M.tile_mag > 0 && M.tile_mag < kTileVariants && g_mag_tile_ok[P - 1 + KM][M.tile_mag]) ? M.tile_mag : 0;
 #define MHD_MAG_EB(V)                                                                                            \
   mag_stage_eb<P, KM, mag_tile_eb(V)>(mode, B, u, e, rho, eta, resistive, B0, u0, e0, Bo, uo, eo, LJ, LE, M, dtp, \
-                                      dtfac, ca, cb, first, st)
+                                      dtfac, ca, cb, first, reduced, st)
   switch (v) {
     case 1: MHD_MAG_EB(1); break;
     case 2: MHD_MAG_EB(2); break;
@@ -815,6 +827,11 @@ static cudaError_t mag_prepare_eb() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_E<P, KM, 1, EBv>, cudaFuncAttributeMaxDynamicSharedMemorySize, se);
   if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_B<P, KM, 0, EBv>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
   if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_B<P, KM, 1, EBv>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_J<P, KM, EBv, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sj);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_E<P, KM, 0, EBv, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, se);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_E<P, KM, 1, EBv, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, se);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_B<P, KM, 0, EBv, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute((const void*)k_mag_B<P, KM, 1, EBv, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sb);
   return e;
 }
 
@@ -865,11 +882,11 @@ size_t mag_load_doubles(int p, int k, int K) {
 void mag_stage(int p, int k, int mode, const double* B, const double* u, const double* e, const double* rho,
                const double* eta, int resistive, const double* B0, const double* u0, const double* e0, double* Bo,
                double* uo, double* eo, double* LJ, double* LE, const Tab* T, const Mesh& M, const double* dtp,
-               double dtfac, double ca, double cb, int first, cudaStream_t st) {
+               double dtfac, double ca, double cb, int first, int reduced, cudaStream_t st) {
   (void)T;  // the magnetic kernels read the constant-memory copy of the tables
 #define MHD_MAG_CASE(PP, KK)                                                                                  \
   mag_stage_impl<PP, KK>(mode, B, u, e, rho, eta, resistive, B0, u0, e0, Bo, uo, eo, LJ, LE, M, dtp, dtfac, ca, \
-                         cb, first, st)
+                         cb, first, reduced, st)
   MHD_DISPATCH_PK(p, k, MHD_MAG_CASE);
 #undef MHD_MAG_CASE
 }

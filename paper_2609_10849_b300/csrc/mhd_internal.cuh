@@ -95,6 +95,7 @@ struct Stab {
   int max_halvings;
   unsigned* activity;  // device word: which maps acted (ACT_* bits), may be null
   int strang_order;    // 0: H-M-H (Algorithm 3), 1: M-H-M
+  int reduced;         // 1: 2D2V magnetic stage (u_z = B_z = 0; in-plane E and J not formed)
 };
 
 // Activity bits of the stabilisation maps (mhd_diag_t.stab_active).

@@ -216,7 +216,9 @@ __global__ void k_global(int nc, int n, StatsView V, Mesh M) {
       const double amp = fmax(o[1] - mean, mean - o[2]);
       D = fmax(D, fmax(amp, 1e-6 * V.glob[c * 4 + 1]));
     }
-    V.lineD[t] = 1.0 / D;
+    // D = 0 only when every component is constant to roundoff (reading R8);
+    // then no component enters sigma, which is 0: keep 0 * (1/D) finite
+    V.lineD[t] = D > 0.0 ? 1.0 / D : 0.0;
   }
   if (threadIdx.x < 2 * n) {
     const int I = threadIdx.x / n, r = threadIdx.x % n;

@@ -33,7 +33,7 @@ class Mesh(C.Structure):
 class Params(C.Structure):
     _fields_ = [("oe_hydro", C.c_int), ("oe_vel", C.c_int), ("pp", C.c_int), ("ar", C.c_int), ("s_H", C.c_double),
                 ("s_M", C.c_double), ("C_s", C.c_double), ("C_eta", C.c_double), ("cfl", C.c_double),
-                ("max_halvings", C.c_int), ("strang_order", C.c_int)]
+                ("max_halvings", C.c_int), ("strang_order", C.c_int), ("reduced_2d2v", C.c_int)]
 
 
 class Diag(C.Structure):
@@ -172,7 +172,7 @@ class Solver:
         _check(lib().mhd_sizes(h, C.byref(K), C.byref(N), C.byref(G), C.byref(Z)))
         self.K, self.N, self.G, self.Z = K.value, N.value, G.value, Z.value
         self.params = dict(oe_hydro=0, oe_vel=0, pp=0, ar=0, s_H=0.02, s_M=0.02, C_s=5.0, C_eta=0.2, cfl=0.4,
-                           max_halvings=20, strang_order=0)
+                           max_halvings=20, strang_order=0, reduced_2d2v=0)
 
     def close(self):
         if getattr(self, "_h", None):
