@@ -962,7 +962,7 @@ void stab_vel_prep(int p, const double* rho, double* chol, const Tab* T, const M
 // Velocity OE map with heating of e; one element per segment of SW lanes.
 // frz (may be null): the damping factors D_0..D_p of every element, [K][p+1],
 // for the adjoint (frozen coefficients).
-template <int P, int KM>
+template <int P, int KM, bool R2 = false>
 __global__ void __launch_bounds__(OCfg<P>::threads) k_vel_oe(const double* __restrict__ rho, double* __restrict__ Y,
                                                              const double* __restrict__ B,
                                                              const double* __restrict__ Psi, StatsView V,
@@ -985,17 +985,19 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_vel_oe(const double* __res
   const int ex = kk % M.nx, ey = kk / M.nx;
   const int qq = node ? q : 0;
   const int i = qq % n, j = qq / n;
-  double u[3];
+  // 2D2V (R2): u_z = B_z = 0, so only u_x, u_y are filtered (u_z stays 0)
+  constexpr int ND = R2 ? 2 : 3;
+  double u[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-  for (int d = 0; d < 3; ++d) u[d] = node ? Y[(1 + d) * N + (size_t)kk * n2 + q] : 0.0;
+  for (int d = 0; d < ND; ++d) u[d] = node ? Y[(1 + d) * N + (size_t)kk * n2 + q] : 0.0;
   const double r_ = node ? rho[(size_t)kk * n2 + q] : 1.0;
   for (int t = q; t < n2 * n2; t += SW) sPsi[el][t] = Psi[(size_t)kk * n2 * n2 + t];
   // rate lambda_M from the nodal max of |u_I| + |B_h| / sqrt(rho) (eq. magnetic-oe-rate)
   double lam[2];
   {
-    double Bv[3];
+    double Bv[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
+    for (int d = 0; d < ND; ++d)
       Bv[d] = B_eval<KM>(B, Z, d, ex, ey, T->L_P[i], T->G_P[i], T->M_P[i], T->L_P[j], T->G_P[j], T->M_P[j], M);
     const double va = sqrt(fma(Bv[0], Bv[0], fma(Bv[1], Bv[1], Bv[2] * Bv[2])) * rcp(r_));
     const double ax = seg_max<SW>(node ? fabs(u[0]) + va : 0.0);
@@ -1005,14 +1007,14 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_vel_oe(const double* __res
   }
   const double W = node ? M.Jdet * T->wp[i] * T->wp[j] * r_ : 0.0;
 #pragma unroll
-  for (int d = 0; d < 3; ++d) sWu[d][tid] = W * u[d];
-  oe_factors<P>(V, 3, q, el, kk, ex, ey, lam, prm.s_M * dtp[0] * dtfac, M, ssig, sD);  // syncs
+  for (int d = 0; d < ND; ++d) sWu[d][tid] = W * u[d];
+  oe_factors<P>(V, ND, q, el, kk, ex, ey, lam, prm.s_M * dtp[0] * dtfac, M, ssig, sD);  // syncs
   if (frz && q < n && k < M.K) frz[(size_t)k * n + q] = sD[el][q];
   warp_or(prm.activity, sD[el][P] < 0.99 ? ACT_OE_VEL : 0u);
   // coefficients c_alpha = sum_t Psi[t][alpha] W_t u_t (lane q plays alpha)
   if (node) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
+    for (int d = 0; d < ND; ++d) {
       double s = 0.0;
 #pragma unroll
       for (int t = 0; t < n2; ++t) s = fma(sPsi[el][t * n2 + q], sWu[d][el * SW + t], s);
@@ -1023,7 +1025,7 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_vel_oe(const double* __res
   if (valid) {
     double de = 0.0;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
+    for (int d = 0; d < ND; ++d) {
       double unew = 0.0;
 #pragma unroll
       for (int l = 0; l <= P; ++l) {  // shell l holds basis indices [l^2, (l+1)^2)
@@ -1045,15 +1047,20 @@ void stab_vel(int p, int k, const double* rho, double* Y, const double* B, const
               cudaStream_t st) {
   StatsView V = stats_view(work, p, M);
   const size_t N = (size_t)M.K * (p + 1) * (p + 1);
+  const int nc = prm.reduced ? 2 : 3;  // 2D2V: u_z = 0 is constant and never enters the sensor
   switch (p) {
-    case 1: launch_stats<1>(Y + N, N, 3, V, T, M, st); break;
-    case 2: launch_stats<2>(Y + N, N, 3, V, T, M, st); break;
-    case 3: launch_stats<3>(Y + N, N, 3, V, T, M, st); break;
-    case 4: launch_stats<4>(Y + N, N, 3, V, T, M, st); break;
+    case 1: launch_stats<1>(Y + N, N, nc, V, T, M, st); break;
+    case 2: launch_stats<2>(Y + N, N, nc, V, T, M, st); break;
+    case 3: launch_stats<3>(Y + N, N, nc, V, T, M, st); break;
+    case 4: launch_stats<4>(Y + N, N, nc, V, T, M, st); break;
   }
-#define MHD_VOE_CASE(PP, KK)                                                                            \
-  k_vel_oe<PP, KK><<<(unsigned)((M.K + OCfg<PP>::EB - 1) / OCfg<PP>::EB), OCfg<PP>::threads, 0, st>>>( \
-      rho, Y, B, chol, V, T, M, prm, dtp, dtfac, frz)
+#define MHD_VOE_CASE(PP, KK)                                                                                    \
+  if (prm.reduced)                                                                                             \
+    k_vel_oe<PP, KK, true><<<(unsigned)((M.K + OCfg<PP>::EB - 1) / OCfg<PP>::EB), OCfg<PP>::threads, 0, st>>>( \
+        rho, Y, B, chol, V, T, M, prm, dtp, dtfac, frz);                                                        \
+  else                                                                                                         \
+    k_vel_oe<PP, KK><<<(unsigned)((M.K + OCfg<PP>::EB - 1) / OCfg<PP>::EB), OCfg<PP>::threads, 0, st>>>(       \
+        rho, Y, B, chol, V, T, M, prm, dtp, dtfac, frz)
   MHD_DISPATCH_PK(p, k, MHD_VOE_CASE);
 #undef MHD_VOE_CASE
 }
