@@ -360,6 +360,42 @@ def reduced_2d2v_leg(s, dt, steps, stream, dofs, full_ms_per_step):
             "note": "reduced_2d2v=1: in-plane E_h, J_h and u_z, B_z are not formed (all identically zero)"}
 
 
+def degree_leg(pairs=((3, 2), (4, 4), (2, 2), (4, 3)), mesh=256, steps=10):
+    """The benchmark workload (Orszag-Tang, all stabilisation on) at other
+    (p, k): the even-m family the paper recommends, (3,2) and (4,4), and two
+    neighbours.  Each pair is tile-autotuned; DOFs per element 5 (p+1)^2 + 3 (k+1)^2."""
+    import torch
+    from paper_2609_10849_b300 import workloads
+    from paper_2609_10849_b300.mhd import Solver
+    out = {}
+    wl = workloads.orszag_tang()
+    for p, k in pairs:
+        s = Solver(mesh, mesh, p, k, wl["gamma"], wl["domain"])
+        X, Y = s.coords("dg")
+        rho, ux, uy, uz, pr, _ = wl["fields"](X, Y)
+        s.set_primitive(rho, np.stack([ux, uy, uz]), pr)
+        XW, YW = s.coords("w")
+        XZ, YZ = s.coords("bz")
+        s.set_B_from_potential(wl["Az"](XW, YW), *wl["B0"], wl["fields"](XZ, YZ)[5])
+        s.set_params(cfl=0.4, **STAB)
+        stream = torch.cuda.Stream()
+        s.set_stream(stream.cuda_stream)
+        tiles = s.autotune()
+        dt = s.compute_dt()
+        s.strang_steps(dt, 3)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.strang_steps(dt, steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[f"p{p}k{k}"] = {"ms_per_step": ms, "value": dofs_per_element(p, k) * s.K / (ms * 1e-3), "unit": UNIT,
+                            "tiles": list(tiles)}
+        s.close()
+    return {"workload": f"orszag_tang_{mesh}x{mesh}", "steps": steps, "pairs": out}
+
+
 def run_batch(args):
     print(json.dumps(batch_leg(args.batch, args.steps)), flush=True)
 
@@ -488,6 +524,7 @@ def main():
         if reduced is not None:
             line["reduced_2d2v"] = reduced
         if not args.no_side_legs and world == 1:
+            line["degrees"] = degree_leg()
             line["adjoint"] = adjoint_leg()
             line["batched"] = batch_leg(256, 2)
         if not args.no_cpu_baseline:
