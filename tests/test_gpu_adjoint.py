@@ -378,3 +378,26 @@ def test_adjoint_segment_matches_steps():
         chain = s.adjoint_step(states[i], chain, dt)
     assert np.array_equal(seg, chain)
     assert s.last_adjoint_flags == 15
+
+
+def test_adjoint_with_reduced_2d2v_stage():
+    """On a 2D2V state (u_z = B_z = 0) the adjoint of a solver stepping with the
+    reduced magnetic stage equals that of the full stage bit for bit (its
+    recomputation runs the full stage; the reduced velocity OE keeps the same
+    frozen coefficients), for every stabilisation map on."""
+    rng = np.random.default_rng(995)
+    p = k = 3
+    t = Tangent(5, 4, p, k, 5 / 3, (0.0, 1.0, 0.0, 1.0))
+    U = generic_state(t, rng)
+    U[3] = 0.0  # m_z
+    Bx, By = rng.uniform(-0.5, 0.5, t.G), rng.uniform(-0.5, 0.5, t.G)
+    Bz = np.zeros(t.Z)
+    x0 = packed(t, U, Bx, By, Bz)
+    lam = rng.standard_normal(x0.shape)
+    out = []
+    for reduced in (0, 1):
+        s = solver_like(t)
+        s.set_params(oe_hydro=1, pp=1, oe_vel=1, ar=1, C_eta=0.2, reduced_2d2v=reduced)
+        out.append((s.adjoint_segment(x0, 3, lam, 1e-3), s.last_adjoint_flags))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1]
