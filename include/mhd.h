@@ -62,9 +62,10 @@ typedef struct { int nx, ny; double x0, x1, y0, y1; } mhd_mesh_t;
  * (not supported by the adjoint).
  * reduced_2d2v: 1 selects the reduced magnetic stage of 2D2V configurations
  * (§4: u_z = B_z = 0, so the in-plane components of E_h and J_h vanish and are
- * not formed); the caller asserts u_z = B_z = 0, which every step then keeps
- * exactly.  On such states the result equals that of the full stage (0,
- * default).  The adjoint recomputes with the full stage. */
+ * not formed); it needs u_z = B_z = 0, which every step then keeps exactly.
+ * On such states the result equals that of the full stage (0, default).  A
+ * step that meets a nonzero m_z or B_z (or NaN) restores the state and
+ * returns MHD_EINVAL.  The adjoint recomputes with the full stage. */
 typedef struct {
   int oe_hydro, oe_vel, pp, ar;
   double s_H, s_M, C_s, C_eta, cfl;

@@ -29,6 +29,7 @@ int fail(int code, const std::string& msg) {
   g_err = msg;
   return code;
 }
+const char* const kNotPlanar = "reduced_2d2v needs u_z = B_z = 0 (a nonzero m_z or B_z was found; state restored)";
 int cuda_fail(cudaError_t e, const char* where) {
   g_err = std::string(where) + ": " + cudaGetErrorString(e);
   return MHD_ECUDA;
@@ -110,6 +111,10 @@ void hydro_substep(mhd_ctx* c, double fac) {
 // exchange before and after (§3.4.1).
 void mag_substep(mhd_ctx* c, double fac) {
   const size_t N = c->N;
+  if (c->prm.reduced) {  // the reduced stage is exact only for u_z = B_z = 0
+    check_planar(c->U + 3 * N, N, c->B + 2 * c->Z, c->Z, c->status, c->st);
+    c->launches++;
+  }
   { Prof pr(c, KC_EXCH); cons_to_prim(c->U, c->Y0, N, c->st); }
   c->launches++;
   int resistive = c->prm.ar && c->prm.C_eta != 0.0;
@@ -473,6 +478,12 @@ int mhd_strang_step(mhd_ctx* c, double dt, double* dt_taken) {
     unsigned s = 0;
     int r = check_status(c, &s);
     if (r != MHD_OK) return r;
+    if (s & ST_NOT_PLANAR) {
+      cudaMemcpyAsync(c->U, c->Usave, 5 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+      cudaMemcpyAsync(c->B, c->Bsave, 3 * c->Z * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+      cudaStreamSynchronize(c->st);
+      return fail(MHD_EINVAL, kNotPlanar);
+    }
     if (!(s & ST_INADMISSIBLE)) {
       if (dt_taken) *dt_taken = dt;
       return att > 0 ? MHD_RETRIED : MHD_OK;
@@ -544,10 +555,11 @@ int mhd_strang_steps(mhd_ctx* c, double dt, int nsteps, int* steps_done) {
   unsigned s = 0;
   r = check_status(c, &s);
   if (r != MHD_OK) return r;
-  if (s & ST_INADMISSIBLE) {
+  if (s & (ST_INADMISSIBLE | ST_NOT_PLANAR)) {
     cudaMemcpyAsync(c->U, c->Usave, 5 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
     cudaMemcpyAsync(c->B, c->Bsave, 3 * c->Z * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
     cudaStreamSynchronize(c->st);
+    if (s & ST_NOT_PLANAR) return fail(MHD_EINVAL, kNotPlanar);
     c->rejections++;
     return fail(MHD_INADMISSIBLE, "inadmissible cell average in a fixed-step sequence");
   }
@@ -776,15 +788,16 @@ int mhd_batch_step(mhd_batch* b, const double* dt, int nsteps, int* status) {
   for (int i = 0; i < n; ++i) {
     mhd_ctx* c = b->runs[i];
     int st = MHD_OK;
-    if (b->h_status[i] & ST_INADMISSIBLE) {  // restore this run; the caller may retry it with a smaller dt
+    if (b->h_status[i] & (ST_INADMISSIBLE | ST_NOT_PLANAR)) {  // restore this run; the caller may retry it
       cudaMemcpyAsync(c->U, c->Usave, 5 * c->N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
       cudaMemcpyAsync(c->B, c->Bsave, 3 * c->Z * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
       cudaStreamSynchronize(c->st);
-      st = MHD_INADMISSIBLE;
-      worst = MHD_INADMISSIBLE;
+      st = (b->h_status[i] & ST_NOT_PLANAR) ? MHD_EINVAL : MHD_INADMISSIBLE;
+      if (worst == MHD_OK || st == MHD_EINVAL) worst = st;
     }
     if (status) status[i] = st;
   }
+  if (worst == MHD_EINVAL) return fail(worst, kNotPlanar);
   return worst == MHD_OK ? MHD_OK : fail(worst, "a run of the batch had an inadmissible cell average");
 }
 
@@ -798,6 +811,13 @@ long long mhd_batch_launch_count(const mhd_batch* b) {
 int mhd_substep(mhd_ctx* c, int which, double tau) {
   if (!c || !(tau > 0) || (which != 0 && which != 1)) return fail(MHD_EINVAL, "invalid argument");
   cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->st);
+  if (which == 1 && c->prm.reduced) {  // refuse before any change of the state
+    unsigned s0 = 0;
+    check_planar(c->U + 3 * c->N, c->N, c->B + 2 * c->Z, c->Z, c->status, c->st);
+    int r0 = check_status(c, &s0);
+    if (r0 != MHD_OK) return r0;
+    if (s0 & ST_NOT_PLANAR) return fail(MHD_EINVAL, kNotPlanar);
+  }
   set_scalar(c->dt, tau, c->st);
   c->launches++;
   if (which == 0) hydro_substep(c, 1.0);

@@ -22,6 +22,7 @@ void mag_stage(int p, int k, int mode, const double* B, const double* u, const d
                double* uo, double* eo, double* LJ, double* LE, const Tab* T, const Mesh& M, const double* dtp,
                double dtfac, double ca, double cb, int first, int reduced, cudaStream_t st);
 void grid_to_blocked(const double* g, double* o, int nx, int ny, int mm, cudaStream_t st);
+void check_planar(const double* mz, size_t N, const double* bz, size_t Z, unsigned* status, cudaStream_t st);
 void l2_project(int k, int nq, const double* fq, double* out, size_t K, cudaStream_t st);
 void blocked_to_grid(const double* o, double* g, int nx, int ny, int mm, cudaStream_t st);
 void cons_to_prim(const double* U, double* Y, size_t N, cudaStream_t st);

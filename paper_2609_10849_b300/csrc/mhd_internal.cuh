@@ -124,6 +124,7 @@ enum : unsigned {
   ST_INADMISSIBLE = 1u,
   ST_NONFINITE = 2u,
   ST_TIMEOUT = 4u,
+  ST_NOT_PLANAR = 8u,  // reduced 2D2V stage on a state with u_z or B_z nonzero
 };
 
 __host__ __device__ inline int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }

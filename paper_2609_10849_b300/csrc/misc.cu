@@ -213,6 +213,24 @@ __global__ void k_finalize_dt(const unsigned long long* __restrict__ maxbits, do
 
 __global__ void k_set_scalar(double* p, double v) { *p = v; }
 
+// The reduced 2D2V stage needs m_z = 0 and B_z = 0 everywhere: flag any other
+// value (NaN included) in the status word.  Every thread reaches the vote.
+__global__ void k_check_planar(const double* __restrict__ mz, size_t N, const double* __restrict__ bz, size_t Z,
+                               unsigned* __restrict__ status) {
+  bool bad = false;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N + Z; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = i < N ? mz[i] : bz[i - N];
+    bad |= !(v == 0.0);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(status, ST_NOT_PLANAR);
+}
+
+void check_planar(const double* mz, size_t N, const double* bz, size_t Z, unsigned* status, cudaStream_t st) {
+  const size_t tot = N + Z;
+  unsigned blocks = (unsigned)std::min<size_t>((tot + 255) / 256, 148 * 8);
+  k_check_planar<<<blocks, 256, 0, st>>>(mz, N, bz, Z, status);
+}
+
 void cfl_dt(int p, int k, const double* U, const double* B, const Tab* T, const Mesh& M,
             unsigned long long* maxbits, double cfl, double* dt, cudaStream_t st) {
   cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long), st);

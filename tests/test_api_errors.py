@@ -109,3 +109,28 @@ def test_host_and_device_buffers_do_not_mix():
         s.set_state(torch.tensor(U, device="cuda"), Bx, By, Bz)
     with pytest.raises(ValueError, match="float64"):
         s.set_state(U.astype(np.float32), Bx, By, Bz)
+
+
+@pytest.mark.gpu
+def test_reduced_2d2v_refuses_out_of_plane_fields():
+    """The reduced 2D2V stage is exact only for u_z = B_z = 0: on a state with
+    B_z != 0 every stepping call refuses it, leaves the state as it was, and
+    the same context steps normally once the full stage is selected again."""
+    from tests.util import oracle_state
+    wl = workloads.alfven_diagonal()  # B_z and u_z nonzero
+    o = oracle_state(wl, 4, 4, 2, 2)
+    s = Solver(4, 4, 2, 2, wl["gamma"], wl["domain"])
+    s.set_state(*o.get_state())
+    s.set_params(reduced_2d2v=1)
+    before = [a.copy() for a in s.get_state()]
+    with pytest.raises(MhdError, match="reduced_2d2v needs") as e:
+        s.strang_step(1e-3)
+    assert e.value.code == MHD_EINVAL
+    with pytest.raises(MhdError, match="reduced_2d2v needs"):
+        s.strang_steps(1e-3, 2)
+    with pytest.raises(MhdError, match="reduced_2d2v needs"):
+        s.substep("M", 1e-3)
+    for a, b in zip(s.get_state(), before):
+        assert np.array_equal(a, b)
+    s.set_params(reduced_2d2v=0)
+    assert s.strang_steps(1e-3, 2) == 2
