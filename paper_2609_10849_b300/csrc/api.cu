@@ -214,6 +214,7 @@ int mhd_create(const mhd_mesh_t* mesh, int p, int k, double gamma, mhd_ctx** out
   c->M.hy = (mesh->y1 - mesh->y0) / mesh->ny;
   c->M.Jdet = c->M.hx * c->M.hy / 4.0;
   c->M.g = gamma;
+  mesh_reciprocals(c->M);
   c->prm = Stab{0, 0, 0, 0, 0.02, 0.02, 5.0, 0.2, 0.4, 20};
   c->N = (size_t)c->M.K * c->n2;
   c->Z = (size_t)c->M.K * c->mm * c->mm;

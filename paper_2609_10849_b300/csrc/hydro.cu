@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __r
   __syncthreads();
 
   // ---- pair fluxes ------------------------------------------------------------
-  const double ig1 = 1.0 / (g - 1.0);
+  const double ig1 = M.ig1;
 #pragma unroll
   for (int s = 0; s < P; ++s) {
     const int pidx = q + s * n2;
@@ -181,8 +181,9 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __r
   double Drow_i[n], Drow_j[n];
 #pragma unroll
   for (int r = 0; r < n; ++r) { Drow_i[r] = T->D[i][r]; Drow_j[r] = T->D[j][r]; }
-  const double cx = -4.0 / M.hx, cy = -4.0 / M.hy;
-  const double w0i = 1.0 / T->wp[0];
+  const double cx = -4.0 * M.ihx, cy = -4.0 * M.ihy;
+  constexpr double w0i = 0.5 * P * (P + 1);  // 1 / w_0 of GLL(p): w_0 = 2 / (p (p + 1))
+  const double fx = 2.0 * M.ihx * w0i, fy = 2.0 * M.ihy * w0i;
   const int ex = kk % M.nx, ey = kk / M.nx;
   const size_t nf = (size_t)M.K * n;
   double L[5];
@@ -203,10 +204,10 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __r
     }
     double v = fma(cx, sx, cy * sy);
     // end nodes: -(2/hx)[-F*_left/w_0] and -(2/hx)[+F*_right/w_p] (w_p = w_0)
-    if (i == 0) v = fma(2.0 / M.hx * w0i, Fx[c * nf + (size_t)kk * n + j], v);
-    if (i == P) v = fma(-2.0 / M.hx * w0i, Fx[c * nf + (size_t)(ey * M.nx + wrap(ex + 1, M.nx)) * n + j], v);
-    if (j == 0) v = fma(2.0 / M.hy * w0i, Fy[c * nf + (size_t)kk * n + i], v);
-    if (j == P) v = fma(-2.0 / M.hy * w0i, Fy[c * nf + (size_t)(wrap(ey + 1, M.ny) * M.nx + ex) * n + i], v);
+    if (i == 0) v = fma(fx, Fx[c * nf + (size_t)kk * n + j], v);
+    if (i == P) v = fma(-fx, Fx[c * nf + (size_t)(ey * M.nx + wrap(ex + 1, M.nx)) * n + j], v);
+    if (j == 0) v = fma(fy, Fy[c * nf + (size_t)kk * n + i], v);
+    if (j == P) v = fma(-fy, Fy[c * nf + (size_t)(wrap(ey + 1, M.ny) * M.nx + ex) * n + i], v);
     L[c] = v;
   }
 

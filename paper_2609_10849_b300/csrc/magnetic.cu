@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(256) k_mag_J(const double* __restrict__ Bx, co
     }
   }
   __syncthreads();
-  const double cy = 2.0 / M.hy * M.Jdet, cx = 2.0 / M.hx * M.Jdet;
+  const double cy = 2.0 * M.ihy * M.Jdet, cx = 2.0 * M.ihx * M.Jdet;
   constexpr int I3 = D::NW + (R2 ? 0 : D::NZ);
   FLAT(I3) {
     int it = idx / D::EB, e = idx % D::EB, k = k0 + e;
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
   extern __shared__ double sm[];
   const int k0 = blockIdx.x * D::EB;
   const size_t N = (size_t)M.K * D::n2;
-  const double iJ = 1.0 / M.Jdet;
+  const double iJ = M.iJ;
   // stage 1: J closure (assembled), B closure, eta (2D2V: J_z, B_x, B_y and eta only)
   constexpr int I1 = (R2 ? 0 : D::NX + D::NY) + D::NW + D::NY + D::NX + (R2 ? 0 : D::NZ) + 1;
   FLAT(I1) {
@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(256) k_mag_B(const double* __restrict__ LEx, c
   const Tab& T = c_mtab[D::SLOT];
   extern __shared__ double sm[];
   const int k0 = blockIdx.x * D::EB;
-  const double iJ = 1.0 / M.Jdet;
+  const double iJ = M.iJ;
   const size_t Z = (size_t)M.K * D::NZ;
   // 2D2V (R2): E_x = E_y = 0, so only E_z is assembled and dB_z = 0
   constexpr int I1 = (R2 ? 0 : D::NX + D::NY) + D::NW;
@@ -714,7 +714,7 @@ __global__ void __launch_bounds__(256) k_mag_B(const double* __restrict__ LEx, c
   }
   __syncthreads();
   const double tau = MODE ? dtp[0] * dtfac : 0.0;
-  const double ax = 2.0 / M.hx, ay = 2.0 / M.hy;
+  const double ax = 2.0 * M.ihx, ay = 2.0 * M.ihy;
   constexpr int I3 = 3 * D::NZ;
   FLAT(I3) {
     int it = idx / D::EB, e = idx % D::EB, k = k0 + e;

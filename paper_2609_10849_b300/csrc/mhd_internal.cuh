@@ -76,7 +76,17 @@ struct Mesh {
   // tile variants chosen by the autotuner (0 = default elements per CTA):
   // volume kernel and magnetic-stage kernels
   int tile_vol, tile_mag;
+  // reciprocals the kernels use, rounded once on the host (mesh_reciprocals)
+  double ihx, ihy, iJ, ig1;
 };
+
+// Fill the reciprocal fields of a mesh whose hx, hy, Jdet and g are set.
+inline void mesh_reciprocals(Mesh& M) {
+  M.ihx = 1.0 / M.hx;
+  M.ihy = 1.0 / M.hy;
+  M.iJ = 1.0 / M.Jdet;
+  M.ig1 = 1.0 / (M.g - 1.0);
+}
 
 // Elements per CTA of the tile variants (index 0 is the default).
 constexpr int vol_tile_eb(int p, int v) {

@@ -99,12 +99,13 @@ extern "C" int mhd_hydro_rhs_static(const mhd_mesh_t* mesh, int p, double gamma,
     snprintf(g_static_err, sizeof g_static_err, "tables: %s", cudaGetErrorString(e));
     return static_fail(MHD_ECUDA);
   }
-  mhd::Mesh M;
+  mhd::Mesh M{};  // default tile variants (0)
   M.nx = mesh->nx; M.ny = mesh->ny; M.K = (int)K;
   M.hx = (mesh->x1 - mesh->x0) / mesh->nx;
   M.hy = (mesh->y1 - mesh->y0) / mesh->ny;
   M.Jdet = M.hx * M.hy / 4.0;
   M.g = gamma;
+  mhd::mesh_reciprocals(M);
   cudaStream_t st = (cudaStream_t)stream;
   double* Fx = scratch;
   double* Fy = scratch + 5ull * K * (p + 1);

@@ -104,8 +104,7 @@ __global__ void k_stats(const double* __restrict__ F, size_t stride, int nc, Sta
   }
   const int I = (w - 1) / n, r = (w - 1) % n;
   const int kA = I == 0 ? ey * M.nx + wrap(ex - 1, M.nx) : wrap(ey - 1, M.ny) * M.nx + ex;  // lower side
-  const double h = I == 0 ? M.hx : M.hy;
-  const double ih = rcp(0.5 * h);
+  const double ih = 2.0 * (I == 0 ? M.ihx : M.ihy);  // 1 / (h / 2)
   double scale = 1.0;  // (2/h)^r, applied once to the averaged square
   for (int i = 0; i < r; ++i) scale *= ih;
   double acc = 0.0;
@@ -352,8 +351,8 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_oe_pp(double* __restrict__
       const double ir = rcp(a0);
       const double pb = (g - 1.0) * fma(-0.5 * ir, fma(a1, a1, fma(a2, a2, a3 * a3)), a4);
       const double cb = sqrt(g * pb * ir);
-      lam[0] = (2.0 * P + 1.0) * (fabs(a1 * ir) + cb) * rcp(M.hx);
-      lam[1] = (2.0 * P + 1.0) * (fabs(a2 * ir) + cb) * rcp(M.hy);
+      lam[0] = (2.0 * P + 1.0) * (fabs(a1 * ir) + cb) * M.ihx;
+      lam[1] = (2.0 * P + 1.0) * (fabs(a2 * ir) + cb) * M.ihy;
     }
     oe_factors<P>(V, 5, q, el, kk, ex, ey, lam, prm.s_H * dtp[0] * dtfac, M, ssig, sD);
 #pragma unroll
@@ -1002,8 +1001,8 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_vel_oe(const double* __res
     const double va = sqrt(fma(Bv[0], Bv[0], fma(Bv[1], Bv[1], Bv[2] * Bv[2])) * rcp(r_));
     const double ax = seg_max<SW>(node ? fabs(u[0]) + va : 0.0);
     const double ay = seg_max<SW>(node ? fabs(u[1]) + va : 0.0);
-    lam[0] = (2.0 * P + 1.0) * rcp(M.hx) * ax;
-    lam[1] = (2.0 * P + 1.0) * rcp(M.hy) * ay;
+    lam[0] = (2.0 * P + 1.0) * M.ihx * ax;
+    lam[1] = (2.0 * P + 1.0) * M.ihy * ay;
   }
   const double W = node ? M.Jdet * T->wp[i] * T->wp[j] * r_ : 0.0;
 #pragma unroll
