@@ -418,9 +418,12 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_oe_pp(double* __restrict__
     for (int c = 0; c < 5; ++c)  // average of U* (eq. euler-pp-average), identical in every lane of the segment
       a[c] = __shfl_sync(0xffffffffu, seg_sum<SW>(wq * u[c]), lead);
     const double rbar = a[0];
-    const double ira = rcp(fmax(a[0], eps_rho));  // only used when rbar > eps_rho
+    // one reciprocal of the average density: 1/rho-bar for p-bar, and 1/max(rho-bar, eps_rho)
+    // (the clamped value, a constant below eps_rho) for the cancellation scale
+    const double ira0 = rcp(a[0]);
+    const double ira = a[0] > eps_rho ? ira0 : 1.0 / eps_rho;
     const double ma2 = fma(a[1], a[1], fma(a[2], a[2], a[3] * a[3]));
-    const double pbar = (g - 1.0) * fma(-0.5 * ma2, a[0] > eps_rho ? ira : 1.0 / a[0], a[4]);
+    const double pbar = (g - 1.0) * fma(-0.5 * ma2, ira0, a[4]);
     const bool bad = !(rbar > 0.0) || !(pbar > 0.0) || !isfinite(rbar) || !isfinite(pbar);
     // density scaling (eq. euler-pp-density)
     const double rmin = seg_min<SW>(node ? u[0] : DBL_MAX);
@@ -433,9 +436,10 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_oe_pp(double* __restrict__
     if (th_r < 1.0) r0 = rbar + th_r * (u[0] - rbar);
     // pressure-cancellation scale and floor (eq. euler-pp-floors), pressure scaling (eq. euler-pp-pressure)
     const double m2 = fma(u[1], u[1], fma(u[2], u[2], u[3] * u[3]));
-    const double ir0 = rcp(fmax(r0, eps_rho));  // nodes are >= eps_rho after the density scaling
+    const double ir0t = rcp(r0);  // nodes are >= eps_rho after the density scaling
+    const double ir0 = r0 >= eps_rho ? ir0t : 1.0 / eps_rho;
     const double Sq = node ? fma(0.5 * m2, ir0, fabs(u[4])) : 0.0;
-    const double pq = node ? (g - 1.0) * fma(-0.5 * m2, r0 >= eps_rho ? ir0 : 1.0 / r0, u[4]) : DBL_MAX;
+    const double pq = node ? (g - 1.0) * fma(-0.5 * m2, ir0t, u[4]) : DBL_MAX;
     const double Sa = fma(0.5 * ma2, ira, fabs(a[4]));
     const double Smax = fmax(Sa, seg_max<SW>(Sq));
     const double pmin = seg_min<SW>(pq);
@@ -672,24 +676,13 @@ __global__ void k_ar_elem(const double* __restrict__ rho, const double* __restri
   const size_t Z = (size_t)M.K * mm * mm, N = (size_t)M.K * n2;
   const int ex = k % M.nx, ey = k / M.nx;
   double out[16];
-  // integrals with the exact magnetic product rules
-  double ix = 0.0, iy = 0.0, iz = 0.0;
-  for (int qy = 0; qy < q2; ++qy)
-    for (int qx = 0; qx < q2; ++qx) {
-      double w = M.Jdet * T->w2[qx] * T->w2[qy];
-      ix = fma(w, B_eval<KM>(B, Z, 0, ex, ey, T->L_2[qx], T->G_2[qx], T->M_2[qx], T->L_2[qy], T->G_2[qy], T->M_2[qy], M), ix);
-      iy = fma(w, B_eval<KM>(B, Z, 1, ex, ey, T->L_2[qx], T->G_2[qx], T->M_2[qx], T->L_2[qy], T->G_2[qy], T->M_2[qy], M), iy);
-    }
-  for (int qy = 0; qy < mm; ++qy)
-    for (int qx = 0; qx < mm; ++qx) {
-      double w = M.Jdet * T->wG[qx] * T->wG[qy];
-      double s = 0.0;
-      const double* Bz = B + 2 * Z + (size_t)k * mm * mm;
-      for (int b = 0; b < mm; ++b)
-        for (int a = 0; a < mm; ++a) s = fma(T->M_G[qx][a] * T->M_G[qy][b], Bz[b * mm + a], s);
-      iz = fma(w, s, iz);
-    }
-  out[0] = ix; out[1] = iy; out[2] = iz;
+  // exact element integrals: the integral of a nodal basis function is its
+  // quadrature weight (GLL(k+1) and Gauss(k) in the RT directions, GLL(k) for
+  // B_z), so B_eval with the weight rows in place of the interpolation rows is
+  // the integral over the reference element
+  out[0] = M.Jdet * B_eval<KM>(B, Z, 0, ex, ey, T->wL, T->wG, T->wM, T->wL, T->wG, T->wM, M);
+  out[1] = M.Jdet * B_eval<KM>(B, Z, 1, ex, ey, T->wL, T->wG, T->wM, T->wL, T->wG, T->wM, M);
+  out[2] = M.Jdet * B_eval<KM>(B, Z, 2, ex, ey, T->wL, T->wG, T->wM, T->wL, T->wG, T->wM, M);
   for (int d = 0; d < 3; ++d) {
     double mx = -DBL_MAX, mn = DBL_MAX;
     const double* A = B + d * Z + (size_t)k * mm * mm;
@@ -726,9 +719,8 @@ __global__ void k_ar_elem(const double* __restrict__ rho, const double* __restri
     double Bv[3];
     for (int d = 0; d < 3; ++d)
       Bv[d] = B_eval<KM>(B, Z, d, ex, ey, T->L_P[i], T->G_P[i], T->M_P[i], T->L_P[j], T->G_P[j], T->M_P[j], M);
-    double bn = sqrt(Bv[0] * Bv[0] + Bv[1] * Bv[1] + Bv[2] * Bv[2]);
-    double r = rho[(size_t)k * n2 + q];
-    double va = bn / sqrt(r);
+    double b2 = fma(Bv[0], Bv[0], fma(Bv[1], Bv[1], Bv[2] * Bv[2]));
+    double va = sqrt(b2 * rcp(rho[(size_t)k * n2 + q]));  // |B_h| / sqrt(rho)
     ax = fmax(ax, fabs(Y[N + (size_t)k * n2 + q]) + va);
     ay = fmax(ay, fabs(Y[2 * N + (size_t)k * n2 + q]) + va);
   }
