@@ -20,7 +20,7 @@ struct Prim {
 __device__ __forceinline__ Prim prim_of(const double U[5], double g) {
   Prim q;
   q.r = U[0];
-  const double ir = 1.0 / U[0];
+  const double ir = rcp(U[0]);
   q.u[0] = U[1] * ir; q.u[1] = U[2] * ir; q.u[2] = U[3] * ir;
   q.u2 = q.u[0] * q.u[0] + q.u[1] * q.u[1] + q.u[2] * q.u[2];
   q.p = (g - 1.0) * (U[4] - 0.5 * U[0] * q.u2);
@@ -31,7 +31,7 @@ __device__ __forceinline__ Prim prim_of(const double U[5], double g) {
 // accumulate into out (conservative adjoint).
 __device__ __forceinline__ void prim_adjoint(const Prim& q, double g, double gr, const double gu[3], double gp,
                                              double out[5]) {
-  const double ir = 1.0 / q.r;
+  const double ir = rcp(q.r);
   // p = (g-1)(E - |m|^2/(2 rho))
   out[4] += (g - 1.0) * gp;
   double dr = gr + (g - 1.0) * gp * 0.5 * q.u2;
@@ -105,7 +105,7 @@ __global__ void k_adj_face(const double* __restrict__ S, const double* __restric
   if (d == 0) { km = ey * M.nx + wrap(ex - 1, M.nx); qm = j * n + P; qp = j * n; }
   else { km = wrap(ey - 1, M.ny) * M.nx + ex; qm = P * n + j; qp = j; }
   double Um[5], Up[5], gF[5], dm[5] = {0, 0, 0, 0, 0}, dp[5] = {0, 0, 0, 0, 0};
-  const double f = 2.0 / ((d == 0 ? M.hx : M.hy) * T->wp[0]);
+  const double f = 2.0 * (d == 0 ? M.ihx : M.ihy) * (0.5 * P * (P + 1));  // 2 / (h w_0), w_0 = 2 / (p (p+1))
   for (int c = 0; c < 5; ++c) {
     Um[c] = S[c * N + (size_t)km * n2 + qm];
     Up[c] = S[c * N + (size_t)k * n2 + qp];
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(ACfg<P>::threads) k_adj_vol(const double* __re
   const bool valid = k < M.K;
   const int kk = valid ? k : M.K - 1;
   const size_t gi = (size_t)kk * n2 + q;
-  const double g = M.g, ig1 = 1.0 / (g - 1.0);
+  const double g = M.g, ig1 = M.ig1;
   double r0, u0[3], b0, u20;
   {
     double Us[5];
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(ACfg<P>::threads) k_adj_vol(const double* __re
     sp[4][tid] = b0; sp[5][tid] = u20; sp[6][tid] = log(r0); sp[7][tid] = log(b0);
   }
   __syncthreads();
-  const double cs[2] = {-4.0 / M.hx, -4.0 / M.hy};
+  const double cs[2] = {-4.0 * M.ihx, -4.0 * M.ihy};
 #pragma unroll
   for (int s = 0; s < P; ++s) {
     const int pidx = q + s * n2;
@@ -368,7 +368,7 @@ __global__ void k_adj_cons_to_prim(const double* __restrict__ U, const double* _
                                    const double* __restrict__ lamR, double* __restrict__ lamU, size_t N) {
   size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= N) return;
-  const double rho = U[q], ir = 1.0 / rho, E = U[4 * N + q];
+  const double rho = U[q], ir = rcp(rho), E = U[4 * N + q];
   const double m[3] = {U[N + q], U[2 * N + q], U[3 * N + q]};
   const double m2 = m[0] * m[0] + m[1] * m[1] + m[2] * m[2];
   const double le = lamY[q];
