@@ -77,3 +77,23 @@ def test_rejection_and_retry():
     assert st == 1 and nrej >= 1 and taken == dt / 2 ** nrej
     d = o.diagnostics()
     assert d["rho_min"] > 0 and d["p_min"] > 0
+
+
+def test_2d2v_states_stay_2d2v():
+    """On a 2D2V state (u_z = B_z = 0) the oracle's full Strang step, every
+    stabilisation map on, keeps m_z and B_z exactly zero: the out-of-plane
+    sources are products with those fields, so they vanish identically (§4:
+    the paper solves such configurations with the reduced system)."""
+    import numpy as np
+    from paper_2609_10849_b300 import workloads
+    from tests.util import oracle_state
+    o = oracle_state(workloads.orszag_tang(), 6, 5, 2, 2)
+    o.set_params(oe_hydro=1, oe_vel=1, pp=1, ar=1, C_eta=0.2, cfl=0.4)
+    U, _, _, Bz = o.get_state()
+    assert not np.any(U[3]) and not np.any(Bz)
+    dt = o.cfl_dt()
+    for _ in range(3):
+        assert o.strang_step(dt)[0] == 0
+    U, _, _, Bz = o.get_state()
+    assert not np.any(U[3]) and not np.any(Bz)
+    assert o.eta().max() > 0  # the A.R. acted, resistive terms included
