@@ -186,6 +186,13 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __r
   const double fx = 2.0 * M.ihx * w0i, fy = 2.0 * M.ihy * w0i;
   const int ex = kk % M.nx, ey = kk / M.nx;
   const size_t nf = (size_t)M.K * n;
+  // face terms as one FMA per direction in every lane: the coefficient is
+  // +-2/(h w_0) on the end nodes and 0 inside (0 * F* adds an exact zero), so
+  // no lane-divergent block is issued; end nodes keep the x-then-y order
+  const double cfx = i == 0 ? fx : (i == P ? -fx : 0.0);
+  const double cfy = j == 0 ? fy : (j == P ? -fy : 0.0);
+  const size_t ifx = (i == P ? (size_t)(ey * M.nx + wrap(ex + 1, M.nx)) : (size_t)kk) * n + j;
+  const size_t ify = (j == P ? (size_t)(wrap(ey + 1, M.ny) * M.nx + ex) : (size_t)kk) * n + i;
   double L[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
@@ -204,10 +211,8 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __r
     }
     double v = fma(cx, sx, cy * sy);
     // end nodes: -(2/hx)[-F*_left/w_0] and -(2/hx)[+F*_right/w_p] (w_p = w_0)
-    if (i == 0) v = fma(fx, Fx[c * nf + (size_t)kk * n + j], v);
-    if (i == P) v = fma(-fx, Fx[c * nf + (size_t)(ey * M.nx + wrap(ex + 1, M.nx)) * n + j], v);
-    if (j == 0) v = fma(fy, Fy[c * nf + (size_t)kk * n + i], v);
-    if (j == P) v = fma(-fy, Fy[c * nf + (size_t)(wrap(ey + 1, M.ny) * M.nx + ex) * n + i], v);
+    v = fma(cfx, Fx[c * nf + ifx], v);
+    v = fma(cfy, Fy[c * nf + ify], v);
     L[c] = v;
   }
 
