@@ -37,7 +37,7 @@ NOMINAL_FP64_TFLOPS = 1.25  # B300 dense FP64, nominal
 # does not read U^n), from the ncu capture summarised in
 # profiles/kvol_dram_orszag_tang_256.md (same kernel source as this bench); reset to None
 # whenever the volume kernel changes until it is captured again.
-K_VOL_TRAFFIC_BYTES = (63020032 + 7488768 + 104963840 + 16432640 + 104963840 + 7402496) / 3.0
+K_VOL_TRAFFIC_BYTES = (63016704 + 7692032 + 104972544 + 16648192 + 105055488 + 7912192) / 3.0
 # The stabilised benchmark workload: OE (both stages), positivity limiter, artificial
 # resistivity and velocity filter active, with the paper's constants.
 STAB = dict(oe_hydro=1, oe_vel=1, pp=1, ar=1, s_H=0.02, s_M=0.02, C_s=5.0, C_eta=0.2)
