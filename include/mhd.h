@@ -97,7 +97,10 @@ int mhd_create(const mhd_mesh_t* mesh, int p, int k, double gamma, mhd_ctx** out
 void mhd_destroy(mhd_ctx* ctx);
 
 /* Stabilisation parameters (default: all off, s_H = s_M = 0.02, C_s = 5,
- * C_eta = 0.2, cfl = 0.4, max_halvings = 20, strang_order = 0). */
+ * C_eta = 0.2, cfl = 0.4, max_halvings = 20, strang_order = 0,
+ * reduced_2d2v = 0).  A negative constant, cfl <= 0, max_halvings < 0 or a
+ * strang_order / reduced_2d2v outside {0, 1} is refused with MHD_EINVAL and
+ * the previous parameters stay in force. */
 int mhd_set_params(mhd_ctx* ctx, const mhd_params_t* prm);
 
 /* Stream on which all work of the context is enqueued (a cudaStream_t). */
