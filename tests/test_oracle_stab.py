@@ -154,3 +154,75 @@ def test_stabilised_vortex_ar_coefficient_table4():
     for _ in range(40):
         assert o.strang_step(0.025)[0] == 0
     assert o.eta().max() == pytest.approx(6.46e-2, rel=0.05)
+
+
+def _uniform_state(o, rho=1.0, u=(0.2, -0.1, 0.05), p=1.0, g=1.4):
+    U = np.zeros((5, o.K * o.n2))
+    U[0] = rho
+    for d in range(3):
+        U[1 + d] = rho * u[d]
+    U[4] = p / (g - 1.0) + 0.5 * rho * sum(v * v for v in u)
+    return U
+
+
+def test_pp_collapses_a_vacuum_element_to_its_average():
+    """Reading R9: an element whose average density is at most 64 eps is
+    replaced by its average in every component (the scaling has nothing to
+    scale towards)."""
+    rng = np.random.default_rng(41)
+    o = Oracle(3, 2, 2, 2, 1.4)
+    o.set_params(pp=1)
+    U = _uniform_state(o)
+    k = 4
+    sl = slice(k * o.n2, (k + 1) * o.n2)
+    U[:, sl] *= 1e-17  # average density 1e-17 < 64 eps
+    U[0, sl] *= 1.0 + 0.5 * rng.uniform(-1, 1, o.n2)
+    a = elem_avg(o, U)[:, k]
+    V = o.hydro_stage_map(U, 0.0)
+    for c in range(5):
+        assert np.all(V[c, sl] == V[c, sl][0])
+        assert abs(V[c, sl][0] - a[c]) <= 1e-12 * max(abs(a[c]), 1e-300)
+    other = np.ones(U.shape[1], bool)
+    other[sl] = False
+    np.testing.assert_array_equal(V[:, other], U[:, other])
+
+
+def test_pp_density_scaling_lands_on_the_floor():
+    """The density scaling (eq. euler-pp-density) is the largest one that keeps
+    every node at or above eps_rho = 64 eps: afterwards the smallest nodal
+    density of a limited element equals the floor (to rounding), the average is
+    kept, and the nodes keep their order."""
+    o = Oracle(2, 2, 3, 3, 1.4)
+    o.set_params(pp=1)
+    U = _uniform_state(o)
+    k = 1
+    sl = slice(k * o.n2, (k + 1) * o.n2)
+    rho = np.linspace(1.5, 0.5, o.n2)
+    rho[3] = -0.2  # one negative node, positive average
+    U[0, sl] = rho
+    U[1:4, sl] = 0.0
+    U[4, sl] = 5.0
+    a = elem_avg(o, U)[:, k]
+    V = o.hydro_stage_map(U, 0.0)
+    eps_rho = 64 * EPS
+    assert abs(V[0, sl].min() - eps_rho) <= 1e-12
+    assert abs(elem_avg(o, V)[0, k] - a[0]) <= 1e-14
+    assert np.array_equal(np.argsort(V[0, sl], kind="stable"), np.argsort(rho, kind="stable"))
+
+
+def test_inadmissible_average_is_rejected_and_restored():
+    """Reading R9 with R3: a negative element-average density makes every
+    halving of the step inadmissible; the step reports it and restores the
+    state."""
+    from oracle import INADMISSIBLE
+    o = Oracle(3, 3, 2, 2, 1.4)
+    o.set_params(pp=1, max_halvings=3)
+    U = _uniform_state(o)
+    U[0, 2 * o.n2:3 * o.n2] = -0.5
+    z = np.zeros(o.G)
+    o.set_state(U, z, z, np.zeros(o.Z))
+    before = [a.copy() for a in o.get_state()]
+    st, _, nrej = o.strang_step(1e-3)
+    assert st == INADMISSIBLE and nrej == 4
+    for a, b in zip(o.get_state(), before):
+        assert np.array_equal(a, b)
