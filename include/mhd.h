@@ -202,6 +202,17 @@ int mhd_substep(mhd_ctx* ctx, int which, double tau);
  * conservative state U [5][N] into L [5][N]. */
 int mhd_hydro_rhs(mhd_ctx* ctx, const double* U, double* L, int on_device);
 
+/* Test hook: the hydro stage map P = P_PP o P_OE (eqs. euler-oe-map and
+ * euler-pp-density/-pressure, §3.2.2-§3.2.3) of the enabled maps applied to a
+ * conservative state U [5][N] with stage length tau >= 0 (the OE factors
+ * D_l = exp(-s_H tau Theta_l)); the result goes to out [5][N] (host or
+ * device per on_device, may alias U).  No residual, no stage combination and
+ * no admissibility check: every element average must be admissible (rho > 0,
+ * p > 0), as it is for the candidates the substeps pass to the map.  The
+ * context's state is not touched; the map's activity bits are recorded as in a
+ * step (mhd_diag_t.stab_active). */
+int mhd_hydro_stage_map(mhd_ctx* ctx, const double* U, double tau, double* out, int on_device);
+
 /* Test hook: magnetic residual L_M (eq. magnetic-dae) of a primitive state
  * (rho, e [N], u [3][N], B in host layouts, eta [K]) into de [N], du [3][N],
  * dBx, dBy [G], dBz [Z]. */
@@ -295,9 +306,14 @@ int mhd_kernel_times(mhd_ctx* ctx, double* ms, long long* counts, int nclasses);
  * with MHD_EINVAL (p = 3: K <= 26,214 elements).  All calls share the array:
  * calls whose kernels overlap on the GPU race and must be serialised by the
  * caller.  Nothing in it needs to start at zero (each call writes what it
- * reads first).  Set-up: the first call on a device looks up the array's
- * device address and uploads the 1D tables for degree p (synchronous copies
- * to device symbols); make that first call before any stream capture.
+ * reads first).  Set-up: every call looks up the array's device address in
+ * the current context (a cheap runtime query, so the address never goes stale
+ * after cudaDeviceReset); the first call in a context also uploads the 1D
+ * tables for degree p (synchronous copies to device symbols, repeated in a
+ * context created after a reset).  Make that first call before any stream
+ * capture.  U and L must be distinct, non-overlapping buffers of exactly
+ * 5 K (p+1)^2 doubles on the current device: the call cannot check this, and
+ * the Python binding does so before calling.
  * Errors: MHD_EINVAL, MHD_ECUDA (message in mhd_last_error). */
 int mhd_hydro_rhs_static(const mhd_mesh_t* mesh, int p, double gamma, const double* U, double* L, void* stream);
 
@@ -305,6 +321,14 @@ int mhd_hydro_rhs_static(const mhd_mesh_t* mesh, int p, double gamma, const doub
  * of the current device in TFLOP/s (FMA = 2 flops), from a probe kernel with
  * every lane active.  Allocates and frees a small buffer. */
 int mhd_fp64_peak(double* tflops);
+
+/* Test hook (no counterpart in the paper): y[i] = the library's FP64
+ * reciprocal of x[i] for n device doubles, enqueued on `stream` without
+ * synchronising.  The kernels use this reciprocal (the PTX seed
+ * rcp.approx.ftz.f64 refined by one cubic Newton step) in place of division
+ * for densities, pressures and their sums; it is specified for normal |x| in
+ * [2^-1000, 2^1000].  Errors: MHD_EINVAL, MHD_ECUDA. */
+int mhd_rcp_check(const double* x, double* y, long long n, void* stream);
 
 const char* mhd_status_string(int status);
 const char* mhd_last_error(void);

@@ -843,6 +843,20 @@ int mhd_hydro_rhs(mhd_ctx* c, const double* U, double* L, int on_device) {
   return MHD_OK;
 }
 
+int mhd_hydro_stage_map(mhd_ctx* c, const double* U, double tau, double* out, int on_device) {
+  if (!c || !U || !out) return fail(MHD_EINVAL, "null argument");
+  if (!(tau >= 0.0) || !std::isfinite(tau)) return fail(MHD_EINVAL, "tau must be finite and >= 0");
+  cudaError_t e;
+  if ((e = copy_in(c, c->S1, U, 5 * c->N, on_device)) != cudaSuccess) return cuda_fail(e, "U");
+  cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->st);
+  set_scalar(c->dt, tau, c->st);
+  stab_hydro(c->p, c->S1, c->status, c->T, c->M, c->prm, c->dt, 1.0, c->work, nullptr, c->st);
+  c->launches += 1 + (c->prm.oe_hydro ? 4 : 1);
+  if ((e = copy_out(c, out, c->S1, 5 * c->N, on_device)) != cudaSuccess) return cuda_fail(e, "out");
+  if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(e, "hydro_stage_map");
+  return MHD_OK;
+}
+
 int mhd_mag_rhs(mhd_ctx* c, const double* rho, const double* e_, const double* u, const double* Bx, const double* By,
                 const double* Bz, const double* eta, double* de, double* du, double* dBx, double* dBy, double* dBz,
                 int on_device) {

@@ -371,3 +371,33 @@ extern "C" int mhd_fp64_peak(double* tflops) {
   *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3) / 1e12;
   return 0;
 }
+
+// ---- test hook: the library's refined reciprocal on caller data ---------------
+namespace mhd {
+void set_error_message(const char* msg);
+__global__ void k_rcp_check(const double* __restrict__ x, double* __restrict__ y, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = rcp(x[i]);
+}
+}  // namespace mhd
+
+extern "C" int mhd_rcp_check(const double* x, double* y, long long n, void* stream) {
+  if (!x || !y || n < 0) {
+    mhd::set_error_message("null argument or negative length");
+    return -1;
+  }
+  if (n == 0) return 0;
+  const int th = 256;
+  const long long blocks = (n + th - 1) / th;
+  if (blocks > 0x7fffffffLL) {
+    mhd::set_error_message("length too large for one launch");
+    return -1;
+  }
+  mhd::k_rcp_check<<<(unsigned)blocks, th, 0, (cudaStream_t)stream>>>(x, y, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    mhd::set_error_message(cudaGetErrorString(e));
+    return -3;
+  }
+  return 0;
+}

@@ -15,7 +15,6 @@
 // residual reads is written by the same call first, so nothing in the array
 // has to start at zero and stale contents from an earlier call are harmless.
 #include <cstdio>
-#include <mutex>
 
 #include "../../include/mhd.h"
 #include "mhd_internal.cuh"
@@ -42,30 +41,19 @@ int static_fail(int code) {
   return code;
 }
 
-// Device address of g_static_scratch, looked up once per device with that
-// device current.
+// Device address of g_static_scratch in the current context.  Looked up on
+// every call (a cheap runtime query): a cached address would dangle after
+// cudaDeviceReset() or in a new primary context.
 double* static_scratch_ptr(int* code) {
-  static std::mutex mu;
-  static double* ptrs[64] = {};
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
-    snprintf(g_static_err, sizeof g_static_err, "no usable current device");
+  double* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress((void**)&p, g_static_scratch);
+  if (e != cudaSuccess || !p) {
+    snprintf(g_static_err, sizeof g_static_err, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
     *code = static_fail(MHD_ECUDA);
     return nullptr;
   }
-  std::lock_guard<std::mutex> lock(mu);
-  if (!ptrs[dev]) {
-    double* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress((void**)&p, g_static_scratch);
-    if (e != cudaSuccess || !p) {
-      snprintf(g_static_err, sizeof g_static_err, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-      *code = static_fail(MHD_ECUDA);
-      return nullptr;
-    }
-    ptrs[dev] = p;
-  }
   *code = MHD_OK;
-  return ptrs[dev];
+  return p;
 }
 }  // namespace
 

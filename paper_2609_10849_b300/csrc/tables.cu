@@ -9,6 +9,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "mhd_internal.cuh"
 
 namespace mhd {
@@ -296,9 +298,36 @@ int table_slot(int p, int k) {
 __device__ Tab g_tables[8];
 void upload_mag_tables(int slot, const Tab* h, cudaError_t* err);  // constant-memory copy (magnetic.cu)
 
+// Unique id of the current CUDA context (cuCtxGetId, fetched through the
+// runtime's driver entry points so the library does not link libcuda), or 0
+// where the driver cannot tell.  Keys the upload cache below: a context made
+// after cudaDeviceReset() has fresh, empty device symbols and a new id.
+static unsigned long long current_context_id() {
+  typedef CUresult (*get_current_t)(CUcontext*);
+  typedef CUresult (*get_id_t)(CUcontext, unsigned long long*);
+  static get_current_t get_current = nullptr;
+  static get_id_t get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&get_current, 12000, cudaEnableDefault, &q1) !=
+            cudaSuccess || q1 != cudaDriverEntryPointSuccess)
+      get_current = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&get_id, 12000, cudaEnableDefault, &q2) !=
+            cudaSuccess || q2 != cudaDriverEntryPointSuccess)
+      get_id = nullptr;
+    looked_up = true;
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
 const Tab* device_tables(int p, int k, cudaError_t* err) {
   static std::mutex mu;
-  static bool filled[64][8] = {};
+  static unsigned long long filled_ctx[64][8] = {};  // context id the slot was uploaded in (0: never)
   int slot = table_slot(p, k);
   *err = cudaSuccess;
   if (slot < 0) { *err = cudaErrorInvalidValue; return nullptr; }
@@ -306,16 +335,18 @@ const Tab* device_tables(int p, int k, cudaError_t* err) {
   if ((*err = cudaGetDevice(&dev)) != cudaSuccess) return nullptr;
   std::lock_guard<std::mutex> lock(mu);
   if (dev < 0 || dev >= 64) { *err = cudaErrorInvalidDevice; return nullptr; }
-  if (!filled[dev][slot]) {
+  void* base = nullptr;  // also initialises the context, so its id is defined below
+  if ((*err = cudaGetSymbolAddress(&base, g_tables)) != cudaSuccess) return nullptr;
+  const unsigned long long ctx = current_context_id();
+  const unsigned long long key = ctx ? ctx : ~0ull;  // no id: one upload per device
+  if (filled_ctx[dev][slot] != key) {
     Tab h;
     host_tables(p, k, &h);
     if ((*err = cudaMemcpyToSymbol(g_tables, &h, sizeof(Tab), slot * sizeof(Tab))) != cudaSuccess) return nullptr;
     upload_mag_tables(slot, &h, err);
     if (*err != cudaSuccess) return nullptr;
-    filled[dev][slot] = true;
+    filled_ctx[dev][slot] = key;
   }
-  void* base = nullptr;
-  if ((*err = cudaGetSymbolAddress(&base, g_tables)) != cudaSuccess) return nullptr;
   return reinterpret_cast<const Tab*>(base) + slot;
 }
 

@@ -65,6 +65,8 @@ _SIGS = {
     "mhd_substep": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
     "mhd_hydro_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "mhd_mag_rhs": (C.c_int, [C.c_void_p] + [C.c_void_p] * 12 + [C.c_int]),
+    "mhd_hydro_stage_map": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_int]),
+    "mhd_rcp_check": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
     "mhd_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(Diag)]),
     "mhd_get_eta": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mhd_launch_count": (C.c_longlong, [C.c_void_p]),
@@ -143,15 +145,50 @@ def fp64_peak_tflops():
     return v.value
 
 
+def rcp_check(x, y, stream=0):
+    """y = the library's FP64 reciprocal of the CUDA tensor x (test hook)."""
+    for t in (x, y):
+        if not (t.is_cuda and str(t.dtype) == "torch.float64" and t.is_contiguous()):
+            raise ValueError("x and y must be contiguous float64 CUDA tensors")
+    if x.numel() != y.numel() or x.device != y.device:
+        raise ValueError("x and y must have equal size and device")
+    _check(lib().mhd_rcp_check(C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.numel(), C.c_void_p(stream)))
+
+
+def _static_args(nx, ny, p, U, L):
+    """Refuse, before anything reaches the library, what the C entry point
+    cannot check itself: the C call sees bare device pointers, so a tensor
+    shorter than the mesh, one on another GPU than the current one, or an
+    output that overlaps the input would make its kernels read or write
+    outside the caller's buffers (or break their no-alias contract)."""
+    need = 5 * int(nx) * int(ny) * (int(p) + 1) ** 2
+    for name, t in (("U", U), ("L", L)):
+        if not hasattr(t, "data_ptr"):
+            raise ValueError(f"{name} must be a torch tensor")
+        if str(t.dtype) != "torch.float64" or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float64 tensor")
+        if t.numel() != need:
+            raise ValueError(f"{name} has {t.numel()} entries; the mesh needs 5 K (p+1)^2 = {need}")
+    u0, l0 = U.data_ptr(), L.data_ptr()
+    if u0 < l0 + 8 * need and l0 < u0 + 8 * need:
+        raise ValueError("L must not overlap U")
+    if not (U.is_cuda and L.is_cuda):
+        raise ValueError("U and L must be CUDA tensors")
+    import torch
+    cur = torch.cuda.current_device()
+    if U.device.index != cur or L.device.index != cur:
+        raise ValueError(f"U and L must be on the current device cuda:{cur}")
+
+
 def hydro_rhs_static(nx, ny, p, gamma, domain, U, L, stream=0):
     """Hydro residual of the device tensor U [5, K (p+1)^2] into the device
     tensor L without any device allocation (fixed library scratch; calls that
-    overlap on the GPU race).  Enqueued on `stream`; does not synchronise."""
+    overlap on the GPU race).  Enqueued on `stream`; does not synchronise.
+    Sizes, device and aliasing are checked here first (ValueError)."""
+    _static_args(nx, ny, p, U, L)
     mesh = Mesh(nx, ny, *(float(v) for v in domain))
-    (pu, pl), dev = _ptrs(U, L)
-    if not dev:
-        raise ValueError("U and L must be device tensors")
-    _check(lib().mhd_hydro_rhs_static(C.byref(mesh), p, float(gamma), pu, pl, C.c_void_p(stream)))
+    _check(lib().mhd_hydro_rhs_static(C.byref(mesh), p, float(gamma), C.c_void_p(U.data_ptr()),
+                                      C.c_void_p(L.data_ptr()), C.c_void_p(stream)))
 
 
 class Solver:
@@ -256,6 +293,13 @@ class Solver:
         L = np.zeros_like(U)
         _check(lib().mhd_hydro_rhs(self._h, _ptr(U)[0], _ptr(L)[0], 0))
         return L
+
+    def hydro_stage_map(self, U, tau):
+        """Stage map P = P_PP o P_OE of the enabled maps on a conservative state."""
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        out = np.zeros_like(U)
+        _check(lib().mhd_hydro_stage_map(self._h, _ptr(U)[0], float(tau), _ptr(out)[0], 0))
+        return out
 
     def mag_rhs(self, rho, e, u, Bx, By, Bz, eta=None):
         f = lambda a: np.ascontiguousarray(a, dtype=np.float64)

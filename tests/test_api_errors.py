@@ -43,6 +43,40 @@ def test_batch_create_rejects_no_runs():
         Batch([])
 
 
+def test_static_residual_wrapper_refuses_bad_buffers_before_the_library(monkeypatch):
+    """The allocation-free residual's C entry point sees bare device pointers
+    and cannot check their extent, device or overlap; the binding refuses a
+    tensor of the wrong size, an output that overlaps the input and tensors
+    that are not on the current CUDA device before anything reaches the
+    library (CPU: the library must not be touched at all)."""
+    import torch
+    from paper_2609_10849_b300 import mhd
+
+    def no_library():
+        raise AssertionError("the library was called")
+
+    monkeypatch.setattr(mhd, "lib", no_library)
+    nx, ny, p = 3, 2, 2
+    need = 5 * nx * ny * (p + 1) ** 2
+    dom = (0.0, 1.0, 0.0, 1.0)
+    good = torch.zeros(need, dtype=torch.float64)
+    with pytest.raises(ValueError, match="entries"):
+        mhd.hydro_rhs_static(nx, ny, p, 1.4, dom, torch.zeros(need - 1, dtype=torch.float64), good)
+    with pytest.raises(ValueError, match="entries"):
+        mhd.hydro_rhs_static(nx, ny, p, 1.4, dom, good, torch.zeros(need + 5, dtype=torch.float64))
+    with pytest.raises(ValueError, match="float64"):
+        mhd.hydro_rhs_static(nx, ny, p, 1.4, dom, good.float(), good.clone())
+    with pytest.raises(ValueError, match="overlap"):
+        mhd.hydro_rhs_static(nx, ny, p, 1.4, dom, good, good)
+    big = torch.zeros(2 * need, dtype=torch.float64)
+    with pytest.raises(ValueError, match="overlap"):
+        mhd.hydro_rhs_static(nx, ny, p, 1.4, dom, big[:need], big[need // 2:need // 2 + need])
+    with pytest.raises(ValueError, match="CUDA"):
+        mhd.hydro_rhs_static(nx, ny, p, 1.4, dom, good, good.clone())
+    with pytest.raises(ValueError, match="torch tensor"):
+        mhd.hydro_rhs_static(nx, ny, p, 1.4, dom, np.zeros(need), good)
+
+
 def _small():
     wl = workloads.orszag_tang()
     s = Solver(4, 3, 2, 2, wl["gamma"], wl["domain"])

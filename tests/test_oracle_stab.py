@@ -226,3 +226,36 @@ def test_inadmissible_average_is_rejected_and_restored():
     assert st == INADMISSIBLE and nrej == 4
     for a, b in zip(o.get_state(), before):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("C_s", [5.0, 2.0])
+def test_ar_coefficient_unsaturated_staircase(C_s):
+    """The A.R. coefficient (eqs. magnetic-ar-sensor, magnetic-ar-coefficient)
+    worked out by hand on a state where the sensor response is below 1.
+
+    Mesh 21 x 1 on [0, 2.1] x [0, 0.5] (h_x = 0.1, h_y = 0.5), rho = 2,
+    u = (0.3, -0.1, 0), in-plane B = 0 and B_z = b + c e_x constant on element
+    e_x (V_h^m is discontinuous).  Then Delta_Omega(B_z) = c (N - 1)/2 and the
+    only tangential jumps are those of B_z across x-faces: c on each face of an
+    inner element, so J_0 = 2c and sigma^B_x = 2/(N - 1); the y-direction
+    jumps vanish (one element row, periodic).  With
+    a_x = |u_x| + |B_z|/sqrt(rho) the inner elements get
+    eta_K = C_eta h_x/(2p + 1) a_x min(C_s 2/(N - 1), 1), and the two
+    elements beside the periodic seam (jump c (N - 1)) are saturated, R = 1.
+    A factor in sigma, C_s, h or 2p + 1 fails this."""
+    N, p, b, c, rho0, ux = 21, 2, 0.3, 0.05, 2.0, 0.3
+    o = Oracle(N, 1, p, p, 5 / 3, (0.0, 2.1, 0.0, 0.5))
+    o.set_params(ar=1, C_eta=0.2, C_s=C_s)
+    rho = np.full(o.K * o.n2, rho0)
+    u = np.zeros((3, o.K * o.n2))
+    u[0], u[1] = ux, -0.1
+    Bx, By = o.b_from_potential(np.zeros(o.G))
+    bz_el = b + c * np.arange(N)
+    Bz = np.repeat(bz_el, o.mm * o.mm)
+    eta = o.ar_coefficient(rho, u, Bx, By, Bz)
+    a_x = ux + bz_el / np.sqrt(rho0)
+    R = np.full(N, min(C_s * 2.0 / (N - 1), 1.0))
+    R[0] = R[-1] = 1.0
+    want = 0.2 * 0.1 / (2 * p + 1) * a_x * R
+    assert R[1] < 1.0
+    np.testing.assert_allclose(eta, want, rtol=1e-13)
