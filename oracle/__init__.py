@@ -26,15 +26,19 @@ _INC = os.path.join(_HERE, "mhd_oracle_stab.inc")
 _DUAL = os.path.join(_HERE, "dual.h")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _LIB_T = os.path.join(_HERE, "liboracle_tangent.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
 
 OK, RETRIED, REJECT, INADMISSIBLE = 0, 1, -10, -11
 
 
 def build(force: bool = False) -> str:
-    """Compile liboracle.so (plain -O2, no FMA contraction) and its forward-mode
-    tangent build liboracle_tangent.so (same source, dual-number scalar) if
-    they are stale."""
-    for out, extra in ((_LIB, []), (_LIB_T, ["-DORACLE_TANGENT"])):
+    """Compile liboracle.so (plain -O2, no FMA contraction), its forward-mode
+    tangent build liboracle_tangent.so (same source, dual-number scalar) and
+    the OpenMP timing build liboracle_omp.so (same source and flags plus
+    -fopenmp: independent element loops on threads, every sum in its serial
+    order, so its results equal the plain build's bit for bit) if they are
+    stale."""
+    for out, extra in ((_LIB, []), (_LIB_T, ["-DORACLE_TANGENT"]), (_LIB_OMP, ["-fopenmp"])):
         stale = force or not os.path.exists(out) or any(
             os.path.getmtime(s) > os.path.getmtime(out) for s in (_SRC, _INC, _DUAL))
         if stale:
@@ -46,6 +50,7 @@ def build(force: bool = False) -> str:
 
 _lib = None
 _lib_t = None
+_lib_omp = None
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 
 
@@ -91,6 +96,8 @@ def _load(path):
     L.or_vel_oe.argtypes = [C.c_void_p] + [_dp] * 6 + [C.c_double]
     L.or_set_frozen.argtypes = [C.c_void_p, C.c_int]
     L.or_set_strang_order.argtypes = [C.c_void_p, C.c_int]
+    L.or_threads.argtypes = [C.c_int]
+    L.or_threads.restype = C.c_int
     return L
 
 
@@ -114,6 +121,15 @@ def tangent_lib():
         L.or_mag_rhs_tangent.argtypes = [C.c_void_p] + [_dp] * 23
         _lib_t = L
     return _lib_t
+
+
+def omp_lib():
+    """The OpenMP timing build (results bitwise equal to :func:`lib`'s)."""
+    global _lib_omp
+    if _lib_omp is None:
+        build()
+        _lib_omp = _load(_LIB_OMP)
+    return _lib_omp
 
 
 def rule(kind: str, r: int):
@@ -331,6 +347,20 @@ class Oracle:
         v, X, Y, W = (np.zeros(size) for _ in range(4))
         self._L.or_sample(self._h, self.FIELDS[field], nq, v, X, Y, W)
         return v, X, Y, W
+
+
+class ParallelOracle(Oracle):
+    """The oracle's OpenMP timing build: the same arithmetic with independent
+    element loops spread over threads (``set_threads``); used to time the CPU
+    baseline on all cores.  Results equal :class:`Oracle`'s bit for bit."""
+
+    @staticmethod
+    def _library():
+        return omp_lib()
+
+    def set_threads(self, n):
+        """Set the thread count (n > 0); returns the count in force."""
+        return self._L.or_threads(int(n))
 
 
 class Tangent(Oracle):

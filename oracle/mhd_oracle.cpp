@@ -29,6 +29,10 @@
 #include <cstring>
 #include <vector>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #ifdef ORACLE_TANGENT
 // Forward-mode tangent build (liboracle_tangent.so): the same source with the
 // scalar type replaced by a dual number; the values it computes are those of
@@ -313,6 +317,7 @@ struct Oracle {
   }
 
   void hydro_rhs(const vec* S, vec* L) const {
+#pragma omp parallel for collapse(2) schedule(static)
     for (int ey = 0; ey < ny; ++ey)
       for (int ex = 0; ex < nx; ++ex) {
         int k = kid(ex, ey);
@@ -409,65 +414,91 @@ struct Oracle {
   // Current J_h from the weak curl (eq. mag-current-proj): lumped A-product
   // (eq. aux-inner-product) on the left, exact magnetic product
   // (eq. magnetic-inner-product) on the right, assembled over the elements.
+  // The element loads are independent (the OpenMP timing build spreads them
+  // over threads); the assembly adds them in element order, so every build
+  // gives the same sums bit for bit.
   void compute_J(const vec& bX, const vec& bY, const vec& bZ, vec& Jx, vec& Jy, vec& Jz) const {
     size_t G = (size_t)NX * NY;
     vec lx(G, 0.0), ly(G, 0.0), lz(G, 0.0), mx(G, 0.0), my(G, 0.0), mz(G, 0.0);
-    std::vector<real> bx(mL * mm), by(mm * mL);
+    const size_t nW = (size_t)mL * mL, nNx = (size_t)mL * mm, nNy = (size_t)mm * mL;
+    vec LW((size_t)K * nW), LNx((size_t)K * nNx), LNy((size_t)K * nNy);
+#pragma omp parallel
+    {
+      std::vector<real> bx(mL * mm), by(mm * mL);
+      std::vector<real> bxq(mL * mL), byq(mL * mL), bzq(mm * mm);
+      std::vector<real> Lq(mL * mL), dLq(mL * mL);
+#pragma omp for collapse(2) schedule(static)
+      for (int ey = 0; ey < ny; ++ey)
+        for (int ex = 0; ex < nx; ++ex) {
+          int k = kid(ex, ey);
+          clX(bX, ex, ey, bx.data()); clY(bY, ex, ey, by.data());
+          const real* bz = &bZ[(size_t)k * mm * mm];
+          // W block: (J_z, phi)_W = (B_x, d_y phi)_B - (B_y, d_x phi)_B
+          for (int qy = 0; qy < mL; ++qy)
+            for (int qx = 0; qx < mL; ++qx) {
+              bxq[qy * mL + qx] = evX(bx.data(), z2[qx], z2[qy]);
+              byq[qy * mL + qx] = evY(by.data(), z2[qx], z2[qy]);
+            }
+          for (int qy = 0; qy < mm; ++qy)
+            for (int qx = 0; qx < mm; ++qx) bzq[qy * mm + qx] = evZ(bz, zG[qx], zG[qy]);
+          // GLL(m+1) basis and derivative at the Gauss(m+2) points
+          for (int a = 0; a < mL; ++a)
+            for (int q = 0; q < mL; ++q) { Lq[a * mL + q] = lag(xL, a, z2[q]); dLq[a * mL + q] = dlag(xL, a, z2[q]); }
+          for (int b = 0; b < mL; ++b)
+            for (int a = 0; a < mL; ++a) {
+              real s = 0.0;
+              for (int qy = 0; qy < mL; ++qy)
+                for (int qx = 0; qx < mL; ++qx) {
+                  real dyphi = (2.0 / hy) * Lq[a * mL + qx] * dLq[b * mL + qy];
+                  real dxphi = (2.0 / hx) * dLq[a * mL + qx] * Lq[b * mL + qy];
+                  s += Jdet * w2[qx] * w2[qy] * (bxq[qy * mL + qx] * dyphi - byq[qy * mL + qx] * dxphi);
+                }
+              LW[k * nW + b * mL + a] = s;
+            }
+          // N block, x-component: DOF g_a(x) l_b(y) e_x; (J_x, phi)_N = (B_z, -d_y phi)_B
+          for (int b = 0; b < mL; ++b)
+            for (int a = 0; a < mm; ++a) {
+              real s = 0.0;
+              for (int qy = 0; qy < mm; ++qy)
+                for (int qx = 0; qx < mm; ++qx) {
+                  real X = zG[qx], Y = zG[qy];
+                  real dyphi = (2.0 / hy) * lag(zG, a, X) * dlag(xL, b, Y);
+                  s += Jdet * wG[qx] * wG[qy] * bzq[qy * mm + qx] * (-dyphi);
+                }
+              LNx[k * nNx + b * mm + a] = s;
+            }
+          // N block, y-component: DOF l_a(x) g_b(y) e_y; (J_y, phi)_N = (B_z, d_x phi)_B
+          for (int b = 0; b < mm; ++b)
+            for (int a = 0; a < mL; ++a) {
+              real s = 0.0;
+              for (int qy = 0; qy < mm; ++qy)
+                for (int qx = 0; qx < mm; ++qx) {
+                  real X = zG[qx], Y = zG[qy];
+                  real dxphi = (2.0 / hx) * dlag(xL, a, X) * lag(zG, b, Y);
+                  s += Jdet * wG[qx] * wG[qy] * bzq[qy * mm + qx] * dxphi;
+                }
+              LNy[k * nNy + b * mL + a] = s;
+            }
+        }
+    }
+    // assembly over the elements sharing each DOF (element order)
     for (int ey = 0; ey < ny; ++ey)
       for (int ex = 0; ex < nx; ++ex) {
-        int k = kid(ex, ey);
-        clX(bX, ex, ey, bx.data()); clY(bY, ex, ey, by.data());
-        const real* bz = &bZ[(size_t)k * mm * mm];
-        // W block: (J_z, phi)_W = (B_x, d_y phi)_B - (B_y, d_x phi)_B
-        std::vector<real> bxq(mL * mL), byq(mL * mL), bzq(mm * mm);
-        for (int qy = 0; qy < mL; ++qy)
-          for (int qx = 0; qx < mL; ++qx) {
-            bxq[qy * mL + qx] = evX(bx.data(), z2[qx], z2[qy]);
-            byq[qy * mL + qx] = evY(by.data(), z2[qx], z2[qy]);
-          }
-        for (int qy = 0; qy < mm; ++qy)
-          for (int qx = 0; qx < mm; ++qx) bzq[qy * mm + qx] = evZ(bz, zG[qx], zG[qy]);
-        // GLL(m+1) basis and derivative at the Gauss(m+2) points
-        std::vector<real> Lq(mL * mL), dLq(mL * mL);
-        for (int a = 0; a < mL; ++a)
-          for (int q = 0; q < mL; ++q) { Lq[a * mL + q] = lag(xL, a, z2[q]); dLq[a * mL + q] = dlag(xL, a, z2[q]); }
+        size_t k = (size_t)kid(ex, ey);
         for (int b = 0; b < mL; ++b)
           for (int a = 0; a < mL; ++a) {
-            real s = 0.0;
-            for (int qy = 0; qy < mL; ++qy)
-              for (int qx = 0; qx < mL; ++qx) {
-                real dyphi = (2.0 / hy) * Lq[a * mL + qx] * dLq[b * mL + qy];
-                real dxphi = (2.0 / hx) * dLq[a * mL + qx] * Lq[b * mL + qy];
-                s += Jdet * w2[qx] * w2[qy] * (bxq[qy * mL + qx] * dyphi - byq[qy * mL + qx] * dxphi);
-              }
             size_t gi = gidx(ex * mm + a, ey * mm + b);
-            lz[gi] += s; mz[gi] += Jdet * wL[a] * wL[b];
+            lz[gi] += LW[k * nW + b * mL + a]; mz[gi] += Jdet * wL[a] * wL[b];
           }
-        // N block, x-component: DOF g_a(x) l_b(y) e_x; (J_x, phi)_N = (B_z, -d_y phi)_B
         for (int b = 0; b < mL; ++b)
           for (int a = 0; a < mm; ++a) {
-            real s = 0.0;
-            for (int qy = 0; qy < mm; ++qy)
-              for (int qx = 0; qx < mm; ++qx) {
-                real X = zG[qx], Y = zG[qy];
-                real dyphi = (2.0 / hy) * lag(zG, a, X) * dlag(xL, b, Y);
-                s += Jdet * wG[qx] * wG[qy] * bzq[qy * mm + qx] * (-dyphi);
-              }
             size_t gi = gidx(ex * mm + a, ey * mm + b);
-            lx[gi] += s; mx[gi] += Jdet * wG[a] * wL[b];
+            lx[gi] += LNx[k * nNx + b * mm + a]; mx[gi] += Jdet * wG[a] * wL[b];
           }
-        // N block, y-component: DOF l_a(x) g_b(y) e_y; (J_y, phi)_N = (B_z, d_x phi)_B
         for (int b = 0; b < mm; ++b)
           for (int a = 0; a < mL; ++a) {
-            real s = 0.0;
-            for (int qy = 0; qy < mm; ++qy)
-              for (int qx = 0; qx < mm; ++qx) {
-                real X = zG[qx], Y = zG[qy];
-                real dxphi = (2.0 / hx) * dlag(xL, a, X) * lag(zG, b, Y);
-                s += Jdet * wG[qx] * wG[qy] * bzq[qy * mm + qx] * dxphi;
-              }
             size_t gi = gidx(ex * mm + a, ey * mm + b);
-            ly[gi] += s; my[gi] += Jdet * wL[a] * wG[b];
+            ly[gi] += LNy[k * nNy + b * mL + a]; my[gi] += Jdet * wL[a] * wG[b];
           }
       }
     Jx.assign(G, 0.0); Jy.assign(G, 0.0); Jz.assign(G, 0.0);
@@ -482,81 +513,105 @@ struct Oracle {
                  const vec& Jx, const vec& Jy, const vec& Jz, vec& Ex, vec& Ey, vec& Ez) const {
     size_t G = (size_t)NX * NY;
     vec lx(G, 0.0), ly(G, 0.0), lz(G, 0.0), mx(G, 0.0), my(G, 0.0), mz(G, 0.0);
-    std::vector<real> bx(mL * mm), by(mm * mL), jx(mm * mL), jy(mL * mm), jz(mL * mL);
+    // element loads (independent; spread over threads in the OpenMP timing
+    // build), then the assembly in element order as for J_h
+    const size_t nNx = (size_t)mL * mm, nNy = (size_t)mm * mL, nW = (size_t)mL * mL;
+    vec LNx((size_t)K * nNx), LNy((size_t)K * nNy), LW((size_t)K * nW);
+#pragma omp parallel
+    {
+      std::vector<real> bx(mL * mm), by(mm * mL), jx(mm * mL), jy(mL * mm), jz(mL * mL);
+#pragma omp for collapse(2) schedule(static)
+      for (int ey = 0; ey < ny; ++ey)
+        for (int ex = 0; ex < nx; ++ex) {
+          int k = kid(ex, ey);
+          clX(bX, ex, ey, bx.data()); clY(bY, ex, ey, by.data());
+          clY(Jx, ex, ey, jx.data()); clX(Jy, ex, ey, jy.data()); clW(Jz, ex, ey, jz.data());
+          const real* bz = &bZ[(size_t)k * mm * mm];
+          const real* ux = &u[0][(size_t)k * n2];
+          const real* uy = &u[1][(size_t)k * n2];
+          const real* uz = &u[2][(size_t)k * n2];
+          real ek = etaK[k];
+          // resistive field J_h at the DG-GLL(p) nodes of this element
+          std::vector<real> Jq(3 * n2);
+          for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+              Jq[0 * n2 + j * n + i] = evY(jx.data(), xp[i], xp[j]);
+              Jq[1 * n2 + j * n + i] = evX(jy.data(), xp[i], xp[j]);
+              Jq[2 * n2 + j * n + i] = evW(jz.data(), xp[i], xp[j]);
+            }
+          // x-component at N_x nodes (zeta_a, xi^L_b)
+          for (int b = 0; b < mL; ++b)
+            for (int a = 0; a < mm; ++a) {
+              real X = zG[a], Y = xL[b], B[3];
+              B_at(bx.data(), by.data(), bz, X, Y, B);
+              real vy = evDG(uy, X, Y), vz = evDG(uz, X, Y);
+              real val = -(vy * B[2] - vz * B[1]);
+              real w = Jdet * wG[a] * wL[b];
+              real load = w * val;
+              if (ek != 0.0) {
+                real r = 0.0;
+                for (int j = 0; j < n; ++j)
+                  for (int i = 0; i < n; ++i)
+                    r += Jdet * wp[i] * wp[j] * Jq[0 * n2 + j * n + i] * lag(zG, a, xp[i]) * lag(xL, b, xp[j]);
+                load += ek * r;
+              }
+              LNx[k * nNx + b * mm + a] = load;
+            }
+          // y-component at N_y nodes (xi^L_a, zeta_b)
+          for (int b = 0; b < mm; ++b)
+            for (int a = 0; a < mL; ++a) {
+              real X = xL[a], Y = zG[b], B[3];
+              B_at(bx.data(), by.data(), bz, X, Y, B);
+              real vx = evDG(ux, X, Y), vz = evDG(uz, X, Y);
+              real val = -(vz * B[0] - vx * B[2]);
+              real w = Jdet * wL[a] * wG[b];
+              real load = w * val;
+              if (ek != 0.0) {
+                real r = 0.0;
+                for (int j = 0; j < n; ++j)
+                  for (int i = 0; i < n; ++i)
+                    r += Jdet * wp[i] * wp[j] * Jq[1 * n2 + j * n + i] * lag(xL, a, xp[i]) * lag(zG, b, xp[j]);
+                load += ek * r;
+              }
+              LNy[k * nNy + b * mL + a] = load;
+            }
+          // z-component at W nodes (xi^L_a, xi^L_b)
+          for (int b = 0; b < mL; ++b)
+            for (int a = 0; a < mL; ++a) {
+              real X = xL[a], Y = xL[b], B[3];
+              B_at(bx.data(), by.data(), bz, X, Y, B);
+              real vx = evDG(ux, X, Y), vy = evDG(uy, X, Y);
+              real val = -(vx * B[1] - vy * B[0]);
+              real w = Jdet * wL[a] * wL[b];
+              real load = w * val;
+              if (ek != 0.0) {
+                real r = 0.0;
+                for (int j = 0; j < n; ++j)
+                  for (int i = 0; i < n; ++i)
+                    r += Jdet * wp[i] * wp[j] * Jq[2 * n2 + j * n + i] * lag(xL, a, xp[i]) * lag(xL, b, xp[j]);
+                load += ek * r;
+              }
+              LW[k * nW + b * mL + a] = load;
+            }
+        }
+    }
     for (int ey = 0; ey < ny; ++ey)
       for (int ex = 0; ex < nx; ++ex) {
-        int k = kid(ex, ey);
-        clX(bX, ex, ey, bx.data()); clY(bY, ex, ey, by.data());
-        clY(Jx, ex, ey, jx.data()); clX(Jy, ex, ey, jy.data()); clW(Jz, ex, ey, jz.data());
-        const real* bz = &bZ[(size_t)k * mm * mm];
-        const real* ux = &u[0][(size_t)k * n2];
-        const real* uy = &u[1][(size_t)k * n2];
-        const real* uz = &u[2][(size_t)k * n2];
-        real ek = etaK[k];
-        // resistive field J_h at the DG-GLL(p) nodes of this element
-        std::vector<real> Jq(3 * n2);
-        for (int j = 0; j < n; ++j)
-          for (int i = 0; i < n; ++i) {
-            Jq[0 * n2 + j * n + i] = evY(jx.data(), xp[i], xp[j]);
-            Jq[1 * n2 + j * n + i] = evX(jy.data(), xp[i], xp[j]);
-            Jq[2 * n2 + j * n + i] = evW(jz.data(), xp[i], xp[j]);
-          }
-        // x-component at N_x nodes (zeta_a, xi^L_b)
+        size_t k = (size_t)kid(ex, ey);
         for (int b = 0; b < mL; ++b)
           for (int a = 0; a < mm; ++a) {
-            real X = zG[a], Y = xL[b], B[3];
-            B_at(bx.data(), by.data(), bz, X, Y, B);
-            real vy = evDG(uy, X, Y), vz = evDG(uz, X, Y);
-            real val = -(vy * B[2] - vz * B[1]);
-            real w = Jdet * wG[a] * wL[b];
-            real load = w * val;
-            if (ek != 0.0) {
-              real r = 0.0;
-              for (int j = 0; j < n; ++j)
-                for (int i = 0; i < n; ++i)
-                  r += Jdet * wp[i] * wp[j] * Jq[0 * n2 + j * n + i] * lag(zG, a, xp[i]) * lag(xL, b, xp[j]);
-              load += ek * r;
-            }
             size_t gi = gidx(ex * mm + a, ey * mm + b);
-            lx[gi] += load; mx[gi] += w;
+            lx[gi] += LNx[k * nNx + b * mm + a]; mx[gi] += Jdet * wG[a] * wL[b];
           }
-        // y-component at N_y nodes (xi^L_a, zeta_b)
         for (int b = 0; b < mm; ++b)
           for (int a = 0; a < mL; ++a) {
-            real X = xL[a], Y = zG[b], B[3];
-            B_at(bx.data(), by.data(), bz, X, Y, B);
-            real vx = evDG(ux, X, Y), vz = evDG(uz, X, Y);
-            real val = -(vz * B[0] - vx * B[2]);
-            real w = Jdet * wL[a] * wG[b];
-            real load = w * val;
-            if (ek != 0.0) {
-              real r = 0.0;
-              for (int j = 0; j < n; ++j)
-                for (int i = 0; i < n; ++i)
-                  r += Jdet * wp[i] * wp[j] * Jq[1 * n2 + j * n + i] * lag(xL, a, xp[i]) * lag(zG, b, xp[j]);
-              load += ek * r;
-            }
             size_t gi = gidx(ex * mm + a, ey * mm + b);
-            ly[gi] += load; my[gi] += w;
+            ly[gi] += LNy[k * nNy + b * mL + a]; my[gi] += Jdet * wL[a] * wG[b];
           }
-        // z-component at W nodes (xi^L_a, xi^L_b)
         for (int b = 0; b < mL; ++b)
           for (int a = 0; a < mL; ++a) {
-            real X = xL[a], Y = xL[b], B[3];
-            B_at(bx.data(), by.data(), bz, X, Y, B);
-            real vx = evDG(ux, X, Y), vy = evDG(uy, X, Y);
-            real val = -(vx * B[1] - vy * B[0]);
-            real w = Jdet * wL[a] * wL[b];
-            real load = w * val;
-            if (ek != 0.0) {
-              real r = 0.0;
-              for (int j = 0; j < n; ++j)
-                for (int i = 0; i < n; ++i)
-                  r += Jdet * wp[i] * wp[j] * Jq[2 * n2 + j * n + i] * lag(xL, a, xp[i]) * lag(xL, b, xp[j]);
-              load += ek * r;
-            }
             size_t gi = gidx(ex * mm + a, ey * mm + b);
-            lz[gi] += load; mz[gi] += w;
+            lz[gi] += LW[k * nW + b * mL + a]; mz[gi] += Jdet * wL[a] * wL[b];
           }
       }
     Ex.assign(G, 0.0); Ey.assign(G, 0.0); Ez.assign(G, 0.0);
@@ -574,8 +629,12 @@ struct Oracle {
     dY.e.assign((size_t)K * n2, 0.0);
     for (int d = 0; d < 3; ++d) dY.u[d].assign((size_t)K * n2, 0.0);
     dY.Bx.assign(G, 0.0); dY.By.assign(G, 0.0); dY.Bz.assign((size_t)K * mm * mm, 0.0);
+    // every element writes only its own DOFs and nodes (threads in the OpenMP timing build)
+#pragma omp parallel
+    {
     std::vector<real> bx(mL * mm), by(mm * mL), jx(mm * mL), jy(mL * mm), jz(mL * mL),
         exc(mm * mL), eyc(mL * mm), ezc(mL * mL);
+#pragma omp for collapse(2) schedule(static)
     for (int ey = 0; ey < ny; ++ey)
       for (int ex = 0; ex < nx; ++ex) {
         int k = kid(ex, ey);
@@ -642,6 +701,7 @@ struct Oracle {
             dY.e[q] = etaK[k] * (jxq * jxq + jyq * jyq + jzq * jzq) / rho[q];
           }
       }
+    }
   }
 
   // Stabilisation pieces of the magnetic stage (velocity OE and A.R.).
@@ -845,6 +905,20 @@ void* or_create(int nx, int ny, double x0, double x1, double y0, double y1, int 
   return o;
 }
 void or_destroy(void* h) { delete (Oracle*)h; }
+
+// Threads of the OpenMP timing build (liboracle_omp.so): n > 0 sets the
+// count; returns the count in force (1 in the serial builds).  The element
+// loops it parallelises write disjoint data and every sum keeps its serial
+// order, so the results equal the serial build's bit for bit.
+int or_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 void or_set_params(void* h, int oe_hydro, int oe_vel, int pp, int ar, double s_H, double s_M, double C_s,
                    double C_eta, double cfl, int max_halvings, int ec_faces) {
