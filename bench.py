@@ -1,24 +1,30 @@
 #!/usr/bin/env python
 """Throughput benchmark: FP64 DOF-updates/s of the H-M-H Strang step.
 
-Workload: the Orszag-Tang vortex on a 256 x 256 periodic mesh of [0,1]^2,
-DGSEM degree p = 3, magnetic degree k = 3, gamma = 5/3, synthetic analytic
-initial state, CFL 0.4 time step fixed at its t = 0 value.  One "step" is one
-full Strang step S^dt = Phi_H^{dt/2} o Phi_M^{dt} o Phi_H^{dt/2}.
-DOFs per element: 5 (p+1)^2 + 3 (k+1)^2 = 128.
+Headline workload: the MHD blast wave on a 1024 x 1024 periodic mesh of
+[-1/2,1/2]^2, DGSEM degree p = 3, magnetic degree k = 3, gamma = 1.4, every
+stabilisation map on (hydro OE, positivity limiter, artificial resistivity,
+velocity OE), synthetic analytic initial state, CFL 0.4 time step fixed at
+its t = 0 value.  One "step" is one full Strang step
+S^dt = Phi_H^{dt/2} o Phi_M^{dt} o Phi_H^{dt/2}.  DOFs per element:
+5 (p+1)^2 + 3 (k+1)^2 = 128.  Side legs: the Orszag-Tang vortex 256 x 256
+(stabilised throughput), the reduced 2D2V stage, other (p, k), the adjoint
+and the batch of independent runs.
 
   python bench.py --gpus N --steps K --warmup W [--impl ours|reference]
 
 N > 1 runs under torchrun: every rank runs an independent replica (the
 method has no data-path collective; weak scaling), the timed region is
 bracketed by a barrier and synchronisation and the max over ranks is used.
---impl reference times the CPU oracle (plain FP64, one core) on a bounded
-sample of the same workload.
+--impl reference times the CPU oracle on the host cores (its OpenMP timing
+build, bitwise equal to the serial oracle) on a bounded sample of the same
+workload.
 """
 import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -33,19 +39,26 @@ import numpy as np  # noqa: E402
 METRIC = "FP64 DOF-updates/s per Strang step at p=3"
 UNIT = "DOF-updates/s"
 NOMINAL_FP64_TFLOPS = 1.25  # B300 dense FP64, nominal
-# DRAM bytes (read + write) of one k_vol<3> launch, mean over the three SSP stages (stage 1
-# does not read U^n), from the ncu capture summarised in
-# profiles/kvol_dram_orszag_tang_256.md (same kernel source as this bench); reset to None
-# whenever the volume kernel changes until it is captured again.
-K_VOL_TRAFFIC_BYTES = (63016704 + 7692032 + 104972544 + 16648192 + 105055488 + 7912192) / 3.0
-# The stabilised benchmark workload: OE (both stages), positivity limiter, artificial
+FALLBACK_HBM_GBS = 6400.0   # profiling recipe's fallback copy bandwidth
+# The stabilised workloads: OE (both stages), positivity limiter, artificial
 # resistivity and velocity filter active, with the paper's constants.
 STAB = dict(oe_hydro=1, oe_vel=1, pp=1, ar=1, s_H=0.02, s_M=0.02, C_s=5.0, C_eta=0.2)
+WORKLOADS = {"blast": ("blast", 1024), "orszag_tang": ("orszag_tang", 256)}
+# DRAM bytes (read + write) per launch of the step kernels, from one ncu
+# capture each of the current kernel sources (profiles/ summaries name the
+# capture); None where the kernel changed after its capture.
+NCU_TRAFFIC_BYTES_PER_ELEMENT = {}
 
 
-def workload_config(stab, mesh=256):
-    return dict(workload=f"orszag_tang_{mesh}x{mesh}_p3k3", mesh=[mesh, mesh], domain=[0.0, 1.0, 0.0, 1.0], p=3, k=3,
-                gamma=5.0 / 3.0, dofs_per_element=128, cfl=0.4, stabilization=stab,
+def workload_config(stab, name="orszag_tang", mesh=None):
+    wl_name, default_mesh = WORKLOADS[name]
+    mesh = mesh or default_mesh
+    if name == "blast":
+        return dict(workload=f"blast_{mesh}x{mesh}_p3k3", mesh=[mesh, mesh], domain=[-0.5, 0.5, -0.5, 0.5], p=3,
+                    k=3, gamma=1.4, dofs_per_element=128, cfl=0.4, stabilization=stab,
+                    l2="working set per step >> 126 MB L2 (state + stage buffers ~7 GB), no flush needed")
+    return dict(workload=f"orszag_tang_{mesh}x{mesh}_p3k3", mesh=[mesh, mesh], domain=[0.0, 1.0, 0.0, 1.0], p=3,
+                k=3, gamma=5.0 / 3.0, dofs_per_element=128, cfl=0.4, stabilization=stab,
                 l2="working set per step > 126 MB L2 (state + stage buffers ~0.5 GB), no flush needed")
 
 
@@ -85,15 +98,141 @@ def vol_flops_per_element_minimal(p):
     return 52 * p * n2 + 16 * n2 + 5 * n2 * (4 * p + 3) + 5 * 4 * n * 2 + 5 * n2 * 4 + 5 * n2 * 2 + 8
 
 
-def make_solver(stab_params, mesh=256):
+def stats_flops(p, nc):
+    """OE statistics of nc DG fields per element (k_stats): the weighted
+    average (one FMA per node), and per direction the jump measures J_r of the
+    lower face: r = 0 the traces (4 flops per face node), r >= 1 the r-th
+    derivative of both traces (2 (p+1) FMAs per face node) and the squared
+    jump (4), each order closed by a scale and a square root."""
+    n = p + 1
+    per_dir = 4 * n + 1 + p * (n * (4 * n + 4) + 2)
+    return nc * (2 * n * n + 2 * per_dir)
+
+
+def b_eval_flops(k):
+    """One evaluation of a B component at a single point from its element
+    DOFs as a tensor product (the larger R_h^k factor: (k+2)(k+1) + (k+1)
+    FMAs)."""
+    mm, mL = k + 1, k + 2
+    return 2 * (mL * mm + mm)
+
+
+def b_nodes_flops(p, k):
+    """B_x, B_y, B_z at all (p+1)^2 DG nodes of an element, sum-factorised:
+    an x-pass over the rows, then a y-pass (2 flops per FMA)."""
+    n, mm, mL = p + 1, k + 1, k + 2
+    return 2 * (2 * (mm * n * mL + n * n * mm) + (mm * n * mm + n * n * mm))
+
+
+def step_work(p, k):
+    """Algorithmic FP64 flops and DRAM bytes per element of each kernel class
+    for one Strang step with every stabilisation map on and a resistive A.R.,
+    counted from the kernels' loop bounds (FMA = 2 flops; add, multiply,
+    reciprocal, square root = 1; index arithmetic, reductions of maxima and
+    table products not counted).  Bytes: every array the class must read and
+    write once from DRAM (no reuse across kernels assumed).  Classes are those
+    of the library's event profiler; a Strang step has 6 hydro stages, 3
+    magnetic stages and 2 nodal exchanges.  The resistive Ohm load and the
+    Ohmic heating run only in elements with eta_K > 0 and are not counted (a
+    lower bound)."""
+    n = p + 1
+    n2, mm, mL = n * n, k + 1, k + 2
+    NX = NY = mm * mL
+    NW, NZ = mL * mL, mm * mm
+    d8 = 8
+    work = {}
+    # LLF on the 2 (p+1) face nodes an element owns: ~70 flops each; reads
+    # both traces, writes the flux (5 components)
+    work["face"] = (6 * 2 * n * 70, 6 * 2 * n * 15 * d8)
+    # volume + SSP combination + raw average; stage input, U^n (stages 2, 3),
+    # output and the face fluxes of the element's own faces
+    work["vol"] = (6 * vol_flops_per_element_minimal(p), 2 * (8 * 5 * n2 + 3 * 2 * 5 * n) * d8)
+    # hydro OE + limiter per stage: statistics of 5 fields, the rate (20), the
+    # sensor (2 n sigma items) and factors (n exponentials), the modal transform
+    # there and back (4 sum-factorised passes: 2 n^3 FMAs per component), the
+    # limiter (~35 per node: average, pressures, scalings)
+    oe = 20 + 2 * n * (5 + 2) + n * (2 * n + 3) + 5 * 4 * n2 * n * 2 + 35 * n2
+    work["stab_hydro"] = (6 * (stats_flops(p, 5) + oe), 6 * 3 * 5 * n2 * d8)
+    # nodal exchange (u = m/rho, e; and back): ~10 flops per node each way
+    work["exchange"] = (2 * 10 * n2, (5 + 4 + 4 + 1 + 5) * n2 * d8)
+    # magnetic stage (J, E, curl) x 3 stages
+    fJ = 2 * (2 * mm * mL * mL + 2 * NZ * mm + 2 * mm * NW + (NX + NY) * mm) + 3 * NW + 2 * (NX + NY)
+    assemble = 4 * NW + 2 * (NX + NY)
+    fE = (assemble
+          + 2 * (2 * n * mm * n + 3 * n * mL * n + NW * mm + NZ * mm + mm * mL * mm)        # x-passes
+          + 2 * ((2 * NX + 2 * NY + 2 * NW) * n + (NX + NY + NW) * mm)                     # y-passes
+          + 10 * (NX + NY + NW)                                                              # Ohm loads, Lorentz
+          + 2 * (4 * n * mm * mL + 2 * n * mL * mL)                                          # transposed y-pass
+          + n2 * (2 * (3 * mL + 2 * mm) + 27))                                               # x-pass, rates, SSP
+    fB = assemble + 2 * (NZ * mL + mL * mm * mm) + 3 * NZ * (2 * mL + 6) + NZ * 2 * mm
+    loads = (NX + NY + NW) * d8
+    bJ = 3 * NZ * d8 + loads
+    bE = loads + 3 * NZ * d8 + (3 + 1 + 1) * n2 * d8 + (3 + 1) * n2 * d8 * 2 + loads
+    bB = loads + 3 * NZ * d8 * 3
+    work["mag_stage"] = (3 * (fJ + fE + fB), 3 * (bJ + bE + bB))
+    # A.R. coefficient once per magnetic substep: element integrals, face jumps
+    # (2 directions x 2 components x (k+2) points x 2 traces), and B at the DG
+    # nodes for the directional speeds
+    be = b_eval_flops(k)
+    work["stab_eta"] = (3 * be + 2 * 2 * (k + 2) * 2 * (be + 3) + b_nodes_flops(p, k) + 8 * n2,
+                        (3 * NZ + 3 * n2 + 16) * d8)
+    # velocity OE: projectors once (rho-weighted Gram matrix, Cholesky, the
+    # rows of Psi = Phi L^-T), then per stage the statistics of 3 fields and the
+    # map (B at the nodes, coefficients and shell sums: 2 n2^2 FMAs per component)
+    prep = (2 * n2 + 2 * n * (n * (n + 1) // 2) * n + 2 * (n2 * (n2 + 1) // 2) * n
+            + 2 * n2 ** 3 // 3 + n2 ** 3)
+    voe = b_nodes_flops(p, k) + 10 * n2 + 3 * 2 * 2 * n2 * n2 + 3 * 3 * n
+    work["stab_vel"] = (prep + 3 * (stats_flops(p, 3) + 20 + 2 * n * 5 + n * (2 * n + 3) + voe),
+                        (n2 + n2 * n2) * d8 + 3 * (3 * n2 + 3 * n2 + n2 + 3 * NZ + n2 * n2 + 4 * n2 + n2) * d8)
+    return work
+
+
+def measured_hbm_gbs():
+    """Copy bandwidth of the B300s (MEASURED_PEAKS.json), else the
+    recipe's fallback; returns (GB/s, source)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_rooflines(kt, K, steps, p, k, p64_tflops, bw_gbs):
+    """Per-class roofline from the live CUDA-event times of `steps` Strang
+    steps: algorithmic flops and bytes per step (step_work) against the FP64
+    issue peak and the copy bandwidth; the bound is the larger of the two
+    times; frac = that time / the measured time.  Also the step-level bound
+    sum_k max(flops_k / P64, bytes_k / BW)."""
+    work = step_work(p, k)
+    out, bound_ms = {}, 0.0
+    for cls, (ms, groups) in kt.items():
+        if cls not in work:
+            continue
+        fl, by = work[cls]
+        fl_step, by_step = fl * K, by * K
+        t_ms = ms / steps
+        t_fl = fl_step / (p64_tflops * 1e12) * 1e3
+        t_by = by_step / (bw_gbs * 1e9) * 1e3
+        bound = "fp64" if t_fl >= t_by else "hbm"
+        bound_ms += max(t_fl, t_by)
+        out[cls] = {"ms_per_step": t_ms, "launch_groups_per_step": groups / steps,
+                    "flops_per_step": fl_step, "bytes_per_step": by_step,
+                    "achieved_tflops": fl_step / (t_ms * 1e-3) / 1e12,
+                    "achieved_gbs": by_step / (t_ms * 1e-3) / 1e9,
+                    "bound": bound, "frac": max(t_fl, t_by) / t_ms}
+    return out, bound_ms
+
+
+def make_solver(name, mesh, stab_params, p=3, k=3):
     from paper_2609_10849_b300 import workloads
     from paper_2609_10849_b300.mhd import Solver
-    wl = workloads.orszag_tang()
-    s = Solver(mesh, mesh, 3, 3, wl["gamma"], wl["domain"])
+    wl = workloads.WORKLOADS[WORKLOADS[name][0]]()
+    s = Solver(mesh, mesh, p, k, wl["gamma"], wl["domain"])
     X, Y = s.coords("dg")
-    rho, ux, uy, uz, p, _ = wl["fields"](X, Y)
+    rho, ux, uy, uz, pr, _ = wl["fields"](X, Y)
     s.set_primitive(np.ascontiguousarray(rho), np.ascontiguousarray(np.stack([ux, uy, uz])),
-                    np.ascontiguousarray(p))
+                    np.ascontiguousarray(pr))
+    del X, Y, rho, ux, uy, uz, pr
     XW, YW = s.coords("w")
     XZ, YZ = s.coords("bz")
     s.set_B_from_potential(np.ascontiguousarray(wl["Az"](XW, YW)), *wl["B0"],
@@ -161,13 +300,32 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_baseline(steps=3, n=64):
-    """The oracle as it stands, single-threaded, on a bounded sample of the same
-    workload: the Orszag-Tang vortex on an n x n mesh, p = k = 3."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.processor() or "unknown"
+
+
+def oracle_for(name, n, parallel):
+    """The oracle (serial, or its bitwise-equal OpenMP build) on an n x n mesh
+    of the same workload and physics as the GPU run."""
     import oracle
     from paper_2609_10849_b300 import workloads
-    wl = workloads.orszag_tang()
-    o = oracle.Oracle(n, n, 3, 3, wl["gamma"], wl["domain"])
+    wl = workloads.WORKLOADS[WORKLOADS[name][0]]()
+    cls = oracle.ParallelOracle if parallel else oracle.Oracle
+    o = cls(n, n, 3, 3, wl["gamma"], wl["domain"])
     X, Y = o.coords("dg")
     rho, ux, uy, uz, pr, _ = wl["fields"](X, Y)
     XW, YW = o.coords("w")
@@ -175,33 +333,40 @@ def cpu_baseline(steps=3, n=64):
     Bx, By = o.b_from_potential(wl["Az"](XW, YW), *wl["B0"])
     o.set_primitive(rho, np.stack([ux, uy, uz]), pr, Bx, By, wl["fields"](XZ, YZ)[5])
     o.set_params(cfl=0.4, **STAB)
-    dt = o.cfl_dt()
-    o.strang_step(dt)  # warm-up
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        o.strang_step(dt)
-    el = time.perf_counter() - t0
-    return dict(value=dofs_per_element(3, 3) * n * n * steps / el, unit=UNIT, cores=1, kind="oracle",
-                sample=f"{steps} Strang steps of the same Orszag-Tang workload on a {n}x{n} mesh (p=k=3), "
-                       f"serial C++ oracle, {el:.1f} s")
+    return o
+
+
+def cpu_baseline(name="blast", n=64, steps_serial=2, steps_parallel=8):
+    """The oracle as it stands on a bounded sample of the same workload (the
+    same physics on an n x n mesh, p = k = 3): single-threaded, and its OpenMP
+    timing build on every host core (bitwise equal results)."""
+    cores = host_cores()
+    res = {}
+    for parallel, steps in ((False, steps_serial), (True, steps_parallel)):
+        o = oracle_for(name, n, parallel)
+        used = o.set_threads(cores) if parallel else 1
+        dt = o.cfl_dt()
+        o.strang_step(dt)  # warm-up
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            o.strang_step(dt)
+        el = time.perf_counter() - t0
+        res[parallel] = (dofs_per_element(3, 3) * n * n * steps / el, used, steps, el)
+    v1, _, s1, e1 = res[False]
+    vN, used, sN, eN = res[True]
+    return dict(value=vN, unit=UNIT, cores=used, kind="oracle", value_1_thread=v1, cpu_model=cpu_model(),
+                host_cores=cores,
+                sample=f"same {name} physics on a {n}x{n} mesh (p=k=3, all stabilisation on): {sN} Strang steps on "
+                       f"{used} threads (OpenMP timing build of the oracle, bitwise equal to the serial one, "
+                       f"{eN:.1f} s) and {s1} steps single-threaded ({e1:.1f} s)")
 
 
 def run_reference(args, rank):
     if rank != 0:
         return
-    stab = STAB
-    n = 32
-    import oracle
-    from paper_2609_10849_b300 import workloads
-    wl = workloads.orszag_tang()
-    o = oracle.Oracle(n, n, 3, 3, wl["gamma"], wl["domain"])
-    X, Y = o.coords("dg")
-    rho, ux, uy, uz, pr, _ = wl["fields"](X, Y)
-    XW, YW = o.coords("w")
-    XZ, YZ = o.coords("bz")
-    Bx, By = o.b_from_potential(wl["Az"](XW, YW), *wl["B0"])
-    o.set_primitive(rho, np.stack([ux, uy, uz]), pr, Bx, By, wl["fields"](XZ, YZ)[5])
-    o.set_params(cfl=0.4, **STAB)
+    n = 64
+    o = oracle_for(args.workload, n, parallel=True)
+    used = o.set_threads(host_cores())
     dt = o.cfl_dt()
     for _ in range(args.warmup):
         o.strang_step(dt)
@@ -210,14 +375,14 @@ def run_reference(args, rank):
         o.strang_step(dt)
     el = time.perf_counter() - t0
     value = dofs_per_element(3, 3) * n * n * args.steps / el
-    sample = (f"each step: one Strang step of the Orszag-Tang workload on a {n}x{n} sample mesh (p=k=3), serial "
-              f"C++ oracle")
+    sample = (f"each step: one Strang step of the {args.workload} workload's physics on a {n}x{n} sample mesh "
+              f"(p=k=3), the oracle's OpenMP timing build on {used} host threads ({cpu_model()})")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(stab, args.mesh),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": workload_config(STAB, args.workload, args.mesh),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -306,14 +471,15 @@ def adjoint_leg(steps=20, every=20, n=128, p=4):
     B, r0, u0, p0 = x[5 * s.N:].clone(), dev(rho), dev(np.stack([ux, uy, uz])), dev(pr)
     rs = dev(workloads.vortex_target_density(X, Y))
     with torch.no_grad():
-        target = strang_steps(s, pack_primitive(rs, u0, p0, s.gamma, B), dt, steps, every)[:s.N].clone()
+        target = strang_steps(s, pack_primitive(s, rs, u0, p0, B), dt, steps, every)[:s.N].clone()
     Mq = dev(np.tile(np.outer(gll_weights(p), gll_weights(p)).ravel() * (10.0 / n) ** 2 / 4, s.K))
+
     def forward_backward():
         rho_v = r0.clone().requires_grad_(True)
         u_v = u0.clone().requires_grad_(True)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        xT = strang_steps(s, pack_primitive(rho_v, u_v, p0, s.gamma, B), dt, steps, every)
+        xT = strang_steps(s, pack_primitive(s, rho_v, u_v, p0, B), dt, steps, every)
         J = 0.5 * (Mq * (xT[:s.N] - target) ** 2).sum()
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -340,60 +506,54 @@ def adjoint_leg(steps=20, every=20, n=128, p=4):
                     "second of two forward/backward passes"}
 
 
-def reduced_2d2v_leg(s, dt, steps, stream, dofs, full_ms_per_step):
-    """The same workload with the reduced 2D2V magnetic stage (the Orszag-Tang
-    state has u_z = B_z = 0, which every step keeps exactly; the result equals
-    the full stage bitwise).  Same DOF count, timed like the headline."""
+def timed_steps(s, dt, steps, stream):
+    """CUDA-event time (ms) of `steps` graph-replayed Strang steps on `stream`."""
     import torch
-    s.set_params(reduced_2d2v=1)
-    s.strang_steps(dt, 3)
-    torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     s.strang_steps(dt, steps)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    return e0.elapsed_time(e1)
+
+
+def reduced_2d2v_leg(s, dt, steps, stream, dofs, full_ms_per_step):
+    """The same workload with the reduced 2D2V magnetic stage (the state has
+    u_z = B_z = 0, which every step keeps exactly; the result equals the full
+    stage bitwise).  Same DOF count, timed like the headline."""
+    import torch
+    s.set_params(reduced_2d2v=1)
+    s.strang_steps(dt, 3)
+    torch.cuda.synchronize()
+    ms = timed_steps(s, dt, steps, stream)
     s.set_params(reduced_2d2v=0)
     return {"ms_per_step": ms / steps, "value": dofs * steps / (ms * 1e-3), "unit": UNIT,
             "speedup_vs_full": full_ms_per_step / (ms / steps),
             "note": "reduced_2d2v=1: in-plane E_h, J_h and u_z, B_z are not formed (all identically zero)"}
 
 
-def degree_leg(pairs=((3, 2), (4, 4), (2, 2), (4, 3)), mesh=256, steps=10):
-    """The benchmark workload (Orszag-Tang, all stabilisation on) at other
-    (p, k): the even-m family the paper recommends, (3,2) and (4,4), and two
-    neighbours.  Each pair is tile-autotuned; DOFs per element 5 (p+1)^2 + 3 (k+1)^2."""
+def throughput_leg(name, mesh, p, k, steps, stream=None):
+    """Stabilised throughput of a workload at (p, k), tile-autotuned."""
     import torch
-    from paper_2609_10849_b300 import workloads
-    from paper_2609_10849_b300.mhd import Solver
-    out = {}
-    wl = workloads.orszag_tang()
-    for p, k in pairs:
-        s = Solver(mesh, mesh, p, k, wl["gamma"], wl["domain"])
-        X, Y = s.coords("dg")
-        rho, ux, uy, uz, pr, _ = wl["fields"](X, Y)
-        s.set_primitive(rho, np.stack([ux, uy, uz]), pr)
-        XW, YW = s.coords("w")
-        XZ, YZ = s.coords("bz")
-        s.set_B_from_potential(wl["Az"](XW, YW), *wl["B0"], wl["fields"](XZ, YZ)[5])
-        s.set_params(cfl=0.4, **STAB)
-        stream = torch.cuda.Stream()
-        s.set_stream(stream.cuda_stream)
-        tiles = s.autotune()
-        dt = s.compute_dt()
-        s.strang_steps(dt, 3)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s.strang_steps(dt, steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
-        out[f"p{p}k{k}"] = {"ms_per_step": ms, "value": dofs_per_element(p, k) * s.K / (ms * 1e-3), "unit": UNIT,
-                            "tiles": list(tiles)}
-        s.close()
-    return {"workload": f"orszag_tang_{mesh}x{mesh}", "steps": steps, "pairs": out}
+    s = make_solver(name, mesh, STAB, p, k)
+    stream = stream or torch.cuda.Stream()
+    s.set_stream(stream.cuda_stream)
+    tiles = s.autotune()
+    dt = s.compute_dt()
+    s.strang_steps(dt, 3)
+    torch.cuda.synchronize()
+    ms = timed_steps(s, dt, steps, stream) / steps
+    s.close()
+    return {"ms_per_step": ms, "value": dofs_per_element(p, k) * mesh * mesh / (ms * 1e-3), "unit": UNIT,
+            "tiles": list(tiles), "steps": steps}
+
+
+def degree_leg(pairs=((3, 2), (4, 4), (2, 2), (4, 3)), mesh=256, steps=10):
+    """The Orszag-Tang workload (all stabilisation on) at other (p, k): the
+    even-m family the paper recommends, (3,2) and (4,4), and two neighbours.
+    Each pair is tile-autotuned; DOFs per element 5 (p+1)^2 + 3 (k+1)^2."""
+    return {"workload": f"orszag_tang_{mesh}x{mesh}", "steps": steps,
+            "pairs": {f"p{p}k{k}": throughput_leg("orszag_tang", mesh, p, k, steps) for p, k in pairs}}
 
 
 def run_batch(args):
@@ -403,19 +563,21 @@ def run_batch(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="blast", choices=list(WORKLOADS))
+    ap.add_argument("--mesh", type=int, default=0, help="elements per direction (0: the workload's own)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mesh", type=int, default=256, help="elements per direction (256 is the benchmark workload)")
     ap.add_argument("--batch", type=int, default=0, help="run the batched workload with this many runs instead")
-    ap.add_argument("--no-side-legs", action="store_true", help="skip the adjoint and batched side measurements")
+    ap.add_argument("--no-side-legs", action="store_true", help="skip the side measurements")
     ap.add_argument("--leg", default="", choices=["", "adjoint"], help="run only this side measurement")
     ap.add_argument("--reduced-2d2v", action="store_true",
                     help="time the reduced 2D2V magnetic stage in the main measurement (for profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    args.mesh = args.mesh or WORKLOADS[args.workload][1]
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -438,8 +600,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     from paper_2609_10849_b300 import mhd
-    stab = STAB
-    s = make_solver(stab, args.mesh)
+    s = make_solver(args.workload, args.mesh, STAB)
     stream = torch.cuda.Stream()  # a capturable stream (the legacy default stream is not)
     torch.cuda.set_stream(stream)
     s.set_stream(stream.cuda_stream)
@@ -471,36 +632,44 @@ def main():
     ms_per_step = ms / args.steps
     value = whole_job_value(world, dofs, args.steps, ms)
 
-    # per-kernel event timing of the same steps (separate pass) for the roofline
+    # per-class CUDA-event timing of the same number of steps (separate, eager
+    # pass on the same stream) for the rooflines
     s.profile_kernels(True)
     s.strang_steps(dt, args.steps)
     kt = s.kernel_times()
     s.profile_kernels(False)
+    p64 = mhd.fp64_peak_tflops()
+    bw, bw_src = measured_hbm_gbs()
+    per_class, bound_ms = kernel_rooflines(kt, s.K, args.steps, 3, 3, p64, bw)
+    events_ms = sum(v[0] for v in kt.values()) / args.steps
+    top = max(per_class, key=lambda c: per_class[c]["ms_per_step"])
     vol_ms = kt["vol"][0] / kt["vol"][1]
-    vol_flops = vol_flops_per_element_pairs(3) * s.K
-    achieved = vol_flops / (vol_ms * 1e-3) / 1e12
-    measured_peak = mhd.fp64_peak_tflops()
-    step_ms_sum = sum(v[0] for v in kt.values())
-    roofline = {"bound": "alu", "kernel": "k_vol<3> (entropy-conservative volume term + SSP stage)",
-                "achieved": achieved, "peak": NOMINAL_FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / NOMINAL_FP64_TFLOPS, "traffic": K_VOL_TRAFFIC_BYTES,
-                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-                "peak_source": "nominal B300 dense FP64 (1.25 TFLOP/s)",
-                "peak_measured_dfma_tflops": measured_peak, "frac_of_measured_dfma": achieved / measured_peak,
-                "flops_per_launch": vol_flops, "avg_launch_ms": vol_ms,
-                "flops_definition": "117 op-equivalents per unique EC pair x p(p+1)^2 pairs per element "
-                                    "(FMA = 2, div = 8)",
-                "frac_minimal_count": vol_flops_per_element_minimal(3) * s.K / (vol_ms * 1e-3) / 1e12
-                / NOMINAL_FP64_TFLOPS,
-                "fp64_pipe_busy_ncu": 0.877,
-                "kernel_share_of_step": {k: v[0] / step_ms_sum for k, v in kt.items()}}
+    top_r = per_class[top]
+    traffic = NCU_TRAFFIC_BYTES_PER_ELEMENT.get(top)
+    roofline = {
+        "bound": "alu", "kernel_class": top, "achieved": top_r["achieved_tflops"], "peak": p64,
+        "unit": "TFLOP/s", "frac": top_r["achieved_tflops"] / p64,
+        "traffic": None if traffic is None else traffic * s.K / top_r["launch_groups_per_step"],
+        "traffic_unit": "DRAM bytes per launch group (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+        "peak_source": "FP64 FMA issue rate measured in this run (mhd_fp64_peak: DFMA probe, all lanes)",
+        "peak_nominal_tflops": NOMINAL_FP64_TFLOPS,
+        "frac_of_nominal": top_r["achieved_tflops"] / NOMINAL_FP64_TFLOPS,
+        "flops_definition": "algorithmic FP64 flops counted from the kernels' loop bounds (bench.step_work: "
+                            "FMA = 2, add/mul/rcp/sqrt = 1)",
+        "hbm_gbs": bw, "hbm_source": bw_src,
+        "per_kernel_class": per_class,
+        "step_bound_ms": bound_ms, "step_ms_events": events_ms, "step_frac": bound_ms / ms_per_step,
+        "vol": {"avg_launch_ms": vol_ms,
+                "tflops_117_per_pair": vol_flops_per_element_pairs(3) * s.K / (vol_ms * 1e-3) / 1e12,
+                "tflops_minimal": vol_flops_per_element_minimal(3) * s.K / (vol_ms * 1e-3) / 1e12},
+    }
 
     # end-to-end through the public API with pinned host buffers
     U, Bx, By, Bz = (torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
                      for n in (5 * s.N, s.G, s.G, s.Z))
     host = (U.reshape(5, s.N), Bx, By, Bz)
     s.get_state(host)
-    e2e_steps = max(5, args.steps // 5)
+    e2e_steps = max(5, args.steps // 4)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -511,29 +680,31 @@ def main():
     nbytes = 8 * (5 * s.N + 2 * s.G + s.Z)
     e2e = {"value": world * dofs * e2e_steps / e2e_el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes}
+    del U, Bx, By, Bz, host
 
-    reduced = None
+    side = {}
     if not args.no_side_legs and world == 1 and not args.reduced_2d2v:
-        reduced = reduced_2d2v_leg(s, dt, args.steps, stream, dofs, ms_per_step)
-
+        side["reduced_2d2v"] = reduced_2d2v_leg(s, dt, args.steps, stream, dofs, ms_per_step)
+    s.close()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic (analytic Orszag-Tang initial state)",
-            "config": dict(workload_config(stab, args.mesh), parallelism=f"replicas{world}", dt=dt,
+            "vs_baseline": None, "dtype": "f64", "data": f"synthetic (analytic {args.workload} initial state)",
+            "config": dict(workload_config(STAB, args.workload, args.mesh), parallelism=f"replicas{world}", dt=dt,
                            magnetic_stage="reduced 2D2V" if args.reduced_2d2v else "full",
                            tiles={"vol_elements_per_cta": tiles[0], "mag_elements_per_cta": tiles[1]}),
             "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches,
         }
-        if reduced is not None:
-            line["reduced_2d2v"] = reduced
+        line.update(side)
         if not args.no_side_legs and world == 1:
+            if args.workload != "orszag_tang":
+                line["orszag_tang_256"] = throughput_leg("orszag_tang", 256, 3, 3, args.steps)
             line["degrees"] = degree_leg()
             line["adjoint"] = adjoint_leg()
-            line["batched"] = batch_leg(256, 2)
+            line["batched"] = batch_leg(256, 5)
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -123,6 +123,20 @@ int mhd_get_state(mhd_ctx* ctx, double* U, double* Bx, double* By, double* Bz, i
  * E_mech = p/(gamma-1) + rho|u|^2/2); the magnetic field is left unchanged. */
 int mhd_set_primitive(mhd_ctx* ctx, const double* rho, const double* u, const double* p, int on_device);
 
+/* The same exchange into a caller buffer, without touching the context's
+ * state: rho [N], u [3][N], p [N] -> U [5][N] (m = rho u,
+ * E_mech = p/(gamma-1) + rho|u|^2/2; the nodal variable exchange of §3.4.1
+ * written for the pressure).  Synchronises the context's stream. */
+int mhd_primitive_to_conservative(mhd_ctx* ctx, const double* rho, const double* u, const double* p, double* U,
+                                  int on_device);
+
+/* Vector-Jacobian product of mhd_primitive_to_conservative at (rho, u): for
+ * lamU [5][N] = dJ/dU writes g_rho [N], g_u [3][N], g_p [N] = dJ/d(rho, u, p)
+ * (the paper has no adjoint; this differentiates the exchange above).
+ * Synchronises the context's stream. */
+int mhd_primitive_to_conservative_vjp(mhd_ctx* ctx, const double* rho, const double* u, const double* lamU,
+                                      double* g_rho, double* g_u, double* g_p, int on_device);
+
 /* Magnetic field B = (Bx0 + (-dAz/dy), By0 + dAz/dx, Bz) from the nodal
  * W_h^{k+1} interpolant of a potential Az (exactly divergence-free). */
 int mhd_set_B_from_potential(mhd_ctx* ctx, const double* Az, double Bx0, double By0, const double* Bz,

@@ -10,7 +10,12 @@
 //
 // Numbering of citations: section numbers of the paper and the LaTeX equation
 // labels, e.g. "eq. (euler-volume-residual)".  Readings of passages that the
-// paper leaves open are tagged R1..R17 and listed in the design notes.
+// paper leaves open are tagged R1..R23 and listed in the design notes.
+//
+// Parity unpinned (no CPU pin a plausible mistake would fail): the CFL time
+// step (reading R2) and the rejection/retry scope (R3).  Both are readings the
+// paper leaves open; the GPU must match the oracle on them, and the field-loop
+// numbers of §4.3 tie R2 to the paper through a GPU test only.
 //
 // Host layouts (shared with the C-ABI of the library, because they are the
 // interface, not the arithmetic):
@@ -782,7 +787,10 @@ struct Oracle {
     B_at(bx.data(), by.data(), &Bz[(size_t)kid(ex, ey) * mm * mm], xp[i], xp[j], B);
   }
 
-  // CFL time step (reading R2).
+  // CFL time step (reading R2): the paper gives the CFL number, not the
+  // formula.  Parity unpinned: no CPU pin fixes this formula; the GPU matches
+  // it to rounding, and the paper's field-loop numbers (§4.3) select it only
+  // through a GPU test of whole runs.
   real cfl_dt() const {
     real mx = 0.0;
     for (int ey = 0; ey < ny; ++ey)

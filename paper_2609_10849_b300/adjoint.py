@@ -61,10 +61,39 @@ def strang_steps(solver: Solver, x0: torch.Tensor, dt: float, nsteps: int, check
     return StrangSteps.apply(x0, solver, dt, nsteps, checkpoint_every)
 
 
-def pack_primitive(rho, u, p, gamma, B):
-    """Packed state from nodal primitives (differentiable torch ops): U = (rho,
-    rho u, p/(gamma-1) + rho |u|^2/2) followed by the magnetic part ``B``
-    (the packed tail [Bx | By | Bz], not differentiated through here)."""
-    m = rho * u
-    E = p / (gamma - 1.0) + 0.5 * rho * (u * u).sum(dim=0)
-    return torch.cat([rho, m[0], m[1], m[2], E, B])
+class PackPrimitive(torch.autograd.Function):
+    """Packed state [U | B] from nodal primitives (rho, u, p) and the packed
+    magnetic tail B; the exchange U(rho, u, p) and its vector-Jacobian product
+    run in the library (mhd_primitive_to_conservative and its _vjp)."""
+
+    @staticmethod
+    def forward(ctx, rho, u, p, B, solver: Solver):
+        for t in (rho, u, p, B):
+            if not t.is_cuda or t.dtype != torch.float64:
+                raise ValueError("rho, u, p and B must be CUDA float64 tensors")
+        rho, u, p = rho.detach().contiguous(), u.detach().contiguous(), p.detach().contiguous()
+        N = solver.N
+        x = torch.empty(5 * N + B.numel(), dtype=torch.float64, device=rho.device)
+        torch.cuda.current_stream().synchronize()  # the library works on its own stream
+        solver.primitive_to_conservative(rho, u, p, x[:5 * N])
+        x[5 * N:] = B.detach()
+        ctx.save_for_backward(rho, u)
+        ctx.solver = solver
+        return x
+
+    @staticmethod
+    def backward(ctx, lam):
+        rho, u = ctx.saved_tensors
+        solver, N = ctx.solver, ctx.solver.N
+        lam = lam.detach().contiguous()
+        g_rho, g_u, g_p = torch.empty_like(rho), torch.empty_like(u), torch.empty_like(rho)
+        torch.cuda.current_stream().synchronize()
+        solver.primitive_to_conservative_vjp(rho, u, lam[:5 * N].contiguous(), g_rho, g_u, g_p)
+        return g_rho, g_u, g_p, lam[5 * N:].clone(), None
+
+
+def pack_primitive(solver: Solver, rho, u, p, B):
+    """Differentiable packed state from nodal primitives rho [N], u [3, N],
+    p [N] (CUDA float64) and the packed magnetic tail ``B`` = [Bx | By | Bz]:
+    U = (rho, rho u, p/(gamma-1) + rho |u|^2/2), computed by the library."""
+    return PackPrimitive.apply(rho, u, p, B, solver)

@@ -396,6 +396,38 @@ int mhd_set_primitive(mhd_ctx* c, const double* rho, const double* u, const doub
   return MHD_OK;
 }
 
+int mhd_primitive_to_conservative(mhd_ctx* c, const double* rho, const double* u, const double* p, double* U,
+                                  int on_device) {
+  if (!c || !rho || !u || !p || !U) return fail(MHD_EINVAL, "null argument");
+  const size_t N = c->N;
+  cudaError_t e;
+  if ((e = copy_in(c, c->io, rho, N, on_device)) != cudaSuccess) return cuda_fail(e, "rho");
+  if ((e = copy_in(c, c->io + N, u, 3 * N, on_device)) != cudaSuccess) return cuda_fail(e, "u");
+  if ((e = copy_in(c, c->io + 4 * N, p, N, on_device)) != cudaSuccess) return cuda_fail(e, "p");
+  prim_in(c->io, c->io + N, c->io + 4 * N, c->S1, N, c->M.g, c->st);
+  c->launches++;
+  if ((e = copy_out(c, U, c->S1, 5 * N, on_device)) != cudaSuccess) return cuda_fail(e, "U");
+  if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(e, "primitive_to_conservative");
+  return MHD_OK;
+}
+
+int mhd_primitive_to_conservative_vjp(mhd_ctx* c, const double* rho, const double* u, const double* lamU,
+                                      double* g_rho, double* g_u, double* g_p, int on_device) {
+  if (!c || !rho || !u || !lamU || !g_rho || !g_u || !g_p) return fail(MHD_EINVAL, "null argument");
+  const size_t N = c->N;
+  cudaError_t e;
+  if ((e = copy_in(c, c->io, rho, N, on_device)) != cudaSuccess) return cuda_fail(e, "rho");
+  if ((e = copy_in(c, c->io + N, u, 3 * N, on_device)) != cudaSuccess) return cuda_fail(e, "u");
+  if ((e = copy_in(c, c->S1, lamU, 5 * N, on_device)) != cudaSuccess) return cuda_fail(e, "lamU");
+  prim_in_vjp(c->io, c->io + N, c->S1, c->S2, N, c->M.ig1, c->st);
+  c->launches++;
+  if ((e = copy_out(c, g_rho, c->S2, N, on_device)) != cudaSuccess) return cuda_fail(e, "g_rho");
+  if ((e = copy_out(c, g_u, c->S2 + N, 3 * N, on_device)) != cudaSuccess) return cuda_fail(e, "g_u");
+  if ((e = copy_out(c, g_p, c->S2 + 4 * N, N, on_device)) != cudaSuccess) return cuda_fail(e, "g_p");
+  if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(e, "primitive_to_conservative_vjp");
+  return MHD_OK;
+}
+
 int mhd_set_B_from_potential(mhd_ctx* c, const double* Az, double Bx0, double By0, const double* Bz, int on_device) {
   if (!c || !Az || !Bz) return fail(MHD_EINVAL, "null argument");
   cudaError_t e;

@@ -28,6 +28,8 @@ void blocked_to_grid(const double* o, double* g, int nx, int ny, int mm, cudaStr
 void cons_to_prim(const double* U, double* Y, size_t N, cudaStream_t st);
 void prim_to_cons(const double* Y, double* U, size_t N, cudaStream_t st);
 void prim_in(const double* rho, const double* u, const double* p, double* U, size_t N, double g, cudaStream_t st);
+void prim_in_vjp(const double* rho, const double* u, const double* lam, double* G, size_t N, double ig1,
+                 cudaStream_t st);
 void b_from_potential(int k, const double* A, double Bx0, double By0, double* Bx, double* By, const Tab* T,
                       const Mesh& M, cudaStream_t st);
 void cfl_dt(int p, int k, const double* U, const double* B, const Tab* T, const Mesh& M,

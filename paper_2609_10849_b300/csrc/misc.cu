@@ -66,6 +66,30 @@ __global__ void k_prim_in(const double* __restrict__ rho, const double* __restri
   U[4 * N + q] = p[q] / (g - 1.0) + 0.5 * r * (ux * ux + uy * uy + uz * uz);
 }
 
+// Vector-Jacobian product of k_prim_in at (rho, u): with lam = dJ/dU,
+//   g_rho = lam_rho + u . lam_m + |u|^2/2 lam_E,
+//   g_u   = rho lam_m + rho u lam_E,
+//   g_p   = lam_E / (gamma - 1).
+// G = [g_rho | g_u (3) | g_p], each [N].
+__global__ void k_prim_in_vjp(const double* __restrict__ rho, const double* __restrict__ u,
+                              const double* __restrict__ lam, double* __restrict__ G, size_t N, double ig1) {
+  size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= N) return;
+  const double r = rho[q], ux = u[q], uy = u[N + q], uz = u[2 * N + q];
+  const double lr = lam[q], lx = lam[N + q], ly = lam[2 * N + q], lz = lam[3 * N + q], le = lam[4 * N + q];
+  const double u2 = fma(ux, ux, fma(uy, uy, uz * uz));
+  G[q] = fma(0.5 * u2, le, fma(ux, lx, fma(uy, ly, fma(uz, lz, lr))));
+  G[N + q] = r * fma(ux, le, lx);
+  G[2 * N + q] = r * fma(uy, le, ly);
+  G[3 * N + q] = r * fma(uz, le, lz);
+  G[4 * N + q] = le * ig1;
+}
+
+void prim_in_vjp(const double* rho, const double* u, const double* lam, double* G, size_t N, double ig1,
+                 cudaStream_t st) {
+  k_prim_in_vjp<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(rho, u, lam, G, N, ig1);
+}
+
 void cons_to_prim(const double* U, double* Y, size_t N, cudaStream_t st) {
   k_cons_to_prim<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(U, Y, N);
 }

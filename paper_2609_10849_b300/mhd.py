@@ -56,6 +56,8 @@ _SIGS = {
     "mhd_set_state": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int]),
     "mhd_get_state": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int]),
     "mhd_set_primitive": (C.c_int, [C.c_void_p] + [C.c_void_p] * 3 + [C.c_int]),
+    "mhd_primitive_to_conservative": (C.c_int, [C.c_void_p] + [C.c_void_p] * 4 + [C.c_int]),
+    "mhd_primitive_to_conservative_vjp": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6 + [C.c_int]),
     "mhd_set_B_from_potential": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_void_p, C.c_int]),
     "mhd_quad_coords": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "mhd_set_Bz_projected": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
@@ -253,6 +255,19 @@ class Solver:
     def set_primitive(self, rho, u, p):
         (a, b, c), dev = _ptrs(rho, u, p)
         _check(lib().mhd_set_primitive(self._h, a, b, c, dev))
+
+    def primitive_to_conservative(self, rho, u, p, out):
+        """U [5, N] = (rho, rho u, p/(gamma-1) + rho|u|^2/2) into ``out``
+        (numpy arrays or CUDA tensors); the solver's state is not touched."""
+        (a, b, c, o), dev = _ptrs(rho, u, p, out)
+        _check(lib().mhd_primitive_to_conservative(self._h, a, b, c, o, dev))
+        return out
+
+    def primitive_to_conservative_vjp(self, rho, u, lamU, g_rho, g_u, g_p):
+        """dJ/d(rho, u, p) from lamU = dJ/dU at (rho, u), into the given buffers."""
+        ps, dev = _ptrs(rho, u, lamU, g_rho, g_u, g_p)
+        _check(lib().mhd_primitive_to_conservative_vjp(self._h, *ps, dev))
+        return g_rho, g_u, g_p
 
     def set_B_from_potential(self, Az, Bx0, By0, Bz):
         (a, z), dev = _ptrs(Az, Bz)

@@ -60,3 +60,37 @@ def test_reference_arm_line():
     assert d["value"] > 0 and d["unit"] == "DOF-updates/s" and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_step_work_accounting():
+    """Per-class algorithmic work of a Strang step: every class present,
+    positive, the volume class equal to 6 launches of the minimal count, and
+    the stabilisation statistics growing with the number of fields."""
+    w = bench.step_work(3, 3)
+    assert set(w) == {"face", "vol", "stab_hydro", "exchange", "mag_stage", "stab_eta", "stab_vel"}
+    assert all(f > 0 and b > 0 for f, b in w.values())
+    assert w["vol"][0] == 6 * bench.vol_flops_per_element_minimal(3)
+    assert w["face"][0] == 6 * 2 * 4 * 70
+    assert bench.stats_flops(3, 5) > bench.stats_flops(3, 3) > 0
+    assert bench.step_work(4, 4)["vol"][0] > w["vol"][0]
+
+
+def test_kernel_rooflines_bound_and_fraction():
+    """A class timed exactly at its FP64 bound reads frac 1 and bound fp64;
+    the step bound is the sum over classes of the larger time."""
+    w = bench.step_work(3, 3)
+    K, steps, p64, bw = 1000, 4, 1.0, 1000.0
+    kt = {}
+    for cls, (fl, by) in w.items():
+        t = max(fl * K / (p64 * 1e12), by * K / (bw * 1e9)) * 1e3  # ms per step at the bound
+        kt[cls] = (t * steps, 2 * steps)
+    out, bound_ms = bench.kernel_rooflines(kt, K, steps, 3, 3, p64, bw)
+    for cls, r in out.items():
+        assert abs(r["frac"] - 1.0) < 1e-12
+    assert out["vol"]["bound"] == "fp64"
+    assert abs(bound_ms - sum(v[0] for v in kt.values()) / steps) < 1e-12
+
+
+def test_workload_config_headline():
+    cfg = bench.workload_config(bench.STAB, "blast")
+    assert cfg["workload"] == "blast_1024x1024_p3k3" and cfg["gamma"] == 1.4 and cfg["mesh"] == [1024, 1024]

@@ -238,7 +238,7 @@ def objective_setup(n, p, nsteps, every):
     from paper_2609_10849_b300.workloads import vortex_target_density
     rs = torch.tensor(vortex_target_density(X, Y), dtype=torch.float64, device="cuda")
     with torch.no_grad():
-        xt = strang_steps(s, pack_primitive(rs, u0, p0, g, B), dt, nsteps, every)
+        xt = strang_steps(s, pack_primitive(s, rs, u0, p0, B), dt, nsteps, every)
     rho_t = xt[:s.N].clone()
     from oracle import rule
     _, w = rule("gll", p)
@@ -246,7 +246,7 @@ def objective_setup(n, p, nsteps, every):
     Mq = torch.tensor(np.tile(np.outer(w, w).ravel() * hx * hx / 4, s.K), device="cuda")
 
     def J(rho, u):
-        x = strang_steps(s, pack_primitive(rho, u, p0, g, B), dt, nsteps, every)
+        x = strang_steps(s, pack_primitive(s, rho, u, p0, B), dt, nsteps, every)
         return 0.5 * (Mq * (x[:s.N] - rho_t) ** 2).sum()
 
     return J, rho0, u0
@@ -401,3 +401,45 @@ def test_adjoint_with_reduced_2d2v_stage():
         out.append((s.adjoint_segment(x0, 3, lam, 1e-3), s.last_adjoint_flags))
     assert np.array_equal(out[0][0], out[1][0])
     assert out[0][1] == out[1][1]
+
+
+def test_primitive_exchange_and_its_vjp():
+    """The input exchange U(rho, u, p) of the differentiable path runs in the
+    library: its value against the oracle's exchange, and its VJP against the
+    oracle's directional derivative: U is a polynomial of degree 3 in
+    (rho, u, p) (E holds rho |u|^2 / 2), so the Richardson combination
+    (4 D(eps) - D(2 eps)) / 3 of two central differences of the oracle's
+    exchange is exact up to rounding; <lam, J d> = <J^T lam, d> at 1e-12."""
+    import torch
+    from paper_2609_10849_b300.mhd import Solver
+    rng = np.random.default_rng(17)
+    o = Oracle(5, 4, 3, 3, 1.4)
+    s = Solver(5, 4, 3, 3, 1.4)
+    N = o.K * o.n2
+    rho = rng.uniform(0.5, 2.0, N)
+    u = rng.uniform(-1.0, 1.0, (3, N))
+    p = rng.uniform(0.2, 1.5, N)
+    z, zb = np.zeros(o.G), np.zeros(o.Z)
+
+    def oracle_U(r, v, q):
+        o.set_primitive(r, v, q, z, z, zb)
+        return o.get_state()[0]
+
+    U = np.zeros((5, N))
+    s.primitive_to_conservative(rho, np.ascontiguousarray(u), p, U)
+    Uo = oracle_U(rho, u, p)
+    assert np.abs(U - Uo).max() <= 1e-14 * np.abs(Uo).max()
+    dr, du, dp = rng.standard_normal(N), rng.standard_normal((3, N)), rng.standard_normal(N)
+    def central(eps):
+        return (oracle_U(rho + eps * dr, u + eps * du, p + eps * dp)
+                - oracle_U(rho - eps * dr, u - eps * du, p - eps * dp)) / (2 * eps)
+
+    jd = (4.0 * central(1e-2) - central(2e-2)) / 3.0
+    lam = rng.standard_normal((5, N))
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    g_rho, g_u, g_p = torch.empty(N, dtype=torch.float64, device="cuda"), t(np.zeros((3, N))), \
+        torch.empty(N, dtype=torch.float64, device="cuda")
+    s.primitive_to_conservative_vjp(t(rho), t(u), t(lam), g_rho, g_u, g_p)
+    lhs = float((lam * jd).sum())
+    rhs = float((g_rho.cpu().numpy() * dr).sum() + (g_u.cpu().numpy() * du).sum() + (g_p.cpu().numpy() * dp).sum())
+    assert abs(lhs - rhs) <= 1e-12 * (np.abs(lam).sum() * np.abs(jd).max()), (lhs, rhs)
