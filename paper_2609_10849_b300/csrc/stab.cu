@@ -314,51 +314,92 @@ __device__ __forceinline__ void oe_factors(const StatsView& V, int nc, int q, in
   __syncthreads();
 }
 
+// ---- k_oe_pp: hydro OE map then the positivity limiter ----------------------------
+// One thread per node (EB elements x (p+1)^2 threads, no padding).  The node
+// work (the sum-factorised modal transform there and back, the nodal parts of
+// the limiter) runs in registers; everything that is one value per element or
+// per (element, direction, order) - the rate lambda, the sensor sigma, the
+// factors D_l, the averages, the limiter's scalars and decisions - runs once
+// per element in flat item loops over the block, so that no FP64 instruction
+// is spent repeating an element's scalar in every node lane.
+template <int P>
+struct PCfg {
+  static constexpr int n = P + 1, n2 = n * n;
+  static constexpr int EB = P == 1 ? 64 : P == 2 ? 28 : P == 3 ? 16 : 10;  // ~256 threads
+  static constexpr int threads = EB * n2;
+};
+
+// Per-element scalars of the limiter in shared memory.
+enum { PE_RBAR = 0, PE_PBAR, PE_SA, PE_THR, PE_EPSP, PE_THP, PE_MODE, PE_TRHO, PE_TALL, PE_N };
+
 // frz (may be null): per element the frozen coefficients of the map, [K][p+3]:
 // D_0..D_p of the OE and the limiter factors t_rho (density) and t (others),
 // U'' = t U* + (1 - t) avg(U*), for the adjoint.
 template <int P>
-__global__ void __launch_bounds__(OCfg<P>::threads) k_oe_pp(double* __restrict__ S, StatsView V,
+__global__ void __launch_bounds__(PCfg<P>::threads) k_oe_pp(double* __restrict__ S, StatsView V,
                                                             const Tab* __restrict__ T, Mesh M, Stab prm,
                                                             const double* __restrict__ dtp, double dtfac,
                                                             unsigned* __restrict__ status,
                                                             double* __restrict__ frz) {
-  using C = OCfg<P>;
-  constexpr int n = C::n, n2 = C::n2, EB = C::EB, SW = C::SW;
-  __shared__ double su[5][EB * SW];
-  __shared__ double st[5][EB * SW];
+  using C = PCfg<P>;
+  constexpr int n = C::n, n2 = C::n2, EB = C::EB, TH = C::threads;
+  __shared__ double su[5][EB * n2];
+  __shared__ double st[5][EB * n2];
   __shared__ double ssig[EB][2 * n];
   __shared__ double sD[EB][n];
+  __shared__ double slam[EB][2];
+  __shared__ double sa[5][EB];
+  __shared__ double se[PE_N][EB];
   const size_t N = (size_t)M.K * n2, K = M.K;
-  const int tid = threadIdx.x, el = tid / SW, q = tid % SW;
-  const bool node = q < n2;
-  const int k = blockIdx.x * EB + el;
-  const bool valid = k < M.K && node;
-  const int kk = k < M.K ? k : M.K - 1;
-  const int ex = kk % M.nx, ey = kk / M.nx;
-  const int qq = node ? q : 0;
-  const int i = qq % n, j = qq / n;
+  const int tid = threadIdx.x, el = tid / n2, q = tid % n2;
+  const int k0 = blockIdx.x * EB;
+  const int k = k0 + el;
+  const bool valid = k < M.K;
+  const int kk = valid ? k : M.K - 1;
+  const int i = q % n, j = q / n;
   const double g = M.g;
   double u[5];
 #pragma unroll
-  for (int c = 0; c < 5; ++c) u[c] = node ? S[c * N + (size_t)kk * n2 + q] : 0.0;
+  for (int c = 0; c < 5; ++c) u[c] = S[c * N + (size_t)kk * n2 + q];
 
   if (prm.oe_hydro) {
-    double lam[2];
-    {
-      const double a0 = V.avg[kk], a1 = V.avg[K + kk], a2 = V.avg[2 * K + kk], a3 = V.avg[3 * K + kk],
-                   a4 = V.avg[4 * K + kk];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) su[c][tid] = u[c];
+    // rate lambda_{E,I} (eq. euler-oe-rate) from the element average, once per element
+    for (int e = tid; e < EB; e += TH) {
+      const int ke = min(k0 + e, M.K - 1);
+      const double a0 = V.avg[ke], a1 = V.avg[K + ke], a2 = V.avg[2 * K + ke], a3 = V.avg[3 * K + ke],
+                   a4 = V.avg[4 * K + ke];
       const double ir = rcp(a0);
       const double pb = (g - 1.0) * fma(-0.5 * ir, fma(a1, a1, fma(a2, a2, a3 * a3)), a4);
       const double cb = sqrt(g * pb * ir);
-      lam[0] = (2.0 * P + 1.0) * (fabs(a1 * ir) + cb) * M.ihx;
-      lam[1] = (2.0 * P + 1.0) * (fabs(a2 * ir) + cb) * M.ihy;
+      slam[e][0] = (2.0 * P + 1.0) * (fabs(a1 * ir) + cb) * M.ihx;
+      slam[e][1] = (2.0 * P + 1.0) * (fabs(a2 * ir) + cb) * M.ihy;
     }
-    oe_factors<P>(V, 5, q, el, kk, ex, ey, lam, prm.s_H * dtp[0] * dtfac, M, ssig, sD);
-#pragma unroll
-    for (int c = 0; c < 5; ++c) su[c][tid] = u[c];
+    // sigma_{r,I} (eq. euler-oe-sigma), once per (element, direction, order)
+    const int Lmax = M.nx > M.ny ? M.nx : M.ny;
+    for (int it = tid; it < EB * 2 * n; it += TH) {
+      const int e = it / (2 * n), w = it % (2 * n), I = w / n, r = w % n;
+      const int ke = min(k0 + e, M.K - 1), ex = ke % M.nx, ey = ke / M.nx;
+      const double iDelta = V.lineD[I * Lmax + (I == 0 ? ey : ex)];
+      const int kB = I == 0 ? ey * M.nx + wrap(ex + 1, M.nx) : wrap(ey + 1, M.ny) * M.nx + ex;
+      ssig[e][w] = sigma_rI(V, 5, n, I, r, ke, kB, iDelta, K);
+    }
     __syncthreads();
-    if (node) {  // T[b][i] = sum_j w_j P_b(x_j) U[j][i]   (b = j of this lane)
+    // D_l = exp(-s_H tau Theta_l) (eq. euler-oe-factor), once per (element, shell)
+    const double s_tau = prm.s_H * dtp[0] * dtfac;
+    for (int it = tid; it < EB * n; it += TH) {
+      const int e = it / n, l = it % n;
+      double Theta = 0.0;
+      for (int I = 0; I < 2; ++I) {
+        double ss = 0.0;
+        for (int r = 0; r <= l; ++r) ss += ssig[e][I * n + r];
+        Theta = fma(slam[e][I], ss, Theta);
+      }
+      sD[e][l] = l == 0 ? 1.0 : exp(-s_tau * Theta);
+    }
+    __syncthreads();
+    {  // T[b][i] = sum_j w_j P_b(x_j) U[j][i]   (b = j of this thread)
       double wl[n];
 #pragma unroll
       for (int jj = 0; jj < n; ++jj) wl[jj] = T->wp[jj] * T->Leg[jj][j];
@@ -366,12 +407,12 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_oe_pp(double* __restrict__
       for (int c = 0; c < 5; ++c) {
         double v = 0.0;
 #pragma unroll
-        for (int jj = 0; jj < n; ++jj) v = fma(wl[jj], su[c][el * SW + jj * n + i], v);
+        for (int jj = 0; jj < n; ++jj) v = fma(wl[jj], su[c][el * n2 + jj * n + i], v);
         st[c][tid] = v;
       }
     }
     __syncthreads();
-    if (node) {  // coef[b][a] = N_a N_b sum_i w_i P_a(x_i) T[b][i], damped by D_max(a,b)   (a = i, b = j)
+    {  // coef[b][a] = N_a N_b sum_i w_i P_a(x_i) T[b][i], damped by D_max(a,b)   (a = i, b = j)
       const double f = T->LegN[i] * T->LegN[j] * sD[el][i > j ? i : j];
       double wl[n];
 #pragma unroll
@@ -380,90 +421,138 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_oe_pp(double* __restrict__
       for (int c = 0; c < 5; ++c) {
         double v = 0.0;
 #pragma unroll
-        for (int ii = 0; ii < n; ++ii) v = fma(wl[ii], st[c][el * SW + j * n + ii], v);
+        for (int ii = 0; ii < n; ++ii) v = fma(wl[ii], st[c][el * n2 + j * n + ii], v);
         su[c][tid] = v;
       }
     }
     __syncthreads();
-    if (node) {  // V[b][i] = sum_a P_a(x_i) coef[b][a]
+    // V[b][i] = sum_a P_a(x_i) coef[b][a]
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        double v = 0.0;
+    for (int c = 0; c < 5; ++c) {
+      double v = 0.0;
 #pragma unroll
-        for (int a = 0; a < n; ++a) v = fma(T->Leg[i][a], su[c][el * SW + j * n + a], v);
-        st[c][tid] = v;
-      }
+      for (int a = 0; a < n; ++a) v = fma(T->Leg[i][a], su[c][el * n2 + j * n + a], v);
+      st[c][tid] = v;
     }
     __syncthreads();
-    if (node) {  // U[j][i] = sum_b P_b(x_j) V[b][i]
+    // U[j][i] = sum_b P_b(x_j) V[b][i]
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        double v = 0.0;
+    for (int c = 0; c < 5; ++c) {
+      double v = 0.0;
 #pragma unroll
-        for (int b = 0; b < n; ++b) v = fma(T->Leg[j][b], st[c][el * SW + b * n + i], v);
-        u[c] = v;
-      }
+      for (int b = 0; b < n; ++b) v = fma(T->Leg[j][b], st[c][el * n2 + b * n + i], v);
+      u[c] = v;
     }
+    __syncthreads();  // su and st are reused below
   }
 
   double t_rho = 1.0, t_all = 1.0;  // frozen limiter factors (adjoint)
   if (prm.pp) {
-    // Every shuffle below runs in all lanes (no per-element branch around it);
-    // the element decisions are taken afterwards from segment-uniform values.
     const double eps = DBL_EPSILON, eps_rho = 64.0 * eps;
-    const double wq = node ? 0.25 * T->wp[i] * T->wp[j] : 0.0;
-    const int lead = (threadIdx.x & 31) & ~(SW - 1);
-    double a[5];
 #pragma unroll
-    for (int c = 0; c < 5; ++c)  // average of U* (eq. euler-pp-average), identical in every lane of the segment
-      a[c] = __shfl_sync(0xffffffffu, seg_sum<SW>(wq * u[c]), lead);
-    const double rbar = a[0];
-    // one reciprocal of the average density: 1/rho-bar for p-bar, and 1/max(rho-bar, eps_rho)
-    // (the clamped value, a constant below eps_rho) for the cancellation scale
-    const double ira0 = rcp(a[0]);
-    const double ira = a[0] > eps_rho ? ira0 : 1.0 / eps_rho;
-    const double ma2 = fma(a[1], a[1], fma(a[2], a[2], a[3] * a[3]));
-    const double pbar = (g - 1.0) * fma(-0.5 * ma2, ira0, a[4]);
-    const bool bad = !(rbar > 0.0) || !(pbar > 0.0) || !isfinite(rbar) || !isfinite(pbar);
-    // density scaling (eq. euler-pp-density)
-    const double rmin = seg_min<SW>(node ? u[0] : DBL_MAX);
-    double th_r = 1.0;
-    if (rmin < eps_rho) {
-      const double den = rbar - rmin;
-      th_r = den > 0.0 ? fmin(1.0, fmax(0.0, (rbar - eps_rho) / den)) : 1.0;
+    for (int c = 0; c < 5; ++c) su[c][tid] = u[c];
+    __syncthreads();
+    // element averages of U* (eq. euler-pp-average), once per (element, component)
+    for (int it = tid; it < EB * 5; it += TH) {
+      const int e = it / 5, c = it % 5;
+      double s = 0.0;
+#pragma unroll
+      for (int t = 0; t < n2; ++t) s = fma(T->Wq[t], su[c][e * n2 + t], s);
+      sa[c][e] = s;
     }
+    __syncthreads();
+    // density scaling (eq. euler-pp-density) and the average pressure, once per element
+    for (int e = tid; e < EB; e += TH) {
+      const double a0 = sa[0][e], a1 = sa[1][e], a2 = sa[2][e], a3 = sa[3][e], a4 = sa[4][e];
+      // one reciprocal of the average density: 1/rho-bar for p-bar, and 1/max(rho-bar, eps_rho)
+      // (the clamped value, a constant below eps_rho) for the cancellation scale
+      const double ira0 = rcp(a0);
+      const double ira = a0 > eps_rho ? ira0 : 1.0 / eps_rho;
+      const double ma2 = fma(a1, a1, fma(a2, a2, a3 * a3));
+      const double pbar = (g - 1.0) * fma(-0.5 * ma2, ira0, a4);
+      long long mn = dkey(DBL_MAX);
+#pragma unroll
+      for (int t = 0; t < n2; ++t) {
+        const long long kv = dkey(su[0][e * n2 + t]);
+        mn = kv < mn ? kv : mn;
+      }
+      const double rmin = dkey_inv(mn);
+      double th_r = 1.0;
+      if (rmin < eps_rho) {
+        const double den = a0 - rmin;
+        th_r = den > 0.0 ? fmin(1.0, fmax(0.0, (a0 - eps_rho) / den)) : 1.0;
+      }
+      se[PE_RBAR][e] = a0;
+      se[PE_PBAR][e] = pbar;
+      se[PE_SA][e] = fma(0.5 * ma2, ira, fabs(a4));
+      se[PE_THR][e] = th_r;
+      se[PE_MODE][e] = (!(a0 > 0.0) || !(pbar > 0.0) || !isfinite(a0) || !isfinite(pbar)) ? 2.0 : 0.0;
+    }
+    __syncthreads();
+    // nodal pressures after the density scaling, and their cancellation scales
+    const double rbar = se[PE_RBAR][el], th_r = se[PE_THR][el];
     double r0 = u[0];
     if (th_r < 1.0) r0 = rbar + th_r * (u[0] - rbar);
-    // pressure-cancellation scale and floor (eq. euler-pp-floors), pressure scaling (eq. euler-pp-pressure)
-    const double m2 = fma(u[1], u[1], fma(u[2], u[2], u[3] * u[3]));
-    const double ir0t = rcp(r0);  // nodes are >= eps_rho after the density scaling
-    const double ir0 = r0 >= eps_rho ? ir0t : 1.0 / eps_rho;
-    const double Sq = node ? fma(0.5 * m2, ir0, fabs(u[4])) : 0.0;
-    const double pq = node ? (g - 1.0) * fma(-0.5 * m2, ir0t, u[4]) : DBL_MAX;
-    const double Sa = fma(0.5 * ma2, ira, fabs(a[4]));
-    const double Smax = fmax(Sa, seg_max<SW>(Sq));
-    const double pmin = seg_min<SW>(pq);
-    const double eps_p = fmax(64.0 * eps, 8192.0 * eps * Smax);
-    if (bad) {
-      if (q == 0 && k < M.K) atomicOr(status, ST_INADMISSIBLE);
-    } else if (rbar <= eps_rho || pbar <= eps_p) {  // vacuum-like average: collapse (reading R9)
+    {
+      const double m2 = fma(u[1], u[1], fma(u[2], u[2], u[3] * u[3]));
+      const double ir0t = rcp(r0);  // nodes are >= eps_rho after the density scaling
+      const double ir0 = r0 >= eps_rho ? ir0t : 1.0 / eps_rho;
+      st[0][tid] = fma(0.5 * m2, ir0, fabs(u[4]));             // S_p of the node
+      st[1][tid] = (g - 1.0) * fma(-0.5 * m2, ir0t, u[4]);     // p of the node
+    }
+    __syncthreads();
+    // floor eps_p (eq. euler-pp-floors), collapse or pressure scaling (eq.
+    // euler-pp-pressure, reading R9), once per element
+    for (int e = tid; e < EB; e += TH) {
+      long long smax = dkey(se[PE_SA][e]), pmn = dkey(DBL_MAX);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) u[c] = a[c];
-      t_rho = t_all = 0.0;
-    } else {
-      u[0] = r0;
-      if (th_r < 1.0) t_rho = th_r;
-      if (pmin < eps_p) {
-        const double den = pbar - pmin;
-        const double th_p = den > 0.0 ? fmin(1.0, fmax(0.0, (pbar - eps_p) / den)) : 1.0;
-        if (th_p < 1.0) {
-#pragma unroll
-          for (int c = 0; c < 5; ++c) u[c] = a[c] + th_p * (u[c] - a[c]);
-          t_rho *= th_p;
-          t_all = th_p;
+      for (int t = 0; t < n2; ++t) {
+        const long long a = dkey(st[0][e * n2 + t]), b = dkey(st[1][e * n2 + t]);
+        smax = a > smax ? a : smax;
+        pmn = b < pmn ? b : pmn;
+      }
+      const double Smax = dkey_inv(smax), pmin = dkey_inv(pmn);
+      const double eps_p = fmax(64.0 * eps, 8192.0 * eps * Smax);
+      const double rb = se[PE_RBAR][e], pbar = se[PE_PBAR][e], thr = se[PE_THR][e];
+      double mode = se[PE_MODE][e], thp = 1.0, trho = 1.0, tall = 1.0;
+      if (mode == 0.0) {
+        if (rb <= eps_rho || pbar <= eps_p) {  // vacuum-like average: collapse (reading R9)
+          mode = 1.0;
+          trho = tall = 0.0;
+        } else {
+          if (thr < 1.0) trho = thr;
+          if (pmin < eps_p) {
+            const double den = pbar - pmin;
+            thp = den > 0.0 ? fmin(1.0, fmax(0.0, (pbar - eps_p) / den)) : 1.0;
+            if (thp < 1.0) {
+              trho *= thp;
+              tall = thp;
+            }
+          }
         }
       }
+      se[PE_MODE][e] = mode;
+      se[PE_THP][e] = thp;
+      se[PE_TRHO][e] = trho;
+      se[PE_TALL][e] = tall;
     }
+    __syncthreads();
+    const double mode = se[PE_MODE][el];
+    if (mode == 2.0) {
+      if (q == 0 && valid) atomicOr(status, ST_INADMISSIBLE);
+    } else if (mode == 1.0) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) u[c] = sa[c][el];
+    } else {
+      u[0] = r0;
+      const double thp = se[PE_THP][el];
+      if (thp < 1.0) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) u[c] = sa[c][el] + thp * (u[c] - sa[c][el]);
+      }
+    }
+    t_rho = se[PE_TRHO][el];
+    t_all = se[PE_TALL][el];
   }
   {
     unsigned act = 0u;
@@ -471,7 +560,7 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_oe_pp(double* __restrict__
     if (t_rho < 1.0 || t_all < 1.0) act |= ACT_PP;
     warp_or(prm.activity, act);
   }
-  if (frz && q == 0 && k < M.K) {
+  if (frz && q == 0 && valid) {
     double* f = frz + (size_t)k * (n + 2);
 #pragma unroll
     for (int l = 0; l < n; ++l) f[l] = prm.oe_hydro ? sD[el][l] : 1.0;
@@ -501,7 +590,7 @@ static void stab_hydro_impl(double* S, unsigned* status, const Tab* T, const Mes
                             const double* dtp, double dtfac, double* work, double* frz, cudaStream_t st) {
   StatsView V = stats_view(work, P, M);
   if (prm.oe_hydro) launch_stats<P>(S, (size_t)M.K * (P + 1) * (P + 1), 5, V, T, M, st);
-  using C = OCfg<P>;
+  using C = PCfg<P>;
   k_oe_pp<P><<<(unsigned)((M.K + C::EB - 1) / C::EB), C::threads, 0, st>>>(S, V, T, M, prm, dtp, dtfac, status,
                                                                              frz);
 }
@@ -950,67 +1039,148 @@ void stab_vel_prep(int p, const double* rho, double* chol, const Tab* T, const M
   }
 }
 
-// Velocity OE map with heating of e; one element per segment of SW lanes.
+// Velocity OE map with heating of e.  One thread per node (EB elements x
+// (p+1)^2 threads, no padding); B at the DG nodes is sum-factorised over the
+// block (an x-pass of the closures, then a y-pass, in the order of the
+// single-point evaluation B_eval, so the values are the same bit for bit); the
+// rate, the sensor and the factors are computed once per element or per
+// (element, direction, order) in flat item loops, as in k_oe_pp.
 // frz (may be null): the damping factors D_0..D_p of every element, [K][p+1],
 // for the adjoint (frozen coefficients).
+template <int P>
+struct VCfg {
+  static constexpr int n = P + 1, n2 = n * n;
+  static constexpr int EB = P == 1 ? 64 : P == 2 ? 28 : P == 3 ? 8 : 4;
+  static constexpr int threads = EB * n2;
+};
+
 template <int P, int KM, bool R2 = false>
-__global__ void __launch_bounds__(OCfg<P>::threads) k_vel_oe(const double* __restrict__ rho, double* __restrict__ Y,
+__global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __restrict__ rho, double* __restrict__ Y,
                                                              const double* __restrict__ B,
                                                              const double* __restrict__ Psi, StatsView V,
                                                              const Tab* __restrict__ T, Mesh M, Stab prm,
                                                              const double* __restrict__ dtp, double dtfac,
                                                              double* __restrict__ frz) {
-  using C = OCfg<P>;
-  constexpr int n = C::n, n2 = C::n2, EB = C::EB, SW = C::SW;
-  __shared__ double sPsi[EB][n2 * n2];
-  __shared__ double sWu[3][EB * SW];
-  __shared__ double sc[3][EB * SW];
-  __shared__ double ssig[EB][2 * n];
-  __shared__ double sD[EB][n];
-  const size_t N = (size_t)M.K * n2, Z = (size_t)M.K * (KM + 1) * (KM + 1);
-  const int tid = threadIdx.x, el = tid / SW, q = tid % SW;
-  const bool node = q < n2;
-  const int k = blockIdx.x * EB + el;
-  const bool valid = k < M.K && node;
-  const int kk = k < M.K ? k : M.K - 1;
-  const int ex = kk % M.nx, ey = kk / M.nx;
-  const int qq = node ? q : 0;
-  const int i = qq % n, j = qq / n;
+  using C = VCfg<P>;
+  constexpr int n = C::n, n2 = C::n2, EB = C::EB, TH = C::threads;
+  constexpr int mm = KM + 1, mL = KM + 2;
   // 2D2V (R2): u_z = B_z = 0, so only u_x, u_y are filtered (u_z stays 0)
   constexpr int ND = R2 ? 2 : 3;
+  __shared__ double sPsi[EB][n2 * n2];
+  __shared__ double sWu[3][EB * n2];
+  __shared__ double sc[3][EB * n2];
+  __shared__ double sB[EB][mm * mL + mL * mm + mm * mm];   // closures of Bx, By and Bz
+  __shared__ double sT[EB][mm * n + mL * n + mm * n];      // x-passes
+  __shared__ double sax[2][EB * n2];                       // |u_I| + |B|/sqrt(rho) per node
+  __shared__ double ssig[EB][2 * n];
+  __shared__ double sD[EB][n];
+  __shared__ double slam[EB][2];
+  const size_t N = (size_t)M.K * n2, Z = (size_t)M.K * mm * mm;
+  const int tid = threadIdx.x, el = tid / n2, q = tid % n2;
+  const int k0 = blockIdx.x * EB;
+  const int k = k0 + el;
+  const bool valid = k < M.K;
+  const int kk = valid ? k : M.K - 1;
+  const int i = q % n, j = q / n;
   double u[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-  for (int d = 0; d < ND; ++d) u[d] = node ? Y[(1 + d) * N + (size_t)kk * n2 + q] : 0.0;
-  const double r_ = node ? rho[(size_t)kk * n2 + q] : 1.0;
-  for (int t = q; t < n2 * n2; t += SW) sPsi[el][t] = Psi[(size_t)kk * n2 * n2 + t];
-  // rate lambda_M from the nodal max of |u_I| + |B_h| / sqrt(rho) (eq. magnetic-oe-rate)
-  double lam[2];
-  {
-    double Bv[3] = {0.0, 0.0, 0.0};
-#pragma unroll
-    for (int d = 0; d < ND; ++d)
-      Bv[d] = B_eval<KM>(B, Z, d, ex, ey, T->L_P[i], T->G_P[i], T->M_P[i], T->L_P[j], T->G_P[j], T->M_P[j], M);
-    const double va = sqrt(fma(Bv[0], Bv[0], fma(Bv[1], Bv[1], Bv[2] * Bv[2])) * rcp(r_));
-    const double ax = seg_max<SW>(node ? fabs(u[0]) + va : 0.0);
-    const double ay = seg_max<SW>(node ? fabs(u[1]) + va : 0.0);
-    lam[0] = (2.0 * P + 1.0) * M.ihx * ax;
-    lam[1] = (2.0 * P + 1.0) * M.ihy * ay;
+  for (int d = 0; d < ND; ++d) u[d] = Y[(1 + d) * N + (size_t)kk * n2 + q];
+  const double r_ = rho[(size_t)kk * n2 + q];
+  for (int t = q; t < n2 * n2; t += n2) sPsi[el][t] = Psi[(size_t)kk * n2 * n2 + t];
+  // closures of B (Bx [b < mm][a < mL], By [b < mL][a < mm], Bz [b][a]) of the block's elements
+  constexpr int NB = mm * mL + mL * mm + (R2 ? 0 : mm * mm);
+  for (int it = tid; it < EB * NB; it += TH) {
+    const int e = it / NB, w = it % NB;
+    const int ke = min(k0 + e, M.K - 1), ex = ke % M.nx, ey = ke / M.nx;
+    double v;
+    if (w < mm * mL) v = bx_cl<KM>(B, ex, ey, w % mL, w / mL, M);
+    else if (w < 2 * mm * mL) { const int r = w - mm * mL; v = by_cl<KM>(B + Z, ex, ey, r % mm, r / mm, M); }
+    else v = B[2 * Z + (size_t)ke * mm * mm + (w - 2 * mm * mL)];
+    sB[e][w] = v;
   }
-  const double W = node ? M.Jdet * T->wp[i] * T->wp[j] * r_ : 0.0;
+  __syncthreads();
+  // x-passes onto the DG x-nodes: Bx rows (Gauss y), By rows (GLL(k+1) y), Bz rows (GLL(k) y)
+  constexpr int NT = mm * n + mL * n + (R2 ? 0 : mm * n);
+  for (int it = tid; it < EB * NT; it += TH) {
+    const int e = it / NT, w = it % NT;
+    double v = 0.0;
+    if (w < mm * n) {
+      const int b = w / n, ii = w % n;
+#pragma unroll
+      for (int a = 0; a < mL; ++a) v = fma(T->L_P[ii][a], sB[e][b * mL + a], v);
+    } else if (w < mm * n + mL * n) {
+      const int r = w - mm * n, b = r / n, ii = r % n;
+#pragma unroll
+      for (int a = 0; a < mm; ++a) v = fma(T->G_P[ii][a], sB[e][mm * mL + b * mm + a], v);
+    } else {
+      const int r = w - mm * n - mL * n, b = r / n, ii = r % n;
+#pragma unroll
+      for (int a = 0; a < mm; ++a) v = fma(T->M_P[ii][a], sB[e][2 * mm * mL + b * mm + a], v);
+    }
+    sT[e][w] = v;
+  }
+  __syncthreads();
+  {  // y-passes at this node, |B_h| / sqrt(rho) (eq. magnetic-oe-rate)
+    double bx = 0.0, by = 0.0, bz = 0.0;
+#pragma unroll
+    for (int b = 0; b < mm; ++b) bx = fma(T->G_P[j][b], sT[el][b * n + i], bx);
+#pragma unroll
+    for (int b = 0; b < mL; ++b) by = fma(T->L_P[j][b], sT[el][mm * n + b * n + i], by);
+    if constexpr (!R2) {
+#pragma unroll
+      for (int b = 0; b < mm; ++b) bz = fma(T->M_P[j][b], sT[el][mm * n + mL * n + b * n + i], bz);
+    }
+    const double va = sqrt(fma(bx, bx, fma(by, by, bz * bz)) * rcp(r_));
+    sax[0][tid] = fabs(u[0]) + va;
+    sax[1][tid] = fabs(u[1]) + va;
+  }
+  const double W = M.Jdet * T->wp[i] * T->wp[j] * r_;
 #pragma unroll
   for (int d = 0; d < ND; ++d) sWu[d][tid] = W * u[d];
-  oe_factors<P>(V, ND, q, el, kk, ex, ey, lam, prm.s_M * dtp[0] * dtfac, M, ssig, sD);  // syncs
-  if (frz && q < n && k < M.K) frz[(size_t)k * n + q] = sD[el][q];
-  warp_or(prm.activity, sD[el][P] < 0.99 ? ACT_OE_VEL : 0u);
-  // coefficients c_alpha = sum_t Psi[t][alpha] W_t u_t (lane q plays alpha)
-  if (node) {
+  __syncthreads();
+  // rate lambda_M,I (eq. magnetic-oe-rate): nodal maxima (integer keys), once per element
+  for (int it = tid; it < EB * 2; it += TH) {
+    const int e = it / 2, I = it % 2;
+    long long mx = dkey(0.0);
 #pragma unroll
-    for (int d = 0; d < ND; ++d) {
-      double s = 0.0;
-#pragma unroll
-      for (int t = 0; t < n2; ++t) s = fma(sPsi[el][t * n2 + q], sWu[d][el * SW + t], s);
-      sc[d][tid] = s;
+    for (int t = 0; t < n2; ++t) {
+      const long long kv = dkey(sax[I][e * n2 + t]);
+      mx = kv > mx ? kv : mx;
     }
+    slam[e][I] = (2.0 * P + 1.0) * (I == 0 ? M.ihx : M.ihy) * dkey_inv(mx);
+  }
+  // sigma_{r,I} (eq. magnetic-oe-sensor), once per (element, direction, order)
+  const int Lmax = M.nx > M.ny ? M.nx : M.ny;
+  for (int it = tid; it < EB * 2 * n; it += TH) {
+    const int e = it / (2 * n), w = it % (2 * n), I = w / n, r = w % n;
+    const int ke = min(k0 + e, M.K - 1), ex = ke % M.nx, ey = ke / M.nx;
+    const double iDelta = V.lineD[I * Lmax + (I == 0 ? ey : ex)];
+    const int kB = I == 0 ? ey * M.nx + wrap(ex + 1, M.nx) : wrap(ey + 1, M.ny) * M.nx + ex;
+    ssig[e][w] = sigma_rI(V, ND, n, I, r, ke, kB, iDelta, M.K);
+  }
+  __syncthreads();
+  // D_l = exp(-s_M tau Theta_l) (eq. magnetic-oe-factor), once per (element, shell)
+  const double s_tau = prm.s_M * dtp[0] * dtfac;
+  for (int it = tid; it < EB * n; it += TH) {
+    const int e = it / n, l = it % n;
+    double Theta = 0.0;
+    for (int I = 0; I < 2; ++I) {
+      double ss = 0.0;
+      for (int r = 0; r <= l; ++r) ss += ssig[e][I * n + r];
+      Theta = fma(slam[e][I], ss, Theta);
+    }
+    sD[e][l] = l == 0 ? 1.0 : exp(-s_tau * Theta);
+  }
+  __syncthreads();
+  if (frz && q < n && valid) frz[(size_t)k * n + q] = sD[el][q];
+  warp_or(prm.activity, sD[el][P] < 0.99 ? ACT_OE_VEL : 0u);
+  // coefficients c_alpha = sum_t Psi[t][alpha] W_t u_t (thread q plays alpha)
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    double s = 0.0;
+#pragma unroll
+    for (int t = 0; t < n2; ++t) s = fma(sPsi[el][t * n2 + q], sWu[d][el * n2 + t], s);
+    sc[d][tid] = s;
   }
   __syncthreads();
   if (valid) {
@@ -1022,7 +1192,7 @@ __global__ void __launch_bounds__(OCfg<P>::threads) k_vel_oe(const double* __res
       for (int l = 0; l <= P; ++l) {  // shell l holds basis indices [l^2, (l+1)^2)
         double wl = 0.0;
 #pragma unroll
-        for (int al = l * l; al < (l + 1) * (l + 1); ++al) wl = fma(sc[d][el * SW + al], sPsi[el][q * n2 + al], wl);
+        for (int al = l * l; al < (l + 1) * (l + 1); ++al) wl = fma(sc[d][el * n2 + al], sPsi[el][q * n2 + al], wl);
         const double Dl = sD[el][l];
         unew = fma(Dl, wl, unew);
         if (l > 0) de = fma(0.5 * (1.0 - Dl * Dl) * wl, wl, de);
@@ -1047,10 +1217,10 @@ void stab_vel(int p, int k, const double* rho, double* Y, const double* B, const
   }
 #define MHD_VOE_CASE(PP, KK)                                                                                    \
   if (prm.reduced)                                                                                             \
-    k_vel_oe<PP, KK, true><<<(unsigned)((M.K + OCfg<PP>::EB - 1) / OCfg<PP>::EB), OCfg<PP>::threads, 0, st>>>( \
+    k_vel_oe<PP, KK, true><<<(unsigned)((M.K + VCfg<PP>::EB - 1) / VCfg<PP>::EB), VCfg<PP>::threads, 0, st>>>( \
         rho, Y, B, chol, V, T, M, prm, dtp, dtfac, frz);                                                        \
   else                                                                                                         \
-    k_vel_oe<PP, KK><<<(unsigned)((M.K + OCfg<PP>::EB - 1) / OCfg<PP>::EB), OCfg<PP>::threads, 0, st>>>(       \
+    k_vel_oe<PP, KK><<<(unsigned)((M.K + VCfg<PP>::EB - 1) / VCfg<PP>::EB), VCfg<PP>::threads, 0, st>>>(       \
         rho, Y, B, chol, V, T, M, prm, dtp, dtfac, frz)
   MHD_DISPATCH_PK(p, k, MHD_VOE_CASE);
 #undef MHD_VOE_CASE
