@@ -93,11 +93,15 @@ void hydro_substep(mhd_ctx* c, double fac) {
   const double* in[3] = {c->U, c->S1, c->S2};
   double* out[3] = {c->S1, c->S2, c->U};
   bool stab = c->prm.oe_hydro || c->prm.pp;
+  // With the limiter on, its own test of the element averages of the OE output
+  // (which keeps the raw averages) is the admissibility check (§3.2.3, reading
+  // R9): the volume kernel then skips its raw-average reduction.
+  unsigned* vol_status = c->prm.pp ? nullptr : c->status;
   for (int s = 0; s < 3; ++s) {
     { Prof pr(c, KC_FACE); hydro_face(c->p, in[s], c->Fx, c->Fy, c->M, c->st); }
     { Prof pr(c, KC_VOL);
-      hydro_vol(c->p, 1, in[s], c->U, c->Fx, c->Fy, out[s], stab ? c->avg : nullptr, c->status, c->T, c->M, c->dt,
-                fac, RK_A[s], RK_B[s], s == 0, c->st); }
+      hydro_vol(c->p, 1, in[s], c->U, c->Fx, c->Fy, out[s], nullptr, vol_status, c->T, c->M, c->dt, fac, RK_A[s],
+                RK_B[s], s == 0, c->st); }
     c->launches += 2;
     if (stab) {
       Prof pr(c, KC_STAB_H);
@@ -244,7 +248,6 @@ int mhd_create(const mhd_mesh_t* mesh, int p, int k, double gamma, mhd_ctx** out
   if ((e = dalloc(c, &c->Fy, 5 * K * c->n)) != cudaSuccess) goto oom;
   if ((e = dalloc(c, &c->LJ, mag_load_doubles(p, k, (int)K))) != cudaSuccess) goto oom;
   if ((e = dalloc(c, &c->LE, mag_load_doubles(p, k, (int)K))) != cudaSuccess) goto oom;
-  if ((e = dalloc(c, &c->avg, 5 * K)) != cudaSuccess) goto oom;
   if ((e = dalloc(c, &c->eta, K)) != cudaSuccess) goto oom;
   if ((e = dalloc(c, &c->dt, 4)) != cudaSuccess) goto oom;
   if ((e = dalloc(c, &c->work, std::max(stab_work_doubles(p, k, c->M), 12 * K))) != cudaSuccess) goto oom;

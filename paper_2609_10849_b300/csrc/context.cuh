@@ -111,7 +111,7 @@ struct mhd_ctx {
   double *U, *Usave, *S1, *S2;
   double *B, *Bsave, *Ba, *Bb;
   double *Y0, *Ya, *Yb;
-  double *Fx, *Fy, *LJ, *LE, *avg, *eta, *dt, *work, *chol, *io;
+  double *Fx, *Fy, *LJ, *LE, *eta, *dt, *work, *chol, *io;
   unsigned* status;
   unsigned long long* maxbits;
   double* h_pinned;  // small pinned host scratch

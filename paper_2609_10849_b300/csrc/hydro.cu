@@ -39,17 +39,36 @@ __device__ __forceinline__ int pair_index(int a, int b) {  // a < b
 // f = (aL - aR)/(aL + aR) is passed in; returns 1/F in *invF and F.  On the
 // series branch 1/F is the reciprocal series 1 - u/3 - 4u^2/45 - 44u^3/945
 // (from F (1/F) = 1 term by term; the first omitted term is below 1e-17).
-__device__ __forceinline__ double logmean_factor(double aL, double aR, double f, double* invF) {
+// On the logarithm branch log(aL/aR) is taken as lL - lR from per-node
+// logarithms when the block has them (have_logs; R1 allows it: the two differ
+// by ~1e-14 relative there), else as log(aL/aR); F = log/(2f) and
+// 1/F = 2f/log by refined reciprocals (|f| >= 0.01 and |log| >= 0.02 here).
+__device__ __forceinline__ double logmean_factor(double aL, double aR, double f, bool have_logs, double lL,
+                                                 double lR, double* invF) {
   double u = f * f;
   // u >= 0: the branch test compares bit patterns (integer pipe), equal to u < 1e-4
   if (__double_as_longlong(u) < __double_as_longlong(1e-4)) {
     *invF = fma(u, fma(u, fma(u, -44.0 / 945.0, -4.0 / 45.0), -1.0 / 3.0), 1.0);
     return fma(u, fma(u, fma(u, 1.0 / 7.0, 1.0 / 5.0), 1.0 / 3.0), 1.0);
   }
-  double lz = log(aL / aR);
-  double F = lz / (2.0 * f);
-  *invF = (2.0 * f) / lz;
-  return F;
+  const double lz = have_logs ? lL - lR : log(aL / aR);
+  *invF = 2.0 * f * rcp(lz);
+  return 0.5 * lz * rcp(f);
+}
+
+// Whether node value x of an element needs the logarithm branch against the
+// element's reference node value r: a pair (a, b) of the element takes the
+// logarithm branch only if a/b >= 1.0202 or <= 1/1.0202 (|f| >= 0.01), which
+// needs two nodes whose ratio is that large.  For positive doubles the bit
+// patterns are monotone and one ulp is a relative step of at most 2^-52, so
+// |bits(x) - bits(r)| < 0.0099 2^52 gives x/r within exp(+-0.0099) and any
+// pair of such nodes a ratio below exp(0.0198) = 1.0200 < 1.0202 (integer
+// pipe only).  Non-positive or NaN values give huge differences: logs are
+// taken (and are NaN where the value is, as the pair formula would be).
+__device__ __forceinline__ bool far_from_reference(double x, double r) {
+  const long long d = __double_as_longlong(x) - __double_as_longlong(r);
+  constexpr long long lim = 44585636310967LL;  // 0.0099 * 2^52, rounded down
+  return d >= lim || d <= -lim;
 }
 
 __device__ __forceinline__ void llf_flux_dev(int d, const double* Um, const double* Up, double g, double* F) {
@@ -109,6 +128,7 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __r
   using C = HCfg<P, EBv>;
   constexpr int n = C::n, n2 = C::n2, EB = C::EB, NP = C::npairs, NPL = C::npl;
   __shared__ double sp[6][EB * n2];           // rho/2, ux/2, uy/2, uz/2, beta, |u|^2/2
+  __shared__ double sl[2][EB * n2];           // log(rho/2), log(beta/2), when a pair needs them
   __shared__ double sf[5][EB * NP];           // pair fluxes
   __shared__ double savg[5][EB];
   const size_t N = (size_t)M.K * n2;
@@ -135,6 +155,16 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __r
     sp[5][tid] = 0.5 * u2;
   }
   __syncthreads();
+  // per-node logarithms for the whole block, only if some element of it has a
+  // node far enough from its first node for a pair to take the log branch
+  // (one block vote; the block's threads take the same branch)
+  const bool far = far_from_reference(sp[0][tid], sp[0][el * n2]) || far_from_reference(sp[4][tid], sp[4][el * n2]);
+  const bool have_logs = __syncthreads_or(far) != 0;
+  if (have_logs) {
+    sl[0][tid] = log(sp[0][tid]);
+    sl[1][tid] = log(sp[4][tid]);
+    __syncthreads();
+  }
 
   // ---- pair fluxes ------------------------------------------------------------
   const double ig1 = M.ig1;
@@ -153,8 +183,10 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __r
     double isr = rcp(hr), isb = rcp(sb);
     double fr = (rL - rR) * isr, fb = (bL - bR) * isb;
     double iFr, iFb;
-    double Fr = logmean_factor(rL, rR, fr, &iFr);
-    double Fb = logmean_factor(bL, bR, fb, &iFb);
+    double Fr = have_logs ? logmean_factor(rL, rR, fr, true, sl[0][qa], sl[0][qb], &iFr)
+                          : logmean_factor(rL, rR, fr, false, 0.0, 0.0, &iFr);
+    double Fb = have_logs ? logmean_factor(bL, bR, fb, true, sl[1][qa], sl[1][qb], &iFb)
+                          : logmean_factor(bL, bR, fb, false, 0.0, 0.0, &iFb);
     double rlog = hr * iFr;                             // rho^log
     double ua0 = sp[1][qa] + sp[1][qb];
     double ua1 = sp[2][qa] + sp[2][qb];
@@ -178,9 +210,18 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __r
 
   // ---- gather: L = -(2/hx)[2 sum D F + end terms] - (2/hy)[...] -----------------
   const int i = q % n, j = q / n;
-  double Drow_i[n], Drow_j[n];
+  // the p off-diagonal terms of rows i and j of D, visited as r = i + o (mod n),
+  // o = 1..p: no lane-dependent skip of the diagonal, so no predicated-off FMA
+  double Dx[P], Dy[P];
+  int px[P], py[P];
 #pragma unroll
-  for (int r = 0; r < n; ++r) { Drow_i[r] = T->D[i][r]; Drow_j[r] = T->D[j][r]; }
+  for (int o = 1; o < n; ++o) {
+    const int rx = i + o < n ? i + o : i + o - n, ry = j + o < n ? j + o : j + o - n;
+    Dx[o - 1] = T->D[i][rx];
+    Dy[o - 1] = T->D[j][ry];
+    px[o - 1] = el * NP + j * NPL + pair_index(min(i, rx), max(i, rx));
+    py[o - 1] = el * NP + NP / 2 + i * NPL + pair_index(min(j, ry), max(j, ry));
+  }
   const double cx = -4.0 * M.ihx, cy = -4.0 * M.ihy;
   constexpr double w0i = 0.5 * P * (P + 1);  // 1 / w_0 of GLL(p): w_0 = 2 / (p (p + 1))
   const double fx = 2.0 * M.ihx * w0i, fy = 2.0 * M.ihy * w0i;
@@ -198,16 +239,9 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __r
   for (int c = 0; c < 5; ++c) {
     double sx = 0.0, sy = 0.0;
 #pragma unroll
-    for (int r = 0; r < n; ++r) {
-      if (r == i) continue;
-      int pi_ = pair_index(min(i, r), max(i, r));
-      sx = fma(Drow_i[r], sf[c][el * NP + j * NPL + pi_], sx);
-    }
-#pragma unroll
-    for (int r = 0; r < n; ++r) {
-      if (r == j) continue;
-      int pi_ = pair_index(min(j, r), max(j, r));
-      sy = fma(Drow_j[r], sf[c][el * NP + NP / 2 + i * NPL + pi_], sy);
+    for (int o = 0; o < P; ++o) {
+      sx = fma(Dx[o], sf[c][px[o]], sx);
+      sy = fma(Dy[o], sf[c][py[o]], sy);
     }
     double v = fma(cx, sx, cy * sy);
     // end nodes: -(2/hx)[-F*_left/w_0] and -(2/hx)[+F*_right/w_p] (w_p = w_0)
@@ -235,6 +269,9 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __r
 #pragma unroll
     for (int c = 0; c < 5; ++c) out[c * N + gi] = Cv[c];
   }
+  // no status word: the caller's limiter tests the same averages itself (the
+  // OE before it keeps them), so the reduction below is skipped (block-uniform)
+  if (status == nullptr && avg_out == nullptr) return;
   // ---- raw element averages and the admissibility check --------------------------
   double a0, a1, a2, a3, a4;
   if constexpr (n2 == 4 || n2 == 16) {
@@ -271,8 +308,10 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __r
     // rho > 0 and p > 0  <=>  rho > 0 and rho E - |m|^2/2 > 0
     double pe = fma(a0, a4, -0.5 * fma(a1, a1, fma(a2, a2, a3 * a3)));
     bool fin = isfinite(a0) && isfinite(a1) && isfinite(a2) && isfinite(a3) && isfinite(a4);
-    if (!fin) atomicOr(status, ST_NONFINITE | ST_INADMISSIBLE);
-    else if (!(a0 > 0.0) || !(pe > 0.0)) atomicOr(status, ST_INADMISSIBLE);
+    if (status) {
+      if (!fin) atomicOr(status, ST_NONFINITE | ST_INADMISSIBLE);
+      else if (!(a0 > 0.0) || !(pe > 0.0)) atomicOr(status, ST_INADMISSIBLE);
+    }
   }
 }
 
