@@ -44,10 +44,13 @@ FALLBACK_HBM_GBS = 6400.0   # profiling recipe's fallback copy bandwidth
 # resistivity and velocity filter active, with the paper's constants.
 STAB = dict(oe_hydro=1, oe_vel=1, pp=1, ar=1, s_H=0.02, s_M=0.02, C_s=5.0, C_eta=0.2)
 WORKLOADS = {"blast": ("blast", 1024), "orszag_tang": ("orszag_tang", 256)}
-# DRAM bytes (read + write) per launch of the step kernels, from one ncu
-# capture each of the current kernel sources (profiles/ summaries name the
-# capture); None where the kernel changed after its capture.
-NCU_TRAFFIC_BYTES_PER_ELEMENT = {}
+# DRAM bytes (read + write) per element of one launch group of a kernel
+# class, from the ncu captures of the current kernels on the 256 x 256 blast
+# (profiles/kernels_blast_256_full.md: 65,536 elements; traffic grows in
+# proportion to the elements, so it is scaled by K).  stab_hydro: k_stats
+# (46.090 MB) + k_oe_pp (61.927 MB); k_lines and k_global move a few KB.
+# vol: k_vol (70.139 MB).  Remove an entry whenever its kernels change.
+NCU_TRAFFIC_BYTES_PER_ELEMENT = {"stab_hydro": (46090496 + 61926912) / 65536, "vol": 70138624 / 65536}
 
 
 def workload_config(stab, name="orszag_tang", mesh=None):
@@ -649,7 +652,8 @@ def main():
     roofline = {
         "bound": "alu", "kernel_class": top, "achieved": top_r["achieved_tflops"], "peak": p64,
         "unit": "TFLOP/s", "frac": top_r["achieved_tflops"] / p64,
-        "traffic": None if traffic is None else traffic * s.K / top_r["launch_groups_per_step"],
+        "traffic": None if traffic is None else traffic * s.K,
+        "traffic_algorithmic": top_r["bytes_per_step"] / top_r["launch_groups_per_step"],
         "traffic_unit": "DRAM bytes per launch group (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
         "peak_source": "FP64 FMA issue rate measured in this run (mhd_fp64_peak: DFMA probe, all lanes)",
         "peak_nominal_tflops": NOMINAL_FP64_TFLOPS,
