@@ -96,6 +96,31 @@ typedef struct mhd_ctx mhd_ctx;
 int mhd_create(const mhd_mesh_t* mesh, int p, int k, double gamma, mhd_ctx** out);
 void mhd_destroy(mhd_ctx* ctx);
 
+/* Reflecting walls by the method of images (§4.5 mirror boundaries, §4.7
+ * reflecting walls; the paper gives no discrete wall treatment, reading R24).
+ * The physical domain is the mesh given; the context stores and steps the
+ * periodic domain doubled in every walled direction (walls: bit 0 the pair of
+ * x-walls at x0, x1, bit 1 the y-walls), with the physical elements at
+ * ex < nx, ey < ny and their mirror images beyond.  Every operator of the step
+ * is reflection-equivariant, so a mirror-symmetric state stays so, and its
+ * physical part is the solution with walls: no mass crosses a wall and the
+ * normal velocity is odd across it.  The image parity of B per wall pair:
+ * `conducting` bit set = a conducting wall (B_n odd, B_t even, so B_n = 0 on
+ * the wall), clear = a symmetry plane (B_n even, B_t odd, field lines cross the
+ * wall normally).  All state layouts, coordinates and sizes of the context
+ * are those of the doubled periodic mesh; set the physical part, then call
+ * mhd_mirror_fill.  mhd_diagnostics reports the physical part only.
+ * Errors as mhd_create; walls outside 1..3 or conducting bits outside walls:
+ * MHD_EINVAL. */
+int mhd_create_walled(const mhd_mesh_t* mesh, int p, int k, double gamma, int walls, int conducting,
+                      mhd_ctx** out);
+
+/* Overwrite the image part of a walled context's state with the mirror images
+ * of its physical part (normal velocity odd, B with the wall pair's parity;
+ * on a conducting wall the normal B on the wall is set to 0).  MHD_EINVAL on a
+ * context without walls.  Synchronises. */
+int mhd_mirror_fill(mhd_ctx* ctx);
+
 /* Stabilisation parameters (default: all off, s_H = s_M = 0.02, C_s = 5,
  * C_eta = 0.2, cfl = 0.4, max_halvings = 20, strang_order = 0,
  * reduced_2d2v = 0).  A negative constant, cfl <= 0, max_halvings < 0 or a

@@ -276,6 +276,38 @@ oom:
   return fail(MHD_ENOMEM, std::string("device allocation: ") + cudaGetErrorString(e));
 }
 
+int mhd_create_walled(const mhd_mesh_t* mesh, int p, int k, double gamma, int walls, int conducting,
+                      mhd_ctx** out) {
+  if (!mesh || !out) return fail(MHD_EINVAL, "null argument");
+  *out = nullptr;
+  if (walls < 1 || walls > 3 || conducting < 0 || conducting > 3 || (conducting & ~walls))
+    return fail(MHD_EINVAL, "walls must be 1 (x), 2 (y) or 3; conducting a subset of the walled directions");
+  if (mesh->nx < 1 || mesh->ny < 1 || !(mesh->x1 > mesh->x0) || !(mesh->y1 > mesh->y0))
+    return fail(MHD_EINVAL, "invalid mesh");
+  if ((long long)mesh->nx * mesh->ny * ((walls & 1) ? 2 : 1) * ((walls & 2) ? 2 : 1) > (1LL << 30))
+    return fail(MHD_EINVAL, "mesh too large");
+  mhd_mesh_t m2 = *mesh;
+  if (walls & 1) { m2.nx = 2 * mesh->nx; m2.x1 = 2.0 * mesh->x1 - mesh->x0; }
+  if (walls & 2) { m2.ny = 2 * mesh->ny; m2.y1 = 2.0 * mesh->y1 - mesh->y0; }
+  int r = mhd_create(&m2, p, k, gamma, out);
+  if (r != MHD_OK) return r;
+  (*out)->walls = walls;
+  (*out)->cond = conducting;
+  (*out)->pnx = mesh->nx;
+  (*out)->pny = mesh->ny;
+  return MHD_OK;
+}
+
+int mhd_mirror_fill(mhd_ctx* c) {
+  if (!c) return fail(MHD_EINVAL, "null context");
+  if (!c->walls) return fail(MHD_EINVAL, "not a walled context (mhd_create_walled)");
+  mirror_fill(c->p, c->k, c->U, c->B, c->M, c->pnx, c->pny, c->walls, c->cond, c->st);
+  c->launches += 2;
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return cuda_fail(e, "mirror_fill");
+  return MHD_OK;
+}
+
 void mhd_destroy(mhd_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
@@ -939,7 +971,13 @@ int mhd_diagnostics(mhd_ctx* c, mhd_diag_t* out) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
   if (e != cudaSuccess) return cuda_fail(e, "diagnostics");
   double acc[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1e300, 1e300};
+  const int nx = c->M.nx;
+  // a walled context reports its physical elements only (the images repeat them)
+  auto physical = [&](size_t k) {
+    return !c->walls || ((int)(k % nx) < c->pnx && (int)(k / nx) < c->pny);
+  };
   for (size_t k = 0; k < K; ++k) {
+    if (!physical(k)) continue;
     for (int q = 0; q < 8; ++q) acc[q] += h[k * 12 + q];
     acc[8] = std::max(acc[8], h[k * 12 + 8]);
     acc[9] = std::max(acc[9], h[k * 12 + 9]);
@@ -947,7 +985,8 @@ int mhd_diagnostics(mhd_ctx* c, mhd_diag_t* out) {
     acc[11] = std::min(acc[11], h[k * 12 + 11]);
   }
   double emax = 0.0;
-  for (double v : eta) emax = std::max(emax, v);
+  for (size_t k = 0; k < K; ++k)
+    if (physical(k)) emax = std::max(emax, eta[k]);
   out->mass = acc[0]; out->mom[0] = acc[1]; out->mom[1] = acc[2]; out->mom[2] = acc[3];
   out->E_kin = acc[4]; out->E_int = acc[5]; out->entropy = acc[6]; out->E_mag = 0.5 * acc[7];
   out->div_B = acc[8]; out->B_max = acc[9]; out->rho_min = acc[10]; out->p_min = acc[11];

@@ -35,6 +35,8 @@ void b_from_potential(int k, const double* A, double Bx0, double By0, double* Bx
 void cfl_dt(int p, int k, const double* U, const double* B, const Tab* T, const Mesh& M,
             unsigned long long* maxbits, double cfl, double* dt, cudaStream_t st);
 void set_scalar(double* ptr, double v, cudaStream_t st);
+void mirror_fill(int p, int k, double* U, double* B, const Mesh& M, int pnx, int pny, int walls, int cond,
+                 cudaStream_t st);
 void diag_partials(int p, int k, const double* U, const double* B, const Tab* T, const Mesh& M, double* out,
                    cudaStream_t st);
 void stab_hydro(int p, double* S, unsigned* status, const Tab* T, const Mesh& M, const Stab& prm, const double* dtp,
@@ -128,4 +130,7 @@ struct mhd_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_rec;
   AdjBufs adj;
+  // reflecting walls by the method of images (mhd_create_walled): bit 0 x, bit 1 y;
+  // the physical elements are ex < pnx, ey < pny of the doubled periodic mesh
+  int walls, cond, pnx, pny;
 };

@@ -425,3 +425,96 @@ extern "C" int mhd_rcp_check(const double* x, double* y, long long n, void* stre
   }
   return 0;
 }
+
+// ---- reflecting walls by the method of images ---------------------------------
+// A walled domain [x0,x1] x [y0,y1] is stored as the periodic domain doubled in
+// every walled direction; the physical elements are ex < pnx, ey < pny.  The
+// image of a field is its reflection about x1 (and/or y1) with the parity of a
+// mirror: the normal velocity is odd, the other fluid fields even; B has, per
+// wall pair, the parity of a conducting wall (B_n odd, B_t even: B_n = 0 on the
+// wall) or of a symmetry plane (B_n even, B_t odd).  Bit 0 of `walls` and
+// `cond` is the x pair, bit 1 the y pair.  Every operator of the step is
+// reflection-equivariant, so a mirror-symmetric state stays mirror-symmetric and
+// its physical part is the solution with the walls (reading R24).
+namespace mhd {
+
+__device__ __forceinline__ int mirror_elem(int e, int pn, bool* refl) {
+  *refl = e >= pn;
+  return *refl ? 2 * pn - 1 - e : e;
+}
+
+template <int P>
+__global__ void k_mirror_dg(double* __restrict__ U, Mesh M, int pnx, int pny, int walls) {
+  constexpr int n = P + 1, n2 = n * n;
+  const size_t N = (size_t)M.K * n2;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  const int k = (int)(t / n2), q = (int)(t % n2), i = q % n, j = q / n;
+  const int ex = k % M.nx, ey = k / M.nx;
+  bool rx = false, ry = false;
+  const int sx = (walls & 1) ? mirror_elem(ex, pnx, &rx) : ex;
+  const int sy = (walls & 2) ? mirror_elem(ey, pny, &ry) : ey;
+  if (!rx && !ry) return;  // a physical node
+  const int si = rx ? P - i : i, sj = ry ? P - j : j;
+  const size_t s = (size_t)(sy * M.nx + sx) * n2 + sj * n + si;
+  U[t] = U[s];
+  U[N + t] = rx ? -U[N + s] : U[N + s];
+  U[2 * N + t] = ry ? -U[2 * N + s] : U[2 * N + s];
+  U[3 * N + t] = U[3 * N + s];
+  U[4 * N + t] = U[4 * N + s];
+}
+
+template <int KM>
+__global__ void k_mirror_B(double* __restrict__ B, Mesh M, int pnx, int pny, int walls, int cond) {
+  constexpr int mm = KM + 1;
+  const size_t Z = (size_t)M.K * mm * mm;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * Z) return;
+  const int comp = (int)(t / Z);
+  const size_t o = t % Z;
+  const int k = (int)(o / (mm * mm)), w = (int)(o % (mm * mm)), a = w % mm, b = w / mm;
+  const int ex = k % M.nx, ey = k / M.nx;
+  const int NX = M.nx * mm, NY = M.ny * mm, PX = pnx * mm, PY = pny * mm;
+  const bool wx = walls & 1, wy = walls & 2, cx = cond & 1, cy = cond & 2;
+  int c = ex * mm + a, r = ey * mm + b;  // global column / row of the DOF
+  double sign = 1.0;
+  bool plane_zero = false, image = false;
+  if (comp == 0) {  // B_x: GLL(k+1) columns (mirror planes at c = 0, PX), Gauss rows
+    if (wx && (c == 0 || c == PX)) plane_zero = cx;
+    else if (wx && c > PX) { c = NX - c; image = true; sign *= cx ? -1.0 : 1.0; }
+    if (wy && r >= PY) { r = NY - 1 - r; image = true; sign *= cy ? 1.0 : -1.0; }
+  } else if (comp == 1) {  // B_y: Gauss columns, GLL(k+1) rows (mirror planes at r = 0, PY)
+    if (wx && c >= PX) { c = NX - 1 - c; image = true; sign *= cx ? 1.0 : -1.0; }
+    if (wy && (r == 0 || r == PY)) plane_zero = cy;
+    else if (wy && r > PY) { r = NY - r; image = true; sign *= cy ? -1.0 : 1.0; }
+  } else {  // B_z: GLL(k) nodes of the element, tangential to every wall
+    if (wx && ex >= pnx) { c = (2 * pnx - 1 - ex) * mm + (KM - a); image = true; sign *= cx ? 1.0 : -1.0; }
+    if (wy && ey >= pny) { r = (2 * pny - 1 - ey) * mm + (KM - b); image = true; sign *= cy ? 1.0 : -1.0; }
+  }
+  if (plane_zero) { B[t] = 0.0; return; }
+  if (!image) return;
+  // the source is a physical DOF off the mirror planes (no thread writes it)
+  const int se = (r / mm) * M.nx + c / mm;
+  B[t] = sign * B[(size_t)comp * Z + (size_t)se * mm * mm + (r % mm) * mm + c % mm];
+}
+
+void mirror_fill(int p, int k, double* U, double* B, const Mesh& M, int pnx, int pny, int walls, int cond,
+                 cudaStream_t st) {
+  const size_t N = (size_t)M.K * (p + 1) * (p + 1), Z3 = 3 * (size_t)M.K * (k + 1) * (k + 1);
+  const unsigned bN = (unsigned)((N + 255) / 256), bZ = (unsigned)((Z3 + 255) / 256);
+  switch (p) {
+    case 1: k_mirror_dg<1><<<bN, 256, 0, st>>>(U, M, pnx, pny, walls); break;
+    case 2: k_mirror_dg<2><<<bN, 256, 0, st>>>(U, M, pnx, pny, walls); break;
+    case 3: k_mirror_dg<3><<<bN, 256, 0, st>>>(U, M, pnx, pny, walls); break;
+    case 4: k_mirror_dg<4><<<bN, 256, 0, st>>>(U, M, pnx, pny, walls); break;
+  }
+  switch (k) {
+    case 0: k_mirror_B<0><<<bZ, 256, 0, st>>>(B, M, pnx, pny, walls, cond); break;
+    case 1: k_mirror_B<1><<<bZ, 256, 0, st>>>(B, M, pnx, pny, walls, cond); break;
+    case 2: k_mirror_B<2><<<bZ, 256, 0, st>>>(B, M, pnx, pny, walls, cond); break;
+    case 3: k_mirror_B<3><<<bZ, 256, 0, st>>>(B, M, pnx, pny, walls, cond); break;
+    case 4: k_mirror_B<4><<<bZ, 256, 0, st>>>(B, M, pnx, pny, walls, cond); break;
+  }
+}
+
+}  // namespace mhd

@@ -49,6 +49,9 @@ _lib = None
 _SIGS = {
     "mhd_create": (C.c_int, [C.POINTER(Mesh), C.c_int, C.c_int, C.c_double, C.POINTER(C.c_void_p)]),
     "mhd_destroy": (None, [C.c_void_p]),
+    "mhd_create_walled": (C.c_int, [C.POINTER(Mesh), C.c_int, C.c_int, C.c_double, C.c_int, C.c_int,
+                                    C.POINTER(C.c_void_p)]),
+    "mhd_mirror_fill": (C.c_int, [C.c_void_p]),
     "mhd_set_params": (C.c_int, [C.c_void_p, C.POINTER(Params)]),
     "mhd_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mhd_sizes": (C.c_int, [C.c_void_p] + [C.POINTER(C.c_longlong)] * 4),
@@ -196,14 +199,29 @@ def hydro_rhs_static(nx, ny, p, gamma, domain, U, L, stream=0):
 class Solver:
     """One periodic mesh with DGSEM degree p and magnetic degree k."""
 
-    def __init__(self, nx, ny, p, k, gamma, domain=(0.0, 1.0, 0.0, 1.0), _handle=None):
-        self.nx, self.ny, self.p, self.k, self.gamma = nx, ny, p, k, gamma
-        self.domain = tuple(float(v) for v in domain)
+    def __init__(self, nx, ny, p, k, gamma, domain=(0.0, 1.0, 0.0, 1.0), _handle=None, walls=0, conducting=0):
+        """walls (bit 0 x, bit 1 y) != 0: reflecting walls on the physical
+        domain by the method of images (mhd_create_walled); the solver then
+        holds the doubled periodic mesh (nx, ny, domain and every layout are
+        the doubled ones; the physical elements are those of ``physical``)."""
+        self.p, self.k, self.gamma = p, k, gamma
+        self.walls, self.conducting = walls, conducting
         self._owned = _handle is None
+        x0, x1, y0, y1 = (float(v) for v in domain)
+        self.physical = (nx, ny, (x0, x1, y0, y1))
+        if walls & 1:
+            nx, x1 = 2 * nx, 2.0 * x1 - x0
+        if walls & 2:
+            ny, y1 = 2 * ny, 2.0 * y1 - y0
+        self.nx, self.ny, self.domain = nx, ny, (x0, x1, y0, y1)
         if _handle is None:
-            mesh = Mesh(nx, ny, *self.domain)
             h = C.c_void_p()
-            _check(lib().mhd_create(C.byref(mesh), p, k, gamma, C.byref(h)))
+            if walls:
+                mesh = Mesh(*self.physical[:2], *self.physical[2])
+                _check(lib().mhd_create_walled(C.byref(mesh), p, k, gamma, int(walls), int(conducting), C.byref(h)))
+            else:
+                mesh = Mesh(nx, ny, *self.domain)
+                _check(lib().mhd_create(C.byref(mesh), p, k, gamma, C.byref(h)))
         else:
             h = C.c_void_p(_handle)
         self._h = h
@@ -224,6 +242,10 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+    def mirror_fill(self):
+        """Write the images of the physical part (walled solvers)."""
+        _check(lib().mhd_mirror_fill(self._h))
 
     def set_params(self, **kw):
         """Update stabilisation / stepping parameters; on MHD_EINVAL the previous

@@ -187,6 +187,33 @@ def blast_oblique(gamma=5.0 / 3.0, p_in=10.0, p_out=0.1, r0=0.1):
     return dict(name="blast_oblique", fields=fields, Az=Az, B0=(c, c), domain=(0.0, 1.0, 0.0, 1.0), gamma=gamma)
 
 
+def rotor(r0=0.1, r1=0.115, rho_in=10.0, u0=1.0, p0=0.5, gamma=5.0 / 3.0):
+    """MHD rotor of §4.5 on [0,1]^2 with mirror walls: a dense core (rho = 10
+    for r < r0 about (1/2, 1/2)) in rigid rotation with unit tangential speed at
+    r0; over r0 <= r < r1 density and tangential speed taper linearly to the
+    ambient rho = 1, u = 0; p = 1/2 everywhere; B = (2.5/sqrt(4 pi), 0, 0).
+    Walls in x and y (walls = 3): the field crosses the x-walls, so they are
+    symmetry planes for B, and lies along the y-walls, which are conducting
+    (conducting = 2) - the wall parities that keep the uniform field."""
+    b = 2.5 / math.sqrt(4 * math.pi)
+
+    def fields(x, y):
+        dx, dy = x - 0.5, y - 0.5
+        r = np.sqrt(dx * dx + dy * dy)
+        f = np.clip((r1 - r) / (r1 - r0), 0.0, 1.0)
+        rho = 1.0 + (rho_in - 1.0) * f
+        speed = np.where(r < r0, u0 * r / r0, u0 * f)
+        inv = np.where(r > 0, 1.0 / np.maximum(r, 1e-300), 0.0)
+        one = np.ones_like(x)
+        return rho, -speed * dy * inv, speed * dx * inv, 0.0 * one, p0 * one, 0.0 * one
+
+    def Az(x, y):
+        return 0.0 * x
+
+    return dict(name="rotor", fields=fields, Az=Az, B0=(b, 0.0), domain=(0.0, 1.0, 0.0, 1.0), gamma=gamma,
+                walls=3, conducting=2)
+
+
 def field_loop(A0=1e-3, R=0.3, u=(2.0, 1.0), gamma=5.0 / 3.0):
     """Weak-field loop of §4.3 on the periodic [-1, 1] x [-1/2, 1/2]: rho = p = 1,
     u = (2, 1, 0), B = curl(A e_z) with A = A0 max(R - r, 0) (``Az`` = -A in
@@ -306,4 +333,5 @@ WORKLOADS = {
     "blast": blast,
     "vortex": balsara_vortex,
     "density_wave": density_wave,
+    "rotor": rotor,
 }

@@ -37,6 +37,22 @@ def test_create_rejects_empty_domain(domain):
         Solver(4, 4, 2, 2, 5 / 3, domain)
 
 
+@pytest.mark.parametrize("walls,cond", [(0, 0), (4, 0), (1, 2), (2, 1), (-1, 0), (3, 4)])
+def test_create_walled_rejects(walls, cond):
+    """mhd_create_walled validates its wall flags before any CUDA call."""
+    with pytest.raises(MhdError, match="walls") as e:
+        Solver(4, 4, 2, 2, 5 / 3, walls=walls, conducting=cond) if walls else _walled_zero()
+    assert e.value.code == MHD_EINVAL
+
+
+def _walled_zero():
+    import ctypes as C
+    from paper_2609_10849_b300 import mhd
+    h = C.c_void_p()
+    mesh = mhd.Mesh(4, 4, 0.0, 1.0, 0.0, 1.0)
+    mhd._check(mhd.lib().mhd_create_walled(C.byref(mesh), 2, 2, 5 / 3, 0, 0, C.byref(h)))
+
+
 def test_batch_create_rejects_no_runs():
     from paper_2609_10849_b300.mhd import Batch
     with pytest.raises(MhdError, match="invalid argument"):
