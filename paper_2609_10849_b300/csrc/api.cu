@@ -252,6 +252,7 @@ int mhd_create(const mhd_mesh_t* mesh, int p, int k, double gamma, mhd_ctx** out
   if ((e = dalloc(c, &c->dt, 4)) != cudaSuccess) goto oom;
   if ((e = dalloc(c, &c->work, std::max(stab_work_doubles(p, k, c->M), 12 * K))) != cudaSuccess) goto oom;
   if ((e = dalloc(c, &c->chol, stab_chol_doubles(p, c->M))) != cudaSuccess) goto oom;
+  if ((e = stab_init_mesh(p, c->hT, c->M, c->work)) != cudaSuccess) { mhd_destroy(c); return cuda_fail(e, "mesh coefficients"); }
   if ((e = dalloc(c, &c->io, std::max(5 * N, 3 * Z + 4 * N))) != cudaSuccess) goto oom;
   {
     void* ptr = nullptr;

@@ -52,6 +52,7 @@ void stab_vel(int p, int k, const double* rho, double* Y, const double* B, const
 void stab_vel_adjoint(int p, const double* rho, double* lam, const double* ustar, const double* chol,
                       const double* frzD, const Tab* T, const Mesh& M, cudaStream_t st);
 size_t stab_work_doubles(int p, int k, const Mesh& M);
+cudaError_t stab_init_mesh(int p, const Tab& hT, const Mesh& M, double* work);
 size_t stab_chol_doubles(int p, const Mesh& M);
 void set_error_message(const char* msg);
 cudaError_t mag_prepare(int p, int k);

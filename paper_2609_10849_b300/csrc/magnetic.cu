@@ -26,14 +26,62 @@
 // item * EB + element, so each half-warp evaluates one item for 16 elements.
 // All lanes of a half-warp take the same branch and read the same table
 // entries, which live in constant memory (broadcast reads).
+#include <cstring>
+
 #include "mhd_internal.cuh"
 
 namespace mhd {
 
-__constant__ Tab c_mtab[8];
+// The 1D tables the magnetic kernels read, in constant memory (broadcast
+// reads), with the products of two table entries that their loops would
+// otherwise form in every iteration rounded once on the host (the same
+// IEEE product, so the results do not change).
+struct MTab {
+  double wp[MHD_NMAX], wL[MHD_LMAX], wG[MHD_NMAX];
+  double ML[MHD_LMAX][MHD_LMAX];
+  double dL_G[MHD_NMAX][MHD_LMAX], G_L[MHD_LMAX][MHD_NMAX], M_G[MHD_NMAX][MHD_NMAX], M_L[MHD_LMAX][MHD_NMAX];
+  double P_G[MHD_NMAX][MHD_NMAX], P_L[MHD_LMAX][MHD_NMAX], dL_M[MHD_NMAX][MHD_LMAX], G_M[MHD_NMAX][MHD_NMAX];
+  double L_P[MHD_NMAX][MHD_LMAX], G_P[MHD_NMAX][MHD_NMAX];
+  double WG_P[MHD_NMAX][MHD_NMAX], WL_P[MHD_NMAX][MHD_LMAX];
+  double iwLs[MHD_LMAX], iwG[MHD_NMAX];
+  double wdL_G[MHD_NMAX][MHD_LMAX];  // wG_j dL_G[j][b]
+  double W_GL[MHD_NMAX][MHD_LMAX];   // wG_a wL_b: lumped weight of an N_x node (a Gauss in x, b GLL in y)
+  double W_LG[MHD_LMAX][MHD_NMAX];   // wL_a wG_b: N_y node
+  double W_LL[MHD_LMAX][MHD_LMAX];   // wL_a wL_b: W node
+};
+
+__constant__ MTab c_mtab[8];
 
 void upload_mag_tables(int slot, const Tab* h, cudaError_t* err) {
-  *err = cudaMemcpyToSymbol(c_mtab, h, sizeof(Tab), slot * sizeof(Tab));
+  MTab m;
+  memcpy(m.wp, h->wp, sizeof m.wp);
+  memcpy(m.wL, h->wL, sizeof m.wL);
+  memcpy(m.wG, h->wG, sizeof m.wG);
+  memcpy(m.ML, h->ML, sizeof m.ML);
+  memcpy(m.dL_G, h->dL_G, sizeof m.dL_G);
+  memcpy(m.G_L, h->G_L, sizeof m.G_L);
+  memcpy(m.M_G, h->M_G, sizeof m.M_G);
+  memcpy(m.M_L, h->M_L, sizeof m.M_L);
+  memcpy(m.P_G, h->P_G, sizeof m.P_G);
+  memcpy(m.P_L, h->P_L, sizeof m.P_L);
+  memcpy(m.dL_M, h->dL_M, sizeof m.dL_M);
+  memcpy(m.G_M, h->G_M, sizeof m.G_M);
+  memcpy(m.L_P, h->L_P, sizeof m.L_P);
+  memcpy(m.G_P, h->G_P, sizeof m.G_P);
+  memcpy(m.WG_P, h->WG_P, sizeof m.WG_P);
+  memcpy(m.WL_P, h->WL_P, sizeof m.WL_P);
+  memcpy(m.iwLs, h->iwLs, sizeof m.iwLs);
+  memcpy(m.iwG, h->iwG, sizeof m.iwG);
+  for (int j = 0; j < MHD_NMAX; ++j)
+    for (int b = 0; b < MHD_LMAX; ++b) {
+      m.wdL_G[j][b] = h->wG[j] * h->dL_G[j][b];
+      m.W_GL[j][b] = h->wG[j] * h->wL[b];
+    }
+  for (int a = 0; a < MHD_LMAX; ++a)
+    for (int b = 0; b < MHD_NMAX; ++b) m.W_LG[a][b] = h->wL[a] * h->wG[b];
+  for (int a = 0; a < MHD_LMAX; ++a)
+    for (int b = 0; b < MHD_LMAX; ++b) m.W_LL[a][b] = h->wL[a] * h->wL[b];
+  *err = cudaMemcpyToSymbol(c_mtab, &m, sizeof(MTab), slot * sizeof(MTab));
 }
 
 template <int P, int KM, int EBv = mag_tile_eb(0)>
@@ -57,7 +105,7 @@ template <int P, int KM>
 __device__ __forceinline__ double assemble_W(const double* __restrict__ Lz, int ex, int ey, int a, int b,
                                              const Mesh& M, double iJ) {
   using D = MD<P, KM>;
-  const Tab& T = c_mtab[D::SLOT];
+  const MTab& T = c_mtab[D::SLOT];
   int ox = ex, oy = ey, ao = a, bo = b;
   if (a == D::mL - 1) { ox = wrap(ex + 1, M.nx); ao = 0; }
   if (b == D::mL - 1) { oy = wrap(ey + 1, M.ny); bo = 0; }
@@ -75,7 +123,7 @@ template <int P, int KM>
 __device__ __forceinline__ double assemble_Nx(const double* __restrict__ Lx, int ex, int ey, int a, int b,
                                               const Mesh& M, double iJ) {
   using D = MD<P, KM>;
-  const Tab& T = c_mtab[D::SLOT];
+  const MTab& T = c_mtab[D::SLOT];
   int oy = ey, bo = b;
   if (b == D::mL - 1) { oy = wrap(ey + 1, M.ny); bo = 0; }
   const int sy = wrap(oy - 1, M.ny);
@@ -90,7 +138,7 @@ template <int P, int KM>
 __device__ __forceinline__ double assemble_Ny(const double* __restrict__ Ly, int ex, int ey, int a, int b,
                                               const Mesh& M, double iJ) {
   using D = MD<P, KM>;
-  const Tab& T = c_mtab[D::SLOT];
+  const MTab& T = c_mtab[D::SLOT];
   int ox = ex, ao = a;
   if (a == D::mL - 1) { ox = wrap(ex + 1, M.nx); ao = 0; }
   const int wx = wrap(ox - 1, M.nx);
@@ -134,7 +182,7 @@ __global__ void __launch_bounds__(256) k_mag_J(const double* __restrict__ Bx, co
                                                double* __restrict__ LJy, double* __restrict__ LJz, Mesh M) {
   using D = MD<P, KM, EBv>;
   using O = LJ_<P, KM>;
-  const Tab& T = c_mtab[D::SLOT];
+  const MTab& T = c_mtab[D::SLOT];
   extern __shared__ double sm[];
   const int k0 = blockIdx.x * D::EB;
   // 2D2V (R2): B_z = 0, so only the W loads of J_z are formed
@@ -182,8 +230,8 @@ __global__ void __launch_bounds__(256) k_mag_J(const double* __restrict__ Bx, co
       double z1 = 0.0, z2 = 0.0;
 #pragma unroll
       for (int j = 0; j < D::mm; ++j) {
-        z1 = fma(T.wG[j] * T.dL_G[j][b], SM(O::T1, j * D::mL + a), z1);
-        z2 = fma(T.wG[j] * T.dL_G[j][a], SM(O::T2, b * D::mm + j), z2);
+        z1 = fma(T.wdL_G[j][b], SM(O::T1, j * D::mL + a), z1);
+        z2 = fma(T.wdL_G[j][a], SM(O::T2, b * D::mm + j), z2);
       }
       if (k < M.K) LJz[(size_t)k * D::NW + it] = fma(cy, z1, -cx * z2);
     } else {
@@ -204,14 +252,14 @@ __global__ void __launch_bounds__(256) k_mag_J(const double* __restrict__ Bx, co
       int b = it / D::mm, a = it % D::mm;
       double s = 0.0;
 #pragma unroll
-      for (int d = 0; d < D::mm; ++d) s = fma(T.wG[d] * T.dL_G[d][b], SM(O::BZG, d * D::mm + a), s);
+      for (int d = 0; d < D::mm; ++d) s = fma(T.wdL_G[d][b], SM(O::BZG, d * D::mm + a), s);
       LJx[(size_t)k * D::NX + it] = -cy * T.wG[a] * s;
     } else {  // J_y: a < mL (GLL x), b < mm
       it -= D::NX;
       int b = it / D::mL, a = it % D::mL;
       double s = 0.0;
 #pragma unroll
-      for (int c = 0; c < D::mm; ++c) s = fma(T.wG[c] * T.dL_G[c][a], SM(O::BZG, b * D::mm + c), s);
+      for (int c = 0; c < D::mm; ++c) s = fma(T.wdL_G[c][a], SM(O::BZG, b * D::mm + c), s);
       LJy[(size_t)k * D::NY + it] = cx * T.wG[b] * s;
     }
   }
@@ -257,7 +305,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
     const double* __restrict__ dtp, double dtfac, double ca, double cb, int first, int resistive) {
   using D = MD<P, KM, EBv>;
   using O = LE_<P, KM>;
-  const Tab& T = c_mtab[D::SLOT];
+  const MTab& T = c_mtab[D::SLOT];
   extern __shared__ double sm[];
   const int k0 = blockIdx.x * D::EB;
   const size_t N = (size_t)M.K * D::n2;
@@ -413,7 +461,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
     int it = idx / D::EB, e = idx % D::EB, k = k0 + e;
     if (!R2 && it < D::NX) {
       int b = it / D::mm, a = it % D::mm;
-      double w = Jd * T.wG[a] * T.wL[b];
+      double w = Jd * T.W_GL[a][b];
       double by_ = SM(O::BY, it), bz_ = SM(O::BZNX, it), jx_ = SM(O::JX, it);
       double uy = SM(O::UNX, it), uz = SM(O::UNX, D::NX + it);
       if (k < M.K) LEx[(size_t)k * D::NX + it] = w * fma(uz, by_, -uy * bz_);
@@ -422,7 +470,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
     } else if (!R2 && it < D::NX + D::NY) {
       it -= D::NX;
       int b = it / D::mL, a = it % D::mL;
-      double w = Jd * T.wL[a] * T.wG[b];
+      double w = Jd * T.W_LG[a][b];
       double bx_ = SM(O::BX, it), bz_ = SM(O::BZNY, it), jy_ = SM(O::JY, it);
       double ux = SM(O::UNY, it), uz = SM(O::UNY, D::NY + it);
       if (k < M.K) LEy[(size_t)k * D::NY + it] = w * fma(ux, bz_, -uz * bx_);
@@ -431,7 +479,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
     } else {
       if constexpr (!R2) it -= D::NX + D::NY;
       int b = it / D::mL, a = it % D::mL;
-      double w = Jd * T.wL[a] * T.wL[b];
+      double w = Jd * T.W_LL[a][b];
       double bx_ = SM(O::BXW, it), by_ = SM(O::BYL, it), jz_ = SM(O::JZ, it);
       double ux = SM(O::UW, it), uy = SM(O::UW, D::NW + it);
       if (k < M.K) LEz[(size_t)k * D::NW + it] = w * fma(uy, bx_, -ux * by_);
@@ -678,7 +726,7 @@ __global__ void __launch_bounds__(256) k_mag_B(const double* __restrict__ LEx, c
                                                double ca, double cb, int first) {
   using D = MD<P, KM, EBv>;
   using O = LB_<P, KM>;
-  const Tab& T = c_mtab[D::SLOT];
+  const MTab& T = c_mtab[D::SLOT];
   extern __shared__ double sm[];
   const int k0 = blockIdx.x * D::EB;
   const double iJ = M.iJ;

@@ -61,6 +61,10 @@ struct Tab {
   double iwG[MHD_NMAX];                       // 1 / wG
   double Wq[MHD_NMAX * MHD_NMAX];             // 0.25 wp_i wp_j at node j*(p+1)+i (element-average weights)
   double hwp[MHD_NMAX];                       // 0.5 wp_i
+  // products of two entries that inner loops would otherwise form per iteration
+  double WLeg[MHD_NMAX][MHD_NMAX];            // wp_j P_b(xp_j): [j][b]
+  double LegN2[MHD_NMAX][MHD_NMAX];           // LegN_a LegN_b
+  double LegLeg[MHD_NMAX][MHD_NMAX][MHD_NMAX];  // P_b(xp_j) P_b2(xp_j): [j][b][b2]
 };
 
 // Device copy of the tables of the 8 supported (p, k) pairs.

@@ -18,6 +18,8 @@
 // every row and column and the order factors of the sensor.  Readings R6-R9 of
 // the design notes apply.
 #include <cfloat>
+#include <cmath>
+#include <vector>
 
 #include "mhd_internal.cuh"
 
@@ -37,6 +39,10 @@ struct StatsView {
   double* part;  // [ceil(K/256)][9] A.R. chunk partials
   double* lineD; // [2][L] 1 / Delta_{I,line} (eq. euler-oe-shared-amplitude), from k_global
   double* rfac;  // [2][8] (2r + 1) h_I^r / (2 r!) of eq. euler-oe-sigma, from k_global
+  // per-mesh coefficients of the face jumps (set at context creation, stab_init_mesh):
+  double* jcoef; // [2 (I)][2 (side: 0 this element's lower face, 1 the neighbour's upper face)][p][n][n]:
+                 //   sqrt(w_t / 2) (2/h_I)^r times row 0 (side 0) or minus row p (side 1) of D^r, r = 1..p
+  double* sqw;   // [n] sqrt(w_t / 2)
 };
 
 static StatsView stats_view(double* work, int p, const Mesh& M) {
@@ -55,13 +61,39 @@ static StatsView stats_view(double* work, int p, const Mesh& M) {
   v.part = v.arg + 8;
   v.lineD = v.part + 9 * (K / 256 + 1);
   v.rfac = v.lineD + 2 * L;
+  v.jcoef = v.rfac + 16;
+  v.sqw = v.jcoef + 4 * p * n * n;
   return v;
 }
 
 size_t stab_work_doubles(int p, int k, const Mesh& M) {
   (void)k;
   const size_t K = M.K, n = p + 1, L = M.nx > M.ny ? M.nx : M.ny;
-  return 3 * 5 * K + 2 * 5 * n * K + 2 * L * 5 * 3 + 5 * 4 + 8 * K + 8 + 9 * (K / 256 + 1) + 2 * L + 16 + 64;
+  return 3 * 5 * K + 2 * 5 * n * K + 2 * L * 5 * 3 + 5 * 4 + 8 * K + 8 + 9 * (K / 256 + 1) + 2 * L + 16 +
+         4 * p * n * n + n + 64;
+}
+
+// The face-jump coefficients of a mesh into the work buffer (once per context).
+cudaError_t stab_init_mesh(int p, const Tab& hT, const Mesh& M, double* work) {
+  const StatsView V = stats_view(work, p, M);
+  const int n = p + 1;
+  std::vector<double> c(4 * p * n * n + n);
+  double* jc = c.data();
+  double* sq = jc + 4 * p * n * n;
+  for (int t = 0; t < n; ++t) sq[t] = sqrt(hT.hwp[t]);
+  for (int I = 0; I < 2; ++I) {
+    const double s2h = 2.0 * (I == 0 ? M.ihx : M.ihy);
+    for (int r = 1; r <= p; ++r) {
+      double scale = 1.0;
+      for (int i = 0; i < r; ++i) scale *= s2h;
+      for (int t = 0; t < n; ++t)
+        for (int q = 0; q < n; ++q) {
+          jc[(((I * 2 + 0) * p + (r - 1)) * n + t) * n + q] = sq[t] * scale * hT.Dr0[r][q];
+          jc[(((I * 2 + 1) * p + (r - 1)) * n + t) * n + q] = -(sq[t] * scale * hT.Drp[r][q]);
+        }
+    }
+  }
+  return cudaMemcpy(V.jcoef, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice);
 }
 
 size_t stab_chol_doubles(int p, const Mesh& M) {
@@ -70,20 +102,59 @@ size_t stab_chol_doubles(int p, const Mesh& M) {
 }
 
 // ---- k_stats: per element and component --------------------------------------------
-// Items (element innermost, so a warp shares one item type): for each component
-// c: [average, max, min] (1 item) and for each direction I and order r the jump
-// measure of the lower face (1 item each).
+// One thread per (component, item, element), element fastest: item 0 the
+// weighted average and the nodal max and min; items 1 and 2 the jump measures
+// J_r, r = 0..p, of the lower face normal to x and to y (eq. euler-oe-jump),
+// from one load of the two elements' nodes.  The face quadrature weight and
+// (2/h)^r are folded into the derivative rows (V.jcoef), so a face node's
+// weighted jump of order r is one chain of 2 (p+1) FMAs and its square one more.
+template <int P, int I>
+__device__ __forceinline__ void face_jumps(const double* __restrict__ f, int k, int kA, const StatsView& V,
+                                           double* __restrict__ out, size_t K, int c) {
+  constexpr int n = P + 1, n2 = n * n;
+  double wA[n2], wB[n2];
+#pragma unroll
+  for (int q = 0; q < n2; ++q) { wA[q] = f[(size_t)kA * n2 + q]; wB[q] = f[(size_t)k * n2 + q]; }
+  // node s of face-normal line t: x-direction (I = 0) rows, y-direction columns
+#define NODE(w, t, s) (I == 0 ? w[(t) * n + (s)] : w[(s) * n + (t)])
+  {  // r = 0: the traces themselves
+    double acc = 0.0;
+#pragma unroll
+    for (int t = 0; t < n; ++t) {
+      const double jw = V.sqw[t] * (NODE(wB, t, 0) - NODE(wA, t, P));
+      acc = fma(jw, jw, acc);
+    }
+    out[((size_t)c * n) * K + k] = sqrt(acc);
+  }
+  const double* cB = V.jcoef + (size_t)(I * 2 + 0) * P * n * n;
+  const double* cA = V.jcoef + (size_t)(I * 2 + 1) * P * n * n;
+#pragma unroll
+  for (int r = 1; r <= P; ++r) {
+    double acc = 0.0;
+#pragma unroll
+    for (int t = 0; t < n; ++t) {
+      double jw = 0.0;
+#pragma unroll
+      for (int s = 0; s < n; ++s) jw = fma(cB[((r - 1) * n + t) * n + s], NODE(wB, t, s), jw);
+#pragma unroll
+      for (int s = 0; s < n; ++s) jw = fma(cA[((r - 1) * n + t) * n + s], NODE(wA, t, s), jw);
+      acc = fma(jw, jw, acc);
+    }
+    out[((size_t)c * n + r) * K + k] = sqrt(acc);
+  }
+#undef NODE
+}
+
 template <int P>
-__global__ void k_stats(const double* __restrict__ F, size_t stride, int nc, StatsView V, const Tab* __restrict__ T,
-                        Mesh M) {
+__global__ void __launch_bounds__(256) k_stats(const double* __restrict__ F, size_t stride, int nc, StatsView V,
+                                               const Tab* __restrict__ T, Mesh M) {
   constexpr int n = P + 1, n2 = n * n;
   const size_t K = M.K;
-  const size_t items = (size_t)nc * (1 + 2 * n);
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= items * K) return;
+  if (t >= (size_t)nc * 3 * K) return;
   const int k = (int)(t % K);
   const int it = (int)(t / K);
-  const int c = it / (1 + 2 * n), w = it % (1 + 2 * n);
+  const int c = it / 3, w = it % 3;
   const double* f = F + c * stride;
   const int ex = k % M.nx, ey = k / M.nx;
   if (w == 0) {  // weighted average; nodal max and min on integer keys
@@ -102,38 +173,8 @@ __global__ void k_stats(const double* __restrict__ F, size_t stride, int nc, Sta
     V.emin[c * K + k] = dkey_inv(mn);
     return;
   }
-  const int I = (w - 1) / n, r = (w - 1) % n;
-  const int kA = I == 0 ? ey * M.nx + wrap(ex - 1, M.nx) : wrap(ey - 1, M.ny) * M.nx + ex;  // lower side
-  const double ih = 2.0 * (I == 0 ? M.ihx : M.ihy);  // 1 / (h / 2)
-  double scale = 1.0;  // (2/h)^r, applied once to the averaged square
-  for (int i = 0; i < r; ++i) scale *= ih;
-  double acc = 0.0;
-  if (r == 0) {  // the traces themselves: end nodes of the two elements
-#pragma unroll
-    for (int tt = 0; tt < n; ++tt) {
-      double wA = I == 0 ? f[(size_t)kA * n2 + tt * n + P] : f[(size_t)kA * n2 + P * n + tt];
-      double wB = I == 0 ? f[(size_t)k * n2 + tt * n] : f[(size_t)k * n2 + tt];
-      double jmp = wB - wA;
-      acc = fma(T->hwp[tt] * jmp, jmp, acc);
-    }
-  } else {
-#pragma unroll
-    for (int tt = 0; tt < n; ++tt) {  // face GLL node
-      double dA = 0.0, dB = 0.0;
-#pragma unroll
-      for (int s = 0; s < n; ++s) {
-        double wA = I == 0 ? f[(size_t)kA * n2 + tt * n + s] : f[(size_t)kA * n2 + s * n + tt];
-        double wB = I == 0 ? f[(size_t)k * n2 + tt * n + s] : f[(size_t)k * n2 + s * n + tt];
-        dA = fma(T->Drp[r][s], wA, dA);
-        dB = fma(T->Dr0[r][s], wB, dB);
-      }
-      double jmp = dB - dA;
-      acc = fma(T->hwp[tt] * jmp, jmp, acc);
-    }
-    acc *= scale * scale;
-  }
-  double* out = I == 0 ? V.jx : V.jy;
-  out[((size_t)c * n + r) * K + k] = sqrt(acc);
+  if (w == 1) face_jumps<P, 0>(f, k, ey * M.nx + wrap(ex - 1, M.nx), V, V.jx, K, c);
+  else face_jumps<P, 1>(f, k, wrap(ey - 1, M.ny) * M.nx + ex, V, V.jy, K, c);
 }
 
 // ---- k_lines: row (blockIdx.y = 0) and column (1) reductions -----------------------
@@ -402,7 +443,7 @@ __global__ void __launch_bounds__(PCfg<P>::threads) k_oe_pp(double* __restrict__
     {  // T[b][i] = sum_j w_j P_b(x_j) U[j][i]   (b = j of this thread)
       double wl[n];
 #pragma unroll
-      for (int jj = 0; jj < n; ++jj) wl[jj] = T->wp[jj] * T->Leg[jj][j];
+      for (int jj = 0; jj < n; ++jj) wl[jj] = T->WLeg[jj][j];
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
         double v = 0.0;
@@ -413,10 +454,10 @@ __global__ void __launch_bounds__(PCfg<P>::threads) k_oe_pp(double* __restrict__
     }
     __syncthreads();
     {  // coef[b][a] = N_a N_b sum_i w_i P_a(x_i) T[b][i], damped by D_max(a,b)   (a = i, b = j)
-      const double f = T->LegN[i] * T->LegN[j] * sD[el][i > j ? i : j];
+      const double f = T->LegN2[i][j] * sD[el][i > j ? i : j];
       double wl[n];
 #pragma unroll
-      for (int ii = 0; ii < n; ++ii) wl[ii] = f * T->wp[ii] * T->Leg[ii][i];
+      for (int ii = 0; ii < n; ++ii) wl[ii] = f * T->WLeg[ii][i];
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
         double v = 0.0;
@@ -577,8 +618,7 @@ __global__ void __launch_bounds__(PCfg<P>::threads) k_oe_pp(double* __restrict__
 template <int P>
 static void launch_stats(const double* F, size_t stride, int nc, const StatsView& V, const Tab* T, const Mesh& M,
                          cudaStream_t st) {
-  constexpr int n = P + 1;
-  size_t total = (size_t)nc * (1 + 2 * n) * M.K;
+  size_t total = (size_t)nc * 3 * M.K;
   k_stats<P><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(F, stride, nc, V, T, M);
   dim3 grid(M.nx > M.ny ? M.nx : M.ny, 2);
   k_lines<<<grid, 256, 0, st>>>(nc, V, M);
@@ -959,7 +999,7 @@ __global__ void __launch_bounds__(32) k_vel_prep(const double* __restrict__ rho,
       for (int a2 = 0; a2 <= a; ++a2) {
         double s = 0.0;
 #pragma unroll
-        for (int i = 0; i < n; ++i) s = fma(W[j * n + i] * T->Leg[i][a], T->Leg[i][a2], s);
+        for (int i = 0; i < n; ++i) s = fma(W[j * n + i], T->LegLeg[i][a][a2], s);
         HS(j * V::NA + tri(a, a2)) = s;
       }
 #pragma unroll
@@ -970,7 +1010,7 @@ __global__ void __launch_bounds__(32) k_vel_prep(const double* __restrict__ rho,
       const int pa = a >= a2 ? tri(a, a2) : tri(a2, a);
       double s = 0.0;
 #pragma unroll
-      for (int j = 0; j < n; ++j) s = fma(T->Leg[j][b] * T->Leg[j][b2], HS(j * V::NA + pa), s);
+      for (int j = 0; j < n; ++j) s = fma(T->LegLeg[j][b][b2], HS(j * V::NA + pa), s);
       LS(tri(al, be)) = s;
     }
   // Cholesky G = L L^T in place (row by row)

@@ -285,6 +285,13 @@ void host_tables(int p, int k, Tab* T) {
     for (int i = 0; i < n; ++i) s += wp[i] * (ld)T->Leg[i][a] * (ld)T->Leg[i][a];
     T->LegN[a] = (double)(1.0L / s);
   }
+  // double products exactly as a kernel would form them (one IEEE multiply)
+  for (int j = 0; j < n; ++j)
+    for (int b = 0; b < n; ++b) {
+      T->WLeg[j][b] = T->wp[j] * T->Leg[j][b];
+      T->LegN2[j][b] = T->LegN[j] * T->LegN[b];
+      for (int b2 = 0; b2 < n; ++b2) T->LegLeg[j][b][b2] = T->Leg[j][b] * T->Leg[j][b2];
+    }
 }
 
 int table_slot(int p, int k) {
