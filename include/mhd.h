@@ -369,6 +369,13 @@ int mhd_fp64_peak(double* tflops);
  * [2^-1000, 2^1000].  Errors: MHD_EINVAL, MHD_ECUDA. */
 int mhd_rcp_check(const double* x, double* y, long long n, void* stream);
 
+/* Debug build only (no counterpart in the paper; libmhd_debug.so, compiled
+ * with MHD_BOUNDS_CHECK): the number of out-of-range global-memory indices the
+ * checked kernels met since the last reset (each such access was redirected
+ * to element 0 instead of being made); reset != 0 clears the counts.  The
+ * release library returns -1.  Synchronises the device. */
+long long mhd_debug_oob(int reset);
+
 const char* mhd_status_string(int status);
 const char* mhd_last_error(void);
 

@@ -183,9 +183,26 @@ int check_status(mhd_ctx* c, unsigned* st_out) {
 
 }  // namespace
 
+namespace mhd {
+unsigned long long oob_hydro(bool reset);
+unsigned long long oob_stab(bool reset);
+unsigned long long oob_magnetic(bool reset);
+unsigned long long oob_misc(bool reset);
+}  // namespace mhd
+
 extern "C" {
 
 const char* mhd_last_error(void) { return g_err.c_str(); }
+
+long long mhd_debug_oob(int reset) {
+#ifdef MHD_BOUNDS_CHECK
+  cudaDeviceSynchronize();
+  return (long long)(oob_hydro(reset) + oob_stab(reset) + oob_magnetic(reset) + oob_misc(reset));
+#else
+  (void)reset;
+  return -1;
+#endif
+}
 
 const char* mhd_status_string(int s) {
   switch (s) {

@@ -107,13 +107,13 @@ __global__ void __launch_bounds__(256) k_face(const double* __restrict__ S, doub
   double Um[5], Up[5], F[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    Um[c] = S[c * N + (size_t)km * n2 + qm];
-    Up[c] = S[c * N + (size_t)k * n2 + qp];
+    Um[c] = S[MHD_CHK(c * N + (size_t)km * n2 + qm, 5 * N)];
+    Up[c] = S[MHD_CHK(c * N + (size_t)k * n2 + qp, 5 * N)];
   }
   llf_flux_dev(d, Um, Up, M.g, F);
   double* out = d ? Fy : Fx;
 #pragma unroll
-  for (int c = 0; c < 5; ++c) out[c * nf + r] = F[c];
+  for (int c = 0; c < 5; ++c) out[MHD_CHK(c * nf + r, 5 * nf)] = F[c];
 }
 
 // mode 0: write L_E; mode 1: SSP stage combination into C.
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __r
 
   double Us[5];
 #pragma unroll
-  for (int c = 0; c < 5; ++c) Us[c] = S[c * N + gi];
+  for (int c = 0; c < 5; ++c) Us[c] = S[MHD_CHK(c * N + gi, 5 * N)];
   {
     double ir = rcp(Us[0]);
     double ux = Us[1] * ir, uy = Us[2] * ir, uz = Us[3] * ir;
@@ -175,8 +175,8 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __r
     const int r = pidx - d * (NP / 2);
     const int line = r / NPL, w = r % NPL;
     const int a = c_pair_a[w], b = c_pair_b[w];
-    const int qa = el * n2 + (d == 0 ? line * n + a : a * n + line);
-    const int qb = el * n2 + (d == 0 ? line * n + b : b * n + line);
+    const int qa = (int)MHD_CHK(el * n2 + (d == 0 ? line * n + a : a * n + line), EB * n2);
+    const int qb = (int)MHD_CHK(el * n2 + (d == 0 ? line * n + b : b * n + line), EB * n2);
     double rL = sp[0][qa], rR = sp[0][qb];              // rho/2 of both nodes
     double bL = sp[4][qa], bR = sp[4][qb];
     double hr = rL + rR, sb = bL + bR;                  // {{rho}}, 2 {{beta}}
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __r
     double hhat = fma(Fb * ig1 + Fr, isb, fma(-0.5, u2a, au2));
     double ud = d == 0 ? ua0 : ua1;
     double f0 = rlog * ud;
-    const int o = el * NP + pidx;
+    const int o = (int)MHD_CHK(el * NP + pidx, EB * NP);
     sf[0][o] = f0;
     sf[1][o] = fma(f0, ua0, d == 0 ? phat : 0.0);
     sf[2][o] = fma(f0, ua1, d == 1 ? phat : 0.0);
@@ -219,8 +219,8 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __r
     const int rx = i + o < n ? i + o : i + o - n, ry = j + o < n ? j + o : j + o - n;
     Dx[o - 1] = T->D[i][rx];
     Dy[o - 1] = T->D[j][ry];
-    px[o - 1] = el * NP + j * NPL + pair_index(min(i, rx), max(i, rx));
-    py[o - 1] = el * NP + NP / 2 + i * NPL + pair_index(min(j, ry), max(j, ry));
+    px[o - 1] = (int)MHD_CHK(el * NP + j * NPL + pair_index(min(i, rx), max(i, rx)), EB * NP);
+    py[o - 1] = (int)MHD_CHK(el * NP + NP / 2 + i * NPL + pair_index(min(j, ry), max(j, ry)), EB * NP);
   }
   const double cx = -4.0 * M.ihx, cy = -4.0 * M.ihy;
   constexpr double w0i = 0.5 * P * (P + 1);  // 1 / w_0 of GLL(p): w_0 = 2 / (p (p + 1))
@@ -245,15 +245,15 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __r
     }
     double v = fma(cx, sx, cy * sy);
     // end nodes: -(2/hx)[-F*_left/w_0] and -(2/hx)[+F*_right/w_p] (w_p = w_0)
-    v = fma(cfx, Fx[c * nf + ifx], v);
-    v = fma(cfy, Fy[c * nf + ify], v);
+    v = fma(cfx, Fx[MHD_CHK(c * nf + ifx, 5 * nf)], v);
+    v = fma(cfy, Fy[MHD_CHK(c * nf + ify, 5 * nf)], v);
     L[c] = v;
   }
 
   if (MODE == 0) {
     if (valid) {
 #pragma unroll
-      for (int c = 0; c < 5; ++c) out[c * N + gi] = L[c];
+      for (int c = 0; c < 5; ++c) out[MHD_CHK(c * N + gi, 5 * N)] = L[c];
     }
     return;
   }
@@ -263,11 +263,11 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __r
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
     double raw = fma(tau, L[c], Us[c]);
-    Cv[c] = first ? raw : fma(ca, U0[c * N + gi], cb * raw);
+    Cv[c] = first ? raw : fma(ca, U0[MHD_CHK(c * N + gi, 5 * N)], cb * raw);
   }
   if (valid) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) out[c * N + gi] = Cv[c];
+    for (int c = 0; c < 5; ++c) out[MHD_CHK(c * N + gi, 5 * N)] = Cv[c];
   }
   // no status word: the caller's limiter tests the same averages itself (the
   // OE before it keeps them), so the reduction below is skipped (block-uniform)
@@ -367,5 +367,7 @@ void hydro_vol(int p, int mode, const double* S, const double* U0, const double*
     case 4: launch_vol<4>(mode, S, U0, Fx, Fy, out, avg, status, T, M, dtp, dtfac, ca, cb, first, st); break;
   }
 }
+
+MHD_OOB_READER(oob_hydro)
 
 }  // namespace mhd

@@ -111,10 +111,11 @@ __device__ __forceinline__ double assemble_W(const double* __restrict__ Lz, int 
   if (b == D::mL - 1) { oy = wrap(ey + 1, M.ny); bo = 0; }
   const int wx = wrap(ox - 1, M.nx), sy = wrap(oy - 1, M.ny);
   double v = 0.0;
-  if (ao == 0 && bo == 0) v += Lz[(size_t)(sy * M.nx + wx) * D::NW + (D::mL - 1) * D::mL + (D::mL - 1)];
-  if (bo == 0) v += Lz[(size_t)(sy * M.nx + ox) * D::NW + (D::mL - 1) * D::mL + ao];
-  if (ao == 0) v += Lz[(size_t)(oy * M.nx + wx) * D::NW + bo * D::mL + (D::mL - 1)];
-  v += Lz[(size_t)(oy * M.nx + ox) * D::NW + bo * D::mL + ao];
+  const size_t KW = (size_t)M.K * D::NW;
+  if (ao == 0 && bo == 0) v += Lz[MHD_CHK((size_t)(sy * M.nx + wx) * D::NW + (D::mL - 1) * D::mL + (D::mL - 1), KW)];
+  if (bo == 0) v += Lz[MHD_CHK((size_t)(sy * M.nx + ox) * D::NW + (D::mL - 1) * D::mL + ao, KW)];
+  if (ao == 0) v += Lz[MHD_CHK((size_t)(oy * M.nx + wx) * D::NW + bo * D::mL + (D::mL - 1), KW)];
+  v += Lz[MHD_CHK((size_t)(oy * M.nx + ox) * D::NW + bo * D::mL + ao, KW)];
   return v * (iJ * T.iwLs[ao] * T.iwLs[bo]);
 }
 
@@ -128,8 +129,9 @@ __device__ __forceinline__ double assemble_Nx(const double* __restrict__ Lx, int
   if (b == D::mL - 1) { oy = wrap(ey + 1, M.ny); bo = 0; }
   const int sy = wrap(oy - 1, M.ny);
   double v = 0.0;
-  if (bo == 0) v += Lx[(size_t)(sy * M.nx + ex) * D::NX + (D::mL - 1) * D::mm + a];
-  v += Lx[(size_t)(oy * M.nx + ex) * D::NX + bo * D::mm + a];
+  const size_t KX = (size_t)M.K * D::NX;
+  if (bo == 0) v += Lx[MHD_CHK((size_t)(sy * M.nx + ex) * D::NX + (D::mL - 1) * D::mm + a, KX)];
+  v += Lx[MHD_CHK((size_t)(oy * M.nx + ex) * D::NX + bo * D::mm + a, KX)];
   return v * (iJ * T.iwG[a] * T.iwLs[bo]);
 }
 
@@ -143,8 +145,9 @@ __device__ __forceinline__ double assemble_Ny(const double* __restrict__ Ly, int
   if (a == D::mL - 1) { ox = wrap(ex + 1, M.nx); ao = 0; }
   const int wx = wrap(ox - 1, M.nx);
   double v = 0.0;
-  if (ao == 0) v += Ly[(size_t)(ey * M.nx + wx) * D::NY + b * D::mL + (D::mL - 1)];
-  v += Ly[(size_t)(ey * M.nx + ox) * D::NY + b * D::mL + ao];
+  const size_t KY = (size_t)M.K * D::NY;
+  if (ao == 0) v += Ly[MHD_CHK((size_t)(ey * M.nx + wx) * D::NY + b * D::mL + (D::mL - 1), KY)];
+  v += Ly[MHD_CHK((size_t)(ey * M.nx + ox) * D::NY + b * D::mL + ao, KY)];
   return v * (iJ * T.iwLs[ao] * T.iwG[b]);
 }
 
@@ -153,15 +156,15 @@ template <int P, int KM>
 __device__ __forceinline__ double closure_Bx(const double* __restrict__ Bx, int ex, int ey, int a, int b,
                                              const Mesh& M) {
   using D = MD<P, KM>;
-  if (a == D::mL - 1) return Bx[(size_t)(ey * M.nx + wrap(ex + 1, M.nx)) * D::NZ + b * D::mm];
-  return Bx[(size_t)(ey * M.nx + ex) * D::NZ + b * D::mm + a];
+  if (a == D::mL - 1) return Bx[MHD_CHK((size_t)(ey * M.nx + wrap(ex + 1, M.nx)) * D::NZ + b * D::mm, (size_t)M.K * D::NZ)];
+  return Bx[MHD_CHK((size_t)(ey * M.nx + ex) * D::NZ + b * D::mm + a, (size_t)M.K * D::NZ)];
 }
 template <int P, int KM>
 __device__ __forceinline__ double closure_By(const double* __restrict__ By, int ex, int ey, int a, int b,
                                              const Mesh& M) {
   using D = MD<P, KM>;
-  if (b == D::mL - 1) return By[(size_t)(wrap(ey + 1, M.ny) * M.nx + ex) * D::NZ + a];
-  return By[(size_t)(ey * M.nx + ex) * D::NZ + b * D::mm + a];
+  if (b == D::mL - 1) return By[MHD_CHK((size_t)(wrap(ey + 1, M.ny) * M.nx + ex) * D::NZ + a, (size_t)M.K * D::NZ)];
+  return By[MHD_CHK((size_t)(ey * M.nx + ex) * D::NZ + b * D::mm + a, (size_t)M.K * D::NZ)];
 }
 
 // ============================ k_mag_J ==========================================
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(256) k_mag_J(const double* __restrict__ Bx, co
     int ex = k % M.nx, ey = k / M.nx;
     if (it < D::NY) SM(O::BX, it) = closure_Bx<P, KM>(Bx, ex, ey, it % D::mL, it / D::mL, M);
     else if (it < D::NY + D::NX) { it -= D::NY; SM(O::BY, it) = closure_By<P, KM>(By, ex, ey, it % D::mm, it / D::mm, M); }
-    else { it -= D::NY + D::NX; SM(O::BZ, it) = Bz[(size_t)k * D::NZ + it]; }
+    else { it -= D::NY + D::NX; SM(O::BZ, it) = Bz[MHD_CHK((size_t)k * D::NZ + it, (size_t)M.K * D::NZ)]; }
   }
   __syncthreads();
   constexpr int I2 = D::mm * D::mL + D::mL * D::mm + (R2 ? 0 : D::NZ);
@@ -233,7 +236,7 @@ __global__ void __launch_bounds__(256) k_mag_J(const double* __restrict__ Bx, co
         z1 = fma(T.wdL_G[j][b], SM(O::T1, j * D::mL + a), z1);
         z2 = fma(T.wdL_G[j][a], SM(O::T2, b * D::mm + j), z2);
       }
-      if (k < M.K) LJz[(size_t)k * D::NW + it] = fma(cy, z1, -cx * z2);
+      if (k < M.K) LJz[MHD_CHK((size_t)k * D::NW + it, (size_t)M.K * D::NW)] = fma(cy, z1, -cx * z2);
     } else {
       it -= D::NW;
       int d = it / D::mm, a = it % D::mm;
@@ -253,14 +256,14 @@ __global__ void __launch_bounds__(256) k_mag_J(const double* __restrict__ Bx, co
       double s = 0.0;
 #pragma unroll
       for (int d = 0; d < D::mm; ++d) s = fma(T.wdL_G[d][b], SM(O::BZG, d * D::mm + a), s);
-      LJx[(size_t)k * D::NX + it] = -cy * T.wG[a] * s;
+      LJx[MHD_CHK((size_t)k * D::NX + it, (size_t)M.K * D::NX)] = -cy * T.wG[a] * s;
     } else {  // J_y: a < mL (GLL x), b < mm
       it -= D::NX;
       int b = it / D::mL, a = it % D::mL;
       double s = 0.0;
 #pragma unroll
       for (int c = 0; c < D::mm; ++c) s = fma(T.wdL_G[c][a], SM(O::BZG, b * D::mm + c), s);
-      LJy[(size_t)k * D::NY + it] = cx * T.wG[b] * s;
+      LJy[MHD_CHK((size_t)k * D::NY + it, (size_t)M.K * D::NY)] = cx * T.wG[b] * s;
     }
   }
 }
@@ -328,9 +331,9 @@ __global__ void __launch_bounds__(256) k_mag_E(
     if (it < D::NX) { SM(O::BY, it) = closure_By<P, KM>(By, ex, ey, it % D::mm, it / D::mm, M); continue; }
     it -= D::NX;
     if constexpr (!R2) {
-      if (it < D::NZ) { SM(O::BZ, it) = Bz[(size_t)k * D::NZ + it]; continue; }
+      if (it < D::NZ) { SM(O::BZ, it) = Bz[MHD_CHK((size_t)k * D::NZ + it, (size_t)M.K * D::NZ)]; continue; }
     }
-    SM(O::ETA, 0) = resistive ? eta[k] : 0.0;
+    SM(O::ETA, 0) = resistive ? eta[MHD_CHK(k, M.K)] : 0.0;
   }
   __syncthreads();
   // stage 2: x-passes (u read straight from global memory); only what the
@@ -343,7 +346,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
     if constexpr (!R2) {
       if (it < NUG) {  // u_y, u_z to Gauss x
         int d = it / (D::n * D::mm), r = it % (D::n * D::mm), j = r / D::mm, a = r % D::mm;
-        const double* ur = u + (1 + d) * N + (size_t)k * D::n2 + j * D::n;
+        const double* ur = u + MHD_CHK((1 + d) * N + (size_t)k * D::n2 + j * D::n, 3 * N - D::n + 1);
         double v = 0.0;
 #pragma unroll
         for (int i = 0; i < D::n; ++i) v = fma(T.P_G[a][i], ur[i], v);
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
     }
     if (it < NUL) {  // u_x, u_y (and u_z) to GLL(k+1) x
       int d = it / (D::n * D::mL), r = it % (D::n * D::mL), j = r / D::mL, a = r % D::mL;
-      const double* ur = u + d * N + (size_t)k * D::n2 + j * D::n;
+      const double* ur = u + MHD_CHK(d * N + (size_t)k * D::n2 + j * D::n, 3 * N - D::n + 1);
       double v = 0.0;
 #pragma unroll
       for (int i = 0; i < D::n; ++i) v = fma(T.P_L[a][i], ur[i], v);
@@ -464,7 +467,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
       double w = Jd * T.W_GL[a][b];
       double by_ = SM(O::BY, it), bz_ = SM(O::BZNX, it), jx_ = SM(O::JX, it);
       double uy = SM(O::UNX, it), uz = SM(O::UNX, D::NX + it);
-      if (k < M.K) LEx[(size_t)k * D::NX + it] = w * fma(uz, by_, -uy * bz_);
+      if (k < M.K) LEx[MHD_CHK((size_t)k * D::NX + it, (size_t)M.K * D::NX)] = w * fma(uz, by_, -uy * bz_);
       SM(O::UNX, it) = -w * bz_ * jx_;         // s_y contribution
       SM(O::UNX, D::NX + it) = w * by_ * jx_;  // s_z contribution
     } else if (!R2 && it < D::NX + D::NY) {
@@ -473,7 +476,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
       double w = Jd * T.W_LG[a][b];
       double bx_ = SM(O::BX, it), bz_ = SM(O::BZNY, it), jy_ = SM(O::JY, it);
       double ux = SM(O::UNY, it), uz = SM(O::UNY, D::NY + it);
-      if (k < M.K) LEy[(size_t)k * D::NY + it] = w * fma(ux, bz_, -uz * bx_);
+      if (k < M.K) LEy[MHD_CHK((size_t)k * D::NY + it, (size_t)M.K * D::NY)] = w * fma(ux, bz_, -uz * bx_);
       SM(O::UNY, it) = w * bz_ * jy_;           // s_x
       SM(O::UNY, D::NY + it) = -w * bx_ * jy_;  // s_z
     } else {
@@ -482,7 +485,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
       double w = Jd * T.W_LL[a][b];
       double bx_ = SM(O::BXW, it), by_ = SM(O::BYL, it), jz_ = SM(O::JZ, it);
       double ux = SM(O::UW, it), uy = SM(O::UW, D::NW + it);
-      if (k < M.K) LEz[(size_t)k * D::NW + it] = w * fma(uy, bx_, -ux * by_);
+      if (k < M.K) LEz[MHD_CHK((size_t)k * D::NW + it, (size_t)M.K * D::NW)] = w * fma(uy, bx_, -ux * by_);
       SM(O::UW, it) = -w * by_ * jz_;          // s_x
       SM(O::UW, D::NW + it) = w * bx_ * jz_;   // s_y
     }
@@ -676,7 +679,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
         sz = fma(T.P_G[a][i], SM(O::VZ1, j * D::mm + a), sz);
       }
     }
-    size_t gq = (size_t)k * D::n2 + q;
+    size_t gq = MHD_CHK((size_t)k * D::n2 + q, N);
     if (MODE == 2) {
       uo[gq] = sx;
       uo[N + gq] = sy;
@@ -789,7 +792,7 @@ __global__ void __launch_bounds__(256) k_mag_B(const double* __restrict__ LEx, c
       for (int c = 0; c < D::mL; ++c) vx = fma(T.dL_M[b][c], SM(O::TX, c * D::mm + a), vx);
       dB = -fma(ax, vy, -ay * vx);
     }
-    size_t gi = comp * Z + (size_t)k * D::NZ + r;
+    size_t gi = MHD_CHK(comp * Z + (size_t)k * D::NZ + r, 3 * Z);
     if (MODE == 0) Bo[gi] = dB;
     else {
       double raw = fma(tau, dB, B[gi]);
@@ -938,5 +941,7 @@ void mag_stage(int p, int k, int mode, const double* B, const double* u, const d
   MHD_DISPATCH_PK(p, k, MHD_MAG_CASE);
 #undef MHD_MAG_CASE
 }
+
+MHD_OOB_READER(oob_magnetic)
 
 }  // namespace mhd

@@ -141,6 +141,37 @@ enum : unsigned {
   ST_NOT_PLANAR = 8u,  // reduced 2D2V stage on a state with u_z or B_z nonzero
 };
 
+// ---- debug index checks ---------------------------------------------------------
+// Built with -DMHD_BOUNDS_CHECK (libmhd_debug.so), MHD_CHK(i, n) counts every
+// index outside [0, n) in a device word of the translation unit and returns 0
+// instead, so a bad index is recorded and never dereferenced; the release build
+// compiles it to the index itself.  mhd_debug_oob() sums the words.
+#ifdef MHD_BOUNDS_CHECK
+static __device__ unsigned long long g_oob_count;
+__device__ __forceinline__ size_t chk_index(long long i, long long n) {
+  if (i < 0 || i >= n) {
+    atomicAdd(&g_oob_count, 1ull);
+    return 0;
+  }
+  return (size_t)i;
+}
+#define MHD_CHK(i, n) (::mhd::chk_index((long long)(i), (long long)(n)))
+#define MHD_OOB_READER(name)                                                   \
+  unsigned long long name(bool reset) {                                        \
+    unsigned long long v = 0;                                                  \
+    cudaMemcpyFromSymbol(&v, g_oob_count, sizeof v);                           \
+    if (reset) {                                                               \
+      const unsigned long long z = 0;                                          \
+      cudaMemcpyToSymbol(g_oob_count, &z, sizeof z);                           \
+    }                                                                          \
+    return v;                                                                  \
+  }
+#else
+#define MHD_CHK(i, n) (i)
+#define MHD_OOB_READER(name) \
+  unsigned long long name(bool) { return 0; }
+#endif
+
 __host__ __device__ inline int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 // ---- fast FP64 reciprocal ---------------------------------------------------

@@ -302,11 +302,11 @@ __global__ void k_diag(const double* __restrict__ U, const double* __restrict__ 
   double bx[mm][mL], by[mL][mm];
   for (int b = 0; b < mm; ++b)
     for (int a = 0; a < mL; ++a)
-      bx[b][a] = a == mL - 1 ? Bx[((size_t)ey * M.nx + wrap(ex + 1, M.nx)) * mm * mm + b * mm]
+      bx[b][a] = a == mL - 1 ? Bx[MHD_CHK(((size_t)ey * M.nx + wrap(ex + 1, M.nx)) * mm * mm + b * mm, Z)]
                              : Bx[(size_t)k * mm * mm + b * mm + a];
   for (int b = 0; b < mL; ++b)
     for (int a = 0; a < mm; ++a)
-      by[b][a] = b == mL - 1 ? By[((size_t)wrap(ey + 1, M.ny) * M.nx + ex) * mm * mm + a]
+      by[b][a] = b == mL - 1 ? By[MHD_CHK(((size_t)wrap(ey + 1, M.ny) * M.nx + ex) * mm * mm + a, Z)]
                              : By[(size_t)k * mm * mm + b * mm + a];
   double em = 0.0;
   for (int qy = 0; qy < mL; ++qy)
@@ -456,7 +456,7 @@ __global__ void k_mirror_dg(double* __restrict__ U, Mesh M, int pnx, int pny, in
   const int sy = (walls & 2) ? mirror_elem(ey, pny, &ry) : ey;
   if (!rx && !ry) return;  // a physical node
   const int si = rx ? P - i : i, sj = ry ? P - j : j;
-  const size_t s = (size_t)(sy * M.nx + sx) * n2 + sj * n + si;
+  const size_t s = MHD_CHK((size_t)(sy * M.nx + sx) * n2 + sj * n + si, N);
   U[t] = U[s];
   U[N + t] = rx ? -U[N + s] : U[N + s];
   U[2 * N + t] = ry ? -U[2 * N + s] : U[2 * N + s];
@@ -495,7 +495,7 @@ __global__ void k_mirror_B(double* __restrict__ B, Mesh M, int pnx, int pny, int
   if (!image) return;
   // the source is a physical DOF off the mirror planes (no thread writes it)
   const int se = (r / mm) * M.nx + c / mm;
-  B[t] = sign * B[(size_t)comp * Z + (size_t)se * mm * mm + (r % mm) * mm + c % mm];
+  B[t] = sign * B[MHD_CHK((size_t)comp * Z + (size_t)se * mm * mm + (r % mm) * mm + c % mm, 3 * Z)];
 }
 
 void mirror_fill(int p, int k, double* U, double* B, const Mesh& M, int pnx, int pny, int walls, int cond,
@@ -516,5 +516,7 @@ void mirror_fill(int p, int k, double* U, double* B, const Mesh& M, int pnx, int
     case 4: k_mirror_B<4><<<bZ, 256, 0, st>>>(B, M, pnx, pny, walls, cond); break;
   }
 }
+
+MHD_OOB_READER(oob_misc)
 
 }  // namespace mhd

@@ -114,7 +114,10 @@ __device__ __forceinline__ void face_jumps(const double* __restrict__ f, int k, 
   constexpr int n = P + 1, n2 = n * n;
   double wA[n2], wB[n2];
 #pragma unroll
-  for (int q = 0; q < n2; ++q) { wA[q] = f[(size_t)kA * n2 + q]; wB[q] = f[(size_t)k * n2 + q]; }
+  for (int q = 0; q < n2; ++q) {
+    wA[q] = f[MHD_CHK((size_t)kA * n2 + q, K * n2)];
+    wB[q] = f[MHD_CHK((size_t)k * n2 + q, K * n2)];
+  }
   // node s of face-normal line t: x-direction (I = 0) rows, y-direction columns
 #define NODE(w, t, s) (I == 0 ? w[(t) * n + (s)] : w[(s) * n + (t)])
   {  // r = 0: the traces themselves
@@ -124,7 +127,7 @@ __device__ __forceinline__ void face_jumps(const double* __restrict__ f, int k, 
       const double jw = V.sqw[t] * (NODE(wB, t, 0) - NODE(wA, t, P));
       acc = fma(jw, jw, acc);
     }
-    out[((size_t)c * n) * K + k] = sqrt(acc);
+    out[MHD_CHK(((size_t)c * n) * K + k, 5 * n * K)] = sqrt(acc);
   }
   const double* cB = V.jcoef + (size_t)(I * 2 + 0) * P * n * n;
   const double* cA = V.jcoef + (size_t)(I * 2 + 1) * P * n * n;
@@ -140,7 +143,7 @@ __device__ __forceinline__ void face_jumps(const double* __restrict__ f, int k, 
       for (int s = 0; s < n; ++s) jw = fma(cA[((r - 1) * n + t) * n + s], NODE(wA, t, s), jw);
       acc = fma(jw, jw, acc);
     }
-    out[((size_t)c * n + r) * K + k] = sqrt(acc);
+    out[MHD_CHK(((size_t)c * n + r) * K + k, 5 * n * K)] = sqrt(acc);
   }
 #undef NODE
 }
@@ -189,7 +192,7 @@ __global__ void k_lines(int nc, StatsView V, Mesh M) {
   for (int c = 0; c < nc; ++c) {
     double s = 0.0, mx = -DBL_MAX, mn = DBL_MAX;
     for (int t = threadIdx.x; t < len; t += blockDim.x) {
-      int k = dir == 0 ? L * M.nx + t : t * M.nx + L;
+      int k = (int)MHD_CHK(dir == 0 ? L * M.nx + t : t * M.nx + L, K);
       s += V.avg[c * K + k];
       mx = fmax(mx, V.emax[c * K + k]);
       mn = fmin(mn, V.emin[c * K + k]);
@@ -280,7 +283,7 @@ __device__ __forceinline__ double sigma_rI(const StatsView& V, int nc, int n, in
   double s = 0.0;
   for (int c = 0; c < nc; ++c) {
     if (__double_as_longlong(V.glob[c * 4 + 3]) != 0) continue;
-    const double Jr = J[((size_t)c * n + r) * K + k] + J[((size_t)c * n + r) * K + kB];
+    const double Jr = J[MHD_CHK(((size_t)c * n + r) * K + k, 5 * n * K)] + J[MHD_CHK(((size_t)c * n + r) * K + kB, 5 * n * K)];
     s = fmax(s, Jr);
   }
   return fac * s * iDelta;
@@ -401,7 +404,7 @@ __global__ void __launch_bounds__(PCfg<P>::threads) k_oe_pp(double* __restrict__
   const double g = M.g;
   double u[5];
 #pragma unroll
-  for (int c = 0; c < 5; ++c) u[c] = S[c * N + (size_t)kk * n2 + q];
+  for (int c = 0; c < 5; ++c) u[c] = S[MHD_CHK(c * N + (size_t)kk * n2 + q, 5 * N)];
 
   if (prm.oe_hydro) {
 #pragma unroll
@@ -409,7 +412,7 @@ __global__ void __launch_bounds__(PCfg<P>::threads) k_oe_pp(double* __restrict__
     // rate lambda_{E,I} (eq. euler-oe-rate) from the element average, once per element
     for (int e = tid; e < EB; e += TH) {
       const int ke = min(k0 + e, M.K - 1);
-      const double a0 = V.avg[ke], a1 = V.avg[K + ke], a2 = V.avg[2 * K + ke], a3 = V.avg[3 * K + ke],
+      const double a0 = V.avg[MHD_CHK(ke, K)], a1 = V.avg[K + ke], a2 = V.avg[2 * K + ke], a3 = V.avg[3 * K + ke],
                    a4 = V.avg[4 * K + ke];
       const double ir = rcp(a0);
       const double pb = (g - 1.0) * fma(-0.5 * ir, fma(a1, a1, fma(a2, a2, a3 * a3)), a4);
@@ -610,7 +613,7 @@ __global__ void __launch_bounds__(PCfg<P>::threads) k_oe_pp(double* __restrict__
   }
   if (valid) {
 #pragma unroll
-    for (int c = 0; c < 5; ++c) S[c * N + (size_t)k * n2 + q] = u[c];
+    for (int c = 0; c < 5; ++c) S[MHD_CHK(c * N + (size_t)k * n2 + q, 5 * N)] = u[c];
   }
 }
 
@@ -752,14 +755,16 @@ void stab_hydro(int p, double* S, unsigned* status, const Tab* T, const Mesh& M,
 template <int KM>
 __device__ __forceinline__ double bx_cl(const double* Bx, int ex, int ey, int a, int b, const Mesh& M) {
   constexpr int mm = KM + 1, mL = KM + 2;
-  if (a == mL - 1) return Bx[((size_t)ey * M.nx + wrap(ex + 1, M.nx)) * mm * mm + b * mm];
-  return Bx[((size_t)ey * M.nx + ex) * mm * mm + b * mm + a];
+  const size_t Z = (size_t)M.K * mm * mm;
+  if (a == mL - 1) return Bx[MHD_CHK(((size_t)ey * M.nx + wrap(ex + 1, M.nx)) * mm * mm + b * mm, Z)];
+  return Bx[MHD_CHK(((size_t)ey * M.nx + ex) * mm * mm + b * mm + a, Z)];
 }
 template <int KM>
 __device__ __forceinline__ double by_cl(const double* By, int ex, int ey, int a, int b, const Mesh& M) {
   constexpr int mm = KM + 1, mL = KM + 2;
-  if (b == mL - 1) return By[((size_t)wrap(ey + 1, M.ny) * M.nx + ex) * mm * mm + a];
-  return By[((size_t)ey * M.nx + ex) * mm * mm + b * mm + a];
+  const size_t Z = (size_t)M.K * mm * mm;
+  if (b == mL - 1) return By[MHD_CHK(((size_t)wrap(ey + 1, M.ny) * M.nx + ex) * mm * mm + a, Z)];
+  return By[MHD_CHK(((size_t)ey * M.nx + ex) * mm * mm + b * mm + a, Z)];
 }
 
 // Component d of B_h of element (ex, ey) at reference point (x, y) given as 1D
@@ -1124,9 +1129,9 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
   const int i = q % n, j = q / n;
   double u[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-  for (int d = 0; d < ND; ++d) u[d] = Y[(1 + d) * N + (size_t)kk * n2 + q];
-  const double r_ = rho[(size_t)kk * n2 + q];
-  for (int t = q; t < n2 * n2; t += n2) sPsi[el][t] = Psi[(size_t)kk * n2 * n2 + t];
+  for (int d = 0; d < ND; ++d) u[d] = Y[MHD_CHK((1 + d) * N + (size_t)kk * n2 + q, 4 * N)];
+  const double r_ = rho[MHD_CHK((size_t)kk * n2 + q, N)];
+  for (int t = q; t < n2 * n2; t += n2) sPsi[el][t] = Psi[MHD_CHK((size_t)kk * n2 * n2 + t, (size_t)M.K * n2 * n2)];
   // closures of B (Bx [b < mm][a < mL], By [b < mL][a < mm], Bz [b][a]) of the block's elements
   constexpr int NB = mm * mL + mL * mm + (R2 ? 0 : mm * mm);
   for (int it = tid; it < EB * NB; it += TH) {
@@ -1135,7 +1140,7 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
     double v;
     if (w < mm * mL) v = bx_cl<KM>(B, ex, ey, w % mL, w / mL, M);
     else if (w < 2 * mm * mL) { const int r = w - mm * mL; v = by_cl<KM>(B + Z, ex, ey, r % mm, r / mm, M); }
-    else v = B[2 * Z + (size_t)ke * mm * mm + (w - 2 * mm * mL)];
+    else v = B[MHD_CHK(2 * Z + (size_t)ke * mm * mm + (w - 2 * mm * mL), 3 * Z)];
     sB[e][w] = v;
   }
   __syncthreads();
@@ -1237,9 +1242,9 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
         unew = fma(Dl, wl, unew);
         if (l > 0) de = fma(0.5 * (1.0 - Dl * Dl) * wl, wl, de);
       }
-      Y[(1 + d) * N + (size_t)k * n2 + q] = unew;
+      Y[MHD_CHK((1 + d) * N + (size_t)k * n2 + q, 4 * N)] = unew;
     }
-    Y[(size_t)k * n2 + q] += de;
+    Y[MHD_CHK((size_t)k * n2 + q, N)] += de;
   }
 }
 
@@ -1372,5 +1377,7 @@ void stab_vel_adjoint(int p, const double* rho, double* lam, const double* ustar
   }
 #undef MHD_ADJ_VOE
 }
+
+MHD_OOB_READER(oob_stab)
 
 }  // namespace mhd

@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmhd.so")
+# MHD_DEBUG_BUILD=1 selects libmhd_debug.so, the build with index checks
+# (mhd_debug_oob); the release library is the default.
+LIB_PATH = os.path.join(_HERE, "libmhd_debug.so" if os.environ.get("MHD_DEBUG_BUILD") == "1" else "libmhd.so")
 
 MHD_OK, MHD_RETRIED = 0, 1
 MHD_EINVAL, MHD_ENOMEM, MHD_ECUDA, MHD_INADMISSIBLE, MHD_NONFINITE, MHD_TIMEOUT = -1, -2, -3, -4, -5, -6
@@ -96,6 +98,7 @@ _SIGS = {
     "mhd_autotune": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mhd_set_tiles": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "mhd_batch_autotune": (C.c_int, [C.c_void_p]),
+    "mhd_debug_oob": (C.c_longlong, [C.c_int]),
     "mhd_status_string": (C.c_char_p, [C.c_int]),
     "mhd_last_error": (C.c_char_p, []),
 }

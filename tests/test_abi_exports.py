@@ -34,3 +34,14 @@ def test_library_exports_every_declared_symbol():
 def test_binding_covers_every_declared_symbol():
     missing = [n for n in declared() if n not in mhd._SIGS]
     assert not missing, missing
+
+
+def test_debug_library_exports_the_same_symbols():
+    """The index-checking build exports the same entry points (and says so)."""
+    path = os.path.join(os.path.dirname(mhd.LIB_PATH), "libmhd_debug.so")
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    rel = ctypes.CDLL(os.path.join(os.path.dirname(mhd.LIB_PATH), "libmhd.so"))
+    rel.mhd_debug_oob.restype = ctypes.c_longlong
+    assert rel.mhd_debug_oob(0) == -1  # the release build has no checks
