@@ -24,6 +24,9 @@ struct HCfg {
   static constexpr int npl = n * (n - 1) / 2;  // pairs per line
   static constexpr int EB = EBv;               // elements per CTA (autotuned variant)
   static constexpr int threads = EB * n2;
+  // at least 32 resident warps per SM (registers <= 64): the pair and gather
+  // phases wait on shared-memory loads and reciprocal seeds, which more warps hide
+  static constexpr int min_blocks = 1024 / threads > 0 ? 1024 / threads : 1;
 };
 
 // Pairs (a, b), a < b, ordered so that the first n(n-1)/2 use only nodes < n.
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(256) k_face(const double* __restrict__ S, doub
 // mode 0: write L_E; mode 1: SSP stage combination into C.
 // Stage s: s == 0: C = S + tau L; otherwise C = a U0 + b (S + tau L).
 template <int P, int MODE, int EBv>
-__global__ void __launch_bounds__(HCfg<P, EBv>::threads) k_vol(const double* __restrict__ S, const double* __restrict__ U0,
+__global__ void __launch_bounds__(HCfg<P, EBv>::threads, HCfg<P, EBv>::min_blocks) k_vol(const double* __restrict__ S, const double* __restrict__ U0,
                                                           const double* __restrict__ Fx, const double* __restrict__ Fy,
                                                           double* __restrict__ out, double* __restrict__ avg_out,
                                                           unsigned* __restrict__ status, const Tab* __restrict__ T,

@@ -112,40 +112,38 @@ template <int P, int I>
 __device__ __forceinline__ void face_jumps(const double* __restrict__ f, int k, int kA, const StatsView& V,
                                            double* __restrict__ out, size_t K, int c) {
   constexpr int n = P + 1, n2 = n * n;
-  double wA[n2], wB[n2];
-#pragma unroll
-  for (int q = 0; q < n2; ++q) {
-    wA[q] = f[MHD_CHK((size_t)kA * n2 + q, K * n2)];
-    wB[q] = f[MHD_CHK((size_t)k * n2 + q, K * n2)];
-  }
-  // node s of face-normal line t: x-direction (I = 0) rows, y-direction columns
-#define NODE(w, t, s) (I == 0 ? w[(t) * n + (s)] : w[(s) * n + (t)])
-  {  // r = 0: the traces themselves
-    double acc = 0.0;
-#pragma unroll
-    for (int t = 0; t < n; ++t) {
-      const double jw = V.sqw[t] * (NODE(wB, t, 0) - NODE(wA, t, P));
-      acc = fma(jw, jw, acc);
-    }
-    out[MHD_CHK(((size_t)c * n) * K + k, 5 * n * K)] = sqrt(acc);
-  }
   const double* cB = V.jcoef + (size_t)(I * 2 + 0) * P * n * n;
   const double* cA = V.jcoef + (size_t)(I * 2 + 1) * P * n * n;
+  double acc[n];
 #pragma unroll
-  for (int r = 1; r <= P; ++r) {
-    double acc = 0.0;
+  for (int r = 0; r < n; ++r) acc[r] = 0.0;
+  // face node t: the normal line t of both elements (x-direction rows, y-direction
+  // columns), then the weighted jumps of every order, accumulated in t order
 #pragma unroll
-    for (int t = 0; t < n; ++t) {
+  for (int t = 0; t < n; ++t) {
+    double a[n], b[n];
+#pragma unroll
+    for (int s = 0; s < n; ++s) {
+      const int q = I == 0 ? t * n + s : s * n + t;
+      a[s] = f[MHD_CHK((size_t)kA * n2 + q, K * n2)];
+      b[s] = f[MHD_CHK((size_t)k * n2 + q, K * n2)];
+    }
+    {  // r = 0: the traces themselves
+      const double jw = V.sqw[t] * (b[0] - a[P]);
+      acc[0] = fma(jw, jw, acc[0]);
+    }
+#pragma unroll
+    for (int r = 1; r <= P; ++r) {
       double jw = 0.0;
 #pragma unroll
-      for (int s = 0; s < n; ++s) jw = fma(cB[((r - 1) * n + t) * n + s], NODE(wB, t, s), jw);
+      for (int s = 0; s < n; ++s) jw = fma(cB[((r - 1) * n + t) * n + s], b[s], jw);
 #pragma unroll
-      for (int s = 0; s < n; ++s) jw = fma(cA[((r - 1) * n + t) * n + s], NODE(wA, t, s), jw);
-      acc = fma(jw, jw, acc);
+      for (int s = 0; s < n; ++s) jw = fma(cA[((r - 1) * n + t) * n + s], a[s], jw);
+      acc[r] = fma(jw, jw, acc[r]);
     }
-    out[MHD_CHK(((size_t)c * n + r) * K + k, 5 * n * K)] = sqrt(acc);
   }
-#undef NODE
+#pragma unroll
+  for (int r = 0; r < n; ++r) out[MHD_CHK(((size_t)c * n + r) * K + k, 5 * n * K)] = sqrt(acc[r]);
 }
 
 template <int P>
@@ -809,54 +807,210 @@ __global__ void k_ar_elem(const double* __restrict__ rho, const double* __restri
   if (k >= M.K) return;
   const size_t Z = (size_t)M.K * mm * mm, N = (size_t)M.K * n2;
   const int ex = k % M.nx, ey = k / M.nx;
+  // this element's closures: Bx [b < mm][a < mL], By [b < mL][a < mm], Bz [b][a]
+  double bx[mm][mL], by[mL][mm], bz[mm][mm];
+#pragma unroll
+  for (int b = 0; b < mm; ++b)
+#pragma unroll
+    for (int a = 0; a < mL; ++a) bx[b][a] = bx_cl<KM>(B, ex, ey, a, b, M);
+#pragma unroll
+  for (int b = 0; b < mL; ++b)
+#pragma unroll
+    for (int a = 0; a < mm; ++a) by[b][a] = by_cl<KM>(B + Z, ex, ey, a, b, M);
+#pragma unroll
+  for (int b = 0; b < mm; ++b)
+#pragma unroll
+    for (int a = 0; a < mm; ++a) bz[b][a] = B[MHD_CHK(2 * Z + (size_t)k * mm * mm + b * mm + a, 3 * Z)];
   double out[16];
   // exact element integrals: the integral of a nodal basis function is its
-  // quadrature weight (GLL(k+1) and Gauss(k) in the RT directions, GLL(k) for
-  // B_z), so B_eval with the weight rows in place of the interpolation rows is
-  // the integral over the reference element
-  out[0] = M.Jdet * B_eval<KM>(B, Z, 0, ex, ey, T->wL, T->wG, T->wM, T->wL, T->wG, T->wM, M);
-  out[1] = M.Jdet * B_eval<KM>(B, Z, 1, ex, ey, T->wL, T->wG, T->wM, T->wL, T->wG, T->wM, M);
-  out[2] = M.Jdet * B_eval<KM>(B, Z, 2, ex, ey, T->wL, T->wG, T->wM, T->wL, T->wG, T->wM, M);
+  // quadrature weight, so the weight rows in place of the interpolation rows
+  // give the integral over the reference element (x-pass, then y-pass)
+  {
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+#pragma unroll
+    for (int b = 0; b < mm; ++b) {
+      double row = 0.0;
+#pragma unroll
+      for (int a = 0; a < mL; ++a) row = fma(T->wL[a], bx[b][a], row);
+      sx = fma(T->wG[b], row, sx);
+    }
+#pragma unroll
+    for (int b = 0; b < mL; ++b) {
+      double row = 0.0;
+#pragma unroll
+      for (int a = 0; a < mm; ++a) row = fma(T->wG[a], by[b][a], row);
+      sy = fma(T->wL[b], row, sy);
+    }
+#pragma unroll
+    for (int b = 0; b < mm; ++b) {
+      double row = 0.0;
+#pragma unroll
+      for (int a = 0; a < mm; ++a) row = fma(T->wM[a], bz[b][a], row);
+      sz = fma(T->wM[b], row, sz);
+    }
+    out[0] = M.Jdet * sx; out[1] = M.Jdet * sy; out[2] = M.Jdet * sz;
+  }
   for (int d = 0; d < 3; ++d) {
     double mx = -DBL_MAX, mn = DBL_MAX;
     const double* A = B + d * Z + (size_t)k * mm * mm;
     for (int t = 0; t < mm * mm; ++t) { mx = fmax(mx, A[t]); mn = fmin(mn, A[t]); }
     out[3 + d] = mx; out[6 + d] = mn;
   }
-  // tangential jumps on the lower faces, Gauss(k+2) face rule (reading R6)
-  for (int I = 0; I < 2; ++I) {
-    const int exA = I == 0 ? wrap(ex - 1, M.nx) : ex, eyA = I == 0 ? ey : wrap(ey - 1, M.ny);
-    const int dcomp[2] = {I == 0 ? 1 : 0, 2};
-    for (int tc = 0; tc < 2; ++tc) {
-      const int d = dcomp[tc];
-      double acc = 0.0;
-      for (int t = 0; t < q2; ++t) {
-        // upper face of A at +1, lower face of this element at -1; face coordinate z2_t
-        double vA, vB;
-        if (I == 0) {
-          vA = B_eval<KM>(B, Z, d, exA, eyA, T->L_end[1], T->G_end[1], T->M_end[1], T->L_2[t], T->G_2[t], T->M_2[t], M);
-          vB = B_eval<KM>(B, Z, d, ex, ey, T->L_end[0], T->G_end[0], T->M_end[0], T->L_2[t], T->G_2[t], T->M_2[t], M);
-        } else {
-          vA = B_eval<KM>(B, Z, d, exA, eyA, T->L_2[t], T->G_2[t], T->M_2[t], T->L_end[1], T->G_end[1], T->M_end[1], M);
-          vB = B_eval<KM>(B, Z, d, ex, ey, T->L_2[t], T->G_2[t], T->M_2[t], T->L_end[0], T->G_end[0], T->M_end[0], M);
-        }
-        double jmp = vB - vA;
-        acc = fma(0.5 * T->w2[t] * jmp, jmp, acc);
+  // tangential jumps on the lower faces, Gauss(k+2) face rule (reading R6):
+  // each trace collapses the normal direction once, then is evaluated at the
+  // face points
+  {  // x-face (I = 0): B_y and B_z of this element at x = -1 and of the -x neighbour at x = +1
+    const int exA = wrap(ex - 1, M.nx);
+    double ryB[mL], ryA[mL], rzB[mm], rzA[mm];
+#pragma unroll
+    for (int b = 0; b < mL; ++b) {
+      double vB = 0.0, vA = 0.0;
+#pragma unroll
+      for (int a = 0; a < mm; ++a) {
+        vB = fma(T->G_end[0][a], by[b][a], vB);
+        vA = fma(T->G_end[1][a], by_cl<KM>(B + Z, exA, ey, a, b, M), vA);
       }
-      out[9 + 2 * I + tc] = sqrt(acc);
+      ryB[b] = vB; ryA[b] = vA;
     }
+    const double* bzA = B + 2 * Z + ((size_t)ey * M.nx + exA) * mm * mm;
+#pragma unroll
+    for (int b = 0; b < mm; ++b) {
+      double vB = 0.0, vA = 0.0;
+#pragma unroll
+      for (int a = 0; a < mm; ++a) {
+        vB = fma(T->M_end[0][a], bz[b][a], vB);
+        vA = fma(T->M_end[1][a], bzA[b * mm + a], vA);
+      }
+      rzB[b] = vB; rzA[b] = vA;
+    }
+    double accy = 0.0, accz = 0.0;
+#pragma unroll
+    for (int t = 0; t < q2; ++t) {
+      double yB = 0.0, yA = 0.0, zB = 0.0, zA = 0.0;
+#pragma unroll
+      for (int b = 0; b < mL; ++b) { yB = fma(T->L_2[t][b], ryB[b], yB); yA = fma(T->L_2[t][b], ryA[b], yA); }
+#pragma unroll
+      for (int b = 0; b < mm; ++b) { zB = fma(T->M_2[t][b], rzB[b], zB); zA = fma(T->M_2[t][b], rzA[b], zA); }
+      const double jy = yB - yA, jz = zB - zA;
+      accy = fma(0.5 * T->w2[t] * jy, jy, accy);
+      accz = fma(0.5 * T->w2[t] * jz, jz, accz);
+    }
+    out[9] = sqrt(accy); out[10] = sqrt(accz);
   }
-  // a_{I,K} = max over DG nodes of |u_I| + |B_h| / sqrt(rho)
+  {  // y-face (I = 1): B_x and B_z of this element at y = -1 and of the -y neighbour at y = +1
+    const int eyA = wrap(ey - 1, M.ny);
+    double cxB[mL], cxA[mL], czB[mm], czA[mm];
+#pragma unroll
+    for (int a = 0; a < mL; ++a) {
+      double vB = 0.0, vA = 0.0;
+#pragma unroll
+      for (int b = 0; b < mm; ++b) {
+        vB = fma(T->G_end[0][b], bx[b][a], vB);
+        vA = fma(T->G_end[1][b], bx_cl<KM>(B, ex, eyA, a, b, M), vA);
+      }
+      cxB[a] = vB; cxA[a] = vA;
+    }
+    const double* bzA = B + 2 * Z + ((size_t)eyA * M.nx + ex) * mm * mm;
+#pragma unroll
+    for (int a = 0; a < mm; ++a) {
+      double vB = 0.0, vA = 0.0;
+#pragma unroll
+      for (int b = 0; b < mm; ++b) {
+        vB = fma(T->M_end[0][b], bz[b][a], vB);
+        vA = fma(T->M_end[1][b], bzA[b * mm + a], vA);
+      }
+      czB[a] = vB; czA[a] = vA;
+    }
+    double accx = 0.0, accz = 0.0;
+#pragma unroll
+    for (int t = 0; t < q2; ++t) {
+      double xB = 0.0, xA = 0.0, zB = 0.0, zA = 0.0;
+#pragma unroll
+      for (int a = 0; a < mL; ++a) { xB = fma(T->L_2[t][a], cxB[a], xB); xA = fma(T->L_2[t][a], cxA[a], xA); }
+#pragma unroll
+      for (int a = 0; a < mm; ++a) { zB = fma(T->M_2[t][a], czB[a], zB); zA = fma(T->M_2[t][a], czA[a], zA); }
+      const double jx = xB - xA, jz = zB - zA;
+      accx = fma(0.5 * T->w2[t] * jx, jx, accx);
+      accz = fma(0.5 * T->w2[t] * jz, jz, accz);
+    }
+    out[11] = sqrt(accx); out[12] = sqrt(accz);
+  }
+  // a_{I,K} = max over DG nodes of |u_I| + |B_h| / sqrt(rho): B at the nodes
+  // sum-factorised (x-pass, then y-pass: the order of the single-point tensor
+  // evaluation), one component at a time
+  double b2[n2];
+#pragma unroll
+  for (int q = 0; q < n2; ++q) b2[q] = 0.0;
+  {
+    double tx[mm][n];
+#pragma unroll
+    for (int b = 0; b < mm; ++b)
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        double v = 0.0;
+#pragma unroll
+        for (int a = 0; a < mL; ++a) v = fma(T->L_P[i][a], bx[b][a], v);
+        tx[b][i] = v;
+      }
+#pragma unroll
+    for (int j = 0; j < n; ++j)
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        double v = 0.0;
+#pragma unroll
+        for (int b = 0; b < mm; ++b) v = fma(T->G_P[j][b], tx[b][i], v);
+        b2[j * n + i] = v * v;
+      }
+  }
+  {
+    double ty[mL][n];
+#pragma unroll
+    for (int b = 0; b < mL; ++b)
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        double v = 0.0;
+#pragma unroll
+        for (int a = 0; a < mm; ++a) v = fma(T->G_P[i][a], by[b][a], v);
+        ty[b][i] = v;
+      }
+#pragma unroll
+    for (int j = 0; j < n; ++j)
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        double v = 0.0;
+#pragma unroll
+        for (int b = 0; b < mL; ++b) v = fma(T->L_P[j][b], ty[b][i], v);
+        b2[j * n + i] = fma(v, v, b2[j * n + i]);
+      }
+  }
+  {
+    double tz[mm][n];
+#pragma unroll
+    for (int b = 0; b < mm; ++b)
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        double v = 0.0;
+#pragma unroll
+        for (int a = 0; a < mm; ++a) v = fma(T->M_P[i][a], bz[b][a], v);
+        tz[b][i] = v;
+      }
+#pragma unroll
+    for (int j = 0; j < n; ++j)
+#pragma unroll
+      for (int i = 0; i < n; ++i) {
+        double v = 0.0;
+#pragma unroll
+        for (int b = 0; b < mm; ++b) v = fma(T->M_P[j][b], tz[b][i], v);
+        b2[j * n + i] = fma(v, v, b2[j * n + i]);
+      }
+  }
   double ax = 0.0, ay = 0.0;
+#pragma unroll
   for (int q = 0; q < n2; ++q) {
-    int i = q % n, j = q / n;
-    double Bv[3];
-    for (int d = 0; d < 3; ++d)
-      Bv[d] = B_eval<KM>(B, Z, d, ex, ey, T->L_P[i], T->G_P[i], T->M_P[i], T->L_P[j], T->G_P[j], T->M_P[j], M);
-    double b2 = fma(Bv[0], Bv[0], fma(Bv[1], Bv[1], Bv[2] * Bv[2]));
-    double va = sqrt(b2 * rcp(rho[(size_t)k * n2 + q]));  // |B_h| / sqrt(rho)
-    ax = fmax(ax, fabs(Y[N + (size_t)k * n2 + q]) + va);
-    ay = fmax(ay, fabs(Y[2 * N + (size_t)k * n2 + q]) + va);
+    const size_t gq = MHD_CHK((size_t)k * n2 + q, N);
+    const double va = sqrt(b2[q] * rcp(rho[gq]));  // |B_h| / sqrt(rho)
+    ax = fmax(ax, fabs(Y[N + gq]) + va);
+    ay = fmax(ay, fabs(Y[2 * N + gq]) + va);
   }
   out[13] = ax; out[14] = ay; out[15] = 0.0;
   for (int c = 0; c < 16; ++c) ar[(size_t)k * 16 + c] = out[c];
