@@ -112,19 +112,34 @@ def stats_flops(p, nc):
     return nc * (2 * n * n + 2 * per_dir)
 
 
-def b_eval_flops(k):
-    """One evaluation of a B component at a single point from its element
-    DOFs as a tensor product (the larger R_h^k factor: (k+2)(k+1) + (k+1)
-    FMAs)."""
-    mm, mL = k + 1, k + 2
-    return 2 * (mL * mm + mm)
-
-
 def b_nodes_flops(p, k):
     """B_x, B_y, B_z at all (p+1)^2 DG nodes of an element, sum-factorised:
-    an x-pass over the rows, then a y-pass (2 flops per FMA)."""
+    an x-pass over the rows, then a y-pass (2 flops per FMA).  A node family
+    that coincides with the DG nodes (GLL(k+1) at k = p - 1, GLL(k) at k = p)
+    needs no interpolation: its passes are copies."""
     n, mm, mL = p + 1, k + 1, k + 2
-    return 2 * (2 * (mm * n * mL + n * n * mm) + (mm * n * mm + n * n * mm))
+    lid, mid = mL == n, mm == n
+    bx = (0 if lid else mm * n * mL) + n * n * mm
+    by = mL * n * mm + (0 if lid else n * n * mL)
+    bz = 0 if mid else mm * n * mm + n * n * mm
+    return 2 * (bx + by + bz)
+
+
+def ar_elem_flops(p, k):
+    """The A.R. partials of one element (k_ar_elem): the exact integrals of
+    B_x, B_y, B_z (weight rows, x-pass then y-pass), per lower face the two
+    tangential traces of both elements with the normal direction collapsed
+    first, their values, jumps and squared sums at the k + 2 face points and a
+    square root per component, and B at the DG nodes with |B|^2 / rho, a
+    square root and the speeds per node."""
+    n, mm, mL = p + 1, k + 1, k + 2
+    n2 = n * n
+    integrals = 2 * (mm * mL + mm) + 2 * (mL * mm + mL) + 2 * (mm * mm + mm) + 3
+    traces = 2 * (2 * mL * mm + 2 * mm * mm)
+    per_point = 2 * (2 * mL + 2 * mm) + 2 + 2 + 2 * 2
+    face = traces + (k + 2) * per_point + 2
+    nodes = b_nodes_flops(p, k) + n2 * (5 + 1 + 1 + 1 + 4)
+    return integrals + 2 * face + nodes
 
 
 def step_work(p, k):
@@ -161,12 +176,14 @@ def step_work(p, k):
     # magnetic stage (J, E, curl) x 3 stages
     fJ = 2 * (2 * mm * mL * mL + 2 * NZ * mm + 2 * mm * NW + (NX + NY) * mm) + 3 * NW + 2 * (NX + NY)
     assemble = 4 * NW + 2 * (NX + NY)
+    # at k = p - 1 the GLL(k+1) nodes are the DG nodes: every pass between them is a copy
+    lid = mL == n
     fE = (assemble
-          + 2 * (2 * n * mm * n + 3 * n * mL * n + NW * mm + NZ * mm + mm * mL * mm)        # x-passes
-          + 2 * ((2 * NX + 2 * NY + 2 * NW) * n + (NX + NY + NW) * mm)                     # y-passes
+          + 2 * (2 * n * mm * n + (0 if lid else 3 * n * mL * n) + NW * mm + NZ * mm + mm * mL * mm)  # x-passes
+          + 2 * ((2 * NY + (0 if lid else 2 * NX + 2 * NW)) * n + (NX + NY + NW) * mm)                  # y-passes
           + 10 * (NX + NY + NW)                                                              # Ohm loads, Lorentz
-          + 2 * (4 * n * mm * mL + 2 * n * mL * mL)                                          # transposed y-pass
-          + n2 * (2 * (3 * mL + 2 * mm) + 27))                                               # x-pass, rates, SSP
+          + (2 * 2 * n * mm * mL + n * mL if lid else 2 * (4 * n * mm * mL + 2 * n * mL * mL))  # transposed y-pass
+          + n2 * (2 * ((0 if lid else 3 * mL) + 2 * mm) + 27))                               # x-pass, rates, SSP
     fB = assemble + 2 * (NZ * mL + mL * mm * mm) + 3 * NZ * (2 * mL + 6) + NZ * 2 * mm
     loads = (NX + NY + NW) * d8
     bJ = 3 * NZ * d8 + loads
@@ -174,11 +191,8 @@ def step_work(p, k):
     bB = loads + 3 * NZ * d8 * 3
     work["mag_stage"] = (3 * (fJ + fE + fB), 3 * (bJ + bE + bB))
     # A.R. coefficient once per magnetic substep: element integrals, face jumps
-    # (2 directions x 2 components x (k+2) points x 2 traces), and B at the DG
-    # nodes for the directional speeds
-    be = b_eval_flops(k)
-    work["stab_eta"] = (3 * be + 2 * 2 * (k + 2) * 2 * (be + 3) + b_nodes_flops(p, k) + 8 * n2,
-                        (3 * NZ + 3 * n2 + 16) * d8)
+    # of the tangential traces, and B at the DG nodes for the directional speeds
+    work["stab_eta"] = (ar_elem_flops(p, k), (3 * NZ + 3 * n2 + 16) * d8)
     # velocity OE: projectors once (rho-weighted Gram matrix, Cholesky, the
     # rows of Psi = Phi L^-T), then per stage the statistics of 3 fields and the
     # map (B at the nodes, coefficients and shell sums: 2 n2^2 FMAs per component)

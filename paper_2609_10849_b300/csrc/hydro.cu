@@ -134,6 +134,8 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads, HCfg<P, EBv>::min_block
   __shared__ double sl[2][EB * n2];           // log(rho/2), log(beta/2), when a pair needs them
   __shared__ double sf[5][EB * NP];           // pair fluxes
   __shared__ double savg[5][EB];
+  __shared__ double sDs[2][n2];               // s (-4/h_I) D: the gather rows of both directions, scaled
+  __shared__ double sFs[2];                   // s (2/h_I) / w_0: the end-node coefficients, scaled
   const size_t N = (size_t)M.K * n2;
   const int tid = threadIdx.x;
   const int el = tid / n2, q = tid % n2;
@@ -146,6 +148,18 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads, HCfg<P, EBv>::min_block
   double Us[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) Us[c] = S[MHD_CHK(c * N + gi, 5 * N)];
+  // the gather's coefficients once per block: D and the end-node factors
+  // times the metric and, in the stage combination, times tau (first stage)
+  // or b tau, so that the gather yields the stage increment directly
+  {
+    const double sc = MODE == 0 ? 1.0 : (first ? dtp[0] * dtfac : cb * (dtp[0] * dtfac));
+    constexpr double w0i = 0.5 * P * (P + 1);  // 1 / w_0 of GLL(p): w_0 = 2 / (p (p + 1))
+    const double sx = -4.0 * M.ihx * sc, sy = -4.0 * M.ihy * sc;
+    for (int t = tid; t < 2 * n2 + 2; t += EB * n2) {
+      if (t < 2 * n2) sDs[t / n2][t % n2] = T->D[(t % n2) / n][t % n] * (t < n2 ? sx : sy);
+      else sFs[t - 2 * n2] = (t == 2 * n2 ? 2.0 * M.ihx : 2.0 * M.ihy) * w0i * sc;
+    }
+  }
   {
     double ir = rcp(Us[0]);
     double ux = Us[1] * ir, uy = Us[2] * ir, uz = Us[3] * ir;
@@ -212,6 +226,7 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads, HCfg<P, EBv>::min_block
   __syncthreads();
 
   // ---- gather: L = -(2/hx)[2 sum D F + end terms] - (2/hy)[...] -----------------
+  // (times the block's scale s: 1 for the residual, tau or b tau in a stage)
   const int i = q % n, j = q / n;
   // the p off-diagonal terms of rows i and j of D, visited as r = i + o (mod n),
   // o = 1..p: no lane-dependent skip of the diagonal, so no predicated-off FMA
@@ -220,33 +235,29 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads, HCfg<P, EBv>::min_block
 #pragma unroll
   for (int o = 1; o < n; ++o) {
     const int rx = i + o < n ? i + o : i + o - n, ry = j + o < n ? j + o : j + o - n;
-    Dx[o - 1] = T->D[i][rx];
-    Dy[o - 1] = T->D[j][ry];
+    Dx[o - 1] = sDs[0][i * n + rx];
+    Dy[o - 1] = sDs[1][j * n + ry];
     px[o - 1] = (int)MHD_CHK(el * NP + j * NPL + pair_index(min(i, rx), max(i, rx)), EB * NP);
     py[o - 1] = (int)MHD_CHK(el * NP + NP / 2 + i * NPL + pair_index(min(j, ry), max(j, ry)), EB * NP);
   }
-  const double cx = -4.0 * M.ihx, cy = -4.0 * M.ihy;
-  constexpr double w0i = 0.5 * P * (P + 1);  // 1 / w_0 of GLL(p): w_0 = 2 / (p (p + 1))
-  const double fx = 2.0 * M.ihx * w0i, fy = 2.0 * M.ihy * w0i;
   const int ex = kk % M.nx, ey = kk / M.nx;
   const size_t nf = (size_t)M.K * n;
   // face terms as one FMA per direction in every lane: the coefficient is
   // +-2/(h w_0) on the end nodes and 0 inside (0 * F* adds an exact zero), so
-  // no lane-divergent block is issued; end nodes keep the x-then-y order
-  const double cfx = i == 0 ? fx : (i == P ? -fx : 0.0);
-  const double cfy = j == 0 ? fy : (j == P ? -fy : 0.0);
+  // no lane-divergent block is issued
+  const double cfx = i == 0 ? sFs[0] : (i == P ? -sFs[0] : 0.0);
+  const double cfy = j == 0 ? sFs[1] : (j == P ? -sFs[1] : 0.0);
   const size_t ifx = (i == P ? (size_t)(ey * M.nx + wrap(ex + 1, M.nx)) : (size_t)kk) * n + j;
   const size_t ify = (j == P ? (size_t)(wrap(ey + 1, M.ny) * M.nx + ex) : (size_t)kk) * n + i;
   double L[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) {
-    double sx = 0.0, sy = 0.0;
+    // one chain over both directions (the rows carry the metric factors)
+    double v = 0.0;
 #pragma unroll
-    for (int o = 0; o < P; ++o) {
-      sx = fma(Dx[o], sf[c][px[o]], sx);
-      sy = fma(Dy[o], sf[c][py[o]], sy);
-    }
-    double v = fma(cx, sx, cy * sy);
+    for (int o = 0; o < P; ++o) v = fma(Dx[o], sf[c][px[o]], v);
+#pragma unroll
+    for (int o = 0; o < P; ++o) v = fma(Dy[o], sf[c][py[o]], v);
     // end nodes: -(2/hx)[-F*_left/w_0] and -(2/hx)[+F*_right/w_p] (w_p = w_0)
     v = fma(cfx, Fx[MHD_CHK(c * nf + ifx, 5 * nf)], v);
     v = fma(cfy, Fy[MHD_CHK(c * nf + ify, 5 * nf)], v);
@@ -261,13 +272,11 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads, HCfg<P, EBv>::min_block
     return;
   }
 
-  const double tau = dtp[0] * dtfac;
+  // L is tau L (first stage) or b tau L: C = S + tau L, or a U0 + b S + b tau L
   double Cv[5];
 #pragma unroll
-  for (int c = 0; c < 5; ++c) {
-    double raw = fma(tau, L[c], Us[c]);
-    Cv[c] = first ? raw : fma(ca, U0[MHD_CHK(c * N + gi, 5 * N)], cb * raw);
-  }
+  for (int c = 0; c < 5; ++c)
+    Cv[c] = first ? Us[c] + L[c] : fma(ca, U0[MHD_CHK(c * N + gi, 5 * N)], fma(cb, Us[c], L[c]));
   if (valid) {
 #pragma unroll
     for (int c = 0; c < 5; ++c) out[MHD_CHK(c * N + gi, 5 * N)] = Cv[c];

@@ -48,6 +48,10 @@ struct MTab {
   double W_GL[MHD_NMAX][MHD_LMAX];   // wG_a wL_b: lumped weight of an N_x node (a Gauss in x, b GLL in y)
   double W_LG[MHD_LMAX][MHD_NMAX];   // wL_a wG_b: N_y node
   double W_LL[MHD_LMAX][MHD_LMAX];   // wL_a wL_b: W node
+  // reciprocal lumped weights of the three families, one product each
+  double iW_LL[MHD_LMAX][MHD_LMAX];  // iwLs_a iwLs_b: W node
+  double iW_GL[MHD_NMAX][MHD_LMAX];  // iwG_a iwLs_b: N_x node
+  double iW_LG[MHD_LMAX][MHD_NMAX];  // iwLs_a iwG_b: N_y node
 };
 
 __constant__ MTab c_mtab[8];
@@ -80,7 +84,14 @@ void upload_mag_tables(int slot, const Tab* h, cudaError_t* err) {
   for (int a = 0; a < MHD_LMAX; ++a)
     for (int b = 0; b < MHD_NMAX; ++b) m.W_LG[a][b] = h->wL[a] * h->wG[b];
   for (int a = 0; a < MHD_LMAX; ++a)
-    for (int b = 0; b < MHD_LMAX; ++b) m.W_LL[a][b] = h->wL[a] * h->wL[b];
+    for (int b = 0; b < MHD_LMAX; ++b) {
+      m.W_LL[a][b] = h->wL[a] * h->wL[b];
+      m.iW_LL[a][b] = h->iwLs[a] * h->iwLs[b];
+    }
+  for (int a = 0; a < MHD_NMAX; ++a)
+    for (int b = 0; b < MHD_LMAX; ++b) m.iW_GL[a][b] = h->iwG[a] * h->iwLs[b];
+  for (int a = 0; a < MHD_LMAX; ++a)
+    for (int b = 0; b < MHD_NMAX; ++b) m.iW_LG[a][b] = h->iwLs[a] * h->iwG[b];
   *err = cudaMemcpyToSymbol(c_mtab, &m, sizeof(MTab), slot * sizeof(MTab));
 }
 
@@ -94,6 +105,12 @@ struct MD {
   static constexpr int EB = EBv;       // elements per block (autotuned variant)
   static constexpr int TH = 256;       // threads per block
   static constexpr int SLOT = P - 1 + KM;
+  // k = p - 1: the GLL(k+1) nodes of the auxiliary families are the DG nodes
+  // (the same rule, so the same doubles), and the tables between them, P_L and
+  // L_P, are exactly the identity; every pass through them is skipped (a copy
+  // gives the same bits as the FMA chain it replaces: one term 1 * x, the
+  // others 0 * x).
+  static constexpr bool LID = mL == n;
 };
 
 #define FLAT(ITEMS) for (int idx = threadIdx.x; idx < D::EB * (ITEMS); idx += blockDim.x)
@@ -116,7 +133,7 @@ __device__ __forceinline__ double assemble_W(const double* __restrict__ Lz, int 
   if (bo == 0) v += Lz[MHD_CHK((size_t)(sy * M.nx + ox) * D::NW + (D::mL - 1) * D::mL + ao, KW)];
   if (ao == 0) v += Lz[MHD_CHK((size_t)(oy * M.nx + wx) * D::NW + bo * D::mL + (D::mL - 1), KW)];
   v += Lz[MHD_CHK((size_t)(oy * M.nx + ox) * D::NW + bo * D::mL + ao, KW)];
-  return v * (iJ * T.iwLs[ao] * T.iwLs[bo]);
+  return v * (iJ * T.iW_LL[ao][bo]);
 }
 
 // Y-type (N_x) closure node (a < mm, b < mL).
@@ -132,7 +149,7 @@ __device__ __forceinline__ double assemble_Nx(const double* __restrict__ Lx, int
   const size_t KX = (size_t)M.K * D::NX;
   if (bo == 0) v += Lx[MHD_CHK((size_t)(sy * M.nx + ex) * D::NX + (D::mL - 1) * D::mm + a, KX)];
   v += Lx[MHD_CHK((size_t)(oy * M.nx + ex) * D::NX + bo * D::mm + a, KX)];
-  return v * (iJ * T.iwG[a] * T.iwLs[bo]);
+  return v * (iJ * T.iW_GL[a][bo]);
 }
 
 // X-type (N_y) closure node (a < mL, b < mm).
@@ -148,7 +165,7 @@ __device__ __forceinline__ double assemble_Ny(const double* __restrict__ Ly, int
   const size_t KY = (size_t)M.K * D::NY;
   if (ao == 0) v += Ly[MHD_CHK((size_t)(ey * M.nx + wx) * D::NY + b * D::mL + (D::mL - 1), KY)];
   v += Ly[MHD_CHK((size_t)(ey * M.nx + ox) * D::NY + b * D::mL + ao, KY)];
-  return v * (iJ * T.iwLs[ao] * T.iwG[b]);
+  return v * (iJ * T.iW_LG[ao][b]);
 }
 
 // B closure loads: Bx (X-type, [b < mm][a < mL]) and By (Y-type, [b < mL][a < mm]).
@@ -359,8 +376,11 @@ __global__ void __launch_bounds__(256) k_mag_E(
       int d = it / (D::n * D::mL), r = it % (D::n * D::mL), j = r / D::mL, a = r % D::mL;
       const double* ur = u + MHD_CHK(d * N + (size_t)k * D::n2 + j * D::n, 3 * N - D::n + 1);
       double v = 0.0;
+      if constexpr (D::LID) v = ur[a];
+      else {
 #pragma unroll
-      for (int i = 0; i < D::n; ++i) v = fma(T.P_L[a][i], ur[i], v);
+        for (int i = 0; i < D::n; ++i) v = fma(T.P_L[a][i], ur[i], v);
+      }
       SM(O::UL, it) = v;
       continue;
     }
@@ -402,8 +422,11 @@ __global__ void __launch_bounds__(256) k_mag_E(
       if (it < 2 * D::NX) {  // u_y, u_z at N_x: GLL(k+1) y from GLL(p)
         int d = it / D::NX, r = it % D::NX, b = r / D::mm, a = r % D::mm;
         double v = 0.0;
+        if constexpr (D::LID) v = SM(O::UG, d * D::n * D::mm + b * D::mm + a);
+        else {
 #pragma unroll
-        for (int j = 0; j < D::n; ++j) v = fma(T.P_L[b][j], SM(O::UG, d * D::n * D::mm + j * D::mm + a), v);
+          for (int j = 0; j < D::n; ++j) v = fma(T.P_L[b][j], SM(O::UG, d * D::n * D::mm + j * D::mm + a), v);
+        }
         SM(O::UNX, it) = v;
         continue;
       }
@@ -422,8 +445,11 @@ __global__ void __launch_bounds__(256) k_mag_E(
     if (it < 2 * D::NW) {  // u_x, u_y at W
       int d = it / D::NW, r = it % D::NW, b = r / D::mL, a = r % D::mL;
       double v = 0.0;
+      if constexpr (D::LID) v = SM(O::UL, d * D::n * D::mL + b * D::mL + a);
+      else {
 #pragma unroll
-      for (int j = 0; j < D::n; ++j) v = fma(T.P_L[b][j], SM(O::UL, d * D::n * D::mL + j * D::mL + a), v);
+        for (int j = 0; j < D::n; ++j) v = fma(T.P_L[b][j], SM(O::UL, d * D::n * D::mL + j * D::mL + a), v);
+      }
       SM(O::UW, it) = v;
       continue;
     }
@@ -468,8 +494,9 @@ __global__ void __launch_bounds__(256) k_mag_E(
       double by_ = SM(O::BY, it), bz_ = SM(O::BZNX, it), jx_ = SM(O::JX, it);
       double uy = SM(O::UNX, it), uz = SM(O::UNX, D::NX + it);
       if (k < M.K) LEx[MHD_CHK((size_t)k * D::NX + it, (size_t)M.K * D::NX)] = w * fma(uz, by_, -uy * bz_);
-      SM(O::UNX, it) = -w * bz_ * jx_;         // s_y contribution
-      SM(O::UNX, D::NX + it) = w * by_ * jx_;  // s_z contribution
+      const double wj = w * jx_;
+      SM(O::UNX, it) = -wj * bz_;         // s_y contribution
+      SM(O::UNX, D::NX + it) = wj * by_;  // s_z contribution
     } else if (!R2 && it < D::NX + D::NY) {
       it -= D::NX;
       int b = it / D::mL, a = it % D::mL;
@@ -477,8 +504,9 @@ __global__ void __launch_bounds__(256) k_mag_E(
       double bx_ = SM(O::BX, it), bz_ = SM(O::BZNY, it), jy_ = SM(O::JY, it);
       double ux = SM(O::UNY, it), uz = SM(O::UNY, D::NY + it);
       if (k < M.K) LEy[MHD_CHK((size_t)k * D::NY + it, (size_t)M.K * D::NY)] = w * fma(ux, bz_, -uz * bx_);
-      SM(O::UNY, it) = w * bz_ * jy_;           // s_x
-      SM(O::UNY, D::NY + it) = -w * bx_ * jy_;  // s_z
+      const double wj = w * jy_;
+      SM(O::UNY, it) = wj * bz_;           // s_x
+      SM(O::UNY, D::NY + it) = -wj * bx_;  // s_z
     } else {
       if constexpr (!R2) it -= D::NX + D::NY;
       int b = it / D::mL, a = it % D::mL;
@@ -486,8 +514,9 @@ __global__ void __launch_bounds__(256) k_mag_E(
       double bx_ = SM(O::BXW, it), by_ = SM(O::BYL, it), jz_ = SM(O::JZ, it);
       double ux = SM(O::UW, it), uy = SM(O::UW, D::NW + it);
       if (k < M.K) LEz[MHD_CHK((size_t)k * D::NW + it, (size_t)M.K * D::NW)] = w * fma(uy, bx_, -ux * by_);
-      SM(O::UW, it) = -w * by_ * jz_;          // s_x
-      SM(O::UW, D::NW + it) = w * bx_ * jz_;   // s_y
+      const double wj = w * jz_;
+      SM(O::UW, it) = -wj * by_;          // s_x
+      SM(O::UW, D::NW + it) = wj * bx_;   // s_y
     }
   }
   __syncthreads();
@@ -502,8 +531,11 @@ __global__ void __launch_bounds__(256) k_mag_E(
 #pragma unroll
         for (int b = 0; b < D::mm; ++b) v = fma(T.P_G[b][j], SM(O::UNY, b * D::mL + a), v);
       }
+      if constexpr (D::LID) v += SM(O::UW, j * D::mL + a);
+      else {
 #pragma unroll
-      for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UW, b * D::mL + a), v);
+        for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UW, b * D::mL + a), v);
+      }
       SM(O::VX, it) = v;
       continue;
     }
@@ -512,8 +544,11 @@ __global__ void __launch_bounds__(256) k_mag_E(
       if (it < D::n * D::mm) {
         int j = it / D::mm, a = it % D::mm;
         double v = 0.0;
+        if constexpr (D::LID) v = SM(O::UNX, j * D::mm + a);
+        else {
 #pragma unroll
-        for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UNX, b * D::mm + a), v);
+          for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UNX, b * D::mm + a), v);
+        }
         SM(O::VY1, it) = v;
         continue;
       }
@@ -522,8 +557,11 @@ __global__ void __launch_bounds__(256) k_mag_E(
     if (it < D::n * D::mL) {
       int j = it / D::mL, a = it % D::mL;
       double v = 0.0;
+      if constexpr (D::LID) v = SM(O::UW, D::NW + j * D::mL + a);
+      else {
 #pragma unroll
-      for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UW, D::NW + b * D::mL + a), v);
+        for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UW, D::NW + b * D::mL + a), v);
+      }
       SM(O::VY2, it) = v;
       continue;
     }
@@ -532,8 +570,11 @@ __global__ void __launch_bounds__(256) k_mag_E(
       if (it < D::n * D::mm) {
         int j = it / D::mm, a = it % D::mm;
         double v = 0.0;
+        if constexpr (D::LID) v = SM(O::UNX, D::NX + j * D::mm + a);
+        else {
 #pragma unroll
-        for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UNX, D::NX + b * D::mm + a), v);
+          for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UNX, D::NX + b * D::mm + a), v);
+        }
         SM(O::VZ1, it) = v;
         continue;
       }
@@ -565,15 +606,21 @@ __global__ void __launch_bounds__(256) k_mag_E(
         it -= D::mL * D::n;
         int b = it / D::n, i = it % D::n;
         double v = 0.0;
+        if constexpr (D::LID) v = SM(O::JY, b * D::mL + i);
+        else {
 #pragma unroll
-        for (int a = 0; a < D::mL; ++a) v = fma(T.L_P[i][a], SM(O::JY, b * D::mL + a), v);
+          for (int a = 0; a < D::mL; ++a) v = fma(T.L_P[i][a], SM(O::JY, b * D::mL + a), v);
+        }
         SM(O::TQ, D::n * D::mL + it) = v;
       } else {
         it -= D::mL * D::n + D::mm * D::n;
         int b = it / D::n, i = it % D::n;
         double v = 0.0;
+        if constexpr (D::LID) v = SM(O::JZ, b * D::mL + i);
+        else {
 #pragma unroll
-        for (int a = 0; a < D::mL; ++a) v = fma(T.L_P[i][a], SM(O::JZ, b * D::mL + a), v);
+          for (int a = 0; a < D::mL; ++a) v = fma(T.L_P[i][a], SM(O::JZ, b * D::mL + a), v);
+        }
         SM(O::TQ, 2 * D::n * D::mL + it) = v;
       }
     }
@@ -586,14 +633,20 @@ __global__ void __launch_bounds__(256) k_mag_E(
       int d = it / D::n2, q = it % D::n2, j = q / D::n, i = q % D::n;
       double v = 0.0;
       if (d == 0) {
+        if constexpr (D::LID) v = SM(O::TQ, j * D::n + i);
+        else {
 #pragma unroll
-        for (int b = 0; b < D::mL; ++b) v = fma(T.L_P[j][b], SM(O::TQ, b * D::n + i), v);
+          for (int b = 0; b < D::mL; ++b) v = fma(T.L_P[j][b], SM(O::TQ, b * D::n + i), v);
+        }
       } else if (d == 1) {
 #pragma unroll
         for (int b = 0; b < D::mm; ++b) v = fma(T.G_P[j][b], SM(O::TQ, D::n * D::mL + b * D::n + i), v);
       } else {
+        if constexpr (D::LID) v = SM(O::TQ, 2 * D::n * D::mL + j * D::n + i);
+        else {
 #pragma unroll
-        for (int b = 0; b < D::mL; ++b) v = fma(T.L_P[j][b], SM(O::TQ, 2 * D::n * D::mL + b * D::n + i), v);
+          for (int b = 0; b < D::mL; ++b) v = fma(T.L_P[j][b], SM(O::TQ, 2 * D::n * D::mL + b * D::n + i), v);
+        }
       }
       SM(O::JQ, it) = v;
     }
@@ -616,15 +669,21 @@ __global__ void __launch_bounds__(256) k_mag_E(
         it -= D::n * D::mm;
         int j = it / D::mL, a = it % D::mL;
         double t = 0.0;
+        if constexpr (D::LID) t = T.WL_P[a][a] * SM(O::JQ, D::n2 + j * D::n + a);
+        else {
 #pragma unroll
-        for (int i = 0; i < D::n; ++i) t = fma(T.WL_P[i][a], SM(O::JQ, D::n2 + j * D::n + i), t);
+          for (int i = 0; i < D::n; ++i) t = fma(T.WL_P[i][a], SM(O::JQ, D::n2 + j * D::n + i), t);
+        }
         SM(O::TQ, D::n * D::mm + it) = t;
       } else {  // W: basis l^L_a in x
         it -= D::n * D::mm + D::n * D::mL;
         int j = it / D::mL, a = it % D::mL;
         double t = 0.0;
+        if constexpr (D::LID) t = T.WL_P[a][a] * SM(O::JQ, 2 * D::n2 + j * D::n + a);
+        else {
 #pragma unroll
-        for (int i = 0; i < D::n; ++i) t = fma(T.WL_P[i][a], SM(O::JQ, 2 * D::n2 + j * D::n + i), t);
+          for (int i = 0; i < D::n; ++i) t = fma(T.WL_P[i][a], SM(O::JQ, 2 * D::n2 + j * D::n + i), t);
+        }
         SM(O::TQ, D::n * D::mm + D::n * D::mL + it) = t;
       }
     }
@@ -639,8 +698,11 @@ __global__ void __launch_bounds__(256) k_mag_E(
       double r = 0.0;
       if (it < D::NX) {  // (a < mm, b < mL): y basis l^L_b
         int b = it / D::mm, a = it % D::mm;
+        if constexpr (D::LID) r = T.WL_P[b][b] * SM(O::TQ, b * D::mm + a);
+        else {
 #pragma unroll
-        for (int j = 0; j < D::n; ++j) r = fma(T.WL_P[j][b], SM(O::TQ, j * D::mm + a), r);
+          for (int j = 0; j < D::n; ++j) r = fma(T.WL_P[j][b], SM(O::TQ, j * D::mm + a), r);
+        }
         LEx[(size_t)k * D::NX + it] += f * r;
       } else if (it < D::NX + D::NY) {  // (a < mL, b < mm): y basis g_b
         it -= D::NX;
@@ -651,8 +713,11 @@ __global__ void __launch_bounds__(256) k_mag_E(
       } else {  // W: y basis l^L_b
         it -= D::NX + D::NY;
         int b = it / D::mL, a = it % D::mL;
+        if constexpr (D::LID) r = T.WL_P[b][b] * SM(O::TQ, D::n * D::mm + D::n * D::mL + b * D::mL + a);
+        else {
 #pragma unroll
-        for (int j = 0; j < D::n; ++j) r = fma(T.WL_P[j][b], SM(O::TQ, D::n * D::mm + D::n * D::mL + j * D::mL + a), r);
+          for (int j = 0; j < D::n; ++j) r = fma(T.WL_P[j][b], SM(O::TQ, D::n * D::mm + D::n * D::mL + j * D::mL + a), r);
+        }
         LEz[(size_t)k * D::NW + it] += f * r;
       }
     }
@@ -666,11 +731,17 @@ __global__ void __launch_bounds__(256) k_mag_E(
     if (k >= M.K) continue;
     int j = q / D::n, i = q % D::n;
     double sx = 0.0, sy = 0.0, sz = 0.0;
+    if constexpr (D::LID) {
+      sx = SM(O::VX, j * D::mL + i);
+      sy = SM(O::VY2, j * D::mL + i);
+      if constexpr (!R2) sz = SM(O::VZ2, j * D::mL + i);
+    } else {
 #pragma unroll
-    for (int a = 0; a < D::mL; ++a) {
-      sx = fma(T.P_L[a][i], SM(O::VX, j * D::mL + a), sx);
-      sy = fma(T.P_L[a][i], SM(O::VY2, j * D::mL + a), sy);
-      if constexpr (!R2) sz = fma(T.P_L[a][i], SM(O::VZ2, j * D::mL + a), sz);
+      for (int a = 0; a < D::mL; ++a) {
+        sx = fma(T.P_L[a][i], SM(O::VX, j * D::mL + a), sx);
+        sy = fma(T.P_L[a][i], SM(O::VY2, j * D::mL + a), sy);
+        if constexpr (!R2) sz = fma(T.P_L[a][i], SM(O::VZ2, j * D::mL + a), sz);
+      }
     }
     if constexpr (!R2) {
 #pragma unroll

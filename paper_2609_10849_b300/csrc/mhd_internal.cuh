@@ -65,6 +65,9 @@ struct Tab {
   double WLeg[MHD_NMAX][MHD_NMAX];            // wp_j P_b(xp_j): [j][b]
   double LegN2[MHD_NMAX][MHD_NMAX];           // LegN_a LegN_b
   double LegLeg[MHD_NMAX][MHD_NMAX][MHD_NMAX];  // P_b(xp_j) P_b2(xp_j): [j][b][b2]
+  // the modal basis at the nodes, P_a(xp_i) P_b(xp_j) at node q = j (p+1) + i, basis
+  // index alpha in shell order (shell l = max(a, b) holds alpha in [l^2, (l+1)^2))
+  double Phi[MHD_NMAX * MHD_NMAX][MHD_NMAX * MHD_NMAX];
 };
 
 // Device copy of the tables of the 8 supported (p, k) pairs.

@@ -803,6 +803,10 @@ template <int P, int KM>
 __global__ void k_ar_elem(const double* __restrict__ rho, const double* __restrict__ Y, const double* __restrict__ B,
                           const Tab* __restrict__ T, Mesh M, double* __restrict__ ar) {
   constexpr int n = P + 1, n2 = n * n, mm = KM + 1, mL = KM + 2, q2 = KM + 2;
+  // node families that coincide with the DG nodes (the same GLL rule, so the
+  // same doubles): GLL(k+1) at k = p - 1, GLL(k) at k = p; the interpolation
+  // between them is exactly the identity and is skipped (same bits)
+  constexpr bool LID = mL == n, MID = mm == n;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= M.K) return;
   const size_t Z = (size_t)M.K * mm * mm, N = (size_t)M.K * n2;
@@ -948,8 +952,11 @@ __global__ void k_ar_elem(const double* __restrict__ rho, const double* __restri
 #pragma unroll
       for (int i = 0; i < n; ++i) {
         double v = 0.0;
+        if constexpr (LID) v = bx[b][i];
+        else {
 #pragma unroll
-        for (int a = 0; a < mL; ++a) v = fma(T->L_P[i][a], bx[b][a], v);
+          for (int a = 0; a < mL; ++a) v = fma(T->L_P[i][a], bx[b][a], v);
+        }
         tx[b][i] = v;
       }
 #pragma unroll
@@ -978,8 +985,11 @@ __global__ void k_ar_elem(const double* __restrict__ rho, const double* __restri
 #pragma unroll
       for (int i = 0; i < n; ++i) {
         double v = 0.0;
+        if constexpr (LID) v = ty[j][i];
+        else {
 #pragma unroll
-        for (int b = 0; b < mL; ++b) v = fma(T->L_P[j][b], ty[b][i], v);
+          for (int b = 0; b < mL; ++b) v = fma(T->L_P[j][b], ty[b][i], v);
+        }
         b2[j * n + i] = fma(v, v, b2[j * n + i]);
       }
   }
@@ -990,8 +1000,11 @@ __global__ void k_ar_elem(const double* __restrict__ rho, const double* __restri
 #pragma unroll
       for (int i = 0; i < n; ++i) {
         double v = 0.0;
+        if constexpr (MID) v = bz[b][i];
+        else {
 #pragma unroll
-        for (int a = 0; a < mm; ++a) v = fma(T->M_P[i][a], bz[b][a], v);
+          for (int a = 0; a < mm; ++a) v = fma(T->M_P[i][a], bz[b][a], v);
+        }
         tz[b][i] = v;
       }
 #pragma unroll
@@ -999,8 +1012,11 @@ __global__ void k_ar_elem(const double* __restrict__ rho, const double* __restri
 #pragma unroll
       for (int i = 0; i < n; ++i) {
         double v = 0.0;
+        if constexpr (MID) v = tz[j][i];
+        else {
 #pragma unroll
-        for (int b = 0; b < mm; ++b) v = fma(T->M_P[j][b], tz[b][i], v);
+          for (int b = 0; b < mm; ++b) v = fma(T->M_P[j][b], tz[b][i], v);
+        }
         b2[j * n + i] = fma(v, v, b2[j * n + i]);
       }
   }
@@ -1194,11 +1210,10 @@ __global__ void __launch_bounds__(32) k_vel_prep(const double* __restrict__ rho,
   double* out = Psi + (size_t)kk * n2 * n2;
 #pragma unroll 1
   for (int q = 0; q < n2; ++q) {
-    const int i = q % n, j = q / n;
     double row[n2];
 #pragma unroll
     for (int al = 0; al < n2; ++al) {
-      double s = T->Leg[i][ia[al]] * T->Leg[j][ib[al]];
+      double s = T->Phi[q][al];
 #pragma unroll
       for (int b = 0; b < al; ++b) s = fma(-row[b], LS(tri(al, b)), s);
       row[al] = s * rdiag[al];
@@ -1263,6 +1278,9 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
   using C = VCfg<P>;
   constexpr int n = C::n, n2 = C::n2, EB = C::EB, TH = C::threads;
   constexpr int mm = KM + 1, mL = KM + 2;
+  // node families equal to the DG nodes (GLL(k+1) at k = p - 1, GLL(k) at
+  // k = p): their interpolation to the DG nodes is the identity, skipped
+  constexpr bool LID = mL == n, MID = mm == n;
   // 2D2V (R2): u_z = B_z = 0, so only u_x, u_y are filtered (u_z stays 0)
   constexpr int ND = R2 ? 2 : 3;
   __shared__ double sPsi[EB][n2 * n2];
@@ -1273,6 +1291,7 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
   __shared__ double sax[2][EB * n2];                       // |u_I| + |B|/sqrt(rho) per node
   __shared__ double ssig[EB][2 * n];
   __shared__ double sD[EB][n];
+  __shared__ double sH[EB][n];                             // (1 - D_l^2) / 2: heating factor of shell l
   __shared__ double slam[EB][2];
   const size_t N = (size_t)M.K * n2, Z = (size_t)M.K * mm * mm;
   const int tid = threadIdx.x, el = tid / n2, q = tid % n2;
@@ -1305,16 +1324,22 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
     double v = 0.0;
     if (w < mm * n) {
       const int b = w / n, ii = w % n;
+      if constexpr (LID) v = sB[e][b * mL + ii];
+      else {
 #pragma unroll
-      for (int a = 0; a < mL; ++a) v = fma(T->L_P[ii][a], sB[e][b * mL + a], v);
+        for (int a = 0; a < mL; ++a) v = fma(T->L_P[ii][a], sB[e][b * mL + a], v);
+      }
     } else if (w < mm * n + mL * n) {
       const int r = w - mm * n, b = r / n, ii = r % n;
 #pragma unroll
       for (int a = 0; a < mm; ++a) v = fma(T->G_P[ii][a], sB[e][mm * mL + b * mm + a], v);
     } else {
       const int r = w - mm * n - mL * n, b = r / n, ii = r % n;
+      if constexpr (MID) v = sB[e][2 * mm * mL + b * mm + ii];
+      else {
 #pragma unroll
-      for (int a = 0; a < mm; ++a) v = fma(T->M_P[ii][a], sB[e][2 * mm * mL + b * mm + a], v);
+        for (int a = 0; a < mm; ++a) v = fma(T->M_P[ii][a], sB[e][2 * mm * mL + b * mm + a], v);
+      }
     }
     sT[e][w] = v;
   }
@@ -1323,11 +1348,17 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
     double bx = 0.0, by = 0.0, bz = 0.0;
 #pragma unroll
     for (int b = 0; b < mm; ++b) bx = fma(T->G_P[j][b], sT[el][b * n + i], bx);
+    if constexpr (LID) by = sT[el][mm * n + j * n + i];
+    else {
 #pragma unroll
-    for (int b = 0; b < mL; ++b) by = fma(T->L_P[j][b], sT[el][mm * n + b * n + i], by);
+      for (int b = 0; b < mL; ++b) by = fma(T->L_P[j][b], sT[el][mm * n + b * n + i], by);
+    }
     if constexpr (!R2) {
+      if constexpr (MID) bz = sT[el][mm * n + mL * n + j * n + i];
+      else {
 #pragma unroll
-      for (int b = 0; b < mm; ++b) bz = fma(T->M_P[j][b], sT[el][mm * n + mL * n + b * n + i], bz);
+        for (int b = 0; b < mm; ++b) bz = fma(T->M_P[j][b], sT[el][mm * n + mL * n + b * n + i], bz);
+      }
     }
     const double va = sqrt(fma(bx, bx, fma(by, by, bz * bz)) * rcp(r_));
     sax[0][tid] = fabs(u[0]) + va;
@@ -1368,7 +1399,9 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
       for (int r = 0; r <= l; ++r) ss += ssig[e][I * n + r];
       Theta = fma(slam[e][I], ss, Theta);
     }
-    sD[e][l] = l == 0 ? 1.0 : exp(-s_tau * Theta);
+    const double Dl = l == 0 ? 1.0 : exp(-s_tau * Theta);
+    sD[e][l] = Dl;
+    sH[e][l] = 0.5 * (1.0 - Dl * Dl);
   }
   __syncthreads();
   if (frz && q < n && valid) frz[(size_t)k * n + q] = sD[el][q];
@@ -1392,9 +1425,8 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
         double wl = 0.0;
 #pragma unroll
         for (int al = l * l; al < (l + 1) * (l + 1); ++al) wl = fma(sc[d][el * n2 + al], sPsi[el][q * n2 + al], wl);
-        const double Dl = sD[el][l];
-        unew = fma(Dl, wl, unew);
-        if (l > 0) de = fma(0.5 * (1.0 - Dl * Dl) * wl, wl, de);
+        unew = fma(sD[el][l], wl, unew);
+        if (l > 0) de = fma(sH[el][l] * wl, wl, de);
       }
       Y[MHD_CHK((1 + d) * N + (size_t)k * n2 + q, 4 * N)] = unew;
     }

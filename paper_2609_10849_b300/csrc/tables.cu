@@ -292,6 +292,15 @@ void host_tables(int p, int k, Tab* T) {
       T->LegN2[j][b] = T->LegN[j] * T->LegN[b];
       for (int b2 = 0; b2 < n; ++b2) T->LegLeg[j][b][b2] = T->Leg[j][b] * T->Leg[j][b2];
     }
+  {
+    int sa[MHD_NMAX * MHD_NMAX], sb[MHD_NMAX * MHD_NMAX], t = 0;
+    for (int l = 0; l < n; ++l)
+      for (int b = 0; b <= l; ++b)
+        for (int a = 0; a <= l; ++a)
+          if ((a > b ? a : b) == l) { sa[t] = a; sb[t] = b; ++t; }
+    for (int q = 0; q < n * n; ++q)
+      for (int al = 0; al < n * n; ++al) T->Phi[q][al] = T->Leg[q % n][sa[al]] * T->Leg[q / n][sb[al]];
+  }
 }
 
 int table_slot(int p, int k) {
