@@ -161,15 +161,18 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads, HCfg<P, EBv>::min_block
     }
   }
   {
-    double ir = rcp(Us[0]);
-    double ux = Us[1] * ir, uy = Us[2] * ir, uz = Us[3] * ir;
-    double u2 = fma(ux, ux, fma(uy, uy, uz * uz));
-    double pr = (g - 1.0) * fma(-0.5 * Us[0], u2, Us[4]);
-    // halves: the pair means {{.}} become plain sums (scaling by 1/2 is exact)
-    sp[0][tid] = 0.5 * Us[0];
-    sp[1][tid] = 0.5 * ux; sp[2][tid] = 0.5 * uy; sp[3][tid] = 0.5 * uz;
-    sp[4][tid] = 0.5 * Us[0] * rcp(pr);
-    sp[5][tid] = 0.5 * u2;
+    // halves: the pair means {{.}} become plain sums.  Scaling by powers of 2
+    // is exact, so v = u/2 = m (1/(2 rho)), q = |v|^2 = |u|^2/4 and
+    // -2 rho q = -rho |u|^2 / 2 are the same doubles as the unscaled forms
+    const double hir = 0.5 * rcp(Us[0]);
+    const double vx = Us[1] * hir, vy = Us[2] * hir, vz = Us[3] * hir;
+    const double q4 = fma(vx, vx, fma(vy, vy, vz * vz));
+    const double pr = (g - 1.0) * fma(-2.0 * Us[0], q4, Us[4]);
+    const double hr = 0.5 * Us[0];
+    sp[0][tid] = hr;
+    sp[1][tid] = vx; sp[2][tid] = vy; sp[3][tid] = vz;
+    sp[4][tid] = hr * rcp(pr);
+    sp[5][tid] = 2.0 * q4;
   }
   __syncthreads();
   // per-node logarithms for the whole block, only if some element of it has a

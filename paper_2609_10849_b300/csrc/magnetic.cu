@@ -117,12 +117,14 @@ struct MD {
 #define SM(off, it) sm[(size_t)((off) + (it)) * D::EB + e]
 
 // ---- assembly of closure values from element loads ----------------------------
+// The sums of the element loads at a closure node (the *_sum helpers, in one
+// canonical order: south-west contribution first) and the assembled values
+// (sum times 1 / (Jdet times the assembled lumped weight)).
 // W-type closure node (a, b), a, b < mL, of element (ex, ey).
 template <int P, int KM>
-__device__ __forceinline__ double assemble_W(const double* __restrict__ Lz, int ex, int ey, int a, int b,
-                                             const Mesh& M, double iJ) {
+__device__ __forceinline__ double assemble_W_sum(const double* __restrict__ Lz, int ex, int ey, int a, int b,
+                                                 const Mesh& M) {
   using D = MD<P, KM>;
-  const MTab& T = c_mtab[D::SLOT];
   int ox = ex, oy = ey, ao = a, bo = b;
   if (a == D::mL - 1) { ox = wrap(ex + 1, M.nx); ao = 0; }
   if (b == D::mL - 1) { oy = wrap(ey + 1, M.ny); bo = 0; }
@@ -133,15 +135,22 @@ __device__ __forceinline__ double assemble_W(const double* __restrict__ Lz, int 
   if (bo == 0) v += Lz[MHD_CHK((size_t)(sy * M.nx + ox) * D::NW + (D::mL - 1) * D::mL + ao, KW)];
   if (ao == 0) v += Lz[MHD_CHK((size_t)(oy * M.nx + wx) * D::NW + bo * D::mL + (D::mL - 1), KW)];
   v += Lz[MHD_CHK((size_t)(oy * M.nx + ox) * D::NW + bo * D::mL + ao, KW)];
-  return v * (iJ * T.iW_LL[ao][bo]);
+  return v;
+}
+template <int P, int KM>
+__device__ __forceinline__ double assemble_W(const double* __restrict__ Lz, int ex, int ey, int a, int b,
+                                             const Mesh& M, double iJ) {
+  using D = MD<P, KM>;
+  const MTab& T = c_mtab[D::SLOT];
+  const int ao = a == D::mL - 1 ? 0 : a, bo = b == D::mL - 1 ? 0 : b;
+  return assemble_W_sum<P, KM>(Lz, ex, ey, a, b, M) * (iJ * T.iW_LL[ao][bo]);
 }
 
 // Y-type (N_x) closure node (a < mm, b < mL).
 template <int P, int KM>
-__device__ __forceinline__ double assemble_Nx(const double* __restrict__ Lx, int ex, int ey, int a, int b,
-                                              const Mesh& M, double iJ) {
+__device__ __forceinline__ double assemble_Nx_sum(const double* __restrict__ Lx, int ex, int ey, int a, int b,
+                                                  const Mesh& M) {
   using D = MD<P, KM>;
-  const MTab& T = c_mtab[D::SLOT];
   int oy = ey, bo = b;
   if (b == D::mL - 1) { oy = wrap(ey + 1, M.ny); bo = 0; }
   const int sy = wrap(oy - 1, M.ny);
@@ -149,15 +158,21 @@ __device__ __forceinline__ double assemble_Nx(const double* __restrict__ Lx, int
   const size_t KX = (size_t)M.K * D::NX;
   if (bo == 0) v += Lx[MHD_CHK((size_t)(sy * M.nx + ex) * D::NX + (D::mL - 1) * D::mm + a, KX)];
   v += Lx[MHD_CHK((size_t)(oy * M.nx + ex) * D::NX + bo * D::mm + a, KX)];
-  return v * (iJ * T.iW_GL[a][bo]);
+  return v;
+}
+template <int P, int KM>
+__device__ __forceinline__ double assemble_Nx(const double* __restrict__ Lx, int ex, int ey, int a, int b,
+                                              const Mesh& M, double iJ) {
+  using D = MD<P, KM>;
+  const MTab& T = c_mtab[D::SLOT];
+  return assemble_Nx_sum<P, KM>(Lx, ex, ey, a, b, M) * (iJ * T.iW_GL[a][b == D::mL - 1 ? 0 : b]);
 }
 
 // X-type (N_y) closure node (a < mL, b < mm).
 template <int P, int KM>
-__device__ __forceinline__ double assemble_Ny(const double* __restrict__ Ly, int ex, int ey, int a, int b,
-                                              const Mesh& M, double iJ) {
+__device__ __forceinline__ double assemble_Ny_sum(const double* __restrict__ Ly, int ex, int ey, int a, int b,
+                                                  const Mesh& M) {
   using D = MD<P, KM>;
-  const MTab& T = c_mtab[D::SLOT];
   int ox = ex, ao = a;
   if (a == D::mL - 1) { ox = wrap(ex + 1, M.nx); ao = 0; }
   const int wx = wrap(ox - 1, M.nx);
@@ -165,7 +180,42 @@ __device__ __forceinline__ double assemble_Ny(const double* __restrict__ Ly, int
   const size_t KY = (size_t)M.K * D::NY;
   if (ao == 0) v += Ly[MHD_CHK((size_t)(ey * M.nx + wx) * D::NY + b * D::mL + (D::mL - 1), KY)];
   v += Ly[MHD_CHK((size_t)(ey * M.nx + ox) * D::NY + b * D::mL + ao, KY)];
-  return v * (iJ * T.iW_LG[ao][b]);
+  return v;
+}
+template <int P, int KM>
+__device__ __forceinline__ double assemble_Ny(const double* __restrict__ Ly, int ex, int ey, int a, int b,
+                                              const Mesh& M, double iJ) {
+  using D = MD<P, KM>;
+  const MTab& T = c_mtab[D::SLOT];
+  return assemble_Ny_sum<P, KM>(Ly, ex, ey, a, b, M) * (iJ * T.iW_LG[a == D::mL - 1 ? 0 : a][b]);
+}
+
+// Per-block factors of the closure families in the order of their items
+// (N_x, then N_y, then W): the assembly factor 1 / (Jdet times the assembled
+// lumped weight), and (lumped) Jdet times the element's lumped weight.  Both
+// are the same doubles the per-item products would give.
+template <int P, int KM>
+__device__ __forceinline__ void closure_factors(double* __restrict__ af, double* __restrict__ pw, const Mesh& M) {
+  using D = MD<P, KM>;
+  const MTab& T = c_mtab[D::SLOT];
+  for (int t = threadIdx.x; t < D::NX + D::NY + D::NW; t += blockDim.x) {
+    double f, w;
+    if (t < D::NX) {
+      const int a = t % D::mm, b = t / D::mm;
+      f = M.iJ * T.iW_GL[a][b == D::mL - 1 ? 0 : b];
+      w = M.Jdet * T.W_GL[a][b];
+    } else if (t < D::NX + D::NY) {
+      const int r = t - D::NX, a = r % D::mL, b = r / D::mL;
+      f = M.iJ * T.iW_LG[a == D::mL - 1 ? 0 : a][b];
+      w = M.Jdet * T.W_LG[a][b];
+    } else {
+      const int r = t - D::NX - D::NY, a = r % D::mL, b = r / D::mL;
+      f = M.iJ * T.iW_LL[a == D::mL - 1 ? 0 : a][b == D::mL - 1 ? 0 : b];
+      w = M.Jdet * T.W_LL[a][b];
+    }
+    af[t] = f;
+    if (pw) pw[t] = w;
+  }
 }
 
 // B closure loads: Bx (X-type, [b < mm][a < mL]) and By (Y-type, [b < mL][a < mm]).
@@ -310,7 +360,11 @@ struct LE_ {  // per-element shared-memory offsets (doubles), with region reuse
   static constexpr int BXNX = UW + 2 * D::NW, BZNX = BXNX + D::NX, BYNY = BZNX + D::NX, BZNY = BYNY + D::NY;
   static constexpr int BXW = BZNY + D::NY, BZW = BXW + D::NW, RC_END = BZW + D::NW;
   static constexpr int TQ = RC, JQ = TQ + 3 * D::n * D::mL, RQ_END = JQ + 3 * D::n2;
-  static constexpr int SIZE = RC_END > RQ_END ? RC_END : RQ_END;
+  // per-block factors (closure_factors: 2 (NX + NY + NW) doubles, then the
+  // lumped DG-node masses Jdet w_i w_j) in slots after the per-element
+  // regions; at least 8 elements per block
+  static constexpr int FAC = RC_END > RQ_END ? RC_END : RQ_END;
+  static constexpr int SIZE = FAC + (2 * (D::NX + D::NY + D::NW) + D::n2 + 7) / 8;
 };
 
 // mode 0: write du, de (residual test hook); mode 1: SSP combination into (uo, eo);
@@ -329,19 +383,28 @@ __global__ void __launch_bounds__(256) k_mag_E(
   extern __shared__ double sm[];
   const int k0 = blockIdx.x * D::EB;
   const size_t N = (size_t)M.K * D::n2;
-  const double iJ = M.iJ;
+  static_assert(D::EB >= 8, "per-block factor slots assume at least 8 elements per block");
+  double* const sAF = sm + (size_t)O::FAC * D::EB;  // assembly factors [NX | NY | NW]
+  double* const sPW = sAF + D::NX + D::NY + D::NW;  // lumped weights Jdet w [NX | NY | NW]
+  double* const sMW = sPW + D::NX + D::NY + D::NW;  // DG-node masses Jdet w_i w_j [n2]
+  closure_factors<P, KM>(sAF, sPW, M);
+  for (int t = threadIdx.x; t < D::n2; t += blockDim.x) sMW[t] = M.Jdet * T.wp[t % D::n] * T.wp[t / D::n];
+  __syncthreads();
   // stage 1: J closure (assembled), B closure, eta (2D2V: J_z, B_x, B_y and eta only)
   constexpr int I1 = (R2 ? 0 : D::NX + D::NY) + D::NW + D::NY + D::NX + (R2 ? 0 : D::NZ) + 1;
   FLAT(I1) {
     int it = idx / D::EB, e = idx % D::EB, k = min(k0 + e, M.K - 1);
     int ex = k % M.nx, ey = k / M.nx;
     if constexpr (!R2) {
-      if (it < D::NX) { SM(O::JX, it) = assemble_Nx<P, KM>(LJx, ex, ey, it % D::mm, it / D::mm, M, iJ); continue; }
+      if (it < D::NX) { SM(O::JX, it) = assemble_Nx_sum<P, KM>(LJx, ex, ey, it % D::mm, it / D::mm, M) * sAF[it]; continue; }
       it -= D::NX;
-      if (it < D::NY) { SM(O::JY, it) = assemble_Ny<P, KM>(LJy, ex, ey, it % D::mL, it / D::mL, M, iJ); continue; }
+      if (it < D::NY) { SM(O::JY, it) = assemble_Ny_sum<P, KM>(LJy, ex, ey, it % D::mL, it / D::mL, M) * sAF[D::NX + it]; continue; }
       it -= D::NY;
     }
-    if (it < D::NW) { SM(O::JZ, it) = assemble_W<P, KM>(LJz, ex, ey, it % D::mL, it / D::mL, M, iJ); continue; }
+    if (it < D::NW) {
+      SM(O::JZ, it) = assemble_W_sum<P, KM>(LJz, ex, ey, it % D::mL, it / D::mL, M) * sAF[D::NX + D::NY + it];
+      continue;
+    }
     it -= D::NW;
     if (it < D::NY) { SM(O::BX, it) = closure_Bx<P, KM>(Bx, ex, ey, it % D::mL, it / D::mL, M); continue; }
     it -= D::NY;
@@ -489,8 +552,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
   FLAT(I4) {
     int it = idx / D::EB, e = idx % D::EB, k = k0 + e;
     if (!R2 && it < D::NX) {
-      int b = it / D::mm, a = it % D::mm;
-      double w = Jd * T.W_GL[a][b];
+      const double w = sPW[it];
       double by_ = SM(O::BY, it), bz_ = SM(O::BZNX, it), jx_ = SM(O::JX, it);
       double uy = SM(O::UNX, it), uz = SM(O::UNX, D::NX + it);
       if (k < M.K) LEx[MHD_CHK((size_t)k * D::NX + it, (size_t)M.K * D::NX)] = w * fma(uz, by_, -uy * bz_);
@@ -499,8 +561,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
       SM(O::UNX, D::NX + it) = wj * by_;  // s_z contribution
     } else if (!R2 && it < D::NX + D::NY) {
       it -= D::NX;
-      int b = it / D::mL, a = it % D::mL;
-      double w = Jd * T.W_LG[a][b];
+      const double w = sPW[D::NX + it];
       double bx_ = SM(O::BX, it), bz_ = SM(O::BZNY, it), jy_ = SM(O::JY, it);
       double ux = SM(O::UNY, it), uz = SM(O::UNY, D::NY + it);
       if (k < M.K) LEy[MHD_CHK((size_t)k * D::NY + it, (size_t)M.K * D::NY)] = w * fma(ux, bz_, -uz * bx_);
@@ -509,8 +570,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
       SM(O::UNY, D::NY + it) = -wj * bx_;  // s_z
     } else {
       if constexpr (!R2) it -= D::NX + D::NY;
-      int b = it / D::mL, a = it % D::mL;
-      double w = Jd * T.W_LL[a][b];
+      const double w = sPW[D::NX + D::NY + it];
       double bx_ = SM(O::BXW, it), by_ = SM(O::BYL, it), jz_ = SM(O::JZ, it);
       double ux = SM(O::UW, it), uy = SM(O::UW, D::NW + it);
       if (k < M.K) LEz[MHD_CHK((size_t)k * D::NW + it, (size_t)M.K * D::NW)] = w * fma(uy, bx_, -ux * by_);
@@ -758,7 +818,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
       continue;
     }
     double r_ = rho[gq];
-    double im = rcp(r_ * Jd * T.wp[i] * T.wp[j]);
+    double im = rcp(r_ * sMW[q]);
     double du[3] = {sx * im, sy * im, sz * im};
     double de = 0.0;
     const double et = SM(O::ETA, 0);
@@ -789,7 +849,9 @@ struct LB_ {
   static constexpr int EX = 0, EY = EX + D::NX, EZ = EY + D::NY;
   static constexpr int TY = EZ + D::NW;          // d/dx of E_y rows at GLL(k) x: [b < mm][a < mm]
   static constexpr int TX = TY + D::NZ;          // E_x rows (GLL y) to GLL(k) x: [b < mL][a < mm]
-  static constexpr int SIZE = TX + D::mL * D::mm;
+  // per-block assembly factors (closure_factors: NX + NY + NW doubles), at least 8 elements per block
+  static constexpr int FAC = TX + D::mL * D::mm;
+  static constexpr int SIZE = FAC + (D::NX + D::NY + D::NW + 7) / 8;
 };
 
 // mode 0: write dB; mode 1: SSP combination into Bo.
@@ -803,17 +865,21 @@ __global__ void __launch_bounds__(256) k_mag_B(const double* __restrict__ LEx, c
   const MTab& T = c_mtab[D::SLOT];
   extern __shared__ double sm[];
   const int k0 = blockIdx.x * D::EB;
-  const double iJ = M.iJ;
   const size_t Z = (size_t)M.K * D::NZ;
+  static_assert(D::EB >= 8, "per-block factor slots assume at least 8 elements per block");
+  double* const sAF = sm + (size_t)O::FAC * D::EB;  // assembly factors [NX | NY | NW]
+  closure_factors<P, KM>(sAF, nullptr, M);
+  __syncthreads();
   // 2D2V (R2): E_x = E_y = 0, so only E_z is assembled and dB_z = 0
   constexpr int I1 = (R2 ? 0 : D::NX + D::NY) + D::NW;
   FLAT(I1) {
     int it = idx / D::EB, e = idx % D::EB, k = min(k0 + e, M.K - 1);
     int ex = k % M.nx, ey = k / M.nx;
     if constexpr (R2) it += D::NX + D::NY;
-    if (it < D::NX) SM(O::EX, it) = assemble_Nx<P, KM>(LEx, ex, ey, it % D::mm, it / D::mm, M, iJ);
-    else if (it < D::NX + D::NY) { it -= D::NX; SM(O::EY, it) = assemble_Ny<P, KM>(LEy, ex, ey, it % D::mL, it / D::mL, M, iJ); }
-    else { it -= D::NX + D::NY; SM(O::EZ, it) = assemble_W<P, KM>(LEz, ex, ey, it % D::mL, it / D::mL, M, iJ); }
+    const double f = sAF[it];
+    if (it < D::NX) SM(O::EX, it) = assemble_Nx_sum<P, KM>(LEx, ex, ey, it % D::mm, it / D::mm, M) * f;
+    else if (it < D::NX + D::NY) { it -= D::NX; SM(O::EY, it) = assemble_Ny_sum<P, KM>(LEy, ex, ey, it % D::mL, it / D::mL, M) * f; }
+    else { it -= D::NX + D::NY; SM(O::EZ, it) = assemble_W_sum<P, KM>(LEz, ex, ey, it % D::mL, it / D::mL, M) * f; }
   }
   __syncthreads();
   constexpr int I2 = R2 ? 0 : D::NZ + D::mL * D::mm;

@@ -1293,6 +1293,7 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
   __shared__ double sD[EB][n];
   __shared__ double sH[EB][n];                             // (1 - D_l^2) / 2: heating factor of shell l
   __shared__ double slam[EB][2];
+  __shared__ double sMw[n2];                               // Jdet w_i w_j of the DG nodes
   const size_t N = (size_t)M.K * n2, Z = (size_t)M.K * mm * mm;
   const int tid = threadIdx.x, el = tid / n2, q = tid % n2;
   const int k0 = blockIdx.x * EB;
@@ -1305,6 +1306,7 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
   for (int d = 0; d < ND; ++d) u[d] = Y[MHD_CHK((1 + d) * N + (size_t)kk * n2 + q, 4 * N)];
   const double r_ = rho[MHD_CHK((size_t)kk * n2 + q, N)];
   for (int t = q; t < n2 * n2; t += n2) sPsi[el][t] = Psi[MHD_CHK((size_t)kk * n2 * n2 + t, (size_t)M.K * n2 * n2)];
+  if (tid < n2) sMw[tid] = M.Jdet * T->wp[tid % n] * T->wp[tid / n];
   // closures of B (Bx [b < mm][a < mL], By [b < mL][a < mm], Bz [b][a]) of the block's elements
   constexpr int NB = mm * mL + mL * mm + (R2 ? 0 : mm * mm);
   for (int it = tid; it < EB * NB; it += TH) {
@@ -1364,7 +1366,7 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
     sax[0][tid] = fabs(u[0]) + va;
     sax[1][tid] = fabs(u[1]) + va;
   }
-  const double W = M.Jdet * T->wp[i] * T->wp[j] * r_;
+  const double W = sMw[q] * r_;
 #pragma unroll
   for (int d = 0; d < ND; ++d) sWu[d][tid] = W * u[d];
   __syncthreads();
