@@ -166,10 +166,13 @@ def step_work(p, k):
     # output and the face fluxes of the element's own faces
     work["vol"] = (6 * vol_flops_per_element_minimal(p), 2 * (8 * 5 * n2 + 3 * 2 * 5 * n) * d8)
     # hydro OE + limiter per stage: statistics of 5 fields, the rate (20), the
-    # sensor (2 n sigma items) and factors (n exponentials), the modal transform
-    # there and back (4 sum-factorised passes: 2 n^3 FMAs per component), the
-    # limiter (~35 per node: average, pressures, scalings)
-    oe = 20 + 2 * n * (5 + 2) + n * (2 * n + 3) + 5 * 4 * n2 * n * 2 + 35 * n2
+    # sensor (2 n sigma items) and factors (n exponentials), the damping as
+    # three sum-factorised passes per component (forward y, the x-filter of
+    # each y-mode, backward y: 2 n^3 FMAs each) after building the x-filters
+    # once per element (n^3 (n+1) / 2 FMAs), the limiter (~35 per node:
+    # average, pressures, scalings)
+    oe = (20 + 2 * n * (5 + 2) + n * (2 * n + 3) + 5 * 3 * n2 * n * 2 + 2 * (n ** 3 * (n + 1) // 2)
+          + 35 * n2)
     work["stab_hydro"] = (6 * (stats_flops(p, 5) + oe), 6 * 3 * 5 * n2 * d8)
     # nodal exchange (u = m/rho, e; and back): ~10 flops per node each way
     work["exchange"] = (2 * 10 * n2, (5 + 4 + 4 + 1 + 5) * n2 * d8)

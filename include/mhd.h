@@ -369,6 +369,16 @@ int mhd_fp64_peak(double* tflops);
  * [2^-1000, 2^1000].  Errors: MHD_EINVAL, MHD_ECUDA. */
 int mhd_rcp_check(const double* x, double* y, long long n, void* stream);
 
+/* Test hook (no counterpart in the paper): y[i] = the square root the kernels
+ * use for sound speeds, Alfven speeds and the sensor's face-jump norms, for
+ * n device doubles x (asynchronous on `stream`; x and y device pointers of n
+ * doubles each, owned by the caller).  It is Heron's iteration seeded by the
+ * PTX approximation rsqrt.approx.ftz.f64 (two steps, each one FMA residual),
+ * within 1 ulp of IEEE sqrt for normal x >= 0; zero, subnormal, infinite and
+ * NaN inputs follow IEEE sqrt, negative ones give NaN.  Errors: MHD_EINVAL,
+ * MHD_ECUDA. */
+int mhd_sqrt_check(const double* x, double* y, long long n, void* stream);
+
 /* Debug build only (no counterpart in the paper; libmhd_debug.so, compiled
  * with MHD_BOUNDS_CHECK): the number of out-of-range global-memory indices the
  * checked kernels met since the last reset (each such access was redirected

@@ -79,8 +79,8 @@ __device__ __forceinline__ void llf_flux_dev(int d, const double* Um, const doub
   double udm = Um[1 + d] * im, udp = Up[1 + d] * ip;
   double pm = (g - 1.0) * (Um[4] - 0.5 * (Um[1] * Um[1] + Um[2] * Um[2] + Um[3] * Um[3]) * im);
   double pp = (g - 1.0) * (Up[4] - 0.5 * (Up[1] * Up[1] + Up[2] * Up[2] + Up[3] * Up[3]) * ip);
-  double sm = fabs(udm) + sqrt(g * pm * im);
-  double sp = fabs(udp) + sqrt(g * pp * ip);
+  double sm = fabs(udm) + fsqrt(g * pm * im);
+  double sp = fabs(udp) + fsqrt(g * pp * ip);
   double lam = fmax(sm, sp);
   double Fm[5], Fp[5];
   Fm[0] = Um[1 + d]; Fp[0] = Up[1 + d];

@@ -63,11 +63,15 @@ struct Tab {
   double hwp[MHD_NMAX];                       // 0.5 wp_i
   // products of two entries that inner loops would otherwise form per iteration
   double WLeg[MHD_NMAX][MHD_NMAX];            // wp_j P_b(xp_j): [j][b]
-  double LegN2[MHD_NMAX][MHD_NMAX];           // LegN_a LegN_b
   double LegLeg[MHD_NMAX][MHD_NMAX][MHD_NMAX];  // P_b(xp_j) P_b2(xp_j): [j][b][b2]
   // the modal basis at the nodes, P_a(xp_i) P_b(xp_j) at node q = j (p+1) + i, basis
   // index alpha in shell order (shell l = max(a, b) holds alpha in [l^2, (l+1)^2))
   double Phi[MHD_NMAX * MHD_NMAX][MHD_NMAX * MHD_NMAX];
+  // the x-direction filter of y-mode b of the hydro OE map (sum-factorised):
+  // K_b[i][i'] = sum_a D_max(a,b) N_b R_a[i][i'], R_a[i][i'] = N_a P_a(xp_i) wp_i' P_a(xp_i'),
+  // split as D_b OES[b] + sum_{a > b} D_a OEQ[b][a] (host sums in long double, rounded once)
+  double OES[MHD_NMAX][MHD_NMAX][MHD_NMAX];              // [b][i][i'] = N_b sum_{a <= b} R_a[i][i']
+  double OEQ[MHD_NMAX][MHD_NMAX][MHD_NMAX][MHD_NMAX];    // [b][a][i][i'] = N_b R_a[i][i']
 };
 
 // Device copy of the tables of the 8 supported (p, k) pairs.
@@ -189,6 +193,26 @@ __device__ __forceinline__ double rcp(double x) {
   double e = fma(-x, r, 1.0);
   double t = fma(e, e, e);
   return fma(r, t, r);
+}
+
+// ---- fast FP64 square root ----------------------------------------------------
+// Heron's (Newton's) iteration for the root, s <- s + (x - s^2) / (2 s), with the
+// reciprocal 1/(2 s) taken from the documented PTX seed rsqrt.approx.ftz.f64,
+// y ~ x^-1/2 with relative error e << 2^-20, and never refined:
+//   s0 = x y = sqrt(x)(1 + e),  s1 = s0 + (x - s0^2) y/2 = sqrt(x)(1 - e^2),
+//   s2 = s1 + (x - s1^2) y/2 = sqrt(x)(1 + e^3)  (then one rounding).
+// The residuals are single FMAs.  Zero returns itself; subnormal, infinite and
+// NaN inputs (which the flushing seed does not cover) take IEEE sqrt; a
+// negative normal input gives NaN, as sqrt does.
+__device__ __forceinline__ double fsqrt(double x) {
+  const unsigned long long a = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+  if (a - 0x0010000000000000ULL >= 0x7fe0000000000000ULL) return a == 0 ? x : sqrt(x);
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double h = 0.5 * y;
+  const double s0 = x * y;
+  const double s1 = fma(fma(-s0, s0, x), h, s0);
+  return fma(fma(-s1, s1, x), h, s1);
 }
 
 // ---- order-preserving integer keys of doubles ---------------------------------

@@ -403,6 +403,10 @@ __global__ void k_rcp_check(const double* __restrict__ x, double* __restrict__ y
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = rcp(x[i]);
 }
+__global__ void k_sqrt_check(const double* __restrict__ x, double* __restrict__ y, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = fsqrt(x[i]);
+}
 }  // namespace mhd
 
 extern "C" int mhd_rcp_check(const double* x, double* y, long long n, void* stream) {
@@ -418,6 +422,27 @@ extern "C" int mhd_rcp_check(const double* x, double* y, long long n, void* stre
     return -1;
   }
   mhd::k_rcp_check<<<(unsigned)blocks, th, 0, (cudaStream_t)stream>>>(x, y, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    mhd::set_error_message(cudaGetErrorString(e));
+    return -3;
+  }
+  return 0;
+}
+
+extern "C" int mhd_sqrt_check(const double* x, double* y, long long n, void* stream) {
+  if (!x || !y || n < 0) {
+    mhd::set_error_message("null argument or negative length");
+    return -1;
+  }
+  if (n == 0) return 0;
+  const int th = 256;
+  const long long blocks = (n + th - 1) / th;
+  if (blocks > 0x7fffffffLL) {
+    mhd::set_error_message("length too large for one launch");
+    return -1;
+  }
+  mhd::k_sqrt_check<<<(unsigned)blocks, th, 0, (cudaStream_t)stream>>>(x, y, n);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     mhd::set_error_message(cudaGetErrorString(e));

@@ -143,7 +143,7 @@ __device__ __forceinline__ void face_jumps(const double* __restrict__ f, int k, 
     }
   }
 #pragma unroll
-  for (int r = 0; r < n; ++r) out[MHD_CHK(((size_t)c * n + r) * K + k, 5 * n * K)] = sqrt(acc[r]);
+  for (int r = 0; r < n; ++r) out[MHD_CHK(((size_t)c * n + r) * K + k, 5 * n * K)] = fsqrt(acc[r]);
 }
 
 template <int P>
@@ -387,6 +387,10 @@ __global__ void __launch_bounds__(PCfg<P>::threads) k_oe_pp(double* __restrict__
   constexpr int n = C::n, n2 = C::n2, EB = C::EB, TH = C::threads;
   __shared__ double su[5][EB * n2];
   __shared__ double st[5][EB * n2];
+  // x-filter rows K_b[i][.] of node (i, b): row stride n + 1 and element stride
+  // n2 (n + 1) + 1 (odd), so neither the per-element writes nor the row reads collide in banks
+  constexpr int KS = n2 * (n + 1) + 1;
+  __shared__ double sK[EB * KS];
   __shared__ double ssig[EB][2 * n];
   __shared__ double sD[EB][n];
   __shared__ double slam[EB][2];
@@ -414,7 +418,7 @@ __global__ void __launch_bounds__(PCfg<P>::threads) k_oe_pp(double* __restrict__
                    a4 = V.avg[4 * K + ke];
       const double ir = rcp(a0);
       const double pb = (g - 1.0) * fma(-0.5 * ir, fma(a1, a1, fma(a2, a2, a3 * a3)), a4);
-      const double cb = sqrt(g * pb * ir);
+      const double cb = fsqrt(g * pb * ir);
       slam[e][0] = (2.0 * P + 1.0) * (fabs(a1 * ir) + cb) * M.ihx;
       slam[e][1] = (2.0 * P + 1.0) * (fabs(a2 * ir) + cb) * M.ihy;
     }
@@ -453,28 +457,29 @@ __global__ void __launch_bounds__(PCfg<P>::threads) k_oe_pp(double* __restrict__
         st[c][tid] = v;
       }
     }
+    // the x-direction filter of every y-mode b, once per element and shared by
+    // the five fields: K_b[i][i'] = sum_a D_max(a,b) N_a N_b P_a(x_i) w_i' P_a(x_i')
+    // (forward x-transform, damping and backward x-transform in one n x n matrix);
+    // items (b, i, i') element-fastest, so a warp's items share b and its cost
+    for (int it = tid; it < EB * n * n2; it += TH) {
+      const int e = it % EB, w = it / EB, b = w / n2, r = w % n2, ii = r / n, i2 = r % n;
+      double v = sD[e][b] * T->OES[b][ii][i2];
+      for (int a = b + 1; a < n; ++a) v = fma(sD[e][a], T->OEQ[b][a][ii][i2], v);
+      sK[e * KS + (b * n + ii) * (n + 1) + i2] = v;
+    }
     __syncthreads();
-    {  // coef[b][a] = N_a N_b sum_i w_i P_a(x_i) T[b][i], damped by D_max(a,b)   (a = i, b = j)
-      const double f = T->LegN2[i][j] * sD[el][i > j ? i : j];
-      double wl[n];
+    // V[b][i] = sum_i' K_b[i][i'] T[b][i']   (b = j of this thread)
+    {
+      double kr[n];
 #pragma unroll
-      for (int ii = 0; ii < n; ++ii) wl[ii] = f * T->WLeg[ii][i];
+      for (int i2 = 0; i2 < n; ++i2) kr[i2] = sK[el * KS + (j * n + i) * (n + 1) + i2];
 #pragma unroll
       for (int c = 0; c < 5; ++c) {
         double v = 0.0;
 #pragma unroll
-        for (int ii = 0; ii < n; ++ii) v = fma(wl[ii], st[c][el * n2 + j * n + ii], v);
+        for (int i2 = 0; i2 < n; ++i2) v = fma(kr[i2], st[c][el * n2 + j * n + i2], v);
         su[c][tid] = v;
       }
-    }
-    __syncthreads();
-    // V[b][i] = sum_a P_a(x_i) coef[b][a]
-#pragma unroll
-    for (int c = 0; c < 5; ++c) {
-      double v = 0.0;
-#pragma unroll
-      for (int a = 0; a < n; ++a) v = fma(T->Leg[i][a], su[c][el * n2 + j * n + a], v);
-      st[c][tid] = v;
     }
     __syncthreads();
     // U[j][i] = sum_b P_b(x_j) V[b][i]
@@ -482,7 +487,7 @@ __global__ void __launch_bounds__(PCfg<P>::threads) k_oe_pp(double* __restrict__
     for (int c = 0; c < 5; ++c) {
       double v = 0.0;
 #pragma unroll
-      for (int b = 0; b < n; ++b) v = fma(T->Leg[j][b], st[c][el * n2 + b * n + i], v);
+      for (int b = 0; b < n; ++b) v = fma(T->Leg[j][b], su[c][el * n2 + b * n + i], v);
       u[c] = v;
     }
     __syncthreads();  // su and st are reused below
@@ -899,7 +904,7 @@ __global__ void k_ar_elem(const double* __restrict__ rho, const double* __restri
       accy = fma(0.5 * T->w2[t] * jy, jy, accy);
       accz = fma(0.5 * T->w2[t] * jz, jz, accz);
     }
-    out[9] = sqrt(accy); out[10] = sqrt(accz);
+    out[9] = fsqrt(accy); out[10] = fsqrt(accz);
   }
   {  // y-face (I = 1): B_x and B_z of this element at y = -1 and of the -y neighbour at y = +1
     const int eyA = wrap(ey - 1, M.ny);
@@ -937,7 +942,7 @@ __global__ void k_ar_elem(const double* __restrict__ rho, const double* __restri
       accx = fma(0.5 * T->w2[t] * jx, jx, accx);
       accz = fma(0.5 * T->w2[t] * jz, jz, accz);
     }
-    out[11] = sqrt(accx); out[12] = sqrt(accz);
+    out[11] = fsqrt(accx); out[12] = fsqrt(accz);
   }
   // a_{I,K} = max over DG nodes of |u_I| + |B_h| / sqrt(rho): B at the nodes
   // sum-factorised (x-pass, then y-pass: the order of the single-point tensor
@@ -1024,7 +1029,7 @@ __global__ void k_ar_elem(const double* __restrict__ rho, const double* __restri
 #pragma unroll
   for (int q = 0; q < n2; ++q) {
     const size_t gq = MHD_CHK((size_t)k * n2 + q, N);
-    const double va = sqrt(b2[q] * rcp(rho[gq]));  // |B_h| / sqrt(rho)
+    const double va = fsqrt(b2[q] * rcp(rho[gq]));  // |B_h| / sqrt(rho)
     ax = fmax(ax, fabs(Y[N + gq]) + va);
     ay = fmax(ay, fabs(Y[2 * N + gq]) + va);
   }
@@ -1198,7 +1203,7 @@ __global__ void __launch_bounds__(32) k_vel_prep(const double* __restrict__ rho,
 #pragma unroll
       for (int t = 0; t < c; ++t) s = fma(-LS(tri(r, t)), LS(tri(c, t)), s);
       if (r == c) {
-        const double d = sqrt(s);
+        const double d = fsqrt(s);
         LS(tri(r, r)) = d;
         rdiag[r] = rcp(d);
       } else {
@@ -1362,7 +1367,7 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
         for (int b = 0; b < mm; ++b) bz = fma(T->M_P[j][b], sT[el][mm * n + mL * n + b * n + i], bz);
       }
     }
-    const double va = sqrt(fma(bx, bx, fma(by, by, bz * bz)) * rcp(r_));
+    const double va = fsqrt(fma(bx, bx, fma(by, by, bz * bz)) * rcp(r_));
     sax[0][tid] = fabs(u[0]) + va;
     sax[1][tid] = fabs(u[1]) + va;
   }

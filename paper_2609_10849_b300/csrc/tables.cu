@@ -289,7 +289,6 @@ void host_tables(int p, int k, Tab* T) {
   for (int j = 0; j < n; ++j)
     for (int b = 0; b < n; ++b) {
       T->WLeg[j][b] = T->wp[j] * T->Leg[j][b];
-      T->LegN2[j][b] = T->LegN[j] * T->LegN[b];
       for (int b2 = 0; b2 < n; ++b2) T->LegLeg[j][b][b2] = T->Leg[j][b] * T->Leg[j][b2];
     }
   {
@@ -300,6 +299,35 @@ void host_tables(int p, int k, Tab* T) {
           if ((a > b ? a : b) == l) { sa[t] = a; sb[t] = b; ++t; }
     for (int q = 0; q < n * n; ++q)
       for (int al = 0; al < n * n; ++al) T->Phi[q][al] = T->Leg[q % n][sa[al]] * T->Leg[q / n][sb[al]];
+  }
+  {
+    ld Pl[MHD_NMAX][MHD_NMAX], Nl[MHD_NMAX];  // P_a(xp_i) and N_a in long double
+    for (int i = 0; i < n; ++i) {
+      ld P0 = 1.0L, P1 = xp[i];
+      Pl[i][0] = 1.0L;
+      if (n > 1) Pl[i][1] = P1;
+      for (int a = 2; a < n; ++a) {
+        ld P2 = ((2 * a - 1) * xp[i] * P1 - (a - 1) * P0) / a;
+        Pl[i][a] = P2;
+        P0 = P1; P1 = P2;
+      }
+    }
+    for (int a = 0; a < n; ++a) {
+      ld s = 0.0L;
+      for (int i = 0; i < n; ++i) s += wp[i] * Pl[i][a] * Pl[i][a];
+      Nl[a] = 1.0L / s;
+    }
+    for (int b = 0; b < n; ++b)
+      for (int i = 0; i < n; ++i)
+        for (int i2 = 0; i2 < n; ++i2) {
+          ld acc = 0.0L;
+          for (int a = 0; a < n; ++a) {
+            const ld R = Nl[b] * Nl[a] * Pl[i][a] * wp[i2] * Pl[i2][a];
+            if (a <= b) acc += R;
+            else T->OEQ[b][a][i][i2] = (double)R;
+          }
+          T->OES[b][i][i2] = (double)acc;
+        }
   }
 }
 

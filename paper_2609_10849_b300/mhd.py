@@ -74,6 +74,7 @@ _SIGS = {
     "mhd_mag_rhs": (C.c_int, [C.c_void_p] + [C.c_void_p] * 12 + [C.c_int]),
     "mhd_hydro_stage_map": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_int]),
     "mhd_rcp_check": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
+    "mhd_sqrt_check": (C.c_int, [C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p]),
     "mhd_diagnostics": (C.c_int, [C.c_void_p, C.POINTER(Diag)]),
     "mhd_get_eta": (C.c_int, [C.c_void_p, C.c_void_p]),
     "mhd_launch_count": (C.c_longlong, [C.c_void_p]),
@@ -161,6 +162,16 @@ def rcp_check(x, y, stream=0):
     if x.numel() != y.numel() or x.device != y.device:
         raise ValueError("x and y must have equal size and device")
     _check(lib().mhd_rcp_check(C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.numel(), C.c_void_p(stream)))
+
+
+def sqrt_check(x, y, stream=0):
+    """y = the library's FP64 square root of the CUDA tensor x (test hook)."""
+    for t in (x, y):
+        if not (t.is_cuda and str(t.dtype) == "torch.float64" and t.is_contiguous()):
+            raise ValueError("x and y must be contiguous float64 CUDA tensors")
+    if x.numel() != y.numel() or x.device != y.device:
+        raise ValueError("x and y must have equal size and device")
+    _check(lib().mhd_sqrt_check(C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.numel(), C.c_void_p(stream)))
 
 
 def _static_args(nx, ny, p, U, L):
