@@ -48,9 +48,9 @@ WORKLOADS = {"blast": ("blast", 1024), "orszag_tang": ("orszag_tang", 256)}
 # class, from the ncu captures of the current kernels on the 256 x 256 blast
 # (profiles/kernels_blast_256_full.md: 65,536 elements; traffic grows in
 # proportion to the elements, so it is scaled by K).  stab_hydro: k_stats
-# (45.074 MB) + k_oe_pp (61.887 MB); k_lines and k_global move a few KB.
-# vol: k_vol (69.986 MB).  Remove an entry whenever its kernels change.
-NCU_TRAFFIC_BYTES_PER_ELEMENT = {"stab_hydro": (45074432 + 61887232) / 65536, "vol": 69986304 / 65536}
+# (45.368 MB) + k_oe_pp (61.970 MB); k_lines and k_global move a few KB.
+# vol: k_vol (69.970 MB).  Remove an entry whenever its kernels change.
+NCU_TRAFFIC_BYTES_PER_ELEMENT = {"stab_hydro": (45367552 + 61970176) / 65536, "vol": (63017728 + 6952448) / 65536}
 
 
 def workload_config(stab, name="orszag_tang", mesh=None):

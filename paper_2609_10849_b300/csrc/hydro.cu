@@ -4,8 +4,8 @@
 //
 // Work mapping (FP64-issue bound part: every warp lane carries FP64 work):
 //   k_face  one thread per face node: LLF flux (eq. euler-lf-flux) on every
-//           x- and y-face, stored once per face: Fs[c][K][n], indexed by the
-//           element on the + side of the face.
+//           x- and y-face, stored once per face as 2 F*: Fs[c][K][n], indexed
+//           by the element on the + side of the face.
 //   k_vol   EB elements x (p+1)^2 threads per block; the p(p+1)^2 unique
 //           entropy-conservative pairs of an element (eq.
 //           euler-chandrashekar-flux) are spread p per thread and evaluated
@@ -24,9 +24,12 @@ struct HCfg {
   static constexpr int npl = n * (n - 1) / 2;  // pairs per line
   static constexpr int EB = EBv;               // elements per CTA (autotuned variant)
   static constexpr int threads = EB * n2;
-  // at least 32 resident warps per SM (registers <= 64): the pair and gather
-  // phases wait on shared-memory loads and reciprocal seeds, which more warps hide
-  static constexpr int min_blocks = 1024 / threads > 0 ? 1024 / threads : 1;
+  // resident warps per SM: the pair and gather phases wait on shared-memory
+  // loads and reciprocal seeds, which more warps hide.  40 at p = 1 and p = 3
+  // (48 registers, no spills; shared memory allows 36 at p = 3 with 8 elements
+  // per CTA), 32 at p = 2 and p = 4, where 48 registers would spill
+  static constexpr int warps_target = (P == 1 || P == 3) ? 40 : 32;
+  static constexpr int min_blocks = warps_target * 32 / threads > 0 ? warps_target * 32 / threads : 1;
 };
 
 // Pairs (a, b), a < b, ordered so that the first n(n-1)/2 use only nodes < n.
@@ -74,7 +77,9 @@ __device__ __forceinline__ bool far_from_reference(double x, double r) {
   return d >= lim || d <= -lim;
 }
 
-__device__ __forceinline__ void llf_flux_dev(int d, const double* Um, const double* Up, double g, double* F) {
+// Twice the LLF flux, 2 F* = F(U-) + F(U+) - lam (U+ - U-) (the factor 1/2 is
+// carried by the volume kernel's end-node coefficient).
+__device__ __forceinline__ void llf_flux2_dev(int d, const double* Um, const double* Up, double g, double* F) {
   double im = rcp(Um[0]), ip = rcp(Up[0]);
   double udm = Um[1 + d] * im, udp = Up[1 + d] * ip;
   double pm = (g - 1.0) * (Um[4] - 0.5 * (Um[1] * Um[1] + Um[2] * Um[2] + Um[3] * Um[3]) * im);
@@ -89,7 +94,7 @@ __device__ __forceinline__ void llf_flux_dev(int d, const double* Um, const doub
   Fm[3] = Um[3] * udm; Fp[3] = Up[3] * udp;
   Fm[4] = (Um[4] + pm) * udm; Fp[4] = (Up[4] + pp) * udp;
 #pragma unroll
-  for (int c = 0; c < 5; ++c) F[c] = 0.5 * (Fm[c] + Fp[c]) - 0.5 * lam * (Up[c] - Um[c]);
+  for (int c = 0; c < 5; ++c) F[c] = fma(-lam, Up[c] - Um[c], Fm[c] + Fp[c]);
 }
 
 template <int P>
@@ -113,7 +118,7 @@ __global__ void __launch_bounds__(256) k_face(const double* __restrict__ S, doub
     Um[c] = S[MHD_CHK(c * N + (size_t)km * n2 + qm, 5 * N)];
     Up[c] = S[MHD_CHK(c * N + (size_t)k * n2 + qp, 5 * N)];
   }
-  llf_flux_dev(d, Um, Up, M.g, F);
+  llf_flux2_dev(d, Um, Up, M.g, F);
   double* out = d ? Fy : Fx;
 #pragma unroll
   for (int c = 0; c < 5; ++c) out[MHD_CHK(c * nf + r, 5 * nf)] = F[c];
@@ -135,7 +140,7 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads, HCfg<P, EBv>::min_block
   __shared__ double sf[5][EB * NP];           // pair fluxes
   __shared__ double savg[5][EB];
   __shared__ double sDs[2][n2];               // s (-4/h_I) D: the gather rows of both directions, scaled
-  __shared__ double sFs[2];                   // s (2/h_I) / w_0: the end-node coefficients, scaled
+  __shared__ double sFs[2];                   // s (1/h_I) / w_0: the end-node coefficients of 2 F*, scaled
   const size_t N = (size_t)M.K * n2;
   const int tid = threadIdx.x;
   const int el = tid / n2, q = tid % n2;
@@ -157,7 +162,7 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads, HCfg<P, EBv>::min_block
     const double sx = -4.0 * M.ihx * sc, sy = -4.0 * M.ihy * sc;
     for (int t = tid; t < 2 * n2 + 2; t += EB * n2) {
       if (t < 2 * n2) sDs[t / n2][t % n2] = T->D[(t % n2) / n][t % n] * (t < n2 ? sx : sy);
-      else sFs[t - 2 * n2] = (t == 2 * n2 ? 2.0 * M.ihx : 2.0 * M.ihy) * w0i * sc;
+      else sFs[t - 2 * n2] = (t == 2 * n2 ? M.ihx : M.ihy) * w0i * sc;  // (2/h) / w_0 times F* = (1/h) / w_0 times 2 F*
     }
   }
   {
@@ -245,9 +250,9 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads, HCfg<P, EBv>::min_block
   }
   const int ex = kk % M.nx, ey = kk / M.nx;
   const size_t nf = (size_t)M.K * n;
-  // face terms as one FMA per direction in every lane: the coefficient is
-  // +-2/(h w_0) on the end nodes and 0 inside (0 * F* adds an exact zero), so
-  // no lane-divergent block is issued
+  // face terms as one FMA per direction in every lane: the coefficient of 2 F*
+  // is +-1/(h w_0) on the end nodes and 0 inside (0 * F* adds an exact zero),
+  // so no lane-divergent block is issued
   const double cfx = i == 0 ? sFs[0] : (i == P ? -sFs[0] : 0.0);
   const double cfy = j == 0 ? sFs[1] : (j == P ? -sFs[1] : 0.0);
   const size_t ifx = (i == P ? (size_t)(ey * M.nx + wrap(ex + 1, M.nx)) : (size_t)kk) * n + j;

@@ -1291,8 +1291,10 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
   __shared__ double sPsi[EB][n2 * n2];
   __shared__ double sWu[3][EB * n2];
   __shared__ double sc[3][EB * n2];
-  __shared__ double sB[EB][mm * mL + mL * mm + mm * mm];   // closures of Bx, By and Bz
-  __shared__ double sT[EB][mm * n + mL * n + mm * n];      // x-passes
+  // closures of Bx, By and Bz, and the x-passes; one pad double per element so
+  // that the element-fastest x-pass items do not collide in banks
+  __shared__ double sB[EB][mm * mL + mL * mm + mm * mm + 1];
+  __shared__ double sT[EB][mm * n + mL * n + mm * n + 1];
   __shared__ double sax[2][EB * n2];                       // |u_I| + |B|/sqrt(rho) per node
   __shared__ double ssig[EB][2 * n];
   __shared__ double sD[EB][n];
@@ -1324,10 +1326,11 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
     sB[e][w] = v;
   }
   __syncthreads();
-  // x-passes onto the DG x-nodes: Bx rows (Gauss y), By rows (GLL(k+1) y), Bz rows (GLL(k) y)
+  // x-passes onto the DG x-nodes: Bx rows (Gauss y), By rows (GLL(k+1) y), Bz rows (GLL(k) y);
+  // items element-fastest, so that a warp's items come from one family (one branch)
   constexpr int NT = mm * n + mL * n + (R2 ? 0 : mm * n);
   for (int it = tid; it < EB * NT; it += TH) {
-    const int e = it / NT, w = it % NT;
+    const int e = it % EB, w = it / EB;
     double v = 0.0;
     if (w < mm * n) {
       const int b = w / n, ii = w % n;
