@@ -159,6 +159,19 @@ __device__ __forceinline__ double logmean_FdF(double f, double lz, double* dF, d
   return F;
 }
 
+// Whether node value x of an element can put a pair of the element on the
+// logarithm branch of logmean_FdF (f^2 >= 1e-2, i.e. a ratio of at least
+// 1.1/0.9 = 1.2222) against the element's reference node value r: two nodes
+// whose bit patterns are within 0.099 2^52 of r's have a ratio below
+// exp(0.198) = 1.2190 (each ulp is a relative step of at most 2^-52), so only
+// blocks with a node further away need the per-node logarithms.  Integer
+// pipe only; non-positive or NaN values give huge differences.
+__device__ __forceinline__ bool adj_far_from_reference(double x, double r) {
+  const long long d = __double_as_longlong(x) - __double_as_longlong(r);
+  constexpr long long lim = 445856363109670LL;  // 0.099 * 2^52, rounded down
+  return d >= lim || d <= -lim;
+}
+
 // Volume part and assembly: EB elements x (p+1)^2 threads, p pairs per
 // thread as in the forward kernel.  Each pair's reverse sweep yields the
 // adjoints of (rho, u, beta) of its two nodes (shared memory); each node then
@@ -198,9 +211,18 @@ __global__ void __launch_bounds__(ACfg<P>::threads) k_adj_vol(const double* __re
     r0 = Us[0];
     b0 = 0.5 * Us[0] * rcp(pr);
     sp[0][tid] = r0; sp[1][tid] = u0[0]; sp[2][tid] = u0[1]; sp[3][tid] = u0[2];
-    sp[4][tid] = b0; sp[5][tid] = u20; sp[6][tid] = log(r0); sp[7][tid] = log(b0);
+    sp[4][tid] = b0; sp[5][tid] = u20;
   }
   __syncthreads();
+  // per-node logarithms for the whole block, only if some element of it has a
+  // node far enough from its first node for a pair to take the log branch
+  const bool far = adj_far_from_reference(r0, sp[0][el * n2]) || adj_far_from_reference(b0, sp[4][el * n2]);
+  const bool have_logs = __syncthreads_or(far) != 0;
+  if (have_logs) {
+    sp[6][tid] = log(r0);
+    sp[7][tid] = log(b0);
+    __syncthreads();
+  }
   const double cs[2] = {-4.0 * M.ihx, -4.0 * M.ihy};
 #pragma unroll
   for (int s = 0; s < P; ++s) {
@@ -221,8 +243,9 @@ __global__ void __launch_bounds__(ACfg<P>::threads) k_adj_vol(const double* __re
     const double isr = rcp(sr), isb = rcp(sb);
     const double fr = (rL - rR) * isr, fb = (bL - bR) * isb;
     double dFr, dFb, iFr, iFb;
-    const double Fr = logmean_FdF(fr, sp[6][qa] - sp[6][qb], &dFr, &iFr);
-    const double Fb = logmean_FdF(fb, sp[7][qa] - sp[7][qb], &dFb, &iFb);
+    const double lzr = have_logs ? sp[6][qa] - sp[6][qb] : 0.0, lzb = have_logs ? sp[7][qa] - sp[7][qb] : 0.0;
+    const double Fr = logmean_FdF(fr, lzr, &dFr, &iFr);
+    const double Fb = logmean_FdF(fb, lzb, &dFb, &iFb);
     const double rlog = 0.5 * sr * iFr;
     double ua[3];
     ua[0] = 0.5 * (sp[1][qa] + sp[1][qb]);

@@ -60,6 +60,35 @@ def test_hydro_vjp_full_jacobian(p):
     assert np.abs(Jg - Jt).max() <= 1e-11 * np.abs(Jt).max()
 
 
+@pytest.mark.parametrize("p", [1, 2])
+def test_hydro_vjp_full_jacobian_strong_variation(p):
+    """Nodal densities and pressures varying by factors of order e inside an
+    element: many pairs take the logarithm branch of the log mean (and its
+    derivative), and the volume kernel's per-node logarithms are formed."""
+    rng = np.random.default_rng(820 + p)
+    dom = (0.0, 1.0, 0.0, 0.8)
+    t = Tangent(2, 2, p, p, 1.4, dom)
+    shape = generic_state(t, rng).shape
+    rho = np.exp(0.4 * rng.standard_normal(shape[1:]))
+    pr = np.exp(0.4 * rng.standard_normal(shape[1:]))
+    u = np.stack([0.4 + 0.1 * rng.standard_normal(shape[1:]), 0.3 + 0.1 * rng.standard_normal(shape[1:]),
+                  0.1 * rng.standard_normal(shape[1:])])
+    U = np.concatenate([rho[None], rho * u, (pr / 0.4 + 0.5 * rho * (u * u).sum(0))[None]])
+    n = U.size
+    Jt = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        Jt[:, j] = t.hydro_rhs_tangent(U, e.reshape(U.shape))[1].ravel()
+    s = solver_like(t)
+    Jg = np.zeros((n, n))
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = 1.0
+        Jg[i, :] = s.hydro_rhs_vjp(U, e.reshape(U.shape)).ravel()
+    assert np.abs(Jg - Jt).max() <= 1e-11 * np.abs(Jt).max()
+
+
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 @pytest.mark.parametrize("mesh", [(5, 4), (3, 7)])
 def test_hydro_vjp_dot(p, mesh):
