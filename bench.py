@@ -181,12 +181,14 @@ def step_work(p, k):
     assemble = 4 * NW + 2 * (NX + NY)
     # at k = p - 1 the GLL(k+1) nodes are the DG nodes: every pass between them is a copy
     lid = mL == n
+    # velocity: u_x rows to GLL(k+1) x and u_y columns to GLL(k+1) y (shared by two families
+    # each), u_z rows to Gauss x and columns to Gauss y, then one second pass per family value
     fE = (assemble
-          + 2 * (2 * n * mm * n + (0 if lid else 3 * n * mL * n) + NW * mm + NZ * mm + mm * mL * mm)  # x-passes
-          + 2 * ((2 * NY + (0 if lid else 2 * NX + 2 * NW)) * n + (NX + NY + NW) * mm)                  # y-passes
+          + 2 * (2 * n * mm * n + (0 if lid else 2 * n * mL * n) + NW * mm + NZ * mm + mm * mL * mm)  # first passes
+          + 2 * ((NX + NY + (0 if lid else NX + NY + 2 * NW)) * n + (NX + NY + NW) * mm)              # second passes
           + 10 * (NX + NY + NW)                                                              # Ohm loads, Lorentz
-          + (2 * 2 * n * mm * mL + n * mL if lid else 2 * (4 * n * mm * mL + 2 * n * mL * mL))  # transposed y-pass
-          + n2 * (2 * ((0 if lid else 3 * mL) + 2 * mm) + 27))                               # x-pass, rates, SSP
+          + (2 * 2 * n * mm * mL if lid else 2 * (4 * n * mm * mL + 2 * n * mL * mL))        # transposed first passes
+          + n2 * (2 * ((0 if lid else 2 * mL) + 2 * mm) + 27))                               # second passes, rates, SSP
     fB = assemble + 2 * (NZ * mL + mL * mm * mm) + 3 * NZ * (2 * mL + 6) + NZ * 2 * mm
     loads = (NX + NY + NW) * d8
     bJ = 3 * NZ * d8 + loads

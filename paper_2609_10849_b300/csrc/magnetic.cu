@@ -343,16 +343,24 @@ struct LE_ {  // per-element shared-memory offsets (doubles), with region reuse
   static constexpr int JX = 0, JY = JX + D::NX, JZ = JY + D::NY, BX = JZ + D::NW, BY = BX + D::NY, BZ = BY + D::NX;
   static constexpr int ETA = BZ + D::NZ;
   static constexpr int RB = ETA + 1;
-  // region B: x-passes (dead after the y-passes), then the transposed y-pass
-  static constexpr int UG = RB;                          // u_y, u_z rows to Gauss x: [d][j][a]
-  static constexpr int UL = UG + 2 * D::n * D::mm;       // u_x, u_y, u_z rows to GLL(k+1) x
-  static constexpr int BXG = UL + 3 * D::n * D::mL;      // Bx rows (Gauss y) to Gauss x
-  static constexpr int BYL = BXG + D::NZ;                // By rows (GLL y) to GLL x (= By at W)
+  // region B: first passes (dead after the second ones; BYL is read by the pointwise stage),
+  // then the transposed passes.  Each velocity component takes, per family, the cheaper pass
+  // order, and a first pass is shared where two families share that direction's nodes:
+  // u_x rows to GLL(k+1) x (N_y, W), u_y columns to GLL(k+1) y (N_x, W), u_z rows to Gauss x
+  // (N_x) and columns to Gauss y (N_y)
+  static constexpr int UGZ = RB;                         // u_z rows to Gauss x: [j < n][a < mm]
+  static constexpr int ULX = UGZ + D::n * D::mm;         // u_x rows to GLL(k+1) x: [j < n][a < mL]
+  static constexpr int CYY = ULX + D::n * D::mL;         // u_y columns to GLL(k+1) y: [b < mL][i < n]
+  static constexpr int CGZ = CYY + D::mL * D::n;         // u_z columns to Gauss y: [b < mm][i < n]
+  static constexpr int BYL = CGZ + D::mm * D::n;         // By rows (GLL y) to GLL x (= By at W)
   static constexpr int BZG = BYL + D::NW;                // Bz rows to Gauss x
   static constexpr int BZL = BZG + D::NZ;                // Bz rows to GLL(k+1) x
   static constexpr int RB_END = BZL + D::mm * D::mL;
-  static constexpr int VX = RB, VY1 = VX + D::n * D::mL, VY2 = VY1 + D::n * D::mm, VZ1 = VY2 + D::n * D::mL,
-                       VZ2 = VZ1 + D::n * D::mm, V_END = VZ2 + D::n * D::mL;
+  // transposed passes of the Lorentz load: s_x (N_y and W, GLL(k+1) x) y-first into VX [j][a];
+  // s_y (N_x and W, GLL(k+1) y) x-first into HY [b][i]; s_z: N_x y-first into VZ1 [j][a],
+  // N_y x-first into HZ [b][i] (each family in its cheaper order)
+  static constexpr int VX = RB, HY = VX + D::n * D::mL, VZ1 = HY + D::mL * D::n, HZ = VZ1 + D::n * D::mm,
+                       V_END = HZ + D::mm * D::n;
   static constexpr int RC = RB_END > V_END ? RB_END : V_END;
   // region C: values at the auxiliary families; Lorentz products overwrite them in place;
   // the resistive stage reuses it afterwards
@@ -416,38 +424,63 @@ __global__ void __launch_bounds__(256) k_mag_E(
     SM(O::ETA, 0) = resistive ? eta[MHD_CHK(k, M.K)] : 0.0;
   }
   __syncthreads();
-  // stage 2: x-passes (u read straight from global memory); only what the
+  // stage 2: first passes (u read straight from global memory); only what the
   // cross products need: E_x = -(u_y B_z - u_z B_y) at N_x, E_y = -(u_z B_x -
   // u_x B_z) at N_y, E_z = -(u_x B_y - u_y B_x) at W
-  constexpr int NUG = R2 ? 0 : 2 * D::n * D::mm, NUL = (R2 ? 2 : 3) * D::n * D::mL;
-  constexpr int I2 = NUG + NUL + D::NW + (R2 ? 0 : D::NZ + D::mm * D::mL);
+  constexpr int NUZ = R2 ? 0 : D::n * D::mm, NUL = 2 * D::n * D::mL;
+  constexpr int I2 = 2 * NUZ + NUL + D::NW + (R2 ? 0 : D::NZ + D::mm * D::mL);
   FLAT(I2) {
     int it = idx / D::EB, e = idx % D::EB, k = min(k0 + e, M.K - 1);
     if constexpr (!R2) {
-      if (it < NUG) {  // u_y, u_z to Gauss x
-        int d = it / (D::n * D::mm), r = it % (D::n * D::mm), j = r / D::mm, a = r % D::mm;
-        const double* ur = u + MHD_CHK((1 + d) * N + (size_t)k * D::n2 + j * D::n, 3 * N - D::n + 1);
+      if (it < NUZ) {  // u_z rows to Gauss x
+        int j = it / D::mm, a = it % D::mm;
+        const double* ur = u + MHD_CHK(2 * N + (size_t)k * D::n2 + j * D::n, 3 * N - D::n + 1);
         double v = 0.0;
 #pragma unroll
         for (int i = 0; i < D::n; ++i) v = fma(T.P_G[a][i], ur[i], v);
-        SM(O::UG, it) = v;
+        SM(O::UGZ, it) = v;
         continue;
       }
-      it -= NUG;
+      it -= NUZ;
     }
-    if (it < NUL) {  // u_x, u_y (and u_z) to GLL(k+1) x
-      int d = it / (D::n * D::mL), r = it % (D::n * D::mL), j = r / D::mL, a = r % D::mL;
-      const double* ur = u + MHD_CHK(d * N + (size_t)k * D::n2 + j * D::n, 3 * N - D::n + 1);
+    if (it < D::n * D::mL) {  // u_x rows to GLL(k+1) x
+      int j = it / D::mL, a = it % D::mL;
+      const double* ur = u + MHD_CHK((size_t)k * D::n2 + j * D::n, 3 * N - D::n + 1);
       double v = 0.0;
       if constexpr (D::LID) v = ur[a];
       else {
 #pragma unroll
         for (int i = 0; i < D::n; ++i) v = fma(T.P_L[a][i], ur[i], v);
       }
-      SM(O::UL, it) = v;
+      SM(O::ULX, it) = v;
       continue;
     }
-    it -= NUL;
+    it -= D::n * D::mL;
+    if (it < D::mL * D::n) {  // u_y columns to GLL(k+1) y
+      int b = it / D::n, i = it % D::n;
+      const double* uc = u + MHD_CHK(N + (size_t)k * D::n2 + i, 3 * N - (D::n - 1) * D::n);
+      double v = 0.0;
+      if constexpr (D::LID) v = uc[b * D::n];
+      else {
+#pragma unroll
+        for (int j = 0; j < D::n; ++j) v = fma(T.P_L[b][j], uc[j * D::n], v);
+      }
+      SM(O::CYY, it) = v;
+      continue;
+    }
+    it -= D::mL * D::n;
+    if constexpr (!R2) {
+      if (it < NUZ) {  // u_z columns to Gauss y
+        int b = it / D::n, i = it % D::n;
+        const double* uc = u + MHD_CHK(2 * N + (size_t)k * D::n2 + i, 3 * N - (D::n - 1) * D::n);
+        double v = 0.0;
+#pragma unroll
+        for (int j = 0; j < D::n; ++j) v = fma(T.P_G[b][j], uc[j * D::n], v);
+        SM(O::CGZ, it) = v;
+        continue;
+      }
+      it -= NUZ;
+    }
     if (it < D::NW) {  // By rows (GLL y) to GLL x
       int j = it / D::mL, a = it % D::mL;
       double v = 0.0;
@@ -477,41 +510,70 @@ __global__ void __launch_bounds__(256) k_mag_E(
     }
   }
   __syncthreads();
-  // stage 3: y-passes to the auxiliary families
+  // stage 3: second passes to the auxiliary families
   constexpr int I3 = (R2 ? 0 : 2 * D::NX + 2 * D::NY) + 2 * D::NW + (R2 ? 0 : D::NX + D::NY) + D::NW;
   FLAT(I3) {
     int it = idx / D::EB, e = idx % D::EB;
     if constexpr (!R2) {
-      if (it < 2 * D::NX) {  // u_y, u_z at N_x: GLL(k+1) y from GLL(p)
-        int d = it / D::NX, r = it % D::NX, b = r / D::mm, a = r % D::mm;
+      if (it < D::NX) {  // u_y at N_x (a < mm Gauss x, b < mL): x-pass of the GLL(k+1)-y columns
+        int b = it / D::mm, a = it % D::mm;
         double v = 0.0;
-        if constexpr (D::LID) v = SM(O::UG, d * D::n * D::mm + b * D::mm + a);
+#pragma unroll
+        for (int i = 0; i < D::n; ++i) v = fma(T.P_G[a][i], SM(O::CYY, b * D::n + i), v);
+        SM(O::UNX, it) = v;
+        continue;
+      }
+      if (it < 2 * D::NX) {  // u_z at N_x: y-pass of the Gauss-x rows
+        const int r = it - D::NX, b = r / D::mm, a = r % D::mm;
+        double v = 0.0;
+        if constexpr (D::LID) v = SM(O::UGZ, b * D::mm + a);
         else {
 #pragma unroll
-          for (int j = 0; j < D::n; ++j) v = fma(T.P_L[b][j], SM(O::UG, d * D::n * D::mm + j * D::mm + a), v);
+          for (int j = 0; j < D::n; ++j) v = fma(T.P_L[b][j], SM(O::UGZ, j * D::mm + a), v);
         }
         SM(O::UNX, it) = v;
         continue;
       }
       it -= 2 * D::NX;
-      if (it < 2 * D::NY) {  // u_x, u_z at N_y: Gauss y
-        int d = it / D::NY, r = it % D::NY, b = r / D::mL, a = r % D::mL;
-        const int src = (d == 0 ? 0 : 2) * D::n * D::mL;
+      if (it < D::NY) {  // u_x at N_y (a < mL, b < mm Gauss y): y-pass of the GLL(k+1)-x rows
+        int b = it / D::mL, a = it % D::mL;
         double v = 0.0;
 #pragma unroll
-        for (int j = 0; j < D::n; ++j) v = fma(T.P_G[b][j], SM(O::UL, src + j * D::mL + a), v);
+        for (int j = 0; j < D::n; ++j) v = fma(T.P_G[b][j], SM(O::ULX, j * D::mL + a), v);
+        SM(O::UNY, it) = v;
+        continue;
+      }
+      if (it < 2 * D::NY) {  // u_z at N_y: x-pass of the Gauss-y columns
+        const int r = it - D::NY, b = r / D::mL, a = r % D::mL;
+        double v = 0.0;
+        if constexpr (D::LID) v = SM(O::CGZ, b * D::n + a);
+        else {
+#pragma unroll
+          for (int i = 0; i < D::n; ++i) v = fma(T.P_L[a][i], SM(O::CGZ, b * D::n + i), v);
+        }
         SM(O::UNY, it) = v;
         continue;
       }
       it -= 2 * D::NY;
     }
-    if (it < 2 * D::NW) {  // u_x, u_y at W
-      int d = it / D::NW, r = it % D::NW, b = r / D::mL, a = r % D::mL;
+    if (it < D::NW) {  // u_x at W: y-pass of the GLL(k+1)-x rows
+      int b = it / D::mL, a = it % D::mL;
       double v = 0.0;
-      if constexpr (D::LID) v = SM(O::UL, d * D::n * D::mL + b * D::mL + a);
+      if constexpr (D::LID) v = SM(O::ULX, b * D::mL + a);
       else {
 #pragma unroll
-        for (int j = 0; j < D::n; ++j) v = fma(T.P_L[b][j], SM(O::UL, d * D::n * D::mL + j * D::mL + a), v);
+        for (int j = 0; j < D::n; ++j) v = fma(T.P_L[b][j], SM(O::ULX, j * D::mL + a), v);
+      }
+      SM(O::UW, it) = v;
+      continue;
+    }
+    if (it < 2 * D::NW) {  // u_y at W: x-pass of the GLL(k+1)-y columns
+      const int r = it - D::NW, b = r / D::mL, a = r % D::mL;
+      double v = 0.0;
+      if constexpr (D::LID) v = SM(O::CYY, b * D::n + a);
+      else {
+#pragma unroll
+        for (int i = 0; i < D::n; ++i) v = fma(T.P_L[a][i], SM(O::CYY, b * D::n + i), v);
       }
       SM(O::UW, it) = v;
       continue;
@@ -580,19 +642,19 @@ __global__ void __launch_bounds__(256) k_mag_E(
     }
   }
   __syncthreads();
-  // stage 5: transposed y-pass onto the DG y-nodes (into region B)
-  constexpr int I5 = R2 ? 2 * D::n * D::mL : 3 * D::n * D::mL + 2 * D::n * D::mm;
+  // stage 5: first transposed passes of the Lorentz load (into region B)
+  constexpr int I5 = 2 * D::n * D::mL + (R2 ? 0 : 2 * D::n * D::mm);
   FLAT(I5) {
     int it = idx / D::EB, e = idx % D::EB;
-    if (it < D::n * D::mL) {
+    if (it < D::n * D::mL) {  // s_x: y-pass of N_y (Gauss y) and W (GLL y) onto the DG rows j
       int j = it / D::mL, a = it % D::mL;
-      double v = 0.0;
+      // at k = p - 1 the W part is a copy: it starts the chain
+      double v = D::LID ? SM(O::UW, j * D::mL + a) : 0.0;
       if constexpr (!R2) {
 #pragma unroll
         for (int b = 0; b < D::mm; ++b) v = fma(T.P_G[b][j], SM(O::UNY, b * D::mL + a), v);
       }
-      if constexpr (D::LID) v += SM(O::UW, j * D::mL + a);
-      else {
+      if constexpr (!D::LID) {
 #pragma unroll
         for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UW, b * D::mL + a), v);
       }
@@ -600,34 +662,23 @@ __global__ void __launch_bounds__(256) k_mag_E(
       continue;
     }
     it -= D::n * D::mL;
-    if constexpr (!R2) {
-      if (it < D::n * D::mm) {
-        int j = it / D::mm, a = it % D::mm;
-        double v = 0.0;
-        if constexpr (D::LID) v = SM(O::UNX, j * D::mm + a);
-        else {
+    if (it < D::mL * D::n) {  // s_y: x-pass of N_x (Gauss x) and W (GLL x) onto the DG columns i, rows b
+      int b = it / D::n, i = it % D::n;
+      double v = D::LID ? SM(O::UW, D::NW + b * D::mL + i) : 0.0;
+      if constexpr (!R2) {
 #pragma unroll
-          for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UNX, b * D::mm + a), v);
-        }
-        SM(O::VY1, it) = v;
-        continue;
+        for (int a = 0; a < D::mm; ++a) v = fma(T.P_G[a][i], SM(O::UNX, b * D::mm + a), v);
       }
-      it -= D::n * D::mm;
-    }
-    if (it < D::n * D::mL) {
-      int j = it / D::mL, a = it % D::mL;
-      double v = 0.0;
-      if constexpr (D::LID) v = SM(O::UW, D::NW + j * D::mL + a);
-      else {
+      if constexpr (!D::LID) {
 #pragma unroll
-        for (int b = 0; b < D::mL; ++b) v = fma(T.P_L[b][j], SM(O::UW, D::NW + b * D::mL + a), v);
+        for (int a = 0; a < D::mL; ++a) v = fma(T.P_L[a][i], SM(O::UW, D::NW + b * D::mL + a), v);
       }
-      SM(O::VY2, it) = v;
+      SM(O::HY, it) = v;
       continue;
     }
-    it -= D::n * D::mL;
+    it -= D::mL * D::n;
     if constexpr (!R2) {
-      if (it < D::n * D::mm) {
+      if (it < D::n * D::mm) {  // s_z from N_x: y-pass (GLL y) onto the DG rows j
         int j = it / D::mm, a = it % D::mm;
         double v = 0.0;
         if constexpr (D::LID) v = SM(O::UNX, D::NX + j * D::mm + a);
@@ -639,12 +690,15 @@ __global__ void __launch_bounds__(256) k_mag_E(
         continue;
       }
       it -= D::n * D::mm;
-      {
-        int j = it / D::mL, a = it % D::mL;
+      {  // s_z from N_y: x-pass (GLL x) onto the DG columns i, rows b (Gauss y)
+        int b = it / D::n, i = it % D::n;
         double v = 0.0;
+        if constexpr (D::LID) v = SM(O::UNY, D::NY + b * D::mL + i);
+        else {
 #pragma unroll
-        for (int b = 0; b < D::mm; ++b) v = fma(T.P_G[b][j], SM(O::UNY, D::NY + b * D::mL + a), v);
-        SM(O::VZ2, it) = v;
+          for (int a = 0; a < D::mL; ++a) v = fma(T.P_L[a][i], SM(O::UNY, D::NY + b * D::mL + a), v);
+        }
+        SM(O::HZ, it) = v;
       }
     }
   }
@@ -790,24 +844,23 @@ __global__ void __launch_bounds__(256) k_mag_E(
     int q = idx / D::EB, e = idx % D::EB, k = k0 + e;
     if (k >= M.K) continue;
     int j = q / D::n, i = q % D::n;
+    // second passes: s_x x-pass, s_y y-pass, s_z x-pass of VZ1 and y-pass of HZ
     double sx = 0.0, sy = 0.0, sz = 0.0;
     if constexpr (D::LID) {
       sx = SM(O::VX, j * D::mL + i);
-      sy = SM(O::VY2, j * D::mL + i);
-      if constexpr (!R2) sz = SM(O::VZ2, j * D::mL + i);
+      sy = SM(O::HY, j * D::n + i);
     } else {
 #pragma unroll
       for (int a = 0; a < D::mL; ++a) {
         sx = fma(T.P_L[a][i], SM(O::VX, j * D::mL + a), sx);
-        sy = fma(T.P_L[a][i], SM(O::VY2, j * D::mL + a), sy);
-        if constexpr (!R2) sz = fma(T.P_L[a][i], SM(O::VZ2, j * D::mL + a), sz);
+        sy = fma(T.P_L[a][j], SM(O::HY, a * D::n + i), sy);
       }
     }
     if constexpr (!R2) {
 #pragma unroll
       for (int a = 0; a < D::mm; ++a) {
-        sy = fma(T.P_G[a][i], SM(O::VY1, j * D::mm + a), sy);
         sz = fma(T.P_G[a][i], SM(O::VZ1, j * D::mm + a), sz);
+        sz = fma(T.P_G[a][j], SM(O::HZ, a * D::n + i), sz);
       }
     }
     size_t gq = MHD_CHK((size_t)k * D::n2 + q, N);
