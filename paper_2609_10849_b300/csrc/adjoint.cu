@@ -150,7 +150,7 @@ void hydro_fwd(mhd_ctx* c, StepTape& t, double* out, double fac, int h) {
     c->launches += 2;
     if (stab_on(c)) {
       stab_hydro(c->p, o[s], c->status, c->T, c->M, c->prm, c->dt, fac, c->work, frz_slot(c, t, h, s), c->st);
-      c->launches += c->prm.oe_hydro ? 4 : 1;
+      c->launches += c->prm.oe_hydro ? kStatsLaunches + 1 : 1;
     }
   }
 }
@@ -165,7 +165,7 @@ void mag_fwd(mhd_ctx* c, StepTape& t, const double* rho, double fac) {
   double* chol = t.chol ? t.chol : c->chol;
   if (res) {  // A.R. coefficient from the state entering the substep
     stab_eta(c->p, c->k, rho, t.Y[0], t.Y[0] + 4 * N, c->T, c->M, c->prm, t.eta, c->work, c->st);
-    c->launches += 3;
+    c->launches += kArLaunches;
   }
   if (c->prm.oe_vel) {
     stab_vel_prep(c->p, rho, chol, c->T, c->M, c->st);
@@ -181,7 +181,7 @@ void mag_fwd(mhd_ctx* c, StepTape& t, const double* rho, double fac) {
       cudaMemcpyAsync(t.vstar + 3 * N * s, out + N, 3 * N * sizeof(double), cudaMemcpyDeviceToDevice, c->st);
       stab_vel(c->p, c->k, rho, out, out + 4 * N, chol, c->T, c->M, c->prm, c->dt, fac, c->work,
                t.vfrz + (size_t)s * c->M.K * c->n, c->st);
-      c->launches += 4;
+      c->launches += kStatsLaunches + 1;
     }
   }
 }

@@ -106,7 +106,7 @@ void hydro_substep(mhd_ctx* c, double fac) {
     if (stab) {
       Prof pr(c, KC_STAB_H);
       stab_hydro(c->p, out[s], c->status, c->T, c->M, c->prm, c->dt, fac, c->work, nullptr, c->st);
-      c->launches += c->prm.oe_hydro ? 4 : 1;
+      c->launches += c->prm.oe_hydro ? kStatsLaunches + 1 : 1;
     }
   }
 }
@@ -125,7 +125,7 @@ void mag_substep(mhd_ctx* c, double fac) {
   if (resistive) {
     Prof pr(c, KC_STAB_ETA);
     stab_eta(c->p, c->k, c->U, c->Y0, c->B, c->T, c->M, c->prm, c->eta, c->work, c->st);
-    c->launches += 3;
+    c->launches += kArLaunches;
   } else {
     cudaMemsetAsync(c->eta, 0, c->M.K * sizeof(double), c->st);
   }
@@ -150,7 +150,7 @@ void mag_substep(mhd_ctx* c, double fac) {
       Prof pr(c, KC_STAB_VEL);
       stab_vel(c->p, c->k, c->U, Yout[s], Bout[s], c->chol, c->T, c->M, c->prm, c->dt, fac, c->work, nullptr,
                c->st);
-      c->launches += 4;
+      c->launches += kStatsLaunches + 1;
     }
   }
   Prof pr(c, KC_EXCH);
@@ -936,7 +936,7 @@ int mhd_hydro_stage_map(mhd_ctx* c, const double* U, double tau, double* out, in
   cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->st);
   set_scalar(c->dt, tau, c->st);
   stab_hydro(c->p, c->S1, c->status, c->T, c->M, c->prm, c->dt, 1.0, c->work, nullptr, c->st);
-  c->launches += 1 + (c->prm.oe_hydro ? 4 : 1);
+  c->launches += 1 + (c->prm.oe_hydro ? kStatsLaunches + 1 : 1);
   if ((e = copy_out(c, out, c->S1, 5 * c->N, on_device)) != cudaSuccess) return cuda_fail(e, "out");
   if ((e = cudaStreamSynchronize(c->st)) != cudaSuccess) return cuda_fail(e, "hydro_stage_map");
   return MHD_OK;

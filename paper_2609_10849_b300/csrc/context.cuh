@@ -11,6 +11,11 @@
 #include "mhd_internal.cuh"
 
 namespace mhd {
+// Kernel launches of the stabilisation launchers, for the contexts' launch counts:
+// the sensor statistics (k_stats, k_lines, k_global) and the A.R. coefficient
+// (k_ar_elem, k_ar_part, k_ar_global, k_ar_eta).
+constexpr int kStatsLaunches = 3;
+constexpr int kArLaunches = 4;
 // kernels / launchers defined in the other translation units
 void hydro_face(int p, const double* S, double* Fx, double* Fy, const Mesh& M, cudaStream_t st);
 void hydro_vol(int p, int mode, const double* S, const double* U0, const double* Fx, const double* Fy, double* out,
