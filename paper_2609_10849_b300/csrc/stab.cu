@@ -1312,7 +1312,16 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
 #pragma unroll
   for (int d = 0; d < ND; ++d) u[d] = Y[MHD_CHK((1 + d) * N + (size_t)kk * n2 + q, 4 * N)];
   const double r_ = rho[MHD_CHK((size_t)kk * n2 + q, N)];
-  for (int t = q; t < n2 * n2; t += n2) sPsi[el][t] = Psi[MHD_CHK((size_t)kk * n2 * n2 + t, (size_t)M.K * n2 * n2)];
+  {  // Psi of the element to shared memory as asynchronous copies (cp.async), waited
+     // for only where the projections need it, so that the B evaluation and the
+     // sensor run meanwhile
+    const double* src = Psi + MHD_CHK((size_t)kk * n2 * n2, (size_t)M.K * n2 * n2);
+    for (int t = q; t < n2 * n2; t += n2) {
+      const unsigned dst = (unsigned)__cvta_generic_to_shared(&sPsi[el][t]);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src + t) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  }
   if (tid < n2) sMw[tid] = M.Jdet * T->wp[tid % n] * T->wp[tid / n];
   // closures of B (Bx [b < mm][a < mL], By [b < mL][a < mm], Bz [b][a]) of the block's elements
   constexpr int NB = mm * mL + mL * mm + (R2 ? 0 : mm * mm);
@@ -1413,7 +1422,8 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
     sD[e][l] = Dl;
     sH[e][l] = 0.5 * (1.0 - Dl * Dl);
   }
-  __syncthreads();
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // this thread's Psi copies
+  __syncthreads();                                         // and everyone else's
   if (frz && q < n && valid) frz[(size_t)k * n + q] = sD[el][q];
   warp_or(prm.activity, sD[el][P] < 0.99 ? ACT_OE_VEL : 0u);
   // coefficients c_alpha = sum_t Psi[t][alpha] W_t u_t (thread q plays alpha)
