@@ -272,65 +272,64 @@ __global__ void __launch_bounds__(HCfg<P, EBv>::threads, HCfg<P, EBv>::min_block
     L[c] = v;
   }
 
-  if (MODE == 0) {
+  if constexpr (MODE == 0) {
     if (valid) {
 #pragma unroll
       for (int c = 0; c < 5; ++c) out[MHD_CHK(c * N + gi, 5 * N)] = L[c];
     }
-    return;
-  }
-
-  // L is tau L (first stage) or b tau L: C = S + tau L, or a U0 + b S + b tau L
-  double Cv[5];
-#pragma unroll
-  for (int c = 0; c < 5; ++c)
-    Cv[c] = first ? Us[c] + L[c] : fma(ca, U0[MHD_CHK(c * N + gi, 5 * N)], fma(cb, Us[c], L[c]));
-  if (valid) {
-#pragma unroll
-    for (int c = 0; c < 5; ++c) out[MHD_CHK(c * N + gi, 5 * N)] = Cv[c];
-  }
-  // no status word: the caller's limiter tests the same averages itself (the
-  // OE before it keeps them), so the reduction below is skipped (block-uniform)
-  if (status == nullptr && avg_out == nullptr) return;
-  // ---- raw element averages and the admissibility check --------------------------
-  double a0, a1, a2, a3, a4;
-  if constexpr (n2 == 4 || n2 == 16) {
-    // an element is an aligned power-of-two lane segment: xor-shuffle sums
-    const double wq = 0.25 * T->wp[i] * T->wp[j];
-    double w[5];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) w[c] = wq * Cv[c];
-#pragma unroll
-    for (int o = n2 / 2; o > 0; o >>= 1)
-#pragma unroll
-      for (int c = 0; c < 5; ++c) w[c] += __shfl_xor_sync(0xffffffffu, w[c], o);
-    a0 = w[0]; a1 = w[1]; a2 = w[2]; a3 = w[3]; a4 = w[4];
   } else {
-    __syncthreads();  // sf is reused for the stage values
+    // L is tau L (first stage) or b tau L: C = S + tau L, or a U0 + b S + b tau L
+    double Cv[5];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) sf[c][el * n2 + q] = Cv[c];
-    __syncthreads();
-    // component c is reduced by node thread c mod n2
-    for (int c = q; c < 5; c += n2) {
-      double s = 0.0;
+    for (int c = 0; c < 5; ++c)
+      Cv[c] = first ? Us[c] + L[c] : fma(ca, U0[MHD_CHK(c * N + gi, 5 * N)], fma(cb, Us[c], L[c]));
+    if (valid) {
 #pragma unroll
-      for (int t2 = 0; t2 < n2; ++t2) s = fma(0.25 * T->wp[t2 % n] * T->wp[t2 / n], sf[c][el * n2 + t2], s);
-      savg[c][el] = s;
+      for (int c = 0; c < 5; ++c) out[MHD_CHK(c * N + gi, 5 * N)] = Cv[c];
     }
-    __syncthreads();
-    a0 = savg[0][el]; a1 = savg[1][el]; a2 = savg[2][el]; a3 = savg[3][el]; a4 = savg[4][el];
-  }
-  if (q == 0 && valid) {
-    if (avg_out) {
-      avg_out[0 * (size_t)M.K + k] = a0; avg_out[1 * (size_t)M.K + k] = a1; avg_out[2 * (size_t)M.K + k] = a2;
-      avg_out[3 * (size_t)M.K + k] = a3; avg_out[4 * (size_t)M.K + k] = a4;
+    // no status word: the caller's limiter tests the same averages itself (the
+    // OE before it keeps them), so the reduction below is skipped (block-uniform)
+    if (status == nullptr && avg_out == nullptr) return;
+    // ---- raw element averages and the admissibility check --------------------------
+    double a0, a1, a2, a3, a4;
+    if constexpr (n2 == 4 || n2 == 16) {
+      // an element is an aligned power-of-two lane segment: xor-shuffle sums
+      const double wq = 0.25 * T->wp[i] * T->wp[j];
+      double w[5];
+#pragma unroll
+      for (int c = 0; c < 5; ++c) w[c] = wq * Cv[c];
+#pragma unroll
+      for (int o = n2 / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < 5; ++c) w[c] += __shfl_xor_sync(0xffffffffu, w[c], o);
+      a0 = w[0]; a1 = w[1]; a2 = w[2]; a3 = w[3]; a4 = w[4];
+    } else {
+      __syncthreads();  // sf is reused for the stage values
+#pragma unroll
+      for (int c = 0; c < 5; ++c) sf[c][el * n2 + q] = Cv[c];
+      __syncthreads();
+      // component c is reduced by node thread c mod n2
+      for (int c = q; c < 5; c += n2) {
+        double s = 0.0;
+#pragma unroll
+        for (int t2 = 0; t2 < n2; ++t2) s = fma(0.25 * T->wp[t2 % n] * T->wp[t2 / n], sf[c][el * n2 + t2], s);
+        savg[c][el] = s;
+      }
+      __syncthreads();
+      a0 = savg[0][el]; a1 = savg[1][el]; a2 = savg[2][el]; a3 = savg[3][el]; a4 = savg[4][el];
     }
-    // rho > 0 and p > 0  <=>  rho > 0 and rho E - |m|^2/2 > 0
-    double pe = fma(a0, a4, -0.5 * fma(a1, a1, fma(a2, a2, a3 * a3)));
-    bool fin = isfinite(a0) && isfinite(a1) && isfinite(a2) && isfinite(a3) && isfinite(a4);
-    if (status) {
-      if (!fin) atomicOr(status, ST_NONFINITE | ST_INADMISSIBLE);
-      else if (!(a0 > 0.0) || !(pe > 0.0)) atomicOr(status, ST_INADMISSIBLE);
+    if (q == 0 && valid) {
+      if (avg_out) {
+        avg_out[0 * (size_t)M.K + k] = a0; avg_out[1 * (size_t)M.K + k] = a1; avg_out[2 * (size_t)M.K + k] = a2;
+        avg_out[3 * (size_t)M.K + k] = a3; avg_out[4 * (size_t)M.K + k] = a4;
+      }
+      // rho > 0 and p > 0  <=>  rho > 0 and rho E - |m|^2/2 > 0
+      double pe = fma(a0, a4, -0.5 * fma(a1, a1, fma(a2, a2, a3 * a3)));
+      bool fin = isfinite(a0) && isfinite(a1) && isfinite(a2) && isfinite(a3) && isfinite(a4);
+      if (status) {
+        if (!fin) atomicOr(status, ST_NONFINITE | ST_INADMISSIBLE);
+        else if (!(a0 > 0.0) || !(pe > 0.0)) atomicOr(status, ST_INADMISSIBLE);
+      }
     }
   }
 }

@@ -1318,7 +1318,8 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
     const double* src = Psi + MHD_CHK((size_t)kk * n2 * n2, (size_t)M.K * n2 * n2);
     for (int t = q; t < n2 * n2; t += n2) {
       const unsigned dst = (unsigned)__cvta_generic_to_shared(&sPsi[el][t]);
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src + t) : "memory");
+      const size_t gsrc = __cvta_generic_to_global(src + t);
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(gsrc) : "memory");
     }
     asm volatile("cp.async.commit_group;\n" ::: "memory");
   }
