@@ -593,6 +593,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=0, help="run the batched workload with this many runs instead")
     ap.add_argument("--no-side-legs", action="store_true", help="skip the side measurements")
+    ap.add_argument("--tiles", default="", help="VOL,MAG tile variants (0 default, 1, 2) instead of the autotuner "
+                    "(for runs under a profiler, whose serialised launches distort the autotuner's timings)")
     ap.add_argument("--leg", default="", choices=["", "adjoint"], help="run only this side measurement")
     ap.add_argument("--reduced-2d2v", action="store_true",
                     help="time the reduced 2D2V magnetic stage in the main measurement (for profiling)")
@@ -628,7 +630,12 @@ def main():
     s.set_stream(stream.cuda_stream)
     if args.reduced_2d2v:
         s.set_params(reduced_2d2v=1)
-    tiles = s.autotune()  # elements per CTA of the volume and magnetic kernels
+    if args.tiles:  # fixed variants; elements per CTA of p = 3 (csrc: vol_tile_eb, mag_tile_eb)
+        tv, tm = (int(x) for x in args.tiles.split(","))
+        s.set_tiles(tv, tm)
+        tiles = ((8, 4, 16)[tv], (16, 8, 32)[tm])
+    else:
+        tiles = s.autotune()  # elements per CTA of the volume and magnetic kernels
     dt = s.compute_dt()
     dofs = dofs_per_element(3, 3) * s.K
 
