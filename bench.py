@@ -593,8 +593,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=0, help="run the batched workload with this many runs instead")
     ap.add_argument("--no-side-legs", action="store_true", help="skip the side measurements")
-    ap.add_argument("--tiles", default="", help="VOL,MAG tile variants (0 default, 1, 2) instead of the autotuner "
-                    "(for runs under a profiler, whose serialised launches distort the autotuner's timings)")
+    ap.add_argument("--tiles", default="", help="VOL,MAG tile variants instead of the autotuner (VOL 0 default, 1, "
+                    "2; MAG 0..2 for all magnetic kernels or the code vE + 3 vJ + 9 vB), for runs under a profiler, "
+                    "whose serialised launches distort the autotuner's timings")
     ap.add_argument("--leg", default="", choices=["", "adjoint"], help="run only this side measurement")
     ap.add_argument("--reduced-2d2v", action="store_true",
                     help="time the reduced 2D2V magnetic stage in the main measurement (for profiling)")
@@ -633,7 +634,7 @@ def main():
     if args.tiles:  # fixed variants; elements per CTA of p = 3 (csrc: vol_tile_eb, mag_tile_eb)
         tv, tm = (int(x) for x in args.tiles.split(","))
         s.set_tiles(tv, tm)
-        tiles = ((8, 4, 16)[tv], (16, 8, 32)[tm])
+        tiles = ((8, 4, 16)[tv], (16, 8, 32)[tm % 3])
     else:
         tiles = s.autotune()  # elements per CTA of the volume and magnetic kernels
     dt = s.compute_dt()

@@ -222,13 +222,17 @@ int mhd_batch_step(mhd_batch* batch, const double* dt, int nsteps, int* status);
 long long mhd_batch_launch_count(const mhd_batch* batch);
 
 /* Tile autotuner (batching of independent problems; the paper has none): times the
- * elements-per-CTA variants of the volume kernel and of the magnetic-stage
- * kernels on the context's own mesh and CURRENT state (set a state first) and
- * keeps the fastest for every later launch (cached graphs are re-captured).
- * choices (may be NULL) receives [volume elements per CTA, magnetic elements
- * per CTA].  Synchronises; leaves the state unchanged. */
+ * elements-per-CTA variants of the volume kernel and of each of the three
+ * magnetic-stage kernels (the E kernel first, then J, then the curl, the
+ * others held) on the context's own mesh and CURRENT state (set a state first)
+ * and keeps the fastest for every later launch (cached graphs are re-captured).
+ * choices (may be NULL) receives [volume elements per CTA, elements per CTA of
+ * the magnetic E kernel].  Synchronises; leaves the state unchanged. */
 int mhd_autotune(mhd_ctx* ctx, int* choices);
-/* Set the tile variants directly (0 = default, 1, 2; see mhd_autotune). */
+/* Set the tile variants directly (0 = default, 1, 2; see mhd_autotune).
+ * mag_variant 0..2 applies to all three magnetic kernels; 3..26 is the code
+ * vE + 3 vJ + 9 vB of one variant per kernel (E, J, curl).  Errors:
+ * MHD_EINVAL (a variant out of range or too large for the device). */
 int mhd_set_tiles(mhd_ctx* ctx, int vol_variant, int mag_variant);
 /* mhd_autotune for every run of a batch (each run keeps its own choice). */
 int mhd_batch_autotune(mhd_batch* batch);

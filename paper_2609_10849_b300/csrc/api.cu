@@ -700,18 +700,27 @@ int mhd_autotune(mhd_ctx* c, int* choices) {
     if (t < best) { best = t; bv = v; }
   }
   cons_to_prim(c->U, c->Y0, N, c->st);
-  best = 1e30f;
-  int bm = 0;
-  for (int v = 0; v < kTileVariants; ++v) {
-    if (!mag_tile_ok(c->p, c->k, v)) continue;
-    Mesh Mv = c->M;
-    Mv.tile_mag = v;
-    float t = time_launches(c, reps, [&] {
-      mag_stage(c->p, c->k, 0, c->B, c->Y0 + N, c->Y0, c->U, c->eta, 0, c->B, c->Y0 + N, c->Y0, c->Ba, c->Ya + N,
-                c->Ya, c->LJ, c->LE, c->T, Mv, c->dt, 1.0, 0.0, 1.0, 1, c->prm.reduced, c->st);
-    }, a, b);
-    if (t < best) { best = t; bm = v; }
+  // magnetic stage: each kernel's own variant (tile code vE + 3 vJ + 9 vB), chosen
+  // one kernel at a time with the others held: E (the largest) first, then J, then B
+  int bv3[3] = {0, 0, 0};  // E, J, B
+  for (int which = 0; which < 3; ++which) {
+    best = 1e30f;
+    int bw = 0;
+    for (int v = 0; v < kTileVariants; ++v) {
+      if (!mag_tile_ok(c->p, c->k, v)) continue;
+      int trial[3] = {bv3[0], bv3[1], bv3[2]};
+      trial[which] = v;
+      Mesh Mv = c->M;
+      Mv.tile_mag = trial[0] + kTileVariants * trial[1] + kTileVariants * kTileVariants * trial[2];
+      float t = time_launches(c, reps, [&] {
+        mag_stage(c->p, c->k, 0, c->B, c->Y0 + N, c->Y0, c->U, c->eta, 0, c->B, c->Y0 + N, c->Y0, c->Ba, c->Ya + N,
+                  c->Ya, c->LJ, c->LE, c->T, Mv, c->dt, 1.0, 0.0, 1.0, 1, c->prm.reduced, c->st);
+      }, a, b);
+      if (t < best) { best = t; bw = v; }
+    }
+    bv3[which] = bw;
   }
+  const int bm = bv3[0] + kTileVariants * bv3[1] + kTileVariants * kTileVariants * bv3[2];
   cudaMemsetAsync(c->status, 0, sizeof(unsigned), c->st);
   e = cudaStreamSynchronize(c->st);
   cudaEventDestroy(a);
@@ -722,17 +731,21 @@ int mhd_autotune(mhd_ctx* c, int* choices) {
   if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
   if (choices) {
     choices[0] = vol_tile_eb(c->p, bv);
-    choices[1] = mag_tile_eb(bm);
+    choices[1] = mag_tile_eb(bv3[0]);
   }
   return MHD_OK;
 }
 
 int mhd_set_tiles(mhd_ctx* c, int vol_variant, int mag_variant) {
   if (!c) return fail(MHD_EINVAL, "null context");
-  if (vol_variant < 0 || vol_variant >= kTileVariants || !mag_tile_ok(c->p, c->k, mag_variant))
+  constexpr int V = kTileVariants;
+  // one variant for the three magnetic kernels, or the code vE + 3 vJ + 9 vB
+  const int code = mag_variant >= 0 && mag_variant < V ? mag_variant * (1 + V + V * V) : mag_variant;
+  if (vol_variant < 0 || vol_variant >= V || code < 0 || code >= V * V * V || !mag_tile_ok(c->p, c->k, code % V) ||
+      !mag_tile_ok(c->p, c->k, code / V % V) || !mag_tile_ok(c->p, c->k, code / (V * V)))
     return fail(MHD_EINVAL, "invalid tile variant");
   c->M.tile_vol = vol_variant;
-  c->M.tile_mag = mag_variant;
+  c->M.tile_mag = code;
   if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
   return MHD_OK;
 }

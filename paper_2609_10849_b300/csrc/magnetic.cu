@@ -992,45 +992,57 @@ __global__ void __launch_bounds__(256) k_mag_B(const double* __restrict__ LEx, c
 }
 
 // ---- launchers ------------------------------------------------------------------
+// Each of the three kernels takes its own tile variant: the mesh's magnetic
+// tile code is vE + 3 vJ + 9 vB (a single variant v is v + 3 v + 9 v).
 template <int P, int KM, int EBv>
-void mag_stage_eb(int mode, const double* B, const double* u, const double* e, const double* rho, const double* eta,
-                  int resistive, const double* B0, const double* u0, const double* e0, double* Bo, double* uo,
-                  double* eo, double* LJ, double* LE, const Mesh& M, const double* dtp, double dtfac, double ca,
-                  double cb, int first, int reduced, cudaStream_t st) {
+void mag_J_eb(const double* B, double* LJ, const Mesh& M, int reduced, cudaStream_t st) {
   using D = MD<P, KM, EBv>;
   const size_t Z = (size_t)M.K * D::NZ;
   double* LJx = LJ; double* LJy = LJ + (size_t)M.K * D::NX; double* LJz = LJy + (size_t)M.K * D::NY;
-  double* LEx = LE; double* LEy = LE + (size_t)M.K * D::NX; double* LEz = LEy + (size_t)M.K * D::NY;
-  unsigned blocks = (unsigned)((M.K + D::EB - 1) / D::EB);
+  const unsigned blocks = (unsigned)((M.K + D::EB - 1) / D::EB);
   const size_t sj = sizeof(double) * LJ_<P, KM>::SIZE * D::EB;
+  if (reduced) k_mag_J<P, KM, EBv, true><<<blocks, D::TH, sj, st>>>(B, B + Z, B + 2 * Z, LJx, LJy, LJz, M);
+  else k_mag_J<P, KM, EBv><<<blocks, D::TH, sj, st>>>(B, B + Z, B + 2 * Z, LJx, LJy, LJz, M);
+}
+
+template <int P, int KM, int EBv>
+void mag_E_eb(int mode, const double* B, const double* u, const double* e, const double* rho, const double* eta,
+              int resistive, const double* u0, const double* e0, double* uo, double* eo, const double* LJ, double* LE,
+              const Mesh& M, const double* dtp, double dtfac, double ca, double cb, int first, int reduced,
+              cudaStream_t st) {
+  using D = MD<P, KM, EBv>;
+  const size_t Z = (size_t)M.K * D::NZ;
+  const double* LJx = LJ; const double* LJy = LJ + (size_t)M.K * D::NX; const double* LJz = LJy + (size_t)M.K * D::NY;
+  double* LEx = LE; double* LEy = LE + (size_t)M.K * D::NX; double* LEz = LEy + (size_t)M.K * D::NY;
+  const unsigned blocks = (unsigned)((M.K + D::EB - 1) / D::EB);
   const size_t se = sizeof(double) * LE_<P, KM>::SIZE * D::EB;
-  const size_t sb = sizeof(double) * LB_<P, KM>::SIZE * D::EB;
+#define MHD_MAG_E_LAUNCH(MODE_, R2_)                                                                          \
+  k_mag_E<P, KM, MODE_, EBv, R2_><<<blocks, D::TH, se, st>>>(LJx, LJy, LJz, B, B + Z, B + 2 * Z, u, e, rho, eta, \
+                                                             u0, e0, uo, eo, LEx, LEy, LEz, M, dtp, dtfac, ca, cb, \
+                                                             first, resistive)
   if (reduced) {  // 2D2V: u_z = B_z = 0, in-plane E and J vanish
-    k_mag_J<P, KM, EBv, true><<<blocks, D::TH, sj, st>>>(B, B + Z, B + 2 * Z, LJx, LJy, LJz, M);
-    if (mode == 0) {
-      k_mag_E<P, KM, 0, EBv, true><<<blocks, D::TH, se, st>>>(LJx, LJy, LJz, B, B + Z, B + 2 * Z, u, e, rho, eta, u0,
-                                                               e0, uo, eo, LEx, LEy, LEz, M, dtp, dtfac, ca, cb,
-                                                               first, resistive);
-      k_mag_B<P, KM, 0, EBv, true><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, M, dtp, dtfac, ca, cb,
-                                                               first);
-    } else {
-      k_mag_E<P, KM, 1, EBv, true><<<blocks, D::TH, se, st>>>(LJx, LJy, LJz, B, B + Z, B + 2 * Z, u, e, rho, eta, u0,
-                                                               e0, uo, eo, LEx, LEy, LEz, M, dtp, dtfac, ca, cb,
-                                                               first, resistive);
-      k_mag_B<P, KM, 1, EBv, true><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, M, dtp, dtfac, ca, cb,
-                                                               first);
-    }
-    return;
-  }
-  k_mag_J<P, KM, EBv><<<blocks, D::TH, sj, st>>>(B, B + Z, B + 2 * Z, LJx, LJy, LJz, M);
-  if (mode == 0) {
-    k_mag_E<P, KM, 0, EBv><<<blocks, D::TH, se, st>>>(LJx, LJy, LJz, B, B + Z, B + 2 * Z, u, e, rho, eta, u0, e0, uo,
-                                                       eo, LEx, LEy, LEz, M, dtp, dtfac, ca, cb, first, resistive);
-    k_mag_B<P, KM, 0, EBv><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, M, dtp, dtfac, ca, cb, first);
+    if (mode == 0) MHD_MAG_E_LAUNCH(0, true);
+    else MHD_MAG_E_LAUNCH(1, true);
   } else {
-    k_mag_E<P, KM, 1, EBv><<<blocks, D::TH, se, st>>>(LJx, LJy, LJz, B, B + Z, B + 2 * Z, u, e, rho, eta, u0, e0, uo,
-                                                       eo, LEx, LEy, LEz, M, dtp, dtfac, ca, cb, first, resistive);
-    k_mag_B<P, KM, 1, EBv><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, M, dtp, dtfac, ca, cb, first);
+    if (mode == 0) MHD_MAG_E_LAUNCH(0, false);
+    else MHD_MAG_E_LAUNCH(1, false);
+  }
+#undef MHD_MAG_E_LAUNCH
+}
+
+template <int P, int KM, int EBv>
+void mag_B_eb(int mode, const double* B, const double* B0, double* Bo, const double* LE, const Mesh& M,
+              const double* dtp, double dtfac, double ca, double cb, int first, int reduced, cudaStream_t st) {
+  using D = MD<P, KM, EBv>;
+  const double* LEx = LE; const double* LEy = LE + (size_t)M.K * D::NX; const double* LEz = LEy + (size_t)M.K * D::NY;
+  const unsigned blocks = (unsigned)((M.K + D::EB - 1) / D::EB);
+  const size_t sb = sizeof(double) * LB_<P, KM>::SIZE * D::EB;
+  if (reduced) {
+    if (mode == 0) k_mag_B<P, KM, 0, EBv, true><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, M, dtp, dtfac, ca, cb, first);
+    else k_mag_B<P, KM, 1, EBv, true><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, M, dtp, dtfac, ca, cb, first);
+  } else {
+    if (mode == 0) k_mag_B<P, KM, 0, EBv><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, M, dtp, dtfac, ca, cb, first);
+    else k_mag_B<P, KM, 1, EBv><<<blocks, D::TH, sb, st>>>(LEx, LEy, LEz, B, B0, Bo, M, dtp, dtfac, ca, cb, first);
   }
 }
 
@@ -1042,16 +1054,31 @@ void mag_stage_impl(int mode, const double* B, const double* u, const double* e,
                     const double* eta, int resistive, const double* B0, const double* u0, const double* e0,
                     double* Bo, double* uo, double* eo, double* LJ, double* LE, const Mesh& M, const double* dtp,
                     double dtfac, double ca, double cb, int first, int reduced, cudaStream_t st) {
-  const int v = (M.tile_mag > 0 && M.tile_mag < kTileVariants && g_mag_tile_ok[P - 1 + KM][M.tile_mag]) ? M.tile_mag : 0;
-#define MHD_MAG_EB(V)                                                                                            \
-  mag_stage_eb<P, KM, mag_tile_eb(V)>(mode, B, u, e, rho, eta, resistive, B0, u0, e0, Bo, uo, eo, LJ, LE, M, dtp, \
-                                      dtfac, ca, cb, first, reduced, st)
-  switch (v) {
-    case 1: MHD_MAG_EB(1); break;
-    case 2: MHD_MAG_EB(2); break;
-    default: MHD_MAG_EB(0); break;
+  const int code = M.tile_mag >= 0 && M.tile_mag < kTileVariants * kTileVariants * kTileVariants ? M.tile_mag : 0;
+  auto ok = [](int v) { return v > 0 && g_mag_tile_ok[P - 1 + KM][v] ? v : 0; };
+  const int vE = ok(code % kTileVariants), vJ = ok(code / kTileVariants % kTileVariants),
+            vB = ok(code / (kTileVariants * kTileVariants));
+  switch (vJ) {
+    case 1: mag_J_eb<P, KM, mag_tile_eb(1)>(B, LJ, M, reduced, st); break;
+    case 2: mag_J_eb<P, KM, mag_tile_eb(2)>(B, LJ, M, reduced, st); break;
+    default: mag_J_eb<P, KM, mag_tile_eb(0)>(B, LJ, M, reduced, st); break;
   }
-#undef MHD_MAG_EB
+#define MHD_MAG_E_EB(V)                                                                                          \
+  mag_E_eb<P, KM, mag_tile_eb(V)>(mode, B, u, e, rho, eta, resistive, u0, e0, uo, eo, LJ, LE, M, dtp, dtfac, ca, cb, \
+                                  first, reduced, st)
+  switch (vE) {
+    case 1: MHD_MAG_E_EB(1); break;
+    case 2: MHD_MAG_E_EB(2); break;
+    default: MHD_MAG_E_EB(0); break;
+  }
+#undef MHD_MAG_E_EB
+#define MHD_MAG_B_EB(V) mag_B_eb<P, KM, mag_tile_eb(V)>(mode, B, B0, Bo, LE, M, dtp, dtfac, ca, cb, first, reduced, st)
+  switch (vB) {
+    case 1: MHD_MAG_B_EB(1); break;
+    case 2: MHD_MAG_B_EB(2); break;
+    default: MHD_MAG_B_EB(0); break;
+  }
+#undef MHD_MAG_B_EB
 }
 
 // Opt-in dynamic shared memory of the magnetic kernels of one (p, k) pair on the

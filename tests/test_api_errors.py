@@ -123,6 +123,10 @@ def test_refused_calls_leave_the_context_usable():
     assert s.strang_steps(1e-3, 0) == 0
     with pytest.raises(MhdError, match="invalid tile variant"):
         s.set_tiles(9, 0)
+    with pytest.raises(MhdError, match="invalid tile variant"):
+        s.set_tiles(0, 27)
+    with pytest.raises(MhdError, match="invalid tile variant"):
+        s.set_tiles(0, -1)
     with pytest.raises(MhdError, match="nq"):
         s.quad_coords(0)
     with pytest.raises(MhdError, match="nq"):

@@ -73,12 +73,13 @@ def test_tile_variants_bitwise(pk):
     wl = workloads.orszag_tang_variant(3)
     o = oracle_state(wl, 9, 7, p, k)
     ref = None
-    for v in range(3):
+    # one variant for all magnetic kernels (0..2), then per-kernel codes vE + 3 vJ + 9 vB
+    for v, m in [(0, 0), (1, 1), (2, 2), (0, 0 + 3 * 2 + 9 * 2), (2, 1 + 3 * 0 + 9 * 2), (1, 2 + 3 * 1 + 9 * 0)]:
         s = Solver(9, 7, p, k, wl["gamma"], wl["domain"])
         s.set_params(**STAB)
         s.set_state(*o.get_state())
         dt = s.compute_dt()
-        s.set_tiles(v, v)
+        s.set_tiles(v, m)
         for _ in range(2):
             st, _ = s.strang_step(dt)
             assert st == 0
@@ -87,7 +88,7 @@ def test_tile_variants_bitwise(pk):
             ref = out
         else:
             for a, b in zip(out, ref):
-                assert np.array_equal(a, b), (pk, v)
+                assert np.array_equal(a, b), (pk, v, m)
 
 
 def test_autotune_keeps_state():
