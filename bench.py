@@ -120,7 +120,7 @@ def b_nodes_flops(p, k):
     n, mm, mL = p + 1, k + 1, k + 2
     lid, mid = mL == n, mm == n
     bx = (0 if lid else mm * n * mL) + n * n * mm
-    by = mL * n * mm + (0 if lid else n * n * mL)
+    by = mL * n * mm if lid else mm * n * mL + n * n * mm  # columns to the DG y-nodes first
     bz = 0 if mid else mm * n * mm + n * n * mm
     return 2 * (bx + by + bz)
 

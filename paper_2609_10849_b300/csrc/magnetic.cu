@@ -354,8 +354,8 @@ struct LE_ {  // per-element shared-memory offsets (doubles), with region reuse
   static constexpr int CGZ = CYY + D::mL * D::n;         // u_z columns to Gauss y: [b < mm][i < n]
   static constexpr int BYL = CGZ + D::mm * D::n;         // By rows (GLL y) to GLL x (= By at W)
   static constexpr int BZG = BYL + D::NW;                // Bz rows to Gauss x
-  static constexpr int BZL = BZG + D::NZ;                // Bz rows to GLL(k+1) x
-  static constexpr int RB_END = BZL + D::mm * D::mL;
+  static constexpr int BZC = BZG + D::NZ;                // Bz columns to Gauss y: [b < mm][a < mm]
+  static constexpr int RB_END = BZC + D::NZ;
   // transposed passes of the Lorentz load: s_x (N_y and W, GLL(k+1) x) y-first into VX [j][a];
   // s_y (N_x and W, GLL(k+1) y) x-first into HY [b][i]; s_z: N_x y-first into VZ1 [j][a],
   // N_y x-first into HZ [b][i] (each family in its cheaper order)
@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(256) k_mag_E(
   // cross products need: E_x = -(u_y B_z - u_z B_y) at N_x, E_y = -(u_z B_x -
   // u_x B_z) at N_y, E_z = -(u_x B_y - u_y B_x) at W
   constexpr int NUZ = R2 ? 0 : D::n * D::mm, NUL = 2 * D::n * D::mL;
-  constexpr int I2 = 2 * NUZ + NUL + D::NW + (R2 ? 0 : D::NZ + D::mm * D::mL);
+  constexpr int I2 = 2 * NUZ + NUL + D::NW + (R2 ? 0 : 2 * D::NZ);
   FLAT(I2) {
     int it = idx / D::EB, e = idx % D::EB, k = min(k0 + e, M.K - 1);
     if constexpr (!R2) {
@@ -500,12 +500,12 @@ __global__ void __launch_bounds__(256) k_mag_E(
         continue;
       }
       it -= D::NZ;
-      {  // Bz rows to GLL(k+1) x
-        int j = it / D::mL, a = it % D::mL;
+      {  // Bz columns to Gauss y (for N_y: y first, then x)
+        int b = it / D::mm, a = it % D::mm;
         double v = 0.0;
 #pragma unroll
-        for (int i = 0; i < D::mm; ++i) v = fma(T.M_L[a][i], SM(O::BZ, j * D::mm + i), v);
-        SM(O::BZL, it) = v;
+        for (int j = 0; j < D::mm; ++j) v = fma(T.M_G[b][j], SM(O::BZ, j * D::mm + a), v);
+        SM(O::BZC, it) = v;
       }
     }
   }
@@ -589,11 +589,11 @@ __global__ void __launch_bounds__(256) k_mag_E(
         continue;
       }
       it -= D::NX;
-      if (it < D::NY) {  // Bz at N_y: GLL(k) y -> Gauss y
+      if (it < D::NY) {  // Bz at N_y: the Gauss-y columns to GLL(k+1) x
         int b = it / D::mL, a = it % D::mL;
         double v = 0.0;
 #pragma unroll
-        for (int j = 0; j < D::mm; ++j) v = fma(T.M_G[b][j], SM(O::BZL, j * D::mL + a), v);
+        for (int c = 0; c < D::mm; ++c) v = fma(T.M_L[a][c], SM(O::BZC, b * D::mm + c), v);
         SM(O::BZNY, it) = v;
         continue;
       }

@@ -974,7 +974,7 @@ __global__ void k_ar_elem(const double* __restrict__ rho, const double* __restri
         b2[j * n + i] = v * v;
       }
   }
-  {
+  if constexpr (LID) {  // By rows to the DG x-nodes; GLL(k+1) y is the DG rule (copy)
     double ty[mL][n];
 #pragma unroll
     for (int b = 0; b < mL; ++b)
@@ -988,13 +988,25 @@ __global__ void k_ar_elem(const double* __restrict__ rho, const double* __restri
 #pragma unroll
     for (int j = 0; j < n; ++j)
 #pragma unroll
+      for (int i = 0; i < n; ++i) b2[j * n + i] = fma(ty[j][i], ty[j][i], b2[j * n + i]);
+  } else {  // By columns to the DG y-nodes, then the x-pass (the cheaper order)
+    double tc[mm][n];
+#pragma unroll
+    for (int a = 0; a < mm; ++a)
+#pragma unroll
+      for (int j = 0; j < n; ++j) {
+        double v = 0.0;
+#pragma unroll
+        for (int b = 0; b < mL; ++b) v = fma(T->L_P[j][b], by[b][a], v);
+        tc[a][j] = v;
+      }
+#pragma unroll
+    for (int j = 0; j < n; ++j)
+#pragma unroll
       for (int i = 0; i < n; ++i) {
         double v = 0.0;
-        if constexpr (LID) v = ty[j][i];
-        else {
 #pragma unroll
-          for (int b = 0; b < mL; ++b) v = fma(T->L_P[j][b], ty[b][i], v);
-        }
+        for (int a = 0; a < mm; ++a) v = fma(T->G_P[i][a], tc[a][j], v);
         b2[j * n + i] = fma(v, v, b2[j * n + i]);
       }
   }
@@ -1336,9 +1348,12 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
     sB[e][w] = v;
   }
   __syncthreads();
-  // x-passes onto the DG x-nodes: Bx rows (Gauss y), By rows (GLL(k+1) y), Bz rows (GLL(k) y);
-  // items element-fastest, so that a warp's items come from one family (one branch)
-  constexpr int NT = mm * n + mL * n + (R2 ? 0 : mm * n);
+  // first passes: Bx rows (Gauss y) to the DG x-nodes; By (Gauss x, GLL(k+1) y) columns to
+  // the DG y-nodes, the cheaper order (at k = p - 1, where GLL(k+1) y is the DG rule, its rows
+  // to the DG x-nodes instead, the y-pass being a copy); Bz rows (GLL(k) y) to the DG x-nodes.
+  // Items element-fastest, so that a warp's items come from one family (one branch)
+  constexpr int NBY = LID ? mL * n : mm * n;
+  constexpr int NT = mm * n + NBY + (R2 ? 0 : mm * n);
   for (int it = tid; it < EB * NT; it += TH) {
     const int e = it % EB, w = it / EB;
     double v = 0.0;
@@ -1349,12 +1364,19 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
 #pragma unroll
         for (int a = 0; a < mL; ++a) v = fma(T->L_P[ii][a], sB[e][b * mL + a], v);
       }
-    } else if (w < mm * n + mL * n) {
-      const int r = w - mm * n, b = r / n, ii = r % n;
+    } else if (w < mm * n + NBY) {
+      const int r = w - mm * n;
+      if constexpr (LID) {  // By rows b to the DG x-nodes
+        const int b = r / n, ii = r % n;
 #pragma unroll
-      for (int a = 0; a < mm; ++a) v = fma(T->G_P[ii][a], sB[e][mm * mL + b * mm + a], v);
+        for (int a = 0; a < mm; ++a) v = fma(T->G_P[ii][a], sB[e][mm * mL + b * mm + a], v);
+      } else {  // By columns a to the DG y-nodes jj
+        const int a = r / n, jj = r % n;
+#pragma unroll
+        for (int b = 0; b < mL; ++b) v = fma(T->L_P[jj][b], sB[e][mm * mL + b * mm + a], v);
+      }
     } else {
-      const int r = w - mm * n - mL * n, b = r / n, ii = r % n;
+      const int r = w - mm * n - NBY, b = r / n, ii = r % n;
       if constexpr (MID) v = sB[e][2 * mm * mL + b * mm + ii];
       else {
 #pragma unroll
@@ -1369,15 +1391,15 @@ __global__ void __launch_bounds__(VCfg<P>::threads) k_vel_oe(const double* __res
 #pragma unroll
     for (int b = 0; b < mm; ++b) bx = fma(T->G_P[j][b], sT[el][b * n + i], bx);
     if constexpr (LID) by = sT[el][mm * n + j * n + i];
-    else {
+    else {  // x-pass of the By columns at DG row j
 #pragma unroll
-      for (int b = 0; b < mL; ++b) by = fma(T->L_P[j][b], sT[el][mm * n + b * n + i], by);
+      for (int a = 0; a < mm; ++a) by = fma(T->G_P[i][a], sT[el][mm * n + a * n + j], by);
     }
     if constexpr (!R2) {
-      if constexpr (MID) bz = sT[el][mm * n + mL * n + j * n + i];
+      if constexpr (MID) bz = sT[el][mm * n + NBY + j * n + i];
       else {
 #pragma unroll
-        for (int b = 0; b < mm; ++b) bz = fma(T->M_P[j][b], sT[el][mm * n + mL * n + b * n + i], bz);
+        for (int b = 0; b < mm; ++b) bz = fma(T->M_P[j][b], sT[el][mm * n + NBY + b * n + i], bz);
       }
     }
     const double va = fsqrt(fma(bx, bx, fma(by, by, bz * bz)) * rcp(r_));
